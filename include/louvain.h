@@ -1,0 +1,158 @@
+/*
+ * louvain.h -- C ABI of the GB300 (sm_103a) Louvain library.
+ *
+ * The library runs the data-parallel hot path of the Louvain method as
+ * studied in arXiv 2501.19004 ("CPU vs. GPU for Community Detection:
+ * Performance Insights from GVE-Louvain and nu-Louvain"): the local-moving
+ * phase (Sec. 4.2.2, Algorithm 2 / Algorithm 5), the aggregation phase
+ * (Sec. 4.2.3, Algorithm 3 / Algorithm 6) and the pass loop around them
+ * (Sec. 4.2.1, Algorithm 1 / Algorithm 4), with modularity as defined by
+ * Eq. 1 and delta-modularity by Eq. 2 (Sec. 3.2).
+ *
+ * Schedule.  The paper moves vertices asynchronously; this library fixes one
+ * deterministic semi-synchronous schedule so that every run is reproducible:
+ * in iteration t of pass p, vertex i belongs to bucket
+ *     fmix32(i ^ fmix32(fold(seed) ^ (((p << 8) | t) * 0x9E3779B1))) mod B
+ * (fmix32 = the MurmurHash3 finaliser, fold(s) = low32(s) ^ high32(s)).
+ * Bucket by bucket, the unprocessed vertices of the bucket are marked
+ * processed, each picks the neighbouring community c maximising
+ *     s(c) = 2m K_{i->c} - K_i Sigma_c            (= 2m^2 dQ + const, Eq. 2)
+ * against a snapshot of the memberships and community weights (ties go to
+ * the lowest id), moves if s(c*) > 2m K_{i->d} - K_i (Sigma_d - K_i) and
+ * Pick-Less mode (Sec. 4.3.1) does not forbid c* > d, and then all moves of
+ * the bucket are applied and the neighbours of movers are marked
+ * unprocessed (vertex pruning, Sec. 4.1.6).  An iteration ends the phase when
+ * 2 * sum(gains) / (2m)^2 <= tau.  All of this is exact integer arithmetic.
+ *
+ * Conventions for every function below:
+ *   - A status code is returned; nothing aborts, exits or traps.  On error,
+ *     louvain_last_error() describes the failure.
+ *   - Arrays passed in are borrowed for the duration of the call (device
+ *     graphs: until louvain_destroy).  Outputs are caller-owned.
+ *   - `stream` arguments are cudaStream_t values passed as void*; NULL means
+ *     the legacy default stream.
+ */
+#ifndef LOUVAIN_GB300_H
+#define LOUVAIN_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct louvain_ctx louvain_ctx; /* opaque, library-owned */
+
+typedef enum {
+  LOUVAIN_OK = 0,
+  LOUVAIN_E_INVAL = 1,          /* bad argument or malformed CSR */
+  LOUVAIN_E_NOMEM = 2,          /* device or host allocation failed */
+  LOUVAIN_E_CUDA = 3,           /* a CUDA call failed (see louvain_last_error) */
+  LOUVAIN_E_HASH_OVERFLOW = 4,  /* a hashtable probe sequence exceeded its bound
+                                   (the paper's "failed" result of Algorithm 7) */
+  LOUVAIN_E_TIMEOUT = 5,        /* a bounded device-side wait gave up */
+  LOUVAIN_E_OVERFLOW = 6,       /* 2m >= 2^32: scores would not fit in int64 */
+  LOUVAIN_E_STATE = 7           /* call out of order (e.g. memberships before run) */
+} louvain_status;
+
+/* Undirected weighted graph in CSR form (Sec. 3: G(V, E, w) with w_ij = w_ji;
+ * Table 2 counts both directions of every edge, and so does nnz).
+ *   offsets [n+1] int64, offsets[0] = 0, non-decreasing, offsets[n] = nnz
+ *   cols    [nnz] int32, 0 <= cols[k] < n; a self-loop is stored once
+ *   weights [nnz] int32 > 0, or NULL for unit weights
+ * on_device = 1: device pointers, borrowed until louvain_destroy;
+ * on_device = 0: host pointers, copied to the device by louvain_create. */
+typedef struct {
+  int64_t n;
+  int64_t nnz;
+  const int64_t *offsets;
+  const int32_t *cols;
+  const int32_t *weights;
+  int32_t on_device;
+} louvain_graph;
+
+typedef enum { LOUVAIN_MODE_PLAIN = 0, LOUVAIN_MODE_LEARNED = 1 } louvain_mode;
+
+/* Run parameters.  Defaults (louvain_config_default) are the paper's:
+ * MAX_PASSES 10 and MAX_ITERATIONS 20 (Sec. 4.3 item 2, Sec. 4.1.2),
+ * tau = 0.01 (Sec. 4.1.4), TOLERANCE_DROP 10 (Sec. 4.1.3), tau_agg 0.8
+ * (Sec. 4.1.5), Pick-Less every rho = 4 iterations (Sec. 4.3.1). */
+typedef struct {
+  int32_t max_passes;
+  int32_t max_iterations;        /* 1 .. 255 */
+  double tolerance;
+  double tolerance_drop;
+  double aggregation_tolerance;
+  int32_t pickless_period;       /* rho; 0 disables Pick-Less mode */
+  int32_t buckets;               /* B >= 1 of the deterministic schedule (4) */
+  uint64_t schedule_seed;
+  int32_t mode;                  /* louvain_mode */
+  const float *model;            /* LEARNED: host pointer to the predictor's
+                                    parameters (louvain_model_size floats) */
+  float skip_threshold;          /* LEARNED: skip a vertex when p < threshold */
+  int32_t record_pass_modularity;/* 1: compute Q after every pass (stats) */
+  int32_t check_symmetry;        /* 1: louvain_create verifies w_ij = w_ji (host graphs) */
+} louvain_config;
+
+/* Fill `cfg` with the defaults above (mode PLAIN, seed 0). */
+void louvain_config_default(louvain_config *cfg);
+
+/* Validate the graph (offsets monotone, ids in range, weights > 0,
+ * optional symmetry), copy or borrow it, and allocate all device workspace
+ * (stream-ordered on `stream`).  Returns LOUVAIN_E_OVERFLOW if the total
+ * weight 2m is 2^32 or more.  *out receives the context. */
+louvain_status louvain_create(const louvain_graph *graph, const louvain_config *cfg, void *stream,
+                              louvain_ctx **out);
+
+/* Run the whole method (all passes and the final modularity) on the
+ * context's stream; returns when the result is ready. */
+louvain_status louvain_run(louvain_ctx *ctx);
+
+/* Final modularity Q (Eq. 1) of the last run, as a double, and optionally
+ * its exact numerator 2m*S_in - sum_c Sigma_c^2 and denominator (2m)^2 as
+ * (hi, lo) pairs of a 128-bit integer (either pointer may be NULL). */
+louvain_status louvain_modularity(const louvain_ctx *ctx, double *q, int64_t *num_hi_lo,
+                                  int64_t *den_hi_lo);
+
+/* Final community of every input vertex, dense ids in [0, |Gamma|) ordered
+ * like the first-level ids.  `out` is caller-owned [n], host or device. */
+louvain_status louvain_memberships(const louvain_ctx *ctx, int32_t *out, int32_t out_on_device);
+
+/* Per-iteration and per-pass records of the last run, same layout as the CPU
+ * oracle's: iter_stats[max_passes][max_iterations][4] = (vertices evaluated,
+ * moves, gain_hi, gain_lo); pass_stats[max_passes][6] = (n', nnz', l_i,
+ * |Gamma|, Qnum_hi, Qnum_lo); summary[8] = (passes, |Gamma|, Qnum hi/lo,
+ * Qden hi/lo, 2m, exit reason 0 max passes / 1 converged / 2 low shrink).
+ * Any pointer may be NULL. */
+louvain_status louvain_records(const louvain_ctx *ctx, int64_t *iter_stats, int64_t *pass_stats,
+                               int64_t *summary);
+
+/* JSON object with timings per phase and per pass (CUDA events), counts and
+ * the memory footprint.  Returns LOUVAIN_E_INVAL if `cap` is too small. */
+louvain_status louvain_stats(const louvain_ctx *ctx, char *json, size_t cap);
+
+/* Release all device memory of the context (stream-ordered). */
+void louvain_destroy(louvain_ctx *ctx);
+
+/* Description of the last error on this context (or of the last failed
+ * louvain_create when ctx is NULL).  Never NULL. */
+const char *louvain_last_error(const louvain_ctx *ctx);
+
+/* Modularity (Eq. 1) of an arbitrary membership on a graph, computed on the
+ * device.  graph and membership are both device or both host arrays
+ * (graph->on_device); membership ids lie in [0, n).  q and the exact
+ * numerator/denominator (hi, lo) as in louvain_modularity. */
+louvain_status louvain_modularity_of(const louvain_graph *graph, const int32_t *membership, void *stream,
+                                     double *q, int64_t *num_hi_lo, int64_t *den_hi_lo);
+
+/* Number of floats of the learned predictor's parameters (8->32->32->1 MLP). */
+int64_t louvain_model_size(void);
+
+/* Library build description (architecture, version). */
+const char *louvain_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,138 @@
+// Device-side building blocks shared by the Louvain kernels (sm_103a).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lv {
+
+constexpr int32_t kEmpty = -1;          // empty hashtable key
+constexpr int kWarp = 32;
+
+// Weight representations of a CSR: unit (no array), int32 (input graph),
+// int64 (super-vertex graphs, whose weights can exceed 2^31).
+enum WKind : int { W_UNIT = 0, W_I32 = 1, W_I64 = 2 };
+
+template <int WK>
+__device__ __forceinline__ int64_t load_w(const void *w, int64_t e) {
+  if constexpr (WK == W_UNIT) {
+    return 1;
+  } else if constexpr (WK == W_I32) {
+    return (int64_t)__ldg((const int32_t *)w + e);
+  } else {
+    return (int64_t)__ldg((const long long *)w + e);
+  }
+}
+
+// Current graph G' as a "holey" CSR: row i occupies [begin[i], end[i]).
+// For a compact CSR end = begin + 1.
+struct GView {
+  int64_t n;
+  const int64_t *begin;
+  const int64_t *end;
+  const int32_t *col;
+  const void *w;
+};
+
+// Error bits written by kernels (never a trap).
+enum ErrBits : unsigned long long { ERR_HASH = 1ull, ERR_RANGE = 2ull, ERR_TIMEOUT = 4ull };
+
+// Small device-resident counters block.
+struct Counters {
+  unsigned long long bin_count[8];  // per-bucket bin sizes (move) / per-pass bins (merge)
+  unsigned long long selected;      // vertices taken into the bucket (incl. degree 0)
+  unsigned long long movers;        // decisions to move in this bucket
+  unsigned long long it_gain_lo;    // iteration: sum of low 32 bits of the gains
+  unsigned long long it_gain_hi;    // iteration: sum of high 32 bits of the gains
+  unsigned long long it_moves;
+  unsigned long long it_evaluated;
+  unsigned long long it_skipped;    // learned mode: flagged vertices skipped by the predictor
+  unsigned long long maxdeg;
+  unsigned long long nnz_out;       // entries written by aggregation
+  unsigned long long error;
+  unsigned long long q_sin;         // modularity: sum of internal weights
+  unsigned long long q_tot_lo;      // modularity: sum of low 32 bits of Sigma_c^2
+  unsigned long long q_tot_hi;      // modularity: sum of high 32 bits of Sigma_c^2
+  unsigned long long scan_total[4]; // totals of the aggregation scans
+  unsigned long long pad[4];
+};
+
+// MurmurHash3 finaliser (Appleby, public domain).
+__host__ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h;
+}
+
+// Salt of the bucket hash for (pass, iteration); see include/louvain.h.
+__host__ __device__ __forceinline__ uint32_t bucket_salt(int pass, int iter, uint64_t seed) {
+  uint32_t fold = (uint32_t)seed ^ (uint32_t)(seed >> 32);
+  uint32_t pt = ((uint32_t)pass << 8) | ((uint32_t)iter & 0xFFu);
+  return fmix32(fold ^ (pt * 0x9E3779B1u));
+}
+
+// Multiplicative (Fibonacci) hash of a community id into a power-of-two
+// table, with one xor-shift so that the low bits see the high ones.
+__device__ __forceinline__ uint32_t slot_of(int32_t key, uint32_t mask) {
+  uint32_t h = (uint32_t)key * 0x9E3779B1u;
+  return (h ^ (h >> 15)) & mask;
+}
+
+// (score, id) pair ordering of the argmax: larger score first, then lower id.
+__device__ __forceinline__ bool better(long long s1, int32_t c1, long long s2, int32_t c2) {
+  return s1 > s2 || (s1 == s2 && c1 < c2);
+}
+
+__device__ __forceinline__ void warp_argmax(long long &s, int32_t &c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    long long s2 = __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    int32_t c2 = __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    if (better(s2, c2, s, c)) { s = s2; c = c2; }
+  }
+}
+
+__device__ __forceinline__ long long warp_sum(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ unsigned long long as_ull(long long v) { return (unsigned long long)v; }
+
+// Exact accumulation of non-negative 64-bit gains into two 64-bit sums
+// (low and high 32-bit halves), reduced per warp before the global atomics.
+__device__ __forceinline__ void flush_gains(unsigned long long lo, unsigned long long hi,
+                                            unsigned long long moves, Counters *ctr) {
+  lo = warp_sum_u(lo);
+  hi = warp_sum_u(hi);
+  moves = warp_sum_u(moves);
+  if ((threadIdx.x & 31) == 0 && (lo | hi | moves)) {
+    atomicAdd(&ctr->it_gain_lo, lo);
+    atomicAdd(&ctr->it_gain_hi, hi);
+    atomicAdd(&ctr->it_moves, moves);
+  }
+}
+
+// Round up to a power of two (x >= 1).
+__host__ __device__ __forceinline__ uint32_t pow2_at_least(uint64_t x) {
+  uint32_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+}  // namespace lv

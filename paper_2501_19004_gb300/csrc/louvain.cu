@@ -1,0 +1,788 @@
+// Host driver and C ABI of the GB300 Louvain library (include/louvain.h).
+//
+// The pass loop follows Algorithm 1 / Algorithm 4 of arXiv 2501.19004
+// (Sec. 4.2.1 and the Appendix): per pass, vertex weights and identity
+// memberships (pass_init), the local-moving phase (move.cu, Algorithm 5)
+// until the iteration tolerance is met, the convergence and aggregation
+// tolerance tests, renumbering, dendrogram lookup and aggregation (aggr.cu,
+// Algorithm 6), then threshold scaling.  Everything stays on the device; the
+// host only reads a few scalars per iteration (the exact gain sum) and per
+// pass (community count, sizes).
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/louvain.h"
+#include "internal.h"
+
+using namespace lv;
+typedef __int128 i128;
+
+struct PassTiming {
+  cudaEvent_t t0, t1, t2;  // pass start, after local moving, after aggregation
+  bool aggregated;
+};
+
+struct louvain_ctx {
+  louvain_config cfg;
+  cudaStream_t stream = nullptr;
+  int device = 0, num_sms = 0;
+  std::string err;
+
+  int64_t n0 = 0, nnz0 = 0;
+  long long two_m = 0;
+  int weighted = 0;
+  const int64_t *off0 = nullptr;
+  const int32_t *col0 = nullptr;
+  const int32_t *w0 = nullptr;
+
+  // per-vertex state
+  int32_t *C = nullptr, *Cp = nullptr;
+  int64_t *K = nullptr, *Kalt = nullptr, *Sigma = nullptr;
+  uint8_t *flag = nullptr;
+  // local moving
+  int32_t *bins[kNumBins] = {};
+  int32_t *mv_vertex = nullptr, *mv_target = nullptr;
+  // aggregation
+  unsigned long long *cnt = nullptr, *cdeg = nullptr;
+  int64_t *newid = nullptr, *coff = nullptr, *hoff = nullptr, *kcoff = nullptr;
+  int32_t *members = nullptr, *kcnt = nullptr;
+  long long *scan_tmp = nullptr;
+  // ping-pong super-vertex graphs
+  int32_t *pcol[2] = {};
+  int64_t *pw[2] = {}, *pbeg[2] = {}, *pend[2] = {};
+  // hub / large-community hashtable workspace
+  HubWs ws;
+  size_t ws_slots_alloc = 0;
+  // learned predictor
+  float *mlp = nullptr, *feat = nullptr;
+
+  Counters *d_ctr = nullptr;
+  Counters *h_ctr = nullptr;  // pinned
+
+  std::vector<void *> allocs;
+  size_t bytes = 0;
+
+  // results of the last run
+  bool ran = false;
+  double q = 0;
+  i128 qnum = 0, qden = 0;
+  int64_t gamma = 0;
+  int passes = 0, exit_reason = 0;
+  std::vector<int64_t> iter_stats, pass_stats;
+  std::vector<PassTiming> timing;
+  cudaEvent_t run0 = nullptr, run1 = nullptr;
+  double run_ms = 0;
+  long long it_total = 0, moves_total = 0, evaluated_total = 0, skipped_total = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+#define LV_CK(call)                                                                         \
+  do {                                                                                      \
+    cudaError_t e__ = (call);                                                               \
+    if (e__ != cudaSuccess) {                                                               \
+      set_err(x, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e__), __FILE__, __LINE__); \
+      return LOUVAIN_E_CUDA;                                                                \
+    }                                                                                       \
+  } while (0)
+
+void set_err(louvain_ctx *x, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (x) x->err = buf;
+  else g_create_err = buf;
+}
+
+louvain_status dalloc(louvain_ctx *x, void **p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMallocAsync(p, bytes, x->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_err(x, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    return LOUVAIN_E_NOMEM;
+  }
+  x->allocs.push_back(*p);
+  x->bytes += bytes;
+  return LOUVAIN_OK;
+}
+
+template <class T>
+louvain_status dalloc_n(louvain_ctx *x, T **p, int64_t n) {
+  return dalloc(x, (void **)p, (size_t)(n > 0 ? n : 1) * sizeof(T));
+}
+
+void release_pool_threshold(int device) {
+  static bool done[64] = {};
+  if (device < 0 || device >= 64 || done[device]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done[device] = true;
+}
+
+// Warp per row: offsets non-decreasing, columns in range, weights positive;
+// the weight total 2m goes to ctr->q_sin.
+__global__ void k_validate(int64_t n, const int64_t *off, const int32_t *col, const int32_t *w, Counters *ctr) {
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  unsigned long long bad = 0, wsum = 0;
+  for (int64_t i = warp; i < n; i += nw) {
+    const int64_t b = off[i], e = off[i + 1];
+    if (e < b) {
+      bad = 1;
+      continue;
+    }
+    for (int64_t k = b + lane; k < e; k += 32) {
+      const int32_t c = col[k];
+      if (c < 0 || c >= n) bad = 1;
+      const int32_t ww = w ? w[k] : 1;
+      if (ww <= 0) bad = 1;
+      wsum += (unsigned long long)(ww > 0 ? ww : 0);
+    }
+  }
+  if (bad) atomicOr(&ctr->error, (unsigned long long)ERR_RANGE);
+  if (wsum) atomicAdd(&ctr->q_sin, wsum);
+}
+
+// Ensure the global hashtable workspace can hold a table for `distinct`
+// keys in every one of its slices.
+louvain_status ensure_ws(louvain_ctx *x, uint64_t distinct) {
+  const int64_t need = (int64_t)pow2_at_least(2 * (distinct ? distinct : 1));
+  const size_t budget_slots = (size_t)1 << 28;  // 3 GiB of table at most
+  int blocks = 2 * x->num_sms;
+  if ((size_t)need * blocks > budget_slots) blocks = (int)std::max<int64_t>(1, (int64_t)(budget_slots / need));
+  const size_t slots = (size_t)need * blocks;
+  if (slots > x->ws_slots_alloc) {
+    if (x->ws.keys) {
+      cudaFreeAsync(x->ws.keys, x->stream);
+      cudaFreeAsync(x->ws.vals, x->stream);
+      x->allocs.erase(std::remove(x->allocs.begin(), x->allocs.end(), (void *)x->ws.keys), x->allocs.end());
+      x->allocs.erase(std::remove(x->allocs.begin(), x->allocs.end(), (void *)x->ws.vals), x->allocs.end());
+      x->bytes -= x->ws_slots_alloc * 12;
+      x->ws.keys = nullptr;
+      x->ws.vals = nullptr;
+      x->ws_slots_alloc = 0;
+    }
+    louvain_status st;
+    if ((st = dalloc_n(x, &x->ws.keys, (int64_t)slots))) return st;
+    if ((st = dalloc_n(x, &x->ws.vals, (int64_t)slots))) return st;
+    x->ws_slots_alloc = slots;
+  }
+  x->ws.slice = need;
+  x->ws.blocks = (int)std::min<size_t>((size_t)blocks, x->ws_slots_alloc / (size_t)need);
+  return LOUVAIN_OK;
+}
+
+louvain_status read_counters(louvain_ctx *x) {
+  LV_CK(cudaMemcpyAsync(x->h_ctr, x->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, x->stream));
+  LV_CK(cudaStreamSynchronize(x->stream));
+  if (x->h_ctr->error & ERR_HASH) {
+    set_err(x, "hashtable probe bound exceeded (table sizing error)");
+    return LOUVAIN_E_HASH_OVERFLOW;
+  }
+  return LOUVAIN_OK;
+}
+
+void put128(int64_t *dst, i128 v) {
+  dst[0] = (int64_t)(v >> 64);
+  dst[1] = (int64_t)(uint64_t)v;
+}
+
+// Local-moving phase (Algorithm 5) under the bucket schedule; returns l_i.
+louvain_status move_phase(louvain_ctx *x, const GView &g, int wk, int pass, double tau, int *li_out) {
+  const louvain_config &cfg = x->cfg;
+  const i128 den2 = (i128)x->two_m * x->two_m;
+  int li = cfg.max_iterations;
+  for (int t = 0; t < cfg.max_iterations; ++t) {
+    const int rho = cfg.pickless_period;
+    const int pickless = rho > 0 && ((t + rho / 2) % rho) == 0;
+    LV_CK(cudaMemsetAsync(&x->d_ctr->it_gain_lo, 0, 5 * sizeof(unsigned long long), x->stream));
+    MoveArgs a{};
+    a.g = g;
+    a.Cp = x->Cp;
+    a.K = x->K;
+    a.Sigma = x->Sigma;
+    a.flag = x->flag;
+    a.two_m = x->two_m;
+    a.pickless = pickless;
+    a.salt = bucket_salt(pass, t, cfg.schedule_seed);
+    a.nbuckets = (uint32_t)cfg.buckets;
+    for (int k = 0; k < kNumBins; ++k) a.bins[k] = x->bins[k];
+    a.mv_vertex = x->mv_vertex;
+    a.mv_target = x->mv_target;
+    a.ws = x->ws;
+    a.ctr = x->d_ctr;
+    a.mlp = x->mlp;
+    a.feat = x->feat;
+    a.skip_threshold = cfg.skip_threshold;
+    a.learned = cfg.mode == LOUVAIN_MODE_LEARNED;
+    for (int b = 0; b < cfg.buckets; ++b) {
+      LV_CK(cudaMemsetAsync(x->d_ctr, 0, 10 * sizeof(unsigned long long), x->stream));
+      a.bucket = (uint32_t)b;
+      move_bucket(a, wk, x->num_sms, x->stream);
+    }
+    LV_CK(cudaGetLastError());
+    louvain_status st = read_counters(x);
+    if (st) return st;
+    const Counters &h = *x->h_ctr;
+    const i128 gain = ((i128)h.it_gain_hi << 32) + (i128)h.it_gain_lo;
+    if (pass < cfg.max_passes) {
+      int64_t *r = &x->iter_stats[((size_t)pass * cfg.max_iterations + t) * 4];
+      r[0] = (int64_t)h.it_evaluated;
+      r[1] = (int64_t)h.it_moves;
+      put128(r + 2, gain);
+    }
+    x->it_total += 1;
+    x->moves_total += (long long)h.it_moves;
+    x->evaluated_total += (long long)h.it_evaluated;
+    x->skipped_total += (long long)h.it_skipped;
+    const double total = den2 ? (double)(2 * gain) / (double)den2 : 0.0;
+    if (total <= tau) {
+      li = t + 1;
+      break;
+    }
+  }
+  *li_out = li;
+  return LOUVAIN_OK;
+}
+
+louvain_status modularity_into(louvain_ctx *x, const GView &g, int wk, const int32_t *memb, const int64_t *sigma,
+                               int64_t *sigma_scratch, i128 *num, i128 *den) {
+  LV_CK(cudaMemsetAsync(&x->d_ctr->q_sin, 0, 3 * sizeof(unsigned long long), x->stream));
+  modularity_sums(g, wk, memb, sigma, sigma_scratch, x->d_ctr, x->num_sms, x->stream);
+  LV_CK(cudaGetLastError());
+  louvain_status st = read_counters(x);
+  if (st) return st;
+  const Counters &h = *x->h_ctr;
+  const i128 s_tot = ((i128)h.q_tot_hi << 32) + (i128)h.q_tot_lo;
+  *num = (i128)x->two_m * (i128)h.q_sin - s_tot;
+  *den = (i128)x->two_m * x->two_m;
+  return LOUVAIN_OK;
+}
+
+louvain_status run_impl(louvain_ctx *x) {
+  const louvain_config &cfg = x->cfg;
+  cudaStream_t s = x->stream;
+  x->ran = false;
+  x->iter_stats.assign((size_t)std::max(cfg.max_passes, 1) * cfg.max_iterations * 4, 0);
+  x->pass_stats.assign((size_t)std::max(cfg.max_passes, 1) * 6, 0);
+  x->it_total = x->moves_total = x->evaluated_total = x->skipped_total = 0;
+  for (auto &pt : x->timing) pt.aggregated = false;
+  LV_CK(cudaEventRecord(x->run0, s));
+  LV_CK(cudaMemsetAsync(x->d_ctr, 0, sizeof(Counters), s));
+
+  GView g{x->n0, x->off0, x->off0 + 1, x->col0, x->w0};
+  int wk = x->weighted ? W_I32 : W_UNIT;
+  iota_i32(x->C, x->n0, x->num_sms, s);
+  double tau = cfg.tolerance;
+  bool pending = false, exhausted = true;
+  int exit_reason = 0, passes = 0, slot = 0;
+  int64_t nnzp = x->nnz0;
+  bool have_pass_state = false;
+  louvain_status st;
+  for (int p = 0; p < cfg.max_passes; ++p) {
+    PassTiming &pt = x->timing[p];
+    LV_CK(cudaEventRecord(pt.t0, s));
+    LV_CK(cudaMemsetAsync(&x->d_ctr->maxdeg, 0, sizeof(unsigned long long), s));
+    pass_init(g, wk, p == 0, x->K, x->Sigma, x->Cp, x->flag, x->d_ctr, x->num_sms, s);
+    LV_CK(cudaGetLastError());
+    if ((st = read_counters(x))) return st;
+    {
+      uint64_t md = x->h_ctr->maxdeg;
+      if (md > kBlockMaxDeg) {
+        if ((st = ensure_ws(x, std::min<uint64_t>(md, (uint64_t)g.n)))) return st;
+      } else {
+        x->ws.blocks = 0;
+      }
+    }
+    int li = 0;
+    if ((st = move_phase(x, g, wk, p, tau, &li))) return st;
+    have_pass_state = true;
+    LV_CK(cudaEventRecord(pt.t1, s));
+    ++passes;
+    AggArgs aa{};
+    aa.g = g;
+    aa.wkind = wk;
+    aa.Cp = x->Cp;
+    aa.Sigma = x->Sigma;
+    aa.Knew = x->Kalt;
+    aa.cnt = x->cnt;
+    aa.cdeg = x->cdeg;
+    aa.newid = x->newid;
+    aa.coff = x->coff;
+    aa.hoff = x->hoff;
+    aa.members = x->members;
+    aa.kcoff = x->kcoff;
+    aa.kcnt = x->kcnt;
+    for (int k = 0; k < kNumBins; ++k) aa.mbins[k] = x->bins[k];
+    aa.obegin = x->pbeg[slot];
+    aa.oend = x->pend[slot];
+    aa.ocol = x->pcol[slot];
+    aa.ow = x->pw[slot];
+    aa.ctr = x->d_ctr;
+    aa.scan_tmp = x->scan_tmp;
+    agg_count_scan(aa, x->num_sms, s);
+    LV_CK(cudaGetLastError());
+    if ((st = read_counters(x))) return st;
+    const int64_t gamma = (int64_t)x->h_ctr->scan_total[0];
+    aa.gamma = gamma;
+    {
+      int64_t *r = &x->pass_stats[(size_t)p * 6];
+      r[0] = g.n;
+      r[1] = nnzp;
+      r[2] = li;
+      r[3] = gamma;
+      if (cfg.record_pass_modularity) {
+        i128 qn, qd;
+        if ((st = modularity_into(x, g, wk, x->Cp, x->Sigma, nullptr, &qn, &qd))) return st;
+        put128(r + 4, qn);
+      }
+    }
+    if (li <= 1) {  // globally converged
+      pending = true;
+      exhausted = false;
+      exit_reason = 1;
+      break;
+    }
+    if ((double)gamma / (double)g.n > cfg.aggregation_tolerance) {  // low shrink
+      pending = true;
+      exhausted = false;
+      exit_reason = 2;
+      break;
+    }
+    LV_CK(cudaMemsetAsync(&x->d_ctr->bin_count[4], 0, 4 * sizeof(unsigned long long), s));
+    LV_CK(cudaMemsetAsync(&x->d_ctr->maxdeg, 0, sizeof(unsigned long long), s));
+    agg_scatter_compact(aa, x->num_sms, s);
+    dendrogram_lookup(x->C, x->Cp, x->n0, x->num_sms, s);
+    LV_CK(cudaGetLastError());
+    if ((st = read_counters(x))) return st;
+    {
+      uint64_t md = x->h_ctr->maxdeg;
+      if (x->h_ctr->bin_count[7] > 0) {
+        if ((st = ensure_ws(x, std::min<uint64_t>(md, (uint64_t)gamma)))) return st;
+        aa.ws = x->ws;
+      } else {
+        aa.ws.blocks = 0;
+      }
+    }
+    LV_CK(cudaMemsetAsync(&x->d_ctr->nnz_out, 0, sizeof(unsigned long long), s));
+    agg_merge(aa, gamma, x->num_sms, s);
+    LV_CK(cudaGetLastError());
+    if ((st = read_counters(x))) return st;
+    LV_CK(cudaEventRecord(pt.t2, s));
+    pt.aggregated = true;
+    nnzp = (int64_t)x->h_ctr->nnz_out;
+    std::swap(x->K, x->Kalt);  // K of the super-vertices
+    g = GView{gamma, x->pbeg[slot], x->pend[slot], x->pcol[slot], x->pw[slot]};
+    wk = W_I64;
+    slot ^= 1;
+    tau /= cfg.tolerance_drop;
+    have_pass_state = false;
+  }
+  (void)exhausted;
+  if (pending) {
+    dendrogram_lookup(x->C, x->Cp, x->n0, x->num_sms, s);
+  } else {
+    // identity memberships on the current graph (after max passes, or none)
+    LV_CK(cudaMemsetAsync(&x->d_ctr->maxdeg, 0, sizeof(unsigned long long), s));
+    pass_init(g, wk, passes == 0, x->K, x->Sigma, x->Cp, x->flag, x->d_ctr, x->num_sms, s);
+    have_pass_state = true;
+  }
+  (void)have_pass_state;
+  i128 qn = 0, qd = 0;
+  if ((st = modularity_into(x, g, wk, x->Cp, x->Sigma, nullptr, &qn, &qd))) return st;
+  renumber_dense(x->C, x->n0, x->n0, x->cnt, x->newid, x->scan_tmp, &x->d_ctr->scan_total[3], x->num_sms, s);
+  LV_CK(cudaEventRecord(x->run1, s));
+  LV_CK(cudaGetLastError());
+  if ((st = read_counters(x))) return st;
+  x->gamma = (int64_t)x->h_ctr->scan_total[3];
+  x->qnum = qn;
+  x->qden = qd;
+  x->q = qd ? (double)qn / (double)qd : 0.0;
+  x->passes = passes;
+  x->exit_reason = exit_reason;
+  float ms = 0;
+  LV_CK(cudaEventElapsedTime(&ms, x->run0, x->run1));
+  x->run_ms = ms;
+  x->ran = true;
+  return LOUVAIN_OK;
+}
+
+louvain_status validate_config(const louvain_config *c) {
+  if (!c) return LOUVAIN_E_INVAL;
+  if (c->max_passes < 0 || c->max_passes > 64 || c->max_iterations < 1 || c->max_iterations > 255) return LOUVAIN_E_INVAL;
+  if (c->buckets < 1 || c->pickless_period < 0) return LOUVAIN_E_INVAL;
+  if (!(c->tolerance >= 0) || !(c->tolerance_drop > 0) || !(c->aggregation_tolerance >= 0)) return LOUVAIN_E_INVAL;
+  if (c->mode != LOUVAIN_MODE_PLAIN && c->mode != LOUVAIN_MODE_LEARNED) return LOUVAIN_E_INVAL;
+  if (c->mode == LOUVAIN_MODE_LEARNED && !c->model) return LOUVAIN_E_INVAL;
+  return LOUVAIN_OK;
+}
+
+// Host-side symmetry check: the multiset of entries (i, j, w) equals the
+// multiset of their reversals (j, i, w).
+bool host_symmetric(int64_t n, const int64_t *off, const int32_t *col, const int32_t *w) {
+  struct E {
+    int32_t a, b, w;
+    bool operator<(const E &o) const { return a != o.a ? a < o.a : b != o.b ? b < o.b : w < o.w; }
+    bool operator!=(const E &o) const { return a != o.a || b != o.b || w != o.w; }
+  };
+  std::vector<E> fwd, rev;
+  fwd.reserve((size_t)off[n]);
+  rev.reserve((size_t)off[n]);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = off[i]; k < off[i + 1]; ++k) {
+      const int32_t ww = w ? w[k] : 1;
+      fwd.push_back({(int32_t)i, col[k], ww});
+      rev.push_back({col[k], (int32_t)i, ww});
+    }
+  std::sort(fwd.begin(), fwd.end());
+  std::sort(rev.begin(), rev.end());
+  for (size_t k = 0; k < fwd.size(); ++k)
+    if (fwd[k] != rev[k]) return false;
+  return true;
+}
+
+louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg, void *stream, louvain_ctx **out,
+                            bool light = false) {
+  *out = nullptr;
+  if (!graph || !cfg) {
+    set_err(nullptr, "null graph or config");
+    return LOUVAIN_E_INVAL;
+  }
+  if (validate_config(cfg)) {
+    set_err(nullptr, "invalid configuration");
+    return LOUVAIN_E_INVAL;
+  }
+  const int64_t n = graph->n, nnz = graph->nnz;
+  if (n < 0 || nnz < 0 || n > INT32_MAX || (n > 0 && !graph->offsets) || (nnz > 0 && !graph->cols) ||
+      (n == 0 && nnz != 0)) {
+    set_err(nullptr, "bad graph sizes or pointers");
+    return LOUVAIN_E_INVAL;
+  }
+  if (!graph->on_device && n > 0) {
+    const int64_t *off = graph->offsets;
+    if (off[0] != 0 || off[n] != nnz) {
+      set_err(nullptr, "offsets[0] must be 0 and offsets[n] must equal nnz");
+      return LOUVAIN_E_INVAL;
+    }
+    if (cfg->check_symmetry && !host_symmetric(n, off, graph->cols, graph->weights)) {
+      set_err(nullptr, "graph is not symmetric (w_ij != w_ji)");
+      return LOUVAIN_E_INVAL;
+    }
+  }
+  louvain_ctx *x = new louvain_ctx();
+  x->cfg = *cfg;
+  x->stream = (cudaStream_t)stream;
+  x->n0 = n;
+  x->nnz0 = nnz;
+  x->weighted = graph->weights != nullptr;
+  auto fail = [&](louvain_status st) {
+    g_create_err = x->err;
+    louvain_destroy(x);
+    return st;
+  };
+  if (cudaGetDevice(&x->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&x->num_sms, cudaDevAttrMultiProcessorCount, x->device) != cudaSuccess) {
+    set_err(x, "no CUDA device");
+    return fail(LOUVAIN_E_CUDA);
+  }
+  release_pool_threshold(x->device);
+  louvain_status st;
+  const int64_t nv = std::max<int64_t>(n, 1);
+  // input graph
+  if (graph->on_device) {
+    x->off0 = graph->offsets;
+    x->col0 = graph->cols;
+    x->w0 = graph->weights;
+  } else {
+    int64_t *o;
+    int32_t *c, *w = nullptr;
+    if ((st = dalloc_n(x, &o, n + 1)) || (st = dalloc_n(x, &c, nnz))) return fail(st);
+    if (x->weighted && (st = dalloc_n(x, &w, nnz))) return fail(st);
+    if (n > 0 && cudaMemcpyAsync(o, graph->offsets, (size_t)(n + 1) * 8, cudaMemcpyHostToDevice, x->stream)) {
+      set_err(x, "copy of offsets failed");
+      return fail(LOUVAIN_E_CUDA);
+    }
+    if (nnz > 0 && cudaMemcpyAsync(c, graph->cols, (size_t)nnz * 4, cudaMemcpyHostToDevice, x->stream)) {
+      set_err(x, "copy of cols failed");
+      return fail(LOUVAIN_E_CUDA);
+    }
+    if (w && nnz > 0 && cudaMemcpyAsync(w, graph->weights, (size_t)nnz * 4, cudaMemcpyHostToDevice, x->stream)) {
+      set_err(x, "copy of weights failed");
+      return fail(LOUVAIN_E_CUDA);
+    }
+    x->off0 = o;
+    x->col0 = c;
+    x->w0 = w;
+  }
+  if (cudaMallocHost((void **)&x->h_ctr, sizeof(Counters)) != cudaSuccess) {
+    set_err(x, "pinned allocation failed");
+    return fail(LOUVAIN_E_NOMEM);
+  }
+  if ((st = dalloc(x, (void **)&x->d_ctr, sizeof(Counters)))) return fail(st);
+  if (cudaMemsetAsync(x->d_ctr, 0, sizeof(Counters), x->stream)) return fail(LOUVAIN_E_CUDA);
+  // validation and 2m
+  if (n > 0) {
+    int grid = (int)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)x->num_sms * 16);
+    k_validate<<<grid, 256, 0, x->stream>>>(n, x->off0, x->col0, x->w0, x->d_ctr);
+    if (cudaGetLastError() != cudaSuccess) {
+      set_err(x, "validation kernel failed to launch");
+      return fail(LOUVAIN_E_CUDA);
+    }
+    if (graph->on_device) {
+      int64_t ends[2];
+      cudaMemcpyAsync(&ends[0], x->off0, 8, cudaMemcpyDeviceToHost, x->stream);
+      cudaMemcpyAsync(&ends[1], x->off0 + n, 8, cudaMemcpyDeviceToHost, x->stream);
+      if (cudaStreamSynchronize(x->stream) != cudaSuccess) {
+        set_err(x, "stream error during validation");
+        return fail(LOUVAIN_E_CUDA);
+      }
+      if (ends[0] != 0 || ends[1] != nnz) {
+        set_err(x, "offsets[0] must be 0 and offsets[n] must equal nnz");
+        return fail(LOUVAIN_E_INVAL);
+      }
+    }
+    if (cudaMemcpyAsync(x->h_ctr, x->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, x->stream) ||
+        cudaStreamSynchronize(x->stream)) {
+      set_err(x, "stream error during validation");
+      return fail(LOUVAIN_E_CUDA);
+    }
+    if (x->h_ctr->error & ERR_RANGE) {
+      set_err(x, "malformed CSR: decreasing offsets, column out of range or non-positive weight");
+      return fail(LOUVAIN_E_INVAL);
+    }
+    x->two_m = (long long)x->h_ctr->q_sin;
+    if ((unsigned long long)x->two_m >= (1ull << 32)) {
+      set_err(x, "total weight 2m = %lld is 2^32 or more; int64 scores would overflow", x->two_m);
+      return fail(LOUVAIN_E_OVERFLOW);
+    }
+  }
+  if (light) {  // enough for louvain_modularity_of
+    if (cudaStreamSynchronize(x->stream) != cudaSuccess) return fail(LOUVAIN_E_CUDA);
+    *out = x;
+    return LOUVAIN_OK;
+  }
+  // per-vertex state and work arrays
+  if ((st = dalloc_n(x, &x->C, nv)) || (st = dalloc_n(x, &x->Cp, nv)) || (st = dalloc_n(x, &x->K, nv)) ||
+      (st = dalloc_n(x, &x->Kalt, nv)) || (st = dalloc_n(x, &x->Sigma, nv)) || (st = dalloc_n(x, &x->flag, nv)))
+    return fail(st);
+  for (int k = 0; k < kNumBins; ++k)
+    if ((st = dalloc_n(x, &x->bins[k], nv))) return fail(st);
+  if ((st = dalloc_n(x, &x->mv_vertex, nv)) || (st = dalloc_n(x, &x->mv_target, nv))) return fail(st);
+  if ((st = dalloc_n(x, &x->cnt, nv)) || (st = dalloc_n(x, &x->cdeg, nv)) || (st = dalloc_n(x, &x->newid, nv + 1)) ||
+      (st = dalloc_n(x, &x->coff, nv + 1)) || (st = dalloc_n(x, &x->hoff, nv + 1)) ||
+      (st = dalloc_n(x, &x->kcoff, nv)) || (st = dalloc_n(x, &x->members, nv)) || (st = dalloc_n(x, &x->kcnt, nv)) ||
+      (st = dalloc_n(x, &x->scan_tmp, (int64_t)scan_tmp_elems(nv))))
+    return fail(st);
+  for (int k = 0; k < 2; ++k)
+    if ((st = dalloc_n(x, &x->pcol[k], nnz)) || (st = dalloc_n(x, &x->pw[k], nnz)) ||
+        (st = dalloc_n(x, &x->pbeg[k], nv)) || (st = dalloc_n(x, &x->pend[k], nv)))
+      return fail(st);
+  if (cfg->mode == LOUVAIN_MODE_LEARNED) {
+    set_err(x, "learned mode is not available in this build");
+    return fail(LOUVAIN_E_INVAL);
+  }
+  x->timing.resize((size_t)std::max(cfg->max_passes, 1));
+  for (auto &pt : x->timing) {
+    if (cudaEventCreate(&pt.t0) || cudaEventCreate(&pt.t1) || cudaEventCreate(&pt.t2)) {
+      set_err(x, "event creation failed");
+      return fail(LOUVAIN_E_CUDA);
+    }
+  }
+  if (cudaEventCreate(&x->run0) || cudaEventCreate(&x->run1)) {
+    set_err(x, "event creation failed");
+    return fail(LOUVAIN_E_CUDA);
+  }
+  if (cudaStreamSynchronize(x->stream) != cudaSuccess) {
+    set_err(x, "stream error after allocation");
+    return fail(LOUVAIN_E_CUDA);
+  }
+  *out = x;
+  return LOUVAIN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void louvain_config_default(louvain_config *c) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->max_passes = 10;
+  c->max_iterations = 20;
+  c->tolerance = 0.01;
+  c->tolerance_drop = 10.0;
+  c->aggregation_tolerance = 0.8;
+  c->pickless_period = 4;
+  c->buckets = 4;
+  c->schedule_seed = 0;
+  c->mode = LOUVAIN_MODE_PLAIN;
+  c->model = nullptr;
+  c->skip_threshold = 0.5f;
+  c->record_pass_modularity = 0;
+  c->check_symmetry = 0;
+}
+
+louvain_status louvain_create(const louvain_graph *graph, const louvain_config *cfg, void *stream, louvain_ctx **out) {
+  if (!out) return LOUVAIN_E_INVAL;
+  return create_impl(graph, cfg, stream, out);
+}
+
+louvain_status louvain_run(louvain_ctx *x) {
+  if (!x) return LOUVAIN_E_INVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != x->device) cudaSetDevice(x->device);
+  louvain_status st = run_impl(x);
+  if (st != LOUVAIN_OK) x->ran = false;
+  return st;
+}
+
+louvain_status louvain_modularity(const louvain_ctx *x, double *q, int64_t *num, int64_t *den) {
+  if (!x) return LOUVAIN_E_INVAL;
+  if (!x->ran) return LOUVAIN_E_STATE;
+  if (q) *q = x->q;
+  if (num) put128(num, x->qnum);
+  if (den) put128(den, x->qden);
+  return LOUVAIN_OK;
+}
+
+louvain_status louvain_memberships(const louvain_ctx *xc, int32_t *out, int32_t out_on_device) {
+  louvain_ctx *x = const_cast<louvain_ctx *>(xc);
+  if (!x || (!out && x->n0 > 0)) return LOUVAIN_E_INVAL;
+  if (!x->ran) return LOUVAIN_E_STATE;
+  if (x->n0 == 0) return LOUVAIN_OK;
+  LV_CK(cudaMemcpyAsync(out, x->C, (size_t)x->n0 * 4, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                        x->stream));
+  LV_CK(cudaStreamSynchronize(x->stream));
+  return LOUVAIN_OK;
+}
+
+louvain_status louvain_records(const louvain_ctx *x, int64_t *iter_stats, int64_t *pass_stats, int64_t *summary) {
+  if (!x) return LOUVAIN_E_INVAL;
+  if (!x->ran) return LOUVAIN_E_STATE;
+  const louvain_config &c = x->cfg;
+  if (iter_stats && c.max_passes > 0)
+    memcpy(iter_stats, x->iter_stats.data(), (size_t)c.max_passes * c.max_iterations * 4 * sizeof(int64_t));
+  if (pass_stats && c.max_passes > 0) memcpy(pass_stats, x->pass_stats.data(), (size_t)c.max_passes * 6 * sizeof(int64_t));
+  if (summary) {
+    summary[0] = x->passes;
+    summary[1] = x->gamma;
+    put128(summary + 2, x->qnum);
+    put128(summary + 4, x->qden);
+    summary[6] = x->two_m;
+    summary[7] = x->exit_reason;
+  }
+  return LOUVAIN_OK;
+}
+
+louvain_status louvain_stats(const louvain_ctx *xc, char *json, size_t cap) {
+  louvain_ctx *x = const_cast<louvain_ctx *>(xc);
+  if (!x || !json) return LOUVAIN_E_INVAL;
+  if (!x->ran) return LOUVAIN_E_STATE;
+  std::string s = "{";
+  char buf[256];
+  snprintf(buf, sizeof buf, "\"run_ms\": %.4f, \"passes\": %d, \"communities\": %lld, \"modularity\": %.12f, ",
+           x->run_ms, x->passes, (long long)x->gamma, x->q);
+  s += buf;
+  snprintf(buf, sizeof buf,
+           "\"iterations\": %lld, \"moves\": %lld, \"evaluated\": %lld, \"skipped\": %lld, \"device_bytes\": %zu, ",
+           x->it_total, x->moves_total, x->evaluated_total, x->skipped_total, x->bytes);
+  s += buf;
+  double tm = 0, ta = 0;
+  std::string per = "\"per_pass\": [";
+  for (int p = 0; p < x->passes; ++p) {
+    float a = 0, b = 0;
+    cudaEventElapsedTime(&a, x->timing[p].t0, x->timing[p].t1);
+    if (x->timing[p].aggregated) cudaEventElapsedTime(&b, x->timing[p].t1, x->timing[p].t2);
+    tm += a;
+    ta += b;
+    snprintf(buf, sizeof buf, "%s{\"move_ms\": %.4f, \"aggregate_ms\": %.4f}", p ? ", " : "", a, b);
+    per += buf;
+  }
+  per += "]";
+  snprintf(buf, sizeof buf, "\"move_ms\": %.4f, \"aggregate_ms\": %.4f, \"other_ms\": %.4f, ", tm, ta,
+           x->run_ms - tm - ta);
+  s += buf;
+  s += per + "}";
+  if (s.size() + 1 > cap) return LOUVAIN_E_INVAL;
+  memcpy(json, s.c_str(), s.size() + 1);
+  return LOUVAIN_OK;
+}
+
+void louvain_destroy(louvain_ctx *x) {
+  if (!x) return;
+  for (void *p : x->allocs) cudaFreeAsync(p, x->stream);
+  cudaStreamSynchronize(x->stream);
+  for (auto &pt : x->timing) {
+    if (pt.t0) cudaEventDestroy(pt.t0);
+    if (pt.t1) cudaEventDestroy(pt.t1);
+    if (pt.t2) cudaEventDestroy(pt.t2);
+  }
+  if (x->run0) cudaEventDestroy(x->run0);
+  if (x->run1) cudaEventDestroy(x->run1);
+  if (x->h_ctr) cudaFreeHost(x->h_ctr);
+  delete x;
+}
+
+const char *louvain_last_error(const louvain_ctx *x) {
+  if (!x) return g_create_err.c_str();
+  return x->err.c_str();
+}
+
+louvain_status louvain_modularity_of(const louvain_graph *graph, const int32_t *membership, void *stream, double *q,
+                                     int64_t *num, int64_t *den) {
+  if (!graph || !membership || graph->n < 0) return LOUVAIN_E_INVAL;
+  louvain_config cfg;
+  louvain_config_default(&cfg);
+  cfg.max_passes = 0;
+  louvain_ctx *x = nullptr;
+  louvain_status st = create_impl(graph, &cfg, stream, &x, true);
+  if (st) return st;
+  const int64_t n = graph->n;
+  const int32_t *memb = membership;
+  int32_t *dm = nullptr;
+  int64_t *sig = nullptr;
+  if (!graph->on_device && n > 0) {
+    if ((st = dalloc_n(x, &dm, n))) {
+      louvain_destroy(x);
+      return st;
+    }
+    cudaMemcpyAsync(dm, membership, (size_t)n * 4, cudaMemcpyHostToDevice, x->stream);
+    memb = dm;
+  }
+  if ((st = dalloc_n(x, &sig, std::max<int64_t>(n, 1)))) {
+    louvain_destroy(x);
+    return st;
+  }
+  i128 qn = 0, qd = 0;
+  GView g{n, x->off0, x->off0 + 1, x->col0, x->w0};
+  if (n > 0) st = modularity_into(x, g, x->weighted ? W_I32 : W_UNIT, memb, nullptr, sig, &qn, &qd);
+  if (!st) {
+    if (q) *q = qd ? (double)qn / (double)qd : 0.0;
+    if (num) put128(num, qn);
+    if (den) put128(den, qd);
+  } else {
+    g_create_err = x->err;
+  }
+  louvain_destroy(x);
+  return st;
+}
+
+int64_t louvain_model_size(void) { return mlp_param_count(); }
+
+const char *louvain_version(void) { return "gb300-louvain 0.1 (sm_103a)"; }
+
+}  // extern "C"

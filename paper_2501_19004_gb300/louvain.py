@@ -1,0 +1,340 @@
+"""Python binding of the C ABI in ``include/louvain.h`` (ctypes).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``liblouvain_gb300.so``.  If the library is missing this module raises; there
+is no fallback.  Functions keep the ABI's names; :class:`Louvain` wraps a
+context.
+
+Graphs are :class:`paper_2501_19004_gb300.graphgen.CSR` objects (host numpy
+arrays) or :class:`DeviceCSR` (torch CUDA tensors).  PyTorch provides device
+memory and the current stream only.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+STATUS = {0: "OK", 1: "E_INVAL", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_HASH_OVERFLOW", 5: "E_TIMEOUT",
+          6: "E_OVERFLOW", 7: "E_STATE"}
+MODE_PLAIN, MODE_LEARNED = 0, 1
+ITER_FIELDS, PASS_FIELDS = 4, 6
+
+
+class LouvainError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class LouvainGraph(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("offsets", ctypes.c_void_p),
+                ("cols", ctypes.c_void_p), ("weights", ctypes.c_void_p), ("on_device", ctypes.c_int32)]
+
+
+class LouvainConfig(ctypes.Structure):
+    _fields_ = [("max_passes", ctypes.c_int32), ("max_iterations", ctypes.c_int32),
+                ("tolerance", ctypes.c_double), ("tolerance_drop", ctypes.c_double),
+                ("aggregation_tolerance", ctypes.c_double), ("pickless_period", ctypes.c_int32),
+                ("buckets", ctypes.c_int32), ("schedule_seed", ctypes.c_uint64), ("mode", ctypes.c_int32),
+                ("model", ctypes.c_void_p), ("skip_threshold", ctypes.c_float),
+                ("record_pass_modularity", ctypes.c_int32), ("check_symmetry", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(path: Optional[str] = None):
+    """Load the CUDA library (built by ``build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library {p} is missing: run paper_2501_19004_gb300.build.build() "
+                           "(or __graft_entry__.build()) on a machine with nvcc")
+    lib = ctypes.CDLL(p)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    P = ctypes.POINTER
+    lib.louvain_config_default.restype = None
+    lib.louvain_config_default.argtypes = [P(LouvainConfig)]
+    lib.louvain_create.restype = ctypes.c_int
+    lib.louvain_create.argtypes = [P(LouvainGraph), P(LouvainConfig), vp, P(vp)]
+    lib.louvain_run.restype = ctypes.c_int
+    lib.louvain_run.argtypes = [vp]
+    lib.louvain_modularity.restype = ctypes.c_int
+    lib.louvain_modularity.argtypes = [vp, P(ctypes.c_double), vp, vp]
+    lib.louvain_memberships.restype = ctypes.c_int
+    lib.louvain_memberships.argtypes = [vp, vp, i32]
+    lib.louvain_records.restype = ctypes.c_int
+    lib.louvain_records.argtypes = [vp, vp, vp, vp]
+    lib.louvain_stats.restype = ctypes.c_int
+    lib.louvain_stats.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+    lib.louvain_destroy.restype = None
+    lib.louvain_destroy.argtypes = [vp]
+    lib.louvain_last_error.restype = ctypes.c_char_p
+    lib.louvain_last_error.argtypes = [vp]
+    lib.louvain_modularity_of.restype = ctypes.c_int
+    lib.louvain_modularity_of.argtypes = [P(LouvainGraph), vp, vp, P(ctypes.c_double), vp, vp]
+    lib.louvain_model_size.restype = i64
+    lib.louvain_model_size.argtypes = []
+    lib.louvain_version.restype = ctypes.c_char_p
+    lib.louvain_version.argtypes = []
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(st: int, ctx=None):
+    if st != 0:
+        msg = load().louvain_last_error(ctx).decode(errors="replace")
+        raise LouvainError(st, msg)
+
+
+@dataclass
+class Config:
+    """Run parameters (defaults as in ``louvain_config_default``)."""
+    max_passes: int = 10
+    max_iterations: int = 20
+    tolerance: float = 0.01
+    tolerance_drop: float = 10.0
+    aggregation_tolerance: float = 0.8
+    pickless_period: int = 4
+    buckets: int = 4
+    schedule_seed: int = 0
+    mode: int = MODE_PLAIN
+    model: Optional[np.ndarray] = None
+    skip_threshold: float = 0.5
+    record_pass_modularity: bool = False
+    check_symmetry: bool = False
+
+    def c(self) -> LouvainConfig:
+        self._model_keep = None
+        mp = None
+        if self.model is not None:
+            self._model_keep = np.ascontiguousarray(self.model, dtype=np.float32)
+            mp = self._model_keep.ctypes.data
+        return LouvainConfig(self.max_passes, self.max_iterations, self.tolerance, self.tolerance_drop,
+                             self.aggregation_tolerance, self.pickless_period, self.buckets,
+                             self.schedule_seed & (2**64 - 1), self.mode, mp, self.skip_threshold,
+                             int(self.record_pass_modularity), int(self.check_symmetry))
+
+
+@dataclass
+class DeviceCSR:
+    """A CSR held in torch CUDA tensors (int64 offsets, int32 cols/weights)."""
+    offsets: "object"
+    cols: "object"
+    weights: "object" = None
+
+    @property
+    def n(self):
+        return int(self.offsets.shape[0] - 1)
+
+    @property
+    def nnz(self):
+        return int(self.cols.shape[0])
+
+    @staticmethod
+    def from_host(g, device="cuda"):
+        import torch
+        return DeviceCSR(torch.from_numpy(np.ascontiguousarray(g.offsets)).to(device),
+                         torch.from_numpy(np.ascontiguousarray(g.cols)).to(device),
+                         None if g.weights is None else torch.from_numpy(np.ascontiguousarray(g.weights)).to(device))
+
+
+def _graph_struct(g):
+    """(LouvainGraph, keep-alive list) for a host CSR or a DeviceCSR."""
+    if isinstance(g, DeviceCSR):
+        import torch
+        for t, dt in ((g.offsets, torch.int64), (g.cols, torch.int32)):
+            if not t.is_cuda or t.dtype != dt or not t.is_contiguous():
+                raise ValueError("DeviceCSR needs contiguous CUDA tensors: int64 offsets, int32 cols/weights")
+        if g.weights is not None and (g.weights.dtype != torch.int32 or not g.weights.is_cuda):
+            raise ValueError("DeviceCSR weights must be int32 CUDA tensors")
+        gs = LouvainGraph(g.n, g.nnz, g.offsets.data_ptr(), g.cols.data_ptr(),
+                          None if g.weights is None else g.weights.data_ptr(), 1)
+        return gs, [g]
+    off = np.ascontiguousarray(g.offsets, dtype=np.int64)
+    col = np.ascontiguousarray(g.cols, dtype=np.int32)
+    w = None if g.weights is None else np.ascontiguousarray(g.weights, dtype=np.int32)
+    gs = LouvainGraph(off.shape[0] - 1, col.shape[0], off.ctypes.data, col.ctypes.data,
+                      None if w is None else w.ctypes.data, 0)
+    return gs, [off, col, w]
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return ctypes.c_void_p(None)
+
+
+# ------------------------------------------------------------- ABI mirror
+def louvain_config_default() -> LouvainConfig:
+    c = LouvainConfig()
+    load().louvain_config_default(ctypes.byref(c))
+    return c
+
+
+def louvain_create(graph, cfg: Optional[Config] = None, stream=None) -> ctypes.c_void_p:
+    cfg = cfg or Config()
+    gs, keep = _graph_struct(graph)
+    cc = cfg.c()
+    ctx = ctypes.c_void_p()
+    st = load().louvain_create(ctypes.byref(gs), ctypes.byref(cc), stream if stream is not None else _current_stream(),
+                               ctypes.byref(ctx))
+    del keep
+    _check(st, None)
+    return ctx
+
+
+def louvain_run(ctx):
+    _check(load().louvain_run(ctx), ctx)
+
+
+def louvain_modularity(ctx):
+    q = ctypes.c_double()
+    num = np.zeros(2, dtype=np.int64)
+    den = np.zeros(2, dtype=np.int64)
+    _check(load().louvain_modularity(ctx, ctypes.byref(q), num.ctypes.data, den.ctypes.data), ctx)
+    return q.value, _i128(num), _i128(den)
+
+
+def louvain_memberships(ctx, out=None, n=None):
+    """Memberships into `out` (numpy int32 host array or int32 CUDA tensor);
+    allocates a numpy array of length n when out is None."""
+    if out is None:
+        out = np.empty(n, dtype=np.int32)
+    if isinstance(out, np.ndarray):
+        assert out.dtype == np.int32 and out.flags.c_contiguous
+        _check(load().louvain_memberships(ctx, out.ctypes.data, 0), ctx)
+    else:
+        _check(load().louvain_memberships(ctx, out.data_ptr(), 1), ctx)
+    return out
+
+
+def louvain_records(ctx, max_passes, max_iterations):
+    it = np.zeros((max(max_passes, 1), max_iterations, ITER_FIELDS), dtype=np.int64)
+    ps = np.zeros((max(max_passes, 1), PASS_FIELDS), dtype=np.int64)
+    summ = np.zeros(8, dtype=np.int64)
+    _check(load().louvain_records(ctx, it.ctypes.data, ps.ctypes.data, summ.ctypes.data), ctx)
+    return it, ps, summ
+
+
+def louvain_stats(ctx) -> dict:
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(load().louvain_stats(ctx, buf, len(buf)), ctx)
+    return json.loads(buf.value.decode())
+
+
+def louvain_destroy(ctx):
+    load().louvain_destroy(ctx)
+
+
+def louvain_modularity_of(graph, membership, stream=None):
+    """Modularity (Eq. 1) of `membership` on `graph`, computed on the device.
+    Returns (Q, exact numerator, exact denominator)."""
+    gs, keep = _graph_struct(graph)
+    if isinstance(graph, DeviceCSR):
+        mp = membership.data_ptr()
+    else:
+        membership = np.ascontiguousarray(membership, dtype=np.int32)
+        mp = membership.ctypes.data
+    q = ctypes.c_double()
+    num = np.zeros(2, dtype=np.int64)
+    den = np.zeros(2, dtype=np.int64)
+    st = load().louvain_modularity_of(ctypes.byref(gs), mp, stream if stream is not None else _current_stream(),
+                                      ctypes.byref(q), num.ctypes.data, den.ctypes.data)
+    del keep
+    _check(st, None)
+    return q.value, _i128(num), _i128(den)
+
+
+def louvain_model_size() -> int:
+    return int(load().louvain_model_size())
+
+
+def louvain_version() -> str:
+    return load().louvain_version().decode()
+
+
+def _i128(a) -> int:
+    return (int(a[0]) << 64) + (int(a[1]) & (2**64 - 1))
+
+
+# ------------------------------------------------------------- convenience
+@dataclass
+class Result:
+    membership: np.ndarray
+    modularity: float
+    q_num: int
+    q_den: int
+    passes: int
+    communities: int
+    two_m: int
+    exit_reason: int
+    iter_stats: np.ndarray
+    pass_stats: np.ndarray
+
+    def iterations(self):
+        out = []
+        for p in range(self.passes):
+            li = int(self.pass_stats[p, 2])
+            out.append([(int(r[0]), int(r[1]), _i128(r[2:4])) for r in self.iter_stats[p, :li]])
+        return out
+
+
+class Louvain:
+    """One graph on the device plus all workspace; ``run()`` can be repeated."""
+
+    def __init__(self, graph, cfg: Optional[Config] = None, stream=None):
+        self.cfg = cfg or Config()
+        self.n = graph.n
+        self.ctx = louvain_create(graph, self.cfg, stream)
+
+    def run(self):
+        louvain_run(self.ctx)
+        return self
+
+    def result(self) -> Result:
+        q, num, den = louvain_modularity(self.ctx)
+        memb = louvain_memberships(self.ctx, n=self.n)
+        it, ps, summ = louvain_records(self.ctx, self.cfg.max_passes, self.cfg.max_iterations)
+        return Result(memb, q, num, den, int(summ[0]), int(summ[1]), int(summ[6]), int(summ[7]), it, ps)
+
+    def stats(self) -> dict:
+        return louvain_stats(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            louvain_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def run(graph, cfg: Optional[Config] = None) -> Result:
+    with Louvain(graph, cfg) as lv:
+        return lv.run().result()
