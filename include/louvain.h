@@ -93,6 +93,8 @@ typedef struct {
   float skip_threshold;          /* LEARNED: skip a vertex when p < threshold */
   int32_t record_pass_modularity;/* 1: compute Q after every pass (stats) */
   int32_t check_symmetry;        /* 1: louvain_create verifies w_ij = w_ji (host graphs) */
+  uint32_t profile_mask;         /* bit k: time kernel group k with CUDA events
+                                    (ids in louvain_stats' "kernels"); 0 = off */
 } louvain_config;
 
 /* Fill `cfg` with the defaults above (mode PLAIN, seed 0). */
@@ -131,6 +133,11 @@ louvain_status louvain_records(const louvain_ctx *ctx, int64_t *iter_stats, int6
 /* JSON object with timings per phase and per pass (CUDA events), counts and
  * the memory footprint.  Returns LOUVAIN_E_INVAL if `cap` is too small. */
 louvain_status louvain_stats(const louvain_ctx *ctx, char *json, size_t cap);
+
+/* Change which kernel groups the next runs time with CUDA events (the
+ * profile_mask of louvain_config).  Timing adds two event records per timed
+ * launch and nothing else. */
+louvain_status louvain_set_profile(louvain_ctx *ctx, uint32_t profile_mask);
 
 /* Release all device memory of the context (stream-ordered). */
 void louvain_destroy(louvain_ctx *ctx);

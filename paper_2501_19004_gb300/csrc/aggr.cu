@@ -16,18 +16,12 @@
 #include <climits>
 
 #include "internal.h"
+#include "tables.cuh"
 
 namespace lv {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-
-int grid_for(int64_t n, int threads, int num_sms, int per_sm) {
-  int64_t g = (n + threads - 1) / threads;
-  int64_t cap = (int64_t)num_sms * per_sm;
-  if (g > cap) g = cap;
-  return (int)(g < 1 ? 1 : g);
-}
 
 // --------------------------------------------------------------- count
 __global__ void __launch_bounds__(256) k_comm_count(GView g, const int32_t *Cp, unsigned long long *cnt,
@@ -162,14 +156,12 @@ __global__ void __launch_bounds__(256) k_comm_scatter(int64_t n, int32_t *Cp, un
 }
 
 // --------------------------------------------------------------- compact
-// Merge bins by total community degree.
-constexpr int kMergeThreadMax = 16;
-constexpr int kMergeWarpMax = 256;   // table kWarpCap
-constexpr int kMergeBlockMax = 4096; // table kBlockCap
+// Merge bins by total community degree (the degree bins of local moving).
+constexpr int kMergeThreadMax = kThreadMaxDeg;
 
 __global__ void __launch_bounds__(256) k_comm_compact(AggArgs a, int64_t n) {
   const int lane = threadIdx.x & 31;
-  unsigned long long md = 0;
+  unsigned long long md = 0, big_slots = 0, big_items = 0;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t c = base + threadIdx.x;
     int bin = -1;
@@ -186,8 +178,13 @@ __global__ void __launch_bounds__(256) k_comm_compact(AggArgs a, int64_t n) {
         const int64_t cd = h1 - h0;
         a.oend[k] = h1;  // row capacity until the merge writes the true end
         if (cd > 0) {
-          bin = cd <= kMergeThreadMax ? 0 : cd <= kMergeWarpMax ? 1 : cd <= kMergeBlockMax ? 2 : 3;
+          bin = degree_bin(cd);
           if ((unsigned long long)cd > md) md = (unsigned long long)cd;
+          if (bin == kBigBin) {
+            const unsigned long long dk = (unsigned long long)(cd < a.gamma ? cd : a.gamma);
+            big_slots += pow2_at_least(2 * dk);
+            big_items += 1;
+          }
         }
       }
     }
@@ -198,7 +195,7 @@ __global__ void __launch_bounds__(256) k_comm_compact(AggArgs a, int64_t n) {
       if (!mask) continue;
       const int leader = __ffs(mask) - 1;
       unsigned long long top = 0;
-      if (lane == leader) top = atomicAdd(&a.ctr->bin_count[4 + b], (unsigned long long)__popc(mask));
+      if (lane == leader) top = atomicAdd(&a.ctr->mbin_count[b], (unsigned long long)__popc(mask));
       top = __shfl_sync(kFull, top, leader);
       if (p) a.mbins[b][top + __popc(mask & lanemask_lt())] = k;
     }
@@ -208,7 +205,22 @@ __global__ void __launch_bounds__(256) k_comm_compact(AggArgs a, int64_t n) {
     unsigned long long x = __shfl_xor_sync(kFull, md, o);
     md = x > md ? x : md;
   }
-  if (lane == 0 && md) atomicMax(&a.ctr->maxdeg, md);
+  big_slots = warp_sum_u(big_slots);
+  big_items = warp_sum_u(big_items);
+  if (lane == 0) {
+    if (md) atomicMax(&a.ctr->maxdeg, md);
+    if (big_slots) atomicAdd(&a.ctr->big_slots, big_slots);
+    if (big_items) atomicAdd(&a.ctr->big_items, big_items);
+  }
+}
+
+// Degree of every member in community-vertex CSR order (input of the
+// member-degree prefix that locates entries of a community's member rows).
+__global__ void k_member_deg(GView g, const int32_t *members, unsigned long long *mdeg) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < g.n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = members[t];
+    mdeg[t] = (unsigned long long)(g.end[v] - g.begin[v]);
+  }
 }
 
 __global__ void k_dendro(int32_t *C, const int32_t *Cp, int64_t n) {
@@ -217,43 +229,14 @@ __global__ void k_dendro(int32_t *C, const int32_t *Cp, int64_t n) {
 }
 
 // --------------------------------------------------------------- merge
-__device__ __forceinline__ void tbl_add(int32_t *keys, unsigned long long *vals, uint32_t mask, int32_t key,
-                                        long long w, Counters *ctr) {
-  uint32_t s = slot_of(key, mask);
-  for (uint32_t t = 0; t <= mask; ++t) {
-    int32_t k = ((volatile int32_t *)keys)[s];
-    if (k == kEmpty) k = atomicCAS(keys + s, kEmpty, key), k = (k == kEmpty) ? key : k;
-    if (k == key) {
-      atomicAdd(vals + s, (unsigned long long)w);
-      return;
-    }
-    s = (s + 1) & mask;
-  }
-  atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
-}
-
-__device__ __forceinline__ void gtbl_add(int32_t *keys, unsigned long long *vals, uint32_t mask, int32_t key,
-                                         long long w, Counters *ctr) {
-  uint32_t s = slot_of(key, mask);
-  for (uint32_t t = 0; t <= mask; ++t) {
-    int32_t k = __ldcg(keys + s);
-    if (k == kEmpty) k = atomicCAS(keys + s, kEmpty, key), k = (k == kEmpty) ? key : k;
-    if (k == key) {
-      atomicAdd(vals + s, (unsigned long long)w);
-      return;
-    }
-    s = (s + 1) & mask;
-  }
-  atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
-}
-
 // Thread per community (total degree <= 16): a short list in shared memory.
 template <int WK, int NT>
 __global__ void __launch_bounds__(NT) k_merge_thread(AggArgs a) {
   __shared__ int32_t skeys[kMergeThreadMax][NT];
-  __shared__ long long svals[kMergeThreadMax][NT];
-  const unsigned long long cnt = a.ctr->bin_count[4];
+  __shared__ uint32_t svals[kMergeThreadMax][NT];
+  const unsigned long long cnt = a.ctr->mbin_count[0];
   const int t = threadIdx.x;
+  unsigned long long work[4] = {0, 0, 0, 0};  // communities, members, entries, written
   for (unsigned long long idx = (unsigned long long)blockIdx.x * NT + t; idx < cnt;
        idx += (unsigned long long)gridDim.x * NT) {
     const int32_t k = a.mbins[0][idx];
@@ -263,7 +246,8 @@ __global__ void __launch_bounds__(NT) k_merge_thread(AggArgs a) {
       const int32_t v = a.members[mi];
       for (int64_t e = a.g.begin[v]; e < a.g.end[v]; ++e) {
         const int32_t c = a.Cp[__ldg(a.g.col + e)];
-        const long long w = load_w<WK>(a.g.w, e);
+        const uint32_t w = load_w<WK>(a.g.w, e);
+        ++work[2];
         int s = 0;
         while (s < nk && skeys[s][t] != c) ++s;
         if (s == nk) {
@@ -284,37 +268,84 @@ __global__ void __launch_bounds__(NT) k_merge_thread(AggArgs a) {
       a.ow[ob + s] = svals[s][t];
     }
     a.oend[k] = ob + nk;
-    atomicAdd(&a.ctr->nnz_out, (unsigned long long)nk);
+    work[0] += 1;
+    work[1] += (unsigned long long)(m1 - m0);
+    work[3] += (unsigned long long)nk;
   }
+  unsigned long long nz[1] = {work[3]};
+  flush_work(nz, &a.ctr->nnz_out);
+  flush_work(work, a.ctr->mg_work[0]);
 }
 
-// Warp per community (total degree <= 256): shared table of up to 512 slots.
+// Gather run [x, xe) of community k's entry sequence (its members' rows
+// concatenated, positions relative to obegin[k]) via the member-degree prefix.
+template <int WK>
+__device__ __forceinline__ void gather_members(const AggArgs &a, int32_t k, int64_t x, int64_t xe,
+                                               int32_t (&kk)[kRun], uint32_t (&ww)[kRun]) {
+#pragma unroll
+  for (int u = 0; u < kRun; ++u) {
+    kk[u] = kEmpty;
+    ww[u] = 0;
+  }
+  if (x >= xe) return;
+  const int64_t m0 = a.kcoff[k];
+  const int64_t base = a.obegin[k];
+  int64_t t = m0 + upper_index(a.mprefix + m0, a.kcnt[k], base + x);
+  int64_t mstart = a.mprefix[t];
+  int32_t v = a.members[t];
+  int64_t rb = a.g.begin[v], rlen = a.g.end[v] - rb;
+  int32_t jj[kRun];
+#pragma unroll
+  for (int u = 0; u < kRun; ++u) {
+    jj[u] = -2;
+    if (x + u < xe) {
+      const int64_t pos = base + x + u;
+      while (pos >= mstart + rlen) {
+        ++t;
+        mstart = a.mprefix[t];
+        v = a.members[t];
+        rb = a.g.begin[v];
+        rlen = a.g.end[v] - rb;
+      }
+      const int64_t e = rb + (pos - mstart);
+      jj[u] = __ldg(a.g.col + e);
+      ww[u] = load_w<WK>(a.g.w, e);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kRun; ++u) kk[u] = jj[u] >= 0 ? a.Cp[jj[u]] : kEmpty;
+}
+
+// Warp per community (total degree <= 256): shared table of up to 512 slots,
+// a run of 8 entries per lane.
 template <int WK, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_merge_warp(AggArgs a) {
   __shared__ int32_t skeys[WARPS][kWarpCap];
-  __shared__ unsigned long long svals[WARPS][kWarpCap];
+  __shared__ uint32_t svals[WARPS][kWarpCap];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t *keys = skeys[warp];
-  unsigned long long *vals = svals[warp];
-  const unsigned long long cnt = a.ctr->bin_count[5];
+  uint32_t *vals = svals[warp];
+  const unsigned long long cnt = a.ctr->mbin_count[1];
+  unsigned long long work[4] = {0, 0, 0, 0};
   for (unsigned long long idx = (unsigned long long)blockIdx.x * WARPS + warp; idx < cnt;
        idx += (unsigned long long)gridDim.x * WARPS) {
     const int32_t k = a.mbins[1][idx];
-    const int64_t m0 = a.kcoff[k], m1 = m0 + a.kcnt[k];
     const int64_t ob = a.obegin[k];
-    const uint64_t tot = (uint64_t)(a.oend[k] - ob);  // total member degree
-    const uint32_t cap = pow2_at_least(2 * tot);
+    const int64_t tot = a.oend[k] - ob;  // total member degree
+    const uint32_t cap = pow2_at_least(2 * (uint64_t)tot);
     const uint32_t mask = cap - 1;
     for (uint32_t s = lane; s < cap; s += 32) {
       keys[s] = kEmpty;
       vals[s] = 0;
     }
     __syncwarp();
-    for (int64_t mi = m0; mi < m1; ++mi) {
-      const int32_t v = a.members[mi];
-      const int64_t e1 = a.g.end[v];
-      for (int64_t e = a.g.begin[v] + lane; e < e1; e += 32)
-        tbl_add(keys, vals, mask, a.Cp[__ldg(a.g.col + e)], load_w<WK>(a.g.w, e), a.ctr);
+    for (int64_t x0 = 0; x0 < tot; x0 += 32 * kRun) {
+      int32_t kk[kRun];
+      uint32_t ww[kRun];
+      const int64_t xs = x0 + lane * kRun;
+      gather_members<WK>(a, k, xs, xs + kRun < tot ? xs + kRun : tot, kk, ww);
+#pragma unroll
+      for (int u = 0; u < kRun; ++u) warp_insert_sm(keys, vals, mask, kk[u], ww[u], a.ctr);
     }
     __syncwarp();
     unsigned long long written = 0;
@@ -322,40 +353,45 @@ __global__ void __launch_bounds__(WARPS * 32) k_merge_warp(AggArgs a) {
       const uint32_t s = s0 + lane;
       const int32_t c = s < cap ? keys[s] : kEmpty;
       const bool occ = c != kEmpty;
-      const unsigned m = __ballot_sync(kFull, occ);
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, occ);
       if (occ) {
         const int64_t pos = ob + (int64_t)written + __popc(m & lanemask_lt());
         a.ocol[pos] = c;
-        a.ow[pos] = (long long)vals[s];
+        a.ow[pos] = vals[s];
       }
       written += __popc(m);
     }
     if (lane == 0) {
       a.oend[k] = ob + (int64_t)written;
-      atomicAdd(&a.ctr->nnz_out, written);
+      work[0] += 1;
+      work[1] += (unsigned long long)a.kcnt[k];
+      work[2] += (unsigned long long)tot;
+      work[3] += written;
     }
     __syncwarp();
   }
+  unsigned long long nz[1] = {work[3]};
+  flush_work(nz, &a.ctr->nnz_out);
+  flush_work(work, a.ctr->mg_work[1]);
 }
 
-// Block per community (total degree <= 4096): shared table of up to 8192
-// slots; warps take members round-robin, lanes stride a member's row.
-template <int WK, int NT>
+// Block per community: 128 threads and a 2048-slot table up to 1024
+// entries, 512 threads and an 8192-slot table up to 4096; a run of 8
+// consecutive entries per thread.
+template <int WK, int NT, int CAP, int BIN>
 __global__ void __launch_bounds__(NT) k_merge_block(AggArgs a) {
-  extern __shared__ unsigned long long dyn[];
-  unsigned long long *vals = dyn;
-  int32_t *keys = (int32_t *)(dyn + kBlockCap);
+  extern __shared__ uint32_t dyn[];
+  int32_t *keys = (int32_t *)dyn;
+  uint32_t *vals = dyn + CAP;
   __shared__ unsigned long long s_written;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const unsigned long long cnt = a.ctr->bin_count[6];
+  const unsigned long long cnt = a.ctr->mbin_count[BIN];
+  unsigned long long work[4] = {0, 0, 0, 0};
   for (unsigned long long idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
-    const int32_t k = a.mbins[2][idx];
-    const int64_t m0 = a.kcoff[k], m1 = m0 + a.kcnt[k];
+    const int32_t k = a.mbins[BIN][idx];
     const int64_t ob = a.obegin[k];
-    const unsigned long long tot = (unsigned long long)(a.oend[k] - ob);
+    const int64_t tot = a.oend[k] - ob;
     if (threadIdx.x == 0) s_written = 0;
-    __syncthreads();
-    uint64_t distinct = tot < (unsigned long long)a.gamma ? tot : (unsigned long long)a.gamma;
+    const uint64_t distinct = (uint64_t)(tot < a.gamma ? tot : a.gamma);
     const uint32_t cap = pow2_at_least(2 * distinct);
     const uint32_t mask = cap - 1;
     for (uint32_t s = threadIdx.x; s < cap; s += NT) {
@@ -363,11 +399,13 @@ __global__ void __launch_bounds__(NT) k_merge_block(AggArgs a) {
       vals[s] = 0;
     }
     __syncthreads();
-    for (int64_t mi = m0 + warp; mi < m1; mi += NT / 32) {
-      const int32_t v = a.members[mi];
-      const int64_t e1 = a.g.end[v];
-      for (int64_t e = a.g.begin[v] + lane; e < e1; e += 32)
-        tbl_add(keys, vals, mask, a.Cp[__ldg(a.g.col + e)], load_w<WK>(a.g.w, e), a.ctr);
+    for (int64_t x0 = 0; x0 < tot; x0 += (int64_t)NT * kRun) {
+      int32_t kk[kRun];
+      uint32_t ww[kRun];
+      const int64_t xs = x0 + (int64_t)threadIdx.x * kRun;
+      gather_members<WK>(a, k, xs, xs + kRun < tot ? xs + kRun : tot, kk, ww);
+#pragma unroll
+      for (int u = 0; u < kRun; ++u) warp_insert_sm(keys, vals, mask, kk[u], ww[u], a.ctr);
     }
     __syncthreads();
     for (uint32_t s = threadIdx.x; s < cap; s += NT) {
@@ -375,76 +413,21 @@ __global__ void __launch_bounds__(NT) k_merge_block(AggArgs a) {
       if (c == kEmpty) continue;
       const unsigned long long pos = atomicAdd(&s_written, 1ull);
       a.ocol[ob + (int64_t)pos] = c;
-      a.ow[ob + (int64_t)pos] = (long long)vals[s];
+      a.ow[ob + (int64_t)pos] = vals[s];
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       a.oend[k] = ob + (int64_t)s_written;
-      atomicAdd(&a.ctr->nnz_out, s_written);
+      work[0] += 1;
+      work[1] += (unsigned long long)a.kcnt[k];
+      work[2] += (unsigned long long)tot;
+      work[3] += s_written;
     }
     __syncthreads();
   }
-}
-
-// Block per community beyond 4096 entries: a global-memory table slice.
-// Members with long rows are scanned by the whole block, the rest by warps.
-template <int WK, int NT>
-__global__ void __launch_bounds__(NT) k_merge_global(AggArgs a) {
-  __shared__ unsigned long long s_written;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int32_t *keys = a.ws.keys + (int64_t)blockIdx.x * a.ws.slice;
-  unsigned long long *vals = a.ws.vals + (int64_t)blockIdx.x * a.ws.slice;
-  const unsigned long long cnt = a.ctr->bin_count[7];
-  for (unsigned long long idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
-    const int32_t k = a.mbins[3][idx];
-    const int64_t m0 = a.kcoff[k], m1 = m0 + a.kcnt[k];
-    const int64_t ob = a.obegin[k];
-    const unsigned long long tot = (unsigned long long)(a.oend[k] - ob);
-    if (threadIdx.x == 0) s_written = 0;
-    __syncthreads();
-    uint64_t distinct = tot < (unsigned long long)a.gamma ? tot : (unsigned long long)a.gamma;
-    const uint32_t cap = pow2_at_least(2 * distinct);
-    if ((int64_t)cap > a.ws.slice) {
-      if (threadIdx.x == 0) atomicOr(&a.ctr->error, (unsigned long long)ERR_HASH);
-      continue;
-    }
-    const uint32_t mask = cap - 1;
-    for (uint32_t s = threadIdx.x; s < cap; s += NT) {
-      keys[s] = kEmpty;
-      vals[s] = 0;
-    }
-    __syncthreads();
-    // short member rows: a warp each
-    for (int64_t mi = m0 + warp; mi < m1; mi += NT / 32) {
-      const int32_t v = a.members[mi];
-      const int64_t e0 = a.g.begin[v], e1 = a.g.end[v];
-      if (e1 - e0 > 1024) continue;
-      for (int64_t e = e0 + lane; e < e1; e += 32)
-        gtbl_add(keys, vals, mask, a.Cp[__ldg(a.g.col + e)], load_w<WK>(a.g.w, e), a.ctr);
-    }
-    // long member rows: the whole block
-    for (int64_t mi = m0; mi < m1; ++mi) {
-      const int32_t v = a.members[mi];
-      const int64_t e0 = a.g.begin[v], e1 = a.g.end[v];
-      if (e1 - e0 <= 1024) continue;
-      for (int64_t e = e0 + threadIdx.x; e < e1; e += NT)
-        gtbl_add(keys, vals, mask, a.Cp[__ldg(a.g.col + e)], load_w<WK>(a.g.w, e), a.ctr);
-    }
-    __syncthreads();
-    for (uint32_t s = threadIdx.x; s < cap; s += NT) {
-      const int32_t c = __ldcg(keys + s);
-      if (c == kEmpty) continue;
-      const unsigned long long pos = atomicAdd(&s_written, 1ull);
-      a.ocol[ob + (int64_t)pos] = c;
-      a.ow[ob + (int64_t)pos] = (long long)__ldcg(vals + s);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      a.oend[k] = ob + (int64_t)s_written;
-      atomicAdd(&a.ctr->nnz_out, s_written);
-    }
-    __syncthreads();
-  }
+  unsigned long long nz[1] = {work[3]};
+  flush_work(nz, &a.ctr->nnz_out);
+  flush_work(work, a.ctr->mg_work[BIN]);
 }
 
 // --------------------------------------------------------------- modularity
@@ -502,23 +485,29 @@ __global__ void k_relabel(int32_t *x, int64_t n, const int64_t *newid) {
 }
 
 template <int WK>
-void merge_t(const AggArgs &a, int num_sms, cudaStream_t s) {
+void merge_t(const AggArgs &a, int num_sms, cudaStream_t s, KernelProf *prof) {
   static bool attr_done = false;
-  constexpr int kNT = 256;
-  constexpr size_t kSmem = (size_t)kBlockCap * (sizeof(unsigned long long) + sizeof(int32_t));
+  constexpr size_t kMidSmem = (size_t)kMidCap * (sizeof(uint32_t) + sizeof(int32_t));
+  constexpr size_t kSmem = (size_t)kBlockCap * (sizeof(uint32_t) + sizeof(int32_t));
   if (!attr_done) {
-    cudaFuncSetAttribute(k_merge_block<WK, kNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    cudaFuncSetAttribute(k_merge_block<WK, 512, kBlockCap, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kSmem);
     attr_done = true;
   }
-  k_merge_thread<WK, 128><<<num_sms * 8, 128, 0, s>>>(a);
-  k_merge_warp<WK, 8><<<num_sms * 4, 256, 0, s>>>(a);
-  k_merge_block<WK, kNT><<<num_sms * 2, kNT, kSmem, s>>>(a);
-  if (a.ws.blocks > 0) k_merge_global<WK, 1024><<<a.ws.blocks, 1024, 0, s>>>(a);
+  LV_TIMED(prof, K_MERGE_THREAD, s, k_merge_thread<WK, 128><<<num_sms * 8, 128, 0, s>>>(a));
+  LV_TIMED(prof, K_MERGE_WARP, s, k_merge_warp<WK, 8><<<num_sms * 7, 256, 0, s>>>(a));
+  LV_TIMED(prof, K_MERGE_MID, s, k_merge_block<WK, 128, kMidCap, 2><<<num_sms * 12, 128, kMidSmem, s>>>(a));
+  LV_TIMED(prof, K_MERGE_BLOCK, s, k_merge_block<WK, 512, kBlockCap, 3><<<num_sms * 3, 512, kSmem, s>>>(a));
+  if (a.big.ws.slots > 0) {
+    if (prof) prof->begin(K_MERGE_BIG, s);
+    big_merge(a.big, WK, num_sms, s);
+    if (prof) prof->end(K_MERGE_BIG, s);
+  }
 }
 
 template <int WK>
 void mod_rows_t(const GView &g, const int32_t *memb, int64_t *sigma_out, Counters *ctr, int num_sms, cudaStream_t s) {
-  k_mod_rows<WK><<<grid_for(g.n * 32, 256, num_sms, 16), 256, 0, s>>>(g, memb, sigma_out, ctr);
+  LV_LAUNCH(k_mod_rows<WK><<<grid_for(g.n * 32, 256, num_sms, 16), 256, 0, s>>>(g, memb, sigma_out, ctr));
 }
 
 }  // namespace
@@ -532,48 +521,49 @@ void scan_u64(const unsigned long long *in, int64_t *out, int64_t n, int mode, l
     return;
   }
   const int64_t nb = (n + kScanTile - 1) / kScanTile;
-  if (mode == 0) k_scan_reduce<0><<<(unsigned)nb, kScanNT, 0, s>>>(in, n, tmp);
-  else k_scan_reduce<1><<<(unsigned)nb, kScanNT, 0, s>>>(in, n, tmp);
-  k_scan_blocks<<<1, kScanNT, 0, s>>>(tmp, nb, total);
-  if (mode == 0) k_scan_down<0><<<(unsigned)nb, kScanNT, 0, s>>>(in, out, n, tmp);
-  else k_scan_down<1><<<(unsigned)nb, kScanNT, 0, s>>>(in, out, n, tmp);
+  if (mode == 0) LV_LAUNCH(k_scan_reduce<0><<<(unsigned)nb, kScanNT, 0, s>>>(in, n, tmp));
+  else LV_LAUNCH(k_scan_reduce<1><<<(unsigned)nb, kScanNT, 0, s>>>(in, n, tmp));
+  LV_LAUNCH(k_scan_blocks<<<1, kScanNT, 0, s>>>(tmp, nb, total));
+  if (mode == 0) LV_LAUNCH(k_scan_down<0><<<(unsigned)nb, kScanNT, 0, s>>>(in, out, n, tmp));
+  else LV_LAUNCH(k_scan_down<1><<<(unsigned)nb, kScanNT, 0, s>>>(in, out, n, tmp));
 }
 
 void agg_count_scan(const AggArgs &a, int num_sms, cudaStream_t s) {
   const int64_t n = a.g.n;
   cudaMemsetAsync(a.cnt, 0, (size_t)n * sizeof(unsigned long long), s);
   cudaMemsetAsync(a.cdeg, 0, (size_t)n * sizeof(unsigned long long), s);
-  k_comm_count<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(a.g, a.Cp, a.cnt, a.cdeg);
+  LV_LAUNCH(k_comm_count<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(a.g, a.Cp, a.cnt, a.cdeg));
   scan_u64(a.cnt, a.newid, n, 1, a.scan_tmp, &a.ctr->scan_total[0], s);
   scan_u64(a.cnt, a.coff, n, 0, a.scan_tmp, &a.ctr->scan_total[1], s);
   scan_u64(a.cdeg, a.hoff, n, 0, a.scan_tmp, &a.ctr->scan_total[2], s);
-  k_write_total<<<1, 1, 0, s>>>(a.newid, n, &a.ctr->scan_total[0]);
-  k_write_total<<<1, 1, 0, s>>>(a.coff, n, &a.ctr->scan_total[1]);
-  k_write_total<<<1, 1, 0, s>>>(a.hoff, n, &a.ctr->scan_total[2]);
+  LV_LAUNCH(k_write_total<<<1, 1, 0, s>>>(a.newid, n, &a.ctr->scan_total[0]));
+  LV_LAUNCH(k_write_total<<<1, 1, 0, s>>>(a.coff, n, &a.ctr->scan_total[1]));
+  LV_LAUNCH(k_write_total<<<1, 1, 0, s>>>(a.hoff, n, &a.ctr->scan_total[2]));
 }
 
 void agg_scatter_compact(const AggArgs &a, int num_sms, cudaStream_t s) {
   const int64_t n = a.g.n;
   // cnt is reused as the scatter cursor
   cudaMemsetAsync(a.cnt, 0, (size_t)n * sizeof(unsigned long long), s);
-  k_comm_scatter<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(n, a.Cp, a.cnt, a.coff, a.newid, a.members);
-  k_comm_compact<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(a, n);
+  LV_LAUNCH(k_comm_scatter<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(n, a.Cp, a.cnt, a.coff, a.newid, a.members));
+  LV_LAUNCH(k_comm_compact<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(a, n));
+  // member-degree prefix in community-vertex CSR order (mprefix[t] of the
+  // first member of a community equals its row offset hoff)
+  LV_LAUNCH(k_member_deg<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(a.g, a.members, a.cdeg));
+  scan_u64(a.cdeg, a.mprefix, n, 0, a.scan_tmp, &a.ctr->scan_total[3], s);
 }
 
-void agg_merge(const AggArgs &a, int64_t gamma, int num_sms, cudaStream_t s) {
+void agg_merge(const AggArgs &a, int64_t gamma, int num_sms, cudaStream_t s, KernelProf *prof) {
   if (gamma <= 0) return;
   (void)gamma;
   // a.wkind describes the input G'
-  switch (a.wkind) {
-    case W_UNIT: merge_t<W_UNIT>(a, num_sms, s); break;
-    case W_I32: merge_t<W_I32>(a, num_sms, s); break;
-    default: merge_t<W_I64>(a, num_sms, s); break;
-  }
+  if (a.wkind == W_UNIT) merge_t<W_UNIT>(a, num_sms, s, prof);
+  else merge_t<W_U32>(a, num_sms, s, prof);
 }
 
 void dendrogram_lookup(int32_t *C, const int32_t *Cp, int64_t n, int num_sms, cudaStream_t s) {
   if (n <= 0) return;
-  k_dendro<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(C, Cp, n);
+  LV_LAUNCH(k_dendro<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(C, Cp, n));
 }
 
 void modularity_sums(const GView &g, int wkind, const int32_t *memb, const int64_t *sigma, int64_t *sigma_scratch,
@@ -585,12 +575,9 @@ void modularity_sums(const GView &g, int wkind, const int32_t *memb, const int64
     sig_out = sigma_scratch;
     sigma = sigma_scratch;
   }
-  switch (wkind) {
-    case W_UNIT: mod_rows_t<W_UNIT>(g, memb, sig_out, ctr, num_sms, s); break;
-    case W_I32: mod_rows_t<W_I32>(g, memb, sig_out, ctr, num_sms, s); break;
-    default: mod_rows_t<W_I64>(g, memb, sig_out, ctr, num_sms, s); break;
-  }
-  k_sigma_sq<<<grid_for(g.n, 256, num_sms, 16), 256, 0, s>>>(sigma, g.n, ctr);
+  if (wkind == W_UNIT) mod_rows_t<W_UNIT>(g, memb, sig_out, ctr, num_sms, s);
+  else mod_rows_t<W_U32>(g, memb, sig_out, ctr, num_sms, s);
+  LV_LAUNCH(k_sigma_sq<<<grid_for(g.n, 256, num_sms, 16), 256, 0, s>>>(sigma, g.n, ctr));
 }
 
 void renumber_dense(int32_t *x, int64_t n, int64_t idspace, unsigned long long *used, int64_t *newid,
@@ -600,9 +587,9 @@ void renumber_dense(int32_t *x, int64_t n, int64_t idspace, unsigned long long *
     return;
   }
   cudaMemsetAsync(used, 0, (size_t)idspace * sizeof(unsigned long long), s);
-  k_mark_used<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(x, n, used);
+  LV_LAUNCH(k_mark_used<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(x, n, used));
   scan_u64(used, newid, idspace, 1, tmp, total, s);
-  k_relabel<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(x, n, newid);
+  LV_LAUNCH(k_relabel<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(x, n, newid));
 }
 
 }  // namespace lv

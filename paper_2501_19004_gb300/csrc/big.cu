@@ -1,0 +1,385 @@
+// Big items on sm_103a: hub vertices of the local-moving phase (Algorithm 5)
+// and large communities of the aggregation phase (Algorithm 6) of arXiv
+// 2501.19004, i.e. every item with more than 4096 table entries.
+//
+// The paper gives such items a thread block each (Sec. 4.3.4).  On skewed
+// graphs one item can hold hundreds of millions of entries, so here an item's
+// entries are cut into chunks of 4096 that all blocks of the grid share:
+//   k_big_plan    table offsets and chunk counts of every item (one block);
+//   k_big_accum   each block pre-aggregates one chunk in shared memory
+//                 (hot keys summed across the warp first), then adds the
+//                 chunk's distinct keys into the item's global table;
+//   k_big_eval    (moving) blocks scan table slices: argmax of Eq. 2 per
+//                 slice, clearing the slots as they go;
+//   k_big_decide  (moving) one block per hub reduces its slices, decides and
+//                 re-marks the neighbours;
+//   k_big_emit    (aggregation) blocks scan table slices and append the
+//                 super-edges to the community's row, clearing the slots.
+// For aggregation an item's entries are the concatenated rows of its member
+// vertices, located through the member-degree prefix (community-vertex CSR).
+#include <climits>
+
+#include "internal.h"
+#include "tables.cuh"
+
+namespace lv {
+namespace {
+
+constexpr int kNT = 512;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+enum { MODE_MOVE = 0, MODE_MERGE = 1 };
+
+__device__ __forceinline__ uint32_t table_cap(int64_t tot, int64_t keyspace) {
+  const uint64_t d = (uint64_t)(tot < keyspace ? tot : keyspace);
+  return pow2_at_least(2 * (d ? d : 1));
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(1024) k_big_plan(BigArgs a) {
+  __shared__ long long sc0[33], sc1[33], sc2[33];
+  const int64_t nb = (int64_t)*a.count;
+  long long c_slots = 0, c_ch = 0, c_ev = 0;
+  unsigned long long members = 0;
+  for (int64_t base = 0; base < nb; base += 1024) {
+    const int64_t k = base + threadIdx.x;
+    long long tot = 0, cap = 0, nch = 0, nev = 0;
+    if (k < nb) {
+      const int32_t it = a.items[k];
+      if (MODE == MODE_MOVE) {
+        tot = a.g.end[it] - a.g.begin[it];
+      } else {
+        tot = a.oend[it] - a.obegin[it];  // row capacity = total member degree
+        a.oend[it] = a.obegin[it];        // becomes the append cursor
+        members += (unsigned long long)a.kcnt[it];
+      }
+      a.ws.tot[k] = tot;
+      cap = table_cap(tot, a.keyspace);
+      nch = (tot + kBigChunk - 1) / kBigChunk;
+      nev = (cap + kBigEvalSlots - 1) / kBigEvalSlots;
+    }
+    long long t0, t1, t2;
+    const long long e0 = block_scan_ex<1024>(cap, sc0, &t0);
+    const long long e1 = block_scan_ex<1024>(nch, sc1, &t1);
+    const long long e2 = block_scan_ex<1024>(nev, sc2, &t2);
+    if (k < nb) {
+      a.ws.toff[k] = c_slots + e0;
+      a.ws.cpre[k] = c_ch + e1;
+      a.ws.epre[k] = c_ev + e2;
+    }
+    c_slots += t0;
+    c_ch += t1;
+    c_ev += t2;
+  }
+  if (MODE == MODE_MERGE) {
+    members = warp_sum_u(members);
+    if ((threadIdx.x & 31) == 0 && members) atomicAdd(&a.ctr->mg_work[kBigBin][1], members);
+  }
+  if (threadIdx.x == 0) {
+    const bool fits = c_slots <= a.ws.slots && c_ev <= a.ws.parts;
+    if (!fits) atomicOr(&a.ctr->error, (unsigned long long)ERR_HASH);
+    a.ws.toff[nb] = c_slots;
+    a.ws.cpre[nb] = fits ? c_ch : 0;
+    a.ws.epre[nb] = fits ? c_ev : 0;
+    if (MODE == MODE_MERGE) atomicAdd(&a.ctr->mg_work[kBigBin][0], (unsigned long long)nb);
+  }
+}
+
+// Gather kRun entries of an item's entry sequence below xe: positions x,
+// x + stride, ... for a hub's row (coalesced across threads), consecutive
+// positions x, x + 1, ... for a community's member rows (one member search
+// per run).
+template <int MODE, int WK>
+__device__ __forceinline__ void gather_item(const BigArgs &a, int32_t it, int64_t x, int64_t stride, int64_t xe,
+                                            int32_t (&kk)[kRun], uint32_t (&ww)[kRun]) {
+#pragma unroll
+  for (int u = 0; u < kRun; ++u) {
+    kk[u] = kEmpty;
+    ww[u] = 0;
+  }
+  if (MODE == MODE_MOVE) {
+    const int64_t b = a.g.begin[it];
+    int32_t jj[kRun];
+#pragma unroll
+    for (int u = 0; u < kRun; ++u) {
+      jj[u] = -2;
+      const int64_t p = x + u * stride;
+      if (p < xe) {
+        jj[u] = __ldg(a.g.col + b + p);
+        ww[u] = load_w<WK>(a.g.w, b + p);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kRun; ++u) kk[u] = (jj[u] >= 0 && jj[u] != it) ? a.Cp[jj[u]] : kEmpty;
+  } else {
+    if (x >= xe) return;
+    const int64_t m0 = a.kcoff[it];
+    const int64_t base = a.obegin[it];  // = mprefix[m0]
+    int64_t t = m0 + upper_index(a.mprefix + m0, a.kcnt[it], base + x);
+    int64_t mstart = a.mprefix[t];
+    int32_t v = a.members[t];
+    int64_t rb = a.g.begin[v], rlen = a.g.end[v] - rb;
+    int32_t jj[kRun];
+    int64_t ee[kRun];
+#pragma unroll
+    for (int u = 0; u < kRun; ++u) {
+      jj[u] = -2;
+      if (x + u < xe) {
+        int64_t pos = base + x + u;
+        while (pos >= mstart + rlen) {  // next member with entries
+          ++t;
+          mstart = a.mprefix[t];
+          v = a.members[t];
+          rb = a.g.begin[v];
+          rlen = a.g.end[v] - rb;
+        }
+        ee[u] = rb + (pos - mstart);
+        jj[u] = __ldg(a.g.col + ee[u]);
+        ww[u] = load_w<WK>(a.g.w, ee[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kRun; ++u) kk[u] = jj[u] >= 0 ? a.Cp[jj[u]] : kEmpty;
+  }
+}
+
+template <int MODE, int WK>
+__global__ void __launch_bounds__(kNT) k_big_accum(BigArgs a) {
+  extern __shared__ uint32_t dyn[];
+  int32_t *skeys = (int32_t *)dyn;
+  uint32_t *svals = dyn + kBigSmemSlots;
+  const int64_t nb = (int64_t)*a.count;
+  const int64_t total = a.ws.cpre[nb];
+  unsigned long long entries = 0;
+  for (int s = threadIdx.x; s < kBigSmemSlots; s += kNT) {
+    skeys[s] = kEmpty;
+    svals[s] = 0;
+  }
+  __syncthreads();
+  for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+    const int64_t k = upper_index(a.ws.cpre, nb, g);
+    const int32_t it = a.items[k];
+    const int64_t tot = a.ws.tot[k];
+    const int64_t x0 = (g - a.ws.cpre[k]) * kBigChunk;
+    const int64_t x1 = x0 + kBigChunk < tot ? x0 + kBigChunk : tot;
+    int32_t kk[kRun];
+    uint32_t ww[kRun];
+    if (MODE == MODE_MOVE) {
+      gather_item<MODE, WK>(a, it, x0 + threadIdx.x, kNT, x1, kk, ww);
+    } else {
+      const int64_t xs = x0 + (int64_t)threadIdx.x * kRun;
+      gather_item<MODE, WK>(a, it, xs, 1, xs + kRun < x1 ? xs + kRun : x1, kk, ww);
+    }
+    if (threadIdx.x == 0) entries += (unsigned long long)(x1 - x0);
+#pragma unroll
+    for (int u = 0; u < kRun; ++u) warp_insert_sm(skeys, svals, kBigSmemSlots - 1, kk[u], ww[u], a.ctr);
+    __syncthreads();
+    const int64_t toff = a.ws.toff[k];
+    const uint32_t gmask = table_cap(tot, a.keyspace) - 1;
+    for (int s = threadIdx.x; s < kBigSmemSlots; s += kNT) {
+      const int32_t key = skeys[s];
+      if (key == kEmpty) continue;
+      gm_insert(a.ws.keys + toff, a.ws.vals + toff, gmask, key, svals[s], a.ctr);
+      skeys[s] = kEmpty;
+      svals[s] = 0;
+    }
+    __syncthreads();
+  }
+  unsigned long long w[1] = {entries};
+  flush_work(w, MODE == MODE_MOVE ? &a.ctr->mv_work[kBigBin][1] : &a.ctr->mg_work[kBigBin][2]);
+}
+
+// Moving: per table slice, the best candidate (score, then lowest id) and
+// the weight to the vertex's own community; slots are cleared.
+__global__ void __launch_bounds__(kNT) k_big_eval(BigArgs a) {
+  const int64_t nb = (int64_t)*a.count;
+  const int64_t total = a.ws.epre[nb];
+  unsigned long long distinct = 0;
+  for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+    const int64_t k = upper_index(a.ws.epre, nb, g);
+    const int32_t i = a.items[k];
+    const int64_t cap = table_cap(a.ws.tot[k], a.keyspace);
+    const int64_t s0 = (g - a.ws.epre[k]) * kBigEvalSlots;
+    const int64_t s1 = s0 + kBigEvalSlots < cap ? s0 + kBigEvalSlots : cap;
+    int32_t *keys = a.ws.keys + a.ws.toff[k];
+    uint32_t *vals = a.ws.vals + a.ws.toff[k];
+    const int32_t d = a.Cp[i];
+    const long long Ki = a.K[i];
+    long long best_s = LLONG_MIN, Kid = 0;
+    int32_t best_c = INT_MAX;
+    for (int64_t s = s0 + threadIdx.x; s < s1; s += kNT) {
+      const int32_t c = __ldcg(keys + s);
+      if (c == kEmpty) continue;
+      const long long v = __ldcg(vals + s);
+      keys[s] = kEmpty;
+      vals[s] = 0;
+      if (c == d) {
+        Kid = v;
+        continue;
+      }
+      ++distinct;
+      const long long sc = a.two_m * v - Ki * a.Sigma[c];
+      if (better(sc, c, best_s, best_c)) {
+        best_s = sc;
+        best_c = c;
+      }
+    }
+    block_argmax_sum<kNT>(best_s, best_c, Kid);
+    if (threadIdx.x == 0) {
+      a.ws.part_s[g] = best_s;
+      a.ws.part_c[g] = best_c;
+      a.ws.part_kid[g] = (unsigned long long)Kid;
+    }
+  }
+  unsigned long long w[1] = {distinct};
+  flush_work(w, &a.ctr->mv_work[kBigBin][2]);
+}
+
+// Moving: one block per hub reduces its slices and applies Algorithm 5's
+// decision; movers re-mark their neighbours.
+__global__ void __launch_bounds__(kNT) k_big_decide(BigArgs a) {
+  __shared__ int32_t s_target;
+  const int64_t nb = (int64_t)*a.count;
+  if (a.ws.epre[nb] == 0 && nb > 0) return;  // plan found no room (error already set)
+  unsigned long long glo = 0, ghi = 0, gm = 0;
+  unsigned long long work[3] = {0, 0, 0};  // vertices, movers, mover entries
+  for (int64_t k = blockIdx.x; k < nb; k += gridDim.x) {
+    const int32_t i = a.items[k];
+    long long best_s = LLONG_MIN, Kid = 0;
+    int32_t best_c = INT_MAX;
+    for (int64_t p = a.ws.epre[k] + threadIdx.x; p < a.ws.epre[k + 1]; p += kNT) {
+      const long long s = a.ws.part_s[p];
+      const int32_t c = a.ws.part_c[p];
+      Kid += (long long)a.ws.part_kid[p];
+      if (better(s, c, best_s, best_c)) {
+        best_s = s;
+        best_c = c;
+      }
+    }
+    block_argmax_sum<kNT>(best_s, best_c, Kid);
+    const int64_t b = a.g.begin[i], e = a.g.end[i];
+    if (threadIdx.x == 0) {
+      const int32_t d = a.Cp[i];
+      const int32_t t = finish_decision(a.two_m, a.Sigma, a.pickless, d, a.K[i], Kid, best_s, best_c, glo, ghi, gm);
+      work[0] += 1;
+      if (t >= 0) {
+        work[1] += 1;
+        work[2] += (unsigned long long)(e - b);
+        const unsigned long long pos = atomicAdd(&a.ctr->movers, 1ull);
+        a.mv_vertex[pos] = i;
+        a.mv_target[pos] = t;
+      }
+      s_target = t;
+    }
+    __syncthreads();
+    if (s_target >= 0)
+      for (int64_t q = b + threadIdx.x; q < e; q += kNT) {
+        const int32_t j = __ldg(a.g.col + q);
+        if (j != i) a.flag[j] = 1;
+      }
+    __syncthreads();
+  }
+  flush_gains(glo, ghi, gm, a.ctr);
+  unsigned long long w0[1] = {work[0]};
+  flush_work(w0, &a.ctr->mv_work[kBigBin][0]);
+  unsigned long long w1[2] = {work[1], work[2]};
+  flush_work(w1, &a.ctr->mv_work[kBigBin][3]);
+}
+
+// Aggregation: append every occupied slot of a slice to the community's row
+// (super-edge (c, key, weight)); slots are cleared.
+__global__ void __launch_bounds__(kNT) k_big_emit(BigArgs a) {
+  __shared__ unsigned long long s_cnt;
+  __shared__ unsigned long long s_base;
+  const int64_t nb = (int64_t)*a.count;
+  const int64_t total = a.ws.epre[nb];
+  unsigned long long written = 0;
+  const int lane = threadIdx.x & 31;
+  for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
+    const int64_t k = upper_index(a.ws.epre, nb, g);
+    const int32_t c = a.items[k];
+    const int64_t cap = table_cap(a.ws.tot[k], a.keyspace);
+    const int64_t s0 = (g - a.ws.epre[k]) * kBigEvalSlots;
+    int32_t *keys = a.ws.keys + a.ws.toff[k];
+    uint32_t *vals = a.ws.vals + a.ws.toff[k];
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    // two passes over the slice: count, then write at a reserved range
+    int32_t key[kBigEvalSlots / kNT];
+    uint32_t val[kBigEvalSlots / kNT];
+    unsigned mine = 0;
+#pragma unroll
+    for (int r = 0; r < kBigEvalSlots / kNT; ++r) {
+      const int64_t s = s0 + r * kNT + threadIdx.x;
+      key[r] = kEmpty;
+      if (s < cap) {
+        key[r] = __ldcg(keys + s);
+        if (key[r] != kEmpty) {
+          val[r] = __ldcg(vals + s);
+          keys[s] = kEmpty;
+          vals[s] = 0;
+          ++mine;
+        }
+      }
+    }
+    const unsigned wsum = __reduce_add_sync(kFull, mine);
+    unsigned woff = 0;
+    if (lane == 0 && wsum) woff = (unsigned)atomicAdd(&s_cnt, (unsigned long long)wsum);
+    woff = __shfl_sync(kFull, woff, 0);
+    // exclusive prefix of `mine` within the warp
+    unsigned incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_cnt) s_base = atomicAdd((unsigned long long *)(a.oend + c), s_cnt);
+    __syncthreads();
+    unsigned long long pos = s_base + woff + (incl - mine);
+#pragma unroll
+    for (int r = 0; r < kBigEvalSlots / kNT; ++r) {
+      if (key[r] == kEmpty) continue;
+      a.ocol[pos] = key[r];
+      a.ow[pos] = val[r];
+      ++pos;
+    }
+    if (threadIdx.x == 0) written += s_cnt;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && written) {
+    atomicAdd(&a.ctr->nnz_out, written);
+    atomicAdd(&a.ctr->mg_work[kBigBin][3], written);
+  }
+}
+
+template <int MODE, int WK>
+void big_run(const BigArgs &b, int num_sms, cudaStream_t s) {
+  static bool attr_done = false;
+  constexpr size_t kSmem = (size_t)kBigSmemSlots * (sizeof(int32_t) + sizeof(uint32_t));
+  if (!attr_done) {
+    cudaFuncSetAttribute(k_big_accum<MODE, WK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+    attr_done = true;
+  }
+  LV_LAUNCH(k_big_plan<MODE><<<1, 1024, 0, s>>>(b));
+  LV_LAUNCH(k_big_accum<MODE, WK><<<num_sms * 3, kNT, kSmem, s>>>(b));
+  if (MODE == MODE_MOVE) {
+    LV_LAUNCH(k_big_eval<<<num_sms * 3, kNT, 0, s>>>(b));
+    LV_LAUNCH(k_big_decide<<<num_sms * 2, kNT, 0, s>>>(b));
+  } else {
+    LV_LAUNCH(k_big_emit<<<num_sms * 3, kNT, 0, s>>>(b));
+  }
+}
+
+}  // namespace
+
+void big_move(const BigArgs &b, int wkind, int num_sms, cudaStream_t s) {
+  if (wkind == W_UNIT) big_run<MODE_MOVE, W_UNIT>(b, num_sms, s);
+  else big_run<MODE_MOVE, W_U32>(b, num_sms, s);
+}
+
+void big_merge(const BigArgs &b, int wkind, int num_sms, cudaStream_t s) {
+  if (wkind == W_UNIT) big_run<MODE_MERGE, W_UNIT>(b, num_sms, s);
+  else big_run<MODE_MERGE, W_U32>(b, num_sms, s);
+}
+
+}  // namespace lv

@@ -8,18 +8,17 @@ namespace lv {
 constexpr int32_t kEmpty = -1;          // empty hashtable key
 constexpr int kWarp = 32;
 
-// Weight representations of a CSR: unit (no array), int32 (input graph),
-// int64 (super-vertex graphs, whose weights can exceed 2^31).
-enum WKind : int { W_UNIT = 0, W_I32 = 1, W_I64 = 2 };
+// Weight representations of a CSR: unit (no array) or uint32.  The input's
+// positive int32 weights are read as uint32; super-vertex graphs store uint32
+// too, because every weight is at most 2m < 2^32.
+enum WKind : int { W_UNIT = 0, W_U32 = 1 };
 
 template <int WK>
-__device__ __forceinline__ int64_t load_w(const void *w, int64_t e) {
+__device__ __forceinline__ uint32_t load_w(const void *w, int64_t e) {
   if constexpr (WK == W_UNIT) {
-    return 1;
-  } else if constexpr (WK == W_I32) {
-    return (int64_t)__ldg((const int32_t *)w + e);
+    return 1u;
   } else {
-    return (int64_t)__ldg((const long long *)w + e);
+    return __ldg((const unsigned int *)w + e);
   }
 }
 
@@ -38,15 +37,22 @@ enum ErrBits : unsigned long long { ERR_HASH = 1ull, ERR_RANGE = 2ull, ERR_TIMEO
 
 // Small device-resident counters block.
 struct Counters {
-  unsigned long long bin_count[8];  // per-bucket bin sizes (move) / per-pass bins (merge)
+  unsigned long long bin_count[8];  // local-moving bin sizes of the current bucket
   unsigned long long selected;      // vertices taken into the bucket (incl. degree 0)
   unsigned long long movers;        // decisions to move in this bucket
-  unsigned long long it_gain_lo;    // iteration: sum of low 32 bits of the gains
-  unsigned long long it_gain_hi;    // iteration: sum of high 32 bits of the gains
+  // ---- zeroed every iteration ----
+  unsigned long long it_gain_lo;    // sum of low 32 bits of the gains
+  unsigned long long it_gain_hi;    // sum of high 32 bits of the gains
   unsigned long long it_moves;
   unsigned long long it_evaluated;
   unsigned long long it_skipped;    // learned mode: flagged vertices skipped by the predictor
+  unsigned long long mv_work[5][5]; // per move bin: vertices, entries, distinct keys, movers, mover entries
+  // ---- zeroed every pass ----
+  unsigned long long mbin_count[8]; // aggregation bin sizes
+  unsigned long long mg_work[5][4]; // per merge bin: communities, members, entries, entries written
   unsigned long long maxdeg;
+  unsigned long long big_slots;     // bound on the global table slots of big items
+  unsigned long long big_items;     // number of big items (hubs / large communities)
   unsigned long long nnz_out;       // entries written by aggregation
   unsigned long long error;
   unsigned long long q_sin;         // modularity: sum of internal weights
@@ -55,6 +61,7 @@ struct Counters {
   unsigned long long scan_total[4]; // totals of the aggregation scans
   unsigned long long pad[4];
 };
+constexpr int kIterCounterWords = 5 + 25;
 
 // MurmurHash3 finaliser (Appleby, public domain).
 __host__ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
@@ -126,6 +133,59 @@ __device__ __forceinline__ void flush_gains(unsigned long long lo, unsigned long
     atomicAdd(&ctr->it_gain_hi, hi);
     atomicAdd(&ctr->it_moves, moves);
   }
+}
+
+// Work counters of one kernel: reduced per warp, then one atomic per field.
+template <int N>
+__device__ __forceinline__ void flush_work(unsigned long long (&w)[N], unsigned long long *dst) {
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const unsigned long long v = warp_sum_u(w[k]);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst + k, v);
+  }
+}
+
+// The decision of Algorithm 5 for vertex i in community d, given the best
+// neighbour community (best_s, best_c) and K_{i->d}: returns the target or -1.
+// A move needs a strictly larger score than staying and, in Pick-Less mode,
+// a target id below d.  The gain s(c*) - s(d) is positive and below 2^64.
+__device__ __forceinline__ int32_t finish_decision(long long two_m, const int64_t *Sigma, int pickless, int32_t d,
+                                                   long long Ki, long long Kid, long long best_s, int32_t best_c,
+                                                   unsigned long long &glo, unsigned long long &ghi,
+                                                   unsigned long long &gm) {
+  const long long s_d = two_m * Kid - Ki * (Sigma[d] - Ki);
+  if (best_c == 0x7FFFFFFF || !(best_s > s_d) || (pickless && best_c > d)) return -1;
+  const unsigned long long gain = (unsigned long long)best_s - (unsigned long long)s_d;
+  glo += gain & 0xFFFFFFFFull;
+  ghi += gain >> 32;
+  gm += 1;
+  return best_c;
+}
+
+// Block-wide argmax (score, then lowest id) and sum; the result is valid in
+// every thread of warp 0.
+template <int NT>
+__device__ __forceinline__ void block_argmax_sum(long long &s, int32_t &c, long long &sum) {
+  __shared__ long long rs[NT / 32];
+  __shared__ int32_t rc[NT / 32];
+  __shared__ long long rsum[NT / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  warp_argmax(s, c);
+  sum = warp_sum(sum);
+  if (lane == 0) {
+    rs[warp] = s;
+    rc[warp] = c;
+    rsum[warp] = sum;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    s = lane < NT / 32 ? rs[lane] : (long long)0x8000000000000000ull;
+    c = lane < NT / 32 ? rc[lane] : 0x7FFFFFFF;
+    sum = lane < NT / 32 ? rsum[lane] : 0;
+    warp_argmax(s, c);
+    sum = warp_sum(sum);
+  }
+  __syncthreads();
 }
 
 // Round up to a power of two (x >= 1).

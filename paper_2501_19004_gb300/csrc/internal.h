@@ -7,25 +7,83 @@
 
 namespace lv {
 
-// Degree bins of the local-moving phase: a thread per vertex up to
-// kThreadMaxDeg entries, a warp with a shared-memory table up to
-// kWarpMaxDeg, a block with a shared-memory table up to kBlockMaxDeg, and a
-// block with a global-memory table beyond (hubs).
+// Degree bins (entries per vertex when moving, per community when
+// aggregating): a thread with registers up to kThreadMaxDeg entries, a warp
+// with a shared-memory table up to kWarpMaxDeg, a 128-thread block up to
+// kMidMaxDeg, a 512-thread block up to kBlockMaxDeg (shared tables of twice
+// the entries), and beyond that chunks over the whole grid with global tables.
 constexpr int kThreadMaxDeg = 16;
 constexpr int kWarpMaxDeg = 256;
 constexpr int kWarpCap = 512;       // >= 2 * kWarpMaxDeg, power of two
+constexpr int kMidMaxDeg = 1024;
+constexpr int kMidCap = 2048;
 constexpr int kBlockMaxDeg = 4096;
-constexpr int kBlockCap = 8192;     // >= 2 * kBlockMaxDeg, power of two
-constexpr int kNumBins = 4;
+constexpr int kBlockCap = 8192;
+constexpr int kNumBins = 5;
+constexpr int kBigBin = 4;
 
-// Global hashtable workspace for hub vertices / large communities: each
-// block of the hub kernels owns one slice of `slice` slots.
-struct HubWs {
+__host__ __device__ __forceinline__ int degree_bin(int64_t d) {
+  return d <= kThreadMaxDeg ? 0 : d <= kWarpMaxDeg ? 1 : d <= kMidMaxDeg ? 2 : d <= kBlockMaxDeg ? 3 : 4;
+}
+
+// Global tables of big items (hub vertices in local moving, communities with
+// more than kBlockMaxDeg entries in aggregation).  Tables are kept empty
+// between uses: the kernels that read a slot also clear it.
+constexpr int kBigChunk = 4096;       // entries per accumulation chunk (512 threads x 8)
+constexpr int kBigSmemSlots = 8192;   // shared pre-aggregation table per block
+constexpr int kBigEvalSlots = 8192;   // table slots per evaluation block
+struct BigWs {
   int32_t *keys = nullptr;
-  unsigned long long *vals = nullptr;
-  int64_t slice = 0;   // slots per block
-  int blocks = 0;      // number of slices
+  uint32_t *vals = nullptr;
+  int64_t slots = 0;                  // capacity of keys/vals
+  int64_t *tot = nullptr;             // [items] entries of each item
+  int64_t *toff = nullptr;            // [items+1] table offset
+  int64_t *cpre = nullptr;            // [items+1] accumulation chunk prefix
+  int64_t *epre = nullptr;            // [items+1] evaluation chunk prefix
+  long long *part_s = nullptr;        // [parts] partial argmax of an evaluation block
+  int32_t *part_c = nullptr;
+  unsigned long long *part_kid = nullptr;
+  int64_t parts = 0;                  // capacity of part_*
+  int64_t item_cap = 0;               // capacity of tot/toff/cpre/epre
 };
+
+struct BigArgs {
+  GView g;
+  const int32_t *Cp;                  // C' (move: snapshot; merge: dense new ids)
+  const int32_t *items;               // big item list (vertices or communities)
+  const unsigned long long *count;    // its length (device)
+  int64_t keyspace;                   // number of possible keys: n' or |Gamma|
+  BigWs ws;
+  Counters *ctr;
+  // local moving
+  const int64_t *K;
+  const int64_t *Sigma;
+  uint8_t *flag;
+  long long two_m;
+  int pickless;
+  int32_t *mv_vertex;
+  int32_t *mv_target;
+  // aggregation
+  const int64_t *mprefix;             // member-degree exclusive prefix (community-vertex CSR order)
+  const int64_t *kcoff;
+  const int32_t *kcnt;
+  const int32_t *members;
+  const int64_t *obegin;
+  int64_t *oend;
+  int32_t *ocol;
+  uint32_t *ow;
+};
+
+// big hub vertices of one bucket step / big communities of one aggregation
+void big_move(const BigArgs &b, int wkind, int num_sms, cudaStream_t s);
+void big_merge(const BigArgs &b, int wkind, int num_sms, cudaStream_t s);
+
+inline int grid_for(int64_t n, int threads, int num_sms, int per_sm) {
+  int64_t g = (n + threads - 1) / threads;
+  const int64_t cap = (int64_t)num_sms * per_sm;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
 
 struct MoveArgs {
   GView g;
@@ -41,7 +99,6 @@ struct MoveArgs {
   int32_t *bins[kNumBins];
   int32_t *mv_vertex;
   int32_t *mv_target;
-  HubWs ws;
   Counters *ctr;
   // learned mode (null when plain)
   const float *mlp;          // device parameters
@@ -50,8 +107,47 @@ struct MoveArgs {
   int learned;
 };
 
+// Kernel identifiers for the optional per-kernel event timing.
+enum KernelId : int {
+  K_SELECT = 0, K_MOVE_THREAD, K_MOVE_WARP, K_MOVE_MID, K_MOVE_BLOCK, K_MOVE_HUB, K_APPLY, K_PASS_INIT,
+  K_COMM_COUNT, K_SCATTER, K_MERGE_THREAD, K_MERGE_WARP, K_MERGE_MID, K_MERGE_BLOCK, K_MERGE_BIG, K_DENDRO,
+  K_MODULARITY, K_RENUMBER, K_NUM_KERNELS
+};
+extern const char *const kKernelNames[K_NUM_KERNELS];
+
+// Host-side event timing of selected kernels: a start and an end event
+// around each launch whose id is in `mask`; collect() (after a stream
+// synchronisation) adds the elapsed times up per kernel.
+struct KernelProf {
+  uint32_t mask = 0;
+  cudaEvent_t *pool = nullptr;
+  int pool_size = 0, used = 0;
+  int pending_kid[256];
+  double ms[K_NUM_KERNELS] = {};
+  long long launches[K_NUM_KERNELS] = {};
+  bool on(int kid) const { return (mask >> kid) & 1u; }
+  void begin(int kid, cudaStream_t s) {
+    if (!on(kid) || used + 2 > pool_size) return;
+    pending_kid[used / 2] = kid;
+    cudaEventRecord(pool[used++], s);
+  }
+  void end(int kid, cudaStream_t s) {
+    if (!on(kid) || (used & 1) == 0) return;
+    cudaEventRecord(pool[used++], s);
+  }
+  void collect() {
+    for (int k = 0; k + 1 < used; k += 2) {
+      float t = 0;
+      cudaEventElapsedTime(&t, pool[k], pool[k + 1]);
+      ms[pending_kid[k / 2]] += t;
+      launches[pending_kid[k / 2]] += 1;
+    }
+    used = 0;
+  }
+};
+
 // local-moving phase, one bucket step (select, decide per bin, apply)
-void move_bucket(const MoveArgs &a, int wkind, int num_sms, cudaStream_t s);
+void move_bucket(const MoveArgs &a, const BigArgs &big, int wkind, int num_sms, cudaStream_t s, KernelProf *prof);
 
 // pass initialisation: K (row sums on pass 0, else given), Sigma = K, C' = id,
 // flags = 1, max degree into ctr->maxdeg
@@ -80,8 +176,9 @@ struct AggArgs {
   int64_t *obegin;          // [Gamma]
   int64_t *oend;            // [Gamma]
   int32_t *ocol;
-  int64_t *ow;
-  HubWs ws;
+  uint32_t *ow;
+  int64_t *mprefix;         // [n'] member-degree prefix (scratch)
+  BigArgs big;
   Counters *ctr;
   long long *scan_tmp;      // block sums for the scans
   int64_t gamma;            // number of communities (keys of the merge tables)
@@ -93,7 +190,7 @@ void agg_count_scan(const AggArgs &a, int num_sms, cudaStream_t s);
 // member scatter + relabel C' to dense ids + per-community arrays + bins
 void agg_scatter_compact(const AggArgs &a, int num_sms, cudaStream_t s);
 // super-vertex rows (hash-merge of member rows); entries into ctr->nnz_out
-void agg_merge(const AggArgs &a, int64_t gamma, int num_sms, cudaStream_t s);
+void agg_merge(const AggArgs &a, int64_t gamma, int num_sms, cudaStream_t s, KernelProf *prof);
 
 // C[v] = Cp[C[v]]
 void dendrogram_lookup(int32_t *C, const int32_t *Cp, int64_t n, int num_sms, cudaStream_t s);
@@ -118,5 +215,16 @@ int64_t mlp_param_count();
 void mlp_features_init(float *feat, int64_t n, int num_sms, cudaStream_t s);
 
 size_t scan_tmp_elems(int64_t n);
+
+// Kernel launches issued by this thread since the last reset (the library's
+// own kernels only; memsets and copies are not counted).
+extern thread_local long long g_launches;
+#define LV_LAUNCH(...) (++::lv::g_launches, __VA_ARGS__)
+#define LV_TIMED(prof, kid, s, ...)          \
+  do {                                       \
+    if (prof) (prof)->begin((kid), (s));     \
+    LV_LAUNCH(__VA_ARGS__);                  \
+    if (prof) (prof)->end((kid), (s));       \
+  } while (0)
 
 }  // namespace lv

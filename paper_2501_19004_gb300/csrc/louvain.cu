@@ -21,6 +21,10 @@
 using namespace lv;
 typedef __int128 i128;
 
+namespace lv {
+thread_local long long g_launches = 0;
+}
+
 struct PassTiming {
   cudaEvent_t t0, t1, t2;  // pass start, after local moving, after aggregation
   bool aggregated;
@@ -53,10 +57,11 @@ struct louvain_ctx {
   long long *scan_tmp = nullptr;
   // ping-pong super-vertex graphs
   int32_t *pcol[2] = {};
-  int64_t *pw[2] = {}, *pbeg[2] = {}, *pend[2] = {};
-  // hub / large-community hashtable workspace
-  HubWs ws;
-  size_t ws_slots_alloc = 0;
+  uint32_t *pw[2] = {};
+  int64_t *pbeg[2] = {}, *pend[2] = {};
+  // global tables of big items (hubs, large communities)
+  BigWs big;
+  bool big_dirty = false;
   // learned predictor
   float *mlp = nullptr, *feat = nullptr;
 
@@ -77,6 +82,13 @@ struct louvain_ctx {
   cudaEvent_t run0 = nullptr, run1 = nullptr;
   double run_ms = 0;
   long long it_total = 0, moves_total = 0, evaluated_total = 0, skipped_total = 0;
+  long long launches = 0;
+  // per-kernel profile of the last run
+  KernelProf prof;
+  std::vector<cudaEvent_t> prof_events;
+  double kbytes[K_NUM_KERNELS] = {};
+  int cur_wbytes = 0;
+  bool pass_has_hubs = false;
 };
 
 namespace {
@@ -157,33 +169,59 @@ __global__ void k_validate(int64_t n, const int64_t *off, const int32_t *col, co
   if (wsum) atomicAdd(&ctr->q_sin, wsum);
 }
 
-// Ensure the global hashtable workspace can hold a table for `distinct`
-// keys in every one of its slices.
-louvain_status ensure_ws(louvain_ctx *x, uint64_t distinct) {
-  const int64_t need = (int64_t)pow2_at_least(2 * (distinct ? distinct : 1));
-  const size_t budget_slots = (size_t)1 << 28;  // 3 GiB of table at most
-  int blocks = 2 * x->num_sms;
-  if ((size_t)need * blocks > budget_slots) blocks = (int)std::max<int64_t>(1, (int64_t)(budget_slots / need));
-  const size_t slots = (size_t)need * blocks;
-  if (slots > x->ws_slots_alloc) {
-    if (x->ws.keys) {
-      cudaFreeAsync(x->ws.keys, x->stream);
-      cudaFreeAsync(x->ws.vals, x->stream);
-      x->allocs.erase(std::remove(x->allocs.begin(), x->allocs.end(), (void *)x->ws.keys), x->allocs.end());
-      x->allocs.erase(std::remove(x->allocs.begin(), x->allocs.end(), (void *)x->ws.vals), x->allocs.end());
-      x->bytes -= x->ws_slots_alloc * 12;
-      x->ws.keys = nullptr;
-      x->ws.vals = nullptr;
-      x->ws_slots_alloc = 0;
-    }
-    louvain_status st;
-    if ((st = dalloc_n(x, &x->ws.keys, (int64_t)slots))) return st;
-    if ((st = dalloc_n(x, &x->ws.vals, (int64_t)slots))) return st;
-    x->ws_slots_alloc = slots;
+void dfree(louvain_ctx *x, void *p) {
+  if (!p) return;
+  cudaFreeAsync(p, x->stream);
+  auto it = std::find(x->allocs.begin(), x->allocs.end(), p);
+  if (it != x->allocs.end()) x->allocs.erase(it);
+}
+
+// Grow the big-item workspace to `slots` table slots, `parts` evaluation
+// partials and `items` items; new tables are cleared (all keys empty).
+louvain_status ensure_big(louvain_ctx *x, int64_t slots, int64_t parts, int64_t items) {
+  louvain_status st;
+  BigWs &b = x->big;
+  if (slots > b.slots) {
+    dfree(x, b.keys);
+    dfree(x, b.vals);
+    b.keys = nullptr;
+    b.vals = nullptr;
+    b.slots = 0;
+    const int64_t want = slots + slots / 4;
+    if ((st = dalloc_n(x, &b.keys, want)) || (st = dalloc_n(x, &b.vals, want))) return st;
+    LV_CK(cudaMemsetAsync(b.keys, 0xFF, (size_t)want * sizeof(int32_t), x->stream));
+    LV_CK(cudaMemsetAsync(b.vals, 0, (size_t)want * sizeof(uint32_t), x->stream));
+    b.slots = want;
   }
-  x->ws.slice = need;
-  x->ws.blocks = (int)std::min<size_t>((size_t)blocks, x->ws_slots_alloc / (size_t)need);
+  if (parts > b.parts) {
+    dfree(x, b.part_s);
+    dfree(x, b.part_c);
+    dfree(x, b.part_kid);
+    const int64_t want = parts + parts / 4 + 64;
+    if ((st = dalloc_n(x, &b.part_s, want)) || (st = dalloc_n(x, &b.part_c, want)) ||
+        (st = dalloc_n(x, &b.part_kid, want)))
+      return st;
+    b.parts = want;
+  }
+  if (items > b.item_cap) {
+    dfree(x, b.tot);
+    dfree(x, b.toff);
+    dfree(x, b.cpre);
+    dfree(x, b.epre);
+    const int64_t want = items + items / 4 + 64;
+    if ((st = dalloc_n(x, &b.tot, want + 1)) || (st = dalloc_n(x, &b.toff, want + 1)) ||
+        (st = dalloc_n(x, &b.cpre, want + 1)) || (st = dalloc_n(x, &b.epre, want + 1)))
+      return st;
+    b.item_cap = want;
+  }
   return LOUVAIN_OK;
+}
+
+// Workspace for the big items counted in ctr->big_slots / big_items.
+louvain_status ensure_big_for(louvain_ctx *x, const Counters &h) {
+  if (h.big_items == 0) return LOUVAIN_OK;
+  const int64_t slots = (int64_t)h.big_slots;
+  return ensure_big(x, slots, slots / kBigEvalSlots + (int64_t)h.big_items + 1, (int64_t)h.big_items + 1);
 }
 
 louvain_status read_counters(louvain_ctx *x) {
@@ -201,6 +239,36 @@ void put128(int64_t *dst, i128 v) {
   dst[1] = (int64_t)(uint64_t)v;
 }
 
+// Algorithmic bytes of one iteration's kernels (what the method must move):
+// decide, per vertex: bin entry 4, row bounds 16, C'[i] 4, K_i 8, Sigma_d 8;
+// per entry: column 4 + weight + C'[j] 4; per distinct candidate: Sigma_c 8;
+// per mover: decision 8 + one flag byte per neighbour.  select: one flag byte
+// per vertex per bucket, plus flag write, row bounds and list entry of the
+// selected.  apply: decision 8, C' read/write 8, K_i 8, two Sigma atomics 16.
+void account_move(louvain_ctx *x, int64_t n, const Counters &h) {
+  if (x->prof.mask) x->prof.collect();
+  const double wb = x->cur_wbytes;
+  for (int b = 0; b < kNumBins; ++b) {
+    const unsigned long long *w = h.mv_work[b];
+    x->kbytes[K_MOVE_THREAD + b] +=
+        40.0 * w[0] + (8.0 + wb) * w[1] + 8.0 * w[2] + 8.0 * w[3] + 1.0 * w[4];
+  }
+  x->kbytes[K_SELECT] += (double)x->cfg.buckets * n + 21.0 * h.it_evaluated;
+  x->kbytes[K_APPLY] += 40.0 * h.it_moves;
+}
+
+// Aggregation kernels: per community: member offset/count 12, row bounds 16,
+// row end write 8; per member: id 4, row bounds 16; per entry: column 4 +
+// weight + C'[j] 4; per output entry: 8 (id and uint32 weight).
+void account_merge(louvain_ctx *x, const Counters &h) {
+  if (x->prof.mask) x->prof.collect();
+  const double wb = x->cur_wbytes;
+  for (int b = 0; b < kNumBins; ++b) {
+    const unsigned long long *w = h.mg_work[b];
+    x->kbytes[K_MERGE_THREAD + b] += 36.0 * w[0] + 20.0 * w[1] + (8.0 + wb) * w[2] + 8.0 * w[3];
+  }
+}
+
 // Local-moving phase (Algorithm 5) under the bucket schedule; returns l_i.
 louvain_status move_phase(louvain_ctx *x, const GView &g, int wk, int pass, double tau, int *li_out) {
   const louvain_config &cfg = x->cfg;
@@ -209,7 +277,7 @@ louvain_status move_phase(louvain_ctx *x, const GView &g, int wk, int pass, doub
   for (int t = 0; t < cfg.max_iterations; ++t) {
     const int rho = cfg.pickless_period;
     const int pickless = rho > 0 && ((t + rho / 2) % rho) == 0;
-    LV_CK(cudaMemsetAsync(&x->d_ctr->it_gain_lo, 0, 5 * sizeof(unsigned long long), x->stream));
+    LV_CK(cudaMemsetAsync(&x->d_ctr->it_gain_lo, 0, kIterCounterWords * sizeof(unsigned long long), x->stream));
     MoveArgs a{};
     a.g = g;
     a.Cp = x->Cp;
@@ -223,8 +291,23 @@ louvain_status move_phase(louvain_ctx *x, const GView &g, int wk, int pass, doub
     for (int k = 0; k < kNumBins; ++k) a.bins[k] = x->bins[k];
     a.mv_vertex = x->mv_vertex;
     a.mv_target = x->mv_target;
-    a.ws = x->ws;
     a.ctr = x->d_ctr;
+    BigArgs big{};
+    big.g = g;
+    big.Cp = x->Cp;
+    big.items = x->bins[kBigBin];
+    big.count = &x->d_ctr->bin_count[kBigBin];
+    big.keyspace = g.n;
+    big.ws = x->big;
+    if (!x->pass_has_hubs) big.ws.slots = 0;
+    big.ctr = x->d_ctr;
+    big.K = x->K;
+    big.Sigma = x->Sigma;
+    big.flag = x->flag;
+    big.two_m = x->two_m;
+    big.pickless = pickless;
+    big.mv_vertex = x->mv_vertex;
+    big.mv_target = x->mv_target;
     a.mlp = x->mlp;
     a.feat = x->feat;
     a.skip_threshold = cfg.skip_threshold;
@@ -232,13 +315,14 @@ louvain_status move_phase(louvain_ctx *x, const GView &g, int wk, int pass, doub
     for (int b = 0; b < cfg.buckets; ++b) {
       LV_CK(cudaMemsetAsync(x->d_ctr, 0, 10 * sizeof(unsigned long long), x->stream));
       a.bucket = (uint32_t)b;
-      move_bucket(a, wk, x->num_sms, x->stream);
+      move_bucket(a, big, wk, x->num_sms, x->stream, x->prof.mask ? &x->prof : nullptr);
     }
     LV_CK(cudaGetLastError());
     louvain_status st = read_counters(x);
     if (st) return st;
     const Counters &h = *x->h_ctr;
     const i128 gain = ((i128)h.it_gain_hi << 32) + (i128)h.it_gain_lo;
+    account_move(x, g.n, h);
     if (pass < cfg.max_passes) {
       int64_t *r = &x->iter_stats[((size_t)pass * cfg.max_iterations + t) * 4];
       r[0] = (int64_t)h.it_evaluated;
@@ -280,12 +364,24 @@ louvain_status run_impl(louvain_ctx *x) {
   x->iter_stats.assign((size_t)std::max(cfg.max_passes, 1) * cfg.max_iterations * 4, 0);
   x->pass_stats.assign((size_t)std::max(cfg.max_passes, 1) * 6, 0);
   x->it_total = x->moves_total = x->evaluated_total = x->skipped_total = 0;
+  const long long launches0 = g_launches;
+  for (int k = 0; k < K_NUM_KERNELS; ++k) {
+    x->prof.ms[k] = 0;
+    x->prof.launches[k] = 0;
+    x->kbytes[k] = 0;
+  }
+  x->prof.used = 0;
   for (auto &pt : x->timing) pt.aggregated = false;
   LV_CK(cudaEventRecord(x->run0, s));
   LV_CK(cudaMemsetAsync(x->d_ctr, 0, sizeof(Counters), s));
 
   GView g{x->n0, x->off0, x->off0 + 1, x->col0, x->w0};
-  int wk = x->weighted ? W_I32 : W_UNIT;
+  int wk = x->weighted ? W_U32 : W_UNIT;
+  if (x->big_dirty && x->big.slots > 0) {  // a failed run may have left table entries behind
+    LV_CK(cudaMemsetAsync(x->big.keys, 0xFF, (size_t)x->big.slots * sizeof(int32_t), s));
+    LV_CK(cudaMemsetAsync(x->big.vals, 0, (size_t)x->big.slots * sizeof(uint32_t), s));
+  }
+  x->big_dirty = true;
   iota_i32(x->C, x->n0, x->num_sms, s);
   double tau = cfg.tolerance;
   bool pending = false, exhausted = true;
@@ -297,17 +393,15 @@ louvain_status run_impl(louvain_ctx *x) {
     PassTiming &pt = x->timing[p];
     LV_CK(cudaEventRecord(pt.t0, s));
     LV_CK(cudaMemsetAsync(&x->d_ctr->maxdeg, 0, sizeof(unsigned long long), s));
+    x->cur_wbytes = wk == W_UNIT ? 0 : 4;
+    LV_CK(cudaMemsetAsync(&x->d_ctr->big_slots, 0, 2 * sizeof(unsigned long long), s));
+    x->prof.begin(K_PASS_INIT, s);
     pass_init(g, wk, p == 0, x->K, x->Sigma, x->Cp, x->flag, x->d_ctr, x->num_sms, s);
+    x->prof.end(K_PASS_INIT, s);
     LV_CK(cudaGetLastError());
     if ((st = read_counters(x))) return st;
-    {
-      uint64_t md = x->h_ctr->maxdeg;
-      if (md > kBlockMaxDeg) {
-        if ((st = ensure_ws(x, std::min<uint64_t>(md, (uint64_t)g.n)))) return st;
-      } else {
-        x->ws.blocks = 0;
-      }
-    }
+    x->pass_has_hubs = x->h_ctr->big_items > 0;
+    if ((st = ensure_big_for(x, *x->h_ctr))) return st;
     int li = 0;
     if ((st = move_phase(x, g, wk, p, tau, &li))) return st;
     have_pass_state = true;
@@ -332,9 +426,12 @@ louvain_status run_impl(louvain_ctx *x) {
     aa.oend = x->pend[slot];
     aa.ocol = x->pcol[slot];
     aa.ow = x->pw[slot];
+    aa.mprefix = x->newid;  // free once the ids are relabelled
     aa.ctr = x->d_ctr;
     aa.scan_tmp = x->scan_tmp;
+    x->prof.begin(K_COMM_COUNT, s);
     agg_count_scan(aa, x->num_sms, s);
+    x->prof.end(K_COMM_COUNT, s);
     LV_CK(cudaGetLastError());
     if ((st = read_counters(x))) return st;
     const int64_t gamma = (int64_t)x->h_ctr->scan_total[0];
@@ -363,31 +460,45 @@ louvain_status run_impl(louvain_ctx *x) {
       exit_reason = 2;
       break;
     }
-    LV_CK(cudaMemsetAsync(&x->d_ctr->bin_count[4], 0, 4 * sizeof(unsigned long long), s));
-    LV_CK(cudaMemsetAsync(&x->d_ctr->maxdeg, 0, sizeof(unsigned long long), s));
+    LV_CK(cudaMemsetAsync(&x->d_ctr->mbin_count[0], 0, sizeof(x->d_ctr->mbin_count), s));
+    LV_CK(cudaMemsetAsync(&x->d_ctr->maxdeg, 0, 3 * sizeof(unsigned long long), s));
+    x->prof.begin(K_SCATTER, s);
     agg_scatter_compact(aa, x->num_sms, s);
+    x->prof.end(K_SCATTER, s);
+    x->prof.begin(K_DENDRO, s);
     dendrogram_lookup(x->C, x->Cp, x->n0, x->num_sms, s);
+    x->prof.end(K_DENDRO, s);
     LV_CK(cudaGetLastError());
     if ((st = read_counters(x))) return st;
-    {
-      uint64_t md = x->h_ctr->maxdeg;
-      if (x->h_ctr->bin_count[7] > 0) {
-        if ((st = ensure_ws(x, std::min<uint64_t>(md, (uint64_t)gamma)))) return st;
-        aa.ws = x->ws;
-      } else {
-        aa.ws.blocks = 0;
-      }
-    }
+    if ((st = ensure_big_for(x, *x->h_ctr))) return st;
+    aa.big.g = g;
+    aa.big.Cp = x->Cp;
+    aa.big.items = x->bins[kBigBin];
+    aa.big.count = &x->d_ctr->mbin_count[kBigBin];
+    aa.big.keyspace = gamma;
+    aa.big.ws = x->big;
+    if (x->h_ctr->big_items == 0) aa.big.ws.slots = 0;
+    aa.big.ctr = x->d_ctr;
+    aa.big.mprefix = aa.mprefix;
+    aa.big.kcoff = x->kcoff;
+    aa.big.kcnt = x->kcnt;
+    aa.big.members = x->members;
+    aa.big.obegin = aa.obegin;
+    aa.big.oend = aa.oend;
+    aa.big.ocol = aa.ocol;
+    aa.big.ow = aa.ow;
     LV_CK(cudaMemsetAsync(&x->d_ctr->nnz_out, 0, sizeof(unsigned long long), s));
-    agg_merge(aa, gamma, x->num_sms, s);
+    LV_CK(cudaMemsetAsync(&x->d_ctr->mg_work[0][0], 0, sizeof(x->d_ctr->mg_work), s));
+    agg_merge(aa, gamma, x->num_sms, s, x->prof.mask ? &x->prof : nullptr);
     LV_CK(cudaGetLastError());
     if ((st = read_counters(x))) return st;
+    account_merge(x, *x->h_ctr);
     LV_CK(cudaEventRecord(pt.t2, s));
     pt.aggregated = true;
     nnzp = (int64_t)x->h_ctr->nnz_out;
     std::swap(x->K, x->Kalt);  // K of the super-vertices
     g = GView{gamma, x->pbeg[slot], x->pend[slot], x->pcol[slot], x->pw[slot]};
-    wk = W_I64;
+    wk = W_U32;
     slot ^= 1;
     tau /= cfg.tolerance_drop;
     have_pass_state = false;
@@ -403,11 +514,16 @@ louvain_status run_impl(louvain_ctx *x) {
   }
   (void)have_pass_state;
   i128 qn = 0, qd = 0;
+  x->prof.begin(K_MODULARITY, s);
   if ((st = modularity_into(x, g, wk, x->Cp, x->Sigma, nullptr, &qn, &qd))) return st;
+  x->prof.end(K_MODULARITY, s);
+  x->prof.begin(K_RENUMBER, s);
   renumber_dense(x->C, x->n0, x->n0, x->cnt, x->newid, x->scan_tmp, &x->d_ctr->scan_total[3], x->num_sms, s);
+  x->prof.end(K_RENUMBER, s);
   LV_CK(cudaEventRecord(x->run1, s));
   LV_CK(cudaGetLastError());
   if ((st = read_counters(x))) return st;
+  if (x->prof.mask) x->prof.collect();
   x->gamma = (int64_t)x->h_ctr->scan_total[3];
   x->qnum = qn;
   x->qden = qd;
@@ -417,7 +533,22 @@ louvain_status run_impl(louvain_ctx *x) {
   float ms = 0;
   LV_CK(cudaEventElapsedTime(&ms, x->run0, x->run1));
   x->run_ms = ms;
+  x->launches = g_launches - launches0;
+  x->big_dirty = false;
   x->ran = true;
+  return LOUVAIN_OK;
+}
+
+louvain_status ensure_prof_events(louvain_ctx *x) {
+  if (!x->prof_events.empty()) return LOUVAIN_OK;
+  x->prof_events.assign(512, nullptr);
+  for (auto &e : x->prof_events)
+    if (cudaEventCreate(&e)) {
+      set_err(x, "event creation failed");
+      return LOUVAIN_E_CUDA;
+    }
+  x->prof.pool = x->prof_events.data();
+  x->prof.pool_size = (int)x->prof_events.size();
   return LOUVAIN_OK;
 }
 
@@ -537,7 +668,7 @@ louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg
   // validation and 2m
   if (n > 0) {
     int grid = (int)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)x->num_sms * 16);
-    k_validate<<<grid, 256, 0, x->stream>>>(n, x->off0, x->col0, x->w0, x->d_ctr);
+    LV_LAUNCH(k_validate<<<grid, 256, 0, x->stream>>>(n, x->off0, x->col0, x->w0, x->d_ctr));
     if (cudaGetLastError() != cudaSuccess) {
       set_err(x, "validation kernel failed to launch");
       return fail(LOUVAIN_E_CUDA);
@@ -602,6 +733,8 @@ louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg
       return fail(LOUVAIN_E_CUDA);
     }
   }
+  if (cfg->profile_mask && ensure_prof_events(x)) return fail(LOUVAIN_E_CUDA);
+  x->prof.mask = cfg->profile_mask;
   if (cudaEventCreate(&x->run0) || cudaEventCreate(&x->run1)) {
     set_err(x, "event creation failed");
     return fail(LOUVAIN_E_CUDA);
@@ -698,8 +831,9 @@ louvain_status louvain_stats(const louvain_ctx *xc, char *json, size_t cap) {
            x->run_ms, x->passes, (long long)x->gamma, x->q);
   s += buf;
   snprintf(buf, sizeof buf,
-           "\"iterations\": %lld, \"moves\": %lld, \"evaluated\": %lld, \"skipped\": %lld, \"device_bytes\": %zu, ",
-           x->it_total, x->moves_total, x->evaluated_total, x->skipped_total, x->bytes);
+           "\"iterations\": %lld, \"moves\": %lld, \"evaluated\": %lld, \"skipped\": %lld, \"device_bytes\": %zu, "
+           "\"kernel_launches\": %lld, ",
+           x->it_total, x->moves_total, x->evaluated_total, x->skipped_total, x->bytes, x->launches);
   s += buf;
   double tm = 0, ta = 0;
   std::string per = "\"per_pass\": [";
@@ -716,9 +850,29 @@ louvain_status louvain_stats(const louvain_ctx *xc, char *json, size_t cap) {
   snprintf(buf, sizeof buf, "\"move_ms\": %.4f, \"aggregate_ms\": %.4f, \"other_ms\": %.4f, ", tm, ta,
            x->run_ms - tm - ta);
   s += buf;
-  s += per + "}";
+  s += per + ", \"kernels\": {";
+  bool first = true;
+  for (int k = 0; k < K_NUM_KERNELS; ++k) {
+    if (x->prof.launches[k] == 0 && x->kbytes[k] == 0) continue;
+    snprintf(buf, sizeof buf, "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"bytes\": %.0f}", first ? "" : ", ",
+             kKernelNames[k], x->prof.launches[k], x->prof.ms[k], x->kbytes[k]);
+    s += buf;
+    first = false;
+  }
+  s += "}}";
   if (s.size() + 1 > cap) return LOUVAIN_E_INVAL;
   memcpy(json, s.c_str(), s.size() + 1);
+  return LOUVAIN_OK;
+}
+
+louvain_status louvain_set_profile(louvain_ctx *x, uint32_t mask) {
+  if (!x) return LOUVAIN_E_INVAL;
+  if (mask) {
+    louvain_status st = ensure_prof_events(x);
+    if (st) return st;
+  }
+  x->prof.mask = mask;
+  x->cfg.profile_mask = mask;
   return LOUVAIN_OK;
 }
 
@@ -731,6 +885,8 @@ void louvain_destroy(louvain_ctx *x) {
     if (pt.t1) cudaEventDestroy(pt.t1);
     if (pt.t2) cudaEventDestroy(pt.t2);
   }
+  for (auto &e : x->prof_events)
+    if (e) cudaEventDestroy(e);
   if (x->run0) cudaEventDestroy(x->run0);
   if (x->run1) cudaEventDestroy(x->run1);
   if (x->h_ctr) cudaFreeHost(x->h_ctr);
@@ -769,7 +925,7 @@ louvain_status louvain_modularity_of(const louvain_graph *graph, const int32_t *
   }
   i128 qn = 0, qd = 0;
   GView g{n, x->off0, x->off0 + 1, x->col0, x->w0};
-  if (n > 0) st = modularity_into(x, g, x->weighted ? W_I32 : W_UNIT, memb, nullptr, sig, &qn, &qd);
+  if (n > 0) st = modularity_into(x, g, x->weighted ? W_U32 : W_UNIT, memb, nullptr, sig, &qn, &qd);
   if (!st) {
     if (q) *q = qd ? (double)qn / (double)qd : 0.0;
     if (num) put128(num, qn);

@@ -1,70 +1,77 @@
 // Local-moving phase of the Louvain method on sm_103a (arXiv 2501.19004,
 // Sec. 4.2.2 Algorithm 2 and its GPU form Algorithm 5).
 //
-// One bucket step of the deterministic schedule is four kernels:
-//   k_select  marks the unprocessed vertices of the bucket processed (pruning,
-//             Sec. 4.1.6) and sorts them into degree bins (warp-aggregated
-//             appends);
-//   k_move_*  one decision per vertex against the snapshot (C', Sigma'):
-//             scanCommunities (Algorithm 2) into a per-vertex table, the
-//             argmax of Eq. 2 scaled by 2m^2, the Pick-Less rejection
-//             (Sec. 4.3.1), and -- for movers -- the re-marking of the
-//             neighbours and the exact gain; decisions go to a mover list;
-//   k_apply   applies the moves: C'[i] = c*, Sigma' updates by 64-bit atomics.
-// The paper's per-vertex global hashtables of 2|E| slots (Sec. 4.3.2) are
-// replaced by register tables (thread bin), shared-memory open addressing
-// (warp and block bins) and per-block global slices for hubs only.
+// One bucket step of the deterministic schedule:
+//   k_select   marks the unprocessed vertices of the bucket processed (vertex
+//              pruning, Sec. 4.1.6) and sorts them into degree bins;
+//   k_move_*   one decision per vertex against the snapshot (C', Sigma'):
+//              scanCommunities (Algorithm 2) into a table, the argmax of
+//              Eq. 2 scaled by 2m^2, the Pick-Less rejection (Sec. 4.3.1),
+//              and, for movers, the exact gain and the re-marking of the
+//              neighbours; decisions go to a mover list;
+//   hubs       (degree > 4096) are split into chunks over the whole grid
+//              (big.cu);
+//   k_apply    applies the moves: C'[i] = c*, Sigma' by 64-bit atomics.
+// The paper's per-vertex global hashtables of 2|E| slots (Sec. 4.3.2) become
+// register tables (thread bin), shared-memory open addressing (warp and block
+// bins) and global tables for hubs only.
 #include <climits>
 
 #include "internal.h"
+#include "tables.cuh"
 
 namespace lv {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-__device__ __forceinline__ void warp_append(bool pred, unsigned long long *counter, int32_t *dst, int32_t v) {
-  unsigned mask = __ballot_sync(kFull, pred);
-  if (!mask) return;
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(mask) - 1;
-  unsigned long long base = 0;
-  if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(mask));
-  base = __shfl_sync(kFull, base, leader);
-  if (pred) dst[base + __popc(mask & lanemask_lt())] = v;
-}
-
+// ------------------------------------------------------------------ select
+// Block-aggregated appends: one global atomic per bin per block and tile.
 __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
+  __shared__ unsigned s_cnt[kNumBins + 1];
+  __shared__ unsigned long long s_base[kNumBins];
   const int64_t n = a.g.n;
   const int lane = threadIdx.x & 31;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = base + threadIdx.x;
+  const bool pow2 = (a.nbuckets & (a.nbuckets - 1)) == 0;
+  for (int64_t tile = (int64_t)blockIdx.x * blockDim.x; tile < n; tile += (int64_t)gridDim.x * blockDim.x) {
+    if (threadIdx.x <= kNumBins) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t i = tile + threadIdx.x;
     int bin = -1;
     bool sel = false;
-    if (i < n && a.flag[i] && fmix32((uint32_t)i ^ a.salt) % a.nbuckets == a.bucket) {
-      a.flag[i] = 0;
-      sel = true;
-      const int64_t deg = a.g.end[i] - a.g.begin[i];
-      if (deg > 0) bin = deg <= kThreadMaxDeg ? 0 : deg <= kWarpMaxDeg ? 1 : deg <= kBlockMaxDeg ? 2 : 3;
+    if (i < n && a.flag[i]) {
+      const uint32_t h = fmix32((uint32_t)i ^ a.salt);
+      const uint32_t bk = pow2 ? (h & (a.nbuckets - 1)) : (h % a.nbuckets);
+      if (bk == a.bucket) {
+        a.flag[i] = 0;
+        sel = true;
+        const int64_t deg = a.g.end[i] - a.g.begin[i];
+        if (deg > 0) bin = degree_bin(deg);
+      }
     }
-    unsigned smask = __ballot_sync(kFull, sel);
-    if (lane == 0 && smask) atomicAdd(&a.ctr->it_evaluated, (unsigned long long)__popc(smask));
+    unsigned woff[kNumBins];
+    unsigned bmask[kNumBins];
 #pragma unroll
-    for (int b = 0; b < kNumBins; ++b) warp_append(bin == b, &a.ctr->bin_count[b], a.bins[b], (int32_t)i);
+    for (int b = 0; b < kNumBins; ++b) {
+      bmask[b] = __ballot_sync(kFull, bin == b);
+      woff[b] = 0;
+      if (lane == 0 && bmask[b]) woff[b] = atomicAdd(&s_cnt[b], (unsigned)__popc(bmask[b]));
+    }
+    const unsigned smask = __ballot_sync(kFull, sel);
+    if (lane == 0 && smask) atomicAdd(&s_cnt[kNumBins], (unsigned)__popc(smask));
+    __syncthreads();
+    if (threadIdx.x < kNumBins && s_cnt[threadIdx.x])
+      s_base[threadIdx.x] = atomicAdd(&a.ctr->bin_count[threadIdx.x], (unsigned long long)s_cnt[threadIdx.x]);
+    if (threadIdx.x == kNumBins && s_cnt[kNumBins])
+      atomicAdd(&a.ctr->it_evaluated, (unsigned long long)s_cnt[kNumBins]);
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < kNumBins; ++b) {
+      const unsigned off = __shfl_sync(kFull, woff[b], 0);
+      if (bin == b) a.bins[b][s_base[b] + off + __popc(bmask[b] & lanemask_lt())] = (int32_t)i;
+    }
+    __syncthreads();
   }
-}
-
-// Decision shared by all bins: returns the target or -1.
-__device__ __forceinline__ int32_t finish_decision(const MoveArgs &a, int32_t d, long long Ki, long long Kid,
-                                                   long long best_s, int32_t best_c, unsigned long long &glo,
-                                                   unsigned long long &ghi, unsigned long long &gm) {
-  const long long s_d = a.two_m * Kid - Ki * (a.Sigma[d] - Ki);
-  if (best_c == INT_MAX || !(best_s > s_d) || (a.pickless && best_c > d)) return -1;
-  const unsigned long long gain = (unsigned long long)best_s - (unsigned long long)s_d;
-  glo += gain & 0xFFFFFFFFull;
-  ghi += gain >> 32;
-  gm += 1;
-  return best_c;
 }
 
 // ---------------------------------------------------------------- thread bin
@@ -75,6 +82,7 @@ __global__ void __launch_bounds__(256) k_move_thread(MoveArgs a) {
   constexpr int D = kThreadMaxDeg;
   const unsigned long long cnt = a.ctr->bin_count[0];
   unsigned long long glo = 0, ghi = 0, gm = 0;
+  unsigned long long work[5] = {0, 0, 0, 0, 0};  // vertices, entries, distinct, movers, mover entries
   for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < cnt;
        base += (unsigned long long)gridDim.x * blockDim.x) {
     const unsigned long long idx = base + threadIdx.x;
@@ -84,7 +92,7 @@ __global__ void __launch_bounds__(256) k_move_thread(MoveArgs a) {
       const int64_t b = a.g.begin[i];
       const int deg = (int)(a.g.end[i] - b);
       int32_t jj[D], cc[D];
-      long long ww[D];
+      uint32_t ww[D];
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         jj[k] = i;
@@ -100,7 +108,7 @@ __global__ void __launch_bounds__(256) k_move_thread(MoveArgs a) {
       const long long Ki = a.K[i];
       long long Kid = 0;
 #pragma unroll
-      for (int k = 0; k < D; ++k) Kid += (cc[k] == d) ? ww[k] : 0;
+      for (int k = 0; k < D; ++k) Kid += (cc[k] == d) ? ww[k] : 0u;
       long long best_s = LLONG_MIN;
       int32_t best_c = INT_MAX;
 #pragma unroll
@@ -111,10 +119,11 @@ __global__ void __launch_bounds__(256) k_move_thread(MoveArgs a) {
 #pragma unroll
         for (int l = 0; l < D; ++l) {
           const bool eq = cc[l] == c;
-          sum += eq ? ww[l] : 0;
+          sum += eq ? ww[l] : 0u;
           if (l < k && eq) first = false;
         }
         if (first) {
+          ++work[2];
           const long long s = a.two_m * sum - Ki * a.Sigma[c];
           if (better(s, c, best_s, best_c)) {
             best_s = s;
@@ -122,15 +131,19 @@ __global__ void __launch_bounds__(256) k_move_thread(MoveArgs a) {
           }
         }
       }
-      target = finish_decision(a, d, Ki, Kid, best_s, best_c, glo, ghi, gm);
+      target = finish_decision(a.two_m, a.Sigma, a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm);
+      work[0] += 1;
+      work[1] += (unsigned long long)deg;
       if (target >= 0) {
+        work[3] += 1;
+        work[4] += (unsigned long long)deg;
 #pragma unroll
         for (int k = 0; k < D; ++k)
           if (jj[k] != i) a.flag[jj[k]] = 1;
       }
     }
     const bool mv = target >= 0;
-    unsigned mask = __ballot_sync(kFull, mv);
+    const unsigned mask = __ballot_sync(kFull, mv);
     if (mask) {
       const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
       unsigned long long pos = 0;
@@ -143,67 +156,60 @@ __global__ void __launch_bounds__(256) k_move_thread(MoveArgs a) {
     }
   }
   flush_gains(glo, ghi, gm, a.ctr);
+  flush_work(work, a.ctr->mv_work[0]);
 }
 
-// ------------------------------------------------------ open-addressing tables
-// Accumulate (key, w) into a table of mask+1 slots (linear probing).  Tables
-// are sized to at least twice the number of distinct keys, so a free slot
-// always exists; the probe bound only guards against a sizing bug.
-__device__ __forceinline__ void smem_accumulate(int32_t *keys, unsigned long long *vals, uint32_t mask, int32_t key,
-                                                long long w, Counters *ctr) {
-  uint32_t s = slot_of(key, mask);
-  for (uint32_t t = 0; t <= mask; ++t) {
-    int32_t k = ((volatile int32_t *)keys)[s];
-    if (k == kEmpty) k = atomicCAS(keys + s, kEmpty, key), k = (k == kEmpty) ? key : k;
-    if (k == key) {
-      atomicAdd(vals + s, (unsigned long long)w);
-      return;
+// Gather kRun entries x, x + stride, ... (< xe) of the row of i that starts
+// at b: the community of each neighbour (kEmpty for the self-loop and past
+// the end) and the weight.  Consecutive threads read consecutive entries.
+template <int WK>
+__device__ __forceinline__ void gather_run(const MoveArgs &a, int32_t i, int64_t b, int64_t x, int64_t stride,
+                                           int64_t xe, int32_t (&kk)[kRun], uint32_t (&ww)[kRun]) {
+#pragma unroll
+  for (int u = 0; u < kRun; ++u) {
+    kk[u] = -2;
+    ww[u] = 0;
+    const int64_t p = x + u * stride;
+    if (p < xe) {
+      kk[u] = __ldg(a.g.col + b + p);
+      ww[u] = load_w<WK>(a.g.w, b + p);
     }
-    s = (s + 1) & mask;
   }
-  atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
-}
-
-__device__ __forceinline__ void gmem_accumulate(int32_t *keys, unsigned long long *vals, uint32_t mask, int32_t key,
-                                                long long w, Counters *ctr) {
-  uint32_t s = slot_of(key, mask);
-  for (uint32_t t = 0; t <= mask; ++t) {
-    int32_t k = __ldcg(keys + s);
-    if (k == kEmpty) k = atomicCAS(keys + s, kEmpty, key), k = (k == kEmpty) ? key : k;
-    if (k == key) {
-      atomicAdd(vals + s, (unsigned long long)w);
-      return;
-    }
-    s = (s + 1) & mask;
-  }
-  atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
+#pragma unroll
+  for (int u = 0; u < kRun; ++u) kk[u] = (kk[u] >= 0 && kk[u] != i) ? a.Cp[kk[u]] : kEmpty;
 }
 
 // ------------------------------------------------------------------ warp bin
+// 16 < degree <= 256: one warp, a shared table of up to 512 slots; each lane
+// reads a run of 8 consecutive entries.
 template <int WK, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_move_warp(MoveArgs a) {
   __shared__ int32_t skeys[WARPS][kWarpCap];
-  __shared__ unsigned long long svals[WARPS][kWarpCap];
+  __shared__ uint32_t svals[WARPS][kWarpCap];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t *keys = skeys[warp];
-  unsigned long long *vals = svals[warp];
+  uint32_t *vals = svals[warp];
   const unsigned long long cnt = a.ctr->bin_count[1];
   unsigned long long glo = 0, ghi = 0, gm = 0;
+  unsigned long long work[5] = {0, 0, 0, 0, 0};
   for (unsigned long long idx = (unsigned long long)blockIdx.x * WARPS + warp; idx < cnt;
        idx += (unsigned long long)gridDim.x * WARPS) {
     const int32_t i = a.bins[1][idx];
     const int64_t b = a.g.begin[i], e = a.g.end[i];
-    const uint32_t cap = pow2_at_least(2 * (uint64_t)(e - b));
+    const int64_t deg = e - b;
+    const uint32_t cap = pow2_at_least(2 * (uint64_t)deg);
     const uint32_t mask = cap - 1;
     for (uint32_t s = lane; s < cap; s += 32) {
       keys[s] = kEmpty;
       vals[s] = 0;
     }
     __syncwarp();
-    for (int64_t k = b + lane; k < e; k += 32) {
-      const int32_t j = __ldg(a.g.col + k);
-      if (j == i) continue;
-      smem_accumulate(keys, vals, mask, a.Cp[j], load_w<WK>(a.g.w, k), a.ctr);
+    for (int64_t x0 = 0; x0 < deg; x0 += 32 * kRun) {
+      int32_t kk[kRun];
+      uint32_t ww[kRun];
+      gather_run<WK>(a, i, b, x0 + lane, 32, deg, kk, ww);
+#pragma unroll
+      for (int u = 0; u < kRun; ++u) warp_insert_sm(keys, vals, mask, kk[u], ww[u], a.ctr);
     }
     __syncwarp();
     const int32_t d = a.Cp[i];
@@ -213,11 +219,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_move_warp(MoveArgs a) {
     for (uint32_t s = lane; s < cap; s += 32) {
       const int32_t c = keys[s];
       if (c == kEmpty) continue;
-      const long long v = (long long)vals[s];
+      const long long v = vals[s];
       if (c == d) {
         Kid = v;
         continue;
       }
+      ++work[2];
       const long long sc = a.two_m * v - Ki * a.Sigma[c];
       if (better(sc, c, best_s, best_c)) {
         best_s = sc;
@@ -228,8 +235,12 @@ __global__ void __launch_bounds__(WARPS * 32) k_move_warp(MoveArgs a) {
     Kid = warp_sum(Kid);
     int32_t target = -1;
     if (lane == 0) {
-      target = finish_decision(a, d, Ki, Kid, best_s, best_c, glo, ghi, gm);
+      target = finish_decision(a.two_m, a.Sigma, a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm);
+      work[0] += 1;
+      work[1] += (unsigned long long)deg;
       if (target >= 0) {
+        work[3] += 1;
+        work[4] += (unsigned long long)deg;
         const unsigned long long pos = atomicAdd(&a.ctr->movers, 1ull);
         a.mv_vertex[pos] = i;
         a.mv_target[pos] = target;
@@ -244,46 +255,27 @@ __global__ void __launch_bounds__(WARPS * 32) k_move_warp(MoveArgs a) {
     __syncwarp();
   }
   flush_gains(glo, ghi, gm, a.ctr);
+  flush_work(work, a.ctr->mv_work[1]);
 }
 
-// ---------------------------------------------- block reductions (argmax, sum)
-template <int NT>
-__device__ __forceinline__ void block_argmax_sum(long long &s, int32_t &c, long long &sum) {
-  __shared__ long long rs[NT / 32];
-  __shared__ int32_t rc[NT / 32];
-  __shared__ long long rsum[NT / 32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  warp_argmax(s, c);
-  sum = warp_sum(sum);
-  if (lane == 0) {
-    rs[warp] = s;
-    rc[warp] = c;
-    rsum[warp] = sum;
-  }
-  __syncthreads();
-  if (warp == 0) {
-    s = lane < NT / 32 ? rs[lane] : LLONG_MIN;
-    c = lane < NT / 32 ? rc[lane] : INT_MAX;
-    sum = lane < NT / 32 ? rsum[lane] : 0;
-    warp_argmax(s, c);
-    sum = warp_sum(sum);
-  }
-  __syncthreads();
-}
-
-// ----------------------------------------------------------------- block bin
-template <int WK, int NT>
+// ---------------------------------------------------------------- block bins
+// 256 < degree <= 1024: 128 threads and a 2048-slot table; 1024 < degree <=
+// 4096: 512 threads and an 8192-slot table (dynamic shared memory).  Each
+// thread reads 8 entries per round, strided by the block size.
+template <int WK, int NT, int CAP, int BIN>
 __global__ void __launch_bounds__(NT) k_move_block(MoveArgs a) {
-  extern __shared__ unsigned long long dyn[];
-  unsigned long long *vals = dyn;
-  int32_t *keys = (int32_t *)(dyn + kBlockCap);
+  extern __shared__ uint32_t dyn[];
+  int32_t *keys = (int32_t *)dyn;
+  uint32_t *vals = dyn + CAP;
   __shared__ int32_t s_target;
-  const unsigned long long cnt = a.ctr->bin_count[2];
+  const unsigned long long cnt = a.ctr->bin_count[BIN];
   unsigned long long glo = 0, ghi = 0, gm = 0;
+  unsigned long long work[5] = {0, 0, 0, 0, 0};
   for (unsigned long long idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
-    const int32_t i = a.bins[2][idx];
+    const int32_t i = a.bins[BIN][idx];
     const int64_t b = a.g.begin[i], e = a.g.end[i];
-    uint64_t distinct = (uint64_t)(e - b);
+    const int64_t deg = e - b;
+    uint64_t distinct = (uint64_t)deg;
     if ((uint64_t)a.g.n < distinct) distinct = (uint64_t)a.g.n;
     const uint32_t cap = pow2_at_least(2 * distinct);
     const uint32_t mask = cap - 1;
@@ -292,10 +284,12 @@ __global__ void __launch_bounds__(NT) k_move_block(MoveArgs a) {
       vals[s] = 0;
     }
     __syncthreads();
-    for (int64_t k = b + threadIdx.x; k < e; k += NT) {
-      const int32_t j = __ldg(a.g.col + k);
-      if (j == i) continue;
-      smem_accumulate(keys, vals, mask, a.Cp[j], load_w<WK>(a.g.w, k), a.ctr);
+    for (int64_t x0 = 0; x0 < deg; x0 += (int64_t)NT * kRun) {
+      int32_t kk[kRun];
+      uint32_t ww[kRun];
+      gather_run<WK>(a, i, b, x0 + threadIdx.x, NT, deg, kk, ww);
+#pragma unroll
+      for (int u = 0; u < kRun; ++u) warp_insert_sm(keys, vals, mask, kk[u], ww[u], a.ctr);
     }
     __syncthreads();
     const int32_t d = a.Cp[i];
@@ -305,11 +299,12 @@ __global__ void __launch_bounds__(NT) k_move_block(MoveArgs a) {
     for (uint32_t s = threadIdx.x; s < cap; s += NT) {
       const int32_t c = keys[s];
       if (c == kEmpty) continue;
-      const long long v = (long long)vals[s];
+      const long long v = vals[s];
       if (c == d) {
         Kid = v;
         continue;
       }
+      ++work[2];
       const long long sc = a.two_m * v - Ki * a.Sigma[c];
       if (better(sc, c, best_s, best_c)) {
         best_s = sc;
@@ -318,8 +313,12 @@ __global__ void __launch_bounds__(NT) k_move_block(MoveArgs a) {
     }
     block_argmax_sum<NT>(best_s, best_c, Kid);
     if (threadIdx.x == 0) {
-      const int32_t t = finish_decision(a, d, Ki, Kid, best_s, best_c, glo, ghi, gm);
+      const int32_t t = finish_decision(a.two_m, a.Sigma, a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm);
+      work[0] += 1;
+      work[1] += (unsigned long long)deg;
       if (t >= 0) {
+        work[3] += 1;
+        work[4] += (unsigned long long)deg;
         const unsigned long long pos = atomicAdd(&a.ctr->movers, 1ull);
         a.mv_vertex[pos] = i;
         a.mv_target[pos] = t;
@@ -335,75 +334,7 @@ __global__ void __launch_bounds__(NT) k_move_block(MoveArgs a) {
     __syncthreads();
   }
   flush_gains(glo, ghi, gm, a.ctr);
-}
-
-// ------------------------------------------------------------------- hub bin
-template <int WK, int NT>
-__global__ void __launch_bounds__(NT) k_move_hub(MoveArgs a) {
-  __shared__ int32_t s_target;
-  int32_t *keys = a.ws.keys + (int64_t)blockIdx.x * a.ws.slice;
-  unsigned long long *vals = a.ws.vals + (int64_t)blockIdx.x * a.ws.slice;
-  const unsigned long long cnt = a.ctr->bin_count[3];
-  unsigned long long glo = 0, ghi = 0, gm = 0;
-  for (unsigned long long idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
-    const int32_t i = a.bins[3][idx];
-    const int64_t b = a.g.begin[i], e = a.g.end[i];
-    uint64_t distinct = (uint64_t)(e - b);
-    if ((uint64_t)a.g.n < distinct) distinct = (uint64_t)a.g.n;
-    const uint32_t cap = pow2_at_least(2 * distinct);
-    if ((int64_t)cap > a.ws.slice) {  // workspace sized by the host from the max degree
-      if (threadIdx.x == 0) atomicOr(&a.ctr->error, (unsigned long long)ERR_HASH);
-      continue;
-    }
-    const uint32_t mask = cap - 1;
-    for (uint32_t s = threadIdx.x; s < cap; s += NT) {
-      keys[s] = kEmpty;
-      vals[s] = 0;
-    }
-    __syncthreads();
-    for (int64_t k = b + threadIdx.x; k < e; k += NT) {
-      const int32_t j = __ldg(a.g.col + k);
-      if (j == i) continue;
-      gmem_accumulate(keys, vals, mask, a.Cp[j], load_w<WK>(a.g.w, k), a.ctr);
-    }
-    __syncthreads();
-    const int32_t d = a.Cp[i];
-    const long long Ki = a.K[i];
-    long long best_s = LLONG_MIN, Kid = 0;
-    int32_t best_c = INT_MAX;
-    for (uint32_t s = threadIdx.x; s < cap; s += NT) {
-      const int32_t c = __ldcg(keys + s);
-      if (c == kEmpty) continue;
-      const long long v = (long long)__ldcg(vals + s);
-      if (c == d) {
-        Kid = v;
-        continue;
-      }
-      const long long sc = a.two_m * v - Ki * a.Sigma[c];
-      if (better(sc, c, best_s, best_c)) {
-        best_s = sc;
-        best_c = c;
-      }
-    }
-    block_argmax_sum<NT>(best_s, best_c, Kid);
-    if (threadIdx.x == 0) {
-      const int32_t t = finish_decision(a, d, Ki, Kid, best_s, best_c, glo, ghi, gm);
-      if (t >= 0) {
-        const unsigned long long pos = atomicAdd(&a.ctr->movers, 1ull);
-        a.mv_vertex[pos] = i;
-        a.mv_target[pos] = t;
-      }
-      s_target = t;
-    }
-    __syncthreads();
-    if (s_target >= 0)
-      for (int64_t k = b + threadIdx.x; k < e; k += NT) {
-        const int32_t j = __ldg(a.g.col + k);
-        if (j != i) a.flag[j] = 1;
-      }
-    __syncthreads();
-  }
-  flush_gains(glo, ghi, gm, a.ctr);
+  flush_work(work, a.ctr->mv_work[BIN]);
 }
 
 // -------------------------------------------------------------------- apply
@@ -421,13 +352,22 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
 }
 
 // ---------------------------------------------------------------- pass init
+// K (row sums on the first pass; given otherwise), Sigma' = K', C' = id,
+// all vertices unprocessed; the maximum degree and the size bound of the hub
+// tables (sum of pow2(2 min(deg, n')) over degrees > 4096) for the host.
 template <int WK>
 __global__ void __launch_bounds__(256) k_pass_init(GView g, int first_pass, int64_t *K, int64_t *Sigma,
                                                    int32_t *Cp, uint8_t *flag, Counters *ctr) {
-  unsigned long long md = 0;
+  unsigned long long md = 0, big_slots = 0, big_items = 0;
+  const int lane = threadIdx.x & 31;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = g.begin[i], e = g.end[i];
-    if ((unsigned long long)(e - b) > md) md = (unsigned long long)(e - b);
+    const unsigned long long deg = (unsigned long long)(e - b);
+    if (deg > md) md = deg;
+    if (degree_bin((int64_t)deg) == kBigBin) {
+      big_slots += pow2_at_least(2 * (deg < (unsigned long long)g.n ? deg : (unsigned long long)g.n));
+      big_items += 1;
+    }
     long long k;
     if (first_pass) {
       if constexpr (WK == W_UNIT) {
@@ -446,10 +386,16 @@ __global__ void __launch_bounds__(256) k_pass_init(GView g, int first_pass, int6
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    unsigned long long x = __shfl_xor_sync(kFull, md, o);
+    const unsigned long long x = __shfl_xor_sync(kFull, md, o);
     md = x > md ? x : md;
   }
-  if ((threadIdx.x & 31) == 0 && md) atomicMax(&ctr->maxdeg, md);
+  big_slots = warp_sum_u(big_slots);
+  big_items = warp_sum_u(big_items);
+  if (lane == 0) {
+    if (md) atomicMax(&ctr->maxdeg, md);
+    if (big_slots) atomicAdd(&ctr->big_slots, big_slots);
+    if (big_items) atomicAdd(&ctr->big_items, big_items);
+  }
 }
 
 __global__ void k_iota(int32_t *x, int64_t n) {
@@ -457,60 +403,58 @@ __global__ void k_iota(int32_t *x, int64_t n) {
     x[i] = (int32_t)i;
 }
 
-int grid_for(int64_t n, int threads, int num_sms, int per_sm) {
-  int64_t g = (n + threads - 1) / threads;
-  int64_t cap = (int64_t)num_sms * per_sm;
-  if (g > cap) g = cap;
-  return (int)(g < 1 ? 1 : g);
-}
-
 template <int WK>
-void move_bucket_t(const MoveArgs &a, int num_sms, cudaStream_t s) {
+void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStream_t s, KernelProf *prof) {
   static bool attr_done = false;
-  constexpr int kBlockNT = 256;
-  constexpr size_t kBlockSmem = (size_t)kBlockCap * (sizeof(unsigned long long) + sizeof(int32_t));
+  constexpr size_t kMidSmem = (size_t)kMidCap * (sizeof(uint32_t) + sizeof(int32_t));
+  constexpr size_t kBlockSmem = (size_t)kBlockCap * (sizeof(uint32_t) + sizeof(int32_t));
   if (!attr_done) {
-    cudaFuncSetAttribute(k_move_block<WK, kBlockNT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBlockSmem);
+    cudaFuncSetAttribute(k_move_block<WK, 512, kBlockCap, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kBlockSmem);
     attr_done = true;
   }
-  k_select<<<grid_for(a.g.n, 256, num_sms, 16), 256, 0, s>>>(a);
-  k_move_thread<WK><<<num_sms * 8, 256, 0, s>>>(a);
-  k_move_warp<WK, 8><<<num_sms * 4, 256, 0, s>>>(a);
-  k_move_block<WK, kBlockNT><<<num_sms * 2, kBlockNT, kBlockSmem, s>>>(a);
-  if (a.ws.blocks > 0) k_move_hub<WK, 1024><<<a.ws.blocks, 1024, 0, s>>>(a);
-  k_apply<<<num_sms * 4, 256, 0, s>>>(a);
+  LV_TIMED(prof, K_SELECT, s, k_select<<<grid_for(a.g.n, 256, num_sms, 8), 256, 0, s>>>(a));
+  LV_TIMED(prof, K_MOVE_THREAD, s, k_move_thread<WK><<<num_sms * 8, 256, 0, s>>>(a));
+  LV_TIMED(prof, K_MOVE_WARP, s, k_move_warp<WK, 8><<<num_sms * 7, 256, 0, s>>>(a));
+  LV_TIMED(prof, K_MOVE_MID, s, k_move_block<WK, 128, kMidCap, 2><<<num_sms * 12, 128, kMidSmem, s>>>(a));
+  LV_TIMED(prof, K_MOVE_BLOCK, s, k_move_block<WK, 512, kBlockCap, 3><<<num_sms * 3, 512, kBlockSmem, s>>>(a));
+  if (big.ws.slots > 0) {
+    if (prof) prof->begin(K_MOVE_HUB, s);
+    big_move(big, WK, num_sms, s);
+    if (prof) prof->end(K_MOVE_HUB, s);
+  }
+  LV_TIMED(prof, K_APPLY, s, k_apply<<<num_sms * 4, 256, 0, s>>>(a));
 }
 
 template <int WK>
 void pass_init_t(const GView &g, int first, int64_t *K, int64_t *Sigma, int32_t *Cp, uint8_t *flag, Counters *ctr,
                  int num_sms, cudaStream_t s) {
-  k_pass_init<WK><<<grid_for(g.n, 256, num_sms, 16), 256, 0, s>>>(g, first, K, Sigma, Cp, flag, ctr);
+  LV_LAUNCH(k_pass_init<WK><<<grid_for(g.n, 256, num_sms, 16), 256, 0, s>>>(g, first, K, Sigma, Cp, flag, ctr));
 }
 
 }  // namespace
 
-void move_bucket(const MoveArgs &a, int wkind, int num_sms, cudaStream_t s) {
+void move_bucket(const MoveArgs &a, const BigArgs &big, int wkind, int num_sms, cudaStream_t s, KernelProf *prof) {
   if (a.g.n <= 0) return;
-  switch (wkind) {
-    case W_UNIT: move_bucket_t<W_UNIT>(a, num_sms, s); break;
-    case W_I32: move_bucket_t<W_I32>(a, num_sms, s); break;
-    default: move_bucket_t<W_I64>(a, num_sms, s); break;
-  }
+  if (wkind == W_UNIT) move_bucket_t<W_UNIT>(a, big, num_sms, s, prof);
+  else move_bucket_t<W_U32>(a, big, num_sms, s, prof);
 }
 
 void pass_init(const GView &g, int wkind, int first_pass, int64_t *K, int64_t *Sigma, int32_t *Cp, uint8_t *flag,
                Counters *ctr, int num_sms, cudaStream_t s) {
   if (g.n <= 0) return;
-  switch (wkind) {
-    case W_UNIT: pass_init_t<W_UNIT>(g, first_pass, K, Sigma, Cp, flag, ctr, num_sms, s); break;
-    case W_I32: pass_init_t<W_I32>(g, first_pass, K, Sigma, Cp, flag, ctr, num_sms, s); break;
-    default: pass_init_t<W_I64>(g, first_pass, K, Sigma, Cp, flag, ctr, num_sms, s); break;
-  }
+  if (wkind == W_UNIT) pass_init_t<W_UNIT>(g, first_pass, K, Sigma, Cp, flag, ctr, num_sms, s);
+  else pass_init_t<W_U32>(g, first_pass, K, Sigma, Cp, flag, ctr, num_sms, s);
 }
 
 void iota_i32(int32_t *x, int64_t n, int num_sms, cudaStream_t s) {
   if (n <= 0) return;
-  k_iota<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(x, n);
+  LV_LAUNCH(k_iota<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(x, n));
 }
+
+const char *const kKernelNames[K_NUM_KERNELS] = {
+    "select", "move_thread", "move_warp", "move_mid", "move_block", "move_hub", "apply", "pass_init",
+    "comm_count", "comm_scatter", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big",
+    "dendrogram", "modularity", "renumber"};
 
 }  // namespace lv

@@ -1,0 +1,117 @@
+// Open-addressing tables (community id -> summed weight) used by the
+// local-moving and aggregation kernels.  Keys are int32 community ids
+// (kEmpty = free), values are uint32: every sum that lands in a table is at
+// most 2m < 2^32 (a K_{i->c} is bounded by K_i, a super-edge weight by 2m).
+// Tables always hold at least twice as many slots as distinct keys, so
+// linear probing always finds a slot; the probe bound only guards against a
+// sizing error and raises ERR_HASH (the "failed" result of Algorithm 7).
+#pragma once
+#include "common.cuh"
+
+namespace lv {
+
+constexpr int kRun = 8;  // consecutive entries handled by one thread per round
+
+__device__ __forceinline__ void sm_insert(int32_t *keys, uint32_t *vals, uint32_t mask, int32_t key, uint32_t w,
+                                          Counters *ctr) {
+  uint32_t s = slot_of(key, mask);
+  for (uint32_t t = 0; t <= mask; ++t) {
+    int32_t k = ((volatile int32_t *)keys)[s];
+    if (k == kEmpty) {
+      k = atomicCAS(keys + s, kEmpty, key);
+      if (k == kEmpty) k = key;
+    }
+    if (k == key) {
+      atomicAdd(vals + s, w);
+      return;
+    }
+    s = (s + 1) & mask;
+  }
+  atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
+}
+
+__device__ __forceinline__ void gm_insert(int32_t *keys, uint32_t *vals, uint32_t mask, int32_t key, uint32_t w,
+                                          Counters *ctr) {
+  uint32_t s = slot_of(key, mask);
+  for (uint32_t t = 0; t <= mask; ++t) {
+    int32_t k = __ldcg(keys + s);
+    if (k == kEmpty) {
+      k = atomicCAS(keys + s, kEmpty, key);
+      if (k == kEmpty) k = key;
+    }
+    if (k == key) {
+      atomicAdd(vals + s, w);
+      return;
+    }
+    s = (s + 1) & mask;
+  }
+  atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
+}
+
+// Warp-cooperative insert into a shared table: all 32 lanes call it (key =
+// kEmpty for nothing).  When the warp holds few distinct keys (a hot
+// community), lanes with equal keys are summed first and one lane inserts;
+// otherwise every lane inserts its own pair.
+__device__ __forceinline__ void warp_insert_sm(int32_t *keys, uint32_t *vals, uint32_t mask, int32_t key, uint32_t w,
+                                               Counters *ctr) {
+  const unsigned full = 0xFFFFFFFFu;
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(full, key);
+  const bool lead = lane == __ffs(peers) - 1;
+  const unsigned leaders = __ballot_sync(full, lead && key != kEmpty);
+  if (__popc(leaders) <= 4) {
+    unsigned todo = leaders;
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int32_t k0 = __shfl_sync(full, key, src);
+      const uint32_t sum = __reduce_add_sync(full, key == k0 ? w : 0u);
+      if (lane == src) sm_insert(keys, vals, mask, k0, sum, ctr);
+    }
+  } else if (key != kEmpty) {
+    sm_insert(keys, vals, mask, key, w, ctr);
+  }
+}
+
+// Block-level exclusive scan of one int64 per thread (NT threads); returns
+// the exclusive prefix and the block total in *total.  Uses `scratch`
+// (NT/32 + 1 words of shared memory).
+template <int NT>
+__device__ __forceinline__ long long block_scan_ex(long long v, long long *scratch, long long *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) scratch[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    long long s = lane < NT / 32 ? scratch[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < NT / 32) scratch[lane] = s;
+  }
+  __syncthreads();
+  const long long before = warp ? scratch[warp - 1] : 0;
+  *total = scratch[NT / 32 - 1];
+  __syncthreads();
+  return before + x - v;
+}
+
+// Largest index k in [0, n) with a[k] <= x (a non-decreasing, a[0] <= x).
+__device__ __forceinline__ int64_t upper_index(const int64_t *a, int64_t n, int64_t x) {
+  int64_t lo = 0, hi = n;  // invariant: a[lo] <= x, answer in [lo, hi)
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+}  // namespace lv

@@ -26,6 +26,17 @@ LIB_PATH = _build.LIB
 STATUS = {0: "OK", 1: "E_INVAL", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_HASH_OVERFLOW", 5: "E_TIMEOUT",
           6: "E_OVERFLOW", 7: "E_STATE"}
 MODE_PLAIN, MODE_LEARNED = 0, 1
+KERNELS = ["select", "move_thread", "move_warp", "move_mid", "move_block", "move_hub", "apply", "pass_init",
+           "comm_count", "comm_scatter", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big",
+           "dendrogram", "modularity", "renumber"]
+
+
+def kernel_mask(*names) -> int:
+    """profile_mask bits for the named kernel groups."""
+    m = 0
+    for nm in names:
+        m |= 1 << KERNELS.index(nm)
+    return m
 ITER_FIELDS, PASS_FIELDS = 4, 6
 
 
@@ -46,7 +57,8 @@ class LouvainConfig(ctypes.Structure):
                 ("aggregation_tolerance", ctypes.c_double), ("pickless_period", ctypes.c_int32),
                 ("buckets", ctypes.c_int32), ("schedule_seed", ctypes.c_uint64), ("mode", ctypes.c_int32),
                 ("model", ctypes.c_void_p), ("skip_threshold", ctypes.c_float),
-                ("record_pass_modularity", ctypes.c_int32), ("check_symmetry", ctypes.c_int32)]
+                ("record_pass_modularity", ctypes.c_int32), ("check_symmetry", ctypes.c_int32),
+                ("profile_mask", ctypes.c_uint32)]
 
 
 _lib = None
@@ -78,6 +90,8 @@ def load(path: Optional[str] = None):
     lib.louvain_records.argtypes = [vp, vp, vp, vp]
     lib.louvain_stats.restype = ctypes.c_int
     lib.louvain_stats.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t]
+    lib.louvain_set_profile.restype = ctypes.c_int
+    lib.louvain_set_profile.argtypes = [vp, ctypes.c_uint32]
     lib.louvain_destroy.restype = None
     lib.louvain_destroy.argtypes = [vp]
     lib.louvain_last_error.restype = ctypes.c_char_p
@@ -115,6 +129,7 @@ class Config:
     skip_threshold: float = 0.5
     record_pass_modularity: bool = False
     check_symmetry: bool = False
+    profile_mask: int = 0
 
     def c(self) -> LouvainConfig:
         self._model_keep = None
@@ -125,7 +140,7 @@ class Config:
         return LouvainConfig(self.max_passes, self.max_iterations, self.tolerance, self.tolerance_drop,
                              self.aggregation_tolerance, self.pickless_period, self.buckets,
                              self.schedule_seed & (2**64 - 1), self.mode, mp, self.skip_threshold,
-                             int(self.record_pass_modularity), int(self.check_symmetry))
+                             int(self.record_pass_modularity), int(self.check_symmetry), self.profile_mask)
 
 
 @dataclass
@@ -239,6 +254,10 @@ def louvain_stats(ctx) -> dict:
     return json.loads(buf.value.decode())
 
 
+def louvain_set_profile(ctx, mask: int):
+    _check(load().louvain_set_profile(ctx, mask), ctx)
+
+
 def louvain_destroy(ctx):
     load().louvain_destroy(ctx)
 
@@ -316,6 +335,9 @@ class Louvain:
 
     def stats(self) -> dict:
         return louvain_stats(self.ctx)
+
+    def set_profile(self, mask: int):
+        louvain_set_profile(self.ctx, mask)
 
     def close(self):
         if self.ctx:
