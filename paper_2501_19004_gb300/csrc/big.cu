@@ -8,13 +8,16 @@
 //   k_big_plan    table offsets and chunk counts of every item (one block);
 //   k_big_accum   each block pre-aggregates one chunk in shared memory
 //                 (hot keys summed across the warp first), then adds the
-//                 chunk's distinct keys into the item's global table;
+//                 chunk's distinct keys into the item's global table and
+//                 lists every slot it claims;
+//   k_big_plan2   (aggregation) slices over the occupied-slot lists;
 //   k_big_eval    (moving) blocks scan table slices: argmax of Eq. 2 per
 //                 slice, clearing the slots as they go;
 //   k_big_decide  (moving) one block per hub reduces its slices, decides and
 //                 re-marks the neighbours;
-//   k_big_emit    (aggregation) blocks scan table slices and append the
-//                 super-edges to the community's row, clearing the slots.
+//   k_big_emit    (aggregation) blocks take slices of occupied slots and
+//                 append the super-edges to the community's row, clearing
+//                 the slots.
 // For aggregation an item's entries are the concatenated rows of its member
 // vertices, located through the member-degree prefix (community-vertex CSR).
 #include <climits>
@@ -53,6 +56,7 @@ __global__ void __launch_bounds__(1024) k_big_plan(BigArgs a) {
         members += (unsigned long long)a.kcnt[it];
       }
       a.ws.tot[k] = tot;
+      a.ws.ocnt[k] = 0;
       cap = table_cap(tot, a.keyspace);
       nch = (tot + kBigChunk - 1) / kBigChunk;
       nev = (cap + kBigEvalSlots - 1) / kBigEvalSlots;
@@ -64,7 +68,7 @@ __global__ void __launch_bounds__(1024) k_big_plan(BigArgs a) {
     if (k < nb) {
       a.ws.toff[k] = c_slots + e0;
       a.ws.cpre[k] = c_ch + e1;
-      a.ws.epre[k] = c_ev + e2;
+      if (MODE == MODE_MOVE) a.ws.epre[k] = c_ev + e2;
     }
     c_slots += t0;
     c_ch += t1;
@@ -75,12 +79,33 @@ __global__ void __launch_bounds__(1024) k_big_plan(BigArgs a) {
     if ((threadIdx.x & 31) == 0 && members) atomicAdd(&a.ctr->mg_work[kBigBin][1], members);
   }
   if (threadIdx.x == 0) {
-    const bool fits = c_slots <= a.ws.slots && c_ev <= a.ws.parts;
+    const bool fits = c_slots <= a.ws.slots && (MODE == MODE_MERGE || c_ev <= a.ws.parts);
     if (!fits) atomicOr(&a.ctr->error, (unsigned long long)ERR_HASH);
     a.ws.toff[nb] = c_slots;
     a.ws.cpre[nb] = fits ? c_ch : 0;
-    a.ws.epre[nb] = fits ? c_ev : 0;
+    a.ws.epre[nb] = (fits && MODE == MODE_MOVE) ? c_ev : 0;
     if (MODE == MODE_MERGE) atomicAdd(&a.ctr->mg_work[kBigBin][0], (unsigned long long)nb);
+  }
+}
+
+// Evaluation slices: kBigEvalSlots occupied slots each (one block).
+__global__ void __launch_bounds__(1024) k_big_plan2(BigArgs a) {
+  __shared__ long long sc[33];
+  const int64_t nb = (int64_t)*a.count;
+  if (a.ws.cpre[nb] == 0) return;  // nothing was accumulated
+  long long c_ev = 0;
+  for (int64_t base = 0; base < nb; base += 1024) {
+    const int64_t k = base + threadIdx.x;
+    const long long nev = k < nb ? (long long)((a.ws.ocnt[k] + kBigEvalSlots - 1) / kBigEvalSlots) : 0;
+    long long t;
+    const long long e = block_scan_ex<1024>(nev, sc, &t);
+    if (k < nb) a.ws.epre[k] = c_ev + e;
+    c_ev += t;
+  }
+  if (threadIdx.x == 0) {
+    const bool fits = c_ev <= a.ws.parts;
+    if (!fits) atomicOr(&a.ctr->error, (unsigned long long)ERR_HASH);
+    a.ws.epre[nb] = fits ? c_ev : 0;
   }
 }
 
@@ -175,12 +200,27 @@ __global__ void __launch_bounds__(kNT) k_big_accum(BigArgs a) {
     __syncthreads();
     const int64_t toff = a.ws.toff[k];
     const uint32_t gmask = table_cap(tot, a.keyspace) - 1;
+    // every warp takes 32 consecutive slots per round; when aggregating,
+    // slots claimed in the global table are appended to the item's list with
+    // one atomic per warp (evaluation then visits occupied slots only)
     for (int s = threadIdx.x; s < kBigSmemSlots; s += kNT) {
       const int32_t key = skeys[s];
-      if (key == kEmpty) continue;
-      gm_insert(a.ws.keys + toff, a.ws.vals + toff, gmask, key, svals[s], a.ctr);
-      skeys[s] = kEmpty;
-      svals[s] = 0;
+      int64_t slot = -1;
+      if (key != kEmpty) {
+        if (MODE == MODE_MERGE) slot = gm_insert_claim(a.ws.keys + toff, a.ws.vals + toff, gmask, key, svals[s], a.ctr);
+        else gm_insert(a.ws.keys + toff, a.ws.vals + toff, gmask, key, svals[s], a.ctr);
+        skeys[s] = kEmpty;
+        svals[s] = 0;
+      }
+      if (MODE == MODE_MOVE) continue;
+      const unsigned claimed = __ballot_sync(kFull, slot >= 0);
+      if (claimed) {
+        const int lane = threadIdx.x & 31, leader = __ffs(claimed) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(a.ws.ocnt + k, (unsigned long long)__popc(claimed));
+        base = __shfl_sync(kFull, base, leader);
+        if (slot >= 0) a.ws.occ[toff / 2 + (int64_t)(base + __popc(claimed & lanemask_lt()))] = (int32_t)slot;
+      }
     }
     __syncthreads();
   }
@@ -188,8 +228,9 @@ __global__ void __launch_bounds__(kNT) k_big_accum(BigArgs a) {
   flush_work(w, MODE == MODE_MOVE ? &a.ctr->mv_work[kBigBin][1] : &a.ctr->mg_work[kBigBin][2]);
 }
 
-// Moving: per table slice, the best candidate (score, then lowest id) and
-// the weight to the vertex's own community; slots are cleared.
+// Moving: per table slice, the best candidate (score, then lowest id) and the
+// weight to the vertex's own community; slots are cleared.  Hub tables are
+// at least a quarter full, so slices are scanned sequentially.
 __global__ void __launch_bounds__(kNT) k_big_eval(BigArgs a) {
   const int64_t nb = (int64_t)*a.count;
   const int64_t total = a.ws.epre[nb];
@@ -239,7 +280,7 @@ __global__ void __launch_bounds__(kNT) k_big_eval(BigArgs a) {
 __global__ void __launch_bounds__(kNT) k_big_decide(BigArgs a) {
   __shared__ int32_t s_target;
   const int64_t nb = (int64_t)*a.count;
-  if (a.ws.epre[nb] == 0 && nb > 0) return;  // plan found no room (error already set)
+  if (a.ws.cpre[nb] == 0 && nb > 0) return;  // plan found no room (error already set)
   unsigned long long glo = 0, ghi = 0, gm = 0;
   unsigned long long work[3] = {0, 0, 0};  // vertices, movers, mover entries
   for (int64_t k = blockIdx.x; k < nb; k += gridDim.x) {
@@ -288,62 +329,33 @@ __global__ void __launch_bounds__(kNT) k_big_decide(BigArgs a) {
 // Aggregation: append every occupied slot of a slice to the community's row
 // (super-edge (c, key, weight)); slots are cleared.
 __global__ void __launch_bounds__(kNT) k_big_emit(BigArgs a) {
-  __shared__ unsigned long long s_cnt;
   __shared__ unsigned long long s_base;
   const int64_t nb = (int64_t)*a.count;
   const int64_t total = a.ws.epre[nb];
   unsigned long long written = 0;
-  const int lane = threadIdx.x & 31;
   for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
     const int64_t k = upper_index(a.ws.epre, nb, g);
     const int32_t c = a.items[k];
-    const int64_t cap = table_cap(a.ws.tot[k], a.keyspace);
-    const int64_t s0 = (g - a.ws.epre[k]) * kBigEvalSlots;
-    int32_t *keys = a.ws.keys + a.ws.toff[k];
-    uint32_t *vals = a.ws.vals + a.ws.toff[k];
-    if (threadIdx.x == 0) s_cnt = 0;
-    __syncthreads();
-    // two passes over the slice: count, then write at a reserved range
-    int32_t key[kBigEvalSlots / kNT];
-    uint32_t val[kBigEvalSlots / kNT];
-    unsigned mine = 0;
-#pragma unroll
-    for (int r = 0; r < kBigEvalSlots / kNT; ++r) {
-      const int64_t s = s0 + r * kNT + threadIdx.x;
-      key[r] = kEmpty;
-      if (s < cap) {
-        key[r] = __ldcg(keys + s);
-        if (key[r] != kEmpty) {
-          val[r] = __ldcg(vals + s);
-          keys[s] = kEmpty;
-          vals[s] = 0;
-          ++mine;
-        }
-      }
-    }
-    const unsigned wsum = __reduce_add_sync(kFull, mine);
-    unsigned woff = 0;
-    if (lane == 0 && wsum) woff = (unsigned)atomicAdd(&s_cnt, (unsigned long long)wsum);
-    woff = __shfl_sync(kFull, woff, 0);
-    // exclusive prefix of `mine` within the warp
-    unsigned incl = mine;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl += y;
+    const int64_t nocc = (int64_t)a.ws.ocnt[k];
+    const int64_t p0 = (g - a.ws.epre[k]) * kBigEvalSlots;
+    const int64_t p1 = p0 + kBigEvalSlots < nocc ? p0 + kBigEvalSlots : nocc;
+    const int64_t toff = a.ws.toff[k];
+    int32_t *keys = a.ws.keys + toff;
+    uint32_t *vals = a.ws.vals + toff;
+    const int32_t *occ = a.ws.occ + toff / 2;
+    if (threadIdx.x == 0) {
+      s_base = atomicAdd((unsigned long long *)(a.oend + c), (unsigned long long)(p1 - p0));
+      written += (unsigned long long)(p1 - p0);
     }
     __syncthreads();
-    if (threadIdx.x == 0 && s_cnt) s_base = atomicAdd((unsigned long long *)(a.oend + c), s_cnt);
-    __syncthreads();
-    unsigned long long pos = s_base + woff + (incl - mine);
-#pragma unroll
-    for (int r = 0; r < kBigEvalSlots / kNT; ++r) {
-      if (key[r] == kEmpty) continue;
-      a.ocol[pos] = key[r];
-      a.ow[pos] = val[r];
-      ++pos;
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += kNT) {
+      const int32_t s = occ[p];
+      const unsigned long long pos = s_base + (unsigned long long)(p - p0);
+      a.ocol[pos] = __ldcg(keys + s);
+      a.ow[pos] = __ldcg(vals + s);
+      keys[s] = kEmpty;
+      vals[s] = 0;
     }
-    if (threadIdx.x == 0) written += s_cnt;
     __syncthreads();
   }
   if (threadIdx.x == 0 && written) {
@@ -362,6 +374,7 @@ void big_run(const BigArgs &b, int num_sms, cudaStream_t s) {
   }
   LV_LAUNCH(k_big_plan<MODE><<<1, 1024, 0, s>>>(b));
   LV_LAUNCH(k_big_accum<MODE, WK><<<num_sms * 3, kNT, kSmem, s>>>(b));
+  if (MODE == MODE_MERGE) LV_LAUNCH(k_big_plan2<<<1, 1024, 0, s>>>(b));
   if (MODE == MODE_MOVE) {
     LV_LAUNCH(k_big_eval<<<num_sms * 3, kNT, 0, s>>>(b));
     LV_LAUNCH(k_big_decide<<<num_sms * 2, kNT, 0, s>>>(b));

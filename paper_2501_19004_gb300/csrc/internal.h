@@ -31,7 +31,7 @@ __host__ __device__ __forceinline__ int degree_bin(int64_t d) {
 // between uses: the kernels that read a slot also clear it.
 constexpr int kBigChunk = 4096;       // entries per accumulation chunk (512 threads x 8)
 constexpr int kBigSmemSlots = 8192;   // shared pre-aggregation table per block
-constexpr int kBigEvalSlots = 8192;   // table slots per evaluation block
+constexpr int kBigEvalSlots = 8192;   // occupied slots per evaluation block
 struct BigWs {
   int32_t *keys = nullptr;
   uint32_t *vals = nullptr;
@@ -40,6 +40,8 @@ struct BigWs {
   int64_t *toff = nullptr;            // [items+1] table offset
   int64_t *cpre = nullptr;            // [items+1] accumulation chunk prefix
   int64_t *epre = nullptr;            // [items+1] evaluation chunk prefix
+  int32_t *occ = nullptr;             // [slots/2] occupied slots; item k's list starts at toff[k]/2
+  unsigned long long *ocnt = nullptr; // [items] occupied slots per item
   long long *part_s = nullptr;        // [parts] partial argmax of an evaluation block
   int32_t *part_c = nullptr;
   unsigned long long *part_kid = nullptr;

@@ -184,11 +184,15 @@ louvain_status ensure_big(louvain_ctx *x, int64_t slots, int64_t parts, int64_t 
   if (slots > b.slots) {
     dfree(x, b.keys);
     dfree(x, b.vals);
+    dfree(x, b.occ);
     b.keys = nullptr;
     b.vals = nullptr;
+    b.occ = nullptr;
     b.slots = 0;
     const int64_t want = slots + slots / 4;
-    if ((st = dalloc_n(x, &b.keys, want)) || (st = dalloc_n(x, &b.vals, want))) return st;
+    if ((st = dalloc_n(x, &b.keys, want)) || (st = dalloc_n(x, &b.vals, want)) ||
+        (st = dalloc_n(x, &b.occ, want / 2 + 1)))
+      return st;
     LV_CK(cudaMemsetAsync(b.keys, 0xFF, (size_t)want * sizeof(int32_t), x->stream));
     LV_CK(cudaMemsetAsync(b.vals, 0, (size_t)want * sizeof(uint32_t), x->stream));
     b.slots = want;
@@ -208,9 +212,11 @@ louvain_status ensure_big(louvain_ctx *x, int64_t slots, int64_t parts, int64_t 
     dfree(x, b.toff);
     dfree(x, b.cpre);
     dfree(x, b.epre);
+    dfree(x, b.ocnt);
     const int64_t want = items + items / 4 + 64;
     if ((st = dalloc_n(x, &b.tot, want + 1)) || (st = dalloc_n(x, &b.toff, want + 1)) ||
-        (st = dalloc_n(x, &b.cpre, want + 1)) || (st = dalloc_n(x, &b.epre, want + 1)))
+        (st = dalloc_n(x, &b.cpre, want + 1)) || (st = dalloc_n(x, &b.epre, want + 1)) ||
+        (st = dalloc_n(x, &b.ocnt, want + 1)))
       return st;
     b.item_cap = want;
   }

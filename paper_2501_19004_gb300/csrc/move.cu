@@ -180,8 +180,8 @@ __device__ __forceinline__ void gather_run(const MoveArgs &a, int32_t i, int64_t
 }
 
 // ------------------------------------------------------------------ warp bin
-// 16 < degree <= 256: one warp, a shared table of up to 512 slots; each lane
-// reads a run of 8 consecutive entries.
+// 16 < degree <= 256: one warp, a shared table of up to 512 slots; lanes read
+// consecutive entries, up to 8 rounds of 32.
 template <int WK, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32) k_move_warp(MoveArgs a) {
   __shared__ int32_t skeys[WARPS][kWarpCap];
@@ -209,7 +209,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_move_warp(MoveArgs a) {
       uint32_t ww[kRun];
       gather_run<WK>(a, i, b, x0 + lane, 32, deg, kk, ww);
 #pragma unroll
-      for (int u = 0; u < kRun; ++u) warp_insert_sm(keys, vals, mask, kk[u], ww[u], a.ctr);
+      for (int u = 0; u < kRun; ++u) {
+        if (x0 + u * 32 >= deg) break;  // warp-uniform
+        warp_insert_sm(keys, vals, mask, kk[u], ww[u], a.ctr);
+      }
     }
     __syncwarp();
     const int32_t d = a.Cp[i];
@@ -289,7 +292,10 @@ __global__ void __launch_bounds__(NT) k_move_block(MoveArgs a) {
       uint32_t ww[kRun];
       gather_run<WK>(a, i, b, x0 + threadIdx.x, NT, deg, kk, ww);
 #pragma unroll
-      for (int u = 0; u < kRun; ++u) warp_insert_sm(keys, vals, mask, kk[u], ww[u], a.ctr);
+      for (int u = 0; u < kRun; ++u) {
+        if (x0 + u * NT + (threadIdx.x & ~31) >= deg) break;  // warp-uniform
+        warp_insert_sm(keys, vals, mask, kk[u], ww[u], a.ctr);
+      }
     }
     __syncthreads();
     const int32_t d = a.Cp[i];

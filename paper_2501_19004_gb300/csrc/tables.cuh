@@ -48,6 +48,31 @@ __device__ __forceinline__ void gm_insert(int32_t *keys, uint32_t *vals, uint32_
   atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
 }
 
+// Global insert that reports the slot it claimed for a new key (-1 when the
+// key was already present), so that callers can list the occupied slots.
+__device__ __forceinline__ int64_t gm_insert_claim(int32_t *keys, uint32_t *vals, uint32_t mask, int32_t key,
+                                                   uint32_t w, Counters *ctr) {
+  uint32_t s = slot_of(key, mask);
+  for (uint32_t t = 0; t <= mask; ++t) {
+    int32_t k = __ldcg(keys + s);
+    bool claimed = false;
+    if (k == kEmpty) {
+      k = atomicCAS(keys + s, kEmpty, key);
+      if (k == kEmpty) {
+        k = key;
+        claimed = true;
+      }
+    }
+    if (k == key) {
+      atomicAdd(vals + s, w);
+      return claimed ? (int64_t)s : -1;
+    }
+    s = (s + 1) & mask;
+  }
+  atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
+  return -1;
+}
+
 // Warp-cooperative insert into a shared table: all 32 lanes call it (key =
 // kEmpty for nothing).  When the warp holds few distinct keys (a hot
 // community), lanes with equal keys are summed first and one lane inserts;
