@@ -498,11 +498,7 @@ void merge_t(const AggArgs &a, int num_sms, cudaStream_t s, KernelProf *prof) {
   LV_TIMED(prof, K_MERGE_WARP, s, k_merge_warp<WK, 8><<<num_sms * 7, 256, 0, s>>>(a));
   LV_TIMED(prof, K_MERGE_MID, s, k_merge_block<WK, 128, kMidCap, 2><<<num_sms * 12, 128, kMidSmem, s>>>(a));
   LV_TIMED(prof, K_MERGE_BLOCK, s, k_merge_block<WK, 512, kBlockCap, 3><<<num_sms * 3, 512, kSmem, s>>>(a));
-  if (a.big.ws.slots > 0) {
-    if (prof) prof->begin(K_MERGE_BIG, s);
-    big_merge(a.big, WK, num_sms, s);
-    if (prof) prof->end(K_MERGE_BIG, s);
-  }
+  if (a.big.ws.slots > 0) big_merge(a.big, WK, num_sms, s, prof);
 }
 
 template <int WK>

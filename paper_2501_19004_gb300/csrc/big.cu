@@ -365,15 +365,20 @@ __global__ void __launch_bounds__(kNT) k_big_emit(BigArgs a) {
 }
 
 template <int MODE, int WK>
-void big_run(const BigArgs &b, int num_sms, cudaStream_t s) {
+void big_run(const BigArgs &b, int num_sms, cudaStream_t s, KernelProf *prof) {
+  const int k_acc = MODE == MODE_MOVE ? K_MOVE_HUB : K_MERGE_BIG;
+  const int k_rest = MODE == MODE_MOVE ? K_MOVE_HUB_EVAL : K_MERGE_BIG_EMIT;
   static bool attr_done = false;
   constexpr size_t kSmem = (size_t)kBigSmemSlots * (sizeof(int32_t) + sizeof(uint32_t));
   if (!attr_done) {
     cudaFuncSetAttribute(k_big_accum<MODE, WK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     attr_done = true;
   }
+  if (prof) prof->begin(k_rest, s);
   LV_LAUNCH(k_big_plan<MODE><<<1, 1024, 0, s>>>(b));
-  LV_LAUNCH(k_big_accum<MODE, WK><<<num_sms * 3, kNT, kSmem, s>>>(b));
+  if (prof) prof->end(k_rest, s);
+  LV_TIMED(prof, k_acc, s, k_big_accum<MODE, WK><<<num_sms * 3, kNT, kSmem, s>>>(b));
+  if (prof) prof->begin(k_rest, s);
   if (MODE == MODE_MERGE) LV_LAUNCH(k_big_plan2<<<1, 1024, 0, s>>>(b));
   if (MODE == MODE_MOVE) {
     LV_LAUNCH(k_big_eval<<<num_sms * 3, kNT, 0, s>>>(b));
@@ -381,18 +386,19 @@ void big_run(const BigArgs &b, int num_sms, cudaStream_t s) {
   } else {
     LV_LAUNCH(k_big_emit<<<num_sms * 3, kNT, 0, s>>>(b));
   }
+  if (prof) prof->end(k_rest, s);
 }
 
 }  // namespace
 
-void big_move(const BigArgs &b, int wkind, int num_sms, cudaStream_t s) {
-  if (wkind == W_UNIT) big_run<MODE_MOVE, W_UNIT>(b, num_sms, s);
-  else big_run<MODE_MOVE, W_U32>(b, num_sms, s);
+void big_move(const BigArgs &b, int wkind, int num_sms, cudaStream_t s, KernelProf *prof) {
+  if (wkind == W_UNIT) big_run<MODE_MOVE, W_UNIT>(b, num_sms, s, prof);
+  else big_run<MODE_MOVE, W_U32>(b, num_sms, s, prof);
 }
 
-void big_merge(const BigArgs &b, int wkind, int num_sms, cudaStream_t s) {
-  if (wkind == W_UNIT) big_run<MODE_MERGE, W_UNIT>(b, num_sms, s);
-  else big_run<MODE_MERGE, W_U32>(b, num_sms, s);
+void big_merge(const BigArgs &b, int wkind, int num_sms, cudaStream_t s, KernelProf *prof) {
+  if (wkind == W_UNIT) big_run<MODE_MERGE, W_UNIT>(b, num_sms, s, prof);
+  else big_run<MODE_MERGE, W_U32>(b, num_sms, s, prof);
 }
 
 }  // namespace lv

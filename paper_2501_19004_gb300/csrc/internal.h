@@ -77,8 +77,12 @@ struct BigArgs {
 };
 
 // big hub vertices of one bucket step / big communities of one aggregation
-void big_move(const BigArgs &b, int wkind, int num_sms, cudaStream_t s);
-void big_merge(const BigArgs &b, int wkind, int num_sms, cudaStream_t s);
+// (event timing: the accumulation kernel under K_MOVE_HUB / K_MERGE_BIG, the
+// planning, evaluation and emission kernels under K_MOVE_HUB_EVAL /
+// K_MERGE_BIG_EMIT)
+struct KernelProf;
+void big_move(const BigArgs &b, int wkind, int num_sms, cudaStream_t s, KernelProf *prof);
+void big_merge(const BigArgs &b, int wkind, int num_sms, cudaStream_t s, KernelProf *prof);
 
 inline int grid_for(int64_t n, int threads, int num_sms, int per_sm) {
   int64_t g = (n + threads - 1) / threads;
@@ -113,7 +117,7 @@ struct MoveArgs {
 enum KernelId : int {
   K_SELECT = 0, K_MOVE_THREAD, K_MOVE_WARP, K_MOVE_MID, K_MOVE_BLOCK, K_MOVE_HUB, K_APPLY, K_PASS_INIT,
   K_COMM_COUNT, K_SCATTER, K_MERGE_THREAD, K_MERGE_WARP, K_MERGE_MID, K_MERGE_BLOCK, K_MERGE_BIG, K_DENDRO,
-  K_MODULARITY, K_RENUMBER, K_NUM_KERNELS
+  K_MODULARITY, K_RENUMBER, K_MOVE_HUB_EVAL, K_MERGE_BIG_EMIT, K_NUM_KERNELS
 };
 extern const char *const kKernelNames[K_NUM_KERNELS];
 

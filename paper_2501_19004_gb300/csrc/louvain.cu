@@ -256,6 +256,11 @@ void account_move(louvain_ctx *x, int64_t n, const Counters &h) {
   const double wb = x->cur_wbytes;
   for (int b = 0; b < kNumBins; ++b) {
     const unsigned long long *w = h.mv_work[b];
+    if (b == kBigBin) {  // entries in the accumulation kernel, the rest in evaluation
+      x->kbytes[K_MOVE_HUB] += (8.0 + wb) * w[1];
+      x->kbytes[K_MOVE_HUB_EVAL] += 40.0 * w[0] + 8.0 * w[2] + 8.0 * w[3] + 1.0 * w[4];
+      continue;
+    }
     x->kbytes[K_MOVE_THREAD + b] +=
         40.0 * w[0] + (8.0 + wb) * w[1] + 8.0 * w[2] + 8.0 * w[3] + 1.0 * w[4];
   }
@@ -271,6 +276,11 @@ void account_merge(louvain_ctx *x, const Counters &h) {
   const double wb = x->cur_wbytes;
   for (int b = 0; b < kNumBins; ++b) {
     const unsigned long long *w = h.mg_work[b];
+    if (b == kBigBin) {
+      x->kbytes[K_MERGE_BIG] += 20.0 * w[1] + (8.0 + wb) * w[2];
+      x->kbytes[K_MERGE_BIG_EMIT] += 36.0 * w[0] + 8.0 * w[3];
+      continue;
+    }
     x->kbytes[K_MERGE_THREAD + b] += 36.0 * w[0] + 20.0 * w[1] + (8.0 + wb) * w[2] + 8.0 * w[3];
   }
 }

@@ -424,11 +424,7 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
   LV_TIMED(prof, K_MOVE_WARP, s, k_move_warp<WK, 8><<<num_sms * 7, 256, 0, s>>>(a));
   LV_TIMED(prof, K_MOVE_MID, s, k_move_block<WK, 128, kMidCap, 2><<<num_sms * 12, 128, kMidSmem, s>>>(a));
   LV_TIMED(prof, K_MOVE_BLOCK, s, k_move_block<WK, 512, kBlockCap, 3><<<num_sms * 3, 512, kBlockSmem, s>>>(a));
-  if (big.ws.slots > 0) {
-    if (prof) prof->begin(K_MOVE_HUB, s);
-    big_move(big, WK, num_sms, s);
-    if (prof) prof->end(K_MOVE_HUB, s);
-  }
+  if (big.ws.slots > 0) big_move(big, WK, num_sms, s, prof);
   LV_TIMED(prof, K_APPLY, s, k_apply<<<num_sms * 4, 256, 0, s>>>(a));
 }
 
@@ -461,6 +457,6 @@ void iota_i32(int32_t *x, int64_t n, int num_sms, cudaStream_t s) {
 const char *const kKernelNames[K_NUM_KERNELS] = {
     "select", "move_thread", "move_warp", "move_mid", "move_block", "move_hub", "apply", "pass_init",
     "comm_count", "comm_scatter", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big",
-    "dendrogram", "modularity", "renumber"};
+    "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit"};
 
 }  // namespace lv
