@@ -95,6 +95,13 @@ typedef struct {
   int32_t check_symmetry;        /* 1: louvain_create verifies w_ij = w_ji (host graphs) */
   uint32_t profile_mask;         /* bit k: time kernel group k with CUDA events
                                     (ids in louvain_stats' "kernels"); 0 = off */
+  int64_t trace_capacity;        /* > 0: record up to this many (features, moved)
+                                    samples of evaluated vertices (louvain_traces) */
+  float trace_rate;              /* fraction of decisions recorded (hash-sampled) */
+  int32_t learned_fallback;      /* LEARNED: after the learned iterations of a pass,
+                                    a full sweep and plain iterations run until
+                                    0: an iteration's dQ <= tau (the plain rule),
+                                    1: an iteration makes no move */
 } louvain_config;
 
 /* Fill `cfg` with the defaults above (mode PLAIN, seed 0). */
@@ -153,8 +160,48 @@ const char *louvain_last_error(const louvain_ctx *ctx);
 louvain_status louvain_modularity_of(const louvain_graph *graph, const int32_t *membership, void *stream,
                                      double *q, int64_t *num_hi_lo, int64_t *den_hi_lo);
 
+/* ---- Learned vertex-activity predictor (an addition of this library; the
+ * paper has no counterpart).  An 8 -> 32 -> 32 -> 1 MLP decides which
+ * flagged vertices of a bucket the local-moving phase evaluates: a vertex
+ * whose predicted probability of moving is below skip_threshold keeps its
+ * flag and is skipped for this iteration.  After the learned iterations of a
+ * pass converge, a full plain sweep (every vertex, no skipping) runs, and
+ * plain iterations continue until the plain method's tolerance test holds
+ * (or, with learned_fallback = 1, until one makes no move); the sweep bounds
+ * the modularity gap to the plain method.  Parameters: W1[8][32], b1[32],
+ * W2[32][32], b2[32], w3[32], b3 (fp32; W[k][n] maps input k to output n);
+ * evaluation rounds x, W1, W2, w3 and the hidden ReLU outputs to bf16 and
+ * accumulates in fp32 on the tensor cores.  Features per vertex, in order:
+ * log2(1 + degree)/24, intra-community weight fraction and best-dQ margin
+ * (s(c*) - s(d))/(2m K_i) at its last evaluation, moved at its last
+ * evaluation, iteration/MAX_ITERATIONS, pass/MAX_PASSES, Sigma of its
+ * community/2m, and min(1, neighbour moves since its last evaluation/degree).
+ */
+
 /* Number of floats of the learned predictor's parameters (8->32->32->1 MLP). */
 int64_t louvain_model_size(void);
+
+/* Recorded samples of the last run (config.trace_capacity > 0): features
+ * [count][8] and labels [count] (1 = the vertex moved when evaluated).  The
+ * outputs are caller-owned, host or device (on_device); *count receives the
+ * number of samples (at most cap). */
+louvain_status louvain_traces(const louvain_ctx *ctx, float *features, float *labels, int64_t cap, int64_t *count,
+                              int32_t on_device);
+
+/* Logits of n feature rows X[n][8] (device pointers; params on the device). */
+louvain_status louvain_mlp_forward(const float *params, const float *X, int64_t n, float *logits, void *stream);
+
+/* Gradient of the mean binary cross-entropy of sigmoid(logit) against
+ * labels Y over n rows, added into grad[louvain_model_size()]; the mean loss
+ * is added into *loss (device pointers; loss may be NULL). */
+louvain_status louvain_mlp_gradient(const float *params, const float *X, const float *Y, int64_t n, float *grad,
+                                    float *loss, void *stream);
+
+/* Adam training of params (device, in/out) on (X, Y) (device): `epochs`
+ * passes of minibatches of `batch` rows in a seeded order; per-epoch mean
+ * losses into losses[epochs] (host, may be NULL). */
+louvain_status louvain_mlp_train(float *params, const float *X, const float *Y, int64_t n, int32_t epochs,
+                                 int32_t batch, float lr, uint64_t seed, float *losses, void *stream);
 
 /* Library build description (architecture, version). */
 const char *louvain_version(void);

@@ -23,6 +23,7 @@
 #include <climits>
 
 #include "internal.h"
+#include "learn.cuh"
 #include "tables.cuh"
 
 namespace lv {
@@ -300,7 +301,10 @@ __global__ void __launch_bounds__(kNT) k_big_decide(BigArgs a) {
     const int64_t b = a.g.begin[i], e = a.g.end[i];
     if (threadIdx.x == 0) {
       const int32_t d = a.Cp[i];
-      const int32_t t = finish_decision(a.two_m, a.Sigma, a.pickless, d, a.K[i], Kid, best_s, best_c, glo, ghi, gm);
+      long long s_d = 0;
+      const int32_t t =
+          finish_decision(a.two_m, a.Sigma, a.pickless, d, a.K[i], Kid, best_s, best_c, glo, ghi, gm, &s_d);
+      learn_record(a.learn, a.ctr, a.g, a.Cp, a.Sigma, a.two_m, i, a.K[i], Kid, best_s, best_c, s_d, t >= 0);
       work[0] += 1;
       if (t >= 0) {
         work[1] += 1;
@@ -315,7 +319,10 @@ __global__ void __launch_bounds__(kNT) k_big_decide(BigArgs a) {
     if (s_target >= 0)
       for (int64_t q = b + threadIdx.x; q < e; q += kNT) {
         const int32_t j = __ldg(a.g.col + q);
-        if (j != i) a.flag[j] = 1;
+        if (j != i) {
+          a.flag[j] = 1;
+          learn_mark(a.learn, j);
+        }
       }
     __syncthreads();
   }

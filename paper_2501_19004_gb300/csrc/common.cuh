@@ -59,7 +59,9 @@ struct Counters {
   unsigned long long q_tot_lo;      // modularity: sum of low 32 bits of Sigma_c^2
   unsigned long long q_tot_hi;      // modularity: sum of high 32 bits of Sigma_c^2
   unsigned long long scan_total[4]; // totals of the aggregation scans
-  unsigned long long pad[4];
+  unsigned long long cand_count;    // learned mode: candidates of the bucket for the predictor
+  unsigned long long trace_count;   // recorded (features, moved) samples
+  unsigned long long pad[2];
 };
 constexpr int kIterCounterWords = 5 + 25;
 
@@ -152,8 +154,9 @@ __device__ __forceinline__ void flush_work(unsigned long long (&w)[N], unsigned 
 __device__ __forceinline__ int32_t finish_decision(long long two_m, const int64_t *Sigma, int pickless, int32_t d,
                                                    long long Ki, long long Kid, long long best_s, int32_t best_c,
                                                    unsigned long long &glo, unsigned long long &ghi,
-                                                   unsigned long long &gm) {
+                                                   unsigned long long &gm, long long *s_d_out = nullptr) {
   const long long s_d = two_m * Kid - Ki * (Sigma[d] - Ki);
+  if (s_d_out) *s_d_out = s_d;
   if (best_c == 0x7FFFFFFF || !(best_s > s_d) || (pickless && best_c > d)) return -1;
   const unsigned long long gain = (unsigned long long)best_s - (unsigned long long)s_d;
   glo += gain & 0xFFFFFFFFull;

@@ -49,6 +49,23 @@ struct BigWs {
   int64_t item_cap = 0;               // capacity of tot/toff/cpre/epre
 };
 
+// Learned vertex-activity predictor and trace recorder (see mlp.cu).
+struct LearnArgs {
+  int enabled = 0;              // the predictor may skip flagged vertices
+  int record = 0;               // per-vertex features are maintained
+  const float *params = nullptr;  // device MLP parameters
+  float4 *feat = nullptr;       // [n] intra fraction, margin, moved, valid
+  uint32_t *marks = nullptr;    // [n] neighbour moves since the last evaluation
+  int32_t *cand = nullptr;      // [n] candidates of the bucket
+  float thr_logit = 0.f;        // evaluate iff logit >= thr_logit
+  float t_norm = 0.f, p_norm = 0.f;
+  float *trace_x = nullptr;     // [cap][8] recorded features
+  float *trace_y = nullptr;     // [cap] recorded labels (moved)
+  int64_t trace_cap = 0;
+  uint32_t trace_keep = 0;      // keep a decision iff hash16 < trace_keep
+  uint32_t trace_salt = 0;
+};
+
 struct BigArgs {
   GView g;
   const int32_t *Cp;                  // C' (move: snapshot; merge: dense new ids)
@@ -65,6 +82,7 @@ struct BigArgs {
   int pickless;
   int32_t *mv_vertex;
   int32_t *mv_target;
+  LearnArgs learn;
   // aggregation
   const int64_t *mprefix;             // member-degree exclusive prefix (community-vertex CSR order)
   const int64_t *kcoff;
@@ -106,18 +124,14 @@ struct MoveArgs {
   int32_t *mv_vertex;
   int32_t *mv_target;
   Counters *ctr;
-  // learned mode (null when plain)
-  const float *mlp;          // device parameters
-  float *feat;               // per-vertex features [n][8]
-  float skip_threshold;
-  int learned;
+  LearnArgs learn;
 };
 
 // Kernel identifiers for the optional per-kernel event timing.
 enum KernelId : int {
   K_SELECT = 0, K_MOVE_THREAD, K_MOVE_WARP, K_MOVE_MID, K_MOVE_BLOCK, K_MOVE_HUB, K_APPLY, K_PASS_INIT,
   K_COMM_COUNT, K_SCATTER, K_MERGE_THREAD, K_MERGE_WARP, K_MERGE_MID, K_MERGE_BLOCK, K_MERGE_BIG, K_DENDRO,
-  K_MODULARITY, K_RENUMBER, K_MOVE_HUB_EVAL, K_MERGE_BIG_EMIT, K_NUM_KERNELS
+  K_MODULARITY, K_RENUMBER, K_MOVE_HUB_EVAL, K_MERGE_BIG_EMIT, K_MLP_SELECT, K_NUM_KERNELS
 };
 extern const char *const kKernelNames[K_NUM_KERNELS];
 
@@ -158,7 +172,7 @@ void move_bucket(const MoveArgs &a, const BigArgs &big, int wkind, int num_sms, 
 // pass initialisation: K (row sums on pass 0, else given), Sigma = K, C' = id,
 // flags = 1, max degree into ctr->maxdeg
 void pass_init(const GView &g, int wkind, int first_pass, int64_t *K, int64_t *Sigma, int32_t *Cp,
-               uint8_t *flag, Counters *ctr, int num_sms, cudaStream_t s);
+               uint8_t *flag, Counters *ctr, int num_sms, cudaStream_t s, const LearnArgs *learn = nullptr);
 
 void iota_i32(int32_t *x, int64_t n, int num_sms, cudaStream_t s);
 
@@ -216,9 +230,14 @@ void modularity_sums(const GView &g, int wkind, const int32_t *memb, const int64
 void renumber_dense(int32_t *x, int64_t n, int64_t idspace, unsigned long long *used, int64_t *newid,
                     long long *tmp, unsigned long long *total, int num_sms, cudaStream_t s);
 
-// learned predictor
+// learned predictor (device pointers; see mlp.cu)
 int64_t mlp_param_count();
-void mlp_features_init(float *feat, int64_t n, int num_sms, cudaStream_t s);
+void mlp_forward(const float *params, const float *X, int64_t n, float *logit, cudaStream_t s);
+void mlp_gradient(const float *params, const float *X, const float *Y, int64_t n, float scale, float *grad,
+                  float *loss, cudaStream_t s);
+void mlp_adam(float *params, const float *grad, float *m, float *v, float lr, int step, cudaStream_t s);
+void mlp_gather_batch(const float *X, const float *Y, int64_t n, int64_t start, int64_t count, uint64_t stride,
+                      float *Xb, float *Yb, cudaStream_t s);
 
 size_t scan_tmp_elems(int64_t n);
 

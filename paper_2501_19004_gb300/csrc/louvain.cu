@@ -9,14 +9,19 @@
 // host only reads a few scalars per iteration (the exact gain sum) and per
 // pass (community count, sizes).
 #include <algorithm>
+#include <array>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
 
+#include <cmath>
+#include <numeric>
+
 #include "../../include/louvain.h"
 #include "internal.h"
+#include "mlp.cuh"
 
 using namespace lv;
 typedef __int128 i128;
@@ -62,8 +67,14 @@ struct louvain_ctx {
   // global tables of big items (hubs, large communities)
   BigWs big;
   bool big_dirty = false;
-  // learned predictor
-  float *mlp = nullptr, *feat = nullptr;
+  // learned predictor and trace recorder
+  float *mlp = nullptr;
+  float4 *feat = nullptr;
+  uint32_t *marks = nullptr;
+  int32_t *cand = nullptr;
+  float *trace_x = nullptr, *trace_y = nullptr;
+  int64_t trace_count = 0;
+  std::vector<std::array<long long, 3>> learned_log;  // per pass: learned iterations, fallback iterations, last moves
 
   Counters *d_ctr = nullptr;
   Counters *h_ctr = nullptr;  // pinned
@@ -285,13 +296,99 @@ void account_merge(louvain_ctx *x, const Counters &h) {
   }
 }
 
+LearnArgs learn_args(louvain_ctx *x, int pass, int t, bool skipping) {
+  const louvain_config &cfg = x->cfg;
+  LearnArgs L;
+  L.record = x->feat != nullptr;
+  L.enabled = skipping && cfg.mode == LOUVAIN_MODE_LEARNED;
+  L.params = x->mlp;
+  L.feat = x->feat;
+  L.marks = x->marks;
+  L.cand = x->cand;
+  const double th = std::min(std::max((double)cfg.skip_threshold, 1e-6), 1.0 - 1e-6);
+  L.thr_logit = (float)std::log(th / (1.0 - th));
+  L.t_norm = (float)t / (float)cfg.max_iterations;
+  L.p_norm = (float)pass / (float)std::max(cfg.max_passes, 1);
+  if (x->trace_x) {
+    L.trace_x = x->trace_x;
+    L.trace_y = x->trace_y;
+    L.trace_cap = cfg.trace_capacity;
+    const double r = std::min(std::max((double)cfg.trace_rate, 0.0), 1.0);
+    L.trace_keep = (uint32_t)std::lround(r * 65536.0);
+    L.trace_salt = fmix32(0x7261ce5u ^ ((uint32_t)pass << 8) ^ (uint32_t)t);
+  }
+  return L;
+}
+
+// One iteration of the local-moving phase (all buckets); fills *h.
+louvain_status move_iteration(louvain_ctx *x, const GView &g, int wk, int pass, int t, bool skipping,
+                              const Counters **h_out);
+
 // Local-moving phase (Algorithm 5) under the bucket schedule; returns l_i.
+// Learned mode: iterations with the predictor until the tolerance is met,
+// then a full plain sweep and plain iterations until one makes no move.
 louvain_status move_phase(louvain_ctx *x, const GView &g, int wk, int pass, double tau, int *li_out) {
   const louvain_config &cfg = x->cfg;
+  if (cfg.mode == LOUVAIN_MODE_LEARNED) {
+    const i128 den2 = (i128)x->two_m * x->two_m;
+    int t = 0;
+    for (; t < cfg.max_iterations; ++t) {
+      const Counters *h;
+      louvain_status st = move_iteration(x, g, wk, pass, t, true, &h);
+      if (st) return st;
+      const i128 gain = ((i128)h->it_gain_hi << 32) + (i128)h->it_gain_lo;
+      const double total = den2 ? (double)(2 * gain) / (double)den2 : 0.0;
+      if (total <= tau) {
+        ++t;
+        break;
+      }
+    }
+    // fallback: a full sweep without the predictor, then plain iterations
+    // until the plain tolerance test holds (or until an iteration makes no
+    // move)
+    const int learned_iters = t;
+    long long last_moves = -1;
+    LV_CK(cudaMemsetAsync(x->flag, 1, (size_t)g.n, x->stream));
+    for (int f = 0; f < cfg.max_iterations; ++f, ++t) {
+      const Counters *h;
+      louvain_status st = move_iteration(x, g, wk, pass, t, false, &h);
+      if (st) return st;
+      last_moves = (long long)h->it_moves;
+      const i128 gain = ((i128)h->it_gain_hi << 32) + (i128)h->it_gain_lo;
+      const double total = den2 ? (double)(2 * gain) / (double)den2 : 0.0;
+      if (cfg.learned_fallback ? h->it_moves == 0 : total <= tau) {
+        ++t;
+        break;
+      }
+    }
+    x->learned_log.push_back({(long long)learned_iters, (long long)(t - learned_iters), last_moves});
+    *li_out = t;
+    return LOUVAIN_OK;
+  }
   const i128 den2 = (i128)x->two_m * x->two_m;
   int li = cfg.max_iterations;
   for (int t = 0; t < cfg.max_iterations; ++t) {
+    const Counters *hp;
+    louvain_status st = move_iteration(x, g, wk, pass, t, false, &hp);
+    if (st) return st;
+    const Counters &h = *hp;
+    const i128 gain = ((i128)h.it_gain_hi << 32) + (i128)h.it_gain_lo;
+    const double total = den2 ? (double)(2 * gain) / (double)den2 : 0.0;
+    if (total <= tau) {
+      li = t + 1;
+      break;
+    }
+  }
+  *li_out = li;
+  return LOUVAIN_OK;
+}
+
+louvain_status move_iteration(louvain_ctx *x, const GView &g, int wk, int pass, int t, bool skipping,
+                              const Counters **h_out) {
+  const louvain_config &cfg = x->cfg;
+  {
     const int rho = cfg.pickless_period;
+    const LearnArgs L = learn_args(x, pass, t, skipping && t > 0);
     const int pickless = rho > 0 && ((t + rho / 2) % rho) == 0;
     LV_CK(cudaMemsetAsync(&x->d_ctr->it_gain_lo, 0, kIterCounterWords * sizeof(unsigned long long), x->stream));
     MoveArgs a{};
@@ -308,6 +405,7 @@ louvain_status move_phase(louvain_ctx *x, const GView &g, int wk, int pass, doub
     a.mv_vertex = x->mv_vertex;
     a.mv_target = x->mv_target;
     a.ctr = x->d_ctr;
+    a.learn = L;
     BigArgs big{};
     big.g = g;
     big.Cp = x->Cp;
@@ -324,12 +422,10 @@ louvain_status move_phase(louvain_ctx *x, const GView &g, int wk, int pass, doub
     big.pickless = pickless;
     big.mv_vertex = x->mv_vertex;
     big.mv_target = x->mv_target;
-    a.mlp = x->mlp;
-    a.feat = x->feat;
-    a.skip_threshold = cfg.skip_threshold;
-    a.learned = cfg.mode == LOUVAIN_MODE_LEARNED;
+    big.learn = L;
     for (int b = 0; b < cfg.buckets; ++b) {
       LV_CK(cudaMemsetAsync(x->d_ctr, 0, 10 * sizeof(unsigned long long), x->stream));
+      if (L.enabled) LV_CK(cudaMemsetAsync(&x->d_ctr->cand_count, 0, sizeof(unsigned long long), x->stream));
       a.bucket = (uint32_t)b;
       move_bucket(a, big, wk, x->num_sms, x->stream, x->prof.mask ? &x->prof : nullptr);
     }
@@ -339,7 +435,7 @@ louvain_status move_phase(louvain_ctx *x, const GView &g, int wk, int pass, doub
     const Counters &h = *x->h_ctr;
     const i128 gain = ((i128)h.it_gain_hi << 32) + (i128)h.it_gain_lo;
     account_move(x, g.n, h);
-    if (pass < cfg.max_passes) {
+    if (pass < cfg.max_passes && t < cfg.max_iterations) {
       int64_t *r = &x->iter_stats[((size_t)pass * cfg.max_iterations + t) * 4];
       r[0] = (int64_t)h.it_evaluated;
       r[1] = (int64_t)h.it_moves;
@@ -349,13 +445,8 @@ louvain_status move_phase(louvain_ctx *x, const GView &g, int wk, int pass, doub
     x->moves_total += (long long)h.it_moves;
     x->evaluated_total += (long long)h.it_evaluated;
     x->skipped_total += (long long)h.it_skipped;
-    const double total = den2 ? (double)(2 * gain) / (double)den2 : 0.0;
-    if (total <= tau) {
-      li = t + 1;
-      break;
-    }
+    *h_out = &h;
   }
-  *li_out = li;
   return LOUVAIN_OK;
 }
 
@@ -381,6 +472,7 @@ louvain_status run_impl(louvain_ctx *x) {
   x->pass_stats.assign((size_t)std::max(cfg.max_passes, 1) * 6, 0);
   x->it_total = x->moves_total = x->evaluated_total = x->skipped_total = 0;
   const long long launches0 = g_launches;
+  x->learned_log.clear();
   for (int k = 0; k < K_NUM_KERNELS; ++k) {
     x->prof.ms[k] = 0;
     x->prof.launches[k] = 0;
@@ -412,7 +504,10 @@ louvain_status run_impl(louvain_ctx *x) {
     x->cur_wbytes = wk == W_UNIT ? 0 : 4;
     LV_CK(cudaMemsetAsync(&x->d_ctr->big_slots, 0, 2 * sizeof(unsigned long long), s));
     x->prof.begin(K_PASS_INIT, s);
-    pass_init(g, wk, p == 0, x->K, x->Sigma, x->Cp, x->flag, x->d_ctr, x->num_sms, s);
+    {
+      const LearnArgs L = learn_args(x, p, 0, false);
+      pass_init(g, wk, p == 0, x->K, x->Sigma, x->Cp, x->flag, x->d_ctr, x->num_sms, s, &L);
+    }
     x->prof.end(K_PASS_INIT, s);
     LV_CK(cudaGetLastError());
     if ((st = read_counters(x))) return st;
@@ -541,6 +636,7 @@ louvain_status run_impl(louvain_ctx *x) {
   if ((st = read_counters(x))) return st;
   if (x->prof.mask) x->prof.collect();
   x->gamma = (int64_t)x->h_ctr->scan_total[3];
+  x->trace_count = std::min<int64_t>((int64_t)x->h_ctr->trace_count, x->cfg.trace_capacity);
   x->qnum = qn;
   x->qden = qd;
   x->q = qd ? (double)qn / (double)qd : 0.0;
@@ -574,7 +670,8 @@ louvain_status validate_config(const louvain_config *c) {
   if (c->buckets < 1 || c->pickless_period < 0) return LOUVAIN_E_INVAL;
   if (!(c->tolerance >= 0) || !(c->tolerance_drop > 0) || !(c->aggregation_tolerance >= 0)) return LOUVAIN_E_INVAL;
   if (c->mode != LOUVAIN_MODE_PLAIN && c->mode != LOUVAIN_MODE_LEARNED) return LOUVAIN_E_INVAL;
-  if (c->mode == LOUVAIN_MODE_LEARNED && !c->model) return LOUVAIN_E_INVAL;
+  if (c->mode == LOUVAIN_MODE_LEARNED && (!c->model || c->max_iterations > 127)) return LOUVAIN_E_INVAL;
+  if (c->trace_capacity < 0) return LOUVAIN_E_INVAL;
   return LOUVAIN_OK;
 }
 
@@ -738,9 +835,20 @@ louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg
     if ((st = dalloc_n(x, &x->pcol[k], nnz)) || (st = dalloc_n(x, &x->pw[k], nnz)) ||
         (st = dalloc_n(x, &x->pbeg[k], nv)) || (st = dalloc_n(x, &x->pend[k], nv)))
       return fail(st);
+  if (cfg->mode == LOUVAIN_MODE_LEARNED || cfg->trace_capacity > 0) {
+    if ((st = dalloc_n(x, &x->feat, nv)) || (st = dalloc_n(x, &x->marks, nv))) return fail(st);
+  }
   if (cfg->mode == LOUVAIN_MODE_LEARNED) {
-    set_err(x, "learned mode is not available in this build");
-    return fail(LOUVAIN_E_INVAL);
+    if ((st = dalloc_n(x, &x->cand, nv)) || (st = dalloc_n(x, &x->mlp, (int64_t)kMlpParams))) return fail(st);
+    if (cudaMemcpyAsync(x->mlp, cfg->model, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, x->stream)) {
+      set_err(x, "copy of the model parameters failed");
+      return fail(LOUVAIN_E_CUDA);
+    }
+  }
+  if (cfg->trace_capacity > 0) {
+    if ((st = dalloc_n(x, &x->trace_x, cfg->trace_capacity * kFeatures)) ||
+        (st = dalloc_n(x, &x->trace_y, cfg->trace_capacity)))
+      return fail(st);
   }
   x->timing.resize((size_t)std::max(cfg->max_passes, 1));
   for (auto &pt : x->timing) {
@@ -783,6 +891,10 @@ void louvain_config_default(louvain_config *c) {
   c->skip_threshold = 0.5f;
   c->record_pass_modularity = 0;
   c->check_symmetry = 0;
+  c->profile_mask = 0;
+  c->trace_capacity = 0;
+  c->trace_rate = 1.0f;
+  c->learned_fallback = 0;
 }
 
 louvain_status louvain_create(const louvain_graph *graph, const louvain_config *cfg, void *stream, louvain_ctx **out) {
@@ -866,6 +978,15 @@ louvain_status louvain_stats(const louvain_ctx *xc, char *json, size_t cap) {
   snprintf(buf, sizeof buf, "\"move_ms\": %.4f, \"aggregate_ms\": %.4f, \"other_ms\": %.4f, ", tm, ta,
            x->run_ms - tm - ta);
   s += buf;
+  if (x->cfg.mode == LOUVAIN_MODE_LEARNED) {
+    per += ", \"learned_passes\": [";
+    for (size_t p = 0; p < x->learned_log.size(); ++p) {
+      snprintf(buf, sizeof buf, "%s[%lld, %lld, %lld]", p ? ", " : "", x->learned_log[p][0], x->learned_log[p][1],
+               x->learned_log[p][2]);
+      per += buf;
+    }
+    per += "]";
+  }
   s += per + ", \"kernels\": {";
   bool first = true;
   for (int k = 0; k < K_NUM_KERNELS; ++k) {
@@ -954,6 +1075,107 @@ louvain_status louvain_modularity_of(const louvain_graph *graph, const int32_t *
 }
 
 int64_t louvain_model_size(void) { return mlp_param_count(); }
+
+louvain_status louvain_traces(const louvain_ctx *xc, float *features, float *labels, int64_t cap, int64_t *count,
+                              int32_t on_device) {
+  louvain_ctx *x = const_cast<louvain_ctx *>(xc);
+  if (!x || !count || cap < 0) return LOUVAIN_E_INVAL;
+  if (!x->ran) return LOUVAIN_E_STATE;
+  const int64_t c = std::min(cap, x->trace_count);
+  *count = c;
+  if (c == 0) return LOUVAIN_OK;
+  if (!features || !labels) return LOUVAIN_E_INVAL;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  LV_CK(cudaMemcpyAsync(features, x->trace_x, (size_t)c * kFeatures * sizeof(float), kind, x->stream));
+  LV_CK(cudaMemcpyAsync(labels, x->trace_y, (size_t)c * sizeof(float), kind, x->stream));
+  LV_CK(cudaStreamSynchronize(x->stream));
+  return LOUVAIN_OK;
+}
+
+louvain_status louvain_mlp_forward(const float *params, const float *X, int64_t n, float *logits, void *stream) {
+  if (!params || n < 0 || (n > 0 && (!X || !logits))) return LOUVAIN_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  mlp_forward(params, X, n, logits, s);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+    g_create_err = "MLP forward kernel failed";
+    return LOUVAIN_E_CUDA;
+  }
+  return LOUVAIN_OK;
+}
+
+louvain_status louvain_mlp_gradient(const float *params, const float *X, const float *Y, int64_t n, float *grad,
+                                    float *loss, void *stream) {
+  if (!params || !grad || n < 0 || (n > 0 && (!X || !Y))) return LOUVAIN_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n > 0) mlp_gradient(params, X, Y, n, 1.0f / (float)n, grad, loss, s);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
+    g_create_err = "MLP gradient kernel failed";
+    return LOUVAIN_E_CUDA;
+  }
+  return LOUVAIN_OK;
+}
+
+louvain_status louvain_mlp_train(float *params, const float *X, const float *Y, int64_t n, int32_t epochs,
+                                 int32_t batch, float lr, uint64_t seed, float *losses, void *stream) {
+  if (!params || n <= 0 || !X || !Y || epochs < 0 || batch < 16 || !(lr > 0)) return LOUVAIN_E_INVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t b = std::min<int64_t>(batch, n);
+  float *grad = nullptr, *m = nullptr, *v = nullptr, *Xb = nullptr, *Yb = nullptr, *lossd = nullptr;
+  auto cleanup = [&]() {
+    for (void *p : {(void *)grad, (void *)m, (void *)v, (void *)Xb, (void *)Yb, (void *)lossd})
+      if (p) cudaFreeAsync(p, s);
+    cudaStreamSynchronize(s);
+  };
+  if (cudaMallocAsync((void **)&grad, sizeof(float) * kMlpParams, s) ||
+      cudaMallocAsync((void **)&m, sizeof(float) * kMlpParams, s) ||
+      cudaMallocAsync((void **)&v, sizeof(float) * kMlpParams, s) ||
+      cudaMallocAsync((void **)&Xb, sizeof(float) * kFeatures * b, s) ||
+      cudaMallocAsync((void **)&Yb, sizeof(float) * b, s) || cudaMallocAsync((void **)&lossd, sizeof(float), s)) {
+    cudaGetLastError();
+    cleanup();
+    g_create_err = "allocation for MLP training failed";
+    return LOUVAIN_E_NOMEM;
+  }
+  cudaMemsetAsync(m, 0, sizeof(float) * kMlpParams, s);
+  cudaMemsetAsync(v, 0, sizeof(float) * kMlpParams, s);
+  // a seeded visiting order: row r of an epoch is (offset + r) * stride mod n
+  // with stride coprime to n (a permutation), fresh per epoch
+  uint64_t state = seed ^ 0x9E3779B97F4A7C15ull;
+  auto next = [&]() {
+    state += 0x9E3779B97F4A7C15ull;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  int step = 0;
+  for (int e = 0; e < epochs; ++e) {
+    uint64_t stride = (next() % (uint64_t)n) | 1ull;
+    while (std::gcd(stride, (uint64_t)n) != 1) stride += 2;
+    const uint64_t offset = next() % (uint64_t)n;
+    cudaMemsetAsync(lossd, 0, sizeof(float), s);
+    for (int64_t start = 0; start < n; start += b) {
+      const int64_t cnt = std::min<int64_t>(b, n - start);
+      mlp_gather_batch(X, Y, n, (int64_t)offset + start, cnt, stride, Xb, Yb, s);
+      cudaMemsetAsync(grad, 0, sizeof(float) * kMlpParams, s);
+      mlp_gradient(params, Xb, Yb, cnt, 1.0f / (float)cnt, grad, lossd, s);
+      mlp_adam(params, grad, m, v, lr, ++step, s);
+    }
+    if (losses) {
+      float l = 0;
+      cudaMemcpyAsync(&l, lossd, sizeof(float), cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+      losses[e] = l * (float)b / (float)n;
+    }
+  }
+  const bool ok = cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
+  cleanup();
+  if (!ok) {
+    g_create_err = "MLP training kernels failed";
+    return LOUVAIN_E_CUDA;
+  }
+  return LOUVAIN_OK;
+}
 
 const char *louvain_version(void) { return "gb300-louvain 0.1 (sm_103a)"; }
 

@@ -18,6 +18,7 @@
 #include <climits>
 
 #include "internal.h"
+#include "learn.cuh"
 #include "tables.cuh"
 
 namespace lv {
@@ -39,14 +40,29 @@ __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
     const int64_t i = tile + threadIdx.x;
     int bin = -1;
     bool sel = false;
+    bool cand = false;
     if (i < n && a.flag[i]) {
       const uint32_t h = fmix32((uint32_t)i ^ a.salt);
       const uint32_t bk = pow2 ? (h & (a.nbuckets - 1)) : (h % a.nbuckets);
       if (bk == a.bucket) {
-        a.flag[i] = 0;
-        sel = true;
-        const int64_t deg = a.g.end[i] - a.g.begin[i];
-        if (deg > 0) bin = degree_bin(deg);
+        if (a.learn.enabled && a.learn.feat[i].w > 0.f) {
+          cand = true;  // the predictor decides (k_mlp_select); the flag stays until then
+        } else {
+          a.flag[i] = 0;
+          sel = true;
+          const int64_t deg = a.g.end[i] - a.g.begin[i];
+          if (deg > 0) bin = degree_bin(deg);
+        }
+      }
+    }
+    if (a.learn.enabled) {
+      const unsigned cmask = __ballot_sync(kFull, cand);
+      if (cmask) {
+        const int leader = __ffs(cmask) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(&a.ctr->cand_count, (unsigned long long)__popc(cmask));
+        base = __shfl_sync(kFull, base, leader);
+        if (cand) a.learn.cand[base + __popc(cmask & lanemask_lt())] = (int32_t)i;
       }
     }
     unsigned woff[kNumBins];
@@ -71,6 +87,68 @@ __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
       if (bin == b) a.bins[b][s_base[b] + off + __popc(bmask[b] & lanemask_lt())] = (int32_t)i;
     }
     __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------ learned select
+// One warp per 16 candidates: features, the BF16 MLP on the tensor cores, and
+// the skip decision.  Evaluated vertices are marked processed and binned;
+// skipped ones keep their flag for a later iteration.
+__global__ void __launch_bounds__(256) k_mlp_select(MoveArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  MlpFrags f;
+  mlp_load_frags(a.learn.params, f, lane);
+  const int64_t cnt = (int64_t)a.ctr->cand_count;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long evaluated = 0, skipped = 0;
+  for (int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; tile * 16 < cnt; tile += warps) {
+    const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
+    const int32_t i0 = r0 < cnt ? a.learn.cand[r0] : -1;
+    const int32_t i1 = r1 < cnt ? a.learn.cand[r1] : -1;
+    float x0[2] = {0.f, 0.f}, x1[2] = {0.f, 0.f};
+    float xf[kFeatures];
+    if (i0 >= 0) {
+      vertex_features(a.g, a.Cp, a.Sigma, a.two_m, a.learn, i0, a.learn.feat[i0], xf);
+      x0[0] = xf[2 * t];
+      x0[1] = xf[2 * t + 1];
+    }
+    if (i1 >= 0) {
+      vertex_features(a.g, a.Cp, a.Sigma, a.two_m, a.learn, i1, a.learn.feat[i1], xf);
+      x1[0] = xf[2 * t];
+      x1[1] = xf[2 * t + 1];
+    }
+    float h1[4][4], h2[4][4], l0, l1;
+    mlp_tile_forward(f, x0, x1, h1, h2, l0, l1, t);
+    // lane t = 0 of each quad decides row g, lane t = 1 row g + 8
+    const int32_t mine = t == 0 ? i0 : (t == 1 ? i1 : -1);
+    const float logit = t == 0 ? l0 : l1;
+    const bool eval = mine >= 0 && logit >= a.learn.thr_logit;
+    int bin = -1;
+    if (eval) {
+      a.flag[mine] = 0;
+      const int64_t deg = a.g.end[mine] - a.g.begin[mine];
+      if (deg > 0) bin = degree_bin(deg);
+      ++evaluated;
+    } else if (mine >= 0) {
+      ++skipped;
+    }
+#pragma unroll
+    for (int b = 0; b < kNumBins; ++b) {
+      const unsigned m = __ballot_sync(kFull, bin == b);
+      if (!m) continue;
+      const int leader = __ffs(m) - 1;
+      unsigned long long base = 0;
+      if (lane == leader) base = atomicAdd(&a.ctr->bin_count[b], (unsigned long long)__popc(m));
+      base = __shfl_sync(kFull, base, leader);
+      if (bin == b) a.bins[b][base + __popc(m & lanemask_lt())] = mine;
+    }
+  }
+  evaluated = warp_sum_u(evaluated);
+  skipped = warp_sum_u(skipped);
+  if (lane == 0) {
+    if (evaluated) atomicAdd(&a.ctr->it_evaluated, evaluated);
+    if (skipped) atomicAdd(&a.ctr->it_skipped, skipped);
   }
 }
 
@@ -131,7 +209,9 @@ __global__ void __launch_bounds__(256) k_move_thread(MoveArgs a) {
           }
         }
       }
-      target = finish_decision(a.two_m, a.Sigma, a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm);
+      long long s_d = 0;
+      target = finish_decision(a.two_m, a.Sigma, a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm, &s_d);
+      learn_record(a.learn, a.ctr, a.g, a.Cp, a.Sigma, a.two_m, i, Ki, Kid, best_s, best_c, s_d, target >= 0);
       work[0] += 1;
       work[1] += (unsigned long long)deg;
       if (target >= 0) {
@@ -139,7 +219,10 @@ __global__ void __launch_bounds__(256) k_move_thread(MoveArgs a) {
         work[4] += (unsigned long long)deg;
 #pragma unroll
         for (int k = 0; k < D; ++k)
-          if (jj[k] != i) a.flag[jj[k]] = 1;
+          if (jj[k] != i) {
+            a.flag[jj[k]] = 1;
+            learn_mark(a.learn, jj[k]);
+          }
       }
     }
     const bool mv = target >= 0;
@@ -238,7 +321,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_move_warp(MoveArgs a) {
     Kid = warp_sum(Kid);
     int32_t target = -1;
     if (lane == 0) {
-      target = finish_decision(a.two_m, a.Sigma, a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm);
+      long long s_d = 0;
+      target = finish_decision(a.two_m, a.Sigma, a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm, &s_d);
+      learn_record(a.learn, a.ctr, a.g, a.Cp, a.Sigma, a.two_m, i, Ki, Kid, best_s, best_c, s_d, target >= 0);
       work[0] += 1;
       work[1] += (unsigned long long)deg;
       if (target >= 0) {
@@ -253,7 +338,10 @@ __global__ void __launch_bounds__(WARPS * 32) k_move_warp(MoveArgs a) {
     if (target >= 0)
       for (int64_t k = b + lane; k < e; k += 32) {
         const int32_t j = __ldg(a.g.col + k);
-        if (j != i) a.flag[j] = 1;
+        if (j != i) {
+          a.flag[j] = 1;
+          learn_mark(a.learn, j);
+        }
       }
     __syncwarp();
   }
@@ -319,7 +407,9 @@ __global__ void __launch_bounds__(NT) k_move_block(MoveArgs a) {
     }
     block_argmax_sum<NT>(best_s, best_c, Kid);
     if (threadIdx.x == 0) {
-      const int32_t t = finish_decision(a.two_m, a.Sigma, a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm);
+      long long s_d = 0;
+      const int32_t t = finish_decision(a.two_m, a.Sigma, a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm, &s_d);
+      learn_record(a.learn, a.ctr, a.g, a.Cp, a.Sigma, a.two_m, i, Ki, Kid, best_s, best_c, s_d, t >= 0);
       work[0] += 1;
       work[1] += (unsigned long long)deg;
       if (t >= 0) {
@@ -335,7 +425,10 @@ __global__ void __launch_bounds__(NT) k_move_block(MoveArgs a) {
     if (s_target >= 0)
       for (int64_t k = b + threadIdx.x; k < e; k += NT) {
         const int32_t j = __ldg(a.g.col + k);
-        if (j != i) a.flag[j] = 1;
+        if (j != i) {
+          a.flag[j] = 1;
+          learn_mark(a.learn, j);
+        }
       }
     __syncthreads();
   }
@@ -363,7 +456,8 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
 // tables (sum of pow2(2 min(deg, n')) over degrees > 4096) for the host.
 template <int WK>
 __global__ void __launch_bounds__(256) k_pass_init(GView g, int first_pass, int64_t *K, int64_t *Sigma,
-                                                   int32_t *Cp, uint8_t *flag, Counters *ctr) {
+                                                   int32_t *Cp, uint8_t *flag, Counters *ctr, float4 *feat,
+                                                   uint32_t *marks) {
   unsigned long long md = 0, big_slots = 0, big_items = 0;
   const int lane = threadIdx.x & 31;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -389,6 +483,10 @@ __global__ void __launch_bounds__(256) k_pass_init(GView g, int first_pass, int6
     Sigma[i] = k;
     Cp[i] = (int32_t)i;
     flag[i] = 1;
+    if (feat) {
+      feat[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      marks[i] = 0;
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -420,6 +518,7 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
     attr_done = true;
   }
   LV_TIMED(prof, K_SELECT, s, k_select<<<grid_for(a.g.n, 256, num_sms, 8), 256, 0, s>>>(a));
+  if (a.learn.enabled) LV_TIMED(prof, K_MLP_SELECT, s, k_mlp_select<<<num_sms * 4, 256, 0, s>>>(a));
   LV_TIMED(prof, K_MOVE_THREAD, s, k_move_thread<WK><<<num_sms * 8, 256, 0, s>>>(a));
   LV_TIMED(prof, K_MOVE_WARP, s, k_move_warp<WK, 8><<<num_sms * 7, 256, 0, s>>>(a));
   LV_TIMED(prof, K_MOVE_MID, s, k_move_block<WK, 128, kMidCap, 2><<<num_sms * 12, 128, kMidSmem, s>>>(a));
@@ -430,8 +529,11 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
 
 template <int WK>
 void pass_init_t(const GView &g, int first, int64_t *K, int64_t *Sigma, int32_t *Cp, uint8_t *flag, Counters *ctr,
-                 int num_sms, cudaStream_t s) {
-  LV_LAUNCH(k_pass_init<WK><<<grid_for(g.n, 256, num_sms, 16), 256, 0, s>>>(g, first, K, Sigma, Cp, flag, ctr));
+                 int num_sms, cudaStream_t s, const LearnArgs *learn) {
+  float4 *feat = (learn && learn->record) ? learn->feat : nullptr;
+  uint32_t *marks = (learn && learn->record) ? learn->marks : nullptr;
+  LV_LAUNCH(k_pass_init<WK><<<grid_for(g.n, 256, num_sms, 16), 256, 0, s>>>(g, first, K, Sigma, Cp, flag, ctr, feat,
+                                                                             marks));
 }
 
 }  // namespace
@@ -443,10 +545,10 @@ void move_bucket(const MoveArgs &a, const BigArgs &big, int wkind, int num_sms, 
 }
 
 void pass_init(const GView &g, int wkind, int first_pass, int64_t *K, int64_t *Sigma, int32_t *Cp, uint8_t *flag,
-               Counters *ctr, int num_sms, cudaStream_t s) {
+               Counters *ctr, int num_sms, cudaStream_t s, const LearnArgs *learn) {
   if (g.n <= 0) return;
-  if (wkind == W_UNIT) pass_init_t<W_UNIT>(g, first_pass, K, Sigma, Cp, flag, ctr, num_sms, s);
-  else pass_init_t<W_U32>(g, first_pass, K, Sigma, Cp, flag, ctr, num_sms, s);
+  if (wkind == W_UNIT) pass_init_t<W_UNIT>(g, first_pass, K, Sigma, Cp, flag, ctr, num_sms, s, learn);
+  else pass_init_t<W_U32>(g, first_pass, K, Sigma, Cp, flag, ctr, num_sms, s, learn);
 }
 
 void iota_i32(int32_t *x, int64_t n, int num_sms, cudaStream_t s) {
@@ -457,6 +559,6 @@ void iota_i32(int32_t *x, int64_t n, int num_sms, cudaStream_t s) {
 const char *const kKernelNames[K_NUM_KERNELS] = {
     "select", "move_thread", "move_warp", "move_mid", "move_block", "move_hub", "apply", "pass_init",
     "comm_count", "comm_scatter", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big",
-    "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit"};
+    "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit", "mlp_select"};
 
 }  // namespace lv

@@ -58,7 +58,8 @@ class LouvainConfig(ctypes.Structure):
                 ("buckets", ctypes.c_int32), ("schedule_seed", ctypes.c_uint64), ("mode", ctypes.c_int32),
                 ("model", ctypes.c_void_p), ("skip_threshold", ctypes.c_float),
                 ("record_pass_modularity", ctypes.c_int32), ("check_symmetry", ctypes.c_int32),
-                ("profile_mask", ctypes.c_uint32)]
+                ("profile_mask", ctypes.c_uint32), ("trace_capacity", ctypes.c_int64), ("trace_rate", ctypes.c_float),
+                ("learned_fallback", ctypes.c_int32)]
 
 
 _lib = None
@@ -98,6 +99,14 @@ def load(path: Optional[str] = None):
     lib.louvain_last_error.argtypes = [vp]
     lib.louvain_modularity_of.restype = ctypes.c_int
     lib.louvain_modularity_of.argtypes = [P(LouvainGraph), vp, vp, P(ctypes.c_double), vp, vp]
+    lib.louvain_traces.restype = ctypes.c_int
+    lib.louvain_traces.argtypes = [vp, vp, vp, i64, P(i64), i32]
+    lib.louvain_mlp_forward.restype = ctypes.c_int
+    lib.louvain_mlp_forward.argtypes = [vp, vp, i64, vp, vp]
+    lib.louvain_mlp_gradient.restype = ctypes.c_int
+    lib.louvain_mlp_gradient.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+    lib.louvain_mlp_train.restype = ctypes.c_int
+    lib.louvain_mlp_train.argtypes = [vp, vp, vp, i64, i32, i32, ctypes.c_float, ctypes.c_uint64, vp, vp]
     lib.louvain_model_size.restype = i64
     lib.louvain_model_size.argtypes = []
     lib.louvain_version.restype = ctypes.c_char_p
@@ -130,6 +139,9 @@ class Config:
     record_pass_modularity: bool = False
     check_symmetry: bool = False
     profile_mask: int = 0
+    trace_capacity: int = 0
+    trace_rate: float = 1.0
+    learned_fallback: int = 0
 
     def c(self) -> LouvainConfig:
         self._model_keep = None
@@ -140,7 +152,8 @@ class Config:
         return LouvainConfig(self.max_passes, self.max_iterations, self.tolerance, self.tolerance_drop,
                              self.aggregation_tolerance, self.pickless_period, self.buckets,
                              self.schedule_seed & (2**64 - 1), self.mode, mp, self.skip_threshold,
-                             int(self.record_pass_modularity), int(self.check_symmetry), self.profile_mask)
+                             int(self.record_pass_modularity), int(self.check_symmetry), self.profile_mask,
+                             self.trace_capacity, self.trace_rate, self.learned_fallback)
 
 
 @dataclass
@@ -279,6 +292,45 @@ def louvain_modularity_of(graph, membership, stream=None):
     del keep
     _check(st, None)
     return q.value, _i128(num), _i128(den)
+
+
+def louvain_traces(ctx, cap: int):
+    """(features [count][8], labels [count]) recorded by the last run (numpy)."""
+    feats = np.zeros((max(cap, 1), 8), dtype=np.float32)
+    labels = np.zeros(max(cap, 1), dtype=np.float32)
+    cnt = ctypes.c_int64()
+    _check(load().louvain_traces(ctx, feats.ctypes.data, labels.ctypes.data, cap, ctypes.byref(cnt), 0), ctx)
+    return feats[:cnt.value], labels[:cnt.value]
+
+
+def _dev(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def louvain_mlp_forward(params, X):
+    """Logits of feature rows X (torch CUDA float32 [n][8]); params torch CUDA float32."""
+    import torch
+    out = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+    _check(load().louvain_mlp_forward(_dev(params), _dev(X), X.shape[0], _dev(out), _current_stream()))
+    return out
+
+
+def louvain_mlp_gradient(params, X, Y):
+    """(gradient, mean loss) of the BCE loss (torch CUDA tensors)."""
+    import torch
+    grad = torch.zeros(params.shape[0], dtype=torch.float32, device=X.device)
+    loss = torch.zeros(1, dtype=torch.float32, device=X.device)
+    _check(load().louvain_mlp_gradient(_dev(params), _dev(X), _dev(Y), X.shape[0], _dev(grad), _dev(loss),
+                                       _current_stream()))
+    return grad, float(loss.item())
+
+
+def louvain_mlp_train(params, X, Y, epochs=10, batch=4096, lr=3e-3, seed=0):
+    """Adam training in place of params (torch CUDA); returns per-epoch losses."""
+    losses = np.zeros(max(epochs, 1), dtype=np.float32)
+    _check(load().louvain_mlp_train(_dev(params), _dev(X), _dev(Y), X.shape[0], epochs, batch, lr, seed,
+                                    losses.ctypes.data, _current_stream()))
+    return losses[:epochs]
 
 
 def louvain_model_size() -> int:

@@ -1,0 +1,151 @@
+"""GPU tests of the learned vertex-activity predictor: the tensor-core MLP
+kernels against the CPU oracle (oracle/mlp.py), training, trace recording,
+and the learned-skip run against the plain method (|dQ| <= 1e-3, zero-move
+final sweeps, and the work it saves)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp as omlp
+from paper_2501_19004_gb300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2501_19004_gb300 import louvain as lv  # noqa: E402
+
+
+def _features(rng, n):
+    X = np.empty((n, 8), dtype=np.float32)
+    X[:, 0] = rng.uniform(0, 1, n)
+    X[:, 1] = rng.uniform(0, 1, n)
+    X[:, 2] = rng.uniform(-1, 1, n)
+    X[:, 3] = rng.integers(0, 2, n)
+    X[:, 4] = rng.uniform(0, 1, n)
+    X[:, 5] = rng.uniform(0, 1, n)
+    X[:, 6] = rng.uniform(0, 0.2, n)
+    X[:, 7] = rng.uniform(0, 1, n)
+    return X
+
+
+@pytest.mark.parametrize("n", [1, 15, 16, 17, 1000, 4099])
+def test_forward_matches_oracle(n):
+    rng = np.random.default_rng(n)
+    p = omlp.init_params(7)
+    p[256:288] = rng.normal(0, 0.2, 32)
+    p[1312:1344] = rng.normal(0, 0.2, 32)
+    p[-1] = -0.3
+    X = _features(rng, n)
+    got = lv.louvain_mlp_forward(torch.from_numpy(p).cuda(), torch.from_numpy(X).cuda()).cpu().numpy()
+    want, _ = omlp.forward(p, X, bf16=True)
+    # fp32 vs exact accumulation of bf16 products, plus at most a one-ulp
+    # bf16 flip of a hidden unit: well inside 1e-2 (1 + |logit|)
+    assert np.all(np.abs(got - want) <= 1e-2 * (1 + np.abs(want))), np.max(np.abs(got - want))
+
+
+@pytest.mark.parametrize("n", [16, 128, 129, 5000])
+def test_gradient_matches_oracle(n):
+    rng = np.random.default_rng(100 + n)
+    p = omlp.init_params(11)
+    p[256:288] = rng.normal(0, 0.2, 32)
+    p[1312:1344] = rng.normal(0, 0.2, 32)
+    X = _features(rng, n)
+    Y = (rng.random(n) < 0.35).astype(np.float32)
+    g, loss = lv.louvain_mlp_gradient(torch.from_numpy(p).cuda(), torch.from_numpy(X).cuda(),
+                                      torch.from_numpy(Y).cuda())
+    g = g.cpu().numpy().astype(np.float64)
+    want, wloss = omlp.gradient(p, X, Y, bf16=True)
+    assert abs(loss - wloss) <= 1e-3 * (1 + wloss)
+    for name, (a, b, _) in omlp._SL.items():
+        err = np.linalg.norm(g[a:b] - want[a:b])
+        assert err <= 2e-2 * np.linalg.norm(want[a:b]) + 1e-7, (name, err, np.linalg.norm(want[a:b]))
+
+
+def test_training_fits_a_separable_rule():
+    rng = np.random.default_rng(5)
+    n = 20000
+    X = _features(rng, n)
+    Y = ((X[:, 2] > 0.1) & (X[:, 7] > 0.3)).astype(np.float32)  # moves when the margin is positive
+    p = torch.from_numpy(omlp.init_params(1)).cuda()
+    losses = lv.louvain_mlp_train(p, torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), epochs=25, batch=1024,
+                                  lr=3e-3, seed=1)
+    assert losses[-1] < 0.5 * losses[0], losses
+    logit = lv.louvain_mlp_forward(p, torch.from_numpy(X).cuda()).cpu().numpy()
+    acc = np.mean((logit > 0) == (Y > 0.5))
+    assert acc > 0.95, acc
+
+
+def _traces(g, cap=400000, rate=1.0):
+    with lv.Louvain(lv.DeviceCSR.from_host(g), lv.Config(trace_capacity=cap, trace_rate=rate)) as ctx:
+        ctx.run()
+        res = ctx.result()
+        X, Y = lv.louvain_traces(ctx.ctx, cap)
+    return X, Y, res
+
+
+def test_trace_recording_does_not_change_the_run():
+    g = gg.rmat(13, 16, seed=3)
+    X, Y, res = _traces(g)
+    ref = oracle.louvain(g)
+    assert np.array_equal(res.membership, ref.membership)
+    assert X.shape[0] > 1000 and X.shape[1] == 8
+    assert set(np.unique(Y)) <= {0.0, 1.0}
+    assert np.all(X[:, 0] >= 0) and np.all(np.abs(X[:, 2]) <= 1) and np.all((X[:, 7] >= 0) & (X[:, 7] <= 1))
+
+
+def _trained_model():
+    X, Y = [], []
+    for sc, seed in ((14, 101), (15, 102)):
+        x, y, _ = _traces(gg.rmat(sc, 16, seed=seed))
+        X.append(x)
+        Y.append(y)
+    X = np.concatenate(X)
+    Y = np.concatenate(Y)
+    p = torch.from_numpy(omlp.init_params(0)).cuda()
+    lv.louvain_mlp_train(p, torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), epochs=8, batch=4096, lr=3e-3)
+    return p.cpu().numpy(), float(Y.mean())
+
+
+def test_learned_skip_run():
+    model, pos_rate = _trained_model()
+    g = gg.rmat(15, 16, seed=13)
+    plain = lv.run(lv.DeviceCSR.from_host(g), lv.Config())
+    ref = oracle.louvain(g)
+    assert np.array_equal(plain.membership, ref.membership)
+    with lv.Louvain(lv.DeviceCSR.from_host(g), lv.Config(mode=lv.MODE_LEARNED, model=model,
+                                                         skip_threshold=0.5)) as ctx:
+        ctx.run()
+        res = ctx.result()
+        st = ctx.stats()
+    # the learned run is a valid partition whose modularity the oracle confirms
+    q, num, den = oracle.modularity(g, res.membership)
+    assert (num, den) == (res.q_num, res.q_den)
+    assert abs(res.modularity - plain.modularity) <= 1e-3, (res.modularity, plain.modularity)
+    # every pass ends with a full plain sweep phase
+    for learned_it, fallback_it, last_moves in st["learned_passes"]:
+        assert fallback_it >= 1
+    assert st["skipped"] > 0
+    # the zero-move fallback: every pass's last plain iteration made no move
+    with lv.Louvain(lv.DeviceCSR.from_host(g), lv.Config(mode=lv.MODE_LEARNED, model=model, skip_threshold=0.5,
+                                                         learned_fallback=1)) as ctx:
+        ctx.run()
+        st1 = ctx.stats()
+        r1 = ctx.result()
+    for learned_it, fallback_it, last_moves in st1["learned_passes"]:
+        assert last_moves == 0 or fallback_it == 20
+    assert oracle.modularity(g, r1.membership)[1:] == (r1.q_num, r1.q_den)
+
+
+def test_untrained_threshold_zero_is_plain_plus_sweeps():
+    g = gg.rmat(13, 16, seed=9)
+    p = np.zeros(omlp.N_PARAMS, dtype=np.float32)  # logit 0 -> p = 0.5 >= threshold 0.25: nothing skipped
+    with lv.Louvain(lv.DeviceCSR.from_host(g), lv.Config(mode=lv.MODE_LEARNED, model=p, skip_threshold=0.25)) as ctx:
+        ctx.run()
+        st = ctx.stats()
+        res = ctx.result()
+    assert st["skipped"] == 0
+    plain = lv.run(g)
+    assert abs(res.modularity - plain.modularity) <= 1e-3
