@@ -178,6 +178,20 @@ louvain_status louvain_modularity_of(const louvain_graph *graph, const int32_t *
  * community/2m, and min(1, neighbour moves since its last evaluation/degree).
  */
 
+/* louvain_modularity_of without any allocation, for callers that cannot let
+ * a library allocate device memory (for example an application whose own
+ * pool allocator owns the whole device, or a serving loop that must not call
+ * cudaMalloc).  The paper has no counterpart.  Same result as
+ * louvain_modularity_of; the graph and the membership must be device arrays
+ * (graph->on_device = 1) and n may not exceed 1,048,576 (LOUVAIN_E_INVAL
+ * beyond that).  Scratch lives in a fixed 8 MiB array inside the library
+ * that every GPU loading the library keeps until exit; calls share it, so
+ * calls that overlap on the GPU race.  The first call on a device looks the
+ * array up (make it before any stream capture).  Out-of-range ids or
+ * non-positive weights give LOUVAIN_E_INVAL, 2m >= 2^32 LOUVAIN_E_OVERFLOW. */
+louvain_status louvain_modularity_noalloc(const louvain_graph *graph, const int32_t *membership, void *stream,
+                                          double *q, int64_t *num_hi_lo, int64_t *den_hi_lo);
+
 /* Number of floats of the learned predictor's parameters (8->32->32->1 MLP). */
 int64_t louvain_model_size(void);
 

@@ -107,6 +107,8 @@ def load(path: Optional[str] = None):
     lib.louvain_mlp_gradient.argtypes = [vp, vp, vp, i64, vp, vp, vp]
     lib.louvain_mlp_train.restype = ctypes.c_int
     lib.louvain_mlp_train.argtypes = [vp, vp, vp, i64, i32, i32, ctypes.c_float, ctypes.c_uint64, vp, vp]
+    lib.louvain_modularity_noalloc.restype = ctypes.c_int
+    lib.louvain_modularity_noalloc.argtypes = [P(LouvainGraph), vp, vp, P(ctypes.c_double), vp, vp]
     lib.louvain_model_size.restype = i64
     lib.louvain_model_size.argtypes = []
     lib.louvain_version.restype = ctypes.c_char_p
@@ -331,6 +333,21 @@ def louvain_mlp_train(params, X, Y, epochs=10, batch=4096, lr=3e-3, seed=0):
     _check(load().louvain_mlp_train(_dev(params), _dev(X), _dev(Y), X.shape[0], epochs, batch, lr, seed,
                                     losses.ctypes.data, _current_stream()))
     return losses[:epochs]
+
+
+def louvain_modularity_noalloc(graph, membership, stream=None):
+    """louvain_modularity_of for a DeviceCSR and a CUDA membership tensor,
+    with no allocation inside the library (fixed scratch; see louvain.h).
+    Returns (status, Q, exact numerator, exact denominator)."""
+    gs, keep = _graph_struct(graph)
+    q = ctypes.c_double()
+    num = np.zeros(2, dtype=np.int64)
+    den = np.zeros(2, dtype=np.int64)
+    st = load().louvain_modularity_noalloc(ctypes.byref(gs), ctypes.c_void_p(membership.data_ptr()),
+                                           stream if stream is not None else _current_stream(), ctypes.byref(q),
+                                           num.ctypes.data, den.ctypes.data)
+    del keep
+    return st, q.value, _i128(num), _i128(den)
 
 
 def louvain_model_size() -> int:
