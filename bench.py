@@ -44,6 +44,9 @@ WORKLOADS = {
                      "long-range edges, uniform integer weights 1-8, seed 11"),
     "sbm1000": dict(kind="sbm", n=1000, block=100, p_in=0.1, p_out=0.002, seed=1, desc="planted-partition SBM, "
                     "1,000 vertices in 10 blocks of 100, p_in=0.1, p_out=0.002, seed 1"),
+    "rmat27": dict(kind="rmat", scale=27, ef=16, seed=13, desc="R-MAT scale 27, edge factor 16, "
+                   "(a,b,c,d)=(0.57,0.19,0.19,0.05), symmetrised, deduplicated, no self-loops, unit int32 weights, "
+                   "seed 13 (learned-skip evaluation graph)"),
 }
 # bounded CPU-oracle samples: the same generator at a smaller size.  The
 # CPU-baseline leg of a GPU run times one oracle run of SAMPLES; the reference
@@ -52,6 +55,7 @@ REF_SAMPLES = {
     "rmat24": dict(kind="rmat", scale=20, ef=16, seed=7, desc="R-MAT scale 20 (same generator and parameters)"),
     "grid8192": dict(kind="grid", side=1024, frac=0.02, seed=11, desc="1024x1024 grid (same generator)"),
     "sbm1000": dict(kind="sbm", n=1000, block=100, p_in=0.1, p_out=0.002, seed=1, desc="the full workload"),
+    "rmat27": dict(kind="rmat", scale=20, ef=16, seed=13, desc="R-MAT scale 20 (same generator and parameters)"),
 }
 SAMPLES = {
     "rmat24": dict(kind="rmat", scale=21, ef=16, seed=7, desc="R-MAT scale 21 (same generator and parameters)"),
@@ -166,6 +170,10 @@ def main():
     ap.add_argument("--workload", default="rmat24", choices=sorted(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-skip leg")
+    ap.add_argument("--skip-threshold", type=float, default=0.8)
+    ap.add_argument("--skip-clears", type=int, default=1)
+    ap.add_argument("--learned-fallback", type=int, default=0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -233,6 +241,44 @@ def main():
     st = ctx.stats()
     value = g.nnz * args.steps * world / (ms / 1e3) / 1e6
 
+    # learned-skip leg: the same workload and step count with the predictor
+    learned = None
+    if not args.no_learned:
+        from paper_2501_19004_gb300 import predictor
+        model = predictor.load_default()
+        source = "stored model (R-MAT 20-22 traces)"
+        if model is None:
+            model, _ = predictor.train_default()
+            source = "trained in this run (R-MAT 20-22 traces)"
+        lctx = lv.Louvain(dg, lv.Config(mode=lv.MODE_LEARNED, model=model, skip_threshold=args.skip_threshold,
+                                        learned_skip_clears=args.skip_clears,
+                                        learned_fallback=args.learned_fallback))
+        for _ in range(args.warmup):
+            lctx.run()
+        torch.cuda.synchronize()
+        barrier()
+        l0 = torch.cuda.Event(enable_timing=True)
+        l1 = torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        for _ in range(args.steps):
+            lctx.run()
+        l1.record(stream)
+        torch.cuda.synchronize()
+        lms = l0.elapsed_time(l1)
+        if world > 1:
+            t = torch.tensor([lms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            lms = float(t.item())
+        lres = lctx.result()
+        lst = lctx.stats()
+        lctx.close()
+        learned = {"value": g.nnz * args.steps * world / (lms / 1e3) / 1e6, "unit": UNIT,
+                   "ms_per_step": lms / args.steps, "modularity": lres.modularity,
+                   "dq_vs_plain": lres.modularity - res.modularity, "skip_threshold": args.skip_threshold,
+                   "skip_clears": args.skip_clears, "fallback": args.learned_fallback,
+                   "evaluated": lst["evaluated"], "evaluated_plain": st["evaluated"], "skipped": lst["skipped"],
+                   "passes": lres.passes, "learned_passes": lst.get("learned_passes"), "model": source}
+
     # end to end through the public API from pinned host memory
     e2e = None
     if args.e2e_steps > 0:
@@ -297,6 +343,7 @@ def main():
                        "l2": f"inputs larger than L2 (CSR {(g.offsets.nbytes + g.cols.nbytes) / 1e9:.2f} GB), no flush",
                        "modularity": res.modularity, "communities": res.communities, "passes": res.passes},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+            "learned_skip": learned,
             "phases_ms": {"move": st["move_ms"], "aggregate": st["aggregate_ms"], "other": st["other_ms"]},
             "kernels_ms_warmup": {k: round(v["ms"], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
         }

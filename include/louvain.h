@@ -99,9 +99,17 @@ typedef struct {
                                     samples of evaluated vertices (louvain_traces) */
   float trace_rate;              /* fraction of decisions recorded (hash-sampled) */
   int32_t learned_fallback;      /* LEARNED: after the learned iterations of a pass,
-                                    a full sweep and plain iterations run until
-                                    0: an iteration's dQ <= tau (the plain rule),
-                                    1: an iteration makes no move */
+                                    plain iterations (no skipping) run:
+                                    0: over the flagged vertices (every skipped
+                                       vertex kept its flag) until an iteration's
+                                       dQ <= tau (the plain rule);
+                                    1: first over all vertices, until an iteration
+                                       makes no move;
+                                    2: first over all vertices, until dQ <= tau */
+  int32_t learned_skip_clears;   /* LEARNED: 1 = a skip counts as a decision to stay
+                                    and clears the vertex's flag (it returns when a
+                                    neighbour moves); 0 = skipped vertices keep
+                                    their flag */
 } louvain_config;
 
 /* Fill `cfg` with the defaults above (mode PLAIN, seed 0). */
@@ -165,10 +173,11 @@ louvain_status louvain_modularity_of(const louvain_graph *graph, const int32_t *
  * flagged vertices of a bucket the local-moving phase evaluates: a vertex
  * whose predicted probability of moving is below skip_threshold keeps its
  * flag and is skipped for this iteration.  After the learned iterations of a
- * pass converge, a full plain sweep (every vertex, no skipping) runs, and
- * plain iterations continue until the plain method's tolerance test holds
- * (or, with learned_fallback = 1, until one makes no move); the sweep bounds
- * the modularity gap to the plain method.  Parameters: W1[8][32], b1[32],
+ * pass converge, plain iterations without skipping follow: by default over
+ * the flagged vertices (which include every skipped one) until the plain
+ * method's tolerance test holds; learned_fallback selects a full sweep over
+ * all vertices first, and a zero-move stopping rule.  These sweeps bound the
+ * modularity gap to the plain method.  Parameters: W1[8][32], b1[32],
  * W2[32][32], b2[32], w3[32], b3 (fp32; W[k][n] maps input k to output n);
  * evaluation rounds x, W1, W2, w3 and the hidden ReLU outputs to bf16 and
  * accumulates in fp32 on the tensor cores.  Features per vertex, in order:

@@ -58,6 +58,7 @@ struct LearnArgs {
   uint32_t *marks = nullptr;    // [n] neighbour moves since the last evaluation
   int32_t *cand = nullptr;      // [n] candidates of the bucket
   float thr_logit = 0.f;        // evaluate iff logit >= thr_logit
+  int skip_clears = 0;          // a skip clears the flag (counts as "stay")
   float t_norm = 0.f, p_norm = 0.f;
   float *trace_x = nullptr;     // [cap][8] recorded features
   float *trace_y = nullptr;     // [cap] recorded labels (moved)

@@ -307,6 +307,7 @@ LearnArgs learn_args(louvain_ctx *x, int pass, int t, bool skipping) {
   L.cand = x->cand;
   const double th = std::min(std::max((double)cfg.skip_threshold, 1e-6), 1.0 - 1e-6);
   L.thr_logit = (float)std::log(th / (1.0 - th));
+  L.skip_clears = cfg.learned_skip_clears;
   L.t_norm = (float)t / (float)cfg.max_iterations;
   L.p_norm = (float)pass / (float)std::max(cfg.max_passes, 1);
   if (x->trace_x) {
@@ -343,12 +344,13 @@ louvain_status move_phase(louvain_ctx *x, const GView &g, int wk, int pass, doub
         break;
       }
     }
-    // fallback: a full sweep without the predictor, then plain iterations
-    // until the plain tolerance test holds (or until an iteration makes no
-    // move)
+    // fallback: plain iterations without the predictor over the flagged
+    // vertices (every skipped vertex kept its flag) or, on request, over all
+    // vertices first; until the plain tolerance test holds or, on request,
+    // until an iteration makes no move
     const int learned_iters = t;
     long long last_moves = -1;
-    LV_CK(cudaMemsetAsync(x->flag, 1, (size_t)g.n, x->stream));
+    if (cfg.learned_fallback != 0) LV_CK(cudaMemsetAsync(x->flag, 1, (size_t)g.n, x->stream));
     for (int f = 0; f < cfg.max_iterations; ++f, ++t) {
       const Counters *h;
       louvain_status st = move_iteration(x, g, wk, pass, t, false, &h);
@@ -356,7 +358,7 @@ louvain_status move_phase(louvain_ctx *x, const GView &g, int wk, int pass, doub
       last_moves = (long long)h->it_moves;
       const i128 gain = ((i128)h->it_gain_hi << 32) + (i128)h->it_gain_lo;
       const double total = den2 ? (double)(2 * gain) / (double)den2 : 0.0;
-      if (cfg.learned_fallback ? h->it_moves == 0 : total <= tau) {
+      if (cfg.learned_fallback == 1 ? h->it_moves == 0 : total <= tau) {
         ++t;
         break;
       }
@@ -671,7 +673,7 @@ louvain_status validate_config(const louvain_config *c) {
   if (!(c->tolerance >= 0) || !(c->tolerance_drop > 0) || !(c->aggregation_tolerance >= 0)) return LOUVAIN_E_INVAL;
   if (c->mode != LOUVAIN_MODE_PLAIN && c->mode != LOUVAIN_MODE_LEARNED) return LOUVAIN_E_INVAL;
   if (c->mode == LOUVAIN_MODE_LEARNED && (!c->model || c->max_iterations > 127)) return LOUVAIN_E_INVAL;
-  if (c->trace_capacity < 0) return LOUVAIN_E_INVAL;
+  if (c->trace_capacity < 0 || c->learned_fallback < 0 || c->learned_fallback > 2) return LOUVAIN_E_INVAL;
   return LOUVAIN_OK;
 }
 
@@ -895,6 +897,7 @@ void louvain_config_default(louvain_config *c) {
   c->trace_capacity = 0;
   c->trace_rate = 1.0f;
   c->learned_fallback = 0;
+  c->learned_skip_clears = 0;
 }
 
 louvain_status louvain_create(const louvain_graph *graph, const louvain_config *cfg, void *stream, louvain_ctx **out) {

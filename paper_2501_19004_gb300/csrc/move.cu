@@ -132,6 +132,7 @@ __global__ void __launch_bounds__(256) k_mlp_select(MoveArgs a) {
       ++evaluated;
     } else if (mine >= 0) {
       ++skipped;
+      if (a.learn.skip_clears) a.flag[mine] = 0;
     }
 #pragma unroll
     for (int b = 0; b < kNumBins; ++b) {

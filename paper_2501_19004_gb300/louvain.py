@@ -59,7 +59,7 @@ class LouvainConfig(ctypes.Structure):
                 ("model", ctypes.c_void_p), ("skip_threshold", ctypes.c_float),
                 ("record_pass_modularity", ctypes.c_int32), ("check_symmetry", ctypes.c_int32),
                 ("profile_mask", ctypes.c_uint32), ("trace_capacity", ctypes.c_int64), ("trace_rate", ctypes.c_float),
-                ("learned_fallback", ctypes.c_int32)]
+                ("learned_fallback", ctypes.c_int32), ("learned_skip_clears", ctypes.c_int32)]
 
 
 _lib = None
@@ -144,6 +144,7 @@ class Config:
     trace_capacity: int = 0
     trace_rate: float = 1.0
     learned_fallback: int = 0
+    learned_skip_clears: int = 0
 
     def c(self) -> LouvainConfig:
         self._model_keep = None
@@ -155,7 +156,8 @@ class Config:
                              self.aggregation_tolerance, self.pickless_period, self.buckets,
                              self.schedule_seed & (2**64 - 1), self.mode, mp, self.skip_threshold,
                              int(self.record_pass_modularity), int(self.check_symmetry), self.profile_mask,
-                             self.trace_capacity, self.trace_rate, self.learned_fallback)
+                             self.trace_capacity, self.trace_rate, self.learned_fallback,
+                             self.learned_skip_clears)
 
 
 @dataclass
