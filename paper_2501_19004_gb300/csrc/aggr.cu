@@ -181,8 +181,7 @@ __global__ void __launch_bounds__(256) k_comm_compact(AggArgs a, int64_t n) {
           bin = degree_bin(cd);
           if ((unsigned long long)cd > md) md = (unsigned long long)cd;
           if (bin == kBigBin) {
-            const unsigned long long dk = (unsigned long long)(cd < a.gamma ? cd : a.gamma);
-            big_slots += pow2_at_least(2 * dk);
+            big_slots += big_table_cap((unsigned long long)cd, (unsigned long long)a.gamma);
             big_items += 1;
           }
         }

@@ -34,8 +34,20 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 enum { MODE_MOVE = 0, MODE_MERGE = 1 };
 
 __device__ __forceinline__ uint32_t table_cap(int64_t tot, int64_t keyspace) {
-  const uint64_t d = (uint64_t)(tot < keyspace ? tot : keyspace);
-  return pow2_at_least(2 * (d ? d : 1));
+  return (uint32_t)big_table_cap((uint64_t)tot, (uint64_t)keyspace);
+}
+
+// Items of round r: [rstart[r], rstart[r + 1]); table offset of item k inside
+// the workspace: toff[k] - r * window.
+struct RoundRange {
+  int64_t k0, k1, base;
+};
+__device__ __forceinline__ RoundRange round_range(const BigArgs &a, int r) {
+  RoundRange rr;
+  rr.k0 = a.ws.rstart[r];
+  rr.k1 = a.ws.rstart[r + 1];
+  rr.base = (int64_t)r * a.window;
+  return rr;
 }
 
 template <int MODE>
@@ -79,35 +91,43 @@ __global__ void __launch_bounds__(1024) k_big_plan(BigArgs a) {
     members = warp_sum_u(members);
     if ((threadIdx.x & 31) == 0 && members) atomicAdd(&a.ctr->mg_work[kBigBin][1], members);
   }
+  // rounds: item k belongs to round toff[k] / window; the host launches
+  // enough rounds for the pass's bound, and the workspace holds the window
+  // plus the largest table
+  const bool fits = c_slots <= (long long)a.rounds * a.window && (MODE == MODE_MERGE || c_ev <= a.ws.parts);
+  __syncthreads();
+  for (int64_t k = threadIdx.x; k <= nb; k += 1024) {
+    const int64_t rk = k < nb ? a.ws.toff[k] / a.window : a.rounds;
+    const int64_t rp = k > 0 ? a.ws.toff[k - 1] / a.window : -1;
+    for (int64_t r = rp + 1; r <= rk && r <= a.rounds; ++r) a.ws.rstart[r] = fits ? k : nb;
+  }
   if (threadIdx.x == 0) {
-    const bool fits = c_slots <= a.ws.slots && (MODE == MODE_MERGE || c_ev <= a.ws.parts);
-    if (!fits) atomicOr(&a.ctr->error, (unsigned long long)ERR_HASH);
+    if (!fits) {
+      atomicOr(&a.ctr->error, (unsigned long long)ERR_HASH);
+      for (int r = 0; r <= a.rounds; ++r) a.ws.rstart[r] = nb;  // nothing runs
+    }
     a.ws.toff[nb] = c_slots;
-    a.ws.cpre[nb] = fits ? c_ch : 0;
-    a.ws.epre[nb] = (fits && MODE == MODE_MOVE) ? c_ev : 0;
+    a.ws.cpre[nb] = c_ch;
+    a.ws.epre[nb] = MODE == MODE_MOVE ? c_ev : 0;
     if (MODE == MODE_MERGE) atomicAdd(&a.ctr->mg_work[kBigBin][0], (unsigned long long)nb);
   }
 }
 
-// Evaluation slices: kBigEvalSlots occupied slots each (one block).
-__global__ void __launch_bounds__(1024) k_big_plan2(BigArgs a) {
+// Emission slices of round r (aggregation): kBigEvalSlots occupied slots
+// each, a prefix over the round's items stored in epre[k0 .. k1].
+__global__ void __launch_bounds__(1024) k_big_plan2(BigArgs a, int r) {
   __shared__ long long sc[33];
-  const int64_t nb = (int64_t)*a.count;
-  if (a.ws.cpre[nb] == 0) return;  // nothing was accumulated
+  const RoundRange rr = round_range(a, r);
   long long c_ev = 0;
-  for (int64_t base = 0; base < nb; base += 1024) {
+  for (int64_t base = rr.k0; base < rr.k1; base += 1024) {
     const int64_t k = base + threadIdx.x;
-    const long long nev = k < nb ? (long long)((a.ws.ocnt[k] + kBigEvalSlots - 1) / kBigEvalSlots) : 0;
+    const long long nev = k < rr.k1 ? (long long)((a.ws.ocnt[k] + kBigEvalSlots - 1) / kBigEvalSlots) : 0;
     long long t;
     const long long e = block_scan_ex<1024>(nev, sc, &t);
-    if (k < nb) a.ws.epre[k] = c_ev + e;
+    if (k < rr.k1) a.ws.epre[k] = c_ev + e;
     c_ev += t;
   }
-  if (threadIdx.x == 0) {
-    const bool fits = c_ev <= a.ws.parts;
-    if (!fits) atomicOr(&a.ctr->error, (unsigned long long)ERR_HASH);
-    a.ws.epre[nb] = fits ? c_ev : 0;
-  }
+  if (threadIdx.x == 0) a.ws.epre[rr.k1] = c_ev;  // total of the round
 }
 
 // Gather kRun entries of an item's entry sequence below xe: positions x,
@@ -169,20 +189,20 @@ __device__ __forceinline__ void gather_item(const BigArgs &a, int32_t it, int64_
 }
 
 template <int MODE, int WK>
-__global__ void __launch_bounds__(kNT) k_big_accum(BigArgs a) {
+__global__ void __launch_bounds__(kNT) k_big_accum(BigArgs a, int r) {
   extern __shared__ uint32_t dyn[];
   int32_t *skeys = (int32_t *)dyn;
   uint32_t *svals = dyn + kBigSmemSlots;
-  const int64_t nb = (int64_t)*a.count;
-  const int64_t total = a.ws.cpre[nb];
+  const RoundRange rr = round_range(a, r);
+  const int64_t g0 = a.ws.cpre[rr.k0], g1 = a.ws.cpre[rr.k1];
   unsigned long long entries = 0;
   for (int s = threadIdx.x; s < kBigSmemSlots; s += kNT) {
     skeys[s] = kEmpty;
     svals[s] = 0;
   }
   __syncthreads();
-  for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
-    const int64_t k = upper_index(a.ws.cpre, nb, g);
+  for (int64_t g = g0 + blockIdx.x; g < g1; g += gridDim.x) {
+    const int64_t k = rr.k0 + upper_index(a.ws.cpre + rr.k0, rr.k1 - rr.k0, g);
     const int32_t it = a.items[k];
     const int64_t tot = a.ws.tot[k];
     const int64_t x0 = (g - a.ws.cpre[k]) * kBigChunk;
@@ -199,8 +219,8 @@ __global__ void __launch_bounds__(kNT) k_big_accum(BigArgs a) {
 #pragma unroll
     for (int u = 0; u < kRun; ++u) warp_insert_sm(skeys, svals, kBigSmemSlots - 1, kk[u], ww[u], a.ctr);
     __syncthreads();
-    const int64_t toff = a.ws.toff[k];
-    const uint32_t gmask = table_cap(tot, a.keyspace) - 1;
+    const int64_t toff = a.ws.toff[k] - rr.base;
+    const uint32_t gcap = table_cap(tot, a.keyspace);
     // every warp takes 32 consecutive slots per round; when aggregating,
     // slots claimed in the global table are appended to the item's list with
     // one atomic per warp (evaluation then visits occupied slots only)
@@ -208,8 +228,8 @@ __global__ void __launch_bounds__(kNT) k_big_accum(BigArgs a) {
       const int32_t key = skeys[s];
       int64_t slot = -1;
       if (key != kEmpty) {
-        if (MODE == MODE_MERGE) slot = gm_insert_claim(a.ws.keys + toff, a.ws.vals + toff, gmask, key, svals[s], a.ctr);
-        else gm_insert(a.ws.keys + toff, a.ws.vals + toff, gmask, key, svals[s], a.ctr);
+        if (MODE == MODE_MERGE) slot = gm_insert_claim(a.ws.keys + toff, a.ws.vals + toff, gcap, key, svals[s], a.ctr);
+        else gm_insert(a.ws.keys + toff, a.ws.vals + toff, gcap, key, svals[s], a.ctr);
         skeys[s] = kEmpty;
         svals[s] = 0;
       }
@@ -232,18 +252,18 @@ __global__ void __launch_bounds__(kNT) k_big_accum(BigArgs a) {
 // Moving: per table slice, the best candidate (score, then lowest id) and the
 // weight to the vertex's own community; slots are cleared.  Hub tables are
 // at least a quarter full, so slices are scanned sequentially.
-__global__ void __launch_bounds__(kNT) k_big_eval(BigArgs a) {
-  const int64_t nb = (int64_t)*a.count;
-  const int64_t total = a.ws.epre[nb];
+__global__ void __launch_bounds__(kNT) k_big_eval(BigArgs a, int r) {
+  const RoundRange rr = round_range(a, r);
+  const int64_t g0 = a.ws.epre[rr.k0], g1 = a.ws.epre[rr.k1];
   unsigned long long distinct = 0;
-  for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
-    const int64_t k = upper_index(a.ws.epre, nb, g);
+  for (int64_t g = g0 + blockIdx.x; g < g1; g += gridDim.x) {
+    const int64_t k = rr.k0 + upper_index(a.ws.epre + rr.k0, rr.k1 - rr.k0, g);
     const int32_t i = a.items[k];
     const int64_t cap = table_cap(a.ws.tot[k], a.keyspace);
     const int64_t s0 = (g - a.ws.epre[k]) * kBigEvalSlots;
     const int64_t s1 = s0 + kBigEvalSlots < cap ? s0 + kBigEvalSlots : cap;
-    int32_t *keys = a.ws.keys + a.ws.toff[k];
-    uint32_t *vals = a.ws.vals + a.ws.toff[k];
+    int32_t *keys = a.ws.keys + (a.ws.toff[k] - rr.base);
+    uint32_t *vals = a.ws.vals + (a.ws.toff[k] - rr.base);
     const int32_t d = a.Cp[i];
     const long long Ki = a.K[i];
     long long best_s = LLONG_MIN, Kid = 0;
@@ -278,13 +298,12 @@ __global__ void __launch_bounds__(kNT) k_big_eval(BigArgs a) {
 
 // Moving: one block per hub reduces its slices and applies Algorithm 5's
 // decision; movers re-mark their neighbours.
-__global__ void __launch_bounds__(kNT) k_big_decide(BigArgs a) {
+__global__ void __launch_bounds__(kNT) k_big_decide(BigArgs a, int r) {
   __shared__ int32_t s_target;
-  const int64_t nb = (int64_t)*a.count;
-  if (a.ws.cpre[nb] == 0 && nb > 0) return;  // plan found no room (error already set)
+  const RoundRange rr = round_range(a, r);
   unsigned long long glo = 0, ghi = 0, gm = 0;
   unsigned long long work[3] = {0, 0, 0};  // vertices, movers, mover entries
-  for (int64_t k = blockIdx.x; k < nb; k += gridDim.x) {
+  for (int64_t k = rr.k0 + blockIdx.x; k < rr.k1; k += gridDim.x) {
     const int32_t i = a.items[k];
     long long best_s = LLONG_MIN, Kid = 0;
     int32_t best_c = INT_MAX;
@@ -335,18 +354,18 @@ __global__ void __launch_bounds__(kNT) k_big_decide(BigArgs a) {
 
 // Aggregation: append every occupied slot of a slice to the community's row
 // (super-edge (c, key, weight)); slots are cleared.
-__global__ void __launch_bounds__(kNT) k_big_emit(BigArgs a) {
+__global__ void __launch_bounds__(kNT) k_big_emit(BigArgs a, int r) {
   __shared__ unsigned long long s_base;
-  const int64_t nb = (int64_t)*a.count;
-  const int64_t total = a.ws.epre[nb];
+  const RoundRange rr = round_range(a, r);
+  const int64_t total = a.ws.epre[rr.k1];  // round-local prefix (k_big_plan2)
   unsigned long long written = 0;
   for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
-    const int64_t k = upper_index(a.ws.epre, nb, g);
+    const int64_t k = rr.k0 + upper_index(a.ws.epre + rr.k0, rr.k1 - rr.k0, g);
     const int32_t c = a.items[k];
     const int64_t nocc = (int64_t)a.ws.ocnt[k];
     const int64_t p0 = (g - a.ws.epre[k]) * kBigEvalSlots;
     const int64_t p1 = p0 + kBigEvalSlots < nocc ? p0 + kBigEvalSlots : nocc;
-    const int64_t toff = a.ws.toff[k];
+    const int64_t toff = a.ws.toff[k] - rr.base;
     int32_t *keys = a.ws.keys + toff;
     uint32_t *vals = a.ws.vals + toff;
     const int32_t *occ = a.ws.occ + toff / 2;
@@ -384,16 +403,18 @@ void big_run(const BigArgs &b, int num_sms, cudaStream_t s, KernelProf *prof) {
   if (prof) prof->begin(k_rest, s);
   LV_LAUNCH(k_big_plan<MODE><<<1, 1024, 0, s>>>(b));
   if (prof) prof->end(k_rest, s);
-  LV_TIMED(prof, k_acc, s, k_big_accum<MODE, WK><<<num_sms * 3, kNT, kSmem, s>>>(b));
-  if (prof) prof->begin(k_rest, s);
-  if (MODE == MODE_MERGE) LV_LAUNCH(k_big_plan2<<<1, 1024, 0, s>>>(b));
-  if (MODE == MODE_MOVE) {
-    LV_LAUNCH(k_big_eval<<<num_sms * 3, kNT, 0, s>>>(b));
-    LV_LAUNCH(k_big_decide<<<num_sms * 2, kNT, 0, s>>>(b));
-  } else {
-    LV_LAUNCH(k_big_emit<<<num_sms * 3, kNT, 0, s>>>(b));
+  for (int r = 0; r < b.rounds; ++r) {
+    LV_TIMED(prof, k_acc, s, k_big_accum<MODE, WK><<<num_sms * 3, kNT, kSmem, s>>>(b, r));
+    if (prof) prof->begin(k_rest, s);
+    if (MODE == MODE_MERGE) LV_LAUNCH(k_big_plan2<<<1, 1024, 0, s>>>(b, r));
+    if (MODE == MODE_MOVE) {
+      LV_LAUNCH(k_big_eval<<<num_sms * 3, kNT, 0, s>>>(b, r));
+      LV_LAUNCH(k_big_decide<<<num_sms * 2, kNT, 0, s>>>(b, r));
+    } else {
+      LV_LAUNCH(k_big_emit<<<num_sms * 3, kNT, 0, s>>>(b, r));
+    }
+    if (prof) prof->end(k_rest, s);
   }
-  if (prof) prof->end(k_rest, s);
 }
 
 }  // namespace

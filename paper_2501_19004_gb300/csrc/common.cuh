@@ -89,6 +89,24 @@ __device__ __forceinline__ uint32_t slot_of(int32_t key, uint32_t mask) {
   return (h ^ (h >> 15)) & mask;
 }
 
+// Capacity of a big item's global table: twice the keys it can hold (its
+// entries, at most the number of possible keys), rounded up to 64 slots.
+__host__ __device__ __forceinline__ uint64_t big_table_cap(uint64_t tot, uint64_t keyspace) {
+  uint64_t d = tot < keyspace ? tot : keyspace;
+  if (d == 0) d = 1;
+  return (2 * d + 63) & ~63ull;
+}
+
+// Hash of a community id onto [0, cap) for tables of any size
+// (multiply-shift range reduction of a mixed 32-bit hash).
+__device__ __forceinline__ uint32_t slot_in_range(int32_t key, uint32_t cap) {
+  uint32_t h = (uint32_t)key * 0x9E3779B1u;
+  h ^= h >> 15;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  return (uint32_t)(((unsigned long long)h * cap) >> 32);
+}
+
 // (score, id) pair ordering of the argmax: larger score first, then lower id.
 __device__ __forceinline__ bool better(long long s1, int32_t c1, long long s2, int32_t c2) {
   return s1 > s2 || (s1 == s2 && c1 < c2);

@@ -47,7 +47,13 @@ struct BigWs {
   unsigned long long *part_kid = nullptr;
   int64_t parts = 0;                  // capacity of part_*
   int64_t item_cap = 0;               // capacity of tot/toff/cpre/epre
+  int64_t *rstart = nullptr;          // [kMaxBigRounds + 1] first item of every round
 };
+// Items whose tables do not fit the workspace at once are processed in
+// rounds: round r takes the items whose global table offset lies in
+// [r * window, (r + 1) * window); the workspace holds window + the largest
+// table, so every item of a round fits.
+constexpr int kMaxBigRounds = 8;
 
 // Learned vertex-activity predictor and trace recorder (see mlp.cu).
 struct LearnArgs {
@@ -74,6 +80,8 @@ struct BigArgs {
   const unsigned long long *count;    // its length (device)
   int64_t keyspace;                   // number of possible keys: n' or |Gamma|
   BigWs ws;
+  int64_t window = 0;                 // table slots per round
+  int rounds = 1;                     // rounds to launch
   Counters *ctr;
   // local moving
   const int64_t *K;

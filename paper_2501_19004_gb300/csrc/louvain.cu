@@ -100,6 +100,8 @@ struct louvain_ctx {
   double kbytes[K_NUM_KERNELS] = {};
   int cur_wbytes = 0;
   bool pass_has_hubs = false;
+  int64_t hub_window = 0;
+  int hub_rounds = 0;
 };
 
 namespace {
@@ -224,21 +226,41 @@ louvain_status ensure_big(louvain_ctx *x, int64_t slots, int64_t parts, int64_t 
     dfree(x, b.cpre);
     dfree(x, b.epre);
     dfree(x, b.ocnt);
+    dfree(x, b.rstart);
     const int64_t want = items + items / 4 + 64;
     if ((st = dalloc_n(x, &b.tot, want + 1)) || (st = dalloc_n(x, &b.toff, want + 1)) ||
         (st = dalloc_n(x, &b.cpre, want + 1)) || (st = dalloc_n(x, &b.epre, want + 1)) ||
-        (st = dalloc_n(x, &b.ocnt, want + 1)))
+        (st = dalloc_n(x, &b.ocnt, want + 1)) || (st = dalloc_n(x, &b.rstart, (int64_t)kMaxBigRounds + 2)))
       return st;
     b.item_cap = want;
   }
   return LOUVAIN_OK;
 }
 
-// Workspace for the big items counted in ctr->big_slots / big_items.
-louvain_status ensure_big_for(louvain_ctx *x, const Counters &h) {
+// Workspace for the big items counted in ctr->big_slots / big_items (their
+// tables' total size, a bound for every bucket), largest item `maxdeg` over
+// `keyspace` keys: tables go through a window of about half the total per
+// round (a bucket holds about 1/B of the pass's items), so the workspace is
+// window + the largest table.
+louvain_status ensure_big_for(louvain_ctx *x, const Counters &h, uint64_t maxdeg, uint64_t keyspace, int64_t *window,
+                              int *rounds) {
+  *window = 0;
+  *rounds = 0;
   if (h.big_items == 0) return LOUVAIN_OK;
-  const int64_t slots = (int64_t)h.big_slots;
-  return ensure_big(x, slots, slots / kBigEvalSlots + (int64_t)h.big_items + 1, (int64_t)h.big_items + 1);
+  const int64_t total = (int64_t)h.big_slots;
+  const int64_t maxcap = (int64_t)big_table_cap(maxdeg, keyspace);
+  int64_t w = ((total + 1) / 2 + 63) & ~63ll;
+  if (w < maxcap) w = maxcap;
+  int r = (int)((total + w - 1) / w);
+  if (r > kMaxBigRounds) {
+    w = ((total + kMaxBigRounds - 1) / kMaxBigRounds + 63) & ~63ll;
+    if (w < maxcap) w = maxcap;
+    r = (int)((total + w - 1) / w);
+  }
+  if (r < 1) r = 1;
+  *window = w;
+  *rounds = r;
+  return ensure_big(x, w + maxcap, total / kBigEvalSlots + (int64_t)h.big_items + 1, (int64_t)h.big_items + 1);
 }
 
 louvain_status read_counters(louvain_ctx *x) {
@@ -415,6 +437,8 @@ louvain_status move_iteration(louvain_ctx *x, const GView &g, int wk, int pass, 
     big.count = &x->d_ctr->bin_count[kBigBin];
     big.keyspace = g.n;
     big.ws = x->big;
+    big.window = x->hub_window;
+    big.rounds = x->hub_rounds;
     if (!x->pass_has_hubs) big.ws.slots = 0;
     big.ctr = x->d_ctr;
     big.K = x->K;
@@ -514,7 +538,8 @@ louvain_status run_impl(louvain_ctx *x) {
     LV_CK(cudaGetLastError());
     if ((st = read_counters(x))) return st;
     x->pass_has_hubs = x->h_ctr->big_items > 0;
-    if ((st = ensure_big_for(x, *x->h_ctr))) return st;
+    if ((st = ensure_big_for(x, *x->h_ctr, x->h_ctr->maxdeg, (uint64_t)g.n, &x->hub_window, &x->hub_rounds)))
+      return st;
     int li = 0;
     if ((st = move_phase(x, g, wk, p, tau, &li))) return st;
     have_pass_state = true;
@@ -583,7 +608,11 @@ louvain_status run_impl(louvain_ctx *x) {
     x->prof.end(K_DENDRO, s);
     LV_CK(cudaGetLastError());
     if ((st = read_counters(x))) return st;
-    if ((st = ensure_big_for(x, *x->h_ctr))) return st;
+    int64_t mwindow = 0;
+    int mrounds = 0;
+    if ((st = ensure_big_for(x, *x->h_ctr, x->h_ctr->maxdeg, (uint64_t)gamma, &mwindow, &mrounds))) return st;
+    aa.big.window = mwindow;
+    aa.big.rounds = mrounds;
     aa.big.g = g;
     aa.big.Cp = x->Cp;
     aa.big.items = x->bins[kBigBin];

@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(256) k_pass_init(GView g, int first_pass, int6
     const unsigned long long deg = (unsigned long long)(e - b);
     if (deg > md) md = deg;
     if (degree_bin((int64_t)deg) == kBigBin) {
-      big_slots += pow2_at_least(2 * (deg < (unsigned long long)g.n ? deg : (unsigned long long)g.n));
+      big_slots += big_table_cap(deg, (unsigned long long)g.n);
       big_items += 1;
     }
     long long k;

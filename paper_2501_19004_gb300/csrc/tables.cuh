@@ -30,10 +30,11 @@ __device__ __forceinline__ void sm_insert(int32_t *keys, uint32_t *vals, uint32_
   atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
 }
 
-__device__ __forceinline__ void gm_insert(int32_t *keys, uint32_t *vals, uint32_t mask, int32_t key, uint32_t w,
+// Global tables have any capacity `cap` (see big_table_cap).
+__device__ __forceinline__ void gm_insert(int32_t *keys, uint32_t *vals, uint32_t cap, int32_t key, uint32_t w,
                                           Counters *ctr) {
-  uint32_t s = slot_of(key, mask);
-  for (uint32_t t = 0; t <= mask; ++t) {
+  uint32_t s = slot_in_range(key, cap);
+  for (uint32_t t = 0; t < cap; ++t) {
     int32_t k = __ldcg(keys + s);
     if (k == kEmpty) {
       k = atomicCAS(keys + s, kEmpty, key);
@@ -43,17 +44,17 @@ __device__ __forceinline__ void gm_insert(int32_t *keys, uint32_t *vals, uint32_
       atomicAdd(vals + s, w);
       return;
     }
-    s = (s + 1) & mask;
+    s = (s + 1 == cap) ? 0u : s + 1;
   }
   atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
 }
 
 // Global insert that reports the slot it claimed for a new key (-1 when the
 // key was already present), so that callers can list the occupied slots.
-__device__ __forceinline__ int64_t gm_insert_claim(int32_t *keys, uint32_t *vals, uint32_t mask, int32_t key,
+__device__ __forceinline__ int64_t gm_insert_claim(int32_t *keys, uint32_t *vals, uint32_t cap, int32_t key,
                                                    uint32_t w, Counters *ctr) {
-  uint32_t s = slot_of(key, mask);
-  for (uint32_t t = 0; t <= mask; ++t) {
+  uint32_t s = slot_in_range(key, cap);
+  for (uint32_t t = 0; t < cap; ++t) {
     int32_t k = __ldcg(keys + s);
     bool claimed = false;
     if (k == kEmpty) {
@@ -67,7 +68,7 @@ __device__ __forceinline__ int64_t gm_insert_claim(int32_t *keys, uint32_t *vals
       atomicAdd(vals + s, w);
       return claimed ? (int64_t)s : -1;
     }
-    s = (s + 1) & mask;
+    s = (s + 1 == cap) ? 0u : s + 1;
   }
   atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
   return -1;

@@ -84,6 +84,15 @@ def test_plain_bit_exact_across_settings(cfg):
     assert_same(res, ref)
 
 
+@pytest.mark.parametrize("buckets", [1, 2])
+def test_hub_rounds_bit_exact(buckets):
+    """With one or two buckets a bucket holds more than half of the pass's hub
+    tables, so the hub path runs in several rounds."""
+    g = gg.rmat(16, 16, seed=11)
+    res, ref = run_both(g, lv.Config(buckets=buckets))
+    assert_same(res, ref)
+
+
 def test_host_and_device_inputs_agree_and_runs_repeat():
     g = gg.rmat(13, 16, seed=5)
     a, ref = run_both(g, device_input=False)
