@@ -201,6 +201,34 @@ louvain_status louvain_modularity_of(const louvain_graph *graph, const int32_t *
 louvain_status louvain_modularity_noalloc(const louvain_graph *graph, const int32_t *membership, void *stream,
                                           double *q, int64_t *num_hi_lo, int64_t *den_hi_lo);
 
+/* ---- Batched runs: many independent graphs in one context.  The paper runs
+ * one graph at a time and names the small, shrinking graphs of late passes
+ * as the cause of nu-Louvain's lost parallelism (Sec. 5.2); a batch runs all graphs'
+ * passes together, so every launch covers the vertices of every graph still
+ * running.  Each graph gets exactly the result of its own run with the same
+ * config: its own 2m (Eq. 2), its own iteration tolerance test, convergence
+ * test (l_i <= 1) and aggregation tolerance test (Sec. 4.1.4, 4.1.5), and the
+ * bucket schedule over its local vertex ids.
+ *
+ * `graph` is the union: graph g owns the vertices [vertex_offsets[g],
+ * vertex_offsets[g+1]) (host array of num_graphs + 1 int64, 0 first, n last,
+ * non-decreasing; empty graphs allowed), columns are union ids, and no entry
+ * may leave its graph (LOUVAIN_E_INVAL).  Each graph's 2m must be below 2^32
+ * (LOUVAIN_E_OVERFLOW); the union's may be larger.  The config must be the
+ * plain mode without traces.  louvain_run runs the batch, louvain_memberships
+ * returns, for every union vertex, its community's dense id within its own
+ * graph, and louvain_modularity is refused (LOUVAIN_E_INVAL): per-graph
+ * results come from louvain_batch_results. */
+louvain_status louvain_create_batched(const louvain_graph *graph, const int64_t *vertex_offsets, int64_t num_graphs,
+                                      const louvain_config *cfg, void *stream, louvain_ctx **out);
+
+/* Per-graph results of the last batched run (host arrays, any may be NULL):
+ * results[num_graphs][8] in the layout of louvain_records' summary (passes,
+ * |Gamma|, Qnum hi/lo, Qden hi/lo, 2m, exit reason); q[num_graphs];
+ * pass_records[num_graphs][max_passes][3] = (n', l_i, |Gamma|) of each pass
+ * the graph ran.  LOUVAIN_E_INVAL on a context that is not batched. */
+louvain_status louvain_batch_results(const louvain_ctx *ctx, int64_t *results, double *q, int64_t *pass_records);
+
 /* Number of floats of the learned predictor's parameters (8->32->32->1 MLP). */
 int64_t louvain_model_size(void);
 

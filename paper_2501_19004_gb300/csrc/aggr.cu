@@ -29,8 +29,9 @@ __global__ void __launch_bounds__(256) k_comm_count(GView g, const int32_t *Cp, 
   const int lane = threadIdx.x & 31;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < g.n; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = base + threadIdx.x;
-    const bool ok = i < g.n;
+    bool ok = i < g.n;
     const int32_t c = ok ? Cp[i] : -1;
+    ok = ok && c >= 0;  // C' < 0: a vertex of a finished graph of a batch
     const unsigned long long deg = ok ? (unsigned long long)(g.end[i] - g.begin[i]) : 0ull;
     const unsigned peers = __match_any_sync(kFull, c);
     unsigned long long sum = 0;
@@ -140,8 +141,8 @@ __global__ void __launch_bounds__(256) k_comm_scatter(int64_t n, int32_t *Cp, un
   const int lane = threadIdx.x & 31;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = base + threadIdx.x;
-    const bool ok = i < n;
-    const int32_t c = ok ? Cp[i] : -1;
+    const int32_t c = i < n ? Cp[i] : -1;
+    const bool ok = c >= 0;  // C' < 0: a vertex of a finished graph of a batch
     const unsigned peers = __match_any_sync(kFull, c);
     const int leader = __ffs(peers) - 1;
     unsigned long long top = 0;
@@ -215,16 +216,25 @@ __global__ void __launch_bounds__(256) k_comm_compact(AggArgs a, int64_t n) {
 
 // Degree of every member in community-vertex CSR order (input of the
 // member-degree prefix that locates entries of a community's member rows).
-__global__ void k_member_deg(GView g, const int32_t *members, unsigned long long *mdeg) {
+// Only the first coff[n] slots hold members (fewer than n when vertices of
+// finished graphs of a batch have left); the rest are zero.
+__global__ void k_member_deg(GView g, const int32_t *members, const int64_t *coff, unsigned long long *mdeg) {
+  const int64_t count = coff[g.n];
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < g.n; t += (int64_t)gridDim.x * blockDim.x) {
+    if (t >= count) {
+      mdeg[t] = 0;
+      continue;
+    }
     const int32_t v = members[t];
     mdeg[t] = (unsigned long long)(g.end[v] - g.begin[v]);
   }
 }
 
 __global__ void k_dendro(int32_t *C, const int32_t *Cp, int64_t n) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-    C[v] = Cp[C[v]];
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = C[v];
+    if (x >= 0) C[v] = Cp[x];  // C < 0: frozen (a finished graph of a batch)
+  }
 }
 
 // --------------------------------------------------------------- merge
@@ -544,7 +554,7 @@ void agg_scatter_compact(const AggArgs &a, int num_sms, cudaStream_t s) {
   LV_LAUNCH(k_comm_compact<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(a, n));
   // member-degree prefix in community-vertex CSR order (mprefix[t] of the
   // first member of a community equals its row offset hoff)
-  LV_LAUNCH(k_member_deg<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(a.g, a.members, a.cdeg));
+  LV_LAUNCH(k_member_deg<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(a.g, a.members, a.coff, a.cdeg));
   scan_u64(a.cdeg, a.mprefix, n, 0, a.scan_tmp, &a.ctr->scan_total[3], s);
 }
 

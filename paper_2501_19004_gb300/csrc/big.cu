@@ -266,6 +266,7 @@ __global__ void __launch_bounds__(kNT) k_big_eval(BigArgs a, int r) {
     uint32_t *vals = a.ws.vals + (a.ws.toff[k] - rr.base);
     const int32_t d = a.Cp[i];
     const long long Ki = a.K[i];
+    const long long tm = vertex_two_m(a.batch, a.two_m, i);
     long long best_s = LLONG_MIN, Kid = 0;
     int32_t best_c = INT_MAX;
     for (int64_t s = s0 + threadIdx.x; s < s1; s += kNT) {
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(kNT) k_big_eval(BigArgs a, int r) {
         continue;
       }
       ++distinct;
-      const long long sc = a.two_m * v - Ki * a.Sigma[c];
+      const long long sc = tm * v - Ki * a.Sigma[c];
       if (better(sc, c, best_s, best_c)) {
         best_s = sc;
         best_c = c;
@@ -321,9 +322,10 @@ __global__ void __launch_bounds__(kNT) k_big_decide(BigArgs a, int r) {
     if (threadIdx.x == 0) {
       const int32_t d = a.Cp[i];
       long long s_d = 0;
-      const int32_t t =
-          finish_decision(a.two_m, a.Sigma, a.pickless, d, a.K[i], Kid, best_s, best_c, glo, ghi, gm, &s_d);
+      const long long tm = vertex_two_m(a.batch, a.two_m, i);
+      const int32_t t = finish_decision(tm, a.Sigma, a.pickless, d, a.K[i], Kid, best_s, best_c, glo, ghi, gm, &s_d);
       learn_record(a.learn, a.ctr, a.g, a.Cp, a.Sigma, a.two_m, i, a.K[i], Kid, best_s, best_c, s_d, t >= 0);
+      if (t >= 0) batch_gain(a.batch, i, best_s, s_d);
       work[0] += 1;
       if (t >= 0) {
         work[1] += 1;

@@ -55,6 +55,31 @@ struct BigWs {
 // table, so every item of a round fits.
 constexpr int kMaxBigRounds = 8;
 
+// Batched runs: many graphs as one union graph whose vertex ranges are the
+// graphs (see batch.cu).  Null gid means a single graph.
+struct BatchView {
+  const int32_t *gid = nullptr;            // [n'] graph of each vertex
+  const int64_t *vo = nullptr;             // [G+1] first vertex of each graph in the union
+  const long long *two_m = nullptr;        // [G] total weight of each graph
+  const int8_t *moving = nullptr;          // [G] 1 while the graph's moving phase runs
+  unsigned long long *gain_lo = nullptr;   // [G] per-graph gain sums (low / high halves) and moves
+  unsigned long long *gain_hi = nullptr;
+  unsigned long long *moves = nullptr;
+};
+
+// 2m of vertex i's graph, and per-graph gain bookkeeping for a move.
+__device__ __forceinline__ long long vertex_two_m(const BatchView &b, long long two_m, int32_t i) {
+  return b.gid ? b.two_m[b.gid[i]] : two_m;
+}
+__device__ __forceinline__ void batch_gain(const BatchView &b, int32_t i, long long best_s, long long s_d) {
+  if (!b.gid) return;
+  const int32_t g = b.gid[i];
+  const unsigned long long gain = (unsigned long long)best_s - (unsigned long long)s_d;
+  atomicAdd(b.gain_lo + g, gain & 0xFFFFFFFFull);
+  atomicAdd(b.gain_hi + g, gain >> 32);
+  atomicAdd(b.moves + g, 1ull);
+}
+
 // Learned vertex-activity predictor and trace recorder (see mlp.cu).
 struct LearnArgs {
   int enabled = 0;              // the predictor may skip flagged vertices
@@ -92,6 +117,7 @@ struct BigArgs {
   int32_t *mv_vertex;
   int32_t *mv_target;
   LearnArgs learn;
+  BatchView batch;
   // aggregation
   const int64_t *mprefix;             // member-degree exclusive prefix (community-vertex CSR order)
   const int64_t *kcoff;
@@ -134,6 +160,7 @@ struct MoveArgs {
   int32_t *mv_target;
   Counters *ctr;
   LearnArgs learn;
+  BatchView batch;
 };
 
 // Kernel identifiers for the optional per-kernel event timing.
@@ -249,6 +276,18 @@ void mlp_gather_batch(const float *X, const float *Y, int64_t n, int64_t start, 
                       float *Xb, float *Yb, cudaStream_t s);
 
 size_t scan_tmp_elems(int64_t n);
+
+// batched runs (batch.cu)
+void batch_gid(const int64_t *vo, int64_t G, int64_t n, int32_t *gid, int num_sms, cudaStream_t s);
+void batch_check(const GView &g, int wkind, const int32_t *gid, const int64_t *vo, long long *two_m, Counters *ctr,
+                 int num_sms, cudaStream_t s);
+void batch_modularity(const GView &g, int wkind, const int32_t *gid, const int32_t *memb, const int64_t *sigma,
+                      const int8_t *sel, unsigned long long *sin, unsigned long long *lo, unsigned long long *hi,
+                      int num_sms, cudaStream_t s);
+void batch_gather(const int64_t *src, const int64_t *idx, int64_t m, int64_t *out, cudaStream_t s);
+void batch_final(int64_t n0, int32_t *C, const int32_t *ogid, const int32_t *Cp, const int64_t *newid,
+                 const int64_t *vo, const int8_t *fin, int32_t *out, int num_sms, cudaStream_t s);
+void batch_exclude(int64_t n, const int32_t *gid, const int8_t *fin, int32_t *Cp, int num_sms, cudaStream_t s);
 
 // Kernel launches issued by this thread since the last reset (the library's
 // own kernels only; memsets and copies are not counted).

@@ -102,6 +102,25 @@ struct louvain_ctx {
   bool pass_has_hubs = false;
   int64_t hub_window = 0;
   int hub_rounds = 0;
+
+  // batched runs: G graphs as one union graph (batch.cu)
+  bool batched = false;
+  int64_t G = 0;
+  std::vector<int64_t> vo0;             // [G+1] vertex offsets of the input union
+  std::vector<long long> gtwo_m;        // [G] 2m of each graph
+  BatchView bview;                      // device view (gid == nullptr for a single graph)
+  int32_t *b_gid = nullptr, *b_ogid = nullptr, *b_out = nullptr;
+  int64_t *b_vo = nullptr, *b_bound = nullptr;
+  long long *b_two_m = nullptr;
+  int8_t *b_moving = nullptr, *b_sel = nullptr;
+  unsigned long long *b_acc = nullptr;  // [6][G]: gain lo, gain hi, moves, S_in, Sigma^2 lo, Sigma^2 hi
+  unsigned long long *h_acc = nullptr;  // pinned copies
+  int64_t *h_bound = nullptr;
+  int8_t *h_flags = nullptr;
+  std::vector<int64_t> b_results;       // [G][8]: passes, communities, Q num (hi, lo), Q den (hi, lo), 2m, exit
+  std::vector<double> b_q;              // [G]
+  std::vector<int64_t> b_passes;        // [G][max_passes][3]: n', l_i, |Gamma|
+  std::vector<void *> pinned;           // pinned host buffers (freed by destroy)
 };
 
 namespace {
@@ -415,6 +434,7 @@ louvain_status move_iteration(louvain_ctx *x, const GView &g, int wk, int pass, 
     const LearnArgs L = learn_args(x, pass, t, skipping && t > 0);
     const int pickless = rho > 0 && ((t + rho / 2) % rho) == 0;
     LV_CK(cudaMemsetAsync(&x->d_ctr->it_gain_lo, 0, kIterCounterWords * sizeof(unsigned long long), x->stream));
+    if (x->batched) LV_CK(cudaMemsetAsync(x->b_acc, 0, 3 * (size_t)x->G * sizeof(unsigned long long), x->stream));
     MoveArgs a{};
     a.g = g;
     a.Cp = x->Cp;
@@ -430,6 +450,7 @@ louvain_status move_iteration(louvain_ctx *x, const GView &g, int wk, int pass, 
     a.mv_target = x->mv_target;
     a.ctr = x->d_ctr;
     a.learn = L;
+    a.batch = x->bview;
     BigArgs big{};
     big.g = g;
     big.Cp = x->Cp;
@@ -449,6 +470,7 @@ louvain_status move_iteration(louvain_ctx *x, const GView &g, int wk, int pass, 
     big.mv_vertex = x->mv_vertex;
     big.mv_target = x->mv_target;
     big.learn = L;
+    big.batch = x->bview;
     for (int b = 0; b < cfg.buckets; ++b) {
       LV_CK(cudaMemsetAsync(x->d_ctr, 0, 10 * sizeof(unsigned long long), x->stream));
       if (L.enabled) LV_CK(cudaMemsetAsync(&x->d_ctr->cand_count, 0, sizeof(unsigned long long), x->stream));
@@ -456,6 +478,9 @@ louvain_status move_iteration(louvain_ctx *x, const GView &g, int wk, int pass, 
       move_bucket(a, big, wk, x->num_sms, x->stream, x->prof.mask ? &x->prof : nullptr);
     }
     LV_CK(cudaGetLastError());
+    if (x->batched)  // per-graph gain sums, read with the counters
+      LV_CK(cudaMemcpyAsync(x->h_acc, x->b_acc, 2 * (size_t)x->G * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                            x->stream));
     louvain_status st = read_counters(x);
     if (st) return st;
     const Counters &h = *x->h_ctr;
@@ -490,14 +515,14 @@ louvain_status modularity_into(louvain_ctx *x, const GView &g, int wk, const int
   return LOUVAIN_OK;
 }
 
-louvain_status run_impl(louvain_ctx *x) {
+// Resets the records of the previous run and starts the run's clock.
+louvain_status begin_run(louvain_ctx *x) {
   const louvain_config &cfg = x->cfg;
   cudaStream_t s = x->stream;
   x->ran = false;
   x->iter_stats.assign((size_t)std::max(cfg.max_passes, 1) * cfg.max_iterations * 4, 0);
   x->pass_stats.assign((size_t)std::max(cfg.max_passes, 1) * 6, 0);
   x->it_total = x->moves_total = x->evaluated_total = x->skipped_total = 0;
-  const long long launches0 = g_launches;
   x->learned_log.clear();
   for (int k = 0; k < K_NUM_KERNELS; ++k) {
     x->prof.ms[k] = 0;
@@ -508,6 +533,95 @@ louvain_status run_impl(louvain_ctx *x) {
   for (auto &pt : x->timing) pt.aggregated = false;
   LV_CK(cudaEventRecord(x->run0, s));
   LV_CK(cudaMemsetAsync(x->d_ctr, 0, sizeof(Counters), s));
+  return LOUVAIN_OK;
+}
+
+AggArgs agg_args(louvain_ctx *x, const GView &g, int wk, int slot) {
+  AggArgs aa{};
+  aa.g = g;
+  aa.wkind = wk;
+  aa.Cp = x->Cp;
+  aa.Sigma = x->Sigma;
+  aa.Knew = x->Kalt;
+  aa.cnt = x->cnt;
+  aa.cdeg = x->cdeg;
+  aa.newid = x->newid;
+  aa.coff = x->coff;
+  aa.hoff = x->hoff;
+  aa.members = x->members;
+  aa.kcoff = x->kcoff;
+  aa.kcnt = x->kcnt;
+  for (int k = 0; k < kNumBins; ++k) aa.mbins[k] = x->bins[k];
+  aa.obegin = x->pbeg[slot];
+  aa.oend = x->pend[slot];
+  aa.ocol = x->pcol[slot];
+  aa.ow = x->pw[slot];
+  aa.mprefix = x->newid;  // free once the ids are relabelled
+  aa.ctr = x->d_ctr;
+  aa.scan_tmp = x->scan_tmp;
+  return aa;
+}
+
+// Aggregation after the counts and ids (Algorithm 6): member lists, bins,
+// dendrogram lookup and the merge into the other ping-pong CSR; g, wk, slot
+// and nnzp then describe the super-vertex graph.
+louvain_status aggregate(louvain_ctx *x, AggArgs &aa, int64_t gamma, PassTiming &pt, GView &g, int &wk, int &slot,
+                         int64_t &nnzp) {
+  cudaStream_t s = x->stream;
+  louvain_status st;
+  LV_CK(cudaMemsetAsync(&x->d_ctr->mbin_count[0], 0, sizeof(x->d_ctr->mbin_count), s));
+  LV_CK(cudaMemsetAsync(&x->d_ctr->maxdeg, 0, 3 * sizeof(unsigned long long), s));
+  x->prof.begin(K_SCATTER, s);
+  agg_scatter_compact(aa, x->num_sms, s);
+  x->prof.end(K_SCATTER, s);
+  x->prof.begin(K_DENDRO, s);
+  dendrogram_lookup(x->C, x->Cp, x->n0, x->num_sms, s);
+  x->prof.end(K_DENDRO, s);
+  LV_CK(cudaGetLastError());
+  if ((st = read_counters(x))) return st;
+  int64_t mwindow = 0;
+  int mrounds = 0;
+  if ((st = ensure_big_for(x, *x->h_ctr, x->h_ctr->maxdeg, (uint64_t)gamma, &mwindow, &mrounds))) return st;
+  aa.big.window = mwindow;
+  aa.big.rounds = mrounds;
+  aa.big.g = g;
+  aa.big.Cp = x->Cp;
+  aa.big.items = x->bins[kBigBin];
+  aa.big.count = &x->d_ctr->mbin_count[kBigBin];
+  aa.big.keyspace = gamma;
+  aa.big.ws = x->big;
+  if (x->h_ctr->big_items == 0) aa.big.ws.slots = 0;
+  aa.big.ctr = x->d_ctr;
+  aa.big.mprefix = aa.mprefix;
+  aa.big.kcoff = x->kcoff;
+  aa.big.kcnt = x->kcnt;
+  aa.big.members = x->members;
+  aa.big.obegin = aa.obegin;
+  aa.big.oend = aa.oend;
+  aa.big.ocol = aa.ocol;
+  aa.big.ow = aa.ow;
+  LV_CK(cudaMemsetAsync(&x->d_ctr->nnz_out, 0, sizeof(unsigned long long), s));
+  LV_CK(cudaMemsetAsync(&x->d_ctr->mg_work[0][0], 0, sizeof(x->d_ctr->mg_work), s));
+  agg_merge(aa, gamma, x->num_sms, s, x->prof.mask ? &x->prof : nullptr);
+  LV_CK(cudaGetLastError());
+  if ((st = read_counters(x))) return st;
+  account_merge(x, *x->h_ctr);
+  LV_CK(cudaEventRecord(pt.t2, s));
+  pt.aggregated = true;
+  nnzp = (int64_t)x->h_ctr->nnz_out;
+  std::swap(x->K, x->Kalt);  // K of the super-vertices
+  g = GView{gamma, x->pbeg[slot], x->pend[slot], x->pcol[slot], x->pw[slot]};
+  wk = W_U32;
+  slot ^= 1;
+  return LOUVAIN_OK;
+}
+
+louvain_status run_impl(louvain_ctx *x) {
+  const louvain_config &cfg = x->cfg;
+  cudaStream_t s = x->stream;
+  louvain_status st;
+  const long long launches0 = g_launches;
+  if ((st = begin_run(x))) return st;
 
   GView g{x->n0, x->off0, x->off0 + 1, x->col0, x->w0};
   int wk = x->weighted ? W_U32 : W_UNIT;
@@ -522,7 +636,6 @@ louvain_status run_impl(louvain_ctx *x) {
   int exit_reason = 0, passes = 0, slot = 0;
   int64_t nnzp = x->nnz0;
   bool have_pass_state = false;
-  louvain_status st;
   for (int p = 0; p < cfg.max_passes; ++p) {
     PassTiming &pt = x->timing[p];
     LV_CK(cudaEventRecord(pt.t0, s));
@@ -545,28 +658,7 @@ louvain_status run_impl(louvain_ctx *x) {
     have_pass_state = true;
     LV_CK(cudaEventRecord(pt.t1, s));
     ++passes;
-    AggArgs aa{};
-    aa.g = g;
-    aa.wkind = wk;
-    aa.Cp = x->Cp;
-    aa.Sigma = x->Sigma;
-    aa.Knew = x->Kalt;
-    aa.cnt = x->cnt;
-    aa.cdeg = x->cdeg;
-    aa.newid = x->newid;
-    aa.coff = x->coff;
-    aa.hoff = x->hoff;
-    aa.members = x->members;
-    aa.kcoff = x->kcoff;
-    aa.kcnt = x->kcnt;
-    for (int k = 0; k < kNumBins; ++k) aa.mbins[k] = x->bins[k];
-    aa.obegin = x->pbeg[slot];
-    aa.oend = x->pend[slot];
-    aa.ocol = x->pcol[slot];
-    aa.ow = x->pw[slot];
-    aa.mprefix = x->newid;  // free once the ids are relabelled
-    aa.ctr = x->d_ctr;
-    aa.scan_tmp = x->scan_tmp;
+    AggArgs aa = agg_args(x, g, wk, slot);
     x->prof.begin(K_COMM_COUNT, s);
     agg_count_scan(aa, x->num_sms, s);
     x->prof.end(K_COMM_COUNT, s);
@@ -598,50 +690,7 @@ louvain_status run_impl(louvain_ctx *x) {
       exit_reason = 2;
       break;
     }
-    LV_CK(cudaMemsetAsync(&x->d_ctr->mbin_count[0], 0, sizeof(x->d_ctr->mbin_count), s));
-    LV_CK(cudaMemsetAsync(&x->d_ctr->maxdeg, 0, 3 * sizeof(unsigned long long), s));
-    x->prof.begin(K_SCATTER, s);
-    agg_scatter_compact(aa, x->num_sms, s);
-    x->prof.end(K_SCATTER, s);
-    x->prof.begin(K_DENDRO, s);
-    dendrogram_lookup(x->C, x->Cp, x->n0, x->num_sms, s);
-    x->prof.end(K_DENDRO, s);
-    LV_CK(cudaGetLastError());
-    if ((st = read_counters(x))) return st;
-    int64_t mwindow = 0;
-    int mrounds = 0;
-    if ((st = ensure_big_for(x, *x->h_ctr, x->h_ctr->maxdeg, (uint64_t)gamma, &mwindow, &mrounds))) return st;
-    aa.big.window = mwindow;
-    aa.big.rounds = mrounds;
-    aa.big.g = g;
-    aa.big.Cp = x->Cp;
-    aa.big.items = x->bins[kBigBin];
-    aa.big.count = &x->d_ctr->mbin_count[kBigBin];
-    aa.big.keyspace = gamma;
-    aa.big.ws = x->big;
-    if (x->h_ctr->big_items == 0) aa.big.ws.slots = 0;
-    aa.big.ctr = x->d_ctr;
-    aa.big.mprefix = aa.mprefix;
-    aa.big.kcoff = x->kcoff;
-    aa.big.kcnt = x->kcnt;
-    aa.big.members = x->members;
-    aa.big.obegin = aa.obegin;
-    aa.big.oend = aa.oend;
-    aa.big.ocol = aa.ocol;
-    aa.big.ow = aa.ow;
-    LV_CK(cudaMemsetAsync(&x->d_ctr->nnz_out, 0, sizeof(unsigned long long), s));
-    LV_CK(cudaMemsetAsync(&x->d_ctr->mg_work[0][0], 0, sizeof(x->d_ctr->mg_work), s));
-    agg_merge(aa, gamma, x->num_sms, s, x->prof.mask ? &x->prof : nullptr);
-    LV_CK(cudaGetLastError());
-    if ((st = read_counters(x))) return st;
-    account_merge(x, *x->h_ctr);
-    LV_CK(cudaEventRecord(pt.t2, s));
-    pt.aggregated = true;
-    nnzp = (int64_t)x->h_ctr->nnz_out;
-    std::swap(x->K, x->Kalt);  // K of the super-vertices
-    g = GView{gamma, x->pbeg[slot], x->pend[slot], x->pcol[slot], x->pw[slot]};
-    wk = W_U32;
-    slot ^= 1;
+    if ((st = aggregate(x, aa, gamma, pt, g, wk, slot, nnzp))) return st;
     tau /= cfg.tolerance_drop;
     have_pass_state = false;
   }
@@ -673,6 +722,230 @@ louvain_status run_impl(louvain_ctx *x) {
   x->q = qd ? (double)qn / (double)qd : 0.0;
   x->passes = passes;
   x->exit_reason = exit_reason;
+  float ms = 0;
+  LV_CK(cudaEventElapsedTime(&ms, x->run0, x->run1));
+  x->run_ms = ms;
+  x->launches = g_launches - launches0;
+  x->big_dirty = false;
+  x->ran = true;
+  return LOUVAIN_OK;
+}
+
+// Graphs of a batch that stop now (sel[g] = 1): exact modularity of each on
+// the current union graph (Eq. 1 with the graph's own 2m) and its final
+// memberships (dense ranks of the community ids of C' when newid is given,
+// else of the current super-vertices).
+louvain_status batch_finish(louvain_ctx *x, const GView &g, int wk, const int64_t *newid,
+                            const std::vector<char> &sel) {
+  cudaStream_t s = x->stream;
+  const int64_t G = x->G;
+  for (int64_t k = 0; k < G; ++k) x->h_flags[k] = sel[k] ? 1 : 0;
+  LV_CK(cudaMemcpyAsync(x->b_sel, x->h_flags, (size_t)G, cudaMemcpyHostToDevice, s));
+  unsigned long long *acc = x->b_acc + 3 * G;
+  LV_CK(cudaMemsetAsync(acc, 0, 3 * (size_t)G * sizeof(unsigned long long), s));
+  x->prof.begin(K_MODULARITY, s);
+  batch_modularity(g, wk, x->b_gid, x->Cp, x->Sigma, x->b_sel, acc, acc + G, acc + 2 * G, x->num_sms, s);
+  x->prof.end(K_MODULARITY, s);
+  x->prof.begin(K_RENUMBER, s);
+  batch_final(x->n0, x->C, x->b_ogid, x->Cp, newid, x->b_vo, x->b_sel, x->b_out, x->num_sms, s);
+  x->prof.end(K_RENUMBER, s);
+  LV_CK(cudaGetLastError());
+  LV_CK(cudaMemcpyAsync(x->h_acc + 3 * G, acc, 3 * (size_t)G * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  LV_CK(cudaStreamSynchronize(s));
+  for (int64_t k = 0; k < G; ++k) {
+    if (!sel[k]) continue;
+    const i128 tm = (i128)x->gtwo_m[k];
+    const i128 sq = ((i128)x->h_acc[5 * G + k] << 32) + (i128)x->h_acc[4 * G + k];
+    const i128 num = tm * (i128)x->h_acc[3 * G + k] - sq;
+    const i128 den = tm * tm;
+    int64_t *r = &x->b_results[(size_t)k * 8];
+    put128(r + 2, num);
+    put128(r + 4, den);
+    x->b_q[k] = den ? (double)num / (double)den : 0.0;
+  }
+  return LOUVAIN_OK;
+}
+
+// Batched run: the pass loop of run_impl over the union of G graphs, with the
+// iteration tolerance, the l_i <= 1 test and the aggregation tolerance taken
+// per graph.  A graph that stops leaves the union at that pass's aggregation
+// (its vertices get C' = -1 and are not renumbered); the remaining graphs
+// are aggregated together.  Every graph sees exactly the sequence of states
+// of a run on its own: the schedule hashes local vertex ids, and dense
+// renumbering keeps each graph's super-vertices in order and contiguous.
+louvain_status run_batched(louvain_ctx *x) {
+  const louvain_config &cfg = x->cfg;
+  cudaStream_t s = x->stream;
+  louvain_status st;
+  const long long launches0 = g_launches;
+  if ((st = begin_run(x))) return st;
+  const int64_t G = x->G;
+  const int P = std::max(cfg.max_passes, 1);
+  x->b_results.assign((size_t)G * 8, 0);
+  x->b_q.assign((size_t)G, 0.0);
+  x->b_passes.assign((size_t)G * P * 3, 0);
+  for (int64_t k = 0; k < G; ++k) x->b_results[(size_t)k * 8 + 6] = x->gtwo_m[k];
+  std::vector<int64_t> vo(x->vo0);
+  std::vector<char> alive((size_t)G, 1), mv((size_t)G, 0), fin((size_t)G, 0);
+  std::vector<int> li((size_t)G, 0);
+  int64_t alive_count = G;
+  LV_CK(cudaMemcpyAsync(x->b_vo, vo.data(), (size_t)(G + 1) * 8, cudaMemcpyHostToDevice, s));
+  LV_CK(cudaMemcpyAsync(x->b_gid, x->b_ogid, (size_t)std::max<int64_t>(x->n0, 1) * 4, cudaMemcpyDeviceToDevice, s));
+
+  GView g{x->n0, x->off0, x->off0 + 1, x->col0, x->w0};
+  int wk = x->weighted ? W_U32 : W_UNIT;
+  if (x->big_dirty && x->big.slots > 0) {
+    LV_CK(cudaMemsetAsync(x->big.keys, 0xFF, (size_t)x->big.slots * sizeof(int32_t), s));
+    LV_CK(cudaMemsetAsync(x->big.vals, 0, (size_t)x->big.slots * sizeof(uint32_t), s));
+  }
+  x->big_dirty = true;
+  iota_i32(x->C, x->n0, x->num_sms, s);
+  double tau = cfg.tolerance;
+  int passes = 0, slot = 0;
+  int64_t nnzp = x->nnz0;
+  for (int p = 0; p < cfg.max_passes && alive_count > 0; ++p) {
+    PassTiming &pt = x->timing[p];
+    LV_CK(cudaEventRecord(pt.t0, s));
+    LV_CK(cudaMemsetAsync(&x->d_ctr->maxdeg, 0, sizeof(unsigned long long), s));
+    x->cur_wbytes = wk == W_UNIT ? 0 : 4;
+    LV_CK(cudaMemsetAsync(&x->d_ctr->big_slots, 0, 2 * sizeof(unsigned long long), s));
+    x->prof.begin(K_PASS_INIT, s);
+    pass_init(g, wk, p == 0, x->K, x->Sigma, x->Cp, x->flag, x->d_ctr, x->num_sms, s);
+    x->prof.end(K_PASS_INIT, s);
+    LV_CK(cudaGetLastError());
+    if ((st = read_counters(x))) return st;
+    x->pass_has_hubs = x->h_ctr->big_items > 0;
+    if ((st = ensure_big_for(x, *x->h_ctr, x->h_ctr->maxdeg, (uint64_t)g.n, &x->hub_window, &x->hub_rounds)))
+      return st;
+    // local-moving phase, each graph until its own tolerance test holds
+    for (int64_t k = 0; k < G; ++k) {
+      mv[k] = alive[k];
+      li[k] = cfg.max_iterations;
+      x->h_flags[k] = mv[k];
+    }
+    LV_CK(cudaMemcpyAsync(x->b_moving, x->h_flags, (size_t)G, cudaMemcpyHostToDevice, s));
+    int li_union = 0;
+    for (int t = 0; t < cfg.max_iterations; ++t) {
+      const Counters *h;
+      if ((st = move_iteration(x, g, wk, p, t, false, &h))) return st;
+      li_union = t + 1;
+      bool any = false;
+      for (int64_t k = 0; k < G; ++k) {
+        if (!mv[k]) continue;
+        const i128 gain = ((i128)x->h_acc[G + k] << 32) + (i128)x->h_acc[k];
+        const i128 den2 = (i128)x->gtwo_m[k] * x->gtwo_m[k];
+        const double total = den2 ? (double)(2 * gain) / (double)den2 : 0.0;
+        if (total <= tau) {
+          mv[k] = 0;
+          li[k] = t + 1;
+        } else {
+          any = true;
+        }
+      }
+      if (!any) break;
+      for (int64_t k = 0; k < G; ++k) x->h_flags[k] = mv[k];
+      LV_CK(cudaMemcpyAsync(x->b_moving, x->h_flags, (size_t)G, cudaMemcpyHostToDevice, s));
+    }
+    LV_CK(cudaEventRecord(pt.t1, s));
+    ++passes;
+    AggArgs aa = agg_args(x, g, wk, slot);
+    x->prof.begin(K_COMM_COUNT, s);
+    agg_count_scan(aa, x->num_sms, s);
+    x->prof.end(K_COMM_COUNT, s);
+    batch_gather(x->newid, x->b_vo, G + 1, x->b_bound, s);
+    LV_CK(cudaGetLastError());
+    LV_CK(cudaMemcpyAsync(x->h_bound, x->b_bound, (size_t)(G + 1) * 8, cudaMemcpyDeviceToHost, s));
+    if ((st = read_counters(x))) return st;
+    int64_t gamma = (int64_t)x->h_ctr->scan_total[0];
+    {
+      int64_t *r = &x->pass_stats[(size_t)p * 6];
+      r[0] = g.n;
+      r[1] = nnzp;
+      r[2] = li_union;
+      r[3] = gamma;
+    }
+    // per-graph convergence (l_i <= 1) and aggregation tolerance tests
+    int64_t nfin = 0;
+    std::vector<int64_t> gam((size_t)G, 0);
+    for (int64_t k = 0; k < G; ++k) {
+      fin[k] = 0;
+      if (!alive[k]) continue;
+      const int64_t ng = vo[k + 1] - vo[k];
+      gam[k] = x->h_bound[k + 1] - x->h_bound[k];
+      int64_t *r = &x->b_passes[((size_t)k * P + p) * 3];
+      r[0] = ng;
+      r[1] = li[k];
+      r[2] = gam[k];
+      int why = 0;
+      if (li[k] <= 1) why = 1;
+      else if ((double)gam[k] / (double)ng > cfg.aggregation_tolerance) why = 2;
+      if (why) {
+        fin[k] = 1;
+        ++nfin;
+        int64_t *res = &x->b_results[(size_t)k * 8];
+        res[0] = p + 1;
+        res[1] = gam[k];
+        res[7] = why;
+      }
+    }
+    if (nfin) {
+      if ((st = batch_finish(x, g, wk, x->newid, fin))) return st;
+      for (int64_t k = 0; k < G; ++k)
+        if (fin[k]) alive[k] = 0;
+      alive_count -= nfin;
+      if (alive_count == 0) break;
+      // the finished graphs leave the union: recount without them
+      batch_exclude(g.n, x->b_gid, x->b_sel, x->Cp, x->num_sms, s);
+      agg_count_scan(aa, x->num_sms, s);
+      LV_CK(cudaGetLastError());
+      if ((st = read_counters(x))) return st;
+      gamma = (int64_t)x->h_ctr->scan_total[0];
+    }
+    aa.gamma = gamma;
+    // vertex offsets of the graphs in the super-vertex union
+    std::vector<int64_t> nvo((size_t)G + 1, 0);
+    for (int64_t k = 0; k < G; ++k) nvo[k + 1] = nvo[k] + (alive[k] ? gam[k] : 0);
+    if (nvo[G] != gamma) {
+      set_err(x, "batched aggregation: community counts do not add up (%lld vs %lld)", (long long)nvo[G],
+              (long long)gamma);
+      return LOUVAIN_E_STATE;
+    }
+    if ((st = aggregate(x, aa, gamma, pt, g, wk, slot, nnzp))) return st;
+    vo.swap(nvo);
+    LV_CK(cudaMemcpyAsync(x->b_vo, vo.data(), (size_t)(G + 1) * 8, cudaMemcpyHostToDevice, s));
+    batch_gid(x->b_vo, G, g.n, x->b_gid, x->num_sms, s);
+    LV_CK(cudaGetLastError());
+    tau /= cfg.tolerance_drop;
+  }
+  if (alive_count > 0) {  // pass cap reached: identity memberships on the current graph
+    LV_CK(cudaMemsetAsync(&x->d_ctr->maxdeg, 0, sizeof(unsigned long long), s));
+    pass_init(g, wk, passes == 0, x->K, x->Sigma, x->Cp, x->flag, x->d_ctr, x->num_sms, s);
+    for (int64_t k = 0; k < G; ++k) {
+      if (!alive[k]) continue;
+      int64_t *res = &x->b_results[(size_t)k * 8];
+      res[0] = passes;
+      res[1] = vo[k + 1] - vo[k];
+      res[7] = 0;
+    }
+    if ((st = batch_finish(x, g, wk, nullptr, alive))) return st;
+  }
+  LV_CK(cudaEventRecord(x->run1, s));
+  LV_CK(cudaGetLastError());
+  if ((st = read_counters(x))) return st;
+  if (x->prof.mask) x->prof.collect();
+  int64_t total = 0;
+  double qsum = 0;
+  int maxp = 0;
+  for (int64_t k = 0; k < G; ++k) {
+    total += x->b_results[(size_t)k * 8 + 1];
+    qsum += x->b_q[k];
+    maxp = std::max<int>(maxp, (int)x->b_results[(size_t)k * 8]);
+  }
+  x->gamma = total;
+  x->q = G ? qsum / (double)G : 0.0;
+  x->qnum = x->qden = 0;
+  x->passes = maxp;
+  x->exit_reason = 0;
   float ms = 0;
   LV_CK(cudaEventElapsedTime(&ms, x->run0, x->run1));
   x->run_ms = ms;
@@ -731,7 +1004,7 @@ bool host_symmetric(int64_t n, const int64_t *off, const int32_t *col, const int
 }
 
 louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg, void *stream, louvain_ctx **out,
-                            bool light = false) {
+                            bool light = false, bool batched = false) {
   *out = nullptr;
   if (!graph || !cfg) {
     set_err(nullptr, "null graph or config");
@@ -840,7 +1113,7 @@ louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg
       return fail(LOUVAIN_E_INVAL);
     }
     x->two_m = (long long)x->h_ctr->q_sin;
-    if ((unsigned long long)x->two_m >= (1ull << 32)) {
+    if (!batched && (unsigned long long)x->two_m >= (1ull << 32)) {  // a batch checks each graph's 2m
       set_err(x, "total weight 2m = %lld is 2^32 or more; int64 scores would overflow", x->two_m);
       return fail(LOUVAIN_E_OVERFLOW);
     }
@@ -902,6 +1175,65 @@ louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg
   return LOUVAIN_OK;
 }
 
+template <typename T>
+louvain_status pinned_n(louvain_ctx *x, T **p, int64_t n) {
+  void *q = nullptr;
+  if (cudaMallocHost(&q, (size_t)std::max<int64_t>(n, 1) * sizeof(T)) != cudaSuccess) {
+    set_err(x, "pinned allocation of %lld bytes failed", (long long)(n * (int64_t)sizeof(T)));
+    return LOUVAIN_E_NOMEM;
+  }
+  x->pinned.push_back(q);
+  *p = (T *)q;
+  return LOUVAIN_OK;
+}
+
+// Batch state on top of a context created for the union graph: vertex
+// offsets, graph of each vertex, per-graph 2m (each must be below 2^32) and
+// the check that no entry leaves its graph.
+louvain_status setup_batch(louvain_ctx *x, const int64_t *vo, int64_t G) {
+  cudaStream_t s = x->stream;
+  louvain_status st;
+  x->batched = true;
+  x->G = G;
+  x->vo0.assign(vo, vo + G + 1);
+  const int64_t nv = std::max<int64_t>(x->n0, 1);
+  if ((st = dalloc_n(x, &x->b_gid, nv)) || (st = dalloc_n(x, &x->b_ogid, nv)) || (st = dalloc_n(x, &x->b_out, nv)) ||
+      (st = dalloc_n(x, &x->b_vo, G + 1)) || (st = dalloc_n(x, &x->b_bound, G + 1)) ||
+      (st = dalloc_n(x, &x->b_two_m, G)) || (st = dalloc_n(x, &x->b_moving, G)) || (st = dalloc_n(x, &x->b_sel, G)) ||
+      (st = dalloc_n(x, &x->b_acc, 6 * G)))
+    return st;
+  if ((st = pinned_n(x, &x->h_acc, 6 * G)) || (st = pinned_n(x, &x->h_bound, G + 1)) ||
+      (st = pinned_n(x, &x->h_flags, G)))
+    return st;
+  LV_CK(cudaMemcpyAsync(x->b_vo, vo, (size_t)(G + 1) * 8, cudaMemcpyHostToDevice, s));
+  LV_CK(cudaMemsetAsync(x->b_two_m, 0, (size_t)G * sizeof(long long), s));
+  LV_CK(cudaMemsetAsync(x->d_ctr, 0, sizeof(Counters), s));
+  batch_gid(x->b_vo, G, x->n0, x->b_ogid, x->num_sms, s);
+  const GView g0{x->n0, x->off0, x->off0 + 1, x->col0, x->w0};
+  batch_check(g0, x->weighted ? W_U32 : W_UNIT, x->b_ogid, x->b_vo, x->b_two_m, x->d_ctr, x->num_sms, s);
+  LV_CK(cudaGetLastError());
+  x->gtwo_m.assign((size_t)G, 0);
+  LV_CK(cudaMemcpyAsync(x->gtwo_m.data(), x->b_two_m, (size_t)G * sizeof(long long), cudaMemcpyDeviceToHost, s));
+  if ((st = read_counters(x))) return st;
+  if (x->h_ctr->error & ERR_RANGE) {
+    set_err(x, "an entry of a graph's rows points outside the graph's vertex range");
+    return LOUVAIN_E_INVAL;
+  }
+  for (int64_t k = 0; k < G; ++k)
+    if ((unsigned long long)x->gtwo_m[k] >= (1ull << 32)) {
+      set_err(x, "graph %lld: total weight 2m = %lld is 2^32 or more", (long long)k, x->gtwo_m[k]);
+      return LOUVAIN_E_OVERFLOW;
+    }
+  x->bview.gid = x->b_gid;
+  x->bview.vo = x->b_vo;
+  x->bview.two_m = x->b_two_m;
+  x->bview.moving = x->b_moving;
+  x->bview.gain_lo = x->b_acc;
+  x->bview.gain_hi = x->b_acc + G;
+  x->bview.moves = x->b_acc + 2 * G;
+  return LOUVAIN_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -934,17 +1266,60 @@ louvain_status louvain_create(const louvain_graph *graph, const louvain_config *
   return create_impl(graph, cfg, stream, out);
 }
 
+louvain_status louvain_create_batched(const louvain_graph *graph, const int64_t *vertex_offsets, int64_t num_graphs,
+                                      const louvain_config *cfg, void *stream, louvain_ctx **out) {
+  if (!out) return LOUVAIN_E_INVAL;
+  *out = nullptr;
+  if (!graph || !cfg || !vertex_offsets || num_graphs < 1 || num_graphs > INT32_MAX) {
+    set_err(nullptr, "null argument or bad number of graphs");
+    return LOUVAIN_E_INVAL;
+  }
+  if (cfg->mode != LOUVAIN_MODE_PLAIN || cfg->trace_capacity != 0) {
+    set_err(nullptr, "batched runs use the plain mode without traces");
+    return LOUVAIN_E_INVAL;
+  }
+  if (vertex_offsets[0] != 0 || vertex_offsets[num_graphs] != graph->n) {
+    set_err(nullptr, "vertex_offsets[0] must be 0 and vertex_offsets[num_graphs] must equal n");
+    return LOUVAIN_E_INVAL;
+  }
+  for (int64_t k = 0; k < num_graphs; ++k)
+    if (vertex_offsets[k + 1] < vertex_offsets[k]) {
+      set_err(nullptr, "vertex_offsets must not decrease");
+      return LOUVAIN_E_INVAL;
+    }
+  louvain_ctx *x = nullptr;
+  louvain_status st = create_impl(graph, cfg, stream, &x, false, true);
+  if (st) return st;
+  if ((st = setup_batch(x, vertex_offsets, num_graphs))) {
+    g_create_err = x->err;
+    louvain_destroy(x);
+    return st;
+  }
+  *out = x;
+  return LOUVAIN_OK;
+}
+
+louvain_status louvain_batch_results(const louvain_ctx *x, int64_t *results, double *q, int64_t *pass_records) {
+  if (!x || !x->batched) return LOUVAIN_E_INVAL;
+  if (!x->ran) return LOUVAIN_E_STATE;
+  if (results) memcpy(results, x->b_results.data(), x->b_results.size() * sizeof(int64_t));
+  if (q) memcpy(q, x->b_q.data(), x->b_q.size() * sizeof(double));
+  if (pass_records && x->cfg.max_passes > 0)
+    memcpy(pass_records, x->b_passes.data(), (size_t)x->G * x->cfg.max_passes * 3 * sizeof(int64_t));
+  return LOUVAIN_OK;
+}
+
 louvain_status louvain_run(louvain_ctx *x) {
   if (!x) return LOUVAIN_E_INVAL;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != x->device) cudaSetDevice(x->device);
-  louvain_status st = run_impl(x);
+  louvain_status st = x->batched ? run_batched(x) : run_impl(x);
   if (st != LOUVAIN_OK) x->ran = false;
   return st;
 }
 
 louvain_status louvain_modularity(const louvain_ctx *x, double *q, int64_t *num, int64_t *den) {
-  if (!x) return LOUVAIN_E_INVAL;
+  if (!x || x->batched) return LOUVAIN_E_INVAL;  // a batch reports per graph (louvain_batch_results)
   if (!x->ran) return LOUVAIN_E_STATE;
   if (q) *q = x->q;
   if (num) put128(num, x->qnum);
@@ -957,7 +1332,7 @@ louvain_status louvain_memberships(const louvain_ctx *xc, int32_t *out, int32_t 
   if (!x || (!out && x->n0 > 0)) return LOUVAIN_E_INVAL;
   if (!x->ran) return LOUVAIN_E_STATE;
   if (x->n0 == 0) return LOUVAIN_OK;
-  LV_CK(cudaMemcpyAsync(out, x->C, (size_t)x->n0 * 4, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+  LV_CK(cudaMemcpyAsync(out, x->batched ? x->b_out : x->C, (size_t)x->n0 * 4, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                         x->stream));
   LV_CK(cudaStreamSynchronize(x->stream));
   return LOUVAIN_OK;
@@ -1059,6 +1434,7 @@ void louvain_destroy(louvain_ctx *x) {
   if (x->run0) cudaEventDestroy(x->run0);
   if (x->run1) cudaEventDestroy(x->run1);
   if (x->h_ctr) cudaFreeHost(x->h_ctr);
+  for (void *p : x->pinned) cudaFreeHost(p);
   delete x;
 }
 

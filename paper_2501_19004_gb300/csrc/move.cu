@@ -41,8 +41,15 @@ __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
     int bin = -1;
     bool sel = false;
     bool cand = false;
-    if (i < n && a.flag[i]) {
-      const uint32_t h = fmix32((uint32_t)i ^ a.salt);
+    bool live = i < n && a.flag[i];
+    uint32_t local = (uint32_t)i;
+    if (live && a.batch.gid) {  // batched: only graphs still moving, hashed by their local ids
+      const int32_t gg = a.batch.gid[i];
+      live = a.batch.moving[gg] != 0;
+      local = (uint32_t)(i - a.batch.vo[gg]);
+    }
+    if (live) {
+      const uint32_t h = fmix32(local ^ a.salt);
       const uint32_t bk = pow2 ? (h & (a.nbuckets - 1)) : (h % a.nbuckets);
       if (bk == a.bucket) {
         if (a.learn.enabled && a.learn.feat[i].w > 0.f) {
@@ -185,6 +192,7 @@ __global__ void __launch_bounds__(256) k_move_thread(MoveArgs a) {
       for (int k = 0; k < D; ++k) cc[k] = (jj[k] == i) ? kEmpty : a.Cp[jj[k]];
       const int32_t d = a.Cp[i];
       const long long Ki = a.K[i];
+      const long long tm = vertex_two_m(a.batch, a.two_m, i);
       long long Kid = 0;
 #pragma unroll
       for (int k = 0; k < D; ++k) Kid += (cc[k] == d) ? ww[k] : 0u;
@@ -203,7 +211,7 @@ __global__ void __launch_bounds__(256) k_move_thread(MoveArgs a) {
         }
         if (first) {
           ++work[2];
-          const long long s = a.two_m * sum - Ki * a.Sigma[c];
+          const long long s = tm * sum - Ki * a.Sigma[c];
           if (better(s, c, best_s, best_c)) {
             best_s = s;
             best_c = c;
@@ -211,8 +219,9 @@ __global__ void __launch_bounds__(256) k_move_thread(MoveArgs a) {
         }
       }
       long long s_d = 0;
-      target = finish_decision(a.two_m, a.Sigma, a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm, &s_d);
+      target = finish_decision(tm, a.Sigma, a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm, &s_d);
       learn_record(a.learn, a.ctr, a.g, a.Cp, a.Sigma, a.two_m, i, Ki, Kid, best_s, best_c, s_d, target >= 0);
+      if (target >= 0) batch_gain(a.batch, i, best_s, s_d);
       work[0] += 1;
       work[1] += (unsigned long long)deg;
       if (target >= 0) {
@@ -301,6 +310,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_move_warp(MoveArgs a) {
     __syncwarp();
     const int32_t d = a.Cp[i];
     const long long Ki = a.K[i];
+    const long long tm = vertex_two_m(a.batch, a.two_m, i);
     long long best_s = LLONG_MIN, Kid = 0;
     int32_t best_c = INT_MAX;
     for (uint32_t s = lane; s < cap; s += 32) {
@@ -312,7 +322,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_move_warp(MoveArgs a) {
         continue;
       }
       ++work[2];
-      const long long sc = a.two_m * v - Ki * a.Sigma[c];
+      const long long sc = tm * v - Ki * a.Sigma[c];
       if (better(sc, c, best_s, best_c)) {
         best_s = sc;
         best_c = c;
@@ -323,8 +333,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_move_warp(MoveArgs a) {
     int32_t target = -1;
     if (lane == 0) {
       long long s_d = 0;
-      target = finish_decision(a.two_m, a.Sigma, a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm, &s_d);
+      target = finish_decision(tm, a.Sigma, a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm, &s_d);
       learn_record(a.learn, a.ctr, a.g, a.Cp, a.Sigma, a.two_m, i, Ki, Kid, best_s, best_c, s_d, target >= 0);
+      if (target >= 0) batch_gain(a.batch, i, best_s, s_d);
       work[0] += 1;
       work[1] += (unsigned long long)deg;
       if (target >= 0) {
@@ -389,6 +400,7 @@ __global__ void __launch_bounds__(NT) k_move_block(MoveArgs a) {
     __syncthreads();
     const int32_t d = a.Cp[i];
     const long long Ki = a.K[i];
+    const long long tm = vertex_two_m(a.batch, a.two_m, i);
     long long best_s = LLONG_MIN, Kid = 0;
     int32_t best_c = INT_MAX;
     for (uint32_t s = threadIdx.x; s < cap; s += NT) {
@@ -400,7 +412,7 @@ __global__ void __launch_bounds__(NT) k_move_block(MoveArgs a) {
         continue;
       }
       ++work[2];
-      const long long sc = a.two_m * v - Ki * a.Sigma[c];
+      const long long sc = tm * v - Ki * a.Sigma[c];
       if (better(sc, c, best_s, best_c)) {
         best_s = sc;
         best_c = c;
@@ -409,8 +421,9 @@ __global__ void __launch_bounds__(NT) k_move_block(MoveArgs a) {
     block_argmax_sum<NT>(best_s, best_c, Kid);
     if (threadIdx.x == 0) {
       long long s_d = 0;
-      const int32_t t = finish_decision(a.two_m, a.Sigma, a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm, &s_d);
+      const int32_t t = finish_decision(tm, a.Sigma, a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm, &s_d);
       learn_record(a.learn, a.ctr, a.g, a.Cp, a.Sigma, a.two_m, i, Ki, Kid, best_s, best_c, s_d, t >= 0);
+      if (t >= 0) batch_gain(a.batch, i, best_s, s_d);
       work[0] += 1;
       work[1] += (unsigned long long)deg;
       if (t >= 0) {

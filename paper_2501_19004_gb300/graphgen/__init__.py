@@ -190,5 +190,30 @@ def batched_sbm(g: int) -> CSR:
     return c
 
 
+def concat(graphs) -> "tuple[CSR, np.ndarray]":
+    """Union of several graphs (the input of a batched run): graph g's vertices
+    become [vo[g], vo[g+1]) and its columns are shifted by vo[g].  Returns
+    (union CSR, vo int64 [G+1]).  The union is weighted if any graph is."""
+    graphs = list(graphs)
+    G = len(graphs)
+    vo = np.zeros(G + 1, dtype=np.int64)
+    eo = np.zeros(G + 1, dtype=np.int64)
+    for k, g in enumerate(graphs):
+        vo[k + 1] = vo[k] + g.n
+        eo[k + 1] = eo[k] + g.nnz
+    off = np.empty(int(vo[G]) + 1, dtype=np.int64)
+    col = np.empty(int(eo[G]), dtype=np.int32)
+    weighted = any(g.weights is not None for g in graphs)
+    w = np.empty(int(eo[G]), dtype=np.int32) if weighted else None
+    for k, g in enumerate(graphs):
+        a, b = int(vo[k]), int(vo[k + 1])
+        off[a:b] = g.offsets[:-1] + eo[k]
+        col[eo[k]:eo[k + 1]] = g.cols + np.int32(vo[k])
+        if weighted:
+            w[eo[k]:eo[k + 1]] = g.weights if g.weights is not None else 1
+    off[int(vo[G])] = eo[G]
+    return CSR(off, col, w, f"union{G}"), vo
+
+
 def num_threads() -> int:
     return int(_load().gg_num_threads())

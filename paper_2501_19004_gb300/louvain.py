@@ -28,7 +28,7 @@ STATUS = {0: "OK", 1: "E_INVAL", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_HASH_OVERFLOW"
 MODE_PLAIN, MODE_LEARNED = 0, 1
 KERNELS = ["select", "move_thread", "move_warp", "move_mid", "move_block", "move_hub", "apply", "pass_init",
            "comm_count", "comm_scatter", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big",
-           "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit"]
+           "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit", "mlp_select"]
 
 
 def kernel_mask(*names) -> int:
@@ -109,6 +109,10 @@ def load(path: Optional[str] = None):
     lib.louvain_mlp_train.argtypes = [vp, vp, vp, i64, i32, i32, ctypes.c_float, ctypes.c_uint64, vp, vp]
     lib.louvain_modularity_noalloc.restype = ctypes.c_int
     lib.louvain_modularity_noalloc.argtypes = [P(LouvainGraph), vp, vp, P(ctypes.c_double), vp, vp]
+    lib.louvain_create_batched.restype = ctypes.c_int
+    lib.louvain_create_batched.argtypes = [P(LouvainGraph), vp, i64, P(LouvainConfig), vp, P(vp)]
+    lib.louvain_batch_results.restype = ctypes.c_int
+    lib.louvain_batch_results.argtypes = [vp, vp, vp, vp]
     lib.louvain_model_size.restype = i64
     lib.louvain_model_size.argtypes = []
     lib.louvain_version.restype = ctypes.c_char_p
@@ -352,6 +356,30 @@ def louvain_modularity_noalloc(graph, membership, stream=None):
     return st, q.value, _i128(num), _i128(den)
 
 
+def louvain_create_batched(graph, vertex_offsets, cfg: Optional[Config] = None, stream=None) -> ctypes.c_void_p:
+    """Context for a batch: `graph` is the union, graph g owning the vertices
+    [vertex_offsets[g], vertex_offsets[g+1])."""
+    cfg = cfg or Config()
+    gs, keep = _graph_struct(graph)
+    vo = np.ascontiguousarray(vertex_offsets, dtype=np.int64)
+    cc = cfg.c()
+    ctx = ctypes.c_void_p()
+    st = load().louvain_create_batched(ctypes.byref(gs), vo.ctypes.data, vo.shape[0] - 1, ctypes.byref(cc),
+                                       stream if stream is not None else _current_stream(), ctypes.byref(ctx))
+    del keep
+    _check(st, None)
+    return ctx
+
+
+def louvain_batch_results(ctx, num_graphs: int, max_passes: int):
+    """(results [G][8], q [G], pass_records [G][max_passes][3]) of the last batched run."""
+    res = np.zeros((num_graphs, 8), dtype=np.int64)
+    q = np.zeros(num_graphs, dtype=np.float64)
+    pr = np.zeros((num_graphs, max(max_passes, 1), 3), dtype=np.int64)
+    _check(load().louvain_batch_results(ctx, res.ctypes.data, q.ctypes.data, pr.ctypes.data), ctx)
+    return res, q, pr
+
+
 def louvain_model_size() -> int:
     return int(load().louvain_model_size())
 
@@ -431,3 +459,60 @@ class Louvain:
 def run(graph, cfg: Optional[Config] = None) -> Result:
     with Louvain(graph, cfg) as lv:
         return lv.run().result()
+
+
+@dataclass
+class BatchResult:
+    """Per-graph results of a batched run; memberships are local dense ids."""
+    membership: np.ndarray      # [n] of the union
+    vertex_offsets: np.ndarray  # [G+1]
+    modularity: np.ndarray      # [G]
+    summary: np.ndarray         # [G][8]: passes, communities, Qnum hi/lo, Qden hi/lo, 2m, exit reason
+    pass_records: np.ndarray    # [G][max_passes][3]: n', l_i, |Gamma|
+
+    def graph(self, g: int):
+        """(membership, modularity, exact numerator, exact denominator, passes, communities, exit reason)."""
+        a, b = int(self.vertex_offsets[g]), int(self.vertex_offsets[g + 1])
+        r = self.summary[g]
+        return (self.membership[a:b], float(self.modularity[g]), _i128(r[2:4]), _i128(r[4:6]), int(r[0]),
+                int(r[1]), int(r[7]))
+
+
+class LouvainBatch:
+    """Many graphs in one context (louvain_create_batched); ``run()`` can be repeated."""
+
+    def __init__(self, graph, vertex_offsets, cfg: Optional[Config] = None, stream=None):
+        self.cfg = cfg or Config()
+        self.n = graph.n
+        self.vo = np.ascontiguousarray(vertex_offsets, dtype=np.int64)
+        self.G = self.vo.shape[0] - 1
+        self.ctx = louvain_create_batched(graph, self.vo, self.cfg, stream)
+
+    def run(self):
+        louvain_run(self.ctx)
+        return self
+
+    def result(self) -> BatchResult:
+        memb = louvain_memberships(self.ctx, n=self.n)
+        res, q, pr = louvain_batch_results(self.ctx, self.G, self.cfg.max_passes)
+        return BatchResult(memb, self.vo, q, res, pr)
+
+    def stats(self) -> dict:
+        return louvain_stats(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            louvain_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
