@@ -47,6 +47,9 @@ WORKLOADS = {
     "rmat27": dict(kind="rmat", scale=27, ef=16, seed=13, desc="R-MAT scale 27, edge factor 16, "
                    "(a,b,c,d)=(0.57,0.19,0.19,0.05), symmetrised, deduplicated, no self-loops, unit int32 weights, "
                    "seed 13 (learned-skip evaluation graph)"),
+    "bsbm4096": dict(kind="batch", G=4096, first=0, desc="batch of 4,096 planted-partition SBM graphs, vertex "
+                     "counts log-uniform in 200-200,000, mean degree uniform in 8-32, blocks of 50, mixing ratio "
+                     "uniform in 0.1-0.4, unit int32 weights, seeds 0-4095, one batched context"),
 }
 # bounded CPU-oracle samples: the same generator at a smaller size.  The
 # CPU-baseline leg of a GPU run times one oracle run of SAMPLES; the reference
@@ -56,20 +59,25 @@ REF_SAMPLES = {
     "grid8192": dict(kind="grid", side=1024, frac=0.02, seed=11, desc="1024x1024 grid (same generator)"),
     "sbm1000": dict(kind="sbm", n=1000, block=100, p_in=0.1, p_out=0.002, seed=1, desc="the full workload"),
     "rmat27": dict(kind="rmat", scale=20, ef=16, seed=13, desc="R-MAT scale 20 (same generator and parameters)"),
+    "bsbm4096": dict(kind="batch", G=48, first=0, desc="graphs 0-47 of the batch, one oracle run each"),
 }
 SAMPLES = {
     "rmat24": dict(kind="rmat", scale=21, ef=16, seed=7, desc="R-MAT scale 21 (same generator and parameters)"),
     "grid8192": dict(kind="grid", side=1448, frac=0.02, seed=11, desc="1448x1448 grid (same generator)"),
     "sbm1000": dict(kind="sbm", n=1000, block=100, p_in=0.1, p_out=0.002, seed=1, desc="the full workload"),
+    "bsbm4096": dict(kind="batch", G=256, first=0, desc="graphs 0-255 of the batch, one oracle run each"),
 }
 
 
 # timing groups that are one kernel per launch (candidates for the roofline)
-SINGLE_KERNELS = {"select", "move_thread", "move_warp", "move_mid", "move_block", "move_hub", "apply",
+SINGLE_KERNELS = {"select", "move_thread", "move_group", "move_warp", "move_mid", "move_block", "move_hub", "apply",
                   "pass_init", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big", "dendrogram"}
 
 
 def make_graph(w):
+    """The workload's graph; for a batch, (union CSR, vertex offsets)."""
+    if w["kind"] == "batch":
+        return gg.batched_sbm_union(w["G"], w.get("first", 0))
     if w["kind"] == "rmat":
         return gg.rmat(w["scale"], w["ef"], seed=w["seed"])
     if w["kind"] == "grid":
@@ -128,14 +136,25 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-def oracle_steps(g, steps: int, warmup: int):
+def sample_graphs(w):
+    """(list of graphs, total entries) of a CPU-oracle sample."""
+    if w["kind"] == "batch":
+        gs = [gg.batched_sbm(k) for k in range(w.get("first", 0), w.get("first", 0) + w["G"])]
+    else:
+        gs = [make_graph(w)]
+    return gs, sum(x.nnz for x in gs)
+
+
+def oracle_steps(gs, steps: int, warmup: int):
     import oracle
     cfg = oracle.Config()
     for _ in range(warmup):
-        oracle.louvain(g, cfg)
+        for g in gs:
+            oracle.louvain(g, cfg)
     t0 = time.perf_counter()
     for _ in range(steps):
-        oracle.louvain(g, cfg)
+        for g in gs:
+            oracle.louvain(g, cfg)
     dt = time.perf_counter() - t0
     return dt, oracle.num_threads()
 
@@ -145,16 +164,16 @@ def run_reference(args, wname):
     if rank != 0:
         return 0
     sample = REF_SAMPLES[wname]
-    g = make_graph(sample)
-    dt, cores = oracle_steps(g, args.steps, args.warmup)
-    value = g.nnz * args.steps / dt / 1e6
+    gs, nnz = sample_graphs(sample)
+    dt, cores = oracle_steps(gs, args.steps, args.warmup)
+    value = nnz * args.steps / dt / 1e6
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic", "config": {"workload": WORKLOADS[wname]["desc"], "sample": sample["desc"]},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{sample['desc']}: {g.nnz} entries, whole run per step"},
+                         "sample": f"{sample['desc']}: {nnz} entries, whole run per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -174,6 +193,9 @@ def main():
     ap.add_argument("--skip-threshold", type=float, default=0.8)
     ap.add_argument("--skip-clears", type=int, default=1)
     ap.add_argument("--learned-fallback", type=int, default=0)
+    ap.add_argument("--graphs", type=int, default=0, help="batch workloads: run only the first N graphs")
+    ap.add_argument("--sequential-sample", type=int, default=256,
+                    help="batch workloads: graphs run one context at a time for comparison")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -197,12 +219,24 @@ def main():
         if world > 1:
             dist.barrier()
 
-    w = WORKLOADS[args.workload]
-    g = make_graph(w)
+    w = dict(WORKLOADS[args.workload])
+    batch = w["kind"] == "batch"
+    if batch and args.graphs:
+        w["G"] = args.graphs
+        w["desc"] += f" (first {args.graphs} graphs only)"
+    vo = None
+    if batch:
+        g, vo = make_graph(w)
+    else:
+        g = make_graph(w)
     dg = lv.DeviceCSR.from_host(g, dev)
     torch.cuda.synchronize()
+
+    def new_ctx(graph, cfg=None):
+        return lv.LouvainBatch(graph, vo, cfg) if batch else lv.Louvain(graph, cfg)
+
     all_mask = (1 << len(lv.KERNELS)) - 1
-    ctx = lv.Louvain(dg, lv.Config(profile_mask=all_mask))
+    ctx = new_ctx(dg, lv.Config(profile_mask=all_mask))
     # warm-up 1: every kernel group timed, to find the dominant kernel
     ctx.run()
     prof = ctx.stats()["kernels"]
@@ -243,7 +277,12 @@ def main():
 
     # learned-skip leg: the same workload and step count with the predictor
     learned = None
-    if not args.no_learned:
+    if batch:
+        summary = {"modularity_mean": float(np.mean(res.modularity)), "communities": int(res.summary[:, 1].sum()),
+                   "passes_max": int(res.summary[:, 0].max()), "graphs": int(vo.shape[0] - 1)}
+    else:
+        summary = {"modularity": res.modularity, "communities": res.communities, "passes": res.passes}
+    if not args.no_learned and not batch:
         from paper_2501_19004_gb300 import predictor
         model = predictor.load_default()
         source = "stored model (R-MAT 20-22 traces)"
@@ -287,12 +326,13 @@ def main():
         host = gg.CSR(off_p.numpy(), col_p.numpy(), None)
         memb_p = torch.empty(g.n, dtype=torch.int32).pin_memory()
         ctx.close()
-        lv.run(host)  # warm the allocator pool
+        with new_ctx(host) as c2:  # warm the allocator pool
+            c2.run()
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            with lv.Louvain(host) as c2:
+            with new_ctx(host) as c2:
                 c2.run()
                 lv.louvain_memberships(c2.ctx, memb_p.numpy())
         torch.cuda.synchronize()
@@ -325,13 +365,40 @@ def main():
                 "algorithmic_bytes_per_launch": dom_bytes / max(dom_launches, 1),
                 "avg_launch_ms": dom_ms / max(dom_launches, 1), "launches": dom_launches}
 
+    # batch only: the same graphs one context at a time (a strided sample),
+    # the way a single-graph library would run them
+    sequential = None
+    if batch and args.sequential_sample > 0:
+        G = int(vo.shape[0] - 1)
+        stride = max(1, G // args.sequential_sample)
+        picks = list(range(0, G, stride))[:args.sequential_sample]
+        seq_ms = 0.0
+        seq_nnz = 0
+        for k in picks:
+            a, b = int(vo[k]), int(vo[k + 1])
+            ea, eb = int(g.offsets[a]), int(g.offsets[b])
+            sub_g = lv.DeviceCSR((dg.offsets[a:b + 1] - ea).contiguous(), (dg.cols[ea:eb] - a).contiguous())
+            with lv.Louvain(sub_g) as c1:
+                c1.run()
+                s0 = torch.cuda.Event(enable_timing=True)
+                s1 = torch.cuda.Event(enable_timing=True)
+                s0.record(stream)
+                c1.run()
+                s1.record(stream)
+                torch.cuda.synchronize()
+                seq_ms += s0.elapsed_time(s1)
+            seq_nnz += sub_g.nnz
+        sequential = {"value": seq_nnz / (seq_ms / 1e3) / 1e6, "unit": UNIT, "graphs": len(picks),
+                      "stride": stride, "ms_total": seq_ms,
+                      "note": "each sampled graph in its own context, one louvain_run each"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample = SAMPLES[args.workload]
-        gs = make_graph(sample)
+        gs, snnz = sample_graphs(sample)
         dt, cores = oracle_steps(gs, 1, 0)
-        cpu = {"value": gs.nnz / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{sample['desc']}: {gs.nnz} entries, one whole run, {dt:.1f} s"}
+        cpu = {"value": snnz / dt / 1e6, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{sample['desc']}: {snnz} entries, one whole run per graph, {dt:.1f} s"}
 
     if rank == 0:
         line = {
@@ -341,9 +408,9 @@ def main():
             "config": {"workload": w["desc"], "n": g.n, "edges_directed": g.nnz, "mode": "plain",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "l2": f"inputs larger than L2 (CSR {(g.offsets.nbytes + g.cols.nbytes) / 1e9:.2f} GB), no flush",
-                       "modularity": res.modularity, "communities": res.communities, "passes": res.passes},
+                       **summary},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
-            "learned_skip": learned,
+            "learned_skip": learned, "sequential": sequential,
             "phases_ms": {"move": st["move_ms"], "aggregate": st["aggregate_ms"], "other": st["other_ms"]},
             "kernels_ms_warmup": {k: round(v["ms"], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
         }

@@ -46,7 +46,7 @@ struct Counters {
   unsigned long long it_moves;
   unsigned long long it_evaluated;
   unsigned long long it_skipped;    // learned mode: flagged vertices skipped by the predictor
-  unsigned long long mv_work[5][5]; // per move bin: vertices, entries, distinct keys, movers, mover entries
+  unsigned long long mv_work[6][5]; // per move bin: vertices, entries, distinct keys, movers, mover entries
   // ---- zeroed every pass ----
   unsigned long long mbin_count[8]; // aggregation bin sizes
   unsigned long long mg_work[5][4]; // per merge bin: communities, members, entries, entries written
@@ -63,7 +63,7 @@ struct Counters {
   unsigned long long trace_count;   // recorded (features, moved) samples
   unsigned long long pad[2];
 };
-constexpr int kIterCounterWords = 5 + 25;
+constexpr int kIterCounterWords = 5 + 30;
 
 // MurmurHash3 finaliser (Appleby, public domain).
 __host__ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
@@ -119,6 +119,24 @@ __device__ __forceinline__ void warp_argmax(long long &s, int32_t &c) {
     int32_t c2 = __shfl_xor_sync(0xFFFFFFFFu, c, o);
     if (better(s2, c2, s, c)) { s = s2; c = c2; }
   }
+}
+
+// Argmax and sum over aligned groups of W lanes (W a power of two <= 32).
+template <int W>
+__device__ __forceinline__ void group_argmax(long long &s, int32_t &c) {
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) {
+    long long s2 = __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    int32_t c2 = __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    if (better(s2, c2, s, c)) { s = s2; c = c2; }
+  }
+}
+
+template <int W>
+__device__ __forceinline__ long long group_sum(long long v) {
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
 }
 
 __device__ __forceinline__ long long warp_sum(long long v) {

@@ -26,6 +26,18 @@ __host__ __device__ __forceinline__ int degree_bin(int64_t d) {
   return d <= kThreadMaxDeg ? 0 : d <= kWarpMaxDeg ? 1 : d <= kMidMaxDeg ? 2 : d <= kBlockMaxDeg ? 3 : 4;
 }
 
+// Local moving splits the warp bin: 16 < degree <= kGroupMaxDeg goes to
+// groups of kGroupLanes lanes (several vertices per warp), the rest of the
+// warp bin to whole warps.  The group bin is numbered after the others.
+constexpr int kGroupLanes = 8;
+constexpr int kGroupMaxDeg = 64;  // kGroupLanes lanes x 8 entries
+constexpr int kGroupBin = 5;
+constexpr int kMoveBins = 6;
+
+__host__ __device__ __forceinline__ int move_bin(int64_t d) {
+  return (d > kThreadMaxDeg && d <= kGroupMaxDeg) ? kGroupBin : degree_bin(d);
+}
+
 // Global tables of big items (hub vertices in local moving, communities with
 // more than kBlockMaxDeg entries in aggregation).  Tables are kept empty
 // between uses: the kernels that read a slot also clear it.
@@ -155,7 +167,7 @@ struct MoveArgs {
   uint32_t salt;
   uint32_t nbuckets;
   uint32_t bucket;
-  int32_t *bins[kNumBins];
+  int32_t *bins[kMoveBins];
   int32_t *mv_vertex;
   int32_t *mv_target;
   Counters *ctr;
@@ -167,7 +179,7 @@ struct MoveArgs {
 enum KernelId : int {
   K_SELECT = 0, K_MOVE_THREAD, K_MOVE_WARP, K_MOVE_MID, K_MOVE_BLOCK, K_MOVE_HUB, K_APPLY, K_PASS_INIT,
   K_COMM_COUNT, K_SCATTER, K_MERGE_THREAD, K_MERGE_WARP, K_MERGE_MID, K_MERGE_BLOCK, K_MERGE_BIG, K_DENDRO,
-  K_MODULARITY, K_RENUMBER, K_MOVE_HUB_EVAL, K_MERGE_BIG_EMIT, K_MLP_SELECT, K_NUM_KERNELS
+  K_MODULARITY, K_RENUMBER, K_MOVE_HUB_EVAL, K_MERGE_BIG_EMIT, K_MLP_SELECT, K_MOVE_GROUP, K_NUM_KERNELS
 };
 extern const char *const kKernelNames[K_NUM_KERNELS];
 

@@ -53,7 +53,7 @@ struct louvain_ctx {
   int64_t *K = nullptr, *Kalt = nullptr, *Sigma = nullptr;
   uint8_t *flag = nullptr;
   // local moving
-  int32_t *bins[kNumBins] = {};
+  int32_t *bins[kMoveBins] = {};
   int32_t *mv_vertex = nullptr, *mv_target = nullptr;
   // aggregation
   unsigned long long *cnt = nullptr, *cdeg = nullptr;
@@ -306,14 +306,14 @@ void put128(int64_t *dst, i128 v) {
 void account_move(louvain_ctx *x, int64_t n, const Counters &h) {
   if (x->prof.mask) x->prof.collect();
   const double wb = x->cur_wbytes;
-  for (int b = 0; b < kNumBins; ++b) {
+  for (int b = 0; b < kMoveBins; ++b) {
     const unsigned long long *w = h.mv_work[b];
     if (b == kBigBin) {  // entries in the accumulation kernel, the rest in evaluation
       x->kbytes[K_MOVE_HUB] += (8.0 + wb) * w[1];
       x->kbytes[K_MOVE_HUB_EVAL] += 40.0 * w[0] + 8.0 * w[2] + 8.0 * w[3] + 1.0 * w[4];
       continue;
     }
-    x->kbytes[K_MOVE_THREAD + b] +=
+    x->kbytes[b == kGroupBin ? K_MOVE_GROUP : K_MOVE_THREAD + b] +=
         40.0 * w[0] + (8.0 + wb) * w[1] + 8.0 * w[2] + 8.0 * w[3] + 1.0 * w[4];
   }
   x->kbytes[K_SELECT] += (double)x->cfg.buckets * n + 21.0 * h.it_evaluated;
@@ -445,7 +445,7 @@ louvain_status move_iteration(louvain_ctx *x, const GView &g, int wk, int pass, 
     a.pickless = pickless;
     a.salt = bucket_salt(pass, t, cfg.schedule_seed);
     a.nbuckets = (uint32_t)cfg.buckets;
-    for (int k = 0; k < kNumBins; ++k) a.bins[k] = x->bins[k];
+    for (int k = 0; k < kMoveBins; ++k) a.bins[k] = x->bins[k];
     a.mv_vertex = x->mv_vertex;
     a.mv_target = x->mv_target;
     a.ctr = x->d_ctr;
@@ -1127,7 +1127,7 @@ louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg
   if ((st = dalloc_n(x, &x->C, nv)) || (st = dalloc_n(x, &x->Cp, nv)) || (st = dalloc_n(x, &x->K, nv)) ||
       (st = dalloc_n(x, &x->Kalt, nv)) || (st = dalloc_n(x, &x->Sigma, nv)) || (st = dalloc_n(x, &x->flag, nv)))
     return fail(st);
-  for (int k = 0; k < kNumBins; ++k)
+  for (int k = 0; k < kMoveBins; ++k)
     if ((st = dalloc_n(x, &x->bins[k], nv))) return fail(st);
   if ((st = dalloc_n(x, &x->mv_vertex, nv)) || (st = dalloc_n(x, &x->mv_target, nv))) return fail(st);
   if ((st = dalloc_n(x, &x->cnt, nv)) || (st = dalloc_n(x, &x->cdeg, nv)) || (st = dalloc_n(x, &x->newid, nv + 1)) ||

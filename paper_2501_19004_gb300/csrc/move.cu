@@ -29,13 +29,13 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 // ------------------------------------------------------------------ select
 // Block-aggregated appends: one global atomic per bin per block and tile.
 __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
-  __shared__ unsigned s_cnt[kNumBins + 1];
-  __shared__ unsigned long long s_base[kNumBins];
+  __shared__ unsigned s_cnt[kMoveBins + 1];
+  __shared__ unsigned long long s_base[kMoveBins];
   const int64_t n = a.g.n;
   const int lane = threadIdx.x & 31;
   const bool pow2 = (a.nbuckets & (a.nbuckets - 1)) == 0;
   for (int64_t tile = (int64_t)blockIdx.x * blockDim.x; tile < n; tile += (int64_t)gridDim.x * blockDim.x) {
-    if (threadIdx.x <= kNumBins) s_cnt[threadIdx.x] = 0;
+    if (threadIdx.x <= kMoveBins) s_cnt[threadIdx.x] = 0;
     __syncthreads();
     const int64_t i = tile + threadIdx.x;
     int bin = -1;
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
           a.flag[i] = 0;
           sel = true;
           const int64_t deg = a.g.end[i] - a.g.begin[i];
-          if (deg > 0) bin = degree_bin(deg);
+          if (deg > 0) bin = move_bin(deg);
         }
       }
     }
@@ -72,24 +72,24 @@ __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
         if (cand) a.learn.cand[base + __popc(cmask & lanemask_lt())] = (int32_t)i;
       }
     }
-    unsigned woff[kNumBins];
-    unsigned bmask[kNumBins];
+    unsigned woff[kMoveBins];
+    unsigned bmask[kMoveBins];
 #pragma unroll
-    for (int b = 0; b < kNumBins; ++b) {
+    for (int b = 0; b < kMoveBins; ++b) {
       bmask[b] = __ballot_sync(kFull, bin == b);
       woff[b] = 0;
       if (lane == 0 && bmask[b]) woff[b] = atomicAdd(&s_cnt[b], (unsigned)__popc(bmask[b]));
     }
     const unsigned smask = __ballot_sync(kFull, sel);
-    if (lane == 0 && smask) atomicAdd(&s_cnt[kNumBins], (unsigned)__popc(smask));
+    if (lane == 0 && smask) atomicAdd(&s_cnt[kMoveBins], (unsigned)__popc(smask));
     __syncthreads();
-    if (threadIdx.x < kNumBins && s_cnt[threadIdx.x])
+    if (threadIdx.x < kMoveBins && s_cnt[threadIdx.x])
       s_base[threadIdx.x] = atomicAdd(&a.ctr->bin_count[threadIdx.x], (unsigned long long)s_cnt[threadIdx.x]);
-    if (threadIdx.x == kNumBins && s_cnt[kNumBins])
-      atomicAdd(&a.ctr->it_evaluated, (unsigned long long)s_cnt[kNumBins]);
+    if (threadIdx.x == kMoveBins && s_cnt[kMoveBins])
+      atomicAdd(&a.ctr->it_evaluated, (unsigned long long)s_cnt[kMoveBins]);
     __syncthreads();
 #pragma unroll
-    for (int b = 0; b < kNumBins; ++b) {
+    for (int b = 0; b < kMoveBins; ++b) {
       const unsigned off = __shfl_sync(kFull, woff[b], 0);
       if (bin == b) a.bins[b][s_base[b] + off + __popc(bmask[b] & lanemask_lt())] = (int32_t)i;
     }
@@ -135,14 +135,14 @@ __global__ void __launch_bounds__(256) k_mlp_select(MoveArgs a) {
     if (eval) {
       a.flag[mine] = 0;
       const int64_t deg = a.g.end[mine] - a.g.begin[mine];
-      if (deg > 0) bin = degree_bin(deg);
+      if (deg > 0) bin = move_bin(deg);
       ++evaluated;
     } else if (mine >= 0) {
       ++skipped;
       if (a.learn.skip_clears) a.flag[mine] = 0;
     }
 #pragma unroll
-    for (int b = 0; b < kNumBins; ++b) {
+    for (int b = 0; b < kMoveBins; ++b) {
       const unsigned m = __ballot_sync(kFull, bin == b);
       if (!m) continue;
       const int leader = __ffs(m) - 1;
@@ -273,15 +273,26 @@ __device__ __forceinline__ void gather_run(const MoveArgs &a, int32_t i, int64_t
 }
 
 // ------------------------------------------------------------------ warp bin
-// 16 < degree <= 256: one warp, a shared table of up to 512 slots; lanes read
+// 64 < degree <= 256: one warp, a shared table of up to 512 slots; lanes read
 // consecutive entries, up to 8 rounds of 32.
 template <int WK, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_move_warp(MoveArgs a) {
+__global__ void __launch_bounds__(WARPS * 32, 4) k_move_warp(MoveArgs a) {
   __shared__ int32_t skeys[WARPS][kWarpCap];
   __shared__ uint32_t svals[WARPS][kWarpCap];
+  __shared__ uint16_t socc[WARPS][kWarpCap];
+  __shared__ unsigned snocc[WARPS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t *keys = skeys[warp];
   uint32_t *vals = svals[warp];
+  uint16_t *occ = socc[warp];
+  unsigned *nocc = &snocc[warp];
+  // empty tables; each vertex clears the slots it occupied
+  for (int s = lane; s < kWarpCap; s += 32) {
+    keys[s] = kEmpty;
+    vals[s] = 0;
+  }
+  if (lane == 0) *nocc = 0;
+  __syncwarp();
   const unsigned long long cnt = a.ctr->bin_count[1];
   unsigned long long glo = 0, ghi = 0, gm = 0;
   unsigned long long work[5] = {0, 0, 0, 0, 0};
@@ -290,22 +301,14 @@ __global__ void __launch_bounds__(WARPS * 32) k_move_warp(MoveArgs a) {
     const int32_t i = a.bins[1][idx];
     const int64_t b = a.g.begin[i], e = a.g.end[i];
     const int64_t deg = e - b;
-    const uint32_t cap = pow2_at_least(2 * (uint64_t)deg);
-    const uint32_t mask = cap - 1;
-    for (uint32_t s = lane; s < cap; s += 32) {
-      keys[s] = kEmpty;
-      vals[s] = 0;
-    }
-    __syncwarp();
+    const uint32_t mask = kWarpCap - 1;
     for (int64_t x0 = 0; x0 < deg; x0 += 32 * kRun) {
       int32_t kk[kRun];
       uint32_t ww[kRun];
       gather_run<WK>(a, i, b, x0 + lane, 32, deg, kk, ww);
 #pragma unroll
-      for (int u = 0; u < kRun; ++u) {
-        if (x0 + u * 32 >= deg) break;  // warp-uniform
-        warp_insert_sm(keys, vals, mask, kk[u], ww[u], a.ctr);
-      }
+      for (int u = 0; u < kRun; ++u)
+        if (x0 + u * 32 < deg) warp_insert_sm_list(keys, vals, mask, kk[u], ww[u], occ, nocc, a.ctr);  // warp-uniform
     }
     __syncwarp();
     const int32_t d = a.Cp[i];
@@ -313,10 +316,13 @@ __global__ void __launch_bounds__(WARPS * 32) k_move_warp(MoveArgs a) {
     const long long tm = vertex_two_m(a.batch, a.two_m, i);
     long long best_s = LLONG_MIN, Kid = 0;
     int32_t best_c = INT_MAX;
-    for (uint32_t s = lane; s < cap; s += 32) {
+    const unsigned nk = *(volatile unsigned *)nocc;
+    for (unsigned t = lane; t < nk; t += 32) {
+      const uint32_t s = occ[t];
       const int32_t c = keys[s];
-      if (c == kEmpty) continue;
       const long long v = vals[s];
+      keys[s] = kEmpty;
+      vals[s] = 0;
       if (c == d) {
         Kid = v;
         continue;
@@ -328,6 +334,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_move_warp(MoveArgs a) {
         best_c = c;
       }
     }
+    __syncwarp();
+    if (lane == 0) *nocc = 0;
     warp_argmax(best_s, best_c);
     Kid = warp_sum(Kid);
     int32_t target = -1;
@@ -359,6 +367,121 @@ __global__ void __launch_bounds__(WARPS * 32) k_move_warp(MoveArgs a) {
   }
   flush_gains(glo, ghi, gm, a.ctr);
   flush_work(work, a.ctr->mv_work[1]);
+}
+
+// ----------------------------------------------------------------- group bin
+// 16 < degree <= 64: GS lanes per vertex, 32 / GS vertices per warp, each
+// group with a shared table of up to 2 * GS * kRun slots; every lane reads up
+// to kRun entries strided by GS.  Several vertices per warp keep more
+// independent row and community reads in flight than a warp per vertex.
+template <int WK, int GS, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 4) k_move_group(MoveArgs a) {
+  constexpr int kGroups = 32 / GS;
+  constexpr int kSlots = 2 * GS * kRun;
+  static_assert(GS * kRun >= kGroupMaxDeg, "a group must hold a whole row");
+  __shared__ int32_t skeys[WARPS * kGroups][kSlots];
+  __shared__ uint32_t svals[WARPS * kGroups][kSlots];
+  __shared__ uint16_t socc[WARPS * kGroups][kSlots];
+  __shared__ unsigned snocc[WARPS * kGroups];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / GS, gl = lane % GS;
+  int32_t *keys = skeys[warp * kGroups + grp];
+  uint32_t *vals = svals[warp * kGroups + grp];
+  uint16_t *occ = socc[warp * kGroups + grp];
+  unsigned *nocc = &snocc[warp * kGroups + grp];
+  // the tables start empty and every vertex leaves its table empty: only
+  // the occupied slots are visited and cleared
+  for (int s = gl; s < kSlots; s += GS) {
+    keys[s] = kEmpty;
+    vals[s] = 0;
+  }
+  if (gl == 0) *nocc = 0;
+  __syncwarp();
+  const unsigned long long cnt = a.ctr->bin_count[kGroupBin];
+  unsigned long long glo = 0, ghi = 0, gm = 0;
+  unsigned long long work[5] = {0, 0, 0, 0, 0};
+  const unsigned long long stride = (unsigned long long)gridDim.x * WARPS * kGroups;
+  for (unsigned long long base = ((unsigned long long)blockIdx.x * WARPS + warp) * kGroups; base < cnt;
+       base += stride) {
+    const unsigned long long idx = base + grp;
+    const bool act = idx < cnt;
+    const int32_t i = act ? a.bins[kGroupBin][idx] : 0;
+    const int64_t b = act ? a.g.begin[i] : 0;
+    const int64_t deg = act ? a.g.end[i] - b : 0;
+    const int32_t d = act ? a.Cp[i] : 0;
+    const long long Ki = act ? a.K[i] : 0;
+    const long long tm = act ? vertex_two_m(a.batch, a.two_m, i) : 0;
+    if (act) {
+      int32_t kk[kRun];
+      uint32_t ww[kRun];
+      gather_run<WK>(a, i, b, gl, GS, deg, kk, ww);
+#pragma unroll
+      for (int u = 0; u < kRun; ++u)
+        if (kk[u] != kEmpty) sm_insert_list(keys, vals, kSlots - 1, kk[u], ww[u], occ, nocc, a.ctr);
+    }
+    __syncwarp();
+    const unsigned nk = *(volatile unsigned *)nocc;
+    long long best_s = LLONG_MIN, Kid = 0;
+    int32_t best_c = INT_MAX;
+    for (unsigned t = gl; t < nk; t += GS) {
+      const uint32_t s = occ[t];
+      const int32_t c = keys[s];
+      const long long v = vals[s];
+      keys[s] = kEmpty;
+      vals[s] = 0;
+      if (c == d) {
+        Kid = v;
+        continue;
+      }
+      ++work[2];
+      const long long sc = tm * v - Ki * a.Sigma[c];
+      if (better(sc, c, best_s, best_c)) {
+        best_s = sc;
+        best_c = c;
+      }
+    }
+    __syncwarp();
+    if (gl == 0) *nocc = 0;
+    group_argmax<GS>(best_s, best_c);
+    Kid = group_sum<GS>(Kid);
+    int32_t target = -1;
+    if (act && gl == 0) {
+      long long s_d = 0;
+      target = finish_decision(tm, a.Sigma, a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm, &s_d);
+      learn_record(a.learn, a.ctr, a.g, a.Cp, a.Sigma, a.two_m, i, Ki, Kid, best_s, best_c, s_d, target >= 0);
+      if (target >= 0) batch_gain(a.batch, i, best_s, s_d);
+      work[0] += 1;
+      work[1] += (unsigned long long)deg;
+      if (target >= 0) {
+        work[3] += 1;
+        work[4] += (unsigned long long)deg;
+      }
+    }
+    // one append per warp for the movers of its groups
+    const unsigned mmask = __ballot_sync(kFull, target >= 0);
+    if (mmask) {
+      const int leader = __ffs(mmask) - 1;
+      unsigned long long pos = 0;
+      if (lane == leader) pos = atomicAdd(&a.ctr->movers, (unsigned long long)__popc(mmask));
+      pos = __shfl_sync(kFull, pos, leader) + __popc(mmask & lanemask_lt());
+      if (target >= 0) {
+        a.mv_vertex[pos] = i;
+        a.mv_target[pos] = target;
+      }
+    }
+    target = __shfl_sync(kFull, target, grp * GS);
+    if (target >= 0)
+      for (int64_t k = b + gl; k < b + deg; k += GS) {
+        const int32_t j = __ldg(a.g.col + k);
+        if (j != i) {
+          a.flag[j] = 1;
+          learn_mark(a.learn, j);
+        }
+      }
+    __syncwarp();
+  }
+  flush_gains(glo, ghi, gm, a.ctr);
+  flush_work(work, a.ctr->mv_work[kGroupBin]);
 }
 
 // ---------------------------------------------------------------- block bins
@@ -534,6 +657,7 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
   LV_TIMED(prof, K_SELECT, s, k_select<<<grid_for(a.g.n, 256, num_sms, 8), 256, 0, s>>>(a));
   if (a.learn.enabled) LV_TIMED(prof, K_MLP_SELECT, s, k_mlp_select<<<num_sms * 4, 256, 0, s>>>(a));
   LV_TIMED(prof, K_MOVE_THREAD, s, k_move_thread<WK><<<num_sms * 8, 256, 0, s>>>(a));
+  LV_TIMED(prof, K_MOVE_GROUP, s, k_move_group<WK, kGroupLanes, 8><<<num_sms * 7, 256, 0, s>>>(a));
   LV_TIMED(prof, K_MOVE_WARP, s, k_move_warp<WK, 8><<<num_sms * 7, 256, 0, s>>>(a));
   LV_TIMED(prof, K_MOVE_MID, s, k_move_block<WK, 128, kMidCap, 2><<<num_sms * 12, 128, kMidSmem, s>>>(a));
   LV_TIMED(prof, K_MOVE_BLOCK, s, k_move_block<WK, 512, kBlockCap, 3><<<num_sms * 3, 512, kBlockSmem, s>>>(a));
@@ -573,6 +697,6 @@ void iota_i32(int32_t *x, int64_t n, int num_sms, cudaStream_t s) {
 const char *const kKernelNames[K_NUM_KERNELS] = {
     "select", "move_thread", "move_warp", "move_mid", "move_block", "move_hub", "apply", "pass_init",
     "comm_count", "comm_scatter", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big",
-    "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit", "mlp_select"};
+    "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit", "mlp_select", "move_group"};
 
 }  // namespace lv

@@ -30,6 +30,32 @@ __device__ __forceinline__ void sm_insert(int32_t *keys, uint32_t *vals, uint32_
   atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
 }
 
+// sm_insert that also appends a slot it claims for a new key to the table's
+// occupied list (occ, *nocc), so that readers visit and clear only the
+// occupied slots.
+__device__ __forceinline__ void sm_insert_list(int32_t *keys, uint32_t *vals, uint32_t mask, int32_t key, uint32_t w,
+                                               uint16_t *occ, unsigned *nocc, Counters *ctr) {
+  uint32_t s = slot_of(key, mask);
+  for (uint32_t t = 0; t <= mask; ++t) {
+    int32_t k = ((volatile int32_t *)keys)[s];
+    bool claimed = false;
+    if (k == kEmpty) {
+      k = atomicCAS(keys + s, kEmpty, key);
+      if (k == kEmpty) {
+        k = key;
+        claimed = true;
+      }
+    }
+    if (k == key) {
+      atomicAdd(vals + s, w);
+      if (claimed) occ[atomicAdd(nocc, 1u)] = (uint16_t)s;
+      return;
+    }
+    s = (s + 1) & mask;
+  }
+  atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
+}
+
 // Global tables have any capacity `cap` (see big_table_cap).
 __device__ __forceinline__ void gm_insert(int32_t *keys, uint32_t *vals, uint32_t cap, int32_t key, uint32_t w,
                                           Counters *ctr) {
@@ -96,6 +122,28 @@ __device__ __forceinline__ void warp_insert_sm(int32_t *keys, uint32_t *vals, ui
     }
   } else if (key != kEmpty) {
     sm_insert(keys, vals, mask, key, w, ctr);
+  }
+}
+
+// warp_insert_sm with the occupied list of sm_insert_list.
+__device__ __forceinline__ void warp_insert_sm_list(int32_t *keys, uint32_t *vals, uint32_t mask, int32_t key,
+                                                    uint32_t w, uint16_t *occ, unsigned *nocc, Counters *ctr) {
+  const unsigned full = 0xFFFFFFFFu;
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(full, key);
+  const bool lead = lane == __ffs(peers) - 1;
+  const unsigned leaders = __ballot_sync(full, lead && key != kEmpty);
+  if (__popc(leaders) <= 4) {
+    unsigned todo = leaders;
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int32_t k0 = __shfl_sync(full, key, src);
+      const uint32_t sum = __reduce_add_sync(full, key == k0 ? w : 0u);
+      if (lane == src) sm_insert_list(keys, vals, mask, k0, sum, occ, nocc, ctr);
+    }
+  } else if (key != kEmpty) {
+    sm_insert_list(keys, vals, mask, key, w, occ, nocc, ctr);
   }
 }
 

@@ -62,6 +62,8 @@ def _load():
             lib.gg_copy.argtypes = [vp, vp, vp, vp]
             lib.gg_free.restype = None
             lib.gg_free.argtypes = [vp]
+            lib.gg_sbm_union.restype = vp
+            lib.gg_sbm_union.argtypes = [i64, vp, vp, vp, vp, vp, vp]
             lib.gg_splitmix64.restype = u64
             lib.gg_splitmix64.argtypes = [u64, u64]
             lib.gg_num_threads.restype = ctypes.c_int
@@ -213,6 +215,23 @@ def concat(graphs) -> "tuple[CSR, np.ndarray]":
             w[eo[k]:eo[k + 1]] = g.weights if g.weights is not None else 1
     off[int(vo[G])] = eo[G]
     return CSR(off, col, w, f"union{G}"), vo
+
+
+def batched_sbm_union(G: int, first: int = 0):
+    """Union of batched_sbm(first) .. batched_sbm(first + G - 1), generated in
+    parallel; equals concat() of the single graphs.  Returns (CSR, vo)."""
+    lib = _load()
+    prm = [batched_sbm_params(g) for g in range(first, first + G)]
+    n = np.array([p[0] for p in prm], dtype=np.int64)
+    blk = np.array([p[1] for p in prm], dtype=np.int64)
+    pin = np.array([p[2] for p in prm], dtype=np.float64)
+    pout = np.array([p[3] for p in prm], dtype=np.float64)
+    seed = np.arange(first, first + G, dtype=np.uint64)
+    vo = np.zeros(G + 1, dtype=np.int64)
+    h = lib.gg_sbm_union(G, n.ctypes.data, blk.ctypes.data, pin.ctypes.data, pout.ctypes.data, seed.ctypes.data,
+                         vo.ctypes.data)
+    c = _take(h, f"bsbm-union{first}+{G}")
+    return c, vo
 
 
 def num_threads() -> int:

@@ -242,6 +242,51 @@ gg_graph *gg_sbm(int64_t n, int64_t block, double p_in, double p_out, uint64_t s
   return build_csr(n, np, pu, pv, NULL);
 }
 
+/* Union of G planted-partition graphs (gg_sbm with the geometric-skip
+ * sampler), generated in parallel one graph per thread: graph k owns the
+ * vertices [vo[k], vo[k+1]) and its columns are shifted by vo[k].  vo_out
+ * receives G + 1 offsets.  Identical to concatenating gg_sbm's outputs. */
+gg_graph *gg_sbm_union(int64_t G, const int64_t *n, const int64_t *block, const double *p_in, const double *p_out,
+                       const uint64_t *seed, int64_t *vo_out) {
+  if (G < 1) return NULL;
+  gg_graph **parts = (gg_graph **)calloc((size_t)G, sizeof(gg_graph *));
+  int64_t *eo = (int64_t *)calloc((size_t)G + 1, sizeof(int64_t));
+  if (!parts || !eo) { free(parts); free(eo); return NULL; }
+  int fail = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t k = 0; k < G; ++k) {
+    parts[k] = gg_sbm(n[k], block[k], p_in[k], p_out[k], seed[k], 0);
+    if (!parts[k]) __atomic_store_n(&fail, 1, __ATOMIC_RELAXED);
+  }
+  gg_graph *u = fail ? NULL : (gg_graph *)calloc(1, sizeof(gg_graph));
+  if (u) {
+    vo_out[0] = 0;
+    for (int64_t k = 0; k < G; ++k) {
+      vo_out[k + 1] = vo_out[k] + parts[k]->n;
+      eo[k + 1] = eo[k] + parts[k]->nnz;
+    }
+    u->n = vo_out[G];
+    u->nnz = eo[G];
+    u->off = (int64_t *)malloc(((size_t)u->n + 1) * sizeof(int64_t));
+    u->col = (int32_t *)malloc((size_t)(u->nnz > 0 ? u->nnz : 1) * sizeof(int32_t));
+    if (!u->off || !u->col) { free(u->off); free(u->col); free(u); u = NULL; }
+  }
+  if (u) {
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t k = 0; k < G; ++k) {
+      const gg_graph *p = parts[k];
+      const int64_t v0 = vo_out[k], e0 = eo[k];
+      for (int64_t i = 0; i < p->n; ++i) u->off[v0 + i] = p->off[i] + e0;
+      for (int64_t e = 0; e < p->nnz; ++e) u->col[e0 + e] = (int32_t)(p->col[e] + v0);
+    }
+    u->off[u->n] = u->nnz;
+  }
+  for (int64_t k = 0; k < G; ++k) gg_free(parts[k]);
+  free(parts);
+  free(eo);
+  return u;
+}
+
 /* side x side 4-neighbour grid plus round(frac * grid_edges) uniform random
  * long-range pairs; weights uniform integers in [wlo, whi] per unordered pair. */
 gg_graph *gg_grid(int64_t side, double frac, uint64_t seed, int wlo, int whi) {

@@ -28,7 +28,7 @@ STATUS = {0: "OK", 1: "E_INVAL", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_HASH_OVERFLOW"
 MODE_PLAIN, MODE_LEARNED = 0, 1
 KERNELS = ["select", "move_thread", "move_warp", "move_mid", "move_block", "move_hub", "apply", "pass_init",
            "comm_count", "comm_scatter", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big",
-           "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit", "mlp_select"]
+           "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit", "mlp_select", "move_group"]
 
 
 def kernel_mask(*names) -> int:
@@ -499,6 +499,9 @@ class LouvainBatch:
 
     def stats(self) -> dict:
         return louvain_stats(self.ctx)
+
+    def set_profile(self, mask: int):
+        louvain_set_profile(self.ctx, mask)
 
     def close(self):
         if self.ctx:
