@@ -328,12 +328,23 @@ __device__ __forceinline__ void gather_members(const AggArgs &a, int32_t k, int6
 // Warp per community (total degree <= 256): shared table of up to 512 slots,
 // a run of 8 entries per lane.
 template <int WK, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) k_merge_warp(AggArgs a) {
+__global__ void __launch_bounds__(WARPS * 32, 4) k_merge_warp(AggArgs a) {
   __shared__ int32_t skeys[WARPS][kWarpCap];
   __shared__ uint32_t svals[WARPS][kWarpCap];
+  __shared__ uint16_t socc[WARPS][kWarpMaxDeg];
+  __shared__ unsigned snocc[WARPS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t *keys = skeys[warp];
   uint32_t *vals = svals[warp];
+  uint16_t *occ = socc[warp];
+  unsigned *nocc = &snocc[warp];
+  // empty tables; each community clears the slots it occupied
+  for (int s = lane; s < kWarpCap; s += 32) {
+    keys[s] = kEmpty;
+    vals[s] = 0;
+  }
+  if (lane == 0) *nocc = 0;
+  __syncwarp();
   const unsigned long long cnt = a.ctr->mbin_count[1];
   unsigned long long work[4] = {0, 0, 0, 0};
   for (unsigned long long idx = (unsigned long long)blockIdx.x * WARPS + warp; idx < cnt;
@@ -341,41 +352,32 @@ __global__ void __launch_bounds__(WARPS * 32) k_merge_warp(AggArgs a) {
     const int32_t k = a.mbins[1][idx];
     const int64_t ob = a.obegin[k];
     const int64_t tot = a.oend[k] - ob;  // total member degree
-    const uint32_t cap = pow2_at_least(2 * (uint64_t)tot);
-    const uint32_t mask = cap - 1;
-    for (uint32_t s = lane; s < cap; s += 32) {
-      keys[s] = kEmpty;
-      vals[s] = 0;
-    }
-    __syncwarp();
     for (int64_t x0 = 0; x0 < tot; x0 += 32 * kRun) {
       int32_t kk[kRun];
       uint32_t ww[kRun];
       const int64_t xs = x0 + lane * kRun;
       gather_members<WK>(a, k, xs, xs + kRun < tot ? xs + kRun : tot, kk, ww);
 #pragma unroll
-      for (int u = 0; u < kRun; ++u) warp_insert_sm(keys, vals, mask, kk[u], ww[u], a.ctr);
+      for (int u = 0; u < kRun; ++u) warp_insert_sm_list(keys, vals, kWarpCap - 1, kk[u], ww[u], occ, nocc, a.ctr);
     }
     __syncwarp();
-    unsigned long long written = 0;
-    for (uint32_t s0 = 0; s0 < cap; s0 += 32) {
-      const uint32_t s = s0 + lane;
-      const int32_t c = s < cap ? keys[s] : kEmpty;
-      const bool occ = c != kEmpty;
-      const unsigned m = __ballot_sync(0xFFFFFFFFu, occ);
-      if (occ) {
-        const int64_t pos = ob + (int64_t)written + __popc(m & lanemask_lt());
-        a.ocol[pos] = c;
-        a.ow[pos] = vals[s];
-      }
-      written += __popc(m);
+    // the occupied slots are the super-vertex's entries (any order)
+    const unsigned nk = *(volatile unsigned *)nocc;
+    for (unsigned t = lane; t < nk; t += 32) {
+      const uint32_t s = occ[t];
+      a.ocol[ob + t] = keys[s];
+      a.ow[ob + t] = vals[s];
+      keys[s] = kEmpty;
+      vals[s] = 0;
     }
+    __syncwarp();
     if (lane == 0) {
-      a.oend[k] = ob + (int64_t)written;
+      *nocc = 0;
+      a.oend[k] = ob + (int64_t)nk;
       work[0] += 1;
       work[1] += (unsigned long long)a.kcnt[k];
       work[2] += (unsigned long long)tot;
-      work[3] += written;
+      work[3] += nk;
     }
     __syncwarp();
   }
@@ -388,49 +390,50 @@ __global__ void __launch_bounds__(WARPS * 32) k_merge_warp(AggArgs a) {
 // entries, 512 threads and an 8192-slot table up to 4096; a run of 8
 // consecutive entries per thread.
 template <int WK, int NT, int CAP, int BIN>
-__global__ void __launch_bounds__(NT) k_merge_block(AggArgs a) {
+__global__ void __launch_bounds__(NT, NT == 128 ? 8 : 2) k_merge_block(AggArgs a) {
+  // dynamic shared memory: keys[CAP], vals[CAP], occupied list[CAP / 2]
   extern __shared__ uint32_t dyn[];
   int32_t *keys = (int32_t *)dyn;
   uint32_t *vals = dyn + CAP;
-  __shared__ unsigned long long s_written;
+  uint16_t *occ = (uint16_t *)(dyn + 2 * CAP);
+  __shared__ unsigned s_nocc;
+  for (int s = threadIdx.x; s < CAP; s += NT) {
+    keys[s] = kEmpty;
+    vals[s] = 0;
+  }
+  if (threadIdx.x == 0) s_nocc = 0;
+  __syncthreads();
   const unsigned long long cnt = a.ctr->mbin_count[BIN];
   unsigned long long work[4] = {0, 0, 0, 0};
   for (unsigned long long idx = blockIdx.x; idx < cnt; idx += gridDim.x) {
     const int32_t k = a.mbins[BIN][idx];
     const int64_t ob = a.obegin[k];
     const int64_t tot = a.oend[k] - ob;
-    if (threadIdx.x == 0) s_written = 0;
-    const uint64_t distinct = (uint64_t)(tot < a.gamma ? tot : a.gamma);
-    const uint32_t cap = pow2_at_least(2 * distinct);
-    const uint32_t mask = cap - 1;
-    for (uint32_t s = threadIdx.x; s < cap; s += NT) {
-      keys[s] = kEmpty;
-      vals[s] = 0;
-    }
-    __syncthreads();
     for (int64_t x0 = 0; x0 < tot; x0 += (int64_t)NT * kRun) {
       int32_t kk[kRun];
       uint32_t ww[kRun];
       const int64_t xs = x0 + (int64_t)threadIdx.x * kRun;
       gather_members<WK>(a, k, xs, xs + kRun < tot ? xs + kRun : tot, kk, ww);
 #pragma unroll
-      for (int u = 0; u < kRun; ++u) warp_insert_sm(keys, vals, mask, kk[u], ww[u], a.ctr);
+      for (int u = 0; u < kRun; ++u) warp_insert_sm_list(keys, vals, CAP - 1, kk[u], ww[u], occ, &s_nocc, a.ctr);
     }
     __syncthreads();
-    for (uint32_t s = threadIdx.x; s < cap; s += NT) {
-      const int32_t c = keys[s];
-      if (c == kEmpty) continue;
-      const unsigned long long pos = atomicAdd(&s_written, 1ull);
-      a.ocol[ob + (int64_t)pos] = c;
-      a.ow[ob + (int64_t)pos] = vals[s];
+    const unsigned nk = s_nocc;
+    for (unsigned t = threadIdx.x; t < nk; t += NT) {
+      const uint32_t s = occ[t];
+      a.ocol[ob + t] = keys[s];
+      a.ow[ob + t] = vals[s];
+      keys[s] = kEmpty;
+      vals[s] = 0;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      a.oend[k] = ob + (int64_t)s_written;
+      s_nocc = 0;
+      a.oend[k] = ob + (int64_t)nk;
       work[0] += 1;
       work[1] += (unsigned long long)a.kcnt[k];
       work[2] += (unsigned long long)tot;
-      work[3] += s_written;
+      work[3] += nk;
     }
     __syncthreads();
   }
@@ -496,8 +499,8 @@ __global__ void k_relabel(int32_t *x, int64_t n, const int64_t *newid) {
 template <int WK>
 void merge_t(const AggArgs &a, int num_sms, cudaStream_t s, KernelProf *prof) {
   static bool attr_done = false;
-  constexpr size_t kMidSmem = (size_t)kMidCap * (sizeof(uint32_t) + sizeof(int32_t));
-  constexpr size_t kSmem = (size_t)kBlockCap * (sizeof(uint32_t) + sizeof(int32_t));
+  constexpr size_t kMidSmem = (size_t)kMidCap * (sizeof(uint32_t) + sizeof(int32_t)) + kMidCap / 2 * sizeof(uint16_t);
+  constexpr size_t kSmem = (size_t)kBlockCap * (sizeof(uint32_t) + sizeof(int32_t)) + kBlockCap / 2 * sizeof(uint16_t);
   if (!attr_done) {
     cudaFuncSetAttribute(k_merge_block<WK, 512, kBlockCap, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kSmem);

@@ -279,7 +279,7 @@ template <int WK, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 4) k_move_warp(MoveArgs a) {
   __shared__ int32_t skeys[WARPS][kWarpCap];
   __shared__ uint32_t svals[WARPS][kWarpCap];
-  __shared__ uint16_t socc[WARPS][kWarpCap];
+  __shared__ uint16_t socc[WARPS][kWarpMaxDeg];
   __shared__ unsigned snocc[WARPS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t *keys = skeys[warp];
@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_move_group(MoveArgs a) {
   static_assert(GS * kRun >= kGroupMaxDeg, "a group must hold a whole row");
   __shared__ int32_t skeys[WARPS * kGroups][kSlots];
   __shared__ uint32_t svals[WARPS * kGroups][kSlots];
-  __shared__ uint16_t socc[WARPS * kGroups][kSlots];
+  __shared__ uint16_t socc[WARPS * kGroups][kSlots / 2];
   __shared__ unsigned snocc[WARPS * kGroups];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int grp = lane / GS, gl = lane % GS;
@@ -489,11 +489,21 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_move_group(MoveArgs a) {
 // 4096: 512 threads and an 8192-slot table (dynamic shared memory).  Each
 // thread reads 8 entries per round, strided by the block size.
 template <int WK, int NT, int CAP, int BIN>
-__global__ void __launch_bounds__(NT) k_move_block(MoveArgs a) {
+__global__ void __launch_bounds__(NT, NT == 128 ? 8 : 2) k_move_block(MoveArgs a) {
+  // dynamic shared memory: keys[CAP], vals[CAP], occupied list[CAP / 2]
+  // (a row of degree <= CAP / 2 has at most CAP / 2 distinct keys)
   extern __shared__ uint32_t dyn[];
   int32_t *keys = (int32_t *)dyn;
   uint32_t *vals = dyn + CAP;
+  uint16_t *occ = (uint16_t *)(dyn + 2 * CAP);
+  __shared__ unsigned s_nocc;
   __shared__ int32_t s_target;
+  for (int s = threadIdx.x; s < CAP; s += NT) {
+    keys[s] = kEmpty;
+    vals[s] = 0;
+  }
+  if (threadIdx.x == 0) s_nocc = 0;
+  __syncthreads();
   const unsigned long long cnt = a.ctr->bin_count[BIN];
   unsigned long long glo = 0, ghi = 0, gm = 0;
   unsigned long long work[5] = {0, 0, 0, 0, 0};
@@ -501,24 +511,14 @@ __global__ void __launch_bounds__(NT) k_move_block(MoveArgs a) {
     const int32_t i = a.bins[BIN][idx];
     const int64_t b = a.g.begin[i], e = a.g.end[i];
     const int64_t deg = e - b;
-    uint64_t distinct = (uint64_t)deg;
-    if ((uint64_t)a.g.n < distinct) distinct = (uint64_t)a.g.n;
-    const uint32_t cap = pow2_at_least(2 * distinct);
-    const uint32_t mask = cap - 1;
-    for (uint32_t s = threadIdx.x; s < cap; s += NT) {
-      keys[s] = kEmpty;
-      vals[s] = 0;
-    }
-    __syncthreads();
     for (int64_t x0 = 0; x0 < deg; x0 += (int64_t)NT * kRun) {
       int32_t kk[kRun];
       uint32_t ww[kRun];
       gather_run<WK>(a, i, b, x0 + threadIdx.x, NT, deg, kk, ww);
 #pragma unroll
-      for (int u = 0; u < kRun; ++u) {
-        if (x0 + u * NT + (threadIdx.x & ~31) >= deg) break;  // warp-uniform
-        warp_insert_sm(keys, vals, mask, kk[u], ww[u], a.ctr);
-      }
+      for (int u = 0; u < kRun; ++u)
+        if (x0 + u * NT + (threadIdx.x & ~31) < deg)  // warp-uniform
+          warp_insert_sm_list(keys, vals, CAP - 1, kk[u], ww[u], occ, &s_nocc, a.ctr);
     }
     __syncthreads();
     const int32_t d = a.Cp[i];
@@ -526,10 +526,13 @@ __global__ void __launch_bounds__(NT) k_move_block(MoveArgs a) {
     const long long tm = vertex_two_m(a.batch, a.two_m, i);
     long long best_s = LLONG_MIN, Kid = 0;
     int32_t best_c = INT_MAX;
-    for (uint32_t s = threadIdx.x; s < cap; s += NT) {
+    const unsigned nk = s_nocc;
+    for (unsigned t = threadIdx.x; t < nk; t += NT) {
+      const uint32_t s = occ[t];
       const int32_t c = keys[s];
-      if (c == kEmpty) continue;
       const long long v = vals[s];
+      keys[s] = kEmpty;
+      vals[s] = 0;
       if (c == d) {
         Kid = v;
         continue;
@@ -557,6 +560,7 @@ __global__ void __launch_bounds__(NT) k_move_block(MoveArgs a) {
         a.mv_target[pos] = t;
       }
       s_target = t;
+      s_nocc = 0;  // every thread read it before block_argmax_sum's barriers
     }
     __syncthreads();
     if (s_target >= 0)
@@ -647,8 +651,9 @@ __global__ void k_iota(int32_t *x, int64_t n) {
 template <int WK>
 void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStream_t s, KernelProf *prof) {
   static bool attr_done = false;
-  constexpr size_t kMidSmem = (size_t)kMidCap * (sizeof(uint32_t) + sizeof(int32_t));
-  constexpr size_t kBlockSmem = (size_t)kBlockCap * (sizeof(uint32_t) + sizeof(int32_t));
+  constexpr size_t kMidSmem = (size_t)kMidCap * (sizeof(uint32_t) + sizeof(int32_t)) + kMidCap / 2 * sizeof(uint16_t);
+  constexpr size_t kBlockSmem =
+      (size_t)kBlockCap * (sizeof(uint32_t) + sizeof(int32_t)) + kBlockCap / 2 * sizeof(uint16_t);
   if (!attr_done) {
     cudaFuncSetAttribute(k_move_block<WK, 512, kBlockCap, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kBlockSmem);
