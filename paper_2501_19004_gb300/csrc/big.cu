@@ -189,7 +189,7 @@ __device__ __forceinline__ void gather_item(const BigArgs &a, int32_t it, int64_
 }
 
 template <int MODE, int WK>
-__global__ void __launch_bounds__(kNT) k_big_accum(BigArgs a, int r) {
+__global__ void __launch_bounds__(kNT, 3) k_big_accum(BigArgs a, int r) {
   extern __shared__ uint32_t dyn[];
   int32_t *skeys = (int32_t *)dyn;
   uint32_t *svals = dyn + kBigSmemSlots;
@@ -221,26 +221,44 @@ __global__ void __launch_bounds__(kNT) k_big_accum(BigArgs a, int r) {
     __syncthreads();
     const int64_t toff = a.ws.toff[k] - rr.base;
     const uint32_t gcap = table_cap(tot, a.keyspace);
-    // every warp takes 32 consecutive slots per round; when aggregating,
-    // slots claimed in the global table are appended to the item's list with
-    // one atomic per warp (evaluation then visits occupied slots only)
-    for (int s = threadIdx.x; s < kBigSmemSlots; s += kNT) {
-      const int32_t key = skeys[s];
-      int64_t slot = -1;
-      if (key != kEmpty) {
-        if (MODE == MODE_MERGE) slot = gm_insert_claim(a.ws.keys + toff, a.ws.vals + toff, gcap, key, svals[s], a.ctr);
-        else gm_insert(a.ws.keys + toff, a.ws.vals + toff, gcap, key, svals[s], a.ctr);
+    unsigned long long *tab = a.ws.tab + toff;
+    // the chunk's distinct keys go to the item's global table: every thread
+    // first reads the home slots of several keys (independent loads in
+    // flight), then claims or adds to each.
+    // When aggregating, claimed slots are appended to the item's list with
+    // one atomic per warp (emission then visits occupied slots only).
+    constexpr int kPer = 4;  // keys in flight per thread
+    for (int s0 = 0; s0 < kBigSmemSlots; s0 += kPer * kNT) {
+      int32_t key[kPer];
+      uint32_t wv[kPer], home[kPer];
+      unsigned long long cur[kPer];
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        const int s = s0 + u * kNT + threadIdx.x;
+        key[u] = skeys[s];
+        wv[u] = svals[s];
         skeys[s] = kEmpty;
         svals[s] = 0;
+        cur[u] = 0ull;
+        home[u] = 0;
+        if (key[u] != kEmpty) {
+          home[u] = slot_in_range(key[u], gcap);
+          cur[u] = __ldcg(tab + home[u]);
+        }
       }
-      if (MODE == MODE_MOVE) continue;
-      const unsigned claimed = __ballot_sync(kFull, slot >= 0);
-      if (claimed) {
-        const int lane = threadIdx.x & 31, leader = __ffs(claimed) - 1;
-        unsigned long long base = 0;
-        if (lane == leader) base = atomicAdd(a.ws.ocnt + k, (unsigned long long)__popc(claimed));
-        base = __shfl_sync(kFull, base, leader);
-        if (slot >= 0) a.ws.occ[toff / 2 + (int64_t)(base + __popc(claimed & lanemask_lt()))] = (int32_t)slot;
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        int64_t slot = -1;
+        if (key[u] != kEmpty) slot = gm_insert_packed_from(tab, gcap, home[u], cur[u], key[u], wv[u], a.ctr);
+        if (MODE == MODE_MOVE) continue;
+        const unsigned claimed = __ballot_sync(kFull, slot >= 0);
+        if (claimed) {
+          const int lane = threadIdx.x & 31, leader = __ffs(claimed) - 1;
+          unsigned long long base = 0;
+          if (lane == leader) base = atomicAdd(a.ws.ocnt + k, (unsigned long long)__popc(claimed));
+          base = __shfl_sync(kFull, base, leader);
+          if (slot >= 0) a.ws.occ[toff / 2 + (int64_t)(base + __popc(claimed & lanemask_lt()))] = (int32_t)slot;
+        }
       }
     }
     __syncthreads();
@@ -262,28 +280,43 @@ __global__ void __launch_bounds__(kNT) k_big_eval(BigArgs a, int r) {
     const int64_t cap = table_cap(a.ws.tot[k], a.keyspace);
     const int64_t s0 = (g - a.ws.epre[k]) * kBigEvalSlots;
     const int64_t s1 = s0 + kBigEvalSlots < cap ? s0 + kBigEvalSlots : cap;
-    int32_t *keys = a.ws.keys + (a.ws.toff[k] - rr.base);
-    uint32_t *vals = a.ws.vals + (a.ws.toff[k] - rr.base);
+    unsigned long long *tab = a.ws.tab + (a.ws.toff[k] - rr.base);
     const int32_t d = a.Cp[i];
     const long long Ki = a.K[i];
     const long long tm = vertex_two_m(a.batch, a.two_m, i);
     long long best_s = LLONG_MIN, Kid = 0;
     int32_t best_c = INT_MAX;
-    for (int64_t s = s0 + threadIdx.x; s < s1; s += kNT) {
-      const int32_t c = __ldcg(keys + s);
-      if (c == kEmpty) continue;
-      const long long v = __ldcg(vals + s);
-      keys[s] = kEmpty;
-      vals[s] = 0;
-      if (c == d) {
-        Kid = v;
-        continue;
+    // 8 slots per thread per round: all loads issued before use
+    constexpr int kPer = 8;
+    for (int64_t r0 = s0; r0 < s1; r0 += kPer * kNT) {
+      unsigned long long pv[kPer];
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        const int64_t s = r0 + u * kNT + threadIdx.x;
+        pv[u] = s < s1 ? __ldcg(tab + s) : 0ull;
       }
-      ++distinct;
-      const long long sc = tm * v - Ki * a.Sigma[c];
-      if (better(sc, c, best_s, best_c)) {
-        best_s = sc;
-        best_c = c;
+      long long sig[kPer];
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        const int32_t c = packed_key(pv[u]);
+        sig[u] = (pv[u] != 0ull && c != d) ? a.Sigma[c] : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kPer; ++u) {
+        if (pv[u] == 0ull) continue;
+        tab[r0 + u * kNT + threadIdx.x] = 0ull;
+        const int32_t c = packed_key(pv[u]);
+        const long long v = packed_val(pv[u]);
+        if (c == d) {
+          Kid = v;
+          continue;
+        }
+        ++distinct;
+        const long long sc = tm * v - Ki * sig[u];
+        if (better(sc, c, best_s, best_c)) {
+          best_s = sc;
+          best_c = c;
+        }
       }
     }
     block_argmax_sum<kNT>(best_s, best_c, Kid);
@@ -368,8 +401,7 @@ __global__ void __launch_bounds__(kNT) k_big_emit(BigArgs a, int r) {
     const int64_t p0 = (g - a.ws.epre[k]) * kBigEvalSlots;
     const int64_t p1 = p0 + kBigEvalSlots < nocc ? p0 + kBigEvalSlots : nocc;
     const int64_t toff = a.ws.toff[k] - rr.base;
-    int32_t *keys = a.ws.keys + toff;
-    uint32_t *vals = a.ws.vals + toff;
+    unsigned long long *tab = a.ws.tab + toff;
     const int32_t *occ = a.ws.occ + toff / 2;
     if (threadIdx.x == 0) {
       s_base = atomicAdd((unsigned long long *)(a.oend + c), (unsigned long long)(p1 - p0));
@@ -379,10 +411,10 @@ __global__ void __launch_bounds__(kNT) k_big_emit(BigArgs a, int r) {
     for (int64_t p = p0 + threadIdx.x; p < p1; p += kNT) {
       const int32_t s = occ[p];
       const unsigned long long pos = s_base + (unsigned long long)(p - p0);
-      a.ocol[pos] = __ldcg(keys + s);
-      a.ow[pos] = __ldcg(vals + s);
-      keys[s] = kEmpty;
-      vals[s] = 0;
+      const unsigned long long pv = __ldcg(tab + s);
+      a.ocol[pos] = packed_key(pv);
+      a.ow[pos] = packed_val(pv);
+      tab[s] = 0ull;
     }
     __syncthreads();
   }

@@ -45,9 +45,8 @@ constexpr int kBigChunk = 4096;       // entries per accumulation chunk (512 thr
 constexpr int kBigSmemSlots = 8192;   // shared pre-aggregation table per block
 constexpr int kBigEvalSlots = 8192;   // occupied slots per evaluation block
 struct BigWs {
-  int32_t *keys = nullptr;
-  uint32_t *vals = nullptr;
-  int64_t slots = 0;                  // capacity of keys/vals
+  unsigned long long *tab = nullptr;  // packed slots (key + 1, weight); 0 = empty
+  int64_t slots = 0;                  // capacity of tab
   int64_t *tot = nullptr;             // [items] entries of each item
   int64_t *toff = nullptr;            // [items+1] table offset
   int64_t *cpre = nullptr;            // [items+1] accumulation chunk prefix

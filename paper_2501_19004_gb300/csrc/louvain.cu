@@ -214,19 +214,14 @@ louvain_status ensure_big(louvain_ctx *x, int64_t slots, int64_t parts, int64_t 
   louvain_status st;
   BigWs &b = x->big;
   if (slots > b.slots) {
-    dfree(x, b.keys);
-    dfree(x, b.vals);
+    dfree(x, b.tab);
     dfree(x, b.occ);
-    b.keys = nullptr;
-    b.vals = nullptr;
+    b.tab = nullptr;
     b.occ = nullptr;
     b.slots = 0;
     const int64_t want = slots + slots / 4;
-    if ((st = dalloc_n(x, &b.keys, want)) || (st = dalloc_n(x, &b.vals, want)) ||
-        (st = dalloc_n(x, &b.occ, want / 2 + 1)))
-      return st;
-    LV_CK(cudaMemsetAsync(b.keys, 0xFF, (size_t)want * sizeof(int32_t), x->stream));
-    LV_CK(cudaMemsetAsync(b.vals, 0, (size_t)want * sizeof(uint32_t), x->stream));
+    if ((st = dalloc_n(x, &b.tab, want)) || (st = dalloc_n(x, &b.occ, want / 2 + 1))) return st;
+    LV_CK(cudaMemsetAsync(b.tab, 0, (size_t)want * sizeof(unsigned long long), x->stream));
     b.slots = want;
   }
   if (parts > b.parts) {
@@ -626,8 +621,7 @@ louvain_status run_impl(louvain_ctx *x) {
   GView g{x->n0, x->off0, x->off0 + 1, x->col0, x->w0};
   int wk = x->weighted ? W_U32 : W_UNIT;
   if (x->big_dirty && x->big.slots > 0) {  // a failed run may have left table entries behind
-    LV_CK(cudaMemsetAsync(x->big.keys, 0xFF, (size_t)x->big.slots * sizeof(int32_t), s));
-    LV_CK(cudaMemsetAsync(x->big.vals, 0, (size_t)x->big.slots * sizeof(uint32_t), s));
+    LV_CK(cudaMemsetAsync(x->big.tab, 0, (size_t)x->big.slots * sizeof(unsigned long long), s));
   }
   x->big_dirty = true;
   iota_i32(x->C, x->n0, x->num_sms, s);
@@ -795,8 +789,7 @@ louvain_status run_batched(louvain_ctx *x) {
   GView g{x->n0, x->off0, x->off0 + 1, x->col0, x->w0};
   int wk = x->weighted ? W_U32 : W_UNIT;
   if (x->big_dirty && x->big.slots > 0) {
-    LV_CK(cudaMemsetAsync(x->big.keys, 0xFF, (size_t)x->big.slots * sizeof(int32_t), s));
-    LV_CK(cudaMemsetAsync(x->big.vals, 0, (size_t)x->big.slots * sizeof(uint32_t), s));
+    LV_CK(cudaMemsetAsync(x->big.tab, 0, (size_t)x->big.slots * sizeof(unsigned long long), s));
   }
   x->big_dirty = true;
   iota_i32(x->C, x->n0, x->num_sms, s);

@@ -56,48 +56,40 @@ __device__ __forceinline__ void sm_insert_list(int32_t *keys, uint32_t *vals, ui
   atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
 }
 
-// Global tables have any capacity `cap` (see big_table_cap).
-__device__ __forceinline__ void gm_insert(int32_t *keys, uint32_t *vals, uint32_t cap, int32_t key, uint32_t w,
-                                          Counters *ctr) {
-  uint32_t s = slot_in_range(key, cap);
-  for (uint32_t t = 0; t < cap; ++t) {
-    int32_t k = __ldcg(keys + s);
-    if (k == kEmpty) {
-      k = atomicCAS(keys + s, kEmpty, key);
-      if (k == kEmpty) k = key;
-    }
-    if (k == key) {
-      atomicAdd(vals + s, w);
-      return;
-    }
-    s = (s + 1 == cap) ? 0u : s + 1;
-  }
-  atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
-}
+// Global tables of big items use packed 64-bit slots: (key + 1) in the high
+// half, the summed weight in the low half (sums stay below 2^32, so adding a
+// weight never carries into the key); 0 is an empty slot.  An insert touches
+// one word: a CAS claims an empty slot with the first weight, later weights
+// of the same key are one 64-bit add.
+__device__ __forceinline__ int32_t packed_key(unsigned long long v) { return (int32_t)(uint32_t)(v >> 32) - 1; }
+__device__ __forceinline__ uint32_t packed_val(unsigned long long v) { return (uint32_t)v; }
 
-// Global insert that reports the slot it claimed for a new key (-1 when the
-// key was already present), so that callers can list the occupied slots.
-__device__ __forceinline__ int64_t gm_insert_claim(int32_t *keys, uint32_t *vals, uint32_t cap, int32_t key,
-                                                   uint32_t w, Counters *ctr) {
-  uint32_t s = slot_in_range(key, cap);
+// Insert of (key, w) starting at slot s, whose current content `cur` the
+// caller has read: claim an empty slot with a CAS, add to the key's slot, or
+// probe on.  Returns the slot it claimed for the key, -1 when the key was
+// present.
+__device__ __forceinline__ int64_t gm_insert_packed_from(unsigned long long *tab, uint32_t cap, uint32_t s,
+                                                         unsigned long long cur, int32_t key, uint32_t w,
+                                                         Counters *ctr) {
+  const unsigned long long hk = (unsigned long long)(uint32_t)(key + 1) << 32;
   for (uint32_t t = 0; t < cap; ++t) {
-    int32_t k = __ldcg(keys + s);
-    bool claimed = false;
-    if (k == kEmpty) {
-      k = atomicCAS(keys + s, kEmpty, key);
-      if (k == kEmpty) {
-        k = key;
-        claimed = true;
-      }
+    if (cur == 0ull) {
+      cur = atomicCAS(tab + s, 0ull, hk | w);
+      if (cur == 0ull) return (int64_t)s;
     }
-    if (k == key) {
-      atomicAdd(vals + s, w);
-      return claimed ? (int64_t)s : -1;
+    if ((cur & 0xFFFFFFFF00000000ull) == hk) {
+      atomicAdd(tab + s, (unsigned long long)w);
+      return -1;
     }
     s = (s + 1 == cap) ? 0u : s + 1;
+    cur = __ldcg(tab + s);
   }
   atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
   return -1;
+}
+
+__device__ __forceinline__ unsigned long long packed_pair(int32_t key, uint32_t w) {
+  return ((unsigned long long)(uint32_t)(key + 1) << 32) | w;
 }
 
 // Warp-cooperative insert into a shared table: all 32 lanes call it (key =
