@@ -44,6 +44,9 @@ WORKLOADS = {
                      "long-range edges, uniform integer weights 1-8, seed 11"),
     "sbm1000": dict(kind="sbm", n=1000, block=100, p_in=0.1, p_out=0.002, seed=1, desc="planted-partition SBM, "
                     "1,000 vertices in 10 blocks of 100, p_in=0.1, p_out=0.002, seed 1"),
+    "rmat22": dict(kind="rmat", scale=22, ef=16, seed=7, desc="R-MAT scale 22, edge factor 16, "
+                   "(a,b,c,d)=(0.57,0.19,0.19,0.05), symmetrised, deduplicated, no self-loops, unit int32 weights, "
+                   "seed 7 (profiling case: the default workload's generator at a quarter of the size)"),
     "rmat27": dict(kind="rmat", scale=27, ef=16, seed=13, desc="R-MAT scale 27, edge factor 16, "
                    "(a,b,c,d)=(0.57,0.19,0.19,0.05), symmetrised, deduplicated, no self-loops, unit int32 weights, "
                    "seed 13 (learned-skip evaluation graph)"),
@@ -58,6 +61,7 @@ REF_SAMPLES = {
     "rmat24": dict(kind="rmat", scale=20, ef=16, seed=7, desc="R-MAT scale 20 (same generator and parameters)"),
     "grid8192": dict(kind="grid", side=1024, frac=0.02, seed=11, desc="1024x1024 grid (same generator)"),
     "sbm1000": dict(kind="sbm", n=1000, block=100, p_in=0.1, p_out=0.002, seed=1, desc="the full workload"),
+    "rmat22": dict(kind="rmat", scale=20, ef=16, seed=7, desc="R-MAT scale 20 (same generator and parameters)"),
     "rmat27": dict(kind="rmat", scale=20, ef=16, seed=13, desc="R-MAT scale 20 (same generator and parameters)"),
     "bsbm4096": dict(kind="batch", G=48, first=0, desc="graphs 0-47 of the batch, one oracle run each"),
 }
@@ -65,6 +69,8 @@ SAMPLES = {
     "rmat24": dict(kind="rmat", scale=21, ef=16, seed=7, desc="R-MAT scale 21 (same generator and parameters)"),
     "grid8192": dict(kind="grid", side=1448, frac=0.02, seed=11, desc="1448x1448 grid (same generator)"),
     "sbm1000": dict(kind="sbm", n=1000, block=100, p_in=0.1, p_out=0.002, seed=1, desc="the full workload"),
+    "rmat22": dict(kind="rmat", scale=20, ef=16, seed=7, desc="R-MAT scale 20 (same generator and parameters)"),
+    "rmat27": dict(kind="rmat", scale=21, ef=16, seed=13, desc="R-MAT scale 21 (same generator and parameters)"),
     "bsbm4096": dict(kind="batch", G=256, first=0, desc="graphs 0-255 of the batch, one oracle run each"),
 }
 

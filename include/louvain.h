@@ -110,6 +110,11 @@ typedef struct {
                                     and clears the vertex's flag (it returns when a
                                     neighbour moves); 0 = skipped vertices keep
                                     their flag */
+  int64_t table_window;          /* global hashtables of vertices and communities with
+                                    more than 4096 entries are processed in rounds of
+                                    this many 8-byte slots (at least the largest
+                                    table); 0 = half of the pass's bound on their
+                                    total size.  Results do not depend on it. */
 } louvain_config;
 
 /* Fill `cfg` with the defaults above (mode PLAIN, seed 0). */

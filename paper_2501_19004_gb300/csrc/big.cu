@@ -91,9 +91,9 @@ __global__ void __launch_bounds__(1024) k_big_plan(BigArgs a) {
     members = warp_sum_u(members);
     if ((threadIdx.x & 31) == 0 && members) atomicAdd(&a.ctr->mg_work[kBigBin][1], members);
   }
-  // rounds: item k belongs to round toff[k] / window; the host launches
-  // enough rounds for the pass's bound, and the workspace holds the window
-  // plus the largest table
+  // rounds: item k belongs to round toff[k] / window; rstart holds the
+  // pass's bound of rounds, the host launches the rounds these items need,
+  // and the workspace holds the window plus the largest table
   const bool fits = c_slots <= (long long)a.rounds * a.window && (MODE == MODE_MERGE || c_ev <= a.ws.parts);
   __syncthreads();
   for (int64_t k = threadIdx.x; k <= nb; k += 1024) {
@@ -104,8 +104,9 @@ __global__ void __launch_bounds__(1024) k_big_plan(BigArgs a) {
   if (threadIdx.x == 0) {
     if (!fits) {
       atomicOr(&a.ctr->error, (unsigned long long)ERR_HASH);
-      for (int r = 0; r <= a.rounds; ++r) a.ws.rstart[r] = nb;  // nothing runs
+      for (int64_t r = 0; r <= a.rounds; ++r) a.ws.rstart[r] = nb;  // nothing runs
     }
+    *a.ws.nrounds = fits ? (c_slots + a.window - 1) / a.window : 0;
     a.ws.toff[nb] = c_slots;
     a.ws.cpre[nb] = c_ch;
     a.ws.epre[nb] = MODE == MODE_MOVE ? c_ev : 0;
@@ -424,8 +425,18 @@ __global__ void __launch_bounds__(kNT) k_big_emit(BigArgs a, int r) {
   }
 }
 
+template <int MODE>
+void big_plan(const BigArgs &b, cudaStream_t s, KernelProf *prof) {
+  const int k_rest = MODE == MODE_MOVE ? K_MOVE_HUB_EVAL : K_MERGE_BIG_EMIT;
+  if (prof) prof->begin(k_rest, s);
+  LV_LAUNCH(k_big_plan<MODE><<<1, 1024, 0, s>>>(b));
+  if (prof) prof->end(k_rest, s);
+  cudaMemcpyAsync(b.h_rounds, b.ws.nrounds, sizeof(long long), cudaMemcpyDeviceToHost, s);
+  cudaEventRecord(b.plan_done, s);
+}
+
 template <int MODE, int WK>
-void big_run(const BigArgs &b, int num_sms, cudaStream_t s, KernelProf *prof) {
+void big_rounds(const BigArgs &b, int num_sms, cudaStream_t s, KernelProf *prof) {
   const int k_acc = MODE == MODE_MOVE ? K_MOVE_HUB : K_MERGE_BIG;
   const int k_rest = MODE == MODE_MOVE ? K_MOVE_HUB_EVAL : K_MERGE_BIG_EMIT;
   static bool attr_done = false;
@@ -434,10 +445,10 @@ void big_run(const BigArgs &b, int num_sms, cudaStream_t s, KernelProf *prof) {
     cudaFuncSetAttribute(k_big_accum<MODE, WK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     attr_done = true;
   }
-  if (prof) prof->begin(k_rest, s);
-  LV_LAUNCH(k_big_plan<MODE><<<1, 1024, 0, s>>>(b));
-  if (prof) prof->end(k_rest, s);
-  for (int r = 0; r < b.rounds; ++r) {
+  cudaEventSynchronize(b.plan_done);
+  long long nr = *b.h_rounds;
+  if (nr > b.rounds) nr = b.rounds;
+  for (int r = 0; r < nr; ++r) {
     LV_TIMED(prof, k_acc, s, k_big_accum<MODE, WK><<<num_sms * 3, kNT, kSmem, s>>>(b, r));
     if (prof) prof->begin(k_rest, s);
     if (MODE == MODE_MERGE) LV_LAUNCH(k_big_plan2<<<1, 1024, 0, s>>>(b, r));
@@ -453,14 +464,17 @@ void big_run(const BigArgs &b, int num_sms, cudaStream_t s, KernelProf *prof) {
 
 }  // namespace
 
-void big_move(const BigArgs &b, int wkind, int num_sms, cudaStream_t s, KernelProf *prof) {
-  if (wkind == W_UNIT) big_run<MODE_MOVE, W_UNIT>(b, num_sms, s, prof);
-  else big_run<MODE_MOVE, W_U32>(b, num_sms, s, prof);
+void big_move_plan(const BigArgs &b, cudaStream_t s, KernelProf *prof) { big_plan<MODE_MOVE>(b, s, prof); }
+
+void big_move_rounds(const BigArgs &b, int wkind, int num_sms, cudaStream_t s, KernelProf *prof) {
+  if (wkind == W_UNIT) big_rounds<MODE_MOVE, W_UNIT>(b, num_sms, s, prof);
+  else big_rounds<MODE_MOVE, W_U32>(b, num_sms, s, prof);
 }
 
 void big_merge(const BigArgs &b, int wkind, int num_sms, cudaStream_t s, KernelProf *prof) {
-  if (wkind == W_UNIT) big_run<MODE_MERGE, W_UNIT>(b, num_sms, s, prof);
-  else big_run<MODE_MERGE, W_U32>(b, num_sms, s, prof);
+  big_plan<MODE_MERGE>(b, s, prof);
+  if (wkind == W_UNIT) big_rounds<MODE_MERGE, W_UNIT>(b, num_sms, s, prof);
+  else big_rounds<MODE_MERGE, W_U32>(b, num_sms, s, prof);
 }
 
 }  // namespace lv

@@ -58,13 +58,14 @@ struct BigWs {
   unsigned long long *part_kid = nullptr;
   int64_t parts = 0;                  // capacity of part_*
   int64_t item_cap = 0;               // capacity of tot/toff/cpre/epre
-  int64_t *rstart = nullptr;          // [kMaxBigRounds + 1] first item of every round
+  int64_t *rstart = nullptr;          // [round_cap + 2] first item of every round
+  int64_t round_cap = 0;              // capacity of rstart (rounds)
+  long long *nrounds = nullptr;       // [1] rounds the current items need (written by the plan)
 };
-// Items whose tables do not fit the workspace at once are processed in
-// rounds: round r takes the items whose global table offset lies in
-// [r * window, (r + 1) * window); the workspace holds window + the largest
-// table, so every item of a round fits.
-constexpr int kMaxBigRounds = 8;
+// Items are processed in rounds: round r takes the items whose global table
+// offset lies in [r * window, (r + 1) * window); the workspace holds window +
+// the largest table, so every item of a round fits.  The plan kernel reports
+// how many rounds the current items need, and only those are launched.
 
 // Batched runs: many graphs as one union graph whose vertex ranges are the
 // graphs (see batch.cu).  Null gid means a single graph.
@@ -117,7 +118,9 @@ struct BigArgs {
   int64_t keyspace;                   // number of possible keys: n' or |Gamma|
   BigWs ws;
   int64_t window = 0;                 // table slots per round
-  int rounds = 1;                     // rounds to launch
+  int64_t rounds = 1;                 // most rounds the items can need (rstart capacity)
+  long long *h_rounds = nullptr;      // pinned host word: rounds needed (copied after the plan)
+  cudaEvent_t plan_done = nullptr;    // recorded after that copy
   Counters *ctr;
   // local moving
   const int64_t *K;
@@ -145,7 +148,11 @@ struct BigArgs {
 // planning, evaluation and emission kernels under K_MOVE_HUB_EVAL /
 // K_MERGE_BIG_EMIT)
 struct KernelProf;
-void big_move(const BigArgs &b, int wkind, int num_sms, cudaStream_t s, KernelProf *prof);
+// Hub path of one bucket in two steps, so that the other bins' kernels run
+// while the host waits for the number of rounds: big_move_plan (plan kernel
+// and the copy of the round count), then big_move_rounds.
+void big_move_plan(const BigArgs &b, cudaStream_t s, KernelProf *prof);
+void big_move_rounds(const BigArgs &b, int wkind, int num_sms, cudaStream_t s, KernelProf *prof);
 void big_merge(const BigArgs &b, int wkind, int num_sms, cudaStream_t s, KernelProf *prof);
 
 inline int grid_for(int64_t n, int threads, int num_sms, int per_sm) {

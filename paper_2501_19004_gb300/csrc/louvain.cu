@@ -101,7 +101,9 @@ struct louvain_ctx {
   int cur_wbytes = 0;
   bool pass_has_hubs = false;
   int64_t hub_window = 0;
-  int hub_rounds = 0;
+  int64_t hub_rounds = 0;
+  long long *h_rounds = nullptr;     // pinned: rounds the current big items need
+  cudaEvent_t plan_done = nullptr;
 
   // batched runs: G graphs as one union graph (batch.cu)
   bool batched = false;
@@ -210,9 +212,24 @@ void dfree(louvain_ctx *x, void *p) {
 
 // Grow the big-item workspace to `slots` table slots, `parts` evaluation
 // partials and `items` items; new tables are cleared (all keys empty).
-louvain_status ensure_big(louvain_ctx *x, int64_t slots, int64_t parts, int64_t items) {
+louvain_status ensure_big(louvain_ctx *x, int64_t slots, int64_t parts, int64_t items, int64_t rounds) {
   louvain_status st;
   BigWs &b = x->big;
+  if (!b.nrounds) {
+    if ((st = dalloc_n(x, &b.nrounds, 1))) return st;
+    if (cudaMallocHost((void **)&x->h_rounds, sizeof(long long)) != cudaSuccess) {
+      set_err(x, "pinned allocation failed");
+      return LOUVAIN_E_NOMEM;
+    }
+    LV_CK(cudaEventCreateWithFlags(&x->plan_done, cudaEventDisableTiming));
+  }
+  if (rounds > b.round_cap) {
+    dfree(x, b.rstart);
+    b.rstart = nullptr;
+    const int64_t want = rounds + rounds / 4 + 8;
+    if ((st = dalloc_n(x, &b.rstart, want + 2))) return st;
+    b.round_cap = want;
+  }
   if (slots > b.slots) {
     dfree(x, b.tab);
     dfree(x, b.occ);
@@ -240,11 +257,10 @@ louvain_status ensure_big(louvain_ctx *x, int64_t slots, int64_t parts, int64_t 
     dfree(x, b.cpre);
     dfree(x, b.epre);
     dfree(x, b.ocnt);
-    dfree(x, b.rstart);
     const int64_t want = items + items / 4 + 64;
     if ((st = dalloc_n(x, &b.tot, want + 1)) || (st = dalloc_n(x, &b.toff, want + 1)) ||
         (st = dalloc_n(x, &b.cpre, want + 1)) || (st = dalloc_n(x, &b.epre, want + 1)) ||
-        (st = dalloc_n(x, &b.ocnt, want + 1)) || (st = dalloc_n(x, &b.rstart, (int64_t)kMaxBigRounds + 2)))
+        (st = dalloc_n(x, &b.ocnt, want + 1)))
       return st;
     b.item_cap = want;
   }
@@ -254,27 +270,24 @@ louvain_status ensure_big(louvain_ctx *x, int64_t slots, int64_t parts, int64_t 
 // Workspace for the big items counted in ctr->big_slots / big_items (their
 // tables' total size, a bound for every bucket), largest item `maxdeg` over
 // `keyspace` keys: tables go through a window of about half the total per
-// round (a bucket holds about 1/B of the pass's items), so the workspace is
-// window + the largest table.
+// round (a bucket holds about 1/B of the pass's items, so one or two rounds
+// run), the workspace is window + the largest table, and rstart holds the
+// rounds of the total.
 louvain_status ensure_big_for(louvain_ctx *x, const Counters &h, uint64_t maxdeg, uint64_t keyspace, int64_t *window,
-                              int *rounds) {
+                              int64_t *rounds) {
   *window = 0;
   *rounds = 0;
   if (h.big_items == 0) return LOUVAIN_OK;
   const int64_t total = (int64_t)h.big_slots;
   const int64_t maxcap = (int64_t)big_table_cap(maxdeg, keyspace);
-  int64_t w = ((total + 1) / 2 + 63) & ~63ll;
+  const int64_t target = x->cfg.table_window > 0 ? x->cfg.table_window : (total + 1) / 2;
+  int64_t w = ((std::min<int64_t>(total, target)) + 63) & ~63ll;
   if (w < maxcap) w = maxcap;
-  int r = (int)((total + w - 1) / w);
-  if (r > kMaxBigRounds) {
-    w = ((total + kMaxBigRounds - 1) / kMaxBigRounds + 63) & ~63ll;
-    if (w < maxcap) w = maxcap;
-    r = (int)((total + w - 1) / w);
-  }
+  int64_t r = (total + w - 1) / w;
   if (r < 1) r = 1;
   *window = w;
   *rounds = r;
-  return ensure_big(x, w + maxcap, total / kBigEvalSlots + (int64_t)h.big_items + 1, (int64_t)h.big_items + 1);
+  return ensure_big(x, w + maxcap, total / kBigEvalSlots + (int64_t)h.big_items + 1, (int64_t)h.big_items + 1, r);
 }
 
 louvain_status read_counters(louvain_ctx *x) {
@@ -455,6 +468,8 @@ louvain_status move_iteration(louvain_ctx *x, const GView &g, int wk, int pass, 
     big.ws = x->big;
     big.window = x->hub_window;
     big.rounds = x->hub_rounds;
+    big.h_rounds = x->h_rounds;
+    big.plan_done = x->plan_done;
     if (!x->pass_has_hubs) big.ws.slots = 0;
     big.ctr = x->d_ctr;
     big.K = x->K;
@@ -575,10 +590,12 @@ louvain_status aggregate(louvain_ctx *x, AggArgs &aa, int64_t gamma, PassTiming 
   LV_CK(cudaGetLastError());
   if ((st = read_counters(x))) return st;
   int64_t mwindow = 0;
-  int mrounds = 0;
+  int64_t mrounds = 0;
   if ((st = ensure_big_for(x, *x->h_ctr, x->h_ctr->maxdeg, (uint64_t)gamma, &mwindow, &mrounds))) return st;
   aa.big.window = mwindow;
   aa.big.rounds = mrounds;
+  aa.big.h_rounds = x->h_rounds;
+  aa.big.plan_done = x->plan_done;
   aa.big.g = g;
   aa.big.Cp = x->Cp;
   aa.big.items = x->bins[kBigBin];
@@ -969,6 +986,7 @@ louvain_status validate_config(const louvain_config *c) {
   if (c->mode != LOUVAIN_MODE_PLAIN && c->mode != LOUVAIN_MODE_LEARNED) return LOUVAIN_E_INVAL;
   if (c->mode == LOUVAIN_MODE_LEARNED && (!c->model || c->max_iterations > 127)) return LOUVAIN_E_INVAL;
   if (c->trace_capacity < 0 || c->learned_fallback < 0 || c->learned_fallback > 2) return LOUVAIN_E_INVAL;
+  if (c->table_window < 0) return LOUVAIN_E_INVAL;
   return LOUVAIN_OK;
 }
 
@@ -1252,6 +1270,7 @@ void louvain_config_default(louvain_config *c) {
   c->trace_rate = 1.0f;
   c->learned_fallback = 0;
   c->learned_skip_clears = 0;
+  c->table_window = 0;
 }
 
 louvain_status louvain_create(const louvain_graph *graph, const louvain_config *cfg, void *stream, louvain_ctx **out) {
@@ -1427,6 +1446,8 @@ void louvain_destroy(louvain_ctx *x) {
   if (x->run0) cudaEventDestroy(x->run0);
   if (x->run1) cudaEventDestroy(x->run1);
   if (x->h_ctr) cudaFreeHost(x->h_ctr);
+  if (x->h_rounds) cudaFreeHost(x->h_rounds);
+  if (x->plan_done) cudaEventDestroy(x->plan_done);
   for (void *p : x->pinned) cudaFreeHost(p);
   delete x;
 }

@@ -661,12 +661,14 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
   }
   LV_TIMED(prof, K_SELECT, s, k_select<<<grid_for(a.g.n, 256, num_sms, 8), 256, 0, s>>>(a));
   if (a.learn.enabled) LV_TIMED(prof, K_MLP_SELECT, s, k_mlp_select<<<num_sms * 4, 256, 0, s>>>(a));
+  const bool hubs = big.ws.slots > 0;
+  if (hubs) big_move_plan(big, s, prof);  // the round count reaches the host while the bins below run
   LV_TIMED(prof, K_MOVE_THREAD, s, k_move_thread<WK><<<num_sms * 8, 256, 0, s>>>(a));
   LV_TIMED(prof, K_MOVE_GROUP, s, k_move_group<WK, kGroupLanes, 8><<<num_sms * 7, 256, 0, s>>>(a));
   LV_TIMED(prof, K_MOVE_WARP, s, k_move_warp<WK, 8><<<num_sms * 7, 256, 0, s>>>(a));
   LV_TIMED(prof, K_MOVE_MID, s, k_move_block<WK, 128, kMidCap, 2><<<num_sms * 12, 128, kMidSmem, s>>>(a));
   LV_TIMED(prof, K_MOVE_BLOCK, s, k_move_block<WK, 512, kBlockCap, 3><<<num_sms * 3, 512, kBlockSmem, s>>>(a));
-  if (big.ws.slots > 0) big_move(big, WK, num_sms, s, prof);
+  if (hubs) big_move_rounds(big, WK, num_sms, s, prof);
   LV_TIMED(prof, K_APPLY, s, k_apply<<<num_sms * 4, 256, 0, s>>>(a));
 }
 

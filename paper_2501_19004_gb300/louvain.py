@@ -59,7 +59,8 @@ class LouvainConfig(ctypes.Structure):
                 ("model", ctypes.c_void_p), ("skip_threshold", ctypes.c_float),
                 ("record_pass_modularity", ctypes.c_int32), ("check_symmetry", ctypes.c_int32),
                 ("profile_mask", ctypes.c_uint32), ("trace_capacity", ctypes.c_int64), ("trace_rate", ctypes.c_float),
-                ("learned_fallback", ctypes.c_int32), ("learned_skip_clears", ctypes.c_int32)]
+                ("learned_fallback", ctypes.c_int32), ("learned_skip_clears", ctypes.c_int32),
+                ("table_window", ctypes.c_int64)]
 
 
 _lib = None
@@ -149,6 +150,7 @@ class Config:
     trace_rate: float = 1.0
     learned_fallback: int = 0
     learned_skip_clears: int = 0
+    table_window: int = 0
 
     def c(self) -> LouvainConfig:
         self._model_keep = None
@@ -161,7 +163,7 @@ class Config:
                              self.schedule_seed & (2**64 - 1), self.mode, mp, self.skip_threshold,
                              int(self.record_pass_modularity), int(self.check_symmetry), self.profile_mask,
                              self.trace_capacity, self.trace_rate, self.learned_fallback,
-                             self.learned_skip_clears)
+                             self.learned_skip_clears, self.table_window)
 
 
 @dataclass

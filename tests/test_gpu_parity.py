@@ -84,12 +84,12 @@ def test_plain_bit_exact_across_settings(cfg):
     assert_same(res, ref)
 
 
-@pytest.mark.parametrize("buckets", [1, 2])
-def test_hub_rounds_bit_exact(buckets):
-    """With one or two buckets a bucket holds more than half of the pass's hub
-    tables, so the hub path runs in several rounds."""
+@pytest.mark.parametrize("buckets,window", [(1, 0), (2, 0), (1, 4096), (4, 4096), (2, 50000)])
+def test_hub_rounds_bit_exact(buckets, window):
+    """Small table windows put the hub and big-community tables through many
+    rounds; results must not change."""
     g = gg.rmat(16, 16, seed=11)
-    res, ref = run_both(g, lv.Config(buckets=buckets))
+    res, ref = run_both(g, lv.Config(buckets=buckets, table_window=window))
     assert_same(res, ref)
 
 
