@@ -200,6 +200,8 @@ def main():
     ap.add_argument("--skip-clears", type=int, default=1)
     ap.add_argument("--learned-fallback", type=int, default=0)
     ap.add_argument("--graphs", type=int, default=0, help="batch workloads: run only the first N graphs")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch schedule")
+    ap.add_argument("--autotune-runs", type=int, default=24)
     ap.add_argument("--sequential-sample", type=int, default=256,
                     help="batch workloads: graphs run one context at a time for comparison")
     args = ap.parse_args()
@@ -238,11 +240,25 @@ def main():
     dg = lv.DeviceCSR.from_host(g, dev)
     torch.cuda.synchronize()
 
+    sched = None  # the tuned launch schedule, applied to every context below
+
     def new_ctx(graph, cfg=None):
-        return lv.LouvainBatch(graph, vo, cfg) if batch else lv.Louvain(graph, cfg)
+        c = lv.LouvainBatch(graph, vo, cfg) if batch else lv.Louvain(graph, cfg)
+        if sched:
+            c.set_schedule(sched)
+        return c
 
     all_mask = (1 << len(lv.KERNELS)) - 1
     ctx = new_ctx(dg, lv.Config(profile_mask=all_mask))
+    # the library's autotuner picks the launch schedule on this workload
+    # (timed runs before the measurement; results do not depend on it)
+    tune = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        rep = ctx.autotune(args.autotune_runs)
+        sched = ctx.schedule()
+        tune = {"seconds": round(time.perf_counter() - t0, 2), "runs": rep["runs"], "start_ms": rep["start_ms"],
+                "tuned_ms": rep["tuned_ms"], "schedule": sched}
     # warm-up 1: every kernel group timed, to find the dominant kernel
     ctx.run()
     prof = ctx.stats()["kernels"]
@@ -298,6 +314,8 @@ def main():
         lctx = lv.Louvain(dg, lv.Config(mode=lv.MODE_LEARNED, model=model, skip_threshold=args.skip_threshold,
                                         learned_skip_clears=args.skip_clears,
                                         learned_fallback=args.learned_fallback))
+        if sched:
+            lctx.set_schedule(sched)
         for _ in range(args.warmup):
             lctx.run()
         torch.cuda.synchronize()
@@ -385,6 +403,8 @@ def main():
             ea, eb = int(g.offsets[a]), int(g.offsets[b])
             sub_g = lv.DeviceCSR((dg.offsets[a:b + 1] - ea).contiguous(), (dg.cols[ea:eb] - a).contiguous())
             with lv.Louvain(sub_g) as c1:
+                if sched:
+                    c1.set_schedule(sched)
                 c1.run()
                 s0 = torch.cuda.Event(enable_timing=True)
                 s1 = torch.cuda.Event(enable_timing=True)
@@ -416,7 +436,7 @@ def main():
                        "l2": f"inputs larger than L2 (CSR {(g.offsets.nbytes + g.cols.nbytes) / 1e9:.2f} GB), no flush",
                        **summary},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
-            "learned_skip": learned, "sequential": sequential,
+            "learned_skip": learned, "sequential": sequential, "autotune": tune,
             "phases_ms": {"move": st["move_ms"], "aggregate": st["aggregate_ms"], "other": st["other_ms"]},
             "kernels_ms_warmup": {k: round(v["ms"], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
         }

@@ -159,6 +159,33 @@ louvain_status louvain_stats(const louvain_ctx *ctx, char *json, size_t cap);
  * launch and nothing else. */
 louvain_status louvain_set_profile(louvain_ctx *ctx, uint32_t profile_mask);
 
+/* ---- Launch schedule and autotuner (an addition of this library; the paper
+ * fixes one kernel configuration).  A schedule is louvain_schedule_words()
+ * int32 words:
+ *   [0] group_max: largest degree handled by 8-lane groups (16 .. 64;
+ *       16 = no group bin); [1] warp_max: largest degree handled by a warp
+ *       (group_max .. 256; larger degrees up to 1024 go to 128-thread blocks);
+ *   [2..7] blocks per SM of the local-moving kernels of the thread, warp,
+ *       128-thread, 512-thread, hub (<= 3) and group bins (1 .. 64);
+ *   [8..12] blocks per SM of the aggregation kernels of the thread, warp,
+ *       128-thread, 512-thread and big-community (<= 3) bins;
+ *   [13] graphs: 1 = each local-moving iteration is replayed from a CUDA
+ *       graph captured once per pass (plain mode, no profiling).
+ * Results never depend on the schedule: every bin computes the same exact
+ * decisions.  The schedule belongs to the context and is used by its next
+ * runs. */
+int32_t louvain_schedule_words(void);
+louvain_status louvain_get_schedule(const louvain_ctx *ctx, int32_t *words, int32_t n);
+louvain_status louvain_set_schedule(louvain_ctx *ctx, const int32_t *words, int32_t n);
+
+/* Choose the context's schedule by timed runs of its own graph (at most
+ * max_runs whole runs): bin thresholds by whole-run time, blocks per SM of
+ * every bin by per-kernel CUDA-event time, then graph replay on or off.  The
+ * tuned schedule is kept only if it beats the starting one.  json (may be
+ * NULL) receives {"runs", "start_ms", "tuned_ms", "schedule", "trials"}.  The
+ * context holds a valid result of the chosen schedule afterwards. */
+louvain_status louvain_autotune(louvain_ctx *ctx, int32_t max_runs, char *json, size_t cap);
+
 /* Release all device memory of the context (stream-ordered). */
 void louvain_destroy(louvain_ctx *ctx);
 

@@ -506,10 +506,11 @@ void merge_t(const AggArgs &a, int num_sms, cudaStream_t s, KernelProf *prof) {
                          (int)kSmem);
     attr_done = true;
   }
-  LV_TIMED(prof, K_MERGE_THREAD, s, k_merge_thread<WK, 128><<<num_sms * 8, 128, 0, s>>>(a));
-  LV_TIMED(prof, K_MERGE_WARP, s, k_merge_warp<WK, 8><<<num_sms * 7, 256, 0, s>>>(a));
-  LV_TIMED(prof, K_MERGE_MID, s, k_merge_block<WK, 128, kMidCap, 2><<<num_sms * 12, 128, kMidSmem, s>>>(a));
-  LV_TIMED(prof, K_MERGE_BLOCK, s, k_merge_block<WK, 512, kBlockCap, 3><<<num_sms * 3, 512, kSmem, s>>>(a));
+  const int *bk = a.sched.merge;
+  LV_TIMED(prof, K_MERGE_THREAD, s, k_merge_thread<WK, 128><<<num_sms * bk[0], 128, 0, s>>>(a));
+  LV_TIMED(prof, K_MERGE_WARP, s, k_merge_warp<WK, 8><<<num_sms * bk[1], 256, 0, s>>>(a));
+  LV_TIMED(prof, K_MERGE_MID, s, k_merge_block<WK, 128, kMidCap, 2><<<num_sms * bk[2], 128, kMidSmem, s>>>(a));
+  LV_TIMED(prof, K_MERGE_BLOCK, s, k_merge_block<WK, 512, kBlockCap, 3><<<num_sms * bk[3], 512, kSmem, s>>>(a));
   if (a.big.ws.slots > 0) big_merge(a.big, WK, num_sms, s, prof);
 }
 

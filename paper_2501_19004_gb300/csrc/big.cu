@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(kNT) k_big_decide(BigArgs a, int r) {
       const int32_t d = a.Cp[i];
       long long s_d = 0;
       const long long tm = vertex_two_m(a.batch, a.two_m, i);
-      const int32_t t = finish_decision(tm, a.Sigma, a.pickless, d, a.K[i], Kid, best_s, best_c, glo, ghi, gm, &s_d);
+      const int32_t t = finish_decision(tm, a.Sigma, a.iter ? (int)a.iter[1] : a.pickless, d, a.K[i], Kid, best_s, best_c, glo, ghi, gm, &s_d);
       learn_record(a.learn, a.ctr, a.g, a.Cp, a.Sigma, a.two_m, i, a.K[i], Kid, best_s, best_c, s_d, t >= 0);
       if (t >= 0) batch_gain(a.batch, i, best_s, s_d);
       work[0] += 1;
@@ -431,6 +431,7 @@ void big_plan(const BigArgs &b, cudaStream_t s, KernelProf *prof) {
   if (prof) prof->begin(k_rest, s);
   LV_LAUNCH(k_big_plan<MODE><<<1, 1024, 0, s>>>(b));
   if (prof) prof->end(k_rest, s);
+  if (b.static_rounds) return;
   cudaMemcpyAsync(b.h_rounds, b.ws.nrounds, sizeof(long long), cudaMemcpyDeviceToHost, s);
   cudaEventRecord(b.plan_done, s);
 }
@@ -445,11 +446,13 @@ void big_rounds(const BigArgs &b, int num_sms, cudaStream_t s, KernelProf *prof)
     cudaFuncSetAttribute(k_big_accum<MODE, WK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
     attr_done = true;
   }
-  cudaEventSynchronize(b.plan_done);
-  long long nr = *b.h_rounds;
-  if (nr > b.rounds) nr = b.rounds;
+  long long nr = b.rounds;  // rounds beyond the items' need find no items
+  if (!b.static_rounds) {
+    cudaEventSynchronize(b.plan_done);
+    nr = *b.h_rounds < b.rounds ? *b.h_rounds : b.rounds;
+  }
   for (int r = 0; r < nr; ++r) {
-    LV_TIMED(prof, k_acc, s, k_big_accum<MODE, WK><<<num_sms * 3, kNT, kSmem, s>>>(b, r));
+    LV_TIMED(prof, k_acc, s, k_big_accum<MODE, WK><<<num_sms * b.accum_blocks, kNT, kSmem, s>>>(b, r));
     if (prof) prof->begin(k_rest, s);
     if (MODE == MODE_MERGE) LV_LAUNCH(k_big_plan2<<<1, 1024, 0, s>>>(b, r));
     if (MODE == MODE_MOVE) {

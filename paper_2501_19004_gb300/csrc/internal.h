@@ -34,8 +34,29 @@ constexpr int kGroupMaxDeg = 64;  // kGroupLanes lanes x 8 entries
 constexpr int kGroupBin = 5;
 constexpr int kMoveBins = 6;
 
-__host__ __device__ __forceinline__ int move_bin(int64_t d) {
-  return (d > kThreadMaxDeg && d <= kGroupMaxDeg) ? kGroupBin : degree_bin(d);
+// Launch schedule of the binned kernels (louvain_autotune chooses one; the
+// results never depend on it, since every bin's kernel computes the same
+// exact decision for a vertex):
+//   group_max  largest degree of the group bin (16 = no group bin, <= 64);
+//   warp_max   largest degree of the warp bin (>= group_max, <= 256); larger
+//              degrees up to 1024 go to the 128-thread block bin;
+//   move[b], merge[b]  blocks per SM of bin b's kernel (grid = SMs x blocks;
+//              every kernel strides over its list, so any grid is correct);
+//   graphs     1 = each iteration's launches are replayed from a CUDA graph.
+struct Sched {
+  int group_max = kGroupMaxDeg;
+  int warp_max = kWarpMaxDeg;
+  int move[kMoveBins] = {2, 8, 12, 2, 3, 4};  // thread, warp, mid, block, hub, group
+  int merge[kNumBins] = {8, 8, 8, 2, 3};      // thread, warp, mid, block, big
+  int graphs = 0;
+};
+constexpr int kSchedWords = 2 + kMoveBins + kNumBins + 1;
+
+__host__ __device__ __forceinline__ int move_bin(int64_t d, int group_max, int warp_max) {
+  if (d <= kThreadMaxDeg) return 0;
+  if (d <= group_max) return kGroupBin;
+  if (d <= warp_max) return 1;
+  return degree_bin(d) == 1 ? 2 : degree_bin(d);
 }
 
 // Global tables of big items (hub vertices in local moving, communities with
@@ -118,9 +139,11 @@ struct BigArgs {
   int64_t keyspace;                   // number of possible keys: n' or |Gamma|
   BigWs ws;
   int64_t window = 0;                 // table slots per round
+  int accum_blocks = 3;               // blocks per SM of the accumulation kernel
   int64_t rounds = 1;                 // most rounds the items can need (rstart capacity)
   long long *h_rounds = nullptr;      // pinned host word: rounds needed (copied after the plan)
   cudaEvent_t plan_done = nullptr;    // recorded after that copy
+  int static_rounds = 0;              // 1: launch all `rounds` rounds without asking (graph capture)
   Counters *ctr;
   // local moving
   const int64_t *K;
@@ -132,6 +155,7 @@ struct BigArgs {
   int32_t *mv_target;
   LearnArgs learn;
   BatchView batch;
+  const uint32_t *iter = nullptr;     // graph replay: device words {salt, pickless} of the iteration
   // aggregation
   const int64_t *mprefix;             // member-degree exclusive prefix (community-vertex CSR order)
   const int64_t *kcoff;
@@ -179,6 +203,8 @@ struct MoveArgs {
   Counters *ctr;
   LearnArgs learn;
   BatchView batch;
+  Sched sched;
+  const uint32_t *iter = nullptr;  // graph replay: device words {salt, pickless} of the iteration
 };
 
 // Kernel identifiers for the optional per-kernel event timing.
@@ -256,6 +282,7 @@ struct AggArgs {
   Counters *ctr;
   long long *scan_tmp;      // block sums for the scans
   int64_t gamma;            // number of communities (keys of the merge tables)
+  Sched sched;
 };
 
 // community sizes and degrees, scans; totals in ctr->scan_total[0..2]

@@ -104,6 +104,14 @@ struct louvain_ctx {
   int64_t hub_rounds = 0;
   long long *h_rounds = nullptr;     // pinned: rounds the current big items need
   cudaEvent_t plan_done = nullptr;
+  Sched sched;                       // launch schedule (louvain_set_schedule / louvain_autotune)
+  // graph replay of local-moving iterations (sched.graphs)
+  cudaGraphExec_t gexec = nullptr;
+  long long graph_launches = 0;      // kernels per replay
+  int graph_pass = -1;               // pass the executable graph was captured for
+  bool graph_broken = false;         // a capture failed: direct launches for the rest of the run
+  uint32_t *d_iter = nullptr;        // {salt, pickless} read by the kernels under replay
+  uint32_t *h_iter = nullptr;        // pinned
 
   // batched runs: G graphs as one union graph (batch.cu)
   bool batched = false;
@@ -373,6 +381,7 @@ LearnArgs learn_args(louvain_ctx *x, int pass, int t, bool skipping) {
 // One iteration of the local-moving phase (all buckets); fills *h.
 louvain_status move_iteration(louvain_ctx *x, const GView &g, int wk, int pass, int t, bool skipping,
                               const Counters **h_out);
+louvain_status begin_run(louvain_ctx *x);
 
 // Local-moving phase (Algorithm 5) under the bucket schedule; returns l_i.
 // Learned mode: iterations with the predictor until the tolerance is met,
@@ -434,8 +443,11 @@ louvain_status move_phase(louvain_ctx *x, const GView &g, int wk, int pass, doub
   return LOUVAIN_OK;
 }
 
-louvain_status move_iteration(louvain_ctx *x, const GView &g, int wk, int pass, int t, bool skipping,
-                              const Counters **h_out) {
+// Launches of one local-moving iteration (all buckets) on x->stream; with
+// `iter` the kernels read the salt and Pick-Less flag from device memory and
+// the hub path launches its rounds without asking (graph capture).
+louvain_status enqueue_iteration(louvain_ctx *x, const GView &g, int wk, int pass, int t, bool skipping,
+                                 const uint32_t *iter) {
   const louvain_config &cfg = x->cfg;
   {
     const int rho = cfg.pickless_period;
@@ -459,6 +471,8 @@ louvain_status move_iteration(louvain_ctx *x, const GView &g, int wk, int pass, 
     a.ctr = x->d_ctr;
     a.learn = L;
     a.batch = x->bview;
+    a.sched = x->sched;
+    a.iter = iter;
     BigArgs big{};
     big.g = g;
     big.Cp = x->Cp;
@@ -481,11 +495,86 @@ louvain_status move_iteration(louvain_ctx *x, const GView &g, int wk, int pass, 
     big.mv_target = x->mv_target;
     big.learn = L;
     big.batch = x->bview;
+    big.accum_blocks = x->sched.move[kBigBin];
+    big.iter = iter;
+    big.static_rounds = iter != nullptr;
     for (int b = 0; b < cfg.buckets; ++b) {
       LV_CK(cudaMemsetAsync(x->d_ctr, 0, 10 * sizeof(unsigned long long), x->stream));
       if (L.enabled) LV_CK(cudaMemsetAsync(&x->d_ctr->cand_count, 0, sizeof(unsigned long long), x->stream));
       a.bucket = (uint32_t)b;
       move_bucket(a, big, wk, x->num_sms, x->stream, x->prof.mask ? &x->prof : nullptr);
+    }
+  }
+  return LOUVAIN_OK;
+}
+
+// Capture the iteration's launches into x->gexec (once per pass).
+louvain_status capture_iteration(louvain_ctx *x, const GView &g, int wk, int pass) {
+  cudaStream_t s = x->stream;
+  if (!x->d_iter) {
+    louvain_status st;
+    if ((st = dalloc_n(x, &x->d_iter, 2))) return st;
+    if (cudaMallocHost((void **)&x->h_iter, 2 * sizeof(uint32_t)) != cudaSuccess) {
+      set_err(x, "pinned allocation failed");
+      return LOUVAIN_E_NOMEM;
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  const long long l0 = g_launches;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    x->graph_broken = true;
+    return LOUVAIN_OK;
+  }
+  louvain_status st = enqueue_iteration(x, g, wk, pass, 0, false, x->d_iter);
+  const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+  x->graph_launches = g_launches - l0;
+  g_launches = l0;
+  if (st != LOUVAIN_OK || ec != cudaSuccess || !graph) {
+    cudaGetLastError();
+    if (graph) cudaGraphDestroy(graph);
+    x->graph_broken = true;
+    return LOUVAIN_OK;
+  }
+  bool ok = false;
+  if (x->gexec) {
+    cudaGraphExecUpdateResultInfo info;
+    ok = cudaGraphExecUpdate(x->gexec, graph, &info) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      cudaGraphExecDestroy(x->gexec);
+      x->gexec = nullptr;
+    }
+  }
+  if (!ok) ok = cudaGraphInstantiate(&x->gexec, graph, 0) == cudaSuccess;
+  cudaGraphDestroy(graph);
+  if (!ok) {
+    cudaGetLastError();
+    x->gexec = nullptr;
+    x->graph_broken = true;
+    return LOUVAIN_OK;
+  }
+  x->graph_pass = pass;
+  return LOUVAIN_OK;
+}
+
+louvain_status move_iteration(louvain_ctx *x, const GView &g, int wk, int pass, int t, bool skipping,
+                              const Counters **h_out) {
+  const louvain_config &cfg = x->cfg;
+  {
+    const bool replay = x->sched.graphs && !x->graph_broken && !x->prof.mask && cfg.mode == LOUVAIN_MODE_PLAIN &&
+                        !x->trace_x;
+    louvain_status st0;
+    if (replay && x->graph_pass != pass && (st0 = capture_iteration(x, g, wk, pass))) return st0;
+    if (replay && !x->graph_broken) {
+      const int rho = cfg.pickless_period;
+      x->h_iter[0] = bucket_salt(pass, t, cfg.schedule_seed);
+      x->h_iter[1] = (rho > 0 && ((t + rho / 2) % rho) == 0) ? 1u : 0u;
+      LV_CK(cudaMemcpyAsync(x->d_iter, x->h_iter, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice, x->stream));
+      LV_CK(cudaGraphLaunch(x->gexec, x->stream));
+      g_launches += x->graph_launches;
+    } else if ((st0 = enqueue_iteration(x, g, wk, pass, t, skipping, nullptr))) {
+      return st0;
     }
     LV_CK(cudaGetLastError());
     if (x->batched)  // per-graph gain sums, read with the counters
@@ -530,6 +619,8 @@ louvain_status begin_run(louvain_ctx *x) {
   const louvain_config &cfg = x->cfg;
   cudaStream_t s = x->stream;
   x->ran = false;
+  x->graph_pass = -1;  // every pass captures its own iteration graph
+  x->graph_broken = false;
   x->iter_stats.assign((size_t)std::max(cfg.max_passes, 1) * cfg.max_iterations * 4, 0);
   x->pass_stats.assign((size_t)std::max(cfg.max_passes, 1) * 6, 0);
   x->it_total = x->moves_total = x->evaluated_total = x->skipped_total = 0;
@@ -548,6 +639,7 @@ louvain_status begin_run(louvain_ctx *x) {
 
 AggArgs agg_args(louvain_ctx *x, const GView &g, int wk, int slot) {
   AggArgs aa{};
+  aa.sched = x->sched;
   aa.g = g;
   aa.wkind = wk;
   aa.Cp = x->Cp;
@@ -594,6 +686,7 @@ louvain_status aggregate(louvain_ctx *x, AggArgs &aa, int64_t gamma, PassTiming 
   if ((st = ensure_big_for(x, *x->h_ctr, x->h_ctr->maxdeg, (uint64_t)gamma, &mwindow, &mrounds))) return st;
   aa.big.window = mwindow;
   aa.big.rounds = mrounds;
+  aa.big.accum_blocks = x->sched.merge[kBigBin];
   aa.big.h_rounds = x->h_rounds;
   aa.big.plan_done = x->plan_done;
   aa.big.g = g;
@@ -1432,6 +1525,201 @@ louvain_status louvain_set_profile(louvain_ctx *x, uint32_t mask) {
   return LOUVAIN_OK;
 }
 
+// ---- launch schedule and autotuner
+
+// Schedule words: group_max, warp_max, move blocks per SM of the bins
+// (thread, warp, mid, block, hub, group), merge blocks per SM (thread, warp,
+// mid, block, big), graphs.
+static void sched_to_words(const Sched &s, int32_t *w) {
+  int k = 0;
+  w[k++] = s.group_max;
+  w[k++] = s.warp_max;
+  for (int b = 0; b < kMoveBins; ++b) w[k++] = s.move[b];
+  for (int b = 0; b < kNumBins; ++b) w[k++] = s.merge[b];
+  w[k++] = s.graphs;
+}
+
+static bool sched_from_words(const int32_t *w, Sched *s) {
+  Sched t;
+  int k = 0;
+  t.group_max = w[k++];
+  t.warp_max = w[k++];
+  for (int b = 0; b < kMoveBins; ++b) t.move[b] = w[k++];
+  for (int b = 0; b < kNumBins; ++b) t.merge[b] = w[k++];
+  t.graphs = w[k++];
+  if (t.group_max < kThreadMaxDeg || t.group_max > kGroupMaxDeg) return false;
+  if (t.warp_max < t.group_max || t.warp_max > kWarpMaxDeg) return false;
+  for (int b = 0; b < kMoveBins; ++b)
+    if (t.move[b] < 1 || t.move[b] > 64) return false;
+  for (int b = 0; b < kNumBins; ++b)
+    if (t.merge[b] < 1 || t.merge[b] > 64) return false;
+  if (t.move[kBigBin] > 3 || t.merge[kBigBin] > 3) return false;  // accumulation: 3 blocks per SM at most
+  if (t.graphs != 0 && t.graphs != 1) return false;
+  *s = t;
+  return true;
+}
+
+int32_t louvain_schedule_words(void) { return kSchedWords; }
+
+louvain_status louvain_get_schedule(const louvain_ctx *x, int32_t *words, int32_t n) {
+  if (!x || !words || n < kSchedWords) return LOUVAIN_E_INVAL;
+  sched_to_words(x->sched, words);
+  return LOUVAIN_OK;
+}
+
+louvain_status louvain_set_schedule(louvain_ctx *x, const int32_t *words, int32_t n) {
+  if (!x || !words || n < kSchedWords) return LOUVAIN_E_INVAL;
+  Sched s;
+  if (!sched_from_words(words, &s)) {
+    set_err(x, "schedule out of range");
+    return LOUVAIN_E_INVAL;
+  }
+  x->sched = s;
+  return LOUVAIN_OK;
+}
+
+// Autotuner: timed runs of the context's own graph choose the schedule.
+// Results do not depend on the schedule, so every trial is a full run.
+//   1. bin thresholds (group_max, warp_max): whole-run time of each pair;
+//   2. blocks per SM: one run per candidate value with every bin set to it
+//      and per-kernel event timing; each bin keeps its fastest value (the
+//      bins' kernels are independent launches);
+//   3. graph replay on or off: whole-run time.
+// The tuned schedule is kept only if a final run beats the starting one.
+louvain_status louvain_autotune(louvain_ctx *x, int32_t max_runs, char *json, size_t cap) {
+  if (!x || max_runs < 1) return LOUVAIN_E_INVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != x->device) cudaSetDevice(x->device);
+  const uint32_t mask0 = x->prof.mask;
+  const Sched start = x->sched;
+  int runs = 0;
+  std::string trials;
+  char buf[256];
+  auto run_once = [&](const Sched &s, bool prof, double *ms) -> louvain_status {
+    x->sched = s;
+    louvain_status st;
+    if (prof && (st = ensure_prof_events(x))) return st;
+    x->prof.mask = prof ? (uint32_t)((1ull << K_NUM_KERNELS) - 1) : 0u;
+    st = x->batched ? run_batched(x) : run_impl(x);
+    x->prof.mask = mask0;
+    ++runs;
+    if (st) return st;
+    *ms = x->run_ms;
+    return LOUVAIN_OK;
+  };
+  auto note = [&](const char *what, const Sched &s, double ms) {
+    int32_t w[kSchedWords];
+    sched_to_words(s, w);
+    std::string ws;
+    for (int k = 0; k < kSchedWords; ++k) ws += (k ? "," : "") + std::to_string(w[k]);
+    snprintf(buf, sizeof buf, "%s{\"step\": \"%s\", \"ms\": %.4f, \"schedule\": [%s]}", trials.empty() ? "" : ", ",
+             what, ms, ws.c_str());
+    trials += buf;
+  };
+  louvain_status st;
+  double ms = 0, start_ms = 0;
+  if ((st = run_once(start, false, &ms))) goto fail;  // warm-up
+  if ((st = run_once(start, false, &start_ms))) goto fail;
+  note("start", start, start_ms);
+  {
+    Sched best = start;
+    double best_ms = start_ms;
+    // 1. thresholds
+    const int gms[] = {16, 32, 48, 64};
+    const int wms[] = {64, 128, 256};
+    for (int gm : gms)
+      for (int wm : wms) {
+        if (wm < gm || runs >= max_runs) continue;
+        if (gm == start.group_max && wm == start.warp_max) continue;
+        Sched t = best;
+        t.group_max = gm;
+        t.warp_max = wm;
+        if ((st = run_once(t, false, &ms))) goto fail;
+        note("thresholds", t, ms);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = t;
+        }
+      }
+    // 2. blocks per SM, all bins at once per candidate
+    const int cands[] = {2, 3, 4, 6, 8, 12, 16};
+    double mv_best[kMoveBins], mg_best[kNumBins];
+    int mv_arg[kMoveBins], mg_arg[kNumBins];
+    for (int b = 0; b < kMoveBins; ++b) {
+      mv_best[b] = 1e30;
+      mv_arg[b] = best.move[b];
+    }
+    for (int b = 0; b < kNumBins; ++b) {
+      mg_best[b] = 1e30;
+      mg_arg[b] = best.merge[b];
+    }
+    static const int mv_kid[kMoveBins] = {K_MOVE_THREAD, K_MOVE_WARP, K_MOVE_MID, K_MOVE_BLOCK, K_MOVE_HUB, K_MOVE_GROUP};
+    static const int mg_kid[kNumBins] = {K_MERGE_THREAD, K_MERGE_WARP, K_MERGE_MID, K_MERGE_BLOCK, K_MERGE_BIG};
+    for (int v : cands) {
+      if (runs >= max_runs) break;
+      Sched t = best;
+      for (int b = 0; b < kMoveBins; ++b) t.move[b] = b == kBigBin ? std::min(v, 3) : v;
+      for (int b = 0; b < kNumBins; ++b) t.merge[b] = b == kBigBin ? std::min(v, 3) : v;
+      if ((st = run_once(t, true, &ms))) goto fail;
+      note("blocks", t, ms);
+      for (int b = 0; b < kMoveBins; ++b)
+        if (x->prof.launches[mv_kid[b]] > 0 && x->prof.ms[mv_kid[b]] < mv_best[b]) {
+          mv_best[b] = x->prof.ms[mv_kid[b]];
+          mv_arg[b] = t.move[b];
+        }
+      for (int b = 0; b < kNumBins; ++b)
+        if (x->prof.launches[mg_kid[b]] > 0 && x->prof.ms[mg_kid[b]] < mg_best[b]) {
+          mg_best[b] = x->prof.ms[mg_kid[b]];
+          mg_arg[b] = t.merge[b];
+        }
+    }
+    {
+      Sched t = best;
+      for (int b = 0; b < kMoveBins; ++b) t.move[b] = mv_arg[b];
+      for (int b = 0; b < kNumBins; ++b) t.merge[b] = mg_arg[b];
+      if (runs < max_runs) {
+        if ((st = run_once(t, false, &ms))) goto fail;
+        note("blocks chosen", t, ms);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = t;
+        }
+      }
+    }
+    // 3. graph replay
+    if (runs < max_runs) {
+      Sched t = best;
+      t.graphs = best.graphs ? 0 : 1;
+      if ((st = run_once(t, false, &ms))) goto fail;
+      note("graphs", t, ms);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
+    }
+    x->sched = best_ms < start_ms ? best : start;
+    if (json) {
+      int32_t w[kSchedWords];
+      sched_to_words(x->sched, w);
+      std::string ws;
+      for (int k = 0; k < kSchedWords; ++k) ws += (k ? "," : "") + std::to_string(w[k]);
+      std::string out = "{\"runs\": " + std::to_string(runs) + ", \"start_ms\": " + std::to_string(start_ms) +
+                        ", \"tuned_ms\": " + std::to_string(std::min(best_ms, start_ms)) + ", \"schedule\": [" + ws +
+                        "], \"trials\": [" + trials + "]}";
+      if (out.size() + 1 > cap) return LOUVAIN_E_INVAL;
+      memcpy(json, out.c_str(), out.size() + 1);
+    }
+  }
+  // leave the context with a valid last run under the chosen schedule
+  if ((st = run_once(x->sched, false, &ms))) goto fail;
+  return LOUVAIN_OK;
+fail:
+  x->sched = start;
+  x->prof.mask = mask0;
+  x->ran = false;
+  return st;
+}
+
 void louvain_destroy(louvain_ctx *x) {
   if (!x) return;
   for (void *p : x->allocs) cudaFreeAsync(p, x->stream);
@@ -1447,6 +1735,8 @@ void louvain_destroy(louvain_ctx *x) {
   if (x->run1) cudaEventDestroy(x->run1);
   if (x->h_ctr) cudaFreeHost(x->h_ctr);
   if (x->h_rounds) cudaFreeHost(x->h_rounds);
+  if (x->h_iter) cudaFreeHost(x->h_iter);
+  if (x->gexec) cudaGraphExecDestroy(x->gexec);
   if (x->plan_done) cudaEventDestroy(x->plan_done);
   for (void *p : x->pinned) cudaFreeHost(p);
   delete x;

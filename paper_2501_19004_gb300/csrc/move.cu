@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
   const int64_t n = a.g.n;
   const int lane = threadIdx.x & 31;
   const bool pow2 = (a.nbuckets & (a.nbuckets - 1)) == 0;
+  const uint32_t salt = a.iter ? a.iter[0] : a.salt;
   for (int64_t tile = (int64_t)blockIdx.x * blockDim.x; tile < n; tile += (int64_t)gridDim.x * blockDim.x) {
     if (threadIdx.x <= kMoveBins) s_cnt[threadIdx.x] = 0;
     __syncthreads();
@@ -49,7 +50,7 @@ __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
       local = (uint32_t)(i - a.batch.vo[gg]);
     }
     if (live) {
-      const uint32_t h = fmix32(local ^ a.salt);
+      const uint32_t h = fmix32(local ^ salt);
       const uint32_t bk = pow2 ? (h & (a.nbuckets - 1)) : (h % a.nbuckets);
       if (bk == a.bucket) {
         if (a.learn.enabled && a.learn.feat[i].w > 0.f) {
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
           a.flag[i] = 0;
           sel = true;
           const int64_t deg = a.g.end[i] - a.g.begin[i];
-          if (deg > 0) bin = move_bin(deg);
+          if (deg > 0) bin = move_bin(deg, a.sched.group_max, a.sched.warp_max);
         }
       }
     }
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(256) k_mlp_select(MoveArgs a) {
     if (eval) {
       a.flag[mine] = 0;
       const int64_t deg = a.g.end[mine] - a.g.begin[mine];
-      if (deg > 0) bin = move_bin(deg);
+      if (deg > 0) bin = move_bin(deg, a.sched.group_max, a.sched.warp_max);
       ++evaluated;
     } else if (mine >= 0) {
       ++skipped;
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(256) k_move_thread(MoveArgs a) {
         }
       }
       long long s_d = 0;
-      target = finish_decision(tm, a.Sigma, a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm, &s_d);
+      target = finish_decision(tm, a.Sigma, a.iter ? (int)a.iter[1] : a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm, &s_d);
       learn_record(a.learn, a.ctr, a.g, a.Cp, a.Sigma, a.two_m, i, Ki, Kid, best_s, best_c, s_d, target >= 0);
       if (target >= 0) batch_gain(a.batch, i, best_s, s_d);
       work[0] += 1;
@@ -341,7 +342,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_move_warp(MoveArgs a) {
     int32_t target = -1;
     if (lane == 0) {
       long long s_d = 0;
-      target = finish_decision(tm, a.Sigma, a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm, &s_d);
+      target = finish_decision(tm, a.Sigma, a.iter ? (int)a.iter[1] : a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm, &s_d);
       learn_record(a.learn, a.ctr, a.g, a.Cp, a.Sigma, a.two_m, i, Ki, Kid, best_s, best_c, s_d, target >= 0);
       if (target >= 0) batch_gain(a.batch, i, best_s, s_d);
       work[0] += 1;
@@ -447,7 +448,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_move_group(MoveArgs a) {
     int32_t target = -1;
     if (act && gl == 0) {
       long long s_d = 0;
-      target = finish_decision(tm, a.Sigma, a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm, &s_d);
+      target = finish_decision(tm, a.Sigma, a.iter ? (int)a.iter[1] : a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm, &s_d);
       learn_record(a.learn, a.ctr, a.g, a.Cp, a.Sigma, a.two_m, i, Ki, Kid, best_s, best_c, s_d, target >= 0);
       if (target >= 0) batch_gain(a.batch, i, best_s, s_d);
       work[0] += 1;
@@ -547,7 +548,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : 2) k_move_block(MoveArgs a
     block_argmax_sum<NT>(best_s, best_c, Kid);
     if (threadIdx.x == 0) {
       long long s_d = 0;
-      const int32_t t = finish_decision(tm, a.Sigma, a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm, &s_d);
+      const int32_t t = finish_decision(tm, a.Sigma, a.iter ? (int)a.iter[1] : a.pickless, d, Ki, Kid, best_s, best_c, glo, ghi, gm, &s_d);
       learn_record(a.learn, a.ctr, a.g, a.Cp, a.Sigma, a.two_m, i, Ki, Kid, best_s, best_c, s_d, t >= 0);
       if (t >= 0) batch_gain(a.batch, i, best_s, s_d);
       work[0] += 1;
@@ -663,11 +664,15 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
   if (a.learn.enabled) LV_TIMED(prof, K_MLP_SELECT, s, k_mlp_select<<<num_sms * 4, 256, 0, s>>>(a));
   const bool hubs = big.ws.slots > 0;
   if (hubs) big_move_plan(big, s, prof);  // the round count reaches the host while the bins below run
-  LV_TIMED(prof, K_MOVE_THREAD, s, k_move_thread<WK><<<num_sms * 8, 256, 0, s>>>(a));
-  LV_TIMED(prof, K_MOVE_GROUP, s, k_move_group<WK, kGroupLanes, 8><<<num_sms * 7, 256, 0, s>>>(a));
-  LV_TIMED(prof, K_MOVE_WARP, s, k_move_warp<WK, 8><<<num_sms * 7, 256, 0, s>>>(a));
-  LV_TIMED(prof, K_MOVE_MID, s, k_move_block<WK, 128, kMidCap, 2><<<num_sms * 12, 128, kMidSmem, s>>>(a));
-  LV_TIMED(prof, K_MOVE_BLOCK, s, k_move_block<WK, 512, kBlockCap, 3><<<num_sms * 3, 512, kBlockSmem, s>>>(a));
+  const int *bk = a.sched.move;
+  LV_TIMED(prof, K_MOVE_THREAD, s, k_move_thread<WK><<<num_sms * bk[0], 256, 0, s>>>(a));
+  if (a.sched.group_max > kThreadMaxDeg)
+    LV_TIMED(prof, K_MOVE_GROUP, s,
+             k_move_group<WK, kGroupLanes, 8><<<num_sms * bk[kGroupBin], 256, 0, s>>>(a));
+  LV_TIMED(prof, K_MOVE_WARP, s, k_move_warp<WK, 8><<<num_sms * bk[1], 256, 0, s>>>(a));
+  LV_TIMED(prof, K_MOVE_MID, s, k_move_block<WK, 128, kMidCap, 2><<<num_sms * bk[2], 128, kMidSmem, s>>>(a));
+  LV_TIMED(prof, K_MOVE_BLOCK, s,
+           k_move_block<WK, 512, kBlockCap, 3><<<num_sms * bk[3], 512, kBlockSmem, s>>>(a));
   if (hubs) big_move_rounds(big, WK, num_sms, s, prof);
   LV_TIMED(prof, K_APPLY, s, k_apply<<<num_sms * 4, 256, 0, s>>>(a));
 }

@@ -114,6 +114,14 @@ def load(path: Optional[str] = None):
     lib.louvain_create_batched.argtypes = [P(LouvainGraph), vp, i64, P(LouvainConfig), vp, P(vp)]
     lib.louvain_batch_results.restype = ctypes.c_int
     lib.louvain_batch_results.argtypes = [vp, vp, vp, vp]
+    lib.louvain_schedule_words.restype = i32
+    lib.louvain_schedule_words.argtypes = []
+    lib.louvain_get_schedule.restype = ctypes.c_int
+    lib.louvain_get_schedule.argtypes = [vp, vp, i32]
+    lib.louvain_set_schedule.restype = ctypes.c_int
+    lib.louvain_set_schedule.argtypes = [vp, vp, i32]
+    lib.louvain_autotune.restype = ctypes.c_int
+    lib.louvain_autotune.argtypes = [vp, i32, ctypes.c_char_p, ctypes.c_size_t]
     lib.louvain_model_size.restype = i64
     lib.louvain_model_size.argtypes = []
     lib.louvain_version.restype = ctypes.c_char_p
@@ -382,6 +390,31 @@ def louvain_batch_results(ctx, num_graphs: int, max_passes: int):
     return res, q, pr
 
 
+SCHEDULE_FIELDS = ["group_max", "warp_max", "move_thread", "move_warp", "move_mid", "move_block", "move_hub",
+                   "move_group", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big", "graphs"]
+
+
+def louvain_get_schedule(ctx) -> dict:
+    n = int(load().louvain_schedule_words())
+    w = np.zeros(n, dtype=np.int32)
+    _check(load().louvain_get_schedule(ctx, w.ctypes.data, n), ctx)
+    return dict(zip(SCHEDULE_FIELDS, (int(v) for v in w)))
+
+
+def louvain_set_schedule(ctx, sched: dict):
+    """Set schedule fields (missing ones keep their current values)."""
+    cur = louvain_get_schedule(ctx)
+    cur.update(sched)
+    w = np.array([cur[k] for k in SCHEDULE_FIELDS], dtype=np.int32)
+    _check(load().louvain_set_schedule(ctx, w.ctypes.data, w.shape[0]), ctx)
+
+
+def louvain_autotune(ctx, max_runs: int = 24) -> dict:
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(load().louvain_autotune(ctx, max_runs, buf, len(buf)), ctx)
+    return json.loads(buf.value.decode())
+
+
 def louvain_model_size() -> int:
     return int(load().louvain_model_size())
 
@@ -439,6 +472,15 @@ class Louvain:
 
     def set_profile(self, mask: int):
         louvain_set_profile(self.ctx, mask)
+
+    def schedule(self) -> dict:
+        return louvain_get_schedule(self.ctx)
+
+    def set_schedule(self, sched: dict):
+        louvain_set_schedule(self.ctx, sched)
+
+    def autotune(self, max_runs: int = 24) -> dict:
+        return louvain_autotune(self.ctx, max_runs)
 
     def close(self):
         if self.ctx:
@@ -504,6 +546,15 @@ class LouvainBatch:
 
     def set_profile(self, mask: int):
         louvain_set_profile(self.ctx, mask)
+
+    def schedule(self) -> dict:
+        return louvain_get_schedule(self.ctx)
+
+    def set_schedule(self, sched: dict):
+        louvain_set_schedule(self.ctx, sched)
+
+    def autotune(self, max_runs: int = 24) -> dict:
+        return louvain_autotune(self.ctx, max_runs)
 
     def close(self):
         if self.ctx:

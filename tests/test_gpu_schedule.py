@@ -1,0 +1,110 @@
+"""Launch schedules, the autotuner and graph replay never change results.
+
+Every schedule (bin thresholds, blocks per SM, CUDA-graph replay of the
+local-moving iterations) must give the oracle's memberships and exact
+modularity bit for bit, for single graphs and batches.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_19004_gb300 import graphgen as gg
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2501_19004_gb300 import louvain as lv  # noqa: E402
+
+
+def check_single(g, res):
+    ref = oracle.louvain(g, oracle.Config())
+    assert res.passes == ref.passes
+    assert np.array_equal(res.membership, ref.membership)
+    assert (res.q_num, res.q_den) == (ref.q_num, ref.q_den)
+    P = ref.passes
+    assert np.array_equal(res.pass_stats[:P, :4], ref.pass_stats[:P, :4])
+
+
+SCHEDULES = [
+    dict(group_max=16),                                    # no group bin
+    dict(group_max=32, warp_max=64),                       # 65..1024 in 128-thread blocks
+    dict(group_max=48, warp_max=128),
+    dict(move_thread=1, move_warp=1, move_mid=1, move_block=1, move_hub=1, move_group=1,
+         merge_thread=1, merge_warp=1, merge_mid=1, merge_block=1, merge_big=1),
+    dict(move_thread=16, move_warp=16, move_mid=16, move_block=16, move_group=16, merge_warp=16),
+    dict(graphs=1),
+    dict(graphs=1, group_max=16, warp_max=64, move_hub=2),
+]
+
+
+@pytest.mark.parametrize("sched", SCHEDULES)
+@pytest.mark.parametrize("name", ["rmat16_hubs", "rmat14_weighted", "grid64"])
+def test_schedules_bit_exact(sched, name):
+    g = {"rmat16_hubs": lambda: gg.rmat(16, 16, seed=7),
+         "rmat14_weighted": lambda: gg.rmat(14, 8, seed=3, weight_range=(1, 5)),
+         "grid64": lambda: gg.grid(64, 0.02, seed=5)}[name]()
+    with lv.Louvain(lv.DeviceCSR.from_host(g)) as ctx:
+        ctx.set_schedule(sched)
+        got = ctx.schedule()
+        for k, v in sched.items():
+            assert got[k] == v
+        r1 = ctx.run().result()
+        r2 = ctx.run().result()  # replay graphs captured by the first run's passes are rebuilt per run
+    check_single(g, r1)
+    check_single(g, r2)
+
+
+def test_graph_replay_batch():
+    graphs = [gg.batched_sbm(k) for k in (0, 1, 3, 8, 10)] + [gg.rmat(12, 16, seed=7)]
+    union, vo = gg.concat(graphs)
+    with lv.LouvainBatch(lv.DeviceCSR.from_host(union), vo) as b:
+        b.set_schedule(dict(graphs=1))
+        res = b.run().result()
+    for k, g in enumerate(graphs):
+        memb, q, num, den, passes, comms, why = res.graph(k)
+        ref = oracle.louvain(g, oracle.Config())
+        assert np.array_equal(memb, ref.membership), k
+        assert (num, den, passes, why) == (ref.q_num, ref.q_den, ref.passes, ref.exit_reason), k
+
+
+def test_autotune_keeps_results():
+    g = gg.rmat(15, 16, seed=9)
+    with lv.Louvain(lv.DeviceCSR.from_host(g)) as ctx:
+        rep = ctx.autotune(max_runs=12)
+        assert rep["runs"] <= 12 + 1
+        assert rep["tuned_ms"] <= rep["start_ms"] + 1e-9
+        assert len(rep["schedule"]) == len(lv.SCHEDULE_FIELDS)
+        assert rep["trials"] and rep["trials"][0]["step"] == "start"
+        after = ctx.result()  # the autotuner leaves a result of the chosen schedule
+        again = ctx.run().result()
+    check_single(g, after)
+    check_single(g, again)
+
+
+def test_autotune_batch():
+    graphs = [gg.batched_sbm(k) for k in (0, 1, 3, 8)]
+    union, vo = gg.concat(graphs)
+    with lv.LouvainBatch(lv.DeviceCSR.from_host(union), vo) as b:
+        rep = b.autotune(max_runs=10)
+        res = b.result()
+    assert rep["runs"] <= 11
+    for k, g in enumerate(graphs):
+        memb, q, num, den, passes, comms, why = res.graph(k)
+        ref = oracle.louvain(g, oracle.Config())
+        assert np.array_equal(memb, ref.membership)
+        assert (num, den) == (ref.q_num, ref.q_den)
+
+
+def test_bad_schedules_refused():
+    g = gg.rmat(10, 8, seed=1)
+    with lv.Louvain(g) as ctx:
+        for bad in (dict(group_max=8), dict(group_max=65), dict(group_max=64, warp_max=32), dict(warp_max=300),
+                    dict(move_warp=0), dict(move_hub=4), dict(merge_big=5), dict(graphs=2), dict(move_thread=65)):
+            before = ctx.schedule()
+            with pytest.raises(lv.LouvainError) as ei:
+                ctx.set_schedule(bad)
+            assert ei.value.status == 1
+            assert ctx.schedule() == before
