@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(256) k_comm_compact(AggArgs a, int64_t n) {
         const int64_t cd = h1 - h0;
         a.oend[k] = h1;  // row capacity until the merge writes the true end
         if (cd > 0) {
-          bin = degree_bin(cd);
+          bin = merge_bin(cd);
           if ((unsigned long long)cd > md) md = (unsigned long long)cd;
           if (bin == kBigBin) {
             big_slots += big_table_cap((unsigned long long)cd, (unsigned long long)a.gamma);
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256) k_comm_compact(AggArgs a, int64_t n) {
       }
     }
 #pragma unroll
-    for (int b = 0; b < kNumBins; ++b) {
+    for (int b = 0; b < kMergeBins; ++b) {
       const bool p = bin == b;
       const unsigned mask = __ballot_sync(kFull, p);
       if (!mask) continue;
@@ -387,10 +387,10 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_merge_warp(AggArgs a) {
 }
 
 // Block per community: 128 threads and a 2048-slot table up to 1024
-// entries, 512 threads and an 8192-slot table up to 4096; a run of 8
-// consecutive entries per thread.
+// entries, 512 threads and an 8192-slot table up to 4096, 1024 threads and a
+// 16384-slot table up to 8192; a run of 8 consecutive entries per thread.
 template <int WK, int NT, int CAP, int BIN>
-__global__ void __launch_bounds__(NT, NT == 128 ? 8 : 2) k_merge_block(AggArgs a) {
+__global__ void __launch_bounds__(NT, NT == 128 ? 8 : NT == 512 ? 2 : 1) k_merge_block(AggArgs a) {
   // dynamic shared memory: keys[CAP], vals[CAP], occupied list[CAP / 2]
   extern __shared__ uint32_t dyn[];
   int32_t *keys = (int32_t *)dyn;
@@ -501,9 +501,12 @@ void merge_t(const AggArgs &a, int num_sms, cudaStream_t s, KernelProf *prof) {
   static bool attr_done = false;
   constexpr size_t kMidSmem = (size_t)kMidCap * (sizeof(uint32_t) + sizeof(int32_t)) + kMidCap / 2 * sizeof(uint16_t);
   constexpr size_t kSmem = (size_t)kBlockCap * (sizeof(uint32_t) + sizeof(int32_t)) + kBlockCap / 2 * sizeof(uint16_t);
+  constexpr size_t kXlSmem = (size_t)kXlCap * (sizeof(uint32_t) + sizeof(int32_t)) + kXlCap / 2 * sizeof(uint16_t);
   if (!attr_done) {
     cudaFuncSetAttribute(k_merge_block<WK, 512, kBlockCap, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kSmem);
+    cudaFuncSetAttribute(k_merge_block<WK, 1024, kXlCap, kMergeXlBin>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kXlSmem);
     attr_done = true;
   }
   const int *bk = a.sched.merge;
@@ -511,6 +514,8 @@ void merge_t(const AggArgs &a, int num_sms, cudaStream_t s, KernelProf *prof) {
   LV_TIMED(prof, K_MERGE_WARP, s, k_merge_warp<WK, 8><<<num_sms * bk[1], 256, 0, s>>>(a));
   LV_TIMED(prof, K_MERGE_MID, s, k_merge_block<WK, 128, kMidCap, 2><<<num_sms * bk[2], 128, kMidSmem, s>>>(a));
   LV_TIMED(prof, K_MERGE_BLOCK, s, k_merge_block<WK, 512, kBlockCap, 3><<<num_sms * bk[3], 512, kSmem, s>>>(a));
+  LV_TIMED(prof, K_MERGE_XL, s,
+           k_merge_block<WK, 1024, kXlCap, kMergeXlBin><<<num_sms * bk[kMergeXlBin], 1024, kXlSmem, s>>>(a));
   if (a.big.ws.slots > 0) big_merge(a.big, WK, num_sms, s, prof);
 }
 

@@ -46,10 +46,10 @@ struct Counters {
   unsigned long long it_moves;
   unsigned long long it_evaluated;
   unsigned long long it_skipped;    // learned mode: flagged vertices skipped by the predictor
-  unsigned long long mv_work[6][5]; // per move bin: vertices, entries, distinct keys, movers, mover entries
+  unsigned long long mv_work[7][5]; // per move bin: vertices, entries, distinct keys, movers, mover entries
   // ---- zeroed every pass ----
   unsigned long long mbin_count[8]; // aggregation bin sizes
-  unsigned long long mg_work[5][4]; // per merge bin: communities, members, entries, entries written
+  unsigned long long mg_work[6][4]; // per merge bin: communities, members, entries, entries written
   unsigned long long maxdeg;
   unsigned long long big_slots;     // bound on the global table slots of big items
   unsigned long long big_items;     // number of big items (hubs / large communities)
@@ -63,7 +63,7 @@ struct Counters {
   unsigned long long trace_count;   // recorded (features, moved) samples
   unsigned long long pad[2];
 };
-constexpr int kIterCounterWords = 5 + 30;
+constexpr int kIterCounterWords = 5 + 35;
 
 // MurmurHash3 finaliser (Appleby, public domain).
 __host__ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {

@@ -32,7 +32,20 @@ __host__ __device__ __forceinline__ int degree_bin(int64_t d) {
 constexpr int kGroupLanes = 8;
 constexpr int kGroupMaxDeg = 64;  // kGroupLanes lanes x 8 entries
 constexpr int kGroupBin = 5;
-constexpr int kMoveBins = 6;
+// Local moving also splits the big bin: 4096 < degree <= kXlMaxDeg goes to
+// one 1024-thread block with a 16384-slot shared table (144 KB); only larger
+// degrees use global tables.
+constexpr int kXlMaxDeg = 8192;
+constexpr int kXlCap = 16384;
+constexpr int kXlBin = 6;
+constexpr int kMoveBins = 7;
+// Aggregation bins: degree_bin's five plus communities with a total member
+// degree in (4096, kXlMaxDeg] for one 1024-thread block (bin 5).
+constexpr int kMergeXlBin = 5;
+constexpr int kMergeBins = 6;
+__host__ __device__ __forceinline__ int merge_bin(int64_t d) {
+  return (d > kBlockMaxDeg && d <= kXlMaxDeg) ? kMergeXlBin : degree_bin(d);
+}
 
 // Launch schedule of the binned kernels (louvain_autotune chooses one; the
 // results never depend on it, since every bin's kernel computes the same
@@ -46,17 +59,19 @@ constexpr int kMoveBins = 6;
 struct Sched {
   int group_max = kGroupMaxDeg;
   int warp_max = kWarpMaxDeg;
-  int move[kMoveBins] = {2, 8, 12, 2, 3, 4};  // thread, warp, mid, block, hub, group
-  int merge[kNumBins] = {8, 8, 8, 2, 3};      // thread, warp, mid, block, big
+  int move[kMoveBins] = {2, 8, 12, 2, 3, 4, 1};  // thread, warp, mid, block, hub, group, xl
+  int merge[kMergeBins] = {8, 8, 8, 2, 3, 1};   // thread, warp, mid, block, big, xl
   int graphs = 0;
 };
-constexpr int kSchedWords = 2 + kMoveBins + kNumBins + 1;
+constexpr int kSchedWords = 2 + kMoveBins + kMergeBins + 1;
 
 __host__ __device__ __forceinline__ int move_bin(int64_t d, int group_max, int warp_max) {
   if (d <= kThreadMaxDeg) return 0;
   if (d <= group_max) return kGroupBin;
   if (d <= warp_max) return 1;
-  return degree_bin(d) == 1 ? 2 : degree_bin(d);
+  if (d <= kMidMaxDeg) return 2;
+  if (d <= kBlockMaxDeg) return 3;
+  return d <= kXlMaxDeg ? kXlBin : kBigBin;
 }
 
 // Global tables of big items (hub vertices in local moving, communities with
@@ -211,7 +226,7 @@ struct MoveArgs {
 enum KernelId : int {
   K_SELECT = 0, K_MOVE_THREAD, K_MOVE_WARP, K_MOVE_MID, K_MOVE_BLOCK, K_MOVE_HUB, K_APPLY, K_PASS_INIT,
   K_COMM_COUNT, K_SCATTER, K_MERGE_THREAD, K_MERGE_WARP, K_MERGE_MID, K_MERGE_BLOCK, K_MERGE_BIG, K_DENDRO,
-  K_MODULARITY, K_RENUMBER, K_MOVE_HUB_EVAL, K_MERGE_BIG_EMIT, K_MLP_SELECT, K_MOVE_GROUP, K_NUM_KERNELS
+  K_MODULARITY, K_RENUMBER, K_MOVE_HUB_EVAL, K_MERGE_BIG_EMIT, K_MLP_SELECT, K_MOVE_GROUP, K_MOVE_XL, K_MERGE_XL, K_NUM_KERNELS
 };
 extern const char *const kKernelNames[K_NUM_KERNELS];
 
@@ -271,7 +286,7 @@ struct AggArgs {
   int32_t *members;         // [n']
   int64_t *kcoff;           // [Gamma]
   int32_t *kcnt;            // [Gamma]
-  int32_t *mbins[kNumBins]; // merge bins [Gamma] each
+  int32_t *mbins[kMergeBins]; // merge bins [Gamma] each
   // output super-vertex graph (holey CSR)
   int64_t *obegin;          // [Gamma]
   int64_t *oend;            // [Gamma]

@@ -329,7 +329,7 @@ void account_move(louvain_ctx *x, int64_t n, const Counters &h) {
       x->kbytes[K_MOVE_HUB_EVAL] += 40.0 * w[0] + 8.0 * w[2] + 8.0 * w[3] + 1.0 * w[4];
       continue;
     }
-    x->kbytes[b == kGroupBin ? K_MOVE_GROUP : K_MOVE_THREAD + b] +=
+    x->kbytes[b == kGroupBin ? K_MOVE_GROUP : b == kXlBin ? K_MOVE_XL : K_MOVE_THREAD + b] +=
         40.0 * w[0] + (8.0 + wb) * w[1] + 8.0 * w[2] + 8.0 * w[3] + 1.0 * w[4];
   }
   x->kbytes[K_SELECT] += (double)x->cfg.buckets * n + 21.0 * h.it_evaluated;
@@ -342,14 +342,15 @@ void account_move(louvain_ctx *x, int64_t n, const Counters &h) {
 void account_merge(louvain_ctx *x, const Counters &h) {
   if (x->prof.mask) x->prof.collect();
   const double wb = x->cur_wbytes;
-  for (int b = 0; b < kNumBins; ++b) {
+  for (int b = 0; b < kMergeBins; ++b) {
     const unsigned long long *w = h.mg_work[b];
     if (b == kBigBin) {
       x->kbytes[K_MERGE_BIG] += 20.0 * w[1] + (8.0 + wb) * w[2];
       x->kbytes[K_MERGE_BIG_EMIT] += 36.0 * w[0] + 8.0 * w[3];
       continue;
     }
-    x->kbytes[K_MERGE_THREAD + b] += 36.0 * w[0] + 20.0 * w[1] + (8.0 + wb) * w[2] + 8.0 * w[3];
+    x->kbytes[b == kMergeXlBin ? K_MERGE_XL : K_MERGE_THREAD + b] +=
+        36.0 * w[0] + 20.0 * w[1] + (8.0 + wb) * w[2] + 8.0 * w[3];
   }
 }
 
@@ -654,6 +655,7 @@ AggArgs agg_args(louvain_ctx *x, const GView &g, int wk, int slot) {
   aa.kcoff = x->kcoff;
   aa.kcnt = x->kcnt;
   for (int k = 0; k < kNumBins; ++k) aa.mbins[k] = x->bins[k];
+  aa.mbins[kMergeXlBin] = x->bins[kXlBin];
   aa.obegin = x->pbeg[slot];
   aa.oend = x->pend[slot];
   aa.ocol = x->pcol[slot];
@@ -1535,7 +1537,7 @@ static void sched_to_words(const Sched &s, int32_t *w) {
   w[k++] = s.group_max;
   w[k++] = s.warp_max;
   for (int b = 0; b < kMoveBins; ++b) w[k++] = s.move[b];
-  for (int b = 0; b < kNumBins; ++b) w[k++] = s.merge[b];
+  for (int b = 0; b < kMergeBins; ++b) w[k++] = s.merge[b];
   w[k++] = s.graphs;
 }
 
@@ -1545,13 +1547,13 @@ static bool sched_from_words(const int32_t *w, Sched *s) {
   t.group_max = w[k++];
   t.warp_max = w[k++];
   for (int b = 0; b < kMoveBins; ++b) t.move[b] = w[k++];
-  for (int b = 0; b < kNumBins; ++b) t.merge[b] = w[k++];
+  for (int b = 0; b < kMergeBins; ++b) t.merge[b] = w[k++];
   t.graphs = w[k++];
   if (t.group_max < kThreadMaxDeg || t.group_max > kGroupMaxDeg) return false;
   if (t.warp_max < t.group_max || t.warp_max > kWarpMaxDeg) return false;
   for (int b = 0; b < kMoveBins; ++b)
     if (t.move[b] < 1 || t.move[b] > 64) return false;
-  for (int b = 0; b < kNumBins; ++b)
+  for (int b = 0; b < kMergeBins; ++b)
     if (t.merge[b] < 1 || t.merge[b] > 64) return false;
   if (t.move[kBigBin] > 3 || t.merge[kBigBin] > 3) return false;  // accumulation: 3 blocks per SM at most
   if (t.graphs != 0 && t.graphs != 1) return false;
@@ -1643,23 +1645,25 @@ louvain_status louvain_autotune(louvain_ctx *x, int32_t max_runs, char *json, si
       }
     // 2. blocks per SM, all bins at once per candidate
     const int cands[] = {2, 3, 4, 6, 8, 12, 16};
-    double mv_best[kMoveBins], mg_best[kNumBins];
-    int mv_arg[kMoveBins], mg_arg[kNumBins];
+    double mv_best[kMoveBins], mg_best[kMergeBins];
+    int mv_arg[kMoveBins], mg_arg[kMergeBins];
     for (int b = 0; b < kMoveBins; ++b) {
       mv_best[b] = 1e30;
       mv_arg[b] = best.move[b];
     }
-    for (int b = 0; b < kNumBins; ++b) {
+    for (int b = 0; b < kMergeBins; ++b) {
       mg_best[b] = 1e30;
       mg_arg[b] = best.merge[b];
     }
-    static const int mv_kid[kMoveBins] = {K_MOVE_THREAD, K_MOVE_WARP, K_MOVE_MID, K_MOVE_BLOCK, K_MOVE_HUB, K_MOVE_GROUP};
-    static const int mg_kid[kNumBins] = {K_MERGE_THREAD, K_MERGE_WARP, K_MERGE_MID, K_MERGE_BLOCK, K_MERGE_BIG};
+    static const int mv_kid[kMoveBins] = {K_MOVE_THREAD, K_MOVE_WARP, K_MOVE_MID, K_MOVE_BLOCK,
+                                          K_MOVE_HUB,    K_MOVE_GROUP, K_MOVE_XL};
+    static const int mg_kid[kMergeBins] = {K_MERGE_THREAD, K_MERGE_WARP, K_MERGE_MID,
+                                           K_MERGE_BLOCK,  K_MERGE_BIG,  K_MERGE_XL};
     for (int v : cands) {
       if (runs >= max_runs) break;
       Sched t = best;
       for (int b = 0; b < kMoveBins; ++b) t.move[b] = b == kBigBin ? std::min(v, 3) : v;
-      for (int b = 0; b < kNumBins; ++b) t.merge[b] = b == kBigBin ? std::min(v, 3) : v;
+      for (int b = 0; b < kMergeBins; ++b) t.merge[b] = b == kBigBin ? std::min(v, 3) : v;
       if ((st = run_once(t, true, &ms))) goto fail;
       note("blocks", t, ms);
       for (int b = 0; b < kMoveBins; ++b)
@@ -1667,7 +1671,7 @@ louvain_status louvain_autotune(louvain_ctx *x, int32_t max_runs, char *json, si
           mv_best[b] = x->prof.ms[mv_kid[b]];
           mv_arg[b] = t.move[b];
         }
-      for (int b = 0; b < kNumBins; ++b)
+      for (int b = 0; b < kMergeBins; ++b)
         if (x->prof.launches[mg_kid[b]] > 0 && x->prof.ms[mg_kid[b]] < mg_best[b]) {
           mg_best[b] = x->prof.ms[mg_kid[b]];
           mg_arg[b] = t.merge[b];
@@ -1676,7 +1680,7 @@ louvain_status louvain_autotune(louvain_ctx *x, int32_t max_runs, char *json, si
     {
       Sched t = best;
       for (int b = 0; b < kMoveBins; ++b) t.move[b] = mv_arg[b];
-      for (int b = 0; b < kNumBins; ++b) t.merge[b] = mg_arg[b];
+      for (int b = 0; b < kMergeBins; ++b) t.merge[b] = mg_arg[b];
       if (runs < max_runs) {
         if ((st = run_once(t, false, &ms))) goto fail;
         note("blocks chosen", t, ms);

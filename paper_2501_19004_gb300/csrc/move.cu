@@ -487,10 +487,11 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_move_group(MoveArgs a) {
 
 // ---------------------------------------------------------------- block bins
 // 256 < degree <= 1024: 128 threads and a 2048-slot table; 1024 < degree <=
-// 4096: 512 threads and an 8192-slot table (dynamic shared memory).  Each
-// thread reads 8 entries per round, strided by the block size.
+// 4096: 512 threads and an 8192-slot table; 4096 < degree <= 8192: 1024
+// threads and a 16384-slot table (dynamic shared memory).  Each thread reads
+// 8 entries per round, strided by the block size.
 template <int WK, int NT, int CAP, int BIN>
-__global__ void __launch_bounds__(NT, NT == 128 ? 8 : 2) k_move_block(MoveArgs a) {
+__global__ void __launch_bounds__(NT, NT == 128 ? 8 : NT == 512 ? 2 : 1) k_move_block(MoveArgs a) {
   // dynamic shared memory: keys[CAP], vals[CAP], occupied list[CAP / 2]
   // (a row of degree <= CAP / 2 has at most CAP / 2 distinct keys)
   extern __shared__ uint32_t dyn[];
@@ -606,7 +607,7 @@ __global__ void __launch_bounds__(256) k_pass_init(GView g, int first_pass, int6
     const int64_t b = g.begin[i], e = g.end[i];
     const unsigned long long deg = (unsigned long long)(e - b);
     if (deg > md) md = deg;
-    if (degree_bin((int64_t)deg) == kBigBin) {
+    if (deg > (unsigned long long)kXlMaxDeg) {  // hubs of the global tables
       big_slots += big_table_cap(deg, (unsigned long long)g.n);
       big_items += 1;
     }
@@ -655,9 +656,12 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
   constexpr size_t kMidSmem = (size_t)kMidCap * (sizeof(uint32_t) + sizeof(int32_t)) + kMidCap / 2 * sizeof(uint16_t);
   constexpr size_t kBlockSmem =
       (size_t)kBlockCap * (sizeof(uint32_t) + sizeof(int32_t)) + kBlockCap / 2 * sizeof(uint16_t);
+  constexpr size_t kXlSmem = (size_t)kXlCap * (sizeof(uint32_t) + sizeof(int32_t)) + kXlCap / 2 * sizeof(uint16_t);
   if (!attr_done) {
     cudaFuncSetAttribute(k_move_block<WK, 512, kBlockCap, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kBlockSmem);
+    cudaFuncSetAttribute(k_move_block<WK, 1024, kXlCap, kXlBin>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kXlSmem);
     attr_done = true;
   }
   LV_TIMED(prof, K_SELECT, s, k_select<<<grid_for(a.g.n, 256, num_sms, 8), 256, 0, s>>>(a));
@@ -673,6 +677,8 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
   LV_TIMED(prof, K_MOVE_MID, s, k_move_block<WK, 128, kMidCap, 2><<<num_sms * bk[2], 128, kMidSmem, s>>>(a));
   LV_TIMED(prof, K_MOVE_BLOCK, s,
            k_move_block<WK, 512, kBlockCap, 3><<<num_sms * bk[3], 512, kBlockSmem, s>>>(a));
+  LV_TIMED(prof, K_MOVE_XL, s,
+           k_move_block<WK, 1024, kXlCap, kXlBin><<<num_sms * bk[kXlBin], 1024, kXlSmem, s>>>(a));
   if (hubs) big_move_rounds(big, WK, num_sms, s, prof);
   LV_TIMED(prof, K_APPLY, s, k_apply<<<num_sms * 4, 256, 0, s>>>(a));
 }
@@ -709,6 +715,6 @@ void iota_i32(int32_t *x, int64_t n, int num_sms, cudaStream_t s) {
 const char *const kKernelNames[K_NUM_KERNELS] = {
     "select", "move_thread", "move_warp", "move_mid", "move_block", "move_hub", "apply", "pass_init",
     "comm_count", "comm_scatter", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big",
-    "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit", "mlp_select", "move_group"};
+    "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit", "mlp_select", "move_group", "move_xl", "merge_xl"};
 
 }  // namespace lv

@@ -28,7 +28,8 @@ STATUS = {0: "OK", 1: "E_INVAL", 2: "E_NOMEM", 3: "E_CUDA", 4: "E_HASH_OVERFLOW"
 MODE_PLAIN, MODE_LEARNED = 0, 1
 KERNELS = ["select", "move_thread", "move_warp", "move_mid", "move_block", "move_hub", "apply", "pass_init",
            "comm_count", "comm_scatter", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big",
-           "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit", "mlp_select", "move_group"]
+           "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit", "mlp_select", "move_group",
+           "move_xl", "merge_xl"]
 
 
 def kernel_mask(*names) -> int:
@@ -391,7 +392,8 @@ def louvain_batch_results(ctx, num_graphs: int, max_passes: int):
 
 
 SCHEDULE_FIELDS = ["group_max", "warp_max", "move_thread", "move_warp", "move_mid", "move_block", "move_hub",
-                   "move_group", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big", "graphs"]
+                   "move_group", "move_xl", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big",
+                   "merge_xl", "graphs"]
 
 
 def louvain_get_schedule(ctx) -> dict:

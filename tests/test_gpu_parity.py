@@ -60,6 +60,7 @@ CASES = {
     "rmat12": lambda: gg.rmat(12, 16, seed=7),
     "rmat14_weighted": lambda: gg.rmat(14, 8, seed=3, weight_range=(1, 5)),
     "rmat16_hubs": lambda: gg.rmat(16, 16, seed=7),
+    "rmat18_hubs": lambda: gg.rmat(18, 16, seed=7),  # 172 vertices above 4096, 19 above 8192
     "grid96": lambda: gg.grid(96, 0.02, seed=11),
     "ring8x10": lambda: gg.ring_of_cliques(8, 10),
     "batched_sbm_0": lambda: gg.batched_sbm(0),
