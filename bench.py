@@ -76,7 +76,7 @@ SAMPLES = {
 
 
 # timing groups that are one kernel per launch (candidates for the roofline)
-SINGLE_KERNELS = {"select", "move_thread", "move_group", "move_xl", "move_warp", "move_mid", "move_block", "move_hub", "apply",
+SINGLE_KERNELS = {"select", "move_thread", "move_group", "move_xl", "move_cluster", "move_warp", "move_mid", "move_block", "move_hub", "apply",
                   "pass_init", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big", "merge_xl", "dendrogram"}
 
 

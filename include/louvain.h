@@ -165,12 +165,13 @@ louvain_status louvain_set_profile(louvain_ctx *ctx, uint32_t profile_mask);
  *   [0] group_max: largest degree handled by 8-lane groups (16 .. 64;
  *       16 = no group bin); [1] warp_max: largest degree handled by a warp
  *       (group_max .. 256; larger degrees up to 1024 go to 128-thread blocks);
- *   [2..8] blocks per SM of the local-moving kernels of the thread, warp,
- *       128-thread, 512-thread, hub (<= 3), group and 1024-thread bins
- *       (1 .. 64);
- *   [9..14] blocks per SM of the aggregation kernels of the thread, warp,
+ *   [2..9] blocks per SM of the local-moving kernels of the thread, warp,
+ *       128-thread, 512-thread, hub (<= 3), group, 1024-thread and
+ *       4-block-cluster bins (1 .. 64; the cluster grid is rounded to whole
+ *       clusters);
+ *   [10..15] blocks per SM of the aggregation kernels of the thread, warp,
  *       128-thread, 512-thread, big-community (<= 3) and 1024-thread bins;
- *   [15] graphs: 1 = each local-moving iteration is replayed from a CUDA
+ *   [16] graphs: 1 = each local-moving iteration is replayed from a CUDA
  *       graph captured once per pass (plain mode, no profiling).
  * Results never depend on the schedule: every bin computes the same exact
  * decisions.  The schedule belongs to the context and is used by its next

@@ -38,7 +38,13 @@ constexpr int kGroupBin = 5;
 constexpr int kXlMaxDeg = 8192;
 constexpr int kXlCap = 16384;
 constexpr int kXlBin = 6;
-constexpr int kMoveBins = 7;
+// Hubs of degree (kXlMaxDeg, kClusterMaxDeg] go to a thread-block cluster of
+// kClusterSize 1024-thread blocks whose shared tables form one distributed
+// table of kClusterSize * kXlCap slots (distributed shared memory).
+constexpr int kClusterSize = 4;
+constexpr int kClusterMaxDeg = kXlMaxDeg * kClusterSize;
+constexpr int kClusterBin = 7;
+constexpr int kMoveBins = 8;
 // Aggregation bins: degree_bin's five plus communities with a total member
 // degree in (4096, kXlMaxDeg] for one 1024-thread block (bin 5).
 constexpr int kMergeXlBin = 5;
@@ -59,7 +65,7 @@ __host__ __device__ __forceinline__ int merge_bin(int64_t d) {
 struct Sched {
   int group_max = kGroupMaxDeg;
   int warp_max = kWarpMaxDeg;
-  int move[kMoveBins] = {2, 8, 12, 2, 3, 4, 1};  // thread, warp, mid, block, hub, group, xl
+  int move[kMoveBins] = {2, 8, 12, 2, 3, 4, 1, 1};  // thread, warp, mid, block, hub, group, xl, cluster
   int merge[kMergeBins] = {8, 8, 8, 2, 3, 1};   // thread, warp, mid, block, big, xl
   int graphs = 0;
 };
@@ -71,7 +77,8 @@ __host__ __device__ __forceinline__ int move_bin(int64_t d, int group_max, int w
   if (d <= warp_max) return 1;
   if (d <= kMidMaxDeg) return 2;
   if (d <= kBlockMaxDeg) return 3;
-  return d <= kXlMaxDeg ? kXlBin : kBigBin;
+  if (d <= kXlMaxDeg) return kXlBin;
+  return d <= kClusterMaxDeg ? kClusterBin : kBigBin;
 }
 
 // Global tables of big items (hub vertices in local moving, communities with
@@ -226,7 +233,7 @@ struct MoveArgs {
 enum KernelId : int {
   K_SELECT = 0, K_MOVE_THREAD, K_MOVE_WARP, K_MOVE_MID, K_MOVE_BLOCK, K_MOVE_HUB, K_APPLY, K_PASS_INIT,
   K_COMM_COUNT, K_SCATTER, K_MERGE_THREAD, K_MERGE_WARP, K_MERGE_MID, K_MERGE_BLOCK, K_MERGE_BIG, K_DENDRO,
-  K_MODULARITY, K_RENUMBER, K_MOVE_HUB_EVAL, K_MERGE_BIG_EMIT, K_MLP_SELECT, K_MOVE_GROUP, K_MOVE_XL, K_MERGE_XL, K_NUM_KERNELS
+  K_MODULARITY, K_RENUMBER, K_MOVE_HUB_EVAL, K_MERGE_BIG_EMIT, K_MLP_SELECT, K_MOVE_GROUP, K_MOVE_XL, K_MERGE_XL, K_MOVE_CLUSTER, K_NUM_KERNELS
 };
 extern const char *const kKernelNames[K_NUM_KERNELS];
 
@@ -329,8 +336,11 @@ void renumber_dense(int32_t *x, int64_t n, int64_t idspace, unsigned long long *
 // learned predictor (device pointers; see mlp.cu)
 int64_t mlp_param_count();
 void mlp_forward(const float *params, const float *X, int64_t n, float *logit, cudaStream_t s);
+// gradient of the mean BCE added into grad (and the loss into *loss);
+// scratch holds mlp_grad_scratch_floats(n) floats (per-block partials)
+size_t mlp_grad_scratch_floats(int64_t n);
 void mlp_gradient(const float *params, const float *X, const float *Y, int64_t n, float scale, float *grad,
-                  float *loss, cudaStream_t s);
+                  float *loss, float *scratch, cudaStream_t s);
 void mlp_adam(float *params, const float *grad, float *m, float *v, float lr, int step, cudaStream_t s);
 void mlp_gather_batch(const float *X, const float *Y, int64_t n, int64_t start, int64_t count, uint64_t stride,
                       float *Xb, float *Yb, cudaStream_t s);

@@ -329,7 +329,7 @@ void account_move(louvain_ctx *x, int64_t n, const Counters &h) {
       x->kbytes[K_MOVE_HUB_EVAL] += 40.0 * w[0] + 8.0 * w[2] + 8.0 * w[3] + 1.0 * w[4];
       continue;
     }
-    x->kbytes[b == kGroupBin ? K_MOVE_GROUP : b == kXlBin ? K_MOVE_XL : K_MOVE_THREAD + b] +=
+    x->kbytes[b == kGroupBin ? K_MOVE_GROUP : b == kXlBin ? K_MOVE_XL : b == kClusterBin ? K_MOVE_CLUSTER : K_MOVE_THREAD + b] +=
         40.0 * w[0] + (8.0 + wb) * w[1] + 8.0 * w[2] + 8.0 * w[3] + 1.0 * w[4];
   }
   x->kbytes[K_SELECT] += (double)x->cfg.buckets * n + 21.0 * h.it_evaluated;
@@ -1656,7 +1656,7 @@ louvain_status louvain_autotune(louvain_ctx *x, int32_t max_runs, char *json, si
       mg_arg[b] = best.merge[b];
     }
     static const int mv_kid[kMoveBins] = {K_MOVE_THREAD, K_MOVE_WARP, K_MOVE_MID, K_MOVE_BLOCK,
-                                          K_MOVE_HUB,    K_MOVE_GROUP, K_MOVE_XL};
+                                          K_MOVE_HUB,    K_MOVE_GROUP, K_MOVE_XL,  K_MOVE_CLUSTER};
     static const int mg_kid[kMergeBins] = {K_MERGE_THREAD, K_MERGE_WARP, K_MERGE_MID,
                                            K_MERGE_BLOCK,  K_MERGE_BIG,  K_MERGE_XL};
     for (int v : cands) {
@@ -1823,7 +1823,16 @@ louvain_status louvain_mlp_gradient(const float *params, const float *X, const f
                                     float *loss, void *stream) {
   if (!params || !grad || n < 0 || (n > 0 && (!X || !Y))) return LOUVAIN_E_INVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  if (n > 0) mlp_gradient(params, X, Y, n, 1.0f / (float)n, grad, loss, s);
+  if (n > 0) {
+    float *scratch = nullptr;
+    if (cudaMallocAsync((void **)&scratch, sizeof(float) * mlp_grad_scratch_floats(n), s) != cudaSuccess) {
+      cudaGetLastError();
+      g_create_err = "allocation for the MLP gradient failed";
+      return LOUVAIN_E_NOMEM;
+    }
+    mlp_gradient(params, X, Y, n, 1.0f / (float)n, grad, loss, scratch, s);
+    cudaFreeAsync(scratch, s);
+  }
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
     g_create_err = "MLP gradient kernel failed";
     return LOUVAIN_E_CUDA;
@@ -1836,9 +1845,9 @@ louvain_status louvain_mlp_train(float *params, const float *X, const float *Y, 
   if (!params || n <= 0 || !X || !Y || epochs < 0 || batch < 16 || !(lr > 0)) return LOUVAIN_E_INVAL;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t b = std::min<int64_t>(batch, n);
-  float *grad = nullptr, *m = nullptr, *v = nullptr, *Xb = nullptr, *Yb = nullptr, *lossd = nullptr;
+  float *grad = nullptr, *m = nullptr, *v = nullptr, *Xb = nullptr, *Yb = nullptr, *lossd = nullptr, *scratch = nullptr;
   auto cleanup = [&]() {
-    for (void *p : {(void *)grad, (void *)m, (void *)v, (void *)Xb, (void *)Yb, (void *)lossd})
+    for (void *p : {(void *)grad, (void *)m, (void *)v, (void *)Xb, (void *)Yb, (void *)lossd, (void *)scratch})
       if (p) cudaFreeAsync(p, s);
     cudaStreamSynchronize(s);
   };
@@ -1846,7 +1855,8 @@ louvain_status louvain_mlp_train(float *params, const float *X, const float *Y, 
       cudaMallocAsync((void **)&m, sizeof(float) * kMlpParams, s) ||
       cudaMallocAsync((void **)&v, sizeof(float) * kMlpParams, s) ||
       cudaMallocAsync((void **)&Xb, sizeof(float) * kFeatures * b, s) ||
-      cudaMallocAsync((void **)&Yb, sizeof(float) * b, s) || cudaMallocAsync((void **)&lossd, sizeof(float), s)) {
+      cudaMallocAsync((void **)&Yb, sizeof(float) * b, s) || cudaMallocAsync((void **)&lossd, sizeof(float), s) ||
+      cudaMallocAsync((void **)&scratch, sizeof(float) * mlp_grad_scratch_floats(b), s)) {
     cudaGetLastError();
     cleanup();
     g_create_err = "allocation for MLP training failed";
@@ -1874,7 +1884,7 @@ louvain_status louvain_mlp_train(float *params, const float *X, const float *Y, 
       const int64_t cnt = std::min<int64_t>(b, n - start);
       mlp_gather_batch(X, Y, n, (int64_t)offset + start, cnt, stride, Xb, Yb, s);
       cudaMemsetAsync(grad, 0, sizeof(float) * kMlpParams, s);
-      mlp_gradient(params, Xb, Yb, cnt, 1.0f / (float)cnt, grad, lossd, s);
+      mlp_gradient(params, Xb, Yb, cnt, 1.0f / (float)cnt, grad, lossd, scratch, s);
       mlp_adam(params, grad, m, v, lr, ++step, s);
     }
     if (losses) {

@@ -16,7 +16,11 @@
 //                   (p - y)/N, ReLU masks), dh1 = dz2 W2^T on the tensor cores,
 //                   weight gradients dW2 = h1^T dz2 and dW1 = x^T dz1 as
 //                   tensor-core contractions over the samples (bf16 operands),
-//                   bias gradients in fp32; atomically added into `grad`;
+//                   bias gradients in fp32; every block sums its tiles in
+//                   shared memory and writes one partial gradient;
+//   k_mlp_reduce    adds the blocks' partials into `grad` in block order, so
+//                   a gradient (and a training run) is the same bit for bit
+//                   on every run;
 //   k_mlp_adam      Adam update of the fp32 parameters.
 #include <cuda_bf16.h>
 
@@ -61,12 +65,15 @@ __global__ void __launch_bounds__(256) k_mlp_forward(const float *params, const 
 // --------------------------------------------------------------- k_mlp_grad
 // Shared tiles per block (row = sample): x (bf16, 16 columns, 8 used), h1 and
 // dz2 and dz1 (bf16, 32 columns); bias-gradient partials in fp32.
+// Per-warp bias partials of a tile (each written by one lane), and the
+// block's running gradient over its tiles (acc, loss).
 struct GradSmem {
   __nv_bfloat16 x[kGradSamples][16];
   __nv_bfloat16 h1[kGradSamples][32];
   __nv_bfloat16 dz2[kGradSamples][32];
   __nv_bfloat16 dz1[kGradSamples][32];
-  float db1[32], db2[32], dw3[32], db3;
+  float db1[8][32], db2[8][32], dw3[8][32], db3[8], wloss[8];
+  float acc[kMlpParams];
   float loss;
 };
 
@@ -78,7 +85,7 @@ __device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16 *a, const __nv_b
 }
 
 __global__ void __launch_bounds__(256) k_mlp_grad(const float *params, const float *X, const float *Y, int64_t n,
-                                                  float scale, float *grad, float *loss) {
+                                                  float scale, float *partial) {
   __shared__ GradSmem sm;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, t = lane & 3;
@@ -95,17 +102,10 @@ __global__ void __launch_bounds__(256) k_mlp_grad(const float *params, const flo
       bT[s][j][0] = pack_bf16(params[kW2 + nn * 32 + k0], params[kW2 + nn * 32 + k0 + 1]);
       bT[s][j][1] = pack_bf16(params[kW2 + nn * 32 + k0 + 8], params[kW2 + nn * 32 + k0 + 9]);
     }
+  for (int p = threadIdx.x; p < kMlpParams; p += blockDim.x) sm.acc[p] = 0.f;
+  if (threadIdx.x == 0) sm.loss = 0.f;
+  __syncthreads();
   for (int64_t base = (int64_t)blockIdx.x * kGradSamples; base < n; base += (int64_t)gridDim.x * kGradSamples) {
-    if (threadIdx.x < 32) {
-      sm.db1[threadIdx.x] = 0.f;
-      sm.db2[threadIdx.x] = 0.f;
-      sm.dw3[threadIdx.x] = 0.f;
-    }
-    if (threadIdx.x == 0) {
-      sm.db3 = 0.f;
-      sm.loss = 0.f;
-    }
-    __syncthreads();
     // ---- per warp: 16 samples forward and backward to dz1 ----
     const int rl0 = warp * 16 + g, rl1 = rl0 + 8;  // rows within the block tile
     const int64_t r0 = base + rl0, r1 = base + rl1;
@@ -132,13 +132,22 @@ __global__ void __launch_bounds__(256) k_mlp_grad(const float *params, const flo
     const float y0 = v0 ? Y[r0] : 0.f, y1 = v1 ? Y[r1] : 0.f;
     const float p0 = 1.f / (1.f + __expf(-l0)), p1 = 1.f / (1.f + __expf(-l1));
     const float d0 = v0 ? (p0 - y0) * scale : 0.f, d1 = v1 ? (p1 - y1) * scale : 0.f;
-    if (t == 0) {
-      // binary cross-entropy from the logit: max(l,0) - l*y + log(1 + exp(-|l|))
+    {
+      // binary cross-entropy from the logit: max(l,0) - l*y + log(1 + exp(-|l|));
+      // lanes with t == 0 hold the rows, summed over the 8 groups
       float ls = 0.f;
-      if (v0) ls += fmaxf(l0, 0.f) - l0 * y0 + log1pf(__expf(-fabsf(l0)));
-      if (v1) ls += fmaxf(l1, 0.f) - l1 * y1 + log1pf(__expf(-fabsf(l1)));
-      atomicAdd(&sm.loss, ls * scale);
-      atomicAdd(&sm.db3, d0 + d1);
+      if (t == 0 && v0) ls += fmaxf(l0, 0.f) - l0 * y0 + log1pf(__expf(-fabsf(l0)));
+      if (t == 0 && v1) ls += fmaxf(l1, 0.f) - l1 * y1 + log1pf(__expf(-fabsf(l1)));
+      float db = t == 0 ? d0 + d1 : 0.f;
+#pragma unroll
+      for (int o = 4; o < 32; o <<= 1) {
+        ls += __shfl_xor_sync(0xFFFFFFFFu, ls, o);
+        db += __shfl_xor_sync(0xFFFFFFFFu, db, o);
+      }
+      if (lane == 0) {
+        sm.wloss[warp] = ls * scale;
+        sm.db3[warp] = db;
+      }
     }
     // dz2 = dlogit * w3 * [z2 > 0]; dw3 = sum dlogit * h2; db2 = sum dz2
     uint32_t adz2[2][4];
@@ -162,10 +171,10 @@ __global__ void __launch_bounds__(256) k_mlp_grad(const float *params, const flo
         s_b2b += __shfl_xor_sync(0xFFFFFFFFu, s_b2b, o);
       }
       if (g == 0) {
-        atomicAdd(&sm.dw3[c], s_w3a);
-        atomicAdd(&sm.dw3[c + 1], s_w3b);
-        atomicAdd(&sm.db2[c], s_b2a);
-        atomicAdd(&sm.db2[c + 1], s_b2b);
+        sm.dw3[warp][c] = s_w3a;
+        sm.dw3[warp][c + 1] = s_w3b;
+        sm.db2[warp][c] = s_b2a;
+        sm.db2[warp][c + 1] = s_b2b;
       }
       sm.dz2[rl0][c] = __float2bfloat16_rn(dz[0]);
       sm.dz2[rl0][c + 1] = __float2bfloat16_rn(dz[1]);
@@ -196,8 +205,8 @@ __global__ void __launch_bounds__(256) k_mlp_grad(const float *params, const flo
         s_b += __shfl_xor_sync(0xFFFFFFFFu, s_b, o);
       }
       if (g == 0) {
-        atomicAdd(&sm.db1[c], s_a);
-        atomicAdd(&sm.db1[c + 1], s_b);
+        sm.db1[warp][c] = s_a;
+        sm.db1[warp][c + 1] = s_b;
       }
       sm.dz1[rl0][c] = __float2bfloat16_rn(dz[0]);
       sm.dz1[rl0][c + 1] = __float2bfloat16_rn(dz[1]);
@@ -230,11 +239,11 @@ __global__ void __launch_bounds__(256) k_mlp_grad(const float *params, const flo
                                ld_pair(&sm.dz2[k0 + 8][n0], &sm.dz2[k0 + 9][n0])};
         mma_bf16(acc, a, b);
       }
-      const int row = 16 * mt + g, col = 8 * nt + 2 * t;
-      atomicAdd(&grad[kW2 + row * 32 + col], acc[0]);
-      atomicAdd(&grad[kW2 + row * 32 + col + 1], acc[1]);
-      atomicAdd(&grad[kW2 + (row + 8) * 32 + col], acc[2]);
-      atomicAdd(&grad[kW2 + (row + 8) * 32 + col + 1], acc[3]);
+      const int row = 16 * mt + g, col = 8 * nt + 2 * t;  // every element has one owner lane
+      sm.acc[kW2 + row * 32 + col] += acc[0];
+      sm.acc[kW2 + row * 32 + col + 1] += acc[1];
+      sm.acc[kW2 + (row + 8) * 32 + col] += acc[2];
+      sm.acc[kW2 + (row + 8) * 32 + col + 1] += acc[3];
     }
     if (warp < 4) {
       const int nt = warp;
@@ -251,20 +260,47 @@ __global__ void __launch_bounds__(256) k_mlp_grad(const float *params, const flo
         mma_bf16(acc, a, b);
       }
       const int row = g, col = 8 * nt + 2 * t;  // rows 8..15 are the zero padding
-      atomicAdd(&grad[kW1 + row * 32 + col], acc[0]);
-      atomicAdd(&grad[kW1 + row * 32 + col + 1], acc[1]);
+      sm.acc[kW1 + row * 32 + col] += acc[0];
+      sm.acc[kW1 + row * 32 + col + 1] += acc[1];
     }
+    // bias partials of the tile, warps summed in order
     if (threadIdx.x < 32) {
-      atomicAdd(&grad[kB1 + threadIdx.x], sm.db1[threadIdx.x]);
-      atomicAdd(&grad[kB2 + threadIdx.x], sm.db2[threadIdx.x]);
-      atomicAdd(&grad[kW3 + threadIdx.x], sm.dw3[threadIdx.x]);
+      float b1 = 0.f, b2 = 0.f, w3 = 0.f;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        b1 += sm.db1[w][threadIdx.x];
+        b2 += sm.db2[w][threadIdx.x];
+        w3 += sm.dw3[w][threadIdx.x];
+      }
+      sm.acc[kB1 + threadIdx.x] += b1;
+      sm.acc[kB2 + threadIdx.x] += b2;
+      sm.acc[kW3 + threadIdx.x] += w3;
     }
-    if (threadIdx.x == 0) {
-      atomicAdd(&grad[kB3], sm.db3);
-      if (loss) atomicAdd(loss, sm.loss);
+    if (threadIdx.x == 32) {
+      float b3 = 0.f, ls = 0.f;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        b3 += sm.db3[w];
+        ls += sm.wloss[w];
+      }
+      sm.acc[kB3] += b3;
+      sm.loss += ls;
     }
     __syncthreads();
   }
+  float *out = partial + (int64_t)blockIdx.x * (kMlpParams + 1);
+  for (int p = threadIdx.x; p < kMlpParams; p += blockDim.x) out[p] = sm.acc[p];
+  if (threadIdx.x == 0) out[kMlpParams] = sm.loss;
+}
+
+// grad[p] += sum over blocks b (in order) of partial[b][p]; likewise the loss.
+__global__ void k_mlp_reduce(const float *partial, int blocks, float *grad, float *loss) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p > kMlpParams) return;
+  float sum = 0.f;
+  for (int b = 0; b < blocks; ++b) sum += partial[(int64_t)b * (kMlpParams + 1) + p];
+  if (p < kMlpParams) grad[p] += sum;
+  else if (loss) *loss += sum;
 }
 
 // Adam (Kingma & Ba 2015) on the fp32 parameters; `step` counts from 1.
@@ -303,11 +339,16 @@ void mlp_forward(const float *params, const float *X, int64_t n, float *logit, c
   LV_LAUNCH(k_mlp_forward<<<blocks, 256, 0, s>>>(params, X, n, logit));
 }
 
+int mlp_grad_blocks(int64_t n) { return (int)std::min<int64_t>((n + kGradSamples - 1) / kGradSamples, 152 * 8); }
+
+size_t mlp_grad_scratch_floats(int64_t n) { return (size_t)std::max(mlp_grad_blocks(n), 1) * (kMlpParams + 1); }
+
 void mlp_gradient(const float *params, const float *X, const float *Y, int64_t n, float scale, float *grad,
-                  float *loss, cudaStream_t s) {
+                  float *loss, float *scratch, cudaStream_t s) {
   if (n <= 0) return;
-  const int blocks = (int)std::min<int64_t>((n + kGradSamples - 1) / kGradSamples, 152 * 8);
-  LV_LAUNCH(k_mlp_grad<<<blocks, 256, 0, s>>>(params, X, Y, n, scale, grad, loss));
+  const int blocks = mlp_grad_blocks(n);
+  LV_LAUNCH(k_mlp_grad<<<blocks, 256, 0, s>>>(params, X, Y, n, scale, scratch));
+  LV_LAUNCH(k_mlp_reduce<<<(kMlpParams + 1 + 255) / 256, 256, 0, s>>>(scratch, blocks, grad, loss));
 }
 
 void mlp_adam(float *params, const float *grad, float *m, float *v, float lr, int step, cudaStream_t s) {

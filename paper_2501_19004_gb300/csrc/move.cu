@@ -17,6 +17,9 @@
 // bins) and global tables for hubs only.
 #include <climits>
 
+#include <algorithm>
+#include <cooperative_groups.h>
+
 #include "internal.h"
 #include "learn.cuh"
 #include "tables.cuh"
@@ -579,6 +582,156 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : NT == 512 ? 2 : 1) k_move_
   flush_work(work, a.ctr->mv_work[BIN]);
 }
 
+// -------------------------------------------------------------- cluster bin
+// 8192 < degree <= 32768: a cluster of kClusterSize 1024-thread blocks per
+// vertex.  The blocks' shared tables form one table of kClusterSize * 16384
+// slots: slot h lives in block h / 16384 of the cluster and is reached
+// through distributed shared memory (remote CAS and add), so no global
+// table is touched.  Every block lists the slots claimed in its own part,
+// scans them for its partial argmax, and block 0 of the cluster reduces the
+// partials and decides.  All blocks of a cluster take the same vertices, so
+// they meet the same cluster barriers.
+__device__ __forceinline__ void cluster_insert(int32_t *keys, uint32_t *vals, uint16_t *occ, unsigned *nocc,
+                                               int32_t key, uint32_t w, Counters *ctr) {
+  namespace cg = cooperative_groups;
+  constexpr uint32_t kMask = (uint32_t)kClusterSize * kXlCap - 1;
+  uint32_t h = slot_of(key, kMask);
+  for (uint32_t t = 0; t <= kMask; ++t) {
+    const int r = (int)(h / kXlCap);
+    const uint32_t s = h % kXlCap;
+    int32_t *k = cg::this_cluster().map_shared_rank(keys, r) + s;
+    int32_t cur = *(volatile int32_t *)k;
+    bool claimed = false;
+    if (cur == kEmpty) {
+      cur = atomicCAS(k, kEmpty, key);
+      if (cur == kEmpty) {
+        cur = key;
+        claimed = true;
+      }
+    }
+    if (cur == key) {
+      atomicAdd(cg::this_cluster().map_shared_rank(vals, r) + s, w);
+      if (claimed) {
+        const unsigned pos = atomicAdd(cg::this_cluster().map_shared_rank(nocc, r), 1u);
+        cg::this_cluster().map_shared_rank(occ, r)[pos] = (uint16_t)s;
+      }
+      return;
+    }
+    h = (h + 1) & kMask;
+  }
+  atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
+}
+
+template <int WK>
+__global__ void __cluster_dims__(kClusterSize, 1, 1) __launch_bounds__(1024, 1) k_move_cluster(MoveArgs a) {
+  namespace cg = cooperative_groups;
+  constexpr int NT = 1024;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  // dynamic shared memory: keys[16384], vals[16384], occupied list[16384]
+  extern __shared__ uint32_t dyn[];
+  int32_t *keys = (int32_t *)dyn;
+  uint32_t *vals = dyn + kXlCap;
+  uint16_t *occ = (uint16_t *)(dyn + 2 * kXlCap);
+  __shared__ unsigned s_nocc;
+  __shared__ long long s_part_s[kClusterSize], s_part_kid[kClusterSize];
+  __shared__ int32_t s_part_c[kClusterSize];
+  __shared__ int32_t s_target;
+  for (int s = threadIdx.x; s < kXlCap; s += NT) {
+    keys[s] = kEmpty;
+    vals[s] = 0;
+  }
+  if (threadIdx.x == 0) s_nocc = 0;
+  cl.sync();
+  const unsigned long long cnt = a.ctr->bin_count[kClusterBin];
+  const unsigned long long nclusters = gridDim.x / kClusterSize;
+  unsigned long long glo = 0, ghi = 0, gm = 0;
+  unsigned long long work[5] = {0, 0, 0, 0, 0};
+  for (unsigned long long idx = blockIdx.x / kClusterSize; idx < cnt; idx += nclusters) {
+    const int32_t i = a.bins[kClusterBin][idx];
+    const int64_t b = a.g.begin[i], e = a.g.end[i];
+    const int64_t deg = e - b;
+    // this block's share of the row: positions rank * NT + tid + u * (cluster threads)
+    for (int64_t x0 = (int64_t)rank * NT; x0 < deg; x0 += (int64_t)kClusterSize * NT * kRun) {
+      int32_t kk[kRun];
+      uint32_t ww[kRun];
+      gather_run<WK>(a, i, b, x0 + threadIdx.x, (int64_t)kClusterSize * NT, deg, kk, ww);
+#pragma unroll
+      for (int u = 0; u < kRun; ++u)
+        if (kk[u] != kEmpty) cluster_insert(keys, vals, occ, &s_nocc, kk[u], ww[u], a.ctr);
+    }
+    cl.sync();  // the distributed table is complete
+    const int32_t d = a.Cp[i];
+    const long long Ki = a.K[i];
+    const long long tm = vertex_two_m(a.batch, a.two_m, i);
+    long long best_s = LLONG_MIN, Kid = 0;
+    int32_t best_c = INT_MAX;
+    const unsigned nk = s_nocc;
+    for (unsigned t = threadIdx.x; t < nk; t += NT) {
+      const uint32_t s = occ[t];
+      const int32_t c = keys[s];
+      const long long v = vals[s];
+      keys[s] = kEmpty;
+      vals[s] = 0;
+      if (c == d) {
+        Kid = v;
+        continue;
+      }
+      ++work[2];
+      const long long sc = tm * v - Ki * a.Sigma[c];
+      if (better(sc, c, best_s, best_c)) {
+        best_s = sc;
+        best_c = c;
+      }
+    }
+    block_argmax_sum<NT>(best_s, best_c, Kid);
+    if (threadIdx.x == 0) {
+      s_nocc = 0;  // read by every thread before block_argmax_sum's barriers
+      cl.map_shared_rank(s_part_s, 0)[rank] = best_s;
+      cl.map_shared_rank(s_part_c, 0)[rank] = best_c;
+      cl.map_shared_rank(s_part_kid, 0)[rank] = Kid;
+    }
+    cl.sync();  // partials in block 0
+    if (rank == 0 && threadIdx.x == 0) {
+      long long bs = LLONG_MIN, kid = 0;
+      int32_t bc = INT_MAX;
+      for (int r = 0; r < kClusterSize; ++r) {
+        kid += s_part_kid[r];
+        if (better(s_part_s[r], s_part_c[r], bs, bc)) {
+          bs = s_part_s[r];
+          bc = s_part_c[r];
+        }
+      }
+      long long s_d = 0;
+      const int32_t t =
+          finish_decision(tm, a.Sigma, a.iter ? (int)a.iter[1] : a.pickless, d, Ki, kid, bs, bc, glo, ghi, gm, &s_d);
+      learn_record(a.learn, a.ctr, a.g, a.Cp, a.Sigma, a.two_m, i, Ki, kid, bs, bc, s_d, t >= 0);
+      if (t >= 0) batch_gain(a.batch, i, bs, s_d);
+      work[0] += 1;
+      work[1] += (unsigned long long)deg;
+      if (t >= 0) {
+        work[3] += 1;
+        work[4] += (unsigned long long)deg;
+        const unsigned long long pos = atomicAdd(&a.ctr->movers, 1ull);
+        a.mv_vertex[pos] = i;
+        a.mv_target[pos] = t;
+      }
+      for (int r = 0; r < kClusterSize; ++r) cl.map_shared_rank(&s_target, r)[0] = t;
+    }
+    cl.sync();  // decision in every block
+    if (s_target >= 0)
+      for (int64_t k = b + (int64_t)rank * NT + threadIdx.x; k < e; k += (int64_t)kClusterSize * NT) {
+        const int32_t j = __ldg(a.g.col + k);
+        if (j != i) {
+          a.flag[j] = 1;
+          learn_mark(a.learn, j);
+        }
+      }
+  }
+  flush_gains(glo, ghi, gm, a.ctr);
+  flush_work(work, a.ctr->mv_work[kClusterBin]);
+}
+
 // -------------------------------------------------------------------- apply
 __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
   const unsigned long long cnt = a.ctr->movers;
@@ -607,7 +760,7 @@ __global__ void __launch_bounds__(256) k_pass_init(GView g, int first_pass, int6
     const int64_t b = g.begin[i], e = g.end[i];
     const unsigned long long deg = (unsigned long long)(e - b);
     if (deg > md) md = deg;
-    if (deg > (unsigned long long)kXlMaxDeg) {  // hubs of the global tables
+    if (deg > (unsigned long long)kClusterMaxDeg) {  // hubs of the global tables
       big_slots += big_table_cap(deg, (unsigned long long)g.n);
       big_items += 1;
     }
@@ -657,7 +810,9 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
   constexpr size_t kBlockSmem =
       (size_t)kBlockCap * (sizeof(uint32_t) + sizeof(int32_t)) + kBlockCap / 2 * sizeof(uint16_t);
   constexpr size_t kXlSmem = (size_t)kXlCap * (sizeof(uint32_t) + sizeof(int32_t)) + kXlCap / 2 * sizeof(uint16_t);
+  constexpr size_t kClSmem = (size_t)kXlCap * (sizeof(uint32_t) + sizeof(int32_t) + sizeof(uint16_t));
   if (!attr_done) {
+    cudaFuncSetAttribute(k_move_cluster<WK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClSmem);
     cudaFuncSetAttribute(k_move_block<WK, 512, kBlockCap, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kBlockSmem);
     cudaFuncSetAttribute(k_move_block<WK, 1024, kXlCap, kXlBin>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -679,6 +834,10 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
            k_move_block<WK, 512, kBlockCap, 3><<<num_sms * bk[3], 512, kBlockSmem, s>>>(a));
   LV_TIMED(prof, K_MOVE_XL, s,
            k_move_block<WK, 1024, kXlCap, kXlBin><<<num_sms * bk[kXlBin], 1024, kXlSmem, s>>>(a));
+  {
+    const int clusters = std::max(1, num_sms * bk[kClusterBin] / kClusterSize);
+    LV_TIMED(prof, K_MOVE_CLUSTER, s, k_move_cluster<WK><<<clusters * kClusterSize, 1024, kClSmem, s>>>(a));
+  }
   if (hubs) big_move_rounds(big, WK, num_sms, s, prof);
   LV_TIMED(prof, K_APPLY, s, k_apply<<<num_sms * 4, 256, 0, s>>>(a));
 }
@@ -715,6 +874,6 @@ void iota_i32(int32_t *x, int64_t n, int num_sms, cudaStream_t s) {
 const char *const kKernelNames[K_NUM_KERNELS] = {
     "select", "move_thread", "move_warp", "move_mid", "move_block", "move_hub", "apply", "pass_init",
     "comm_count", "comm_scatter", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big",
-    "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit", "mlp_select", "move_group", "move_xl", "merge_xl"};
+    "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit", "mlp_select", "move_group", "move_xl", "merge_xl", "move_cluster"};
 
 }  // namespace lv

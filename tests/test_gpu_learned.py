@@ -78,6 +78,26 @@ def test_training_fits_a_separable_rule():
     assert acc > 0.95, acc
 
 
+def test_gradient_and_training_are_reproducible():
+    """Per-block partial gradients are summed in block order: two gradients,
+    and two training runs with the same seed, agree bit for bit."""
+    rng = np.random.default_rng(9)
+    n = 50000
+    X = torch.from_numpy(_features(rng, n)).cuda()
+    Y = torch.from_numpy((rng.random(n) < 0.3).astype(np.float32)).cuda()
+    p0 = torch.from_numpy(omlp.init_params(3)).cuda()
+    g1, l1 = lv.louvain_mlp_gradient(p0, X, Y)
+    g2, l2 = lv.louvain_mlp_gradient(p0, X, Y)
+    assert torch.equal(g1, g2) and l1 == l2
+    runs = []
+    for _ in range(2):
+        p = p0.clone()
+        losses = lv.louvain_mlp_train(p, X, Y, epochs=3, batch=4096, lr=3e-3, seed=7)
+        runs.append((p.cpu().numpy(), losses))
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert np.array_equal(runs[0][1], runs[1][1])
+
+
 def _traces(g, cap=400000, rate=1.0):
     with lv.Louvain(lv.DeviceCSR.from_host(g), lv.Config(trace_capacity=cap, trace_rate=rate)) as ctx:
         ctx.run()

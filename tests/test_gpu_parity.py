@@ -61,6 +61,7 @@ CASES = {
     "rmat14_weighted": lambda: gg.rmat(14, 8, seed=3, weight_range=(1, 5)),
     "rmat16_hubs": lambda: gg.rmat(16, 16, seed=7),
     "rmat18_hubs": lambda: gg.rmat(18, 16, seed=7),  # 172 vertices above 4096, 19 above 8192
+    "rmat19_hubs": lambda: gg.rmat(19, 16, seed=7),  # one vertex above 32768 (global tables)
     "grid96": lambda: gg.grid(96, 0.02, seed=11),
     "ring8x10": lambda: gg.ring_of_cliques(8, 10),
     "batched_sbm_0": lambda: gg.batched_sbm(0),
@@ -89,7 +90,7 @@ def test_plain_bit_exact_across_settings(cfg):
 def test_hub_rounds_bit_exact(buckets, window):
     """Small table windows put the hub and big-community tables through many
     rounds; results must not change."""
-    g = gg.rmat(16, 16, seed=11)
+    g = gg.rmat(19, 16, seed=7)
     res, ref = run_both(g, lv.Config(buckets=buckets, table_window=window))
     assert_same(res, ref)
 
@@ -117,13 +118,14 @@ def test_edge_cases():
     z = gg.CSR(np.zeros(1, dtype=np.int64), np.zeros(0, dtype=np.int32), None)
     res = lv.run(z)
     assert res.membership.shape == (0,)
-    # self-loops and a star (one hub with many leaves, all in the hub bin)
-    n = 9000
-    u = np.zeros(n - 1, dtype=np.int64)
-    v = np.arange(1, n, dtype=np.int64)
-    star = gg.from_pairs(n, u, v)
-    res, ref = run_both(star)
-    assert_same(res, ref)
+    # stars: one hub with many leaves, in the cluster bin (8999 leaves) and
+    # in the global-table bin (40000 leaves)
+    for n in (9000, 40001):
+        u = np.zeros(n - 1, dtype=np.int64)
+        v = np.arange(1, n, dtype=np.int64)
+        star = gg.from_pairs(n, u, v)
+        res, ref = run_both(star)
+        assert_same(res, ref)
 
 
 def test_modularity_of_matches_oracle():
