@@ -172,7 +172,9 @@ louvain_status louvain_set_profile(louvain_ctx *ctx, uint32_t profile_mask);
  *   [10..15] blocks per SM of the aggregation kernels of the thread, warp,
  *       128-thread, 512-thread, big-community (<= 3) and 1024-thread bins;
  *   [16] graphs: 1 = each local-moving iteration is replayed from a CUDA
- *       graph captured once per pass (plain mode, no profiling).
+ *       graph captured once per pass (plain mode, no profiling);
+ *   [17] concurrent: 1 = a bucket's bin kernels run at the same time on
+ *       side streams of the context (joined before the moves are applied).
  * Results never depend on the schedule: every bin computes the same exact
  * decisions.  The schedule belongs to the context and is used by its next
  * runs. */
@@ -183,7 +185,8 @@ louvain_status louvain_set_schedule(louvain_ctx *ctx, const int32_t *words, int3
 /* Choose the context's schedule by timed runs of its own graph (at most
  * max_runs whole runs): bin thresholds by whole-run time, blocks per SM of
  * every bin by per-kernel CUDA-event time, then graph replay on or off.  The
- * tuned schedule is kept only if it beats the starting one.  json (may be
+ * tuned schedule is kept only if it beats the starting one (the last steps
+ * try concurrent bin kernels and graph replay on and off).  json (may be
  * NULL) receives {"runs", "start_ms", "tuned_ms", "schedule", "trials"}.  The
  * context holds a valid result of the chosen schedule afterwards. */
 louvain_status louvain_autotune(louvain_ctx *ctx, int32_t max_runs, char *json, size_t cap);

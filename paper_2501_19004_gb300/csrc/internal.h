@@ -61,15 +61,26 @@ __host__ __device__ __forceinline__ int merge_bin(int64_t d) {
 //              degrees up to 1024 go to the 128-thread block bin;
 //   move[b], merge[b]  blocks per SM of bin b's kernel (grid = SMs x blocks;
 //              every kernel strides over its list, so any grid is correct);
-//   graphs     1 = each iteration's launches are replayed from a CUDA graph.
+//   graphs     1 = each iteration's launches are replayed from a CUDA graph;
+//   concurrent 1 = a bucket's bin kernels run on side streams at the same
+//              time (fork and join through events).
 struct Sched {
   int group_max = kGroupMaxDeg;
   int warp_max = kWarpMaxDeg;
   int move[kMoveBins] = {2, 8, 12, 2, 3, 4, 1, 1};  // thread, warp, mid, block, hub, group, xl, cluster
   int merge[kMergeBins] = {8, 8, 8, 2, 3, 1};   // thread, warp, mid, block, big, xl
   int graphs = 0;
+  int concurrent = 0;
 };
-constexpr int kSchedWords = 2 + kMoveBins + kMergeBins + 1;
+constexpr int kSchedWords = 2 + kMoveBins + kMergeBins + 2;
+
+// Side streams for concurrent bin kernels (created with the context).
+constexpr int kSideStreams = 3;
+struct SideStreams {
+  cudaStream_t s[kSideStreams] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[kSideStreams] = {};
+};
 
 __host__ __device__ __forceinline__ int move_bin(int64_t d, int group_max, int warp_max) {
   if (d <= kThreadMaxDeg) return 0;
@@ -269,7 +280,8 @@ struct KernelProf {
 };
 
 // local-moving phase, one bucket step (select, decide per bin, apply)
-void move_bucket(const MoveArgs &a, const BigArgs &big, int wkind, int num_sms, cudaStream_t s, KernelProf *prof);
+void move_bucket(const MoveArgs &a, const BigArgs &big, int wkind, int num_sms, cudaStream_t s, KernelProf *prof,
+                 const SideStreams *side = nullptr);
 
 // pass initialisation: K (row sums on pass 0, else given), Sigma = K, C' = id,
 // flags = 1, max degree into ctr->maxdeg

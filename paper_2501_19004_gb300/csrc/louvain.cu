@@ -105,6 +105,7 @@ struct louvain_ctx {
   long long *h_rounds = nullptr;     // pinned: rounds the current big items need
   cudaEvent_t plan_done = nullptr;
   Sched sched;                       // launch schedule (louvain_set_schedule / louvain_autotune)
+  SideStreams side;                  // side streams for concurrent bin kernels
   // graph replay of local-moving iterations (sched.graphs)
   cudaGraphExec_t gexec = nullptr;
   long long graph_launches = 0;      // kernels per replay
@@ -503,7 +504,8 @@ louvain_status enqueue_iteration(louvain_ctx *x, const GView &g, int wk, int pas
       LV_CK(cudaMemsetAsync(x->d_ctr, 0, 10 * sizeof(unsigned long long), x->stream));
       if (L.enabled) LV_CK(cudaMemsetAsync(&x->d_ctr->cand_count, 0, sizeof(unsigned long long), x->stream));
       a.bucket = (uint32_t)b;
-      move_bucket(a, big, wk, x->num_sms, x->stream, x->prof.mask ? &x->prof : nullptr);
+      move_bucket(a, big, wk, x->num_sms, x->stream, x->prof.mask ? &x->prof : nullptr,
+                  x->side.fork ? &x->side : nullptr);
     }
   }
   return LOUVAIN_OK;
@@ -1273,6 +1275,16 @@ louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg
     set_err(x, "event creation failed");
     return fail(LOUVAIN_E_CUDA);
   }
+  for (int k = 0; k < kSideStreams; ++k)
+    if (cudaStreamCreateWithFlags(&x->side.s[k], cudaStreamNonBlocking) ||
+        cudaEventCreateWithFlags(&x->side.join[k], cudaEventDisableTiming)) {
+      set_err(x, "side stream creation failed");
+      return fail(LOUVAIN_E_CUDA);
+    }
+  if (cudaEventCreateWithFlags(&x->side.fork, cudaEventDisableTiming)) {
+    set_err(x, "event creation failed");
+    return fail(LOUVAIN_E_CUDA);
+  }
   if (cudaStreamSynchronize(x->stream) != cudaSuccess) {
     set_err(x, "stream error after allocation");
     return fail(LOUVAIN_E_CUDA);
@@ -1539,6 +1551,7 @@ static void sched_to_words(const Sched &s, int32_t *w) {
   for (int b = 0; b < kMoveBins; ++b) w[k++] = s.move[b];
   for (int b = 0; b < kMergeBins; ++b) w[k++] = s.merge[b];
   w[k++] = s.graphs;
+  w[k++] = s.concurrent;
 }
 
 static bool sched_from_words(const int32_t *w, Sched *s) {
@@ -1549,6 +1562,7 @@ static bool sched_from_words(const int32_t *w, Sched *s) {
   for (int b = 0; b < kMoveBins; ++b) t.move[b] = w[k++];
   for (int b = 0; b < kMergeBins; ++b) t.merge[b] = w[k++];
   t.graphs = w[k++];
+  t.concurrent = w[k++];
   if (t.group_max < kThreadMaxDeg || t.group_max > kGroupMaxDeg) return false;
   if (t.warp_max < t.group_max || t.warp_max > kWarpMaxDeg) return false;
   for (int b = 0; b < kMoveBins; ++b)
@@ -1557,6 +1571,7 @@ static bool sched_from_words(const int32_t *w, Sched *s) {
     if (t.merge[b] < 1 || t.merge[b] > 64) return false;
   if (t.move[kBigBin] > 3 || t.merge[kBigBin] > 3) return false;  // accumulation: 3 blocks per SM at most
   if (t.graphs != 0 && t.graphs != 1) return false;
+  if (t.concurrent != 0 && t.concurrent != 1) return false;
   *s = t;
   return true;
 }
@@ -1690,7 +1705,17 @@ louvain_status louvain_autotune(louvain_ctx *x, int32_t max_runs, char *json, si
         }
       }
     }
-    // 3. graph replay
+    // 3. concurrent bins, then graph replay
+    if (runs < max_runs) {
+      Sched t = best;
+      t.concurrent = best.concurrent ? 0 : 1;
+      if ((st = run_once(t, false, &ms))) goto fail;
+      note("concurrent", t, ms);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
+    }
     if (runs < max_runs) {
       Sched t = best;
       t.graphs = best.graphs ? 0 : 1;
@@ -1739,6 +1764,11 @@ void louvain_destroy(louvain_ctx *x) {
   if (x->run1) cudaEventDestroy(x->run1);
   if (x->h_ctr) cudaFreeHost(x->h_ctr);
   if (x->h_rounds) cudaFreeHost(x->h_rounds);
+  for (int k = 0; k < kSideStreams; ++k) {
+    if (x->side.s[k]) cudaStreamDestroy(x->side.s[k]);
+    if (x->side.join[k]) cudaEventDestroy(x->side.join[k]);
+  }
+  if (x->side.fork) cudaEventDestroy(x->side.fork);
   if (x->h_iter) cudaFreeHost(x->h_iter);
   if (x->gexec) cudaGraphExecDestroy(x->gexec);
   if (x->plan_done) cudaEventDestroy(x->plan_done);

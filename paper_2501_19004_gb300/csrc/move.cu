@@ -804,7 +804,8 @@ __global__ void k_iota(int32_t *x, int64_t n) {
 }
 
 template <int WK>
-void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStream_t s, KernelProf *prof) {
+void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStream_t s, KernelProf *prof,
+                   const SideStreams *side) {
   static bool attr_done = false;
   constexpr size_t kMidSmem = (size_t)kMidCap * (sizeof(uint32_t) + sizeof(int32_t)) + kMidCap / 2 * sizeof(uint16_t);
   constexpr size_t kBlockSmem =
@@ -824,14 +825,26 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
   const bool hubs = big.ws.slots > 0;
   if (hubs) big_move_plan(big, s, prof);  // the round count reaches the host while the bins below run
   const int *bk = a.sched.move;
-  LV_TIMED(prof, K_MOVE_THREAD, s, k_move_thread<WK><<<num_sms * bk[0], 256, 0, s>>>(a));
+  // the bins' decide kernels are independent (they read the snapshot and
+  // append to the mover list with atomics): with `concurrent` they run on
+  // side streams at the same time and join before the apply kernel
+  const bool conc = side && a.sched.concurrent;
+  cudaStream_t s1 = s, s2 = s, s3 = s;
+  if (conc) {
+    cudaEventRecord(side->fork, s);
+    for (int k = 0; k < kSideStreams; ++k) cudaStreamWaitEvent(side->s[k], side->fork, 0);
+    s1 = side->s[0];
+    s2 = side->s[1];
+    s3 = side->s[2];
+  }
+  LV_TIMED(prof, K_MOVE_THREAD, s1, k_move_thread<WK><<<num_sms * bk[0], 256, 0, s1>>>(a));
   if (a.sched.group_max > kThreadMaxDeg)
-    LV_TIMED(prof, K_MOVE_GROUP, s,
-             k_move_group<WK, kGroupLanes, 8><<<num_sms * bk[kGroupBin], 256, 0, s>>>(a));
-  LV_TIMED(prof, K_MOVE_WARP, s, k_move_warp<WK, 8><<<num_sms * bk[1], 256, 0, s>>>(a));
-  LV_TIMED(prof, K_MOVE_MID, s, k_move_block<WK, 128, kMidCap, 2><<<num_sms * bk[2], 128, kMidSmem, s>>>(a));
-  LV_TIMED(prof, K_MOVE_BLOCK, s,
-           k_move_block<WK, 512, kBlockCap, 3><<<num_sms * bk[3], 512, kBlockSmem, s>>>(a));
+    LV_TIMED(prof, K_MOVE_GROUP, s2,
+             k_move_group<WK, kGroupLanes, 8><<<num_sms * bk[kGroupBin], 256, 0, s2>>>(a));
+  LV_TIMED(prof, K_MOVE_WARP, s2, k_move_warp<WK, 8><<<num_sms * bk[1], 256, 0, s2>>>(a));
+  LV_TIMED(prof, K_MOVE_MID, s3, k_move_block<WK, 128, kMidCap, 2><<<num_sms * bk[2], 128, kMidSmem, s3>>>(a));
+  LV_TIMED(prof, K_MOVE_BLOCK, s3,
+           k_move_block<WK, 512, kBlockCap, 3><<<num_sms * bk[3], 512, kBlockSmem, s3>>>(a));
   LV_TIMED(prof, K_MOVE_XL, s,
            k_move_block<WK, 1024, kXlCap, kXlBin><<<num_sms * bk[kXlBin], 1024, kXlSmem, s>>>(a));
   {
@@ -839,6 +852,11 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
     LV_TIMED(prof, K_MOVE_CLUSTER, s, k_move_cluster<WK><<<clusters * kClusterSize, 1024, kClSmem, s>>>(a));
   }
   if (hubs) big_move_rounds(big, WK, num_sms, s, prof);
+  if (conc)
+    for (int k = 0; k < kSideStreams; ++k) {
+      cudaEventRecord(side->join[k], side->s[k]);
+      cudaStreamWaitEvent(s, side->join[k], 0);
+    }
   LV_TIMED(prof, K_APPLY, s, k_apply<<<num_sms * 4, 256, 0, s>>>(a));
 }
 
@@ -853,10 +871,11 @@ void pass_init_t(const GView &g, int first, int64_t *K, int64_t *Sigma, int32_t 
 
 }  // namespace
 
-void move_bucket(const MoveArgs &a, const BigArgs &big, int wkind, int num_sms, cudaStream_t s, KernelProf *prof) {
+void move_bucket(const MoveArgs &a, const BigArgs &big, int wkind, int num_sms, cudaStream_t s, KernelProf *prof,
+                 const SideStreams *side) {
   if (a.g.n <= 0) return;
-  if (wkind == W_UNIT) move_bucket_t<W_UNIT>(a, big, num_sms, s, prof);
-  else move_bucket_t<W_U32>(a, big, num_sms, s, prof);
+  if (wkind == W_UNIT) move_bucket_t<W_UNIT>(a, big, num_sms, s, prof, side);
+  else move_bucket_t<W_U32>(a, big, num_sms, s, prof, side);
 }
 
 void pass_init(const GView &g, int wkind, int first_pass, int64_t *K, int64_t *Sigma, int32_t *Cp, uint8_t *flag,

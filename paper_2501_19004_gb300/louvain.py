@@ -313,13 +313,20 @@ def louvain_modularity_of(graph, membership, stream=None):
     return q.value, _i128(num), _i128(den)
 
 
-def louvain_traces(ctx, cap: int):
-    """(features [count][8], labels [count]) recorded by the last run (numpy)."""
+def louvain_traces(ctx, cap: int, canonical: bool = True):
+    """(features [count][8], labels [count]) recorded by the last run (numpy).
+    The device appends samples in whatever order its threads finish; with
+    `canonical` they are sorted (by label, then the features) so that the
+    same run always yields the same training set in the same order."""
     feats = np.zeros((max(cap, 1), 8), dtype=np.float32)
     labels = np.zeros(max(cap, 1), dtype=np.float32)
     cnt = ctypes.c_int64()
     _check(load().louvain_traces(ctx, feats.ctypes.data, labels.ctypes.data, cap, ctypes.byref(cnt), 0), ctx)
-    return feats[:cnt.value], labels[:cnt.value]
+    X, Y = feats[:cnt.value], labels[:cnt.value]
+    if canonical and X.shape[0]:
+        order = np.lexsort(tuple(X[:, k] for k in range(7, -1, -1)) + (Y,))
+        X, Y = np.ascontiguousarray(X[order]), np.ascontiguousarray(Y[order])
+    return X, Y
 
 
 def _dev(t):
@@ -393,7 +400,7 @@ def louvain_batch_results(ctx, num_graphs: int, max_passes: int):
 
 SCHEDULE_FIELDS = ["group_max", "warp_max", "move_thread", "move_warp", "move_mid", "move_block", "move_hub",
                    "move_group", "move_xl", "move_cluster", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big",
-                   "merge_xl", "graphs"]
+                   "merge_xl", "graphs", "concurrent"]
 
 
 def louvain_get_schedule(ctx) -> dict:

@@ -37,6 +37,8 @@ SCHEDULES = [
     dict(move_thread=16, move_warp=16, move_mid=16, move_block=16, move_group=16, merge_warp=16),
     dict(graphs=1),
     dict(graphs=1, group_max=16, warp_max=64, move_hub=2),
+    dict(concurrent=1),
+    dict(concurrent=1, graphs=1),
 ]
 
 
@@ -61,7 +63,7 @@ def test_graph_replay_batch():
     graphs = [gg.batched_sbm(k) for k in (0, 1, 3, 8, 10)] + [gg.rmat(12, 16, seed=7)]
     union, vo = gg.concat(graphs)
     with lv.LouvainBatch(lv.DeviceCSR.from_host(union), vo) as b:
-        b.set_schedule(dict(graphs=1))
+        b.set_schedule(dict(graphs=1, concurrent=1))
         res = b.run().result()
     for k, g in enumerate(graphs):
         memb, q, num, den, passes, comms, why = res.graph(k)
@@ -102,7 +104,8 @@ def test_bad_schedules_refused():
     g = gg.rmat(10, 8, seed=1)
     with lv.Louvain(g) as ctx:
         for bad in (dict(group_max=8), dict(group_max=65), dict(group_max=64, warp_max=32), dict(warp_max=300),
-                    dict(move_warp=0), dict(move_hub=4), dict(merge_big=5), dict(graphs=2), dict(move_thread=65)):
+                    dict(move_warp=0), dict(move_hub=4), dict(merge_big=5), dict(graphs=2), dict(move_thread=65),
+                    dict(concurrent=3)):
             before = ctx.schedule()
             with pytest.raises(lv.LouvainError) as ei:
                 ctx.set_schedule(bad)
