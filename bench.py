@@ -259,10 +259,16 @@ def main():
         sched = ctx.schedule()
         tune = {"seconds": round(time.perf_counter() - t0, 2), "runs": rep["runs"], "start_ms": rep["start_ms"],
                 "tuned_ms": rep["tuned_ms"], "schedule": sched}
-    # warm-up 1: every kernel group timed, to find the dominant kernel
+    # warm-up 1: every kernel group timed, to find the dominant kernel; the
+    # bins run one after another here (with concurrent bins, a kernel's event
+    # time would include the others running beside it)
+    run_sched = ctx.schedule()
+    serial_sched = dict(run_sched, concurrent=0)
+    ctx.set_schedule(serial_sched)
     ctx.run()
     prof = ctx.stats()["kernels"]
     dom = max((k for k in prof if prof[k]["launches"] > 0 and k in SINGLE_KERNELS), key=lambda k: prof[k]["ms"])
+    ctx.set_schedule(run_sched)
     ctx.set_profile(lv.kernel_mask(dom))
     for _ in range(args.warmup - 1):
         ctx.run()
@@ -296,6 +302,16 @@ def main():
     res = ctx.result()
     st = ctx.stats()
     value = g.nnz * args.steps * world / (ms / 1e3) / 1e6
+    # the dominant kernel once more with the bins serialised (untimed run)
+    serial = None
+    if run_sched.get("concurrent"):
+        ctx.set_schedule(serial_sched)
+        ctx.run()
+        k = ctx.stats()["kernels"][dom]
+        ctx.set_schedule(run_sched)
+        if k["ms"] > 0:
+            serial = {"achieved": k["bytes"] / (k["ms"] / 1e3) / 1e9, "avg_launch_ms": k["ms"] / max(k["launches"], 1),
+                      "launches": k["launches"]}
 
     # learned-skip leg: the same workload and step count with the predictor
     learned = None
@@ -387,7 +403,11 @@ def main():
                 "frac": (achieved / peaks["hbm_gbs"]) if achieved else None, "peak_source": f"{src} hbm_gbs",
                 "traffic": traffic,
                 "algorithmic_bytes_per_launch": dom_bytes / max(dom_launches, 1),
-                "avg_launch_ms": dom_ms / max(dom_launches, 1), "launches": dom_launches}
+                "avg_launch_ms": dom_ms / max(dom_launches, 1), "launches": dom_launches,
+                "concurrent_bins": bool(run_sched.get("concurrent"))}
+    if serial:
+        serial["frac"] = serial["achieved"] / peaks["hbm_gbs"]
+        roofline["serial"] = serial
 
     # batch only: the same graphs one context at a time (a strided sample),
     # the way a single-graph library would run them

@@ -497,7 +497,7 @@ __global__ void k_relabel(int32_t *x, int64_t n, const int64_t *newid) {
 }
 
 template <int WK>
-void merge_t(const AggArgs &a, int num_sms, cudaStream_t s, KernelProf *prof) {
+void merge_t(const AggArgs &a, int num_sms, cudaStream_t s, KernelProf *prof, const SideStreams *side) {
   static bool attr_done = false;
   constexpr size_t kMidSmem = (size_t)kMidCap * (sizeof(uint32_t) + sizeof(int32_t)) + kMidCap / 2 * sizeof(uint16_t);
   constexpr size_t kSmem = (size_t)kBlockCap * (sizeof(uint32_t) + sizeof(int32_t)) + kBlockCap / 2 * sizeof(uint16_t);
@@ -510,13 +510,29 @@ void merge_t(const AggArgs &a, int num_sms, cudaStream_t s, KernelProf *prof) {
     attr_done = true;
   }
   const int *bk = a.sched.merge;
-  LV_TIMED(prof, K_MERGE_THREAD, s, k_merge_thread<WK, 128><<<num_sms * bk[0], 128, 0, s>>>(a));
-  LV_TIMED(prof, K_MERGE_WARP, s, k_merge_warp<WK, 8><<<num_sms * bk[1], 256, 0, s>>>(a));
-  LV_TIMED(prof, K_MERGE_MID, s, k_merge_block<WK, 128, kMidCap, 2><<<num_sms * bk[2], 128, kMidSmem, s>>>(a));
-  LV_TIMED(prof, K_MERGE_BLOCK, s, k_merge_block<WK, 512, kBlockCap, 3><<<num_sms * bk[3], 512, kSmem, s>>>(a));
+  // the bins write disjoint super-vertex rows: with `concurrent` they run on
+  // side streams at the same time and join before returning
+  const bool conc = side && a.sched.concurrent;
+  cudaStream_t s1 = s, s2 = s, s3 = s;
+  if (conc) {
+    cudaEventRecord(side->fork, s);
+    for (int k = 0; k < kSideStreams; ++k) cudaStreamWaitEvent(side->s[k], side->fork, 0);
+    s1 = side->s[0];
+    s2 = side->s[1];
+    s3 = side->s[2];
+  }
+  LV_TIMED(prof, K_MERGE_THREAD, s1, k_merge_thread<WK, 128><<<num_sms * bk[0], 128, 0, s1>>>(a));
+  LV_TIMED(prof, K_MERGE_WARP, s2, k_merge_warp<WK, 8><<<num_sms * bk[1], 256, 0, s2>>>(a));
+  LV_TIMED(prof, K_MERGE_MID, s3, k_merge_block<WK, 128, kMidCap, 2><<<num_sms * bk[2], 128, kMidSmem, s3>>>(a));
+  LV_TIMED(prof, K_MERGE_BLOCK, s3, k_merge_block<WK, 512, kBlockCap, 3><<<num_sms * bk[3], 512, kSmem, s3>>>(a));
   LV_TIMED(prof, K_MERGE_XL, s,
            k_merge_block<WK, 1024, kXlCap, kMergeXlBin><<<num_sms * bk[kMergeXlBin], 1024, kXlSmem, s>>>(a));
   if (a.big.ws.slots > 0) big_merge(a.big, WK, num_sms, s, prof);
+  if (conc)
+    for (int k = 0; k < kSideStreams; ++k) {
+      cudaEventRecord(side->join[k], side->s[k]);
+      cudaStreamWaitEvent(s, side->join[k], 0);
+    }
 }
 
 template <int WK>
@@ -567,12 +583,13 @@ void agg_scatter_compact(const AggArgs &a, int num_sms, cudaStream_t s) {
   scan_u64(a.cdeg, a.mprefix, n, 0, a.scan_tmp, &a.ctr->scan_total[3], s);
 }
 
-void agg_merge(const AggArgs &a, int64_t gamma, int num_sms, cudaStream_t s, KernelProf *prof) {
+void agg_merge(const AggArgs &a, int64_t gamma, int num_sms, cudaStream_t s, KernelProf *prof,
+               const SideStreams *side) {
   if (gamma <= 0) return;
   (void)gamma;
   // a.wkind describes the input G'
-  if (a.wkind == W_UNIT) merge_t<W_UNIT>(a, num_sms, s, prof);
-  else merge_t<W_U32>(a, num_sms, s, prof);
+  if (a.wkind == W_UNIT) merge_t<W_UNIT>(a, num_sms, s, prof, side);
+  else merge_t<W_U32>(a, num_sms, s, prof, side);
 }
 
 void dendrogram_lookup(int32_t *C, const int32_t *Cp, int64_t n, int num_sms, cudaStream_t s) {

@@ -325,7 +325,8 @@ void agg_count_scan(const AggArgs &a, int num_sms, cudaStream_t s);
 // member scatter + relabel C' to dense ids + per-community arrays + bins
 void agg_scatter_compact(const AggArgs &a, int num_sms, cudaStream_t s);
 // super-vertex rows (hash-merge of member rows); entries into ctr->nnz_out
-void agg_merge(const AggArgs &a, int64_t gamma, int num_sms, cudaStream_t s, KernelProf *prof);
+void agg_merge(const AggArgs &a, int64_t gamma, int num_sms, cudaStream_t s, KernelProf *prof,
+               const SideStreams *side = nullptr);
 
 // C[v] = Cp[C[v]]
 void dendrogram_lookup(int32_t *C, const int32_t *Cp, int64_t n, int num_sms, cudaStream_t s);

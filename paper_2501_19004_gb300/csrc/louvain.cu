@@ -711,7 +711,7 @@ louvain_status aggregate(louvain_ctx *x, AggArgs &aa, int64_t gamma, PassTiming 
   aa.big.ow = aa.ow;
   LV_CK(cudaMemsetAsync(&x->d_ctr->nnz_out, 0, sizeof(unsigned long long), s));
   LV_CK(cudaMemsetAsync(&x->d_ctr->mg_work[0][0], 0, sizeof(x->d_ctr->mg_work), s));
-  agg_merge(aa, gamma, x->num_sms, s, x->prof.mask ? &x->prof : nullptr);
+  agg_merge(aa, gamma, x->num_sms, s, x->prof.mask ? &x->prof : nullptr, x->side.fork ? &x->side : nullptr);
   LV_CK(cudaGetLastError());
   if ((st = read_counters(x))) return st;
   account_merge(x, *x->h_ctr);
