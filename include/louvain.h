@@ -183,7 +183,8 @@ louvain_status louvain_get_schedule(const louvain_ctx *ctx, int32_t *words, int3
 louvain_status louvain_set_schedule(louvain_ctx *ctx, const int32_t *words, int32_t n);
 
 /* Choose the context's schedule by timed runs of its own graph (at most
- * max_runs whole runs): bin thresholds by whole-run time, blocks per SM of
+ * max_runs trials; a whole-run trial is the faster of two runs): bin
+ * thresholds by whole-run time, blocks per SM of
  * every bin by per-kernel CUDA-event time, then graph replay on or off.  The
  * tuned schedule is kept only if it beats the starting one (the last steps
  * try concurrent bin kernels and graph replay on and off).  json (may be

@@ -152,7 +152,8 @@ struct LearnArgs {
   int record = 0;               // per-vertex features are maintained
   const float *params = nullptr;  // device MLP parameters
   float4 *feat = nullptr;       // [n] intra fraction, margin, moved, valid
-  uint32_t *marks = nullptr;    // [n] neighbour moves since the last evaluation
+  uint32_t *marks = nullptr;    // [n] neighbour moves since the last evaluation (as of the bucket's snapshot)
+  uint32_t *marks_next = nullptr;  // [n] moves of the current bucket, folded into marks by the next selection
   int32_t *cand = nullptr;      // [n] candidates of the bucket
   float thr_logit = 0.f;        // evaluate iff logit >= thr_logit
   int skip_clears = 0;          // a skip clears the flag (counts as "stay")

@@ -62,8 +62,11 @@ __device__ __forceinline__ void learn_record(const LearnArgs &L, Counters *ctr, 
   L.marks[i] = 0;
 }
 
+// Moves of the current bucket count for the neighbours' next evaluation: they
+// go to marks_next, which the next selection folds into marks, so a
+// decision never sees marks that change while its bucket runs.
 __device__ __forceinline__ void learn_mark(const LearnArgs &L, int32_t j) {
-  if (L.record) atomicAdd(L.marks + j, 1u);
+  if (L.record) atomicAdd(L.marks_next + j, 1u);
 }
 
 }  // namespace lv

@@ -45,6 +45,13 @@ __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
     int bin = -1;
     bool sel = false;
     bool cand = false;
+    if (a.learn.record && i < n) {  // the previous bucket's neighbour moves
+      const uint32_t mn = a.learn.marks_next[i];
+      if (mn) {
+        a.learn.marks[i] += mn;
+        a.learn.marks_next[i] = 0;
+      }
+    }
     bool live = i < n && a.flag[i];
     uint32_t local = (uint32_t)i;
     if (live && a.batch.gid) {  // batched: only graphs still moving, hashed by their local ids
@@ -585,39 +592,37 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : NT == 512 ? 2 : 1) k_move_
 // -------------------------------------------------------------- cluster bin
 // 8192 < degree <= 32768: a cluster of kClusterSize 1024-thread blocks per
 // vertex.  The blocks' shared tables form one table of kClusterSize * 16384
-// slots: slot h lives in block h / 16384 of the cluster and is reached
-// through distributed shared memory (remote CAS and add), so no global
-// table is touched.  Every block lists the slots claimed in its own part,
-// scans them for its partial argmax, and block 0 of the cluster reduces the
-// partials and decides.  All blocks of a cluster take the same vertices, so
+// slots: key k's home slot h lies in block h / 16384, which owns the key and
+// probes only within its own 16384 slots.  The row is taken in rounds of
+// 8192 entries: every block gathers its share and sends each (key, weight)
+// to the owner's staging buffer through distributed shared memory (one
+// posted store per entry after one reservation per warp and owner); after a
+// cluster barrier every block adds its staged entries into its own part with
+// local shared-memory atomics.  Then every block scans the slots it claimed
+// for its partial argmax, and block 0 of the cluster reduces the partials and
+// decides.  All blocks of a cluster take the same vertices and rounds, so
 // they meet the same cluster barriers.
-__device__ __forceinline__ void cluster_insert(int32_t *keys, uint32_t *vals, uint16_t *occ, unsigned *nocc,
-                                               int32_t key, uint32_t w, Counters *ctr) {
-  namespace cg = cooperative_groups;
-  constexpr uint32_t kMask = (uint32_t)kClusterSize * kXlCap - 1;
-  uint32_t h = slot_of(key, kMask);
-  for (uint32_t t = 0; t <= kMask; ++t) {
-    const int r = (int)(h / kXlCap);
-    const uint32_t s = h % kXlCap;
-    int32_t *k = cg::this_cluster().map_shared_rank(keys, r) + s;
-    int32_t cur = *(volatile int32_t *)k;
+constexpr int kClusterRound = kClusterSize * 1024 * 2;  // entries per round (2 per thread)
+
+__device__ __forceinline__ void owner_insert(int32_t *keys, uint32_t *vals, uint16_t *occ, unsigned *nocc,
+                                             uint32_t h, int32_t key, uint32_t w, Counters *ctr) {
+  uint32_t s = h % kXlCap;
+  for (int t = 0; t < kXlCap; ++t) {
+    int32_t cur = ((volatile int32_t *)keys)[s];
     bool claimed = false;
     if (cur == kEmpty) {
-      cur = atomicCAS(k, kEmpty, key);
+      cur = atomicCAS(keys + s, kEmpty, key);
       if (cur == kEmpty) {
         cur = key;
         claimed = true;
       }
     }
     if (cur == key) {
-      atomicAdd(cg::this_cluster().map_shared_rank(vals, r) + s, w);
-      if (claimed) {
-        const unsigned pos = atomicAdd(cg::this_cluster().map_shared_rank(nocc, r), 1u);
-        cg::this_cluster().map_shared_rank(occ, r)[pos] = (uint16_t)s;
-      }
+      atomicAdd(vals + s, w);
+      if (claimed) occ[atomicAdd(nocc, 1u)] = (uint16_t)s;
       return;
     }
-    h = (h + 1) & kMask;
+    s = (s + 1) & (kXlCap - 1);
   }
   atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
 }
@@ -626,14 +631,20 @@ template <int WK>
 __global__ void __cluster_dims__(kClusterSize, 1, 1) __launch_bounds__(1024, 1) k_move_cluster(MoveArgs a) {
   namespace cg = cooperative_groups;
   constexpr int NT = 1024;
+  constexpr uint32_t kMask = (uint32_t)kClusterSize * kXlCap - 1;
+  constexpr int kStage = kClusterRound;  // worst case: a whole round sent to one owner
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  // dynamic shared memory: keys[16384], vals[16384], occupied list[16384]
+  const int lane = threadIdx.x & 31;
+  // dynamic shared memory: keys[16384], vals[16384], occupied list[16384],
+  // staged keys[kStage], staged weights[kStage]
   extern __shared__ uint32_t dyn[];
   int32_t *keys = (int32_t *)dyn;
   uint32_t *vals = dyn + kXlCap;
   uint16_t *occ = (uint16_t *)(dyn + 2 * kXlCap);
-  __shared__ unsigned s_nocc;
+  int32_t *stage_k = (int32_t *)(dyn + 2 * kXlCap + kXlCap / 2);
+  uint32_t *stage_w = (uint32_t *)(stage_k + kStage);
+  __shared__ unsigned s_nocc, s_nstage;
   __shared__ long long s_part_s[kClusterSize], s_part_kid[kClusterSize];
   __shared__ int32_t s_part_c[kClusterSize];
   __shared__ int32_t s_target;
@@ -641,7 +652,10 @@ __global__ void __cluster_dims__(kClusterSize, 1, 1) __launch_bounds__(1024, 1) 
     keys[s] = kEmpty;
     vals[s] = 0;
   }
-  if (threadIdx.x == 0) s_nocc = 0;
+  if (threadIdx.x == 0) {
+    s_nocc = 0;
+    s_nstage = 0;
+  }
   cl.sync();
   const unsigned long long cnt = a.ctr->bin_count[kClusterBin];
   const unsigned long long nclusters = gridDim.x / kClusterSize;
@@ -651,16 +665,46 @@ __global__ void __cluster_dims__(kClusterSize, 1, 1) __launch_bounds__(1024, 1) 
     const int32_t i = a.bins[kClusterBin][idx];
     const int64_t b = a.g.begin[i], e = a.g.end[i];
     const int64_t deg = e - b;
-    // this block's share of the row: positions rank * NT + tid + u * (cluster threads)
-    for (int64_t x0 = (int64_t)rank * NT; x0 < deg; x0 += (int64_t)kClusterSize * NT * kRun) {
-      int32_t kk[kRun];
-      uint32_t ww[kRun];
-      gather_run<WK>(a, i, b, x0 + threadIdx.x, (int64_t)kClusterSize * NT, deg, kk, ww);
+    for (int64_t r0 = 0; r0 < deg; r0 += kClusterRound) {
+      // this block's 2 * NT entries of the round, routed to their owners
 #pragma unroll
-      for (int u = 0; u < kRun; ++u)
-        if (kk[u] != kEmpty) cluster_insert(keys, vals, occ, &s_nocc, kk[u], ww[u], a.ctr);
+      for (int u = 0; u < 2; ++u) {
+        const int64_t p = r0 + (int64_t)rank * 2 * NT + u * NT + threadIdx.x;
+        int32_t key = kEmpty;
+        uint32_t w = 0;
+        if (p < deg) {
+          const int32_t j = __ldg(a.g.col + b + p);
+          if (j != i) {
+            key = a.Cp[j];
+            w = load_w<WK>(a.g.w, b + p);
+          }
+        }
+        const int owner = key == kEmpty ? -1 : (int)(slot_of(key, kMask) / kXlCap);
+#pragma unroll
+        for (int o = 0; o < kClusterSize; ++o) {
+          const unsigned m = __ballot_sync(kFull, owner == o);
+          if (!m) continue;
+          const int leader = __ffs(m) - 1;
+          unsigned base = 0;
+          if (lane == leader) base = atomicAdd(cl.map_shared_rank(&s_nstage, o), (unsigned)__popc(m));
+          base = __shfl_sync(kFull, base, leader);
+          if (owner == o) {
+            const unsigned pos = base + __popc(m & lanemask_lt());
+            cl.map_shared_rank(stage_k, o)[pos] = key;
+            cl.map_shared_rank(stage_w, o)[pos] = w;
+          }
+        }
+      }
+      cl.sync();  // every block's staging buffer is complete
+      const unsigned ns = s_nstage;
+      for (unsigned t = threadIdx.x; t < ns; t += NT) {
+        const int32_t key = stage_k[t];
+        owner_insert(keys, vals, occ, &s_nocc, slot_of(key, kMask), key, stage_w[t], a.ctr);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) s_nstage = 0;
+      cl.sync();  // staging buffers are free for the next round
     }
-    cl.sync();  // the distributed table is complete
     const int32_t d = a.Cp[i];
     const long long Ki = a.K[i];
     const long long tm = vertex_two_m(a.batch, a.two_m, i);
@@ -753,7 +797,7 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
 template <int WK>
 __global__ void __launch_bounds__(256) k_pass_init(GView g, int first_pass, int64_t *K, int64_t *Sigma,
                                                    int32_t *Cp, uint8_t *flag, Counters *ctr, float4 *feat,
-                                                   uint32_t *marks) {
+                                                   uint32_t *marks, uint32_t *marks_next) {
   unsigned long long md = 0, big_slots = 0, big_items = 0;
   const int lane = threadIdx.x & 31;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -782,6 +826,7 @@ __global__ void __launch_bounds__(256) k_pass_init(GView g, int first_pass, int6
     if (feat) {
       feat[i] = make_float4(0.f, 0.f, 0.f, 0.f);
       marks[i] = 0;
+      marks_next[i] = 0;
     }
   }
 #pragma unroll
@@ -811,7 +856,8 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
   constexpr size_t kBlockSmem =
       (size_t)kBlockCap * (sizeof(uint32_t) + sizeof(int32_t)) + kBlockCap / 2 * sizeof(uint16_t);
   constexpr size_t kXlSmem = (size_t)kXlCap * (sizeof(uint32_t) + sizeof(int32_t)) + kXlCap / 2 * sizeof(uint16_t);
-  constexpr size_t kClSmem = (size_t)kXlCap * (sizeof(uint32_t) + sizeof(int32_t) + sizeof(uint16_t));
+  constexpr size_t kClSmem = (size_t)kXlCap * (sizeof(uint32_t) + sizeof(int32_t) + sizeof(uint16_t)) +
+                             (size_t)kClusterRound * (sizeof(int32_t) + sizeof(uint32_t));
   if (!attr_done) {
     cudaFuncSetAttribute(k_move_cluster<WK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClSmem);
     cudaFuncSetAttribute(k_move_block<WK, 512, kBlockCap, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -865,8 +911,9 @@ void pass_init_t(const GView &g, int first, int64_t *K, int64_t *Sigma, int32_t 
                  int num_sms, cudaStream_t s, const LearnArgs *learn) {
   float4 *feat = (learn && learn->record) ? learn->feat : nullptr;
   uint32_t *marks = (learn && learn->record) ? learn->marks : nullptr;
+  uint32_t *marks_next = (learn && learn->record) ? learn->marks_next : nullptr;
   LV_LAUNCH(k_pass_init<WK><<<grid_for(g.n, 256, num_sms, 16), 256, 0, s>>>(g, first, K, Sigma, Cp, flag, ctr, feat,
-                                                                             marks));
+                                                                             marks, marks_next));
 }
 
 }  // namespace

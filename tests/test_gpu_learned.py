@@ -106,6 +106,19 @@ def _traces(g, cap=400000, rate=1.0):
     return X, Y, res
 
 
+def test_traces_are_reproducible():
+    """Recorded features depend only on the schedule: two runs give the same
+    (canonically ordered) traces, also with concurrent bin kernels."""
+    g = gg.rmat(14, 16, seed=21)
+    X1, Y1, _ = _traces(g)
+    with lv.Louvain(lv.DeviceCSR.from_host(g), lv.Config(trace_capacity=400000, trace_rate=1.0)) as ctx:
+        ctx.set_schedule(dict(concurrent=1))
+        ctx.run()
+        X2, Y2 = lv.louvain_traces(ctx.ctx, 400000)
+    assert X1.shape[0] > 1000
+    assert np.array_equal(X1, X2) and np.array_equal(Y1, Y2)
+
+
 def test_trace_recording_does_not_change_the_run():
     g = gg.rmat(13, 16, seed=3)
     X, Y, res = _traces(g)
