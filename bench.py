@@ -77,7 +77,8 @@ SAMPLES = {
 
 # timing groups that are one kernel per launch (candidates for the roofline)
 SINGLE_KERNELS = {"select", "move_thread", "move_group", "move_xl", "move_cluster", "move_warp", "move_mid", "move_block", "move_hub", "apply",
-                  "pass_init", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big", "merge_xl", "dendrogram"}
+                  "pass_init", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big", "merge_xl", "merge_group",
+                  "dendrogram"}
 
 
 def make_graph(w):

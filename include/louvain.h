@@ -169,12 +169,13 @@ louvain_status louvain_set_profile(louvain_ctx *ctx, uint32_t profile_mask);
  *       128-thread, 512-thread, hub (<= 3), group, 1024-thread and
  *       4-block-cluster bins (1 .. 64; the cluster grid is rounded to whole
  *       clusters);
- *   [10..15] blocks per SM of the aggregation kernels of the thread, warp,
- *       128-thread, 512-thread, big-community (<= 3) and 1024-thread bins;
- *   [16] graphs: 1 = each local-moving iteration is replayed from a CUDA
+ *   [10..16] blocks per SM of the aggregation kernels of the thread, warp,
+ *       128-thread, 512-thread, big-community (<= 3), 1024-thread and
+ *       group bins;
+ *   [17] graphs: 1 = each local-moving iteration is replayed from a CUDA
  *       graph captured once per pass (plain mode, no profiling);
- *   [17] concurrent: 1 = a bucket's bin kernels run at the same time on
- *       side streams of the context (joined before the moves are applied).
+ *   [18] concurrent: 1 = a bucket's bin kernels (and an aggregation's) run at
+ *       the same time on side streams of the context.
  * Results never depend on the schedule: every bin computes the same exact
  * decisions.  The schedule belongs to the context and is used by its next
  * runs. */

@@ -325,6 +325,73 @@ __device__ __forceinline__ void gather_members(const AggArgs &a, int32_t k, int6
   for (int u = 0; u < kRun; ++u) kk[u] = jj[u] >= 0 ? a.Cp[jj[u]] : kEmpty;
 }
 
+// Group of GS lanes per community (16 < total degree <= 64), 32 / GS
+// communities per warp, a 128-slot shared table per group.
+template <int WK, int GS, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 4) k_merge_group(AggArgs a) {
+  constexpr int kGroups = 32 / GS;
+  constexpr int kSlots = 2 * GS * kRun;
+  static_assert(GS * kRun >= kGroupMaxDeg, "a group must hold a whole community");
+  __shared__ int32_t skeys[WARPS * kGroups][kSlots];
+  __shared__ uint32_t svals[WARPS * kGroups][kSlots];
+  __shared__ uint16_t socc[WARPS * kGroups][kSlots / 2];
+  __shared__ unsigned snocc[WARPS * kGroups];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / GS, gl = lane % GS;
+  int32_t *keys = skeys[warp * kGroups + grp];
+  uint32_t *vals = svals[warp * kGroups + grp];
+  uint16_t *occ = socc[warp * kGroups + grp];
+  unsigned *nocc = &snocc[warp * kGroups + grp];
+  for (int s = gl; s < kSlots; s += GS) {
+    keys[s] = kEmpty;
+    vals[s] = 0;
+  }
+  if (gl == 0) *nocc = 0;
+  __syncwarp();
+  const unsigned long long cnt = a.ctr->mbin_count[kMergeGroupBin];
+  unsigned long long work[4] = {0, 0, 0, 0};
+  const unsigned long long stride = (unsigned long long)gridDim.x * WARPS * kGroups;
+  for (unsigned long long base = ((unsigned long long)blockIdx.x * WARPS + warp) * kGroups; base < cnt;
+       base += stride) {
+    const unsigned long long idx = base + grp;
+    const bool act = idx < cnt;
+    const int32_t k = act ? a.mbins[kMergeGroupBin][idx] : 0;
+    const int64_t ob = act ? a.obegin[k] : 0;
+    const int64_t tot = act ? a.oend[k] - ob : 0;  // total member degree
+    if (act) {
+      int32_t kk[kRun];
+      uint32_t ww[kRun];
+      const int64_t xs = (int64_t)gl * kRun;
+      gather_members<WK>(a, k, xs, xs + kRun < tot ? xs + kRun : tot, kk, ww);
+#pragma unroll
+      for (int u = 0; u < kRun; ++u)
+        if (kk[u] != kEmpty) sm_insert_list(keys, vals, kSlots - 1, kk[u], ww[u], occ, nocc, a.ctr);
+    }
+    __syncwarp();
+    const unsigned nk = *(volatile unsigned *)nocc;
+    for (unsigned t = gl; t < nk; t += GS) {
+      const uint32_t s = occ[t];
+      a.ocol[ob + t] = keys[s];
+      a.ow[ob + t] = vals[s];
+      keys[s] = kEmpty;
+      vals[s] = 0;
+    }
+    __syncwarp();
+    if (act && gl == 0) {
+      *nocc = 0;
+      a.oend[k] = ob + (int64_t)nk;
+      work[0] += 1;
+      work[1] += (unsigned long long)a.kcnt[k];
+      work[2] += (unsigned long long)tot;
+      work[3] += nk;
+    }
+    __syncwarp();
+  }
+  unsigned long long nz[1] = {work[3]};
+  flush_work(nz, &a.ctr->nnz_out);
+  flush_work(work, a.ctr->mg_work[kMergeGroupBin]);
+}
+
 // Warp per community (total degree <= 256): shared table of up to 512 slots,
 // a run of 8 entries per lane.
 template <int WK, int WARPS>
@@ -522,6 +589,8 @@ void merge_t(const AggArgs &a, int num_sms, cudaStream_t s, KernelProf *prof, co
     s3 = side->s[2];
   }
   LV_TIMED(prof, K_MERGE_THREAD, s1, k_merge_thread<WK, 128><<<num_sms * bk[0], 128, 0, s1>>>(a));
+  LV_TIMED(prof, K_MERGE_GROUP, s1,
+           k_merge_group<WK, kGroupLanes, 8><<<num_sms * bk[kMergeGroupBin], 256, 0, s1>>>(a));
   LV_TIMED(prof, K_MERGE_WARP, s2, k_merge_warp<WK, 8><<<num_sms * bk[1], 256, 0, s2>>>(a));
   LV_TIMED(prof, K_MERGE_MID, s3, k_merge_block<WK, 128, kMidCap, 2><<<num_sms * bk[2], 128, kMidSmem, s3>>>(a));
   LV_TIMED(prof, K_MERGE_BLOCK, s3, k_merge_block<WK, 512, kBlockCap, 3><<<num_sms * bk[3], 512, kSmem, s3>>>(a));

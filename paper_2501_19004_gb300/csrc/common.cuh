@@ -49,7 +49,7 @@ struct Counters {
   unsigned long long mv_work[8][5]; // per move bin: vertices, entries, distinct keys, movers, mover entries
   // ---- zeroed every pass ----
   unsigned long long mbin_count[8]; // aggregation bin sizes
-  unsigned long long mg_work[6][4]; // per merge bin: communities, members, entries, entries written
+  unsigned long long mg_work[7][4]; // per merge bin: communities, members, entries, entries written
   unsigned long long maxdeg;
   unsigned long long big_slots;     // bound on the global table slots of big items
   unsigned long long big_items;     // number of big items (hubs / large communities)

@@ -46,10 +46,13 @@ constexpr int kClusterMaxDeg = kXlMaxDeg * kClusterSize;
 constexpr int kClusterBin = 7;
 constexpr int kMoveBins = 8;
 // Aggregation bins: degree_bin's five plus communities with a total member
-// degree in (4096, kXlMaxDeg] for one 1024-thread block (bin 5).
+// degree in (4096, kXlMaxDeg] for one 1024-thread block (bin 5) and in
+// (16, kGroupMaxDeg] for groups of kGroupLanes lanes (bin 6).
 constexpr int kMergeXlBin = 5;
-constexpr int kMergeBins = 6;
+constexpr int kMergeGroupBin = 6;
+constexpr int kMergeBins = 7;
 __host__ __device__ __forceinline__ int merge_bin(int64_t d) {
+  if (d > kThreadMaxDeg && d <= kGroupMaxDeg) return kMergeGroupBin;
   return (d > kBlockMaxDeg && d <= kXlMaxDeg) ? kMergeXlBin : degree_bin(d);
 }
 
@@ -68,7 +71,7 @@ struct Sched {
   int group_max = kGroupMaxDeg;
   int warp_max = kWarpMaxDeg;
   int move[kMoveBins] = {2, 8, 12, 2, 3, 4, 1, 1};  // thread, warp, mid, block, hub, group, xl, cluster
-  int merge[kMergeBins] = {8, 8, 8, 2, 3, 1};   // thread, warp, mid, block, big, xl
+  int merge[kMergeBins] = {8, 8, 8, 2, 3, 1, 4};   // thread, warp, mid, block, big, xl, group
   int graphs = 0;
   int concurrent = 0;
 };
@@ -245,7 +248,7 @@ struct MoveArgs {
 enum KernelId : int {
   K_SELECT = 0, K_MOVE_THREAD, K_MOVE_WARP, K_MOVE_MID, K_MOVE_BLOCK, K_MOVE_HUB, K_APPLY, K_PASS_INIT,
   K_COMM_COUNT, K_SCATTER, K_MERGE_THREAD, K_MERGE_WARP, K_MERGE_MID, K_MERGE_BLOCK, K_MERGE_BIG, K_DENDRO,
-  K_MODULARITY, K_RENUMBER, K_MOVE_HUB_EVAL, K_MERGE_BIG_EMIT, K_MLP_SELECT, K_MOVE_GROUP, K_MOVE_XL, K_MERGE_XL, K_MOVE_CLUSTER, K_NUM_KERNELS
+  K_MODULARITY, K_RENUMBER, K_MOVE_HUB_EVAL, K_MERGE_BIG_EMIT, K_MLP_SELECT, K_MOVE_GROUP, K_MOVE_XL, K_MERGE_XL, K_MOVE_CLUSTER, K_MERGE_GROUP, K_NUM_KERNELS
 };
 extern const char *const kKernelNames[K_NUM_KERNELS];
 

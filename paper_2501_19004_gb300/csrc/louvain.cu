@@ -350,7 +350,7 @@ void account_merge(louvain_ctx *x, const Counters &h) {
       x->kbytes[K_MERGE_BIG_EMIT] += 36.0 * w[0] + 8.0 * w[3];
       continue;
     }
-    x->kbytes[b == kMergeXlBin ? K_MERGE_XL : K_MERGE_THREAD + b] +=
+    x->kbytes[b == kMergeXlBin ? K_MERGE_XL : b == kMergeGroupBin ? K_MERGE_GROUP : K_MERGE_THREAD + b] +=
         36.0 * w[0] + 20.0 * w[1] + (8.0 + wb) * w[2] + 8.0 * w[3];
   }
 }
@@ -659,6 +659,7 @@ AggArgs agg_args(louvain_ctx *x, const GView &g, int wk, int slot) {
   aa.kcnt = x->kcnt;
   for (int k = 0; k < kNumBins; ++k) aa.mbins[k] = x->bins[k];
   aa.mbins[kMergeXlBin] = x->bins[kXlBin];
+  aa.mbins[kMergeGroupBin] = x->bins[kGroupBin];
   aa.obegin = x->pbeg[slot];
   aa.oend = x->pend[slot];
   aa.ocol = x->pcol[slot];
@@ -1682,8 +1683,8 @@ louvain_status louvain_autotune(louvain_ctx *x, int32_t max_runs, char *json, si
     }
     static const int mv_kid[kMoveBins] = {K_MOVE_THREAD, K_MOVE_WARP, K_MOVE_MID, K_MOVE_BLOCK,
                                           K_MOVE_HUB,    K_MOVE_GROUP, K_MOVE_XL,  K_MOVE_CLUSTER};
-    static const int mg_kid[kMergeBins] = {K_MERGE_THREAD, K_MERGE_WARP, K_MERGE_MID,
-                                           K_MERGE_BLOCK,  K_MERGE_BIG,  K_MERGE_XL};
+    static const int mg_kid[kMergeBins] = {K_MERGE_THREAD, K_MERGE_WARP, K_MERGE_MID,   K_MERGE_BLOCK,
+                                           K_MERGE_BIG,    K_MERGE_XL,   K_MERGE_GROUP};
     for (int v : cands) {
       if (runs >= max_runs) break;
       Sched t = best;
