@@ -242,6 +242,7 @@ struct MoveArgs {
   BatchView batch;
   Sched sched;
   const uint32_t *iter = nullptr;  // graph replay: device words {salt, pickless} of the iteration
+  const uint8_t *vbin = nullptr;   // [n'] move bin of every vertex this pass (0xFF: degree 0)
 };
 
 // Kernel identifiers for the optional per-kernel event timing.
@@ -288,9 +289,11 @@ void move_bucket(const MoveArgs &a, const BigArgs &big, int wkind, int num_sms, 
                  const SideStreams *side = nullptr);
 
 // pass initialisation: K (row sums on pass 0, else given), Sigma = K, C' = id,
-// flags = 1, max degree into ctr->maxdeg
+// flags = 1, max degree into ctr->maxdeg; with vbin, every vertex's move
+// bin under `sched` (0xFF for degree 0), read by the selection kernels
 void pass_init(const GView &g, int wkind, int first_pass, int64_t *K, int64_t *Sigma, int32_t *Cp,
-               uint8_t *flag, Counters *ctr, int num_sms, cudaStream_t s, const LearnArgs *learn = nullptr);
+               uint8_t *flag, Counters *ctr, int num_sms, cudaStream_t s, const LearnArgs *learn = nullptr,
+               uint8_t *vbin = nullptr, const Sched *sched = nullptr);
 
 void iota_i32(int32_t *x, int64_t n, int num_sms, cudaStream_t s);
 

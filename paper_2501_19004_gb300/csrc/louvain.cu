@@ -52,6 +52,7 @@ struct louvain_ctx {
   int32_t *C = nullptr, *Cp = nullptr;
   int64_t *K = nullptr, *Kalt = nullptr, *Sigma = nullptr;
   uint8_t *flag = nullptr;
+  uint8_t *vbin = nullptr;  // move bin per vertex of the current pass
   // local moving
   int32_t *bins[kMoveBins] = {};
   int32_t *mv_vertex = nullptr, *mv_target = nullptr;
@@ -476,6 +477,7 @@ louvain_status enqueue_iteration(louvain_ctx *x, const GView &g, int wk, int pas
     a.batch = x->bview;
     a.sched = x->sched;
     a.iter = iter;
+    a.vbin = x->vbin;
     BigArgs big{};
     big.g = g;
     big.Cp = x->Cp;
@@ -755,7 +757,7 @@ louvain_status run_impl(louvain_ctx *x) {
     x->prof.begin(K_PASS_INIT, s);
     {
       const LearnArgs L = learn_args(x, p, 0, false);
-      pass_init(g, wk, p == 0, x->K, x->Sigma, x->Cp, x->flag, x->d_ctr, x->num_sms, s, &L);
+      pass_init(g, wk, p == 0, x->K, x->Sigma, x->Cp, x->flag, x->d_ctr, x->num_sms, s, &L, x->vbin, &x->sched);
     }
     x->prof.end(K_PASS_INIT, s);
     LV_CK(cudaGetLastError());
@@ -919,7 +921,7 @@ louvain_status run_batched(louvain_ctx *x) {
     x->cur_wbytes = wk == W_UNIT ? 0 : 4;
     LV_CK(cudaMemsetAsync(&x->d_ctr->big_slots, 0, 2 * sizeof(unsigned long long), s));
     x->prof.begin(K_PASS_INIT, s);
-    pass_init(g, wk, p == 0, x->K, x->Sigma, x->Cp, x->flag, x->d_ctr, x->num_sms, s);
+    pass_init(g, wk, p == 0, x->K, x->Sigma, x->Cp, x->flag, x->d_ctr, x->num_sms, s, nullptr, x->vbin, &x->sched);
     x->prof.end(K_PASS_INIT, s);
     LV_CK(cudaGetLastError());
     if ((st = read_counters(x))) return st;
@@ -1235,7 +1237,8 @@ louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg
   }
   // per-vertex state and work arrays
   if ((st = dalloc_n(x, &x->C, nv)) || (st = dalloc_n(x, &x->Cp, nv)) || (st = dalloc_n(x, &x->K, nv)) ||
-      (st = dalloc_n(x, &x->Kalt, nv)) || (st = dalloc_n(x, &x->Sigma, nv)) || (st = dalloc_n(x, &x->flag, nv)))
+      (st = dalloc_n(x, &x->Kalt, nv)) || (st = dalloc_n(x, &x->Sigma, nv)) || (st = dalloc_n(x, &x->flag, nv)) ||
+      (st = dalloc_n(x, &x->vbin, nv)))
     return fail(st);
   for (int k = 0; k < kMoveBins; ++k)
     if ((st = dalloc_n(x, &x->bins[k], nv))) return fail(st);

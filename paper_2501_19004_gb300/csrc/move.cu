@@ -30,7 +30,12 @@ namespace {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // ------------------------------------------------------------------ select
-// Block-aggregated appends: one global atomic per bin per block and tile.
+// Each thread takes 8 consecutive vertices (one 8-byte load of their flags);
+// per bin, a warp scan places every thread's selections and one shared
+// atomic per warp and one global atomic per block and tile reserve space,
+// so a bin list holds each warp's vertices in increasing order.
+constexpr int kSelVPT = 8;
+
 __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
   __shared__ unsigned s_cnt[kMoveBins + 1];
   __shared__ unsigned long long s_base[kMoveBins];
@@ -38,61 +43,113 @@ __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
   const int lane = threadIdx.x & 31;
   const bool pow2 = (a.nbuckets & (a.nbuckets - 1)) == 0;
   const uint32_t salt = a.iter ? a.iter[0] : a.salt;
-  for (int64_t tile = (int64_t)blockIdx.x * blockDim.x; tile < n; tile += (int64_t)gridDim.x * blockDim.x) {
+  constexpr int64_t kTile = 256 * kSelVPT;
+  for (int64_t tile = (int64_t)blockIdx.x * kTile; tile < n; tile += (int64_t)gridDim.x * kTile) {
     if (threadIdx.x <= kMoveBins) s_cnt[threadIdx.x] = 0;
     __syncthreads();
-    const int64_t i = tile + threadIdx.x;
-    int bin = -1;
-    bool sel = false;
-    bool cand = false;
-    if (a.learn.record && i < n) {  // the previous bucket's neighbour moves
-      const uint32_t mn = a.learn.marks_next[i];
-      if (mn) {
-        a.learn.marks[i] += mn;
-        a.learn.marks_next[i] = 0;
+    const int64_t i0 = tile + (int64_t)threadIdx.x * kSelVPT;
+    const bool whole = i0 + kSelVPT <= n;
+    unsigned long long fl = 0, vbw = 0;
+    if (whole) {
+      fl = *reinterpret_cast<const unsigned long long *>(a.flag + i0);
+      if (fl && a.vbin) vbw = *reinterpret_cast<const unsigned long long *>(a.vbin + i0);
+    } else {
+#pragma unroll
+      for (int v = 0; v < kSelVPT; ++v)
+        if (i0 + v < n) {
+          fl |= (unsigned long long)a.flag[i0 + v] << (8 * v);
+          if (a.vbin) vbw |= (unsigned long long)a.vbin[i0 + v] << (8 * v);
+        }
+    }
+    unsigned long long clear = 0;
+    int vb[kSelVPT];
+    unsigned cnt[kMoveBins];
+#pragma unroll
+    for (int b = 0; b < kMoveBins; ++b) cnt[b] = 0;
+    unsigned nsel = 0;
+#pragma unroll
+    for (int v = 0; v < kSelVPT; ++v) {
+      const int64_t i = i0 + v;
+      vb[v] = -1;
+      bool cand = false;
+      if (a.learn.record && i < n) {  // the previous bucket's neighbour moves
+        const uint32_t mn = a.learn.marks_next[i];
+        if (mn) {
+          a.learn.marks[i] += mn;
+          a.learn.marks_next[i] = 0;
+        }
       }
-    }
-    bool live = i < n && a.flag[i];
-    uint32_t local = (uint32_t)i;
-    if (live && a.batch.gid) {  // batched: only graphs still moving, hashed by their local ids
-      const int32_t gg = a.batch.gid[i];
-      live = a.batch.moving[gg] != 0;
-      local = (uint32_t)(i - a.batch.vo[gg]);
-    }
-    if (live) {
-      const uint32_t h = fmix32(local ^ salt);
-      const uint32_t bk = pow2 ? (h & (a.nbuckets - 1)) : (h % a.nbuckets);
-      if (bk == a.bucket) {
-        if (a.learn.enabled && a.learn.feat[i].w > 0.f) {
-          cand = true;  // the predictor decides (k_mlp_select); the flag stays until then
-        } else {
-          a.flag[i] = 0;
-          sel = true;
-          const int64_t deg = a.g.end[i] - a.g.begin[i];
-          if (deg > 0) bin = move_bin(deg, a.sched.group_max, a.sched.warp_max);
+      bool live = ((fl >> (8 * v)) & 0xFFull) != 0;
+      uint32_t local = (uint32_t)i;
+      if (live && a.batch.gid) {  // batched: only graphs still moving, hashed by their local ids
+        const int32_t gg = a.batch.gid[i];
+        live = a.batch.moving[gg] != 0;
+        local = (uint32_t)(i - a.batch.vo[gg]);
+      }
+      if (live) {
+        const uint32_t h = fmix32(local ^ salt);
+        const uint32_t bk = pow2 ? (h & (a.nbuckets - 1)) : (h % a.nbuckets);
+        if (bk == a.bucket) {
+          if (a.learn.enabled && a.learn.feat[i].w > 0.f) {
+            cand = true;  // the predictor decides (k_mlp_select); the flag stays until then
+          } else {
+            clear |= 0xFFull << (8 * v);
+            ++nsel;
+            int b = -1;
+            if (a.vbin) {
+              const unsigned byte = (unsigned)((vbw >> (8 * v)) & 0xFFull);
+              if (byte != 0xFFu) b = (int)byte;
+            } else {
+              const int64_t deg = a.g.end[i] - a.g.begin[i];
+              if (deg > 0) b = move_bin(deg, a.sched.group_max, a.sched.warp_max);
+            }
+            if (b >= 0) {
+              vb[v] = b;
+#pragma unroll
+              for (int q = 0; q < kMoveBins; ++q) cnt[q] += (q == b) ? 1u : 0u;
+            }
+          }
+        }
+      }
+      if (a.learn.enabled) {
+        const unsigned cmask = __ballot_sync(kFull, cand);
+        if (cmask) {
+          const int leader = __ffs(cmask) - 1;
+          unsigned long long base = 0;
+          if (lane == leader) base = atomicAdd(&a.ctr->cand_count, (unsigned long long)__popc(cmask));
+          base = __shfl_sync(kFull, base, leader);
+          if (cand) a.learn.cand[base + __popc(cmask & lanemask_lt())] = (int32_t)i;
         }
       }
     }
-    if (a.learn.enabled) {
-      const unsigned cmask = __ballot_sync(kFull, cand);
-      if (cmask) {
-        const int leader = __ffs(cmask) - 1;
-        unsigned long long base = 0;
-        if (lane == leader) base = atomicAdd(&a.ctr->cand_count, (unsigned long long)__popc(cmask));
-        base = __shfl_sync(kFull, base, leader);
-        if (cand) a.learn.cand[base + __popc(cmask & lanemask_lt())] = (int32_t)i;
+    if (clear) {
+      if (whole) {
+        *reinterpret_cast<unsigned long long *>(a.flag + i0) = fl & ~clear;
+      } else {
+#pragma unroll
+        for (int v = 0; v < kSelVPT; ++v)
+          if ((clear >> (8 * v)) & 0xFFull) a.flag[i0 + v] = 0;
       }
     }
-    unsigned woff[kMoveBins];
-    unsigned bmask[kMoveBins];
+    // per bin: this thread's offset within the warp, the warp's offset
+    // within the block
+    unsigned woff[kMoveBins], wbase[kMoveBins];
 #pragma unroll
     for (int b = 0; b < kMoveBins; ++b) {
-      bmask[b] = __ballot_sync(kFull, bin == b);
-      woff[b] = 0;
-      if (lane == 0 && bmask[b]) woff[b] = atomicAdd(&s_cnt[b], (unsigned)__popc(bmask[b]));
+      unsigned x = cnt[b];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+      }
+      woff[b] = x - cnt[b];
+      const unsigned wtot = __shfl_sync(kFull, x, 31);
+      unsigned wb = 0;
+      if (lane == 0 && wtot) wb = atomicAdd(&s_cnt[b], wtot);
+      wbase[b] = __shfl_sync(kFull, wb, 0);
     }
-    const unsigned smask = __ballot_sync(kFull, sel);
-    if (lane == 0 && smask) atomicAdd(&s_cnt[kMoveBins], (unsigned)__popc(smask));
+    nsel = warp_sum_u(nsel);
+    if (lane == 0 && nsel) atomicAdd(&s_cnt[kMoveBins], (unsigned)nsel);
     __syncthreads();
     if (threadIdx.x < kMoveBins && s_cnt[threadIdx.x])
       s_base[threadIdx.x] = atomicAdd(&a.ctr->bin_count[threadIdx.x], (unsigned long long)s_cnt[threadIdx.x]);
@@ -101,8 +158,11 @@ __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
     __syncthreads();
 #pragma unroll
     for (int b = 0; b < kMoveBins; ++b) {
-      const unsigned off = __shfl_sync(kFull, woff[b], 0);
-      if (bin == b) a.bins[b][s_base[b] + off + __popc(bmask[b] & lanemask_lt())] = (int32_t)i;
+      if (!cnt[b]) continue;
+      unsigned long long pos = s_base[b] + wbase[b] + woff[b];
+#pragma unroll
+      for (int v = 0; v < kSelVPT; ++v)
+        if (vb[v] == b) a.bins[b][pos++] = (int32_t)(i0 + v);
     }
     __syncthreads();
   }
@@ -797,13 +857,15 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
 template <int WK>
 __global__ void __launch_bounds__(256) k_pass_init(GView g, int first_pass, int64_t *K, int64_t *Sigma,
                                                    int32_t *Cp, uint8_t *flag, Counters *ctr, float4 *feat,
-                                                   uint32_t *marks, uint32_t *marks_next) {
+                                                   uint32_t *marks, uint32_t *marks_next, uint8_t *vbin,
+                                                   int group_max, int warp_max) {
   unsigned long long md = 0, big_slots = 0, big_items = 0;
   const int lane = threadIdx.x & 31;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = g.begin[i], e = g.end[i];
     const unsigned long long deg = (unsigned long long)(e - b);
     if (deg > md) md = deg;
+    if (vbin) vbin[i] = deg > 0 ? (uint8_t)move_bin((int64_t)deg, group_max, warp_max) : (uint8_t)0xFF;
     if (deg > (unsigned long long)kClusterMaxDeg) {  // hubs of the global tables
       big_slots += big_table_cap(deg, (unsigned long long)g.n);
       big_items += 1;
@@ -866,7 +928,7 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
                          (int)kXlSmem);
     attr_done = true;
   }
-  LV_TIMED(prof, K_SELECT, s, k_select<<<grid_for(a.g.n, 256, num_sms, 8), 256, 0, s>>>(a));
+  LV_TIMED(prof, K_SELECT, s, k_select<<<grid_for((a.g.n + kSelVPT - 1) / kSelVPT, 256, num_sms, 8), 256, 0, s>>>(a));
   if (a.learn.enabled) LV_TIMED(prof, K_MLP_SELECT, s, k_mlp_select<<<num_sms * 4, 256, 0, s>>>(a));
   const bool hubs = big.ws.slots > 0;
   if (hubs) big_move_plan(big, s, prof);  // the round count reaches the host while the bins below run
@@ -908,12 +970,14 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
 
 template <int WK>
 void pass_init_t(const GView &g, int first, int64_t *K, int64_t *Sigma, int32_t *Cp, uint8_t *flag, Counters *ctr,
-                 int num_sms, cudaStream_t s, const LearnArgs *learn) {
+                 int num_sms, cudaStream_t s, const LearnArgs *learn, uint8_t *vbin, const Sched *sched) {
   float4 *feat = (learn && learn->record) ? learn->feat : nullptr;
   uint32_t *marks = (learn && learn->record) ? learn->marks : nullptr;
   uint32_t *marks_next = (learn && learn->record) ? learn->marks_next : nullptr;
   LV_LAUNCH(k_pass_init<WK><<<grid_for(g.n, 256, num_sms, 16), 256, 0, s>>>(g, first, K, Sigma, Cp, flag, ctr, feat,
-                                                                             marks, marks_next));
+                                                                             marks, marks_next, vbin,
+                                                                             sched ? sched->group_max : 0,
+                                                                             sched ? sched->warp_max : 0));
 }
 
 }  // namespace
@@ -926,10 +990,11 @@ void move_bucket(const MoveArgs &a, const BigArgs &big, int wkind, int num_sms, 
 }
 
 void pass_init(const GView &g, int wkind, int first_pass, int64_t *K, int64_t *Sigma, int32_t *Cp, uint8_t *flag,
-               Counters *ctr, int num_sms, cudaStream_t s, const LearnArgs *learn) {
+               Counters *ctr, int num_sms, cudaStream_t s, const LearnArgs *learn, uint8_t *vbin, const Sched *sched) {
   if (g.n <= 0) return;
-  if (wkind == W_UNIT) pass_init_t<W_UNIT>(g, first_pass, K, Sigma, Cp, flag, ctr, num_sms, s, learn);
-  else pass_init_t<W_U32>(g, first_pass, K, Sigma, Cp, flag, ctr, num_sms, s, learn);
+  if (!sched) vbin = nullptr;
+  if (wkind == W_UNIT) pass_init_t<W_UNIT>(g, first_pass, K, Sigma, Cp, flag, ctr, num_sms, s, learn, vbin, sched);
+  else pass_init_t<W_U32>(g, first_pass, K, Sigma, Cp, flag, ctr, num_sms, s, learn, vbin, sched);
 }
 
 void iota_i32(int32_t *x, int64_t n, int num_sms, cudaStream_t s) {
