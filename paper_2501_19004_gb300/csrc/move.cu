@@ -266,27 +266,34 @@ __global__ void __launch_bounds__(256) k_move_thread(MoveArgs a) {
       const long long tm = vertex_two_m(a.batch, a.two_m, i);
       long long Kid = 0;
 #pragma unroll
-      for (int k = 0; k < D; ++k) Kid += (cc[k] == d) ? ww[k] : 0u;
+      for (int k = 0; k < D; ++k) {
+        if (k >= deg) break;
+        Kid += (cc[k] == d) ? ww[k] : 0u;
+      }
       long long best_s = LLONG_MIN;
       int32_t best_c = INT_MAX;
+      // every community once, at its first occurrence in the row: its weight
+      // is the sum over that and the later occurrences (the loops stop at
+      // the row's degree)
 #pragma unroll
       for (int k = 0; k < D; ++k) {
+        if (k >= deg) break;
         const int32_t c = cc[k];
         bool first = (c != kEmpty) && (c != d);
-        long long sum = 0;
 #pragma unroll
-        for (int l = 0; l < D; ++l) {
-          const bool eq = cc[l] == c;
-          sum += eq ? ww[l] : 0u;
-          if (l < k && eq) first = false;
+        for (int l = 0; l < k; ++l) first = first && (cc[l] != c);
+        if (!first) continue;
+        long long sum = ww[k];
+#pragma unroll
+        for (int l = k + 1; l < D; ++l) {
+          if (l >= deg) break;
+          sum += (cc[l] == c) ? ww[l] : 0u;
         }
-        if (first) {
-          ++work[2];
-          const long long s = tm * sum - Ki * a.Sigma[c];
-          if (better(s, c, best_s, best_c)) {
-            best_s = s;
-            best_c = c;
-          }
+        ++work[2];
+        const long long s = tm * sum - Ki * a.Sigma[c];
+        if (better(s, c, best_s, best_c)) {
+          best_s = s;
+          best_c = c;
         }
       }
       long long s_d = 0;
