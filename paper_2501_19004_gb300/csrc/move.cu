@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_move_warp(MoveArgs a) {
       gather_run<WK>(a, i, b, x0 + lane, 32, deg, kk, ww);
 #pragma unroll
       for (int u = 0; u < kRun; ++u)
-        if (x0 + u * 32 < deg) warp_insert_sm_list(keys, vals, mask, kk[u], ww[u], occ, nocc, a.ctr);  // warp-uniform
+        if (x0 + u * 32 < deg && kk[u] != kEmpty) sm_insert_list(keys, vals, mask, kk[u], ww[u], occ, nocc, a.ctr);
     }
     __syncwarp();
     const int32_t d = a.Cp[i];
@@ -596,8 +596,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : NT == 512 ? 2 : 1) k_move_
       gather_run<WK>(a, i, b, x0 + threadIdx.x, NT, deg, kk, ww);
 #pragma unroll
       for (int u = 0; u < kRun; ++u)
-        if (x0 + u * NT + (threadIdx.x & ~31) < deg)  // warp-uniform
-          warp_insert_sm_list(keys, vals, CAP - 1, kk[u], ww[u], occ, &s_nocc, a.ctr);
+        if (kk[u] != kEmpty) sm_insert_list(keys, vals, CAP - 1, kk[u], ww[u], occ, &s_nocc, a.ctr);
     }
     __syncthreads();
     const int32_t d = a.Cp[i];
