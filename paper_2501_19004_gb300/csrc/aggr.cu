@@ -425,7 +425,8 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_merge_warp(AggArgs a) {
       const int64_t xs = x0 + lane * kRun;
       gather_members<WK>(a, k, xs, xs + kRun < tot ? xs + kRun : tot, kk, ww);
 #pragma unroll
-      for (int u = 0; u < kRun; ++u) warp_insert_sm_list(keys, vals, kWarpCap - 1, kk[u], ww[u], occ, nocc, a.ctr);
+      for (int u = 0; u < kRun; ++u)
+        if (kk[u] != kEmpty) sm_insert_list(keys, vals, kWarpCap - 1, kk[u], ww[u], occ, nocc, a.ctr);
     }
     __syncwarp();
     // the occupied slots are the super-vertex's entries (any order)
@@ -482,7 +483,8 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : NT == 512 ? 2 : 1) k_merge
       const int64_t xs = x0 + (int64_t)threadIdx.x * kRun;
       gather_members<WK>(a, k, xs, xs + kRun < tot ? xs + kRun : tot, kk, ww);
 #pragma unroll
-      for (int u = 0; u < kRun; ++u) warp_insert_sm_list(keys, vals, CAP - 1, kk[u], ww[u], occ, &s_nocc, a.ctr);
+      for (int u = 0; u < kRun; ++u)
+        if (kk[u] != kEmpty) sm_insert_list(keys, vals, CAP - 1, kk[u], ww[u], occ, &s_nocc, a.ctr);
     }
     __syncthreads();
     const unsigned nk = s_nocc;
