@@ -218,7 +218,13 @@ __global__ void __launch_bounds__(kNT, 3) k_big_accum(BigArgs a, int r) {
     }
     if (threadIdx.x == 0) entries += (unsigned long long)(x1 - x0);
 #pragma unroll
-    for (int u = 0; u < kRun; ++u) warp_insert_sm(skeys, svals, kBigSmemSlots - 1, kk[u], ww[u], a.ctr);
+    for (int u = 0; u < kRun; ++u) {
+      if (MODE == MODE_MERGE) {  // community rows repeat keys a lot: sum equal keys across the warp first
+        warp_insert_sm(skeys, svals, kBigSmemSlots - 1, kk[u], ww[u], a.ctr);
+      } else if (kk[u] != kEmpty) {
+        sm_insert(skeys, svals, kBigSmemSlots - 1, kk[u], ww[u], a.ctr);
+      }
+    }
     __syncthreads();
     const int64_t toff = a.ws.toff[k] - rr.base;
     const uint32_t gcap = table_cap(tot, a.keyspace);
