@@ -76,7 +76,7 @@ SAMPLES = {
 
 
 # timing groups that are one kernel per launch (candidates for the roofline)
-SINGLE_KERNELS = {"select", "move_thread", "move_group", "move_xl", "move_cluster", "move_warp", "move_mid", "move_block", "move_hub", "apply",
+SINGLE_KERNELS = {"select", "move_thread", "move_group", "move_half", "move_xl", "move_cluster", "move_warp", "move_mid", "move_block", "move_hub", "apply",
                   "pass_init", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big", "merge_xl", "merge_group",
                   "dendrogram"}
 
@@ -202,7 +202,7 @@ def main():
     ap.add_argument("--learned-fallback", type=int, default=0)
     ap.add_argument("--graphs", type=int, default=0, help="batch workloads: run only the first N graphs")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch schedule")
-    ap.add_argument("--autotune-runs", type=int, default=24)
+    ap.add_argument("--autotune-runs", type=int, default=32)
     ap.add_argument("--sequential-sample", type=int, default=256,
                     help="batch workloads: graphs run one context at a time for comparison")
     args = ap.parse_args()

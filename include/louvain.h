@@ -163,18 +163,20 @@ louvain_status louvain_set_profile(louvain_ctx *ctx, uint32_t profile_mask);
  * fixes one kernel configuration).  A schedule is louvain_schedule_words()
  * int32 words:
  *   [0] group_max: largest degree handled by 8-lane groups (16 .. 64;
- *       16 = no group bin); [1] warp_max: largest degree handled by a warp
- *       (group_max .. 256; larger degrees up to 1024 go to 128-thread blocks);
- *   [2..9] blocks per SM of the local-moving kernels of the thread, warp,
- *       128-thread, 512-thread, hub (<= 3), group, 1024-thread and
- *       4-block-cluster bins (1 .. 64; the cluster grid is rounded to whole
- *       clusters);
- *   [10..16] blocks per SM of the aggregation kernels of the thread, warp,
- *       128-thread, 512-thread, big-community (<= 3), 1024-thread and
- *       group bins;
- *   [17] graphs: 1 = each local-moving iteration is replayed from a CUDA
+ *       16 = no 8-lane groups); [1] half_max: largest degree handled by
+ *       16-lane groups (group_max .. 128; = group_max for none); [2]
+ *       warp_max: largest degree handled by a warp (half_max .. 256; larger
+ *       degrees up to 1024 go to 128-thread blocks);
+ *   [3..11] blocks per SM of the local-moving kernels of the thread, warp,
+ *       128-thread, 512-thread, hub (<= 3), 8-lane group, 1024-thread,
+ *       4-block-cluster (the grid is rounded to whole clusters) and 16-lane
+ *       group bins (1 .. 64);
+ *   [12..18] blocks per SM of the aggregation kernels of the thread, warp,
+ *       128-thread, 512-thread, big-community (<= 3), 1024-thread and group
+ *       bins;
+ *   [19] graphs: 1 = each local-moving iteration is replayed from a CUDA
  *       graph captured once per pass (plain mode, no profiling);
- *   [18] concurrent: 1 = a bucket's bin kernels (and an aggregation's) run at
+ *   [20] concurrent: 1 = a bucket's bin kernels (and an aggregation's) run at
  *       the same time on side streams of the context.
  * Results never depend on the schedule: every bin computes the same exact
  * decisions.  The schedule belongs to the context and is used by its next

@@ -46,7 +46,7 @@ struct Counters {
   unsigned long long it_moves;
   unsigned long long it_evaluated;
   unsigned long long it_skipped;    // learned mode: flagged vertices skipped by the predictor
-  unsigned long long mv_work[8][5]; // per move bin: vertices, entries, distinct keys, movers, mover entries
+  unsigned long long mv_work[9][5]; // per move bin: vertices, entries, distinct keys, movers, mover entries
   // ---- zeroed every pass ----
   unsigned long long mbin_count[8]; // aggregation bin sizes
   unsigned long long mg_work[7][4]; // per merge bin: communities, members, entries, entries written
@@ -63,7 +63,7 @@ struct Counters {
   unsigned long long trace_count;   // recorded (features, moved) samples
   unsigned long long pad[2];
 };
-constexpr int kIterCounterWords = 5 + 40;
+constexpr int kIterCounterWords = 5 + 45;
 
 // MurmurHash3 finaliser (Appleby, public domain).
 __host__ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {

@@ -44,7 +44,12 @@ constexpr int kXlBin = 6;
 constexpr int kClusterSize = 4;
 constexpr int kClusterMaxDeg = kXlMaxDeg * kClusterSize;
 constexpr int kClusterBin = 7;
-constexpr int kMoveBins = 8;
+// Degrees (group_max, half_max] go to groups of 16 lanes (two vertices per
+// warp, rows of up to 128 entries).
+constexpr int kHalfLanes = 16;
+constexpr int kHalfMaxDeg = 128;
+constexpr int kHalfBin = 8;
+constexpr int kMoveBins = 9;
 // Aggregation bins: degree_bin's five plus communities with a total member
 // degree in (4096, kXlMaxDeg] for one 1024-thread block (bin 5) and in
 // (16, kGroupMaxDeg] for groups of kGroupLanes lanes (bin 6).
@@ -69,13 +74,14 @@ __host__ __device__ __forceinline__ int merge_bin(int64_t d) {
 //              time (fork and join through events).
 struct Sched {
   int group_max = kGroupMaxDeg;
+  int half_max = kHalfMaxDeg;
   int warp_max = kWarpMaxDeg;
-  int move[kMoveBins] = {2, 8, 12, 2, 3, 4, 1, 1};  // thread, warp, mid, block, hub, group, xl, cluster
+  int move[kMoveBins] = {2, 8, 12, 2, 3, 4, 1, 1, 4};  // thread, warp, mid, block, hub, group, xl, cluster, half
   int merge[kMergeBins] = {8, 8, 8, 2, 3, 1, 4};   // thread, warp, mid, block, big, xl, group
   int graphs = 0;
   int concurrent = 0;
 };
-constexpr int kSchedWords = 2 + kMoveBins + kMergeBins + 2;
+constexpr int kSchedWords = 3 + kMoveBins + kMergeBins + 2;
 
 // Side streams for concurrent bin kernels (created with the context).
 constexpr int kSideStreams = 3;
@@ -85,9 +91,10 @@ struct SideStreams {
   cudaEvent_t join[kSideStreams] = {};
 };
 
-__host__ __device__ __forceinline__ int move_bin(int64_t d, int group_max, int warp_max) {
+__host__ __device__ __forceinline__ int move_bin(int64_t d, int group_max, int half_max, int warp_max) {
   if (d <= kThreadMaxDeg) return 0;
   if (d <= group_max) return kGroupBin;
+  if (d <= half_max) return kHalfBin;
   if (d <= warp_max) return 1;
   if (d <= kMidMaxDeg) return 2;
   if (d <= kBlockMaxDeg) return 3;
@@ -249,7 +256,7 @@ struct MoveArgs {
 enum KernelId : int {
   K_SELECT = 0, K_MOVE_THREAD, K_MOVE_WARP, K_MOVE_MID, K_MOVE_BLOCK, K_MOVE_HUB, K_APPLY, K_PASS_INIT,
   K_COMM_COUNT, K_SCATTER, K_MERGE_THREAD, K_MERGE_WARP, K_MERGE_MID, K_MERGE_BLOCK, K_MERGE_BIG, K_DENDRO,
-  K_MODULARITY, K_RENUMBER, K_MOVE_HUB_EVAL, K_MERGE_BIG_EMIT, K_MLP_SELECT, K_MOVE_GROUP, K_MOVE_XL, K_MERGE_XL, K_MOVE_CLUSTER, K_MERGE_GROUP, K_NUM_KERNELS
+  K_MODULARITY, K_RENUMBER, K_MOVE_HUB_EVAL, K_MERGE_BIG_EMIT, K_MLP_SELECT, K_MOVE_GROUP, K_MOVE_XL, K_MERGE_XL, K_MOVE_CLUSTER, K_MERGE_GROUP, K_MOVE_HALF, K_NUM_KERNELS
 };
 extern const char *const kKernelNames[K_NUM_KERNELS];
 

@@ -331,7 +331,11 @@ void account_move(louvain_ctx *x, int64_t n, const Counters &h) {
       x->kbytes[K_MOVE_HUB_EVAL] += 40.0 * w[0] + 8.0 * w[2] + 8.0 * w[3] + 1.0 * w[4];
       continue;
     }
-    x->kbytes[b == kGroupBin ? K_MOVE_GROUP : b == kXlBin ? K_MOVE_XL : b == kClusterBin ? K_MOVE_CLUSTER : K_MOVE_THREAD + b] +=
+    x->kbytes[b == kGroupBin     ? K_MOVE_GROUP
+              : b == kXlBin      ? K_MOVE_XL
+              : b == kClusterBin ? K_MOVE_CLUSTER
+              : b == kHalfBin    ? K_MOVE_HALF
+                                 : K_MOVE_THREAD + b] +=
         40.0 * w[0] + (8.0 + wb) * w[1] + 8.0 * w[2] + 8.0 * w[3] + 1.0 * w[4];
   }
   x->kbytes[K_SELECT] += (double)x->cfg.buckets * n + 21.0 * h.it_evaluated;
@@ -1554,6 +1558,7 @@ louvain_status louvain_set_profile(louvain_ctx *x, uint32_t mask) {
 static void sched_to_words(const Sched &s, int32_t *w) {
   int k = 0;
   w[k++] = s.group_max;
+  w[k++] = s.half_max;
   w[k++] = s.warp_max;
   for (int b = 0; b < kMoveBins; ++b) w[k++] = s.move[b];
   for (int b = 0; b < kMergeBins; ++b) w[k++] = s.merge[b];
@@ -1565,13 +1570,15 @@ static bool sched_from_words(const int32_t *w, Sched *s) {
   Sched t;
   int k = 0;
   t.group_max = w[k++];
+  t.half_max = w[k++];
   t.warp_max = w[k++];
   for (int b = 0; b < kMoveBins; ++b) t.move[b] = w[k++];
   for (int b = 0; b < kMergeBins; ++b) t.merge[b] = w[k++];
   t.graphs = w[k++];
   t.concurrent = w[k++];
   if (t.group_max < kThreadMaxDeg || t.group_max > kGroupMaxDeg) return false;
-  if (t.warp_max < t.group_max || t.warp_max > kWarpMaxDeg) return false;
+  if (t.half_max < t.group_max || t.half_max > kHalfMaxDeg) return false;
+  if (t.warp_max < t.half_max || t.warp_max > kWarpMaxDeg) return false;
   for (int b = 0; b < kMoveBins; ++b)
     if (t.move[b] < 1 || t.move[b] > 64) return false;
   for (int b = 0; b < kMergeBins; ++b)
@@ -1655,23 +1662,25 @@ louvain_status louvain_autotune(louvain_ctx *x, int32_t max_runs, char *json, si
   {
     Sched best = start;
     double best_ms = start_ms;
-    // 1. thresholds
+    // 1. thresholds (a half bin with half_max == group_max is empty)
     const int gms[] = {16, 32, 48, 64};
-    const int wms[] = {64, 128, 256};
+    const int wms[] = {128, 256};
     for (int gm : gms)
-      for (int wm : wms) {
-        if (wm < gm || runs >= max_runs) continue;
-        if (gm == start.group_max && wm == start.warp_max) continue;
-        Sched t = best;
-        t.group_max = gm;
-        t.warp_max = wm;
-        if ((st = run_once(t, false, &ms))) goto fail;
-        note("thresholds", t, ms);
-        if (ms < best_ms) {
-          best_ms = ms;
-          best = t;
+      for (int hm : {gm, kHalfMaxDeg})
+        for (int wm : wms) {
+          if (wm < hm || runs >= max_runs) continue;
+          if (gm == start.group_max && hm == start.half_max && wm == start.warp_max) continue;
+          Sched t = best;
+          t.group_max = gm;
+          t.half_max = hm;
+          t.warp_max = wm;
+          if ((st = run_once(t, false, &ms))) goto fail;
+          note("thresholds", t, ms);
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = t;
+          }
         }
-      }
     // 2. blocks per SM, all bins at once per candidate
     const int cands[] = {2, 3, 4, 6, 8, 12, 16};
     double mv_best[kMoveBins], mg_best[kMergeBins];
@@ -1684,8 +1693,8 @@ louvain_status louvain_autotune(louvain_ctx *x, int32_t max_runs, char *json, si
       mg_best[b] = 1e30;
       mg_arg[b] = best.merge[b];
     }
-    static const int mv_kid[kMoveBins] = {K_MOVE_THREAD, K_MOVE_WARP, K_MOVE_MID, K_MOVE_BLOCK,
-                                          K_MOVE_HUB,    K_MOVE_GROUP, K_MOVE_XL,  K_MOVE_CLUSTER};
+    static const int mv_kid[kMoveBins] = {K_MOVE_THREAD, K_MOVE_WARP, K_MOVE_MID,     K_MOVE_BLOCK, K_MOVE_HUB,
+                                          K_MOVE_GROUP,  K_MOVE_XL,   K_MOVE_CLUSTER, K_MOVE_HALF};
     static const int mg_kid[kMergeBins] = {K_MERGE_THREAD, K_MERGE_WARP, K_MERGE_MID,   K_MERGE_BLOCK,
                                            K_MERGE_BIG,    K_MERGE_XL,   K_MERGE_GROUP};
     for (int v : cands) {

@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
               if (byte != 0xFFu) b = (int)byte;
             } else {
               const int64_t deg = a.g.end[i] - a.g.begin[i];
-              if (deg > 0) b = move_bin(deg, a.sched.group_max, a.sched.warp_max);
+              if (deg > 0) b = move_bin(deg, a.sched.group_max, a.sched.half_max, a.sched.warp_max);
             }
             if (b >= 0) {
               vb[v] = b;
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(256) k_mlp_select(MoveArgs a) {
     if (eval) {
       a.flag[mine] = 0;
       const int64_t deg = a.g.end[mine] - a.g.begin[mine];
-      if (deg > 0) bin = move_bin(deg, a.sched.group_max, a.sched.warp_max);
+      if (deg > 0) bin = move_bin(deg, a.sched.group_max, a.sched.half_max, a.sched.warp_max);
       ++evaluated;
     } else if (mine >= 0) {
       ++skipped;
@@ -447,16 +447,17 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_move_warp(MoveArgs a) {
   flush_work(work, a.ctr->mv_work[1]);
 }
 
-// ----------------------------------------------------------------- group bin
-// 16 < degree <= 64: GS lanes per vertex, 32 / GS vertices per warp, each
-// group with a shared table of up to 2 * GS * kRun slots; every lane reads up
-// to kRun entries strided by GS.  Several vertices per warp keep more
-// independent row and community reads in flight than a warp per vertex.
-template <int WK, int GS, int WARPS>
+// ----------------------------------------------------------------- group bins
+// 16 < degree <= 64 (GS = 8) and 64 < degree <= 128 (GS = 16): GS lanes per
+// vertex, 32 / GS vertices per warp, each group with a shared table of up to
+// 2 * GS * kRun slots; every lane reads up to kRun entries strided by GS.
+// Several vertices per warp keep more independent row and community reads in
+// flight than a warp per vertex.
+template <int WK, int GS, int WARPS, int BIN>
 __global__ void __launch_bounds__(WARPS * 32, 4) k_move_group(MoveArgs a) {
   constexpr int kGroups = 32 / GS;
   constexpr int kSlots = 2 * GS * kRun;
-  static_assert(GS * kRun >= kGroupMaxDeg, "a group must hold a whole row");
+  static_assert(GS * kRun >= (BIN == kGroupBin ? kGroupMaxDeg : kHalfMaxDeg), "a group must hold a whole row");
   __shared__ int32_t skeys[WARPS * kGroups][kSlots];
   __shared__ uint32_t svals[WARPS * kGroups][kSlots];
   __shared__ uint16_t socc[WARPS * kGroups][kSlots / 2];
@@ -475,7 +476,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_move_group(MoveArgs a) {
   }
   if (gl == 0) *nocc = 0;
   __syncwarp();
-  const unsigned long long cnt = a.ctr->bin_count[kGroupBin];
+  const unsigned long long cnt = a.ctr->bin_count[BIN];
   unsigned long long glo = 0, ghi = 0, gm = 0;
   unsigned long long work[5] = {0, 0, 0, 0, 0};
   const unsigned long long stride = (unsigned long long)gridDim.x * WARPS * kGroups;
@@ -483,7 +484,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_move_group(MoveArgs a) {
        base += stride) {
     const unsigned long long idx = base + grp;
     const bool act = idx < cnt;
-    const int32_t i = act ? a.bins[kGroupBin][idx] : 0;
+    const int32_t i = act ? a.bins[BIN][idx] : 0;
     const int64_t b = act ? a.g.begin[i] : 0;
     const int64_t deg = act ? a.g.end[i] - b : 0;
     const int32_t d = act ? a.Cp[i] : 0;
@@ -559,7 +560,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_move_group(MoveArgs a) {
     __syncwarp();
   }
   flush_gains(glo, ghi, gm, a.ctr);
-  flush_work(work, a.ctr->mv_work[kGroupBin]);
+  flush_work(work, a.ctr->mv_work[BIN]);
 }
 
 // ---------------------------------------------------------------- block bins
@@ -864,14 +865,14 @@ template <int WK>
 __global__ void __launch_bounds__(256) k_pass_init(GView g, int first_pass, int64_t *K, int64_t *Sigma,
                                                    int32_t *Cp, uint8_t *flag, Counters *ctr, float4 *feat,
                                                    uint32_t *marks, uint32_t *marks_next, uint8_t *vbin,
-                                                   int group_max, int warp_max) {
+                                                   int group_max, int half_max, int warp_max) {
   unsigned long long md = 0, big_slots = 0, big_items = 0;
   const int lane = threadIdx.x & 31;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = g.begin[i], e = g.end[i];
     const unsigned long long deg = (unsigned long long)(e - b);
     if (deg > md) md = deg;
-    if (vbin) vbin[i] = deg > 0 ? (uint8_t)move_bin((int64_t)deg, group_max, warp_max) : (uint8_t)0xFF;
+    if (vbin) vbin[i] = deg > 0 ? (uint8_t)move_bin((int64_t)deg, group_max, half_max, warp_max) : (uint8_t)0xFF;
     if (deg > (unsigned long long)kClusterMaxDeg) {  // hubs of the global tables
       big_slots += big_table_cap(deg, (unsigned long long)g.n);
       big_items += 1;
@@ -954,7 +955,10 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
   LV_TIMED(prof, K_MOVE_THREAD, s1, k_move_thread<WK><<<num_sms * bk[0], 256, 0, s1>>>(a));
   if (a.sched.group_max > kThreadMaxDeg)
     LV_TIMED(prof, K_MOVE_GROUP, s2,
-             k_move_group<WK, kGroupLanes, 8><<<num_sms * bk[kGroupBin], 256, 0, s2>>>(a));
+             k_move_group<WK, kGroupLanes, 8, kGroupBin><<<num_sms * bk[kGroupBin], 256, 0, s2>>>(a));
+  if (a.sched.half_max > a.sched.group_max)
+    LV_TIMED(prof, K_MOVE_HALF, s2,
+             k_move_group<WK, kHalfLanes, 8, kHalfBin><<<num_sms * bk[kHalfBin], 256, 0, s2>>>(a));
   LV_TIMED(prof, K_MOVE_WARP, s2, k_move_warp<WK, 8><<<num_sms * bk[1], 256, 0, s2>>>(a));
   LV_TIMED(prof, K_MOVE_MID, s3, k_move_block<WK, 128, kMidCap, 2><<<num_sms * bk[2], 128, kMidSmem, s3>>>(a));
   LV_TIMED(prof, K_MOVE_BLOCK, s3,
@@ -983,6 +987,7 @@ void pass_init_t(const GView &g, int first, int64_t *K, int64_t *Sigma, int32_t 
   LV_LAUNCH(k_pass_init<WK><<<grid_for(g.n, 256, num_sms, 16), 256, 0, s>>>(g, first, K, Sigma, Cp, flag, ctr, feat,
                                                                              marks, marks_next, vbin,
                                                                              sched ? sched->group_max : 0,
+                                                                             sched ? sched->half_max : 0,
                                                                              sched ? sched->warp_max : 0));
 }
 
@@ -1011,6 +1016,6 @@ void iota_i32(int32_t *x, int64_t n, int num_sms, cudaStream_t s) {
 const char *const kKernelNames[K_NUM_KERNELS] = {
     "select", "move_thread", "move_warp", "move_mid", "move_block", "move_hub", "apply", "pass_init",
     "comm_count", "comm_scatter", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big",
-    "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit", "mlp_select", "move_group", "move_xl", "merge_xl", "move_cluster", "merge_group"};
+    "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit", "mlp_select", "move_group", "move_xl", "merge_xl", "move_cluster", "merge_group", "move_half"};
 
 }  // namespace lv

@@ -29,7 +29,7 @@ MODE_PLAIN, MODE_LEARNED = 0, 1
 KERNELS = ["select", "move_thread", "move_warp", "move_mid", "move_block", "move_hub", "apply", "pass_init",
            "comm_count", "comm_scatter", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big",
            "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit", "mlp_select", "move_group",
-           "move_xl", "merge_xl", "move_cluster", "merge_group"]
+           "move_xl", "merge_xl", "move_cluster", "merge_group", "move_half"]
 
 
 def kernel_mask(*names) -> int:
@@ -398,9 +398,11 @@ def louvain_batch_results(ctx, num_graphs: int, max_passes: int):
     return res, q, pr
 
 
-SCHEDULE_FIELDS = ["group_max", "warp_max", "move_thread", "move_warp", "move_mid", "move_block", "move_hub",
-                   "move_group", "move_xl", "move_cluster", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big",
-                   "merge_xl", "merge_group", "graphs", "concurrent"]
+SCHEDULE_FIELDS = ["group_max", "half_max", "warp_max",
+                   "move_thread", "move_warp", "move_mid", "move_block", "move_hub", "move_group", "move_xl",
+                   "move_cluster", "move_half",
+                   "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big", "merge_xl", "merge_group",
+                   "graphs", "concurrent"]
 
 
 def louvain_get_schedule(ctx) -> dict:

@@ -29,14 +29,15 @@ def check_single(g, res):
 
 
 SCHEDULES = [
-    dict(group_max=16),                                    # no group bin
-    dict(group_max=32, warp_max=64),                       # 65..1024 in 128-thread blocks
-    dict(group_max=48, warp_max=128),
+    dict(group_max=16, half_max=16),                       # no group bins
+    dict(group_max=32, half_max=32, warp_max=64),          # 65..1024 in 128-thread blocks
+    dict(group_max=48, half_max=128, warp_max=128),        # no warp bin
+    dict(group_max=64, half_max=96, warp_max=256),
     dict(move_thread=1, move_warp=1, move_mid=1, move_block=1, move_hub=1, move_group=1,
          merge_thread=1, merge_warp=1, merge_mid=1, merge_block=1, merge_big=1),
     dict(move_thread=16, move_warp=16, move_mid=16, move_block=16, move_group=16, merge_warp=16),
     dict(graphs=1),
-    dict(graphs=1, group_max=16, warp_max=64, move_hub=2),
+    dict(graphs=1, group_max=16, half_max=16, warp_max=64, move_hub=2),
     dict(concurrent=1),
     dict(concurrent=1, graphs=1),
 ]
@@ -104,6 +105,7 @@ def test_bad_schedules_refused():
     g = gg.rmat(10, 8, seed=1)
     with lv.Louvain(g) as ctx:
         for bad in (dict(group_max=8), dict(group_max=65), dict(group_max=64, warp_max=32), dict(warp_max=300),
+                    dict(half_max=200), dict(group_max=64, half_max=32),
                     dict(move_warp=0), dict(move_hub=4), dict(merge_big=5), dict(graphs=2), dict(move_thread=65),
                     dict(concurrent=3)):
             before = ctx.schedule()
