@@ -512,31 +512,42 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : NT == 512 ? 2 : 1) k_merge
 }
 
 // --------------------------------------------------------------- modularity
-// Warp per vertex: internal weight sum_{j in row(i), memb[j] == memb[i]} w_ij
-// (self-loop entries included) and, when sigma_out is given, the row sum
-// K_i added into sigma_out[memb[i]].
+// Groups of 8 lanes per vertex (4 vertices per warp): internal weight
+// sum_{j in row(i), memb[j] == memb[i]} w_ij (self-loop entries included)
+// and, when sigma_out is given, the row sum K_i added into
+// sigma_out[memb[i]].
 template <int WK>
 __global__ void __launch_bounds__(256) k_mod_rows(GView g, const int32_t *memb, int64_t *sigma_out, Counters *ctr) {
-  const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-  const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
-  const int lane = threadIdx.x & 31;
+  constexpr int GS = 8;
+  const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / GS;
+  const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / GS;
+  const int gl = threadIdx.x % GS;
   unsigned long long sin = 0;
-  for (int64_t i = warp; i < g.n; i += nw) {
-    const int32_t ci = memb[i];
+  // every lane of a warp runs the same number of rounds (shuffles below)
+  const int64_t rounds = (g.n + ngrp - 1) / ngrp;
+  for (int64_t r = 0; r < rounds; ++r) {
+    const int64_t i = grp + r * ngrp;
+    const bool act = i < g.n;
+    const int32_t ci = act ? memb[i] : 0;
     long long in = 0, k = 0;
-    for (int64_t e = g.begin[i] + lane; e < g.end[i]; e += 32) {
-      const long long w = load_w<WK>(g.w, e);
-      k += w;
-      if (memb[__ldg(g.col + e)] == ci) in += w;
+    if (act)
+      for (int64_t e = g.begin[i] + gl; e < g.end[i]; e += GS) {
+        const long long w = load_w<WK>(g.w, e);
+        k += w;
+        if (memb[__ldg(g.col + e)] == ci) in += w;
+      }
+#pragma unroll
+    for (int o = GS / 2; o > 0; o >>= 1) {
+      in += __shfl_xor_sync(0xFFFFFFFFu, in, o);
+      k += __shfl_xor_sync(0xFFFFFFFFu, k, o);
     }
-    in = warp_sum(in);
-    if (sigma_out) {
-      k = warp_sum(k);
-      if (lane == 0 && k) atomicAdd((unsigned long long *)(sigma_out + ci), as_ull(k));
+    if (act && gl == 0) {
+      if (sigma_out && k) atomicAdd((unsigned long long *)(sigma_out + ci), as_ull(k));
+      sin += (unsigned long long)in;
     }
-    sin += (unsigned long long)in;
   }
-  if (lane == 0 && sin) atomicAdd(&ctr->q_sin, sin);
+  sin = warp_sum_u(sin);
+  if ((threadIdx.x & 31) == 0 && sin) atomicAdd(&ctr->q_sin, sin);
 }
 
 __global__ void __launch_bounds__(256) k_sigma_sq(const int64_t *sigma, int64_t n, Counters *ctr) {
@@ -608,7 +619,7 @@ void merge_t(const AggArgs &a, int num_sms, cudaStream_t s, KernelProf *prof, co
 
 template <int WK>
 void mod_rows_t(const GView &g, const int32_t *memb, int64_t *sigma_out, Counters *ctr, int num_sms, cudaStream_t s) {
-  LV_LAUNCH(k_mod_rows<WK><<<grid_for(g.n * 32, 256, num_sms, 16), 256, 0, s>>>(g, memb, sigma_out, ctr));
+  LV_LAUNCH(k_mod_rows<WK><<<grid_for(g.n * 8, 256, num_sms, 16), 256, 0, s>>>(g, memb, sigma_out, ctr));
 }
 
 }  // namespace

@@ -190,27 +190,32 @@ void release_pool_threshold(int device) {
 
 // Warp per row: offsets non-decreasing, columns in range, weights positive;
 // the weight total 2m goes to ctr->q_sin.
-__global__ void k_validate(int64_t n, const int64_t *off, const int32_t *col, const int32_t *w, Counters *ctr) {
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  unsigned long long bad = 0, wsum = 0;
-  for (int64_t i = warp; i < n; i += nw) {
-    const int64_t b = off[i], e = off[i + 1];
-    if (e < b) {
-      bad = 1;
-      continue;
-    }
-    for (int64_t k = b + lane; k < e; k += 32) {
-      const int32_t c = col[k];
-      if (c < 0 || c >= n) bad = 1;
-      const int32_t ww = w ? w[k] : 1;
-      if (ww <= 0) bad = 1;
-      wsum += (unsigned long long)(ww > 0 ? ww : 0);
-    }
+// Input validation: offsets non-decreasing (thread per row), then every
+// entry's column in [0, n) and weight > 0, with the weights summed into 2m
+// (thread per entry, coalesced); per-warp reductions before the atomics.
+__global__ void k_validate_rows(int64_t n, const int64_t *off, Counters *ctr) {
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    if (off[i + 1] < off[i]) bad = true;
+  if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(&ctr->error, (unsigned long long)ERR_RANGE);
+}
+
+__global__ void k_validate_entries(int64_t nnz, int64_t n, const int32_t *col, const int32_t *w, Counters *ctr) {
+  bool bad = false;
+  unsigned long long wsum = 0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = col[k];
+    if (c < 0 || c >= n) bad = true;
+    const int32_t ww = w ? w[k] : 1;
+    if (ww <= 0) bad = true;
+    wsum += (unsigned long long)(ww > 0 ? ww : 0);
   }
-  if (bad) atomicOr(&ctr->error, (unsigned long long)ERR_RANGE);
-  if (wsum) atomicAdd(&ctr->q_sin, wsum);
+  wsum = warp_sum_u(wsum);
+  const bool any_bad = __any_sync(0xFFFFFFFFu, bad);
+  if ((threadIdx.x & 31) == 0) {
+    if (any_bad) atomicOr(&ctr->error, (unsigned long long)ERR_RANGE);
+    if (wsum) atomicAdd(&ctr->q_sin, wsum);
+  }
 }
 
 void dfree(louvain_ctx *x, void *p) {
@@ -1200,8 +1205,10 @@ louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg
   if (cudaMemsetAsync(x->d_ctr, 0, sizeof(Counters), x->stream)) return fail(LOUVAIN_E_CUDA);
   // validation and 2m
   if (n > 0) {
-    int grid = (int)std::min<int64_t>((n * 32 + 255) / 256, (int64_t)x->num_sms * 16);
-    LV_LAUNCH(k_validate<<<grid, 256, 0, x->stream>>>(n, x->off0, x->col0, x->w0, x->d_ctr));
+    LV_LAUNCH(k_validate_rows<<<grid_for(n, 256, x->num_sms, 8), 256, 0, x->stream>>>(n, x->off0, x->d_ctr));
+    if (nnz > 0)
+      LV_LAUNCH(k_validate_entries<<<grid_for(nnz, 256, x->num_sms, 8), 256, 0, x->stream>>>(nnz, n, x->col0, x->w0,
+                                                                                            x->d_ctr));
     if (cudaGetLastError() != cudaSuccess) {
       set_err(x, "validation kernel failed to launch");
       return fail(LOUVAIN_E_CUDA);

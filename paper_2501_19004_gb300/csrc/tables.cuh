@@ -117,28 +117,6 @@ __device__ __forceinline__ void warp_insert_sm(int32_t *keys, uint32_t *vals, ui
   }
 }
 
-// warp_insert_sm with the occupied list of sm_insert_list.
-__device__ __forceinline__ void warp_insert_sm_list(int32_t *keys, uint32_t *vals, uint32_t mask, int32_t key,
-                                                    uint32_t w, uint16_t *occ, unsigned *nocc, Counters *ctr) {
-  const unsigned full = 0xFFFFFFFFu;
-  const int lane = threadIdx.x & 31;
-  const unsigned peers = __match_any_sync(full, key);
-  const bool lead = lane == __ffs(peers) - 1;
-  const unsigned leaders = __ballot_sync(full, lead && key != kEmpty);
-  if (__popc(leaders) <= 4) {
-    unsigned todo = leaders;
-    while (todo) {
-      const int src = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const int32_t k0 = __shfl_sync(full, key, src);
-      const uint32_t sum = __reduce_add_sync(full, key == k0 ? w : 0u);
-      if (lane == src) sm_insert_list(keys, vals, mask, k0, sum, occ, nocc, ctr);
-    }
-  } else if (key != kEmpty) {
-    sm_insert_list(keys, vals, mask, key, w, occ, nocc, ctr);
-  }
-}
-
 // Block-level exclusive scan of one int64 per thread (NT threads); returns
 // the exclusive prefix and the block total in *total.  Uses `scratch`
 // (NT/32 + 1 words of shared memory).
