@@ -37,8 +37,7 @@ enum ErrBits : unsigned long long { ERR_HASH = 1ull, ERR_RANGE = 2ull, ERR_TIMEO
 
 // Small device-resident counters block.
 struct Counters {
-  unsigned long long bin_count[8];  // local-moving bin sizes of the current bucket
-  unsigned long long selected;      // vertices taken into the bucket (incl. degree 0)
+  unsigned long long bin_count[9];  // local-moving bin sizes of the current bucket (one per move bin)
   unsigned long long movers;        // decisions to move in this bucket
   // ---- zeroed every iteration ----
   unsigned long long it_gain_lo;    // sum of low 32 bits of the gains

@@ -50,6 +50,7 @@ constexpr int kHalfLanes = 16;
 constexpr int kHalfMaxDeg = 128;
 constexpr int kHalfBin = 8;
 constexpr int kMoveBins = 9;
+static_assert(sizeof(Counters::bin_count) == kMoveBins * sizeof(unsigned long long), "one counter per move bin");
 // Aggregation bins: degree_bin's five plus communities with a total member
 // degree in (4096, kXlMaxDeg] for one 1024-thread block (bin 5) and in
 // (16, kGroupMaxDeg] for groups of kGroupLanes lanes (bin 6).

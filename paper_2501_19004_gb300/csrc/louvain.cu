@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <array>
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -513,7 +514,7 @@ louvain_status enqueue_iteration(louvain_ctx *x, const GView &g, int wk, int pas
     big.iter = iter;
     big.static_rounds = iter != nullptr;
     for (int b = 0; b < cfg.buckets; ++b) {
-      LV_CK(cudaMemsetAsync(x->d_ctr, 0, 10 * sizeof(unsigned long long), x->stream));
+      LV_CK(cudaMemsetAsync(x->d_ctr, 0, offsetof(Counters, it_gain_lo), x->stream));
       if (L.enabled) LV_CK(cudaMemsetAsync(&x->d_ctr->cand_count, 0, sizeof(unsigned long long), x->stream));
       a.bucket = (uint32_t)b;
       move_bucket(a, big, wk, x->num_sms, x->stream, x->prof.mask ? &x->prof : nullptr,
