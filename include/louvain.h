@@ -131,6 +131,49 @@ louvain_status louvain_create(const louvain_graph *graph, const louvain_config *
  * context's stream; returns when the result is ready. */
 louvain_status louvain_run(louvain_ctx *ctx);
 
+/* Pass-level control and checkpoints of a single-graph run (Algorithm 1's
+ * pass loop; a pass is one local-moving phase plus one aggregation).
+ *
+ * louvain_run_passes starts a run like louvain_run but, when
+ * max_new_passes > 0 and the run still has a pass to do after that many
+ * passes, stops between two passes: *suspended = 1 (may be NULL), and the
+ * context holds the dendrogram, the super-vertex graph, its vertex weights,
+ * the tolerance of the next pass and the records of the passes done.
+ * Otherwise the run finishes (*suspended = 0) exactly as louvain_run.
+ * louvain_resume continues a suspended run the same way (max_new_passes <= 0:
+ * to the end); LOUVAIN_E_STATE if the context is not suspended.  A suspended
+ * run gives no results yet (LOUVAIN_E_STATE from louvain_modularity and the
+ * other result calls).  Stopping and resuming never changes results: the
+ * memberships, the exact modularity and the per-pass and per-iteration
+ * records equal those of an uninterrupted run.  louvain_stats then times
+ * only the passes run in this context since the last start or load.
+ * Batched contexts: LOUVAIN_E_INVAL. */
+louvain_status louvain_run_passes(louvain_ctx *ctx, int32_t max_new_passes, int32_t *suspended);
+louvain_status louvain_resume(louvain_ctx *ctx, int32_t max_new_passes, int32_t *suspended);
+
+/* Checkpoint of a suspended run into a caller-owned host buffer (8-byte
+ * aligned, at least *size bytes; buf = NULL only reports *size).  Layout,
+ * native byte order: a header of 20 int64 words (magic "LVCKPT01", sizes, an
+ * FNV-1a checksum of the payload, the input graph's n, nnz, 2m and weight
+ * kind, a fingerprint of every setting that decides results, the next pass,
+ * tau and the run totals), then the records of the passes done, C[n] int32,
+ * K[n'] int64 and the super-vertex graph as a compact CSR (offsets[n'+1]
+ * int64, cols[nnz'] int32, weights[nnz'] uint32).  LOUVAIN_E_STATE if the
+ * context is not suspended; LOUVAIN_E_INVAL for a short or unaligned buffer. */
+louvain_status louvain_save_state(const louvain_ctx *ctx, void *buf, size_t cap, size_t *size);
+
+/* Restore a checkpoint into a context created on the same input graph with
+ * the same result-deciding settings (and model, in learned mode); the
+ * context is then suspended and louvain_resume continues the run.  Any
+ * previous results of the context are dropped, also when the checkpoint is
+ * refused.  It is refused (LOUVAIN_E_INVAL, nothing suspended; the context
+ * stays usable for louvain_run) when its magic, size or checksum is
+ * wrong, when it was taken on another graph or configuration, or when its
+ * rows, dendrogram ids, vertex weights or entries are out of range (entries
+ * are checked on the device: columns in [0, n'), weights > 0, their sum
+ * 2m).  Recorded traces are not part of a checkpoint. */
+louvain_status louvain_load_state(louvain_ctx *ctx, const void *buf, size_t size);
+
 /* Final modularity Q (Eq. 1) of the last run, as a double, and optionally
  * its exact numerator 2m*S_in - sum_c Sigma_c^2 and denominator (2m)^2 as
  * (hi, lo) pairs of a 128-bit integer (either pointer may be NULL). */

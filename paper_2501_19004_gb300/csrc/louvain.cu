@@ -33,7 +33,19 @@ thread_local long long g_launches = 0;
 
 struct PassTiming {
   cudaEvent_t t0, t1, t2;  // pass start, after local moving, after aggregation
+  bool timed;              // t0 and t1 were recorded (false for passes restored from a checkpoint)
   bool aggregated;
+};
+
+// Where a run stands between two passes: what louvain_run_passes leaves for
+// louvain_resume, and what a checkpoint holds besides the per-vertex arrays.
+struct RunState {
+  GView g{};          // current (super-)vertex graph
+  int wk = 0;         // its weight kind
+  int slot = 0;       // ping-pong buffer the next aggregation writes
+  int next_pass = 0;  // index of the next pass (= passes completed)
+  int64_t nnzp = 0;   // entries of g
+  double tau = 0;     // tolerance of the next pass
 };
 
 struct louvain_ctx {
@@ -86,6 +98,9 @@ struct louvain_ctx {
 
   // results of the last run
   bool ran = false;
+  bool suspended = false;  // a run stopped between two passes (louvain_run_passes, louvain_load_state)
+  RunState rs;
+  uint64_t model_hash = 0; // of the learned predictor's parameters (checkpoint compatibility)
   double q = 0;
   i128 qnum = 0, qden = 0;
   int64_t gamma = 0;
@@ -201,15 +216,19 @@ __global__ void k_validate_rows(int64_t n, const int64_t *off, Counters *ctr) {
   if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(&ctr->error, (unsigned long long)ERR_RANGE);
 }
 
-__global__ void k_validate_entries(int64_t nnz, int64_t n, const int32_t *col, const int32_t *w, Counters *ctr) {
+// Entries of a CSR (input int32 weights, or the uint32 weights of a
+// super-vertex graph restored from a checkpoint): column in [0, n), weight
+// > 0; the weights are summed into ctr->q_sin.
+template <typename WT>
+__global__ void k_validate_entries(int64_t nnz, int64_t n, const int32_t *col, const WT *w, Counters *ctr) {
   bool bad = false;
   unsigned long long wsum = 0;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x) {
     const int32_t c = col[k];
     if (c < 0 || c >= n) bad = true;
-    const int32_t ww = w ? w[k] : 1;
-    if (ww <= 0) bad = true;
-    wsum += (unsigned long long)(ww > 0 ? ww : 0);
+    const WT ww = w ? w[k] : WT(1);
+    if (ww <= WT(0)) bad = true;
+    wsum += (unsigned long long)(ww > WT(0) ? ww : WT(0));
   }
   wsum = warp_sum_u(wsum);
   const bool any_bad = __any_sync(0xFFFFFFFFu, bad);
@@ -314,6 +333,17 @@ louvain_status read_counters(louvain_ctx *x) {
     return LOUVAIN_E_HASH_OVERFLOW;
   }
   return LOUVAIN_OK;
+}
+
+// FNV-1a (Fowler, Noll, Vo), 64-bit, over bytes: fingerprints of
+// checkpoint payloads, configurations and model parameters.
+uint64_t fnv1a_bytes(const void *p, size_t n, uint64_t h = 0xcbf29ce484222325ull) {
+  const unsigned char *b = static_cast<const unsigned char *>(p);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 0x100000001b3ull;
+  }
+  return h;
 }
 
 void put128(int64_t *dst, i128 v) {
@@ -647,7 +677,7 @@ louvain_status begin_run(louvain_ctx *x) {
     x->kbytes[k] = 0;
   }
   x->prof.used = 0;
-  for (auto &pt : x->timing) pt.aggregated = false;
+  for (auto &pt : x->timing) pt.timed = pt.aggregated = false;
   LV_CK(cudaEventRecord(x->run0, s));
   LV_CK(cudaMemsetAsync(x->d_ctr, 0, sizeof(Counters), s));
   return LOUVAIN_OK;
@@ -739,28 +769,59 @@ louvain_status aggregate(louvain_ctx *x, AggArgs &aa, int64_t gamma, PassTiming 
   return LOUVAIN_OK;
 }
 
-louvain_status run_impl(louvain_ctx *x) {
+// Runs passes of Algorithm 1 from the start (fresh) or from where a
+// suspended run stopped.  With budget > 0, a run that still has a pass to do
+// after `budget` passes stops between two passes (*suspended = 1) and keeps
+// its state for louvain_resume and louvain_save_state.
+louvain_status run_impl(louvain_ctx *x, bool fresh = true, int32_t budget = 0, int32_t *suspended = nullptr) {
   const louvain_config &cfg = x->cfg;
   cudaStream_t s = x->stream;
   louvain_status st;
   const long long launches0 = g_launches;
-  if ((st = begin_run(x))) return st;
-
-  GView g{x->n0, x->off0, x->off0 + 1, x->col0, x->w0};
-  int wk = x->weighted ? W_U32 : W_UNIT;
+  if (suspended) *suspended = 0;
+  RunState &rs = x->rs;
+  if (fresh) {
+    x->suspended = false;
+    x->launches = 0;
+    if ((st = begin_run(x))) return st;
+    rs.g = GView{x->n0, x->off0, x->off0 + 1, x->col0, x->w0};
+    rs.wk = x->weighted ? W_U32 : W_UNIT;
+    rs.slot = 0;
+    rs.next_pass = 0;
+    rs.nnzp = x->nnz0;
+    rs.tau = cfg.tolerance;
+    iota_i32(x->C, x->n0, x->num_sms, s);
+  } else {
+    if (!x->suspended) return LOUVAIN_E_STATE;
+    x->suspended = false;
+    x->graph_pass = -1;
+    x->graph_broken = false;
+    LV_CK(cudaEventRecord(x->run0, s));
+  }
   if (x->big_dirty && x->big.slots > 0) {  // a failed run may have left table entries behind
     LV_CK(cudaMemsetAsync(x->big.tab, 0, (size_t)x->big.slots * sizeof(unsigned long long), s));
   }
   x->big_dirty = true;
-  iota_i32(x->C, x->n0, x->num_sms, s);
-  double tau = cfg.tolerance;
+  GView g = rs.g;
+  int wk = rs.wk;
+  double tau = rs.tau;
   bool pending = false, exhausted = true;
-  int exit_reason = 0, passes = 0, slot = 0;
-  int64_t nnzp = x->nnz0;
+  int exit_reason = 0, passes = rs.next_pass, slot = rs.slot;
+  int64_t nnzp = rs.nnzp;
   bool have_pass_state = false;
-  for (int p = 0; p < cfg.max_passes; ++p) {
+  for (int p = rs.next_pass; p < cfg.max_passes; ++p) {
+    if (budget > 0 && p - rs.next_pass == budget) {  // stop between two passes
+      rs = RunState{g, wk, slot, p, nnzp, tau};
+      LV_CK(cudaStreamSynchronize(s));
+      x->launches += g_launches - launches0;
+      x->big_dirty = false;
+      x->suspended = true;
+      if (suspended) *suspended = 1;
+      return LOUVAIN_OK;
+    }
     PassTiming &pt = x->timing[p];
     LV_CK(cudaEventRecord(pt.t0, s));
+    pt.timed = true;
     LV_CK(cudaMemsetAsync(&x->d_ctr->maxdeg, 0, sizeof(unsigned long long), s));
     x->cur_wbytes = wk == W_UNIT ? 0 : 4;
     LV_CK(cudaMemsetAsync(&x->d_ctr->big_slots, 0, 2 * sizeof(unsigned long long), s));
@@ -847,7 +908,7 @@ louvain_status run_impl(louvain_ctx *x) {
   float ms = 0;
   LV_CK(cudaEventElapsedTime(&ms, x->run0, x->run1));
   x->run_ms = ms;
-  x->launches = g_launches - launches0;
+  x->launches += g_launches - launches0;
   x->big_dirty = false;
   x->ran = true;
   return LOUVAIN_OK;
@@ -927,6 +988,7 @@ louvain_status run_batched(louvain_ctx *x) {
   for (int p = 0; p < cfg.max_passes && alive_count > 0; ++p) {
     PassTiming &pt = x->timing[p];
     LV_CK(cudaEventRecord(pt.t0, s));
+    pt.timed = true;
     LV_CK(cudaMemsetAsync(&x->d_ctr->maxdeg, 0, sizeof(unsigned long long), s));
     x->cur_wbytes = wk == W_UNIT ? 0 : 4;
     LV_CK(cudaMemsetAsync(&x->d_ctr->big_slots, 0, 2 * sizeof(unsigned long long), s));
@@ -1208,7 +1270,7 @@ louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg
   if (n > 0) {
     LV_LAUNCH(k_validate_rows<<<grid_for(n, 256, x->num_sms, 8), 256, 0, x->stream>>>(n, x->off0, x->d_ctr));
     if (nnz > 0)
-      LV_LAUNCH(k_validate_entries<<<grid_for(nnz, 256, x->num_sms, 8), 256, 0, x->stream>>>(nnz, n, x->col0, x->w0,
+      LV_LAUNCH(k_validate_entries<int32_t><<<grid_for(nnz, 256, x->num_sms, 8), 256, 0, x->stream>>>(nnz, n, x->col0, x->w0,
                                                                                             x->d_ctr));
     if (cudaGetLastError() != cudaSuccess) {
       set_err(x, "validation kernel failed to launch");
@@ -1275,6 +1337,7 @@ louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg
       set_err(x, "copy of the model parameters failed");
       return fail(LOUVAIN_E_CUDA);
     }
+    x->model_hash = fnv1a_bytes(cfg->model, sizeof(float) * kMlpParams);
   }
   if (cfg->trace_capacity > 0) {
     if ((st = dalloc_n(x, &x->trace_x, cfg->trace_capacity * kFeatures)) ||
@@ -1456,6 +1519,271 @@ louvain_status louvain_run(louvain_ctx *x) {
   return st;
 }
 
+louvain_status louvain_run_passes(louvain_ctx *x, int32_t max_new_passes, int32_t *suspended) {
+  if (!x || x->batched) return LOUVAIN_E_INVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != x->device) cudaSetDevice(x->device);
+  louvain_status st = run_impl(x, true, max_new_passes, suspended);
+  if (st != LOUVAIN_OK) x->ran = x->suspended = false;
+  return st;
+}
+
+louvain_status louvain_resume(louvain_ctx *x, int32_t max_new_passes, int32_t *suspended) {
+  if (!x || x->batched) return LOUVAIN_E_INVAL;
+  if (!x->suspended) return LOUVAIN_E_STATE;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != x->device) cudaSetDevice(x->device);
+  louvain_status st = run_impl(x, false, max_new_passes, suspended);
+  if (st != LOUVAIN_OK) x->ran = x->suspended = false;
+  return st;
+}
+
+namespace {
+
+// Checkpoint layout: kCkptHeader int64 words, then the payload sections,
+// each padded to 8 bytes (native byte order; the magic's bytes fail to match
+// in the other order).
+const char kCkptMagic[8] = {'L', 'V', 'C', 'K', 'P', 'T', '0', '1'};
+constexpr int64_t kCkptHeader = 20;
+enum CkptWord {
+  CK_MAGIC = 0, CK_HEADER, CK_BYTES, CK_SUM, CK_N0, CK_NNZ0, CK_TWO_M, CK_WEIGHTED, CK_CONFIG, CK_PASS, CK_N, CK_NNZ,
+  CK_TAU, CK_IT_TOTAL, CK_MOVES, CK_EVALUATED, CK_SKIPPED, CK_LEARNED_LOG
+};
+
+size_t pad8(size_t b) { return (b + 7) & ~(size_t)7; }
+
+size_t ckpt_bytes(int64_t P, int64_t T, int64_t L, int64_t n0, int64_t n, int64_t nnz) {
+  return 8 * (size_t)kCkptHeader + 8 * (size_t)(P * 6 + P * T * 4 + L * 3) + pad8(4 * (size_t)n0) +
+         8 * (size_t)n + 8 * (size_t)(n + 1) + 2 * pad8(4 * (size_t)nnz);
+}
+
+// FNV-1a with 64-bit words as its symbols (the byte-wise constants, eight
+// bytes per step): the payload checksum.
+uint64_t fnv1a_words(const uint64_t *w, size_t n) {
+  uint64_t h = 0xcbf29ce484222325ull;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= w[i];
+    h *= 0x100000001b3ull;
+  }
+  return h;
+}
+
+// Every setting that decides the remaining passes' results or the records.
+uint64_t config_fingerprint(const louvain_ctx *x) {
+  const louvain_config &c = x->cfg;
+  const bool learned = c.mode == LOUVAIN_MODE_LEARNED;
+  int64_t f[14] = {};
+  f[0] = c.max_passes;
+  f[1] = c.max_iterations;
+  memcpy(&f[2], &c.tolerance, 8);
+  memcpy(&f[3], &c.tolerance_drop, 8);
+  memcpy(&f[4], &c.aggregation_tolerance, 8);
+  f[5] = c.pickless_period;
+  f[6] = c.buckets;
+  f[7] = (int64_t)c.schedule_seed;
+  f[8] = c.mode;
+  f[9] = c.record_pass_modularity;
+  if (learned) {
+    memcpy(&f[10], &c.skip_threshold, 4);
+    f[11] = c.learned_fallback;
+    f[12] = c.learned_skip_clears;
+    f[13] = (int64_t)x->model_hash;
+  }
+  return fnv1a_bytes(f, sizeof f);
+}
+
+}  // namespace
+
+louvain_status louvain_save_state(const louvain_ctx *xc, void *buf, size_t cap, size_t *size) {
+  louvain_ctx *x = const_cast<louvain_ctx *>(xc);
+  if (!x || x->batched) return LOUVAIN_E_INVAL;
+  if (!x->suspended) return LOUVAIN_E_STATE;
+  const RunState &rs = x->rs;
+  const int64_t P = rs.next_pass, T = x->cfg.max_iterations, L = (int64_t)x->learned_log.size();
+  const int64_t n = rs.g.n, nnz = rs.nnzp;
+  const size_t need = ckpt_bytes(P, T, L, x->n0, n, nnz);
+  if (size) *size = need;
+  if (!buf) return LOUVAIN_OK;
+  if (cap < need || ((uintptr_t)buf & 7)) {
+    set_err(x, "checkpoint buffer must be 8-byte aligned and hold %zu bytes", need);
+    return LOUVAIN_E_INVAL;
+  }
+  cudaStream_t s = x->stream;
+  char *base = static_cast<char *>(buf);
+  memset(base, 0, need);
+  int64_t *h = reinterpret_cast<int64_t *>(base);
+  memcpy(h, kCkptMagic, 8);
+  h[CK_HEADER] = kCkptHeader;
+  h[CK_BYTES] = (int64_t)need;
+  h[CK_N0] = x->n0;
+  h[CK_NNZ0] = x->nnz0;
+  h[CK_TWO_M] = x->two_m;
+  h[CK_WEIGHTED] = x->weighted;
+  h[CK_CONFIG] = (int64_t)config_fingerprint(x);
+  h[CK_PASS] = P;
+  h[CK_N] = n;
+  h[CK_NNZ] = nnz;
+  memcpy(&h[CK_TAU], &rs.tau, 8);
+  h[CK_IT_TOTAL] = x->it_total;
+  h[CK_MOVES] = x->moves_total;
+  h[CK_EVALUATED] = x->evaluated_total;
+  h[CK_SKIPPED] = x->skipped_total;
+  h[CK_LEARNED_LOG] = L;
+  char *q = base + 8 * kCkptHeader;
+  memcpy(q, x->pass_stats.data(), (size_t)P * 6 * 8);
+  q += (size_t)P * 6 * 8;
+  memcpy(q, x->iter_stats.data(), (size_t)P * T * 4 * 8);
+  q += (size_t)P * T * 4 * 8;
+  for (int64_t k = 0; k < L; ++k, q += 24) memcpy(q, x->learned_log[k].data(), 24);
+  // dendrogram C[n0] and the super-vertex degrees K[n]
+  if (x->n0) LV_CK(cudaMemcpyAsync(q, x->C, (size_t)x->n0 * 4, cudaMemcpyDeviceToHost, s));
+  q += pad8((size_t)x->n0 * 4);
+  if (n) LV_CK(cudaMemcpyAsync(q, x->K, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+  q += (size_t)n * 8;
+  // the super-vertex graph, compacted: its rows sit at the prefix of their
+  // capacity bounds in the ping-pong buffer
+  std::vector<int64_t> b((size_t)n), e((size_t)n);
+  if (n) {
+    LV_CK(cudaMemcpyAsync(b.data(), rs.g.begin, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+    LV_CK(cudaMemcpyAsync(e.data(), rs.g.end, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+  }
+  LV_CK(cudaStreamSynchronize(s));
+  int64_t *off = reinterpret_cast<int64_t *>(q);
+  int64_t lo = INT64_MAX, hi = 0;
+  off[0] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    off[i + 1] = off[i] + (e[i] - b[i]);
+    if (e[i] > b[i]) {
+      lo = std::min(lo, b[i]);
+      hi = std::max(hi, e[i]);
+    }
+  }
+  if (off[n] != nnz) {
+    set_err(x, "suspended graph holds %lld entries, expected %lld", (long long)off[n], (long long)nnz);
+    return LOUVAIN_E_STATE;
+  }
+  q += (size_t)(n + 1) * 8;
+  int32_t *cols = reinterpret_cast<int32_t *>(q);
+  uint32_t *wts = reinterpret_cast<uint32_t *>(q + pad8((size_t)nnz * 4));
+  if (nnz) {
+    std::vector<int32_t> sc((size_t)(hi - lo));
+    std::vector<uint32_t> sw((size_t)(hi - lo));
+    LV_CK(cudaMemcpyAsync(sc.data(), rs.g.col + lo, (size_t)(hi - lo) * 4, cudaMemcpyDeviceToHost, s));
+    LV_CK(cudaMemcpyAsync(sw.data(), static_cast<const uint32_t *>(rs.g.w) + lo, (size_t)(hi - lo) * 4,
+                          cudaMemcpyDeviceToHost, s));
+    LV_CK(cudaStreamSynchronize(s));
+    for (int64_t i = 0; i < n; ++i) {
+      const int64_t len = e[i] - b[i];
+      if (len <= 0) continue;
+      memcpy(cols + off[i], sc.data() + (b[i] - lo), (size_t)len * 4);
+      memcpy(wts + off[i], sw.data() + (b[i] - lo), (size_t)len * 4);
+    }
+  }
+  h[CK_SUM] = (int64_t)fnv1a_words(reinterpret_cast<const uint64_t *>(base + 8 * kCkptHeader),
+                                   (need - 8 * kCkptHeader) / 8);
+  return LOUVAIN_OK;
+}
+
+louvain_status louvain_load_state(louvain_ctx *x, const void *buf, size_t size) {
+  if (!x || x->batched || !buf || ((uintptr_t)buf & 7) || size < 8 * (size_t)kCkptHeader) return LOUVAIN_E_INVAL;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != x->device) cudaSetDevice(x->device);
+  const char *base = static_cast<const char *>(buf);
+  const int64_t *h = reinterpret_cast<const int64_t *>(base);
+  const louvain_config &cfg = x->cfg;
+  auto refuse = [&](const char *why) {
+    set_err(x, "checkpoint refused: %s", why);
+    return LOUVAIN_E_INVAL;
+  };
+  x->ran = x->suspended = false;  // a refused checkpoint leaves neither results nor a suspended run
+  if (memcmp(h, kCkptMagic, 8) || h[CK_HEADER] != kCkptHeader || h[CK_BYTES] != (int64_t)size)
+    return refuse("not a checkpoint of this format, or truncated");
+  if (h[CK_N0] != x->n0 || h[CK_NNZ0] != x->nnz0 || h[CK_TWO_M] != x->two_m || h[CK_WEIGHTED] != x->weighted)
+    return refuse("taken on another input graph");
+  if ((uint64_t)h[CK_CONFIG] != config_fingerprint(x)) return refuse("taken with another configuration or model");
+  const int64_t P = h[CK_PASS], n = h[CK_N], nnz = h[CK_NNZ], L = h[CK_LEARNED_LOG], T = cfg.max_iterations;
+  if (P < 1 || P >= cfg.max_passes || n < 1 || n > x->n0 || nnz < 0 || nnz > x->nnz0 || L < 0 || L > P)
+    return refuse("sizes out of range");
+  if (ckpt_bytes(P, T, L, x->n0, n, nnz) != size) return refuse("size does not match its header");
+  if ((uint64_t)h[CK_SUM] !=
+      fnv1a_words(reinterpret_cast<const uint64_t *>(base + 8 * kCkptHeader), (size - 8 * kCkptHeader) / 8))
+    return refuse("checksum mismatch");
+  double tau;
+  memcpy(&tau, &h[CK_TAU], 8);
+  if (!(tau >= 0) || !std::isfinite(tau)) return refuse("tolerance out of range");
+  const char *q = base + 8 * kCkptHeader;
+  const int64_t *pass_stats = reinterpret_cast<const int64_t *>(q);
+  q += (size_t)P * 6 * 8;
+  const int64_t *iter_stats = reinterpret_cast<const int64_t *>(q);
+  q += (size_t)P * T * 4 * 8;
+  const int64_t *llog = reinterpret_cast<const int64_t *>(q);
+  q += (size_t)L * 24;
+  const int32_t *C = reinterpret_cast<const int32_t *>(q);
+  q += pad8((size_t)x->n0 * 4);
+  const int64_t *K = reinterpret_cast<const int64_t *>(q);
+  q += (size_t)n * 8;
+  const int64_t *off = reinterpret_cast<const int64_t *>(q);
+  q += (size_t)(n + 1) * 8;
+  const int32_t *cols = reinterpret_cast<const int32_t *>(q);
+  const uint32_t *wts = reinterpret_cast<const uint32_t *>(q + pad8((size_t)nnz * 4));
+  // host checks: rows, dendrogram ids and degrees
+  if (off[0] != 0 || off[n] != nnz) return refuse("row offsets do not span the entries");
+  for (int64_t i = 0; i < n; ++i)
+    if (off[i + 1] < off[i]) return refuse("decreasing row offsets");
+  for (int64_t v = 0; v < x->n0; ++v)
+    if (C[v] < 0 || C[v] >= n) return refuse("dendrogram id out of range");
+  long long ksum = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (K[i] < 0 || K[i] > x->two_m) return refuse("vertex weight out of range");
+    ksum += K[i];
+  }
+  if (ksum != x->two_m) return refuse("vertex weights do not sum to 2m");
+  // restore into slot 0 of the ping-pong buffers, then check the entries
+  cudaStream_t s = x->stream;
+  LV_CK(cudaMemcpyAsync(x->C, C, (size_t)x->n0 * 4, cudaMemcpyHostToDevice, s));
+  LV_CK(cudaMemcpyAsync(x->K, K, (size_t)n * 8, cudaMemcpyHostToDevice, s));
+  LV_CK(cudaMemcpyAsync(x->pbeg[0], off, (size_t)n * 8, cudaMemcpyHostToDevice, s));
+  LV_CK(cudaMemcpyAsync(x->pend[0], off + 1, (size_t)n * 8, cudaMemcpyHostToDevice, s));
+  if (nnz) {
+    LV_CK(cudaMemcpyAsync(x->pcol[0], cols, (size_t)nnz * 4, cudaMemcpyHostToDevice, s));
+    LV_CK(cudaMemcpyAsync(x->pw[0], wts, (size_t)nnz * 4, cudaMemcpyHostToDevice, s));
+  }
+  LV_CK(cudaMemsetAsync(x->d_ctr, 0, sizeof(Counters), s));
+  if (nnz)
+    LV_LAUNCH(k_validate_entries<uint32_t><<<grid_for(nnz, 256, x->num_sms, 8), 256, 0, s>>>(nnz, n, x->pcol[0],
+                                                                                          x->pw[0], x->d_ctr));
+  LV_CK(cudaGetLastError());
+  LV_CK(cudaMemcpyAsync(x->h_ctr, x->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+  LV_CK(cudaStreamSynchronize(s));
+  if ((x->h_ctr->error & ERR_RANGE) || (long long)x->h_ctr->q_sin != x->two_m)
+    return refuse("entries out of range, or weights that do not sum to 2m");
+  LV_CK(cudaMemsetAsync(x->d_ctr, 0, sizeof(Counters), s));
+  // records of the passes done, and the state the next pass starts from
+  x->iter_stats.assign((size_t)cfg.max_passes * T * 4, 0);
+  x->pass_stats.assign((size_t)cfg.max_passes * 6, 0);
+  memcpy(x->pass_stats.data(), pass_stats, (size_t)P * 6 * 8);
+  memcpy(x->iter_stats.data(), iter_stats, (size_t)P * T * 4 * 8);
+  x->learned_log.assign((size_t)L, {});
+  for (int64_t k = 0; k < L; ++k) memcpy(x->learned_log[k].data(), llog + 3 * k, 24);
+  x->it_total = h[CK_IT_TOTAL];
+  x->moves_total = h[CK_MOVES];
+  x->evaluated_total = h[CK_EVALUATED];
+  x->skipped_total = h[CK_SKIPPED];
+  for (int k = 0; k < K_NUM_KERNELS; ++k) {
+    x->prof.ms[k] = 0;
+    x->prof.launches[k] = 0;
+    x->kbytes[k] = 0;
+  }
+  x->prof.used = 0;
+  for (auto &pt : x->timing) pt.timed = pt.aggregated = false;
+  x->launches = 0;
+  x->graph_pass = -1;
+  x->graph_broken = false;
+  x->rs = RunState{GView{n, x->pbeg[0], x->pend[0], x->pcol[0], x->pw[0]}, W_U32, 1, (int)P, nnz, tau};
+  x->suspended = true;
+  return LOUVAIN_OK;
+}
+
 louvain_status louvain_modularity(const louvain_ctx *x, double *q, int64_t *num, int64_t *den) {
   if (!x || x->batched) return LOUVAIN_E_INVAL;  // a batch reports per graph (louvain_batch_results)
   if (!x->ran) return LOUVAIN_E_STATE;
@@ -1512,7 +1840,7 @@ louvain_status louvain_stats(const louvain_ctx *xc, char *json, size_t cap) {
   std::string per = "\"per_pass\": [";
   for (int p = 0; p < x->passes; ++p) {
     float a = 0, b = 0;
-    cudaEventElapsedTime(&a, x->timing[p].t0, x->timing[p].t1);
+    if (x->timing[p].timed) cudaEventElapsedTime(&a, x->timing[p].t0, x->timing[p].t1);
     if (x->timing[p].aggregated) cudaEventElapsedTime(&b, x->timing[p].t1, x->timing[p].t2);
     tm += a;
     ta += b;

@@ -85,6 +85,14 @@ def load(path: Optional[str] = None):
     lib.louvain_create.argtypes = [P(LouvainGraph), P(LouvainConfig), vp, P(vp)]
     lib.louvain_run.restype = ctypes.c_int
     lib.louvain_run.argtypes = [vp]
+    lib.louvain_run_passes.restype = ctypes.c_int
+    lib.louvain_run_passes.argtypes = [vp, i32, P(i32)]
+    lib.louvain_resume.restype = ctypes.c_int
+    lib.louvain_resume.argtypes = [vp, i32, P(i32)]
+    lib.louvain_save_state.restype = ctypes.c_int
+    lib.louvain_save_state.argtypes = [vp, vp, ctypes.c_size_t, P(ctypes.c_size_t)]
+    lib.louvain_load_state.restype = ctypes.c_int
+    lib.louvain_load_state.argtypes = [vp, vp, ctypes.c_size_t]
     lib.louvain_modularity.restype = ctypes.c_int
     lib.louvain_modularity.argtypes = [vp, P(ctypes.c_double), vp, vp]
     lib.louvain_memberships.restype = ctypes.c_int
@@ -249,6 +257,38 @@ def louvain_create(graph, cfg: Optional[Config] = None, stream=None) -> ctypes.c
 
 def louvain_run(ctx):
     _check(load().louvain_run(ctx), ctx)
+
+
+def louvain_run_passes(ctx, max_new_passes: int) -> bool:
+    """Start a run; True if it stopped between two passes after
+    ``max_new_passes`` passes (0 = run to the end)."""
+    sus = ctypes.c_int32()
+    _check(load().louvain_run_passes(ctx, int(max_new_passes), ctypes.byref(sus)), ctx)
+    return bool(sus.value)
+
+
+def louvain_resume(ctx, max_new_passes: int = 0) -> bool:
+    """Continue a suspended run; True if it stopped again."""
+    sus = ctypes.c_int32()
+    _check(load().louvain_resume(ctx, int(max_new_passes), ctypes.byref(sus)), ctx)
+    return bool(sus.value)
+
+
+def louvain_save_state(ctx) -> np.ndarray:
+    """Checkpoint of a suspended run as a uint8 array (host)."""
+    size = ctypes.c_size_t()
+    _check(load().louvain_save_state(ctx, None, 0, ctypes.byref(size)), ctx)
+    buf = np.zeros((size.value + 7) // 8, dtype=np.int64).view(np.uint8)[:size.value]
+    _check(load().louvain_save_state(ctx, buf.ctypes.data, size.value, ctypes.byref(size)), ctx)
+    return buf
+
+
+def louvain_load_state(ctx, buf) -> None:
+    """Restore a checkpoint (bytes or a uint8 array) into ``ctx``."""
+    raw = np.frombuffer(bytes(buf), dtype=np.uint8) if not isinstance(buf, np.ndarray) else buf.view(np.uint8)
+    if raw.ctypes.data % 8:
+        raw = np.frombuffer(raw.tobytes(), dtype=np.uint8)  # fresh bytes objects are 8-byte aligned
+    _check(load().louvain_load_state(ctx, raw.ctypes.data, raw.nbytes), ctx)
 
 
 def louvain_modularity(ctx):
@@ -470,6 +510,21 @@ class Louvain:
 
     def run(self):
         louvain_run(self.ctx)
+        return self
+
+    def run_passes(self, max_new_passes: int) -> bool:
+        """Start a run that stops between two passes after ``max_new_passes``
+        passes; True if it stopped (False: finished)."""
+        return louvain_run_passes(self.ctx, max_new_passes)
+
+    def resume(self, max_new_passes: int = 0) -> bool:
+        return louvain_resume(self.ctx, max_new_passes)
+
+    def save_state(self) -> np.ndarray:
+        return louvain_save_state(self.ctx)
+
+    def load_state(self, buf):
+        louvain_load_state(self.ctx, buf)
         return self
 
     def result(self) -> Result:
