@@ -197,6 +197,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-skip leg")
+    ap.add_argument("--no-async", action="store_true", help="skip the asynchronous-form leg")
     ap.add_argument("--skip-threshold", type=float, default=0.8)
     ap.add_argument("--skip-clears", type=int, default=1)
     ap.add_argument("--learned-fallback", type=int, default=0)
@@ -321,6 +322,32 @@ def main():
                    "passes_max": int(res.summary[:, 0].max()), "graphs": int(vo.shape[0] - 1)}
     else:
         summary = {"modularity": res.modularity, "communities": res.communities, "passes": res.passes}
+    def timed_leg(cfg):
+        """Warm-up and timed runs of another configuration on the same graph
+        and schedule; returns (ms for all timed steps, result, stats)."""
+        c = lv.Louvain(dg, cfg)
+        if sched:
+            c.set_schedule(sched)
+        for _ in range(args.warmup):
+            c.run()
+        torch.cuda.synchronize()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            c.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([t_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_ms = float(t.item())
+        r, s_ = c.result(), c.stats()
+        c.close()
+        return t_ms, r, s_
+
     if not args.no_learned and not batch:
         from paper_2501_19004_gb300 import predictor
         model = predictor.load_default()
@@ -328,36 +355,25 @@ def main():
         if model is None:
             model, _ = predictor.train_default()
             source = "trained in this run (R-MAT 20-22 traces)"
-        lctx = lv.Louvain(dg, lv.Config(mode=lv.MODE_LEARNED, model=model, skip_threshold=args.skip_threshold,
-                                        learned_skip_clears=args.skip_clears,
-                                        learned_fallback=args.learned_fallback))
-        if sched:
-            lctx.set_schedule(sched)
-        for _ in range(args.warmup):
-            lctx.run()
-        torch.cuda.synchronize()
-        barrier()
-        l0 = torch.cuda.Event(enable_timing=True)
-        l1 = torch.cuda.Event(enable_timing=True)
-        l0.record(stream)
-        for _ in range(args.steps):
-            lctx.run()
-        l1.record(stream)
-        torch.cuda.synchronize()
-        lms = l0.elapsed_time(l1)
-        if world > 1:
-            t = torch.tensor([lms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            lms = float(t.item())
-        lres = lctx.result()
-        lst = lctx.stats()
-        lctx.close()
+        lms, lres, lst = timed_leg(lv.Config(mode=lv.MODE_LEARNED, model=model, skip_threshold=args.skip_threshold,
+                                             learned_skip_clears=args.skip_clears,
+                                             learned_fallback=args.learned_fallback))
         learned = {"value": g.nnz * args.steps * world / (lms / 1e3) / 1e6, "unit": UNIT,
                    "ms_per_step": lms / args.steps, "modularity": lres.modularity,
                    "dq_vs_plain": lres.modularity - res.modularity, "skip_threshold": args.skip_threshold,
                    "skip_clears": args.skip_clears, "fallback": args.learned_fallback,
                    "evaluated": lst["evaluated"], "evaluated_plain": st["evaluated"], "skipped": lst["skipped"],
                    "passes": lres.passes, "learned_passes": lst.get("learned_passes"), "model": source}
+
+    # asynchronous form (moves applied at their decision; not reproducible)
+    asynchronous = None
+    if not args.no_async and not batch:
+        ams, ares, ast = timed_leg(lv.Config(asynchronous=True))
+        asynchronous = {"value": g.nnz * args.steps * world / (ams / 1e3) / 1e6, "unit": UNIT,
+                        "ms_per_step": ams / args.steps, "modularity": ares.modularity,
+                        "dq_vs_plain": ares.modularity - res.modularity, "passes": ares.passes,
+                        "iterations": ast["iterations"], "evaluated": ast["evaluated"],
+                        "evaluated_plain": st["evaluated"], "communities": ares.communities}
 
     # end to end through the public API from pinned host memory
     e2e = None
@@ -457,7 +473,7 @@ def main():
                        "l2": f"inputs larger than L2 (CSR {(g.offsets.nbytes + g.cols.nbytes) / 1e9:.2f} GB), no flush",
                        **summary},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
-            "learned_skip": learned, "sequential": sequential, "autotune": tune,
+            "learned_skip": learned, "asynchronous": asynchronous, "sequential": sequential, "autotune": tune,
             "phases_ms": {"move": st["move_ms"], "aggregate": st["aggregate_ms"], "other": st["other_ms"]},
             "kernels_ms_warmup": {k: round(v["ms"], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
         }

@@ -115,6 +115,17 @@ typedef struct {
                                     this many 8-byte slots (at least the largest
                                     table); 0 = half of the pass's bound on their
                                     total size.  Results do not depend on it. */
+  int32_t asynchronous;          /* 1: the asynchronous form of the paper's GPU
+                                    algorithm (Algorithm 5 as written, Sec. 4.3):
+                                    each iteration is one sweep over all unprocessed
+                                    vertices, and every move is applied the moment
+                                    it is decided (C'[i] and Sigma' by atomics), so
+                                    later decisions of the sweep see it.  Results
+                                    then depend on thread timing and are not
+                                    reproducible; buckets and schedule_seed are
+                                    ignored.  Plain mode, no traces, single graphs
+                                    only (LOUVAIN_E_INVAL otherwise).  0: the
+                                    deterministic bucket schedule. */
 } louvain_config;
 
 /* Fill `cfg` with the defaults above (mode PLAIN, seed 0). */

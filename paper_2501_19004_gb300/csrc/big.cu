@@ -371,8 +371,7 @@ __global__ void __launch_bounds__(kNT) k_big_decide(BigArgs a, int r) {
         work[1] += 1;
         work[2] += (unsigned long long)(e - b);
         const unsigned long long pos = atomicAdd(&a.ctr->movers, 1ull);
-        a.mv_vertex[pos] = i;
-        a.mv_target[pos] = t;
+        emit_move(a.async_apply, a.apply_Cp, a.K, a.apply_Sigma, a.mv_vertex, a.mv_target, pos, i, t);
       }
       s_target = t;
     }

@@ -158,6 +158,27 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 __device__ __forceinline__ unsigned long long as_ull(long long v) { return (unsigned long long)v; }
 
+// A decision to move vertex i to community c.  Deterministic schedule: onto
+// the mover list at pos, applied by k_apply after all decisions of the
+// bucket.  Asynchronous form: applied at once (C'[i], then Sigma' of the old
+// and the new community by 64-bit atomics), so that decisions made later in
+// the same sweep see it.  A vertex is decided once per sweep, so no other
+// thread writes C'[i] meanwhile.
+__device__ __forceinline__ void emit_move(int async_apply, int32_t *Cp, const int64_t *K, int64_t *Sigma,
+                                          int32_t *mv_vertex, int32_t *mv_target, unsigned long long pos,
+                                          int32_t i, int32_t c) {
+  if (async_apply) {
+    const int32_t d = Cp[i];
+    const long long Ki = K[i];
+    Cp[i] = c;
+    atomicAdd((unsigned long long *)(Sigma + d), as_ull(-Ki));
+    atomicAdd((unsigned long long *)(Sigma + c), as_ull(Ki));
+  } else {
+    mv_vertex[pos] = i;
+    mv_target[pos] = c;
+  }
+}
+
 // Exact accumulation of non-negative 64-bit gains into two 64-bit sums
 // (low and high 32-bit halves), reduced per warp before the global atomics.
 __device__ __forceinline__ void flush_gains(unsigned long long lo, unsigned long long hi,

@@ -198,6 +198,9 @@ struct BigArgs {
   int pickless;
   int32_t *mv_vertex;
   int32_t *mv_target;
+  int async_apply = 0;                // asynchronous form: apply each move at its decision (emit_move)
+  int32_t *apply_Cp = nullptr;        //   C' and Sigma' those moves write
+  int64_t *apply_Sigma = nullptr;
   LearnArgs learn;
   BatchView batch;
   const uint32_t *iter = nullptr;     // graph replay: device words {salt, pickless} of the iteration
@@ -251,6 +254,7 @@ struct MoveArgs {
   Sched sched;
   const uint32_t *iter = nullptr;  // graph replay: device words {salt, pickless} of the iteration
   const uint8_t *vbin = nullptr;   // [n'] move bin of every vertex this pass (0xFF: degree 0)
+  int async_apply = 0;             // asynchronous form: movers apply their move at once (emit_move)
 };
 
 // Kernel identifiers for the optional per-kernel event timing.

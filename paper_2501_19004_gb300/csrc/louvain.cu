@@ -508,7 +508,9 @@ louvain_status enqueue_iteration(louvain_ctx *x, const GView &g, int wk, int pas
     a.two_m = x->two_m;
     a.pickless = pickless;
     a.salt = bucket_salt(pass, t, cfg.schedule_seed);
-    a.nbuckets = (uint32_t)cfg.buckets;
+    const int nbuckets = cfg.asynchronous ? 1 : cfg.buckets;  // the asynchronous form sweeps all vertices at once
+    a.nbuckets = (uint32_t)nbuckets;
+    a.async_apply = cfg.asynchronous;
     for (int k = 0; k < kMoveBins; ++k) a.bins[k] = x->bins[k];
     a.mv_vertex = x->mv_vertex;
     a.mv_target = x->mv_target;
@@ -538,12 +540,15 @@ louvain_status enqueue_iteration(louvain_ctx *x, const GView &g, int wk, int pas
     big.pickless = pickless;
     big.mv_vertex = x->mv_vertex;
     big.mv_target = x->mv_target;
+    big.async_apply = cfg.asynchronous;
+    big.apply_Cp = x->Cp;
+    big.apply_Sigma = x->Sigma;
     big.learn = L;
     big.batch = x->bview;
     big.accum_blocks = x->sched.move[kBigBin];
     big.iter = iter;
     big.static_rounds = iter != nullptr;
-    for (int b = 0; b < cfg.buckets; ++b) {
+    for (int b = 0; b < nbuckets; ++b) {
       LV_CK(cudaMemsetAsync(x->d_ctr, 0, offsetof(Counters, it_gain_lo), x->stream));
       if (L.enabled) LV_CK(cudaMemsetAsync(&x->d_ctr->cand_count, 0, sizeof(unsigned long long), x->stream));
       a.bucket = (uint32_t)b;
@@ -1160,6 +1165,8 @@ louvain_status validate_config(const louvain_config *c) {
   if (c->mode == LOUVAIN_MODE_LEARNED && (!c->model || c->max_iterations > 127)) return LOUVAIN_E_INVAL;
   if (c->trace_capacity < 0 || c->learned_fallback < 0 || c->learned_fallback > 2) return LOUVAIN_E_INVAL;
   if (c->table_window < 0) return LOUVAIN_E_INVAL;
+  if (c->asynchronous != 0 && c->asynchronous != 1) return LOUVAIN_E_INVAL;
+  if (c->asynchronous && (c->mode != LOUVAIN_MODE_PLAIN || c->trace_capacity > 0)) return LOUVAIN_E_INVAL;
   return LOUVAIN_OK;
 }
 
@@ -1460,6 +1467,7 @@ void louvain_config_default(louvain_config *c) {
   c->learned_fallback = 0;
   c->learned_skip_clears = 0;
   c->table_window = 0;
+  c->asynchronous = 0;
 }
 
 louvain_status louvain_create(const louvain_graph *graph, const louvain_config *cfg, void *stream, louvain_ctx **out) {
@@ -1475,8 +1483,8 @@ louvain_status louvain_create_batched(const louvain_graph *graph, const int64_t 
     set_err(nullptr, "null argument or bad number of graphs");
     return LOUVAIN_E_INVAL;
   }
-  if (cfg->mode != LOUVAIN_MODE_PLAIN || cfg->trace_capacity != 0) {
-    set_err(nullptr, "batched runs use the plain mode without traces");
+  if (cfg->mode != LOUVAIN_MODE_PLAIN || cfg->trace_capacity != 0 || cfg->asynchronous) {
+    set_err(nullptr, "batched runs use the plain mode without traces, on the deterministic schedule");
     return LOUVAIN_E_INVAL;
   }
   if (vertex_offsets[0] != 0 || vertex_offsets[num_graphs] != graph->n) {
@@ -1572,7 +1580,7 @@ uint64_t fnv1a_words(const uint64_t *w, size_t n) {
 uint64_t config_fingerprint(const louvain_ctx *x) {
   const louvain_config &c = x->cfg;
   const bool learned = c.mode == LOUVAIN_MODE_LEARNED;
-  int64_t f[14] = {};
+  int64_t f[15] = {};
   f[0] = c.max_passes;
   f[1] = c.max_iterations;
   memcpy(&f[2], &c.tolerance, 8);
@@ -1583,6 +1591,7 @@ uint64_t config_fingerprint(const louvain_ctx *x) {
   f[7] = (int64_t)c.schedule_seed;
   f[8] = c.mode;
   f[9] = c.record_pass_modularity;
+  f[14] = c.asynchronous;
   if (learned) {
     memcpy(&f[10], &c.skip_threshold, 4);
     f[11] = c.learned_fallback;

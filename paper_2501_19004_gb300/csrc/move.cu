@@ -320,10 +320,7 @@ __global__ void __launch_bounds__(256) k_move_thread(MoveArgs a) {
       unsigned long long pos = 0;
       if (lane == leader) pos = atomicAdd(&a.ctr->movers, (unsigned long long)__popc(mask));
       pos = __shfl_sync(kFull, pos, leader) + __popc(mask & lanemask_lt());
-      if (mv) {
-        a.mv_vertex[pos] = i;
-        a.mv_target[pos] = target;
-      }
+      if (mv) emit_move(a.async_apply, a.Cp, a.K, a.Sigma, a.mv_vertex, a.mv_target, pos, i, target);
     }
   }
   flush_gains(glo, ghi, gm, a.ctr);
@@ -428,8 +425,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_move_warp(MoveArgs a) {
         work[3] += 1;
         work[4] += (unsigned long long)deg;
         const unsigned long long pos = atomicAdd(&a.ctr->movers, 1ull);
-        a.mv_vertex[pos] = i;
-        a.mv_target[pos] = target;
+        emit_move(a.async_apply, a.Cp, a.K, a.Sigma, a.mv_vertex, a.mv_target, pos, i, target);
       }
     }
     target = __shfl_sync(kFull, target, 0);
@@ -543,10 +539,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_move_group(MoveArgs a) {
       unsigned long long pos = 0;
       if (lane == leader) pos = atomicAdd(&a.ctr->movers, (unsigned long long)__popc(mmask));
       pos = __shfl_sync(kFull, pos, leader) + __popc(mmask & lanemask_lt());
-      if (target >= 0) {
-        a.mv_vertex[pos] = i;
-        a.mv_target[pos] = target;
-      }
+      if (target >= 0) emit_move(a.async_apply, a.Cp, a.K, a.Sigma, a.mv_vertex, a.mv_target, pos, i, target);
     }
     target = __shfl_sync(kFull, target, grp * GS);
     if (target >= 0)
@@ -635,8 +628,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : NT == 512 ? 2 : 1) k_move_
         work[3] += 1;
         work[4] += (unsigned long long)deg;
         const unsigned long long pos = atomicAdd(&a.ctr->movers, 1ull);
-        a.mv_vertex[pos] = i;
-        a.mv_target[pos] = t;
+        emit_move(a.async_apply, a.Cp, a.K, a.Sigma, a.mv_vertex, a.mv_target, pos, i, t);
       }
       s_target = t;
       s_nocc = 0;  // every thread read it before block_argmax_sum's barriers
@@ -824,8 +816,7 @@ __global__ void __cluster_dims__(kClusterSize, 1, 1) __launch_bounds__(1024, 1) 
         work[3] += 1;
         work[4] += (unsigned long long)deg;
         const unsigned long long pos = atomicAdd(&a.ctr->movers, 1ull);
-        a.mv_vertex[pos] = i;
-        a.mv_target[pos] = t;
+        emit_move(a.async_apply, a.Cp, a.K, a.Sigma, a.mv_vertex, a.mv_target, pos, i, t);
       }
       for (int r = 0; r < kClusterSize; ++r) cl.map_shared_rank(&s_target, r)[0] = t;
     }
@@ -975,7 +966,7 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
       cudaEventRecord(side->join[k], side->s[k]);
       cudaStreamWaitEvent(s, side->join[k], 0);
     }
-  LV_TIMED(prof, K_APPLY, s, k_apply<<<num_sms * 4, 256, 0, s>>>(a));
+  if (!a.async_apply) LV_TIMED(prof, K_APPLY, s, k_apply<<<num_sms * 4, 256, 0, s>>>(a));
 }
 
 template <int WK>

@@ -398,3 +398,20 @@ def test_pickless_and_bucket_settings_change_the_run_but_not_validity():
         r = oracle.louvain(g, cfg)
         assert abs(r.modularity - base.modularity) < 0.05
         assert set(np.unique(r.membership)) == set(range(r.communities))
+
+
+def test_fully_simultaneous_decisions_collapse_a_mixed_sbm():
+    """Why the schedule has buckets: with one bucket every vertex decides
+    against the same snapshot, and on a planted partition with heavy mixing
+    (about 45% of each vertex's edges leave its block) the moves that each
+    raise modularity alone pile onto the same communities and swap back and
+    forth (the community swaps of Sec. 4.3.1): the second pass hits the
+    iteration cap and modularity falls to well under half.  Two or four
+    buckets, where later decisions see earlier moves, stay near the planted
+    partition's modularity."""
+    g = gg.sbm(3000, 50, 0.3, 0.004, seed=4)
+    one = oracle.louvain(g, oracle.Config(buckets=1))
+    assert one.modularity < 0.3
+    assert int(one.pass_stats[1, 2]) == oracle.Config().max_iterations
+    for B in (2, 4):
+        assert oracle.louvain(g, oracle.Config(buckets=B)).modularity > 0.52
