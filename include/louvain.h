@@ -23,6 +23,8 @@
  * the bucket are applied and the neighbours of movers are marked
  * unprocessed (vertex pruning, Sec. 4.1.6).  An iteration ends the phase when
  * 2 * sum(gains) / (2m)^2 <= tau.  All of this is exact integer arithmetic.
+ * louvain_config.asynchronous = 1 selects the paper's own asynchronous form
+ * instead (moves applied in place as they are decided; not reproducible).
  *
  * Conventions for every function below:
  *   - A status code is returned; nothing aborts, exits or traps.  On error,
@@ -232,21 +234,21 @@ louvain_status louvain_set_profile(louvain_ctx *ctx, uint32_t profile_mask);
  *       graph captured once per pass (plain mode, no profiling);
  *   [20] concurrent: 1 = a bucket's bin kernels (and an aggregation's) run at
  *       the same time on side streams of the context.
- * Results never depend on the schedule: every bin computes the same exact
- * decisions.  The schedule belongs to the context and is used by its next
- * runs. */
+ * Results of the deterministic form never depend on the schedule: every bin
+ * computes the same exact decisions.  The schedule belongs to the context
+ * and is used by its next runs. */
 int32_t louvain_schedule_words(void);
 louvain_status louvain_get_schedule(const louvain_ctx *ctx, int32_t *words, int32_t n);
 louvain_status louvain_set_schedule(louvain_ctx *ctx, const int32_t *words, int32_t n);
 
 /* Choose the context's schedule by timed runs of its own graph (at most
- * max_runs trials; a whole-run trial is the faster of two runs): bin
- * thresholds by whole-run time, blocks per SM of
- * every bin by per-kernel CUDA-event time, then graph replay on or off.  The
- * tuned schedule is kept only if it beats the starting one (the last steps
- * try concurrent bin kernels and graph replay on and off).  json (may be
- * NULL) receives {"runs", "start_ms", "tuned_ms", "schedule", "trials"}.  The
- * context holds a valid result of the chosen schedule afterwards. */
+ * max_runs trials; a whole-run trial is the faster of two runs), in order:
+ * the bin thresholds by whole-run time; the blocks per SM of every bin by
+ * per-kernel CUDA-event time; concurrent bin kernels on or off; graph replay
+ * on or off.  The tuned schedule is kept only if it beats the starting one.
+ * json (may be NULL) receives {"runs", "start_ms", "tuned_ms", "schedule",
+ * "trials"}.  The context holds a valid result of the chosen schedule
+ * afterwards. */
 louvain_status louvain_autotune(louvain_ctx *ctx, int32_t max_runs, char *json, size_t cap);
 
 /* Release all device memory of the context (stream-ordered). */
