@@ -115,6 +115,7 @@ struct louvain_ctx {
   KernelProf prof;
   std::vector<cudaEvent_t> prof_events;
   double kbytes[K_NUM_KERNELS] = {};
+  double kunits[K_NUM_KERNELS][2] = {};  // work per kernel group: vertices (or communities), entries
   int cur_wbytes = 0;
   bool pass_has_hubs = false;
   int64_t hub_window = 0;
@@ -365,17 +366,22 @@ void account_move(louvain_ctx *x, int64_t n, const Counters &h) {
     if (b == kBigBin) {  // entries in the accumulation kernel, the rest in evaluation
       x->kbytes[K_MOVE_HUB] += (8.0 + wb) * w[1];
       x->kbytes[K_MOVE_HUB_EVAL] += 40.0 * w[0] + 8.0 * w[2] + 8.0 * w[3] + 1.0 * w[4];
+      x->kunits[K_MOVE_HUB][0] += (double)w[0];
+      x->kunits[K_MOVE_HUB][1] += (double)w[1];
       continue;
     }
-    x->kbytes[b == kGroupBin     ? K_MOVE_GROUP
-              : b == kXlBin      ? K_MOVE_XL
-              : b == kClusterBin ? K_MOVE_CLUSTER
-              : b == kHalfBin    ? K_MOVE_HALF
-                                 : K_MOVE_THREAD + b] +=
-        40.0 * w[0] + (8.0 + wb) * w[1] + 8.0 * w[2] + 8.0 * w[3] + 1.0 * w[4];
+    const int kid = b == kGroupBin     ? K_MOVE_GROUP
+                    : b == kXlBin      ? K_MOVE_XL
+                    : b == kClusterBin ? K_MOVE_CLUSTER
+                    : b == kHalfBin    ? K_MOVE_HALF
+                                       : K_MOVE_THREAD + b;
+    x->kbytes[kid] += 40.0 * w[0] + (8.0 + wb) * w[1] + 8.0 * w[2] + 8.0 * w[3] + 1.0 * w[4];
+    x->kunits[kid][0] += (double)w[0];
+    x->kunits[kid][1] += (double)w[1];
   }
-  x->kbytes[K_SELECT] += (double)x->cfg.buckets * n + 21.0 * h.it_evaluated;
-  x->kbytes[K_APPLY] += 40.0 * h.it_moves;
+  const int nbuckets = x->cfg.asynchronous ? 1 : x->cfg.buckets;
+  x->kbytes[K_SELECT] += (double)nbuckets * n + 21.0 * h.it_evaluated;
+  if (!x->cfg.asynchronous) x->kbytes[K_APPLY] += 40.0 * h.it_moves;  // the asynchronous form applies in place
 }
 
 // Aggregation kernels: per community: member offset/count 12, row bounds 16,
@@ -389,10 +395,14 @@ void account_merge(louvain_ctx *x, const Counters &h) {
     if (b == kBigBin) {
       x->kbytes[K_MERGE_BIG] += 20.0 * w[1] + (8.0 + wb) * w[2];
       x->kbytes[K_MERGE_BIG_EMIT] += 36.0 * w[0] + 8.0 * w[3];
+      x->kunits[K_MERGE_BIG][0] += (double)w[0];
+      x->kunits[K_MERGE_BIG][1] += (double)w[2];
       continue;
     }
-    x->kbytes[b == kMergeXlBin ? K_MERGE_XL : b == kMergeGroupBin ? K_MERGE_GROUP : K_MERGE_THREAD + b] +=
-        36.0 * w[0] + 20.0 * w[1] + (8.0 + wb) * w[2] + 8.0 * w[3];
+    const int kid = b == kMergeXlBin ? K_MERGE_XL : b == kMergeGroupBin ? K_MERGE_GROUP : K_MERGE_THREAD + b;
+    x->kbytes[kid] += 36.0 * w[0] + 20.0 * w[1] + (8.0 + wb) * w[2] + 8.0 * w[3];
+    x->kunits[kid][0] += (double)w[0];
+    x->kunits[kid][1] += (double)w[2];
   }
 }
 
@@ -680,6 +690,7 @@ louvain_status begin_run(louvain_ctx *x) {
     x->prof.ms[k] = 0;
     x->prof.launches[k] = 0;
     x->kbytes[k] = 0;
+    x->kunits[k][0] = x->kunits[k][1] = 0;
   }
   x->prof.used = 0;
   for (auto &pt : x->timing) pt.timed = pt.aggregated = false;
@@ -1782,6 +1793,7 @@ louvain_status louvain_load_state(louvain_ctx *x, const void *buf, size_t size) 
     x->prof.ms[k] = 0;
     x->prof.launches[k] = 0;
     x->kbytes[k] = 0;
+    x->kunits[k][0] = x->kunits[k][1] = 0;
   }
   x->prof.used = 0;
   for (auto &pt : x->timing) pt.timed = pt.aggregated = false;
@@ -1873,8 +1885,10 @@ louvain_status louvain_stats(const louvain_ctx *xc, char *json, size_t cap) {
   bool first = true;
   for (int k = 0; k < K_NUM_KERNELS; ++k) {
     if (x->prof.launches[k] == 0 && x->kbytes[k] == 0) continue;
-    snprintf(buf, sizeof buf, "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"bytes\": %.0f}", first ? "" : ", ",
-             kKernelNames[k], x->prof.launches[k], x->prof.ms[k], x->kbytes[k]);
+    snprintf(buf, sizeof buf,
+             "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"bytes\": %.0f, \"vertices\": %.0f, \"entries\": %.0f}",
+             first ? "" : ", ", kKernelNames[k], x->prof.launches[k], x->prof.ms[k], x->kbytes[k], x->kunits[k][0],
+             x->kunits[k][1]);
     s += buf;
     first = false;
   }
