@@ -315,6 +315,35 @@ def main():
             serial = {"achieved": k["bytes"] / (k["ms"] / 1e3) / 1e9, "avg_launch_ms": k["ms"] / max(k["launches"], 1),
                       "launches": k["launches"]}
 
+    # end to end through the public API from pinned host memory
+    e2e = None
+    if args.e2e_steps > 0:
+        off_p = torch.from_numpy(g.offsets).pin_memory()
+        col_p = torch.from_numpy(g.cols).pin_memory()
+        host = gg.CSR(off_p.numpy(), col_p.numpy(), None)
+        memb_p = torch.empty(g.n, dtype=torch.int32).pin_memory()
+        ctx.close()
+        with new_ctx(host) as c2:  # warm the allocator pool
+            c2.run()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            with new_ctx(host) as c2:
+                c2.run()
+                lv.louvain_memberships(c2.ctx, memb_p.numpy())
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": g.nnz * args.e2e_steps * world / dt / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(g.offsets.nbytes + g.cols.nbytes),
+               "d2h_bytes_per_step": int(g.n * 4), "steps": args.e2e_steps}
+    else:
+        ctx.close()
+
     # learned-skip leg: the same workload and step count with the predictor
     learned = None
     if batch:
@@ -374,35 +403,6 @@ def main():
                         "dq_vs_plain": ares.modularity - res.modularity, "passes": ares.passes,
                         "iterations": ast["iterations"], "evaluated": ast["evaluated"],
                         "evaluated_plain": st["evaluated"], "communities": ares.communities}
-
-    # end to end through the public API from pinned host memory
-    e2e = None
-    if args.e2e_steps > 0:
-        off_p = torch.from_numpy(g.offsets).pin_memory()
-        col_p = torch.from_numpy(g.cols).pin_memory()
-        host = gg.CSR(off_p.numpy(), col_p.numpy(), None)
-        memb_p = torch.empty(g.n, dtype=torch.int32).pin_memory()
-        ctx.close()
-        with new_ctx(host) as c2:  # warm the allocator pool
-            c2.run()
-        torch.cuda.synchronize()
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            with new_ctx(host) as c2:
-                c2.run()
-                lv.louvain_memberships(c2.ctx, memb_p.numpy())
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": g.nnz * args.e2e_steps * world / dt / 1e6, "unit": UNIT,
-               "h2d_bytes_per_step": int(g.offsets.nbytes + g.cols.nbytes),
-               "d2h_bytes_per_step": int(g.n * 4), "steps": args.e2e_steps}
-    else:
-        ctx.close()
 
     peaks, src = load_peaks()
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else None
