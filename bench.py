@@ -166,6 +166,24 @@ def oracle_steps(gs, steps: int, warmup: int):
     return dt, oracle.num_threads()
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest x over all ranks (the slowest rank's time), by one
+    all-reduce; x itself on a single rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, steps: int, world: int, seconds: float) -> float:
+    """Whole-job M units/s: every rank processed units_per_rank in each of
+    `steps` steps, and the job took as long as its slowest rank."""
+    return units_per_rank * steps * world / seconds / 1e6
+
+
 def run_reference(args, wname):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -297,13 +315,10 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     res = ctx.result()
     st = ctx.stats()
-    value = g.nnz * args.steps * world / (ms / 1e3) / 1e6
+    value = job_rate(g.nnz, args.steps, world, ms / 1e3)
     # the dominant kernel once more with the bins serialised (untimed run)
     serial = None
     if run_sched.get("concurrent"):
@@ -333,12 +348,8 @@ def main():
                 c2.run()
                 lv.louvain_memberships(c2.ctx, memb_p.numpy())
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": g.nnz * args.e2e_steps * world / dt / 1e6, "unit": UNIT,
+        dt = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e = {"value": job_rate(g.nnz, args.e2e_steps, world, dt), "unit": UNIT,
                "h2d_bytes_per_step": int(g.offsets.nbytes + g.cols.nbytes),
                "d2h_bytes_per_step": int(g.n * 4), "steps": args.e2e_steps}
     else:
@@ -368,11 +379,7 @@ def main():
             c.run()
         e1.record(stream)
         torch.cuda.synchronize()
-        t_ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([t_ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_ms = float(t.item())
+        t_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
         r, s_ = c.result(), c.stats()
         c.close()
         return t_ms, r, s_
@@ -387,7 +394,7 @@ def main():
         lms, lres, lst = timed_leg(lv.Config(mode=lv.MODE_LEARNED, model=model, skip_threshold=args.skip_threshold,
                                              learned_skip_clears=args.skip_clears,
                                              learned_fallback=args.learned_fallback))
-        learned = {"value": g.nnz * args.steps * world / (lms / 1e3) / 1e6, "unit": UNIT,
+        learned = {"value": job_rate(g.nnz, args.steps, world, lms / 1e3), "unit": UNIT,
                    "ms_per_step": lms / args.steps, "modularity": lres.modularity,
                    "dq_vs_plain": lres.modularity - res.modularity, "skip_threshold": args.skip_threshold,
                    "skip_clears": args.skip_clears, "fallback": args.learned_fallback,
@@ -398,7 +405,7 @@ def main():
     asynchronous = None
     if not args.no_async and not batch:
         ams, ares, ast = timed_leg(lv.Config(asynchronous=True))
-        asynchronous = {"value": g.nnz * args.steps * world / (ams / 1e3) / 1e6, "unit": UNIT,
+        asynchronous = {"value": job_rate(g.nnz, args.steps, world, ams / 1e3), "unit": UNIT,
                         "ms_per_step": ams / args.steps, "modularity": ares.modularity,
                         "dq_vs_plain": ares.modularity - res.modularity, "passes": ares.passes,
                         "iterations": ast["iterations"], "evaluated": ast["evaluated"],

@@ -286,7 +286,10 @@ def louvain_save_state(ctx) -> np.ndarray:
 
 def louvain_load_state(ctx, buf) -> None:
     """Restore a checkpoint (bytes or a uint8 array) into ``ctx``."""
-    raw = np.frombuffer(bytes(buf), dtype=np.uint8) if not isinstance(buf, np.ndarray) else buf.view(np.uint8)
+    if isinstance(buf, np.ndarray):
+        raw = np.ascontiguousarray(buf).view(np.uint8).reshape(-1)
+    else:
+        raw = np.frombuffer(bytes(buf), dtype=np.uint8)
     if raw.ctypes.data % 8:
         raw = np.frombuffer(raw.tobytes(), dtype=np.uint8)  # fresh bytes objects are 8-byte aligned
     _check(load().louvain_load_state(ctx, raw.ctypes.data, raw.nbytes), ctx)
