@@ -166,6 +166,16 @@ def oracle_steps(gs, steps: int, warmup: int):
     return dt, oracle.num_threads()
 
 
+def move_bin_degrees(kernel: str, sched: dict):
+    """Degree range [lo, hi] (hi None: unbounded) of the vertices a
+    local-moving kernel takes under a launch schedule; None for kernels that
+    are not a degree bin of local moving."""
+    gm, hm, wm = sched["group_max"], sched["half_max"], sched["warp_max"]
+    return {"move_thread": [1, 16], "move_group": [17, gm], "move_half": [gm + 1, hm], "move_warp": [hm + 1, wm],
+            "move_mid": [wm + 1, 1024], "move_block": [1025, 4096], "move_xl": [4097, 8192],
+            "move_cluster": [8193, 32768], "move_hub": [32769, None]}.get(kernel)
+
+
 def max_over_ranks(x: float, world: int, device=None) -> float:
     """The largest x over all ranks (the slowest rank's time), by one
     all-reduce; x itself on a single rank."""
@@ -419,7 +429,9 @@ def main():
         try:
             tj = json.load(open(tpath))
             ent = tj.get(args.workload, {}).get(dom)
-            if ent:
+            # per-launch DRAM bytes describe the same work only if the bin
+            # took the same degrees when they were captured
+            if ent and ent.get("bin_degrees") == move_bin_degrees(dom, run_sched):
                 traffic = ent.get("dram_bytes_per_launch")
         except (OSError, ValueError):
             traffic = None

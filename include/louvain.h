@@ -243,7 +243,9 @@ louvain_status louvain_set_schedule(louvain_ctx *ctx, const int32_t *words, int3
 
 /* Choose the context's schedule by timed runs of its own graph (at most
  * max_runs trials; a whole-run trial is the faster of two runs), in order:
- * the bin thresholds by whole-run time; the blocks per SM of every bin by
+ * the bin thresholds by whole-run time (a triple replaces the current one
+ * only if it is at least 1.5% faster, more than run-to-run noise); the
+ * blocks per SM of every bin by
  * per-kernel CUDA-event time; concurrent bin kernels on or off; graph replay
  * on or off.  The tuned schedule is kept only if it beats the starting one.
  * json (may be NULL) receives {"runs", "start_ms", "tuned_ms", "schedule",

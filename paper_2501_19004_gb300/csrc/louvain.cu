@@ -2021,7 +2021,11 @@ louvain_status louvain_autotune(louvain_ctx *x, int32_t max_runs, char *json, si
   {
     Sched best = start;
     double best_ms = start_ms;
-    // 1. thresholds (a half bin with half_max == group_max is empty)
+    // 1. thresholds (a half bin with half_max == group_max is empty).  The
+    // triples differ by about as much as runs do, so a triple must beat the
+    // current best by kMargin to replace it; otherwise noise alone would pick
+    // a different triple, and different bins, from run to run.
+    constexpr double kMargin = 0.015;
     const int gms[] = {16, 32, 48, 64};
     const int wms[] = {128, 256};
     for (int gm : gms)
@@ -2035,7 +2039,7 @@ louvain_status louvain_autotune(louvain_ctx *x, int32_t max_runs, char *json, si
           t.warp_max = wm;
           if ((st = run_once(t, false, &ms))) goto fail;
           note("thresholds", t, ms);
-          if (ms < best_ms) {
+          if (ms < best_ms * (1.0 - kMargin)) {
             best_ms = ms;
             best = t;
           }
