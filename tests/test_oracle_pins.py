@@ -415,3 +415,27 @@ def test_fully_simultaneous_decisions_collapse_a_mixed_sbm():
     assert int(one.pass_stats[1, 2]) == oracle.Config().max_iterations
     for B in (2, 4):
         assert oracle.louvain(g, oracle.Config(buckets=B)).modularity > 0.52
+
+
+def test_passes_form_a_refinement_chain_with_conserved_weight():
+    """Each pass moves super-vertices of the previous pass's communities
+    (Algorithm 1), so the partition after p + 1 passes is a coarsening of the
+    one after p passes; and aggregating the input by any of them keeps its
+    total weight 2m (Algorithm 3).  With the pass cap at p the memberships
+    are the communities found by the first p passes."""
+    for g in (gg.grid(64, 0.02, seed=5), gg.sbm(3000, 50, 0.3, 0.004, seed=4), gg.rmat(13, 12, seed=21,
+                                                                                          weight_range=(1, 3))):
+        full = oracle.louvain(g)
+        assert full.passes >= 3
+        chain = [oracle.louvain(g, oracle.Config(max_passes=p)).membership for p in range(1, full.passes + 1)]
+        chain.append(full.membership)
+        for fine, coarse in zip(chain, chain[1:]):
+            # every community of the finer partition lies inside one community of the coarser
+            ncomm = int(fine.max()) + 1
+            first = np.full(ncomm, -1, dtype=np.int64)
+            first[fine[::-1]] = coarse[::-1]
+            assert np.array_equal(first[fine], coarse)
+            assert int(np.unique(coarse).shape[0]) <= ncomm
+        for memb in chain:
+            o, c, w = oracle.aggregate(g, memb, int(memb.max()) + 1)
+            assert int(w.sum()) == g.total_weight()
