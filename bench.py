@@ -444,6 +444,14 @@ def main():
     if serial:
         serial["frac"] = serial["achieved"] / peaks["hbm_gbs"]
         roofline["serial"] = serial
+    # whole run: every kernel's algorithmic bytes of the last timed run at
+    # the peak give the shortest possible run and so a bound on edges/s
+    run_bytes = sum(float(v.get("bytes", 0.0)) for v in st.get("kernels", {}).values())
+    if run_bytes > 0:
+        bound_ms = run_bytes / (peaks["hbm_gbs"] * 1e9) * 1e3
+        roofline["run"] = {"algorithmic_bytes": run_bytes, "bound_ms": bound_ms,
+                           "implied_bound": job_rate(g.nnz, 1, world, bound_ms / 1e3),
+                           "frac": bound_ms / (ms / args.steps)}
 
     # batch only: the same graphs one context at a time (a strided sample),
     # the way a single-graph library would run them
