@@ -1,6 +1,8 @@
 // Big items on sm_103a: hub vertices of the local-moving phase (Algorithm 5)
 // and large communities of the aggregation phase (Algorithm 6) of arXiv
-// 2501.19004, i.e. every item with more than 4096 table entries.
+// 2501.19004: vertices of degree above 32768 (smaller ones fit a block's or
+// a cluster's shared memory) and communities whose members hold more than
+// 8192 entries.
 //
 // The paper gives such items a thread block each (Sec. 4.3.4).  On skewed
 // graphs one item can hold hundreds of millions of entries, so here an item's

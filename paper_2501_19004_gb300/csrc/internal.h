@@ -63,10 +63,12 @@ __host__ __device__ __forceinline__ int merge_bin(int64_t d) {
 }
 
 // Launch schedule of the binned kernels (louvain_autotune chooses one; the
-// results never depend on it, since every bin's kernel computes the same
-// exact decision for a vertex):
-//   group_max  largest degree of the group bin (16 = no group bin, <= 64);
-//   warp_max   largest degree of the warp bin (>= group_max, <= 256); larger
+// deterministic form's results never depend on it, since every bin's kernel
+// computes the same exact decision for a vertex):
+//   group_max  largest degree of the 8-lane group bin (16 = none, <= 64);
+//   half_max   largest degree of the 16-lane group bin (>= group_max,
+//              <= 128; = group_max for none);
+//   warp_max   largest degree of the warp bin (>= half_max, <= 256); larger
 //              degrees up to 1024 go to the 128-thread block bin;
 //   move[b], merge[b]  blocks per SM of bin b's kernel (grid = SMs x blocks;
 //              every kernel strides over its list, so any grid is correct);

@@ -7,7 +7,10 @@
 // tolerance tests, renumbering, dendrogram lookup and aggregation (aggr.cu,
 // Algorithm 6), then threshold scaling.  Everything stays on the device; the
 // host only reads a few scalars per iteration (the exact gain sum) and per
-// pass (community count, sizes).
+// pass (community count, sizes).  The same loop can stop between two passes
+// and resume, also from a checkpoint in host memory; a batch of graphs runs
+// it in lockstep over their union (batch.cu); and louvain_autotune picks the
+// launch schedule by timed runs.
 #include <algorithm>
 #include <array>
 #include <cstdarg>

@@ -12,6 +12,8 @@
 //   hubs       (degree > 4096) are split into chunks over the whole grid
 //              (big.cu);
 //   k_apply    applies the moves: C'[i] = c*, Sigma' by 64-bit atomics.
+// In the asynchronous form (one bucket per iteration) each mover applies its
+// own move at the decision instead (emit_move) and k_apply is not launched.
 // The paper's per-vertex global hashtables of 2|E| slots (Sec. 4.3.2) become
 // register tables (thread bin), shared-memory open addressing (warp and block
 // bins) and global tables for hubs only.
