@@ -46,3 +46,22 @@ def test_stored_traffic_matches_its_capture_range():
             assert ent["bin_degrees"] == bench.move_bin_degrees(kern, default), (wl, kern)
             assert ent["dram_bytes_per_launch"] == ent["dram_read_per_launch"] + ent["dram_write_per_launch"] or \
                 abs(ent["dram_bytes_per_launch"] - ent["dram_read_per_launch"] - ent["dram_write_per_launch"]) <= 1
+
+
+def test_reference_arm_line_on_cpu():
+    """The reference arm times the CPU oracle only; its JSON line carries the
+    contract's keys (run here on the small planted-partition workload)."""
+    import subprocess
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "sbm1000",
+                        "--steps", "2", "--warmup", "3"], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 3
+    assert line["value"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
