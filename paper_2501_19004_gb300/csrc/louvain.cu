@@ -242,6 +242,21 @@ __global__ void k_validate_entries(int64_t nnz, int64_t n, const int32_t *col, c
   }
 }
 
+// Rows of a holey CSR copied to consecutive positions (row i to off[i]),
+// one warp per row.
+__global__ void k_compact_rows(int64_t n, const int64_t *b, const int64_t *e, const int64_t *off, const int32_t *cs,
+                               const uint32_t *ws, int32_t *cd, uint32_t *wd) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+    const int64_t b0 = b[i], len = e[i] - b0, o = off[i];
+    for (int64_t k = lane; k < len; k += 32) {
+      cd[o + k] = cs[b0 + k];
+      wd[o + k] = ws[b0 + k];
+    }
+  }
+}
+
 void dfree(louvain_ctx *x, void *p) {
   if (!p) return;
   cudaFreeAsync(p, x->stream);
@@ -1664,7 +1679,9 @@ louvain_status louvain_save_state(const louvain_ctx *xc, void *buf, size_t cap, 
   if (n) LV_CK(cudaMemcpyAsync(q, x->K, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
   q += (size_t)n * 8;
   // the super-vertex graph, compacted: its rows sit at the prefix of their
-  // capacity bounds in the ping-pong buffer
+  // capacity bounds in one ping-pong buffer, and the device packs them into
+  // the other one, which the next aggregation would write (free between
+  // passes); the offsets are computed here from the row bounds
   std::vector<int64_t> b((size_t)n), e((size_t)n);
   if (n) {
     LV_CK(cudaMemcpyAsync(b.data(), rs.g.begin, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
@@ -1672,15 +1689,8 @@ louvain_status louvain_save_state(const louvain_ctx *xc, void *buf, size_t cap, 
   }
   LV_CK(cudaStreamSynchronize(s));
   int64_t *off = reinterpret_cast<int64_t *>(q);
-  int64_t lo = INT64_MAX, hi = 0;
   off[0] = 0;
-  for (int64_t i = 0; i < n; ++i) {
-    off[i + 1] = off[i] + (e[i] - b[i]);
-    if (e[i] > b[i]) {
-      lo = std::min(lo, b[i]);
-      hi = std::max(hi, e[i]);
-    }
-  }
+  for (int64_t i = 0; i < n; ++i) off[i + 1] = off[i] + (e[i] - b[i]);
   if (off[n] != nnz) {
     set_err(x, "suspended graph holds %lld entries, expected %lld", (long long)off[n], (long long)nnz);
     return LOUVAIN_E_STATE;
@@ -1689,18 +1699,16 @@ louvain_status louvain_save_state(const louvain_ctx *xc, void *buf, size_t cap, 
   int32_t *cols = reinterpret_cast<int32_t *>(q);
   uint32_t *wts = reinterpret_cast<uint32_t *>(q + pad8((size_t)nnz * 4));
   if (nnz) {
-    std::vector<int32_t> sc((size_t)(hi - lo));
-    std::vector<uint32_t> sw((size_t)(hi - lo));
-    LV_CK(cudaMemcpyAsync(sc.data(), rs.g.col + lo, (size_t)(hi - lo) * 4, cudaMemcpyDeviceToHost, s));
-    LV_CK(cudaMemcpyAsync(sw.data(), static_cast<const uint32_t *>(rs.g.w) + lo, (size_t)(hi - lo) * 4,
-                          cudaMemcpyDeviceToHost, s));
+    const int free_slot = rs.slot;  // rs.g lives in the other buffer
+    int64_t *d_off = x->hoff;        // aggregation scratch of n0 + 1 words, free between passes
+    LV_CK(cudaMemcpyAsync(d_off, off, (size_t)(n + 1) * 8, cudaMemcpyHostToDevice, s));
+    LV_LAUNCH(k_compact_rows<<<grid_for(n * 32, 256, x->num_sms, 8), 256, 0, s>>>(
+        n, rs.g.begin, rs.g.end, d_off, rs.g.col, static_cast<const uint32_t *>(rs.g.w), x->pcol[free_slot],
+        x->pw[free_slot]));
+    LV_CK(cudaGetLastError());
+    LV_CK(cudaMemcpyAsync(cols, x->pcol[free_slot], (size_t)nnz * 4, cudaMemcpyDeviceToHost, s));
+    LV_CK(cudaMemcpyAsync(wts, x->pw[free_slot], (size_t)nnz * 4, cudaMemcpyDeviceToHost, s));
     LV_CK(cudaStreamSynchronize(s));
-    for (int64_t i = 0; i < n; ++i) {
-      const int64_t len = e[i] - b[i];
-      if (len <= 0) continue;
-      memcpy(cols + off[i], sc.data() + (b[i] - lo), (size_t)len * 4);
-      memcpy(wts + off[i], sw.data() + (b[i] - lo), (size_t)len * 4);
-    }
   }
   h[CK_SUM] = (int64_t)fnv1a_words(reinterpret_cast<const uint64_t *>(base + 8 * kCkptHeader),
                                    (need - 8 * kCkptHeader) / 8);
