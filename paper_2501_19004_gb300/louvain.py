@@ -522,12 +522,16 @@ class Louvain:
         return louvain_run_passes(self.ctx, max_new_passes)
 
     def resume(self, max_new_passes: int = 0) -> bool:
+        """Continue a stopped run (0 = to the end); True if it stopped again."""
         return louvain_resume(self.ctx, max_new_passes)
 
     def save_state(self) -> np.ndarray:
+        """Checkpoint of the stopped run (uint8 array in host memory)."""
         return louvain_save_state(self.ctx)
 
     def load_state(self, buf):
+        """Restore a checkpoint taken on the same graph and settings; resume()
+        then continues the run."""
         louvain_load_state(self.ctx, buf)
         return self
 
