@@ -53,7 +53,9 @@ typedef enum {
   LOUVAIN_E_CUDA = 3,           /* a CUDA call failed (see louvain_last_error) */
   LOUVAIN_E_HASH_OVERFLOW = 4,  /* a hashtable probe sequence exceeded its bound
                                    (the paper's "failed" result of Algorithm 7) */
-  LOUVAIN_E_TIMEOUT = 5,        /* a bounded device-side wait gave up */
+  LOUVAIN_E_TIMEOUT = 5,        /* a bounded device-side wait gave up (reserved: no
+                                   kernel of this library waits on a flag; thread-block
+                                   clusters meet at hardware barriers) */
   LOUVAIN_E_OVERFLOW = 6,       /* 2m >= 2^32: scores would not fit in int64 */
   LOUVAIN_E_STATE = 7           /* call out of order (e.g. memberships before run) */
 } louvain_status;
