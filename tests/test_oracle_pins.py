@@ -439,3 +439,44 @@ def test_passes_form_a_refinement_chain_with_conserved_weight():
         for memb in chain:
             o, c, w = oracle.aggregate(g, memb, int(memb.max()) + 1)
             assert int(w.sum()) == g.total_weight()
+
+
+def test_pass_loop_stopping_rules_at_their_boundaries():
+    """Algorithm 1's two stopping rules exactly at their boundaries.
+
+    A pass whose local moving ends in a single iteration (l_i = 1) ends the
+    run as converged: on a ring of cliques with r <= k, merging two cliques
+    lowers modularity, so the second pass makes no move and the run stops
+    there with exit reason 1, not through the shrink test.  And aggregation
+    goes on while |Gamma|/n' <= tau_agg (the algorithm's strict '>' for
+    stopping): a triangle next to seven isolated vertices leaves 8 of 10
+    communities, exactly tau_agg = 0.8, so the run must aggregate and stop
+    in the second pass."""
+    ring = oracle.louvain(gg.ring_of_cliques(8, 10))
+    assert ring.passes == 2 and ring.exit_reason == 1
+    assert int(ring.pass_stats[1, 2]) == 1 and int(ring.pass_stats[1, 3]) == 8
+    tri = gg.from_pairs(10, [0, 1, 0], [1, 2, 2])
+    r = oracle.louvain(tri)
+    assert (int(r.pass_stats[0, 0]), int(r.pass_stats[0, 3])) == (10, 8)
+    assert r.passes == 2 and r.exit_reason == 1
+    # with tau_agg just below 0.8 the first pass is the last
+    r = oracle.louvain(tri, oracle.Config(aggregation_tolerance=0.79))
+    assert r.passes == 1 and r.exit_reason == 2
+
+
+def test_final_modularity_is_the_last_pass_modularity():
+    """Aggregation keeps modularity (Q of the super-vertex graph under C'
+    equals Q of the input under the looked-up memberships), and so does the
+    dendrogram lookup.  So the run's final exact numerator equals the one
+    recorded at the end of its last pass, whichever rule ended the run."""
+    cases = [gg.sbm(1000, 100, 0.1, 0.002, seed=1), gg.grid(64, 0.02, seed=5),
+             gg.rmat(13, 12, seed=21, weight_range=(1, 3)), gg.ring_of_cliques(8, 10),
+             gg.from_pairs(10, [0, 1, 0], [1, 2, 2]), gg.sbm(3000, 50, 0.3, 0.004, seed=4)]
+    reasons = set()
+    for g in cases:
+        for cfg in (oracle.Config(), oracle.Config(max_passes=2)):
+            r = oracle.louvain(g, cfg)
+            hi, lo = int(r.pass_stats[r.passes - 1, 4]), int(r.pass_stats[r.passes - 1, 5])
+            assert (hi << 64) + (lo & (2**64 - 1)) == r.q_num, (g.n, cfg.max_passes)
+            reasons.add(r.exit_reason)
+    assert reasons == {0, 1, 2}  # every way a run can end is covered
