@@ -1,11 +1,14 @@
 """Mutation check of the oracle's pins (not collected by pytest).
 
-Each mutant is one plausible mistake planted in a scratch copy of
-oracle/louvain_oracle.c: a dropped or sign-flipped term of Eq. 2, a reversed
-tie-break or Pick-Less rule, a missing Sigma' or C' update, a stopping rule
-off at its boundary, a missing dendrogram lookup, and so on.  The copy is
-compiled and tests/test_oracle_pins.py runs against it; every mutant must
-make some pin fail.  The repository's own oracle is never modified.
+Each mutant is one plausible mistake planted in a scratch copy of the
+oracle.  In oracle/louvain_oracle.c: a dropped or sign-flipped term of
+Eq. 2, a reversed tie-break or Pick-Less rule, a missing Sigma' or C'
+update, a stopping rule off at its boundary, a missing dendrogram lookup,
+and so on; the copy is compiled and tests/test_oracle_pins.py runs against
+it.  In oracle/mlp.py (the predictor): a missing ReLU or bias, a transposed
+weight or gradient, a wrong loss scale or sign, bf16 rounding without ties
+to even; tests/test_oracle_mlp.py runs against it.  Every mutant must make
+some pin fail.  The repository's own oracle is never modified.
 
     python tests/oracle_mutants.py [scratch_dir]
 
@@ -63,11 +66,26 @@ MUTANTS = {
 }
 
 
+MLP_MUTANTS = {
+    "no ReLU on the second layer": ('h2 = rb(np.maximum(z2, 0.0))', 'h2 = rb(z2)'),
+    "no second-layer bias": ('z2 = h1 @ W2 + P["b2"]', 'z2 = h1 @ W2'),
+    "W2 transposed": ('z2 = h1 @ W2 + P["b2"]', 'z2 = h1 @ W2.T + P["b2"]'),
+    "loss gradient not divided by n": ('dl = (p - Y) / n', 'dl = (p - Y)'),
+    "ReLU mask of the wrong layer": ('dz1 = dh1 * (c["z1"] > 0)', 'dz1 = dh1 * (c["z2"] > 0)'),
+    "W2 gradient transposed": ('g["W2"] = c["h1"].T @ dz2b', 'g["W2"] = (c["h1"].T @ dz2b).T'),
+    "back-propagation through W2, not its transpose": ('dh1 = dz2b @ c["W2"].T', 'dh1 = dz2b @ c["W2"]'),
+    "bf16 rounds half up": ('+ np.uint64(0x7FFF) + lsb)', '+ np.uint64(0x8000))'),
+    "loss sign": ('- logit * Y +', '+ logit * Y +'),
+    "b3 gradient averaged": ('g["b3"] = dl.sum()', 'g["b3"] = dl.mean()'),
+}
+
+
 def copy_tree(scratch: str) -> str:
     for sub in ("oracle", os.path.join("paper_2501_19004_gb300", "graphgen"), os.path.join("tests", "golden")):
         shutil.copytree(os.path.join(ROOT, sub), os.path.join(scratch, sub), dirs_exist_ok=True,
                         ignore=shutil.ignore_patterns("__pycache__", "*.so"))
-    for f in ("paper_2501_19004_gb300/__init__.py", "tests/conftest.py", "tests/test_oracle_pins.py"):
+    for f in ("paper_2501_19004_gb300/__init__.py", "tests/conftest.py", "tests/test_oracle_pins.py",
+              "tests/test_oracle_mlp.py"):
         shutil.copy(os.path.join(ROOT, f), os.path.join(scratch, f))
     return os.path.join(scratch, "oracle", "louvain_oracle.c")
 
@@ -102,7 +120,26 @@ def main() -> int:
                 print(f"{name:34s} SURVIVED")
     finally:
         open(src, "w").write(orig)
-    print(f"{len(MUTANTS) - survivors} of {len(MUTANTS)} mutants killed")
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-o", lib, src])
+    mlp_src = os.path.join(scratch, "oracle", "mlp.py")
+    mlp_orig = open(mlp_src).read()
+    mlp_pins = [sys.executable, "-m", "pytest", "tests/test_oracle_mlp.py", "-x", "-q", "-p", "no:cacheprovider"]
+    assert subprocess.run(mlp_pins, cwd=scratch, capture_output=True).returncode == 0, "MLP pins fail unmutated"
+    try:
+        for name, (old, new) in MLP_MUTANTS.items():
+            assert mlp_orig.count(old) >= 1, f"mutant pattern not found: {name}"
+            open(mlp_src, "w").write(mlp_orig.replace(old, new, 1))
+            r = subprocess.run(mlp_pins, cwd=scratch, capture_output=True, text=True, timeout=900)
+            failed = [ln for ln in r.stdout.splitlines() if ln.startswith("FAILED")]
+            if r.returncode:
+                print(f"mlp: {name:48s} killed by {failed[0].split('::')[1].split(' ')[0] if failed else '(error)'}")
+            else:
+                survivors += 1
+                print(f"mlp: {name:48s} SURVIVED")
+    finally:
+        open(mlp_src, "w").write(mlp_orig)
+    total = len(MUTANTS) + len(MLP_MUTANTS)
+    print(f"{total - survivors} of {total} mutants killed")
     return 1 if survivors else 0
 
 
