@@ -50,3 +50,19 @@ def test_binding_fails_loudly_without_the_library(tmp_path):
     from paper_2501_19004_gb300 import louvain as lv
     with pytest.raises(RuntimeError):
         lv.load(str(tmp_path / "missing.so"))
+
+
+def test_config_struct_layout_matches_the_header(lib):
+    """The binding's louvain_config has the C struct's size: the library's
+    louvain_config_default zeroes sizeof(louvain_config) bytes, which must
+    end exactly where the binding's struct ends."""
+    import ctypes
+    from paper_2501_19004_gb300 import louvain as lv
+    n = ctypes.sizeof(lv.LouvainConfig)
+    buf = (ctypes.c_uint8 * (n + 64))(*([0xAB] * (n + 64)))
+    lib.louvain_config_default(ctypes.cast(buf, ctypes.POINTER(lv.LouvainConfig)))
+    assert all(b == 0xAB for b in buf[n:]), "the library writes past the binding's struct"
+    assert buf[n - 1] != 0xAB, "the binding's struct is longer than the library's"
+    c = lv.LouvainConfig.from_buffer(buf)
+    assert (c.asynchronous, c.table_window, c.learned_fallback, c.trace_capacity) == (0, 0, 0, 0)
+    assert c.max_passes == 10 and c.buckets == 4
