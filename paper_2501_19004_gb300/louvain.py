@@ -449,6 +449,16 @@ SCHEDULE_FIELDS = ["group_max", "half_max", "warp_max",
                    "graphs", "concurrent"]
 
 
+def louvain_schedule_words() -> int:
+    """Number of int32 words of a launch schedule."""
+    return int(load().louvain_schedule_words())
+
+
+def louvain_last_error(ctx=None) -> str:
+    """Description of the last error on ctx (or of the last failed create)."""
+    return load().louvain_last_error(ctx).decode(errors="replace")
+
+
 def louvain_get_schedule(ctx) -> dict:
     n = int(load().louvain_schedule_words())
     w = np.zeros(n, dtype=np.int32)

@@ -66,3 +66,10 @@ def test_config_struct_layout_matches_the_header(lib):
     c = lv.LouvainConfig.from_buffer(buf)
     assert (c.asynchronous, c.table_window, c.learned_fallback, c.trace_capacity) == (0, 0, 0, 0)
     assert c.max_passes == 10 and c.buckets == 4
+
+
+def test_binding_has_every_declared_function():
+    """The Python binding keeps the C ABI's names: one wrapper per function."""
+    from paper_2501_19004_gb300 import louvain as lv
+    missing = [n for n in declared_functions() if not hasattr(lv, n)]
+    assert not missing, missing
