@@ -114,11 +114,12 @@ typedef struct {
                                     and clears the vertex's flag (it returns when a
                                     neighbour moves); 0 = skipped vertices keep
                                     their flag */
-  int64_t table_window;          /* global hashtables of vertices and communities with
-                                    more than 4096 entries are processed in rounds of
-                                    this many 8-byte slots (at least the largest
-                                    table); 0 = half of the pass's bound on their
-                                    total size.  Results do not depend on it. */
+  int64_t table_window;          /* the global hashtables of hub vertices (degree above
+                                    32768) and large communities (members holding more
+                                    than 8192 entries) are processed in rounds of this
+                                    many 8-byte slots (at least the largest table);
+                                    0 = half of the pass's bound on their total size.
+                                    Results do not depend on it. */
   int32_t asynchronous;          /* 1: the asynchronous form of the paper's GPU
                                     algorithm (Algorithm 5 as written, Sec. 4.3):
                                     each iteration is one sweep over all unprocessed
