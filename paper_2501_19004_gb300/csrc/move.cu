@@ -9,7 +9,7 @@
 //              Eq. 2 scaled by 2m^2, the Pick-Less rejection (Sec. 4.3.1),
 //              and, for movers, the exact gain and the re-marking of the
 //              neighbours; decisions go to a mover list;
-//   hubs       (degree > 4096) are split into chunks over the whole grid
+//   hubs       (degree > 32768) are split into chunks over the whole grid
 //              (big.cu);
 //   k_apply    applies the moves: C'[i] = c*, Sigma' by 64-bit atomics.
 // In the asynchronous form (one bucket per iteration) each mover applies its
@@ -853,7 +853,7 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
 // ---------------------------------------------------------------- pass init
 // K (row sums on the first pass; given otherwise), Sigma' = K', C' = id,
 // all vertices unprocessed; the maximum degree and the size bound of the hub
-// tables (sum of pow2(2 min(deg, n')) over degrees > 4096) for the host.
+// tables (sum of pow2(2 min(deg, n')) over degrees > 32768) for the host.
 template <int WK>
 __global__ void __launch_bounds__(256) k_pass_init(GView g, int first_pass, int64_t *K, int64_t *Sigma,
                                                    int32_t *Cp, uint8_t *flag, Counters *ctr, float4 *feat,

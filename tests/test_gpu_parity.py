@@ -60,7 +60,7 @@ CASES = {
     "rmat12": lambda: gg.rmat(12, 16, seed=7),
     "rmat14_weighted": lambda: gg.rmat(14, 8, seed=3, weight_range=(1, 5)),
     "rmat16_hubs": lambda: gg.rmat(16, 16, seed=7),
-    "rmat18_hubs": lambda: gg.rmat(18, 16, seed=7),  # 172 vertices above 4096, 19 above 8192
+    "rmat18_hubs": lambda: gg.rmat(18, 16, seed=7),  # 172 vertices above 4096, 19 above 8192 (cluster bin)
     "rmat19_hubs": lambda: gg.rmat(19, 16, seed=7),  # one vertex above 32768 (global tables)
     "grid96": lambda: gg.grid(96, 0.02, seed=11),
     "ring8x10": lambda: gg.ring_of_cliques(8, 10),
