@@ -131,6 +131,11 @@ typedef struct {
                                     ignored.  Plain mode, no traces, single graphs
                                     only (LOUVAIN_E_INVAL otherwise).  0: the
                                     deterministic bucket schedule. */
+  int32_t learned_min_degree;    /* LEARNED and trace recording: only vertices of at
+                                    least this degree are candidates of the predictor
+                                    and keep features (and only they are recorded);
+                                    lower-degree vertices are always evaluated when
+                                    flagged, as in the plain method.  0 = all. */
 } louvain_config;
 
 /* Fill `cfg` with the defaults above (mode PLAIN, seed 0). */
@@ -265,7 +270,8 @@ const char *louvain_last_error(const louvain_ctx *ctx);
 
 /* Modularity (Eq. 1) of an arbitrary membership on a graph, computed on the
  * device.  graph and membership are both device or both host arrays
- * (graph->on_device); membership ids lie in [0, n).  q and the exact
+ * (graph->on_device); membership ids lie in [0, n) (LOUVAIN_E_INVAL
+ * otherwise; nothing is written for such a vertex).  q and the exact
  * numerator/denominator (hi, lo) as in louvain_modularity. */
 louvain_status louvain_modularity_of(const louvain_graph *graph, const int32_t *membership, void *stream,
                                      double *q, int64_t *num_hi_lo, int64_t *den_hi_lo);
@@ -297,9 +303,15 @@ louvain_status louvain_modularity_of(const louvain_graph *graph, const int32_t *
  * (graph->on_device = 1) and n may not exceed 1,048,576 (LOUVAIN_E_INVAL
  * beyond that).  Scratch lives in a fixed 8 MiB array inside the library
  * that every GPU loading the library keeps until exit; calls share it, so
- * calls that overlap on the GPU race.  The first call on a device looks the
- * array up (make it before any stream capture).  Out-of-range ids or
- * non-positive weights give LOUVAIN_E_INVAL, 2m >= 2^32 LOUVAIN_E_OVERFLOW. */
+ * calls that overlap on the GPU race.  The first call on a device does the
+ * set-up: it loads the library's device code there (which reserves the
+ * array) and looks the array's address up once for the rest of the process.
+ * Make that first call before any stream capture begins and before your own
+ * pool claims the device's memory; do not use the library on a device after
+ * cudaDeviceReset of it.  The CSR is checked on the device before any entry
+ * is read: offsets[0] = 0, offsets[n] = nnz, every row within [0, nnz) and
+ * not decreasing, columns and membership ids in [0, n), weights > 0
+ * (LOUVAIN_E_INVAL otherwise); 2m >= 2^32 gives LOUVAIN_E_OVERFLOW. */
 louvain_status louvain_modularity_noalloc(const louvain_graph *graph, const int32_t *membership, void *stream,
                                           double *q, int64_t *num_hi_lo, int64_t *den_hi_lo);
 
@@ -341,12 +353,32 @@ int64_t louvain_model_size(void);
 louvain_status louvain_traces(const louvain_ctx *ctx, float *features, float *labels, int64_t cap, int64_t *count,
                               int32_t on_device);
 
+/* The predictor's arithmetic (the definition both louvain_mlp_forward and
+ * louvain_mlp_gradient compute; bf() = round to the nearest bfloat16, ties
+ * to even; every sum is accumulated in fp32 unless marked otherwise):
+ *   forward, per row:  x~ = bf(x), W1~ = bf(W1), W2~ = bf(W2), w3~ = bf(w3);
+ *     z1 = x~ W1~ + b1;   h1 = bf(max(z1, 0));
+ *     z2 = h1 W2~ + b2;   h2 = bf(max(z2, 0));
+ *     logit = h2 . w3~ + b3;   p = sigmoid(logit).
+ *   backward of L = (1/n) sum_rows BCE(p, y):
+ *     dl = (p - y) / n                                  (fp32, not rounded)
+ *     db3 = sum dl;   dw3 = sum dl h2
+ *     dz2 = dl w3~ [z2 > 0];   db2 = sum dz2            (dz2 not rounded)
+ *     dW2 = h1^T bf(dz2)                                (bf16 operands)
+ *     dh1 = bf(dz2) W2~^T;   dz1 = dh1 [z1 > 0];   db1 = sum dz1
+ *     dW1 = x~^T bf(dz1)                                (bf16 operands)
+ * So exactly two deltas are rounded, bf(dz2) and bf(dz1), each where it
+ * enters a tensor-core contraction; bias and w3 gradients use the unrounded
+ * fp32 deltas.  The fp32 sums run over the rows in tiles (16 rows per mma
+ * step, 128 rows per block, block partials added in block order). */
+
 /* Logits of n feature rows X[n][8] (device pointers; params on the device). */
 louvain_status louvain_mlp_forward(const float *params, const float *X, int64_t n, float *logits, void *stream);
 
 /* Gradient of the mean binary cross-entropy of sigmoid(logit) against
- * labels Y over n rows, added into grad[louvain_model_size()]; the mean loss
- * is added into *loss (device pointers; loss may be NULL). */
+ * labels Y over n rows (the backward definition above), added into
+ * grad[louvain_model_size()]; the mean loss is added into *loss (device
+ * pointers; loss may be NULL). */
 louvain_status louvain_mlp_gradient(const float *params, const float *X, const float *Y, int64_t n, float *grad,
                                     float *loss, void *stream);
 

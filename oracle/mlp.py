@@ -3,16 +3,17 @@
 TEST INFRASTRUCTURE ONLY (tests, smoke check, CPU baseline); the product path
 never imports it and it shares no code with the CUDA kernels.
 
-The paper has no predictor; its definition is the library's (header
-louvain.h): parameters W1[8][32], b1[32], W2[32][32], b2[32], w3[32], b3 in
-one flat float vector; evaluation rounds the inputs, the weights and the
-hidden ReLU outputs to bf16 (round to nearest even) and accumulates exactly
-here (fp64; the device accumulates in fp32).  Loss: mean binary
-cross-entropy of sigmoid(logit).  The backward pass follows the same
-mixed-precision definition as the device kernels: the back-propagated
-deltas entering a weight-gradient contraction or dh1 = dz2 W2^T are rounded
-to bf16, bias gradients are exact sums.  With bf16=False everything is
-plain fp64 (used to pin the gradient against finite differences).
+The paper has no predictor; its definition is the library's, written out
+in include/louvain.h (above louvain_mlp_forward): parameters W1[8][32],
+b1[32], W2[32][32], b2[32], w3[32], b3 in one flat float vector; the
+inputs, the weights and the hidden ReLU outputs are rounded to bf16 (round
+to nearest even) and products are summed exactly here (fp64; the device
+sums in fp32).  Loss: mean binary cross-entropy of sigmoid(logit).  The
+backward pass restates the header's definition: of the back-propagated
+deltas exactly two are rounded to bf16, dz2 where it enters dW2 = h1^T dz2
+and dh1 = dz2 W2^T, and dz1 where it enters dW1 = x^T dz1; bias and w3
+gradients use the unrounded deltas.  With bf16=False everything is plain
+fp64 (used to pin the gradient against finite differences).
 """
 from __future__ import annotations
 
@@ -111,3 +112,4 @@ def init_params(seed: int = 0, scale: float = 1.0):
         "b3": 0.0,
     }
     return pack(d).astype(np.float32)
+

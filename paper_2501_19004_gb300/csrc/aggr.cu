@@ -512,26 +512,55 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : NT == 512 ? 2 : 1) k_merge
 }
 
 // --------------------------------------------------------------- modularity
-// Groups of 8 lanes per vertex (4 vertices per warp): internal weight
-// sum_{j in row(i), memb[j] == memb[i]} w_ij (self-loop entries included)
-// and, when sigma_out is given, the row sum K_i added into
-// sigma_out[memb[i]].
+// Internal weight S_in = sum over entries (i, j) with memb[j] == memb[i] of
+// w_ij (self-loop entries included) and, when sigma_out is given, the row
+// sum K_i added into sigma_out[memb[i]] (Eq. 1's Sigma_c).  Rows are split
+// by degree so that no row is walked by too few lanes: rows up to
+// kModGroupDeg entries by groups of 8 lanes (4 rows per warp, this kernel),
+// rows up to kModWarpDeg by a warp each and longer rows by a 1024-thread
+// block each (k_mod_long, from two lists this kernel fills).  A membership
+// id outside [0, n) sets ERR_MEMB and its row is skipped (nothing is
+// written for it).
+constexpr int64_t kModGroupDeg = 64;
+constexpr int64_t kModWarpDeg = 4096;
+
 template <int WK>
-__global__ void __launch_bounds__(256) k_mod_rows(GView g, const int32_t *memb, int64_t *sigma_out, Counters *ctr) {
+__global__ void __launch_bounds__(256) k_mod_rows(GView g, const int32_t *memb, int64_t *sigma_out, int32_t *warp_rows,
+                                                  int32_t *block_rows, Counters *ctr) {
   constexpr int GS = 8;
   const int64_t grp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / GS;
   const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / GS;
   const int gl = threadIdx.x % GS;
+  const int lane = threadIdx.x & 31;
   unsigned long long sin = 0;
+  bool bad = false;
   // every lane of a warp runs the same number of rounds (shuffles below)
   const int64_t rounds = (g.n + ngrp - 1) / ngrp;
   for (int64_t r = 0; r < rounds; ++r) {
     const int64_t i = grp + r * ngrp;
-    const bool act = i < g.n;
+    bool act = i < g.n;
     const int32_t ci = act ? memb[i] : 0;
+    if (act && (ci < 0 || ci >= g.n)) {
+      bad = true;
+      act = false;
+    }
+    const int64_t rb = act ? g.begin[i] : 0, re = act ? g.end[i] : 0;
+    // long rows go to the warp and block lists (one append per warp and list)
+    const int cls = (act && re - rb > kModWarpDeg) ? 2 : (act && re - rb > kModGroupDeg) ? 1 : 0;
+#pragma unroll
+    for (int l = 1; l <= 2; ++l) {
+      const unsigned m = __ballot_sync(0xFFFFFFFFu, cls == l && gl == 0);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(&ctr->mod_count[l - 1], (unsigned long long)__popc(m));
+        base = __shfl_sync(0xFFFFFFFFu, base, leader);
+        if (cls == l && gl == 0) (l == 1 ? warp_rows : block_rows)[base + __popc(m & lanemask_lt())] = (int32_t)i;
+      }
+    }
     long long in = 0, k = 0;
-    if (act)
-      for (int64_t e = g.begin[i] + gl; e < g.end[i]; e += GS) {
+    if (cls == 0 && act)
+      for (int64_t e = rb + gl; e < re; e += GS) {
         const long long w = load_w<WK>(g.w, e);
         k += w;
         if (memb[__ldg(g.col + e)] == ci) in += w;
@@ -541,9 +570,53 @@ __global__ void __launch_bounds__(256) k_mod_rows(GView g, const int32_t *memb, 
       in += __shfl_xor_sync(0xFFFFFFFFu, in, o);
       k += __shfl_xor_sync(0xFFFFFFFFu, k, o);
     }
-    if (act && gl == 0) {
+    if (cls == 0 && act && gl == 0) {
       if (sigma_out && k) atomicAdd((unsigned long long *)(sigma_out + ci), as_ull(k));
       sin += (unsigned long long)in;
+    }
+  }
+  sin = warp_sum_u(sin);
+  if ((threadIdx.x & 31) == 0 && sin) atomicAdd(&ctr->q_sin, sin);
+  if (bad) atomicOr(&ctr->error, (unsigned long long)ERR_MEMB);
+}
+
+// Rows of the warp list (one warp each, 8 entries in flight per lane) and
+// of the block list (one 1024-thread block each); the list lengths are in
+// ctr->mod_count.  Ids were checked by k_mod_rows.
+template <int WK, int NT>
+__global__ void __launch_bounds__(NT) k_mod_long(GView g, const int32_t *memb, int64_t *sigma_out,
+                                                 const int32_t *rows, const unsigned long long *count, Counters *ctr) {
+  constexpr int U = 8;
+  constexpr int kRowThreads = NT == 1024 ? 1024 : 32;  // threads per row
+  const int64_t cnt = (int64_t)*count;
+  const int64_t slot = NT == 1024 ? blockIdx.x : ((int64_t)blockIdx.x * NT + threadIdx.x) / 32;
+  const int64_t nslots = NT == 1024 ? gridDim.x : ((int64_t)gridDim.x * NT) / 32;
+  const int t = NT == 1024 ? threadIdx.x : (threadIdx.x & 31);
+  unsigned long long sin = 0;
+  for (int64_t idx = slot; idx < cnt; idx += nslots) {
+    const int32_t i = rows[idx];
+    const int32_t ci = memb[i];
+    const int64_t rb = g.begin[i], re = g.end[i];
+    unsigned long long in = 0, k = 0;
+    for (int64_t e0 = rb + t; e0 < re; e0 += (int64_t)kRowThreads * U) {
+      int32_t jj[U];
+      uint32_t ww[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t e = e0 + (int64_t)u * kRowThreads;
+        jj[u] = e < re ? __ldg(g.col + e) : -1;
+        ww[u] = e < re ? load_w<WK>(g.w, e) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        k += ww[u];
+        if (jj[u] >= 0 && memb[jj[u]] == ci) in += ww[u];
+      }
+    }
+    sin += in;
+    if (sigma_out) {
+      k = warp_sum_u(k);
+      if ((threadIdx.x & 31) == 0 && k) atomicAdd((unsigned long long *)(sigma_out + ci), k);
     }
   }
   sin = warp_sum_u(sin);
@@ -618,8 +691,14 @@ void merge_t(const AggArgs &a, int num_sms, cudaStream_t s, KernelProf *prof, co
 }
 
 template <int WK>
-void mod_rows_t(const GView &g, const int32_t *memb, int64_t *sigma_out, Counters *ctr, int num_sms, cudaStream_t s) {
-  LV_LAUNCH(k_mod_rows<WK><<<grid_for(g.n * 8, 256, num_sms, 16), 256, 0, s>>>(g, memb, sigma_out, ctr));
+void mod_rows_t(const GView &g, const int32_t *memb, int64_t *sigma_out, int32_t *warp_rows, int32_t *block_rows,
+                Counters *ctr, int num_sms, cudaStream_t s) {
+  cudaMemsetAsync(&ctr->mod_count[0], 0, sizeof(ctr->mod_count), s);
+  LV_LAUNCH(k_mod_rows<WK><<<grid_for(g.n * 8, 256, num_sms, 16), 256, 0, s>>>(g, memb, sigma_out, warp_rows,
+                                                                                 block_rows, ctr));
+  LV_LAUNCH(k_mod_long<WK, 256><<<num_sms * 8, 256, 0, s>>>(g, memb, sigma_out, warp_rows, &ctr->mod_count[0], ctr));
+  LV_LAUNCH(k_mod_long<WK, 1024><<<num_sms * 2, 1024, 0, s>>>(g, memb, sigma_out, block_rows, &ctr->mod_count[1],
+                                                              ctr));
 }
 
 }  // namespace
@@ -680,7 +759,7 @@ void dendrogram_lookup(int32_t *C, const int32_t *Cp, int64_t n, int num_sms, cu
 }
 
 void modularity_sums(const GView &g, int wkind, const int32_t *memb, const int64_t *sigma, int64_t *sigma_scratch,
-                     Counters *ctr, int num_sms, cudaStream_t s) {
+                     int32_t *warp_rows, int32_t *block_rows, Counters *ctr, int num_sms, cudaStream_t s) {
   if (g.n <= 0) return;
   int64_t *sig_out = nullptr;
   if (!sigma) {
@@ -688,8 +767,8 @@ void modularity_sums(const GView &g, int wkind, const int32_t *memb, const int64
     sig_out = sigma_scratch;
     sigma = sigma_scratch;
   }
-  if (wkind == W_UNIT) mod_rows_t<W_UNIT>(g, memb, sig_out, ctr, num_sms, s);
-  else mod_rows_t<W_U32>(g, memb, sig_out, ctr, num_sms, s);
+  if (wkind == W_UNIT) mod_rows_t<W_UNIT>(g, memb, sig_out, warp_rows, block_rows, ctr, num_sms, s);
+  else mod_rows_t<W_U32>(g, memb, sig_out, warp_rows, block_rows, ctr, num_sms, s);
   LV_LAUNCH(k_sigma_sq<<<grid_for(g.n, 256, num_sms, 16), 256, 0, s>>>(sigma, g.n, ctr));
 }
 

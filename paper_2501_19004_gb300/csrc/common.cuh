@@ -33,7 +33,8 @@ struct GView {
 };
 
 // Error bits written by kernels (never a trap).
-enum ErrBits : unsigned long long { ERR_HASH = 1ull, ERR_RANGE = 2ull, ERR_TIMEOUT = 4ull };
+// ERR_MEMB: a membership id given to the modularity kernel lies outside [0, n).
+enum ErrBits : unsigned long long { ERR_HASH = 1ull, ERR_RANGE = 2ull, ERR_TIMEOUT = 4ull, ERR_MEMB = 8ull };
 
 // Small device-resident counters block.
 struct Counters {
@@ -60,7 +61,7 @@ struct Counters {
   unsigned long long scan_total[4]; // totals of the aggregation scans
   unsigned long long cand_count;    // learned mode: candidates of the bucket for the predictor
   unsigned long long trace_count;   // recorded (features, moved) samples
-  unsigned long long pad[2];
+  unsigned long long mod_count[2];  // modularity: rows handed to warps / to whole blocks
 };
 constexpr int kIterCounterWords = 5 + 45;
 

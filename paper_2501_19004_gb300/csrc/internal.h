@@ -170,6 +170,7 @@ struct LearnArgs {
   int32_t *cand = nullptr;      // [n] candidates of the bucket
   float thr_logit = 0.f;        // evaluate iff logit >= thr_logit
   int skip_clears = 0;          // a skip clears the flag (counts as "stay")
+  int64_t min_degree = 0;       // only vertices of at least this degree are candidates and keep features
   float t_norm = 0.f, p_norm = 0.f;
   float *trace_x = nullptr;     // [cap][8] recorded features
   float *trace_y = nullptr;     // [cap] recorded labels (moved)
@@ -358,9 +359,11 @@ void scan_u64(const unsigned long long *in, int64_t *out, int64_t n, int mode, l
 
 // modularity of membership `memb` on g: internal weight into ctr->q_sin and
 // sum of Sigma_c^2 (split) into ctr->q_tot_lo/hi.  If sigma is null it is
-// computed from the rows into sigma_scratch (zeroed here).
+// computed from the rows into sigma_scratch (zeroed here).  warp_rows and
+// block_rows (g.n int32 each) receive the lists of long rows.
 void modularity_sums(const GView &g, int wkind, const int32_t *memb, const int64_t *sigma,
-                     int64_t *sigma_scratch, Counters *ctr, int num_sms, cudaStream_t s);
+                     int64_t *sigma_scratch, int32_t *warp_rows, int32_t *block_rows, Counters *ctr, int num_sms,
+                     cudaStream_t s);
 
 // order-preserving dense renumbering of x[0..n) with ids in [0, idspace);
 // the number of distinct ids lands in *total

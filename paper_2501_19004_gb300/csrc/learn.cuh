@@ -37,6 +37,7 @@ __device__ __forceinline__ void learn_record(const LearnArgs &L, Counters *ctr, 
                                              long long Kid, long long best_s, int32_t best_c, long long s_d,
                                              bool moved) {
   if (!L.record) return;
+  if (L.min_degree > 0 && g.end[i] - g.begin[i] < L.min_degree) return;  // no features below the predictor's degree
   const float4 old = L.feat[i];
   if (L.trace_x && old.w > 0.f && (fmix32((uint32_t)i ^ L.trace_salt) & 0xFFFFu) < L.trace_keep) {
     const unsigned long long pos = atomicAdd(&ctr->trace_count, 1ull);

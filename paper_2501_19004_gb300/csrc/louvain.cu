@@ -437,6 +437,7 @@ LearnArgs learn_args(louvain_ctx *x, int pass, int t, bool skipping) {
   const double th = std::min(std::max((double)cfg.skip_threshold, 1e-6), 1.0 - 1e-6);
   L.thr_logit = (float)std::log(th / (1.0 - th));
   L.skip_clears = cfg.learned_skip_clears;
+  L.min_degree = cfg.learned_min_degree;
   L.t_norm = (float)t / (float)cfg.max_iterations;
   L.p_norm = (float)pass / (float)std::max(cfg.max_passes, 1);
   if (x->trace_x) {
@@ -679,10 +680,15 @@ louvain_status move_iteration(louvain_ctx *x, const GView &g, int wk, int pass, 
   return LOUVAIN_OK;
 }
 
+// Exact modularity of `memb` on g (Eq. 1).  The lists of long rows go to
+// rows[0..1] (g.n int32 each); by default two move-bin lists, which are free
+// whenever modularity is computed.
 louvain_status modularity_into(louvain_ctx *x, const GView &g, int wk, const int32_t *memb, const int64_t *sigma,
-                               int64_t *sigma_scratch, i128 *num, i128 *den) {
+                               int64_t *sigma_scratch, i128 *num, i128 *den, int32_t *const *rows = nullptr) {
   LV_CK(cudaMemsetAsync(&x->d_ctr->q_sin, 0, 3 * sizeof(unsigned long long), x->stream));
-  modularity_sums(g, wk, memb, sigma, sigma_scratch, x->d_ctr, x->num_sms, x->stream);
+  int32_t *warp_rows = rows ? rows[0] : x->bins[kBigBin];
+  int32_t *block_rows = rows ? rows[1] : x->bins[kClusterBin];
+  modularity_sums(g, wk, memb, sigma, sigma_scratch, warp_rows, block_rows, x->d_ctr, x->num_sms, x->stream);
   LV_CK(cudaGetLastError());
   louvain_status st = read_counters(x);
   if (st) return st;
@@ -1193,7 +1199,7 @@ louvain_status validate_config(const louvain_config *c) {
   if (c->mode != LOUVAIN_MODE_PLAIN && c->mode != LOUVAIN_MODE_LEARNED) return LOUVAIN_E_INVAL;
   if (c->mode == LOUVAIN_MODE_LEARNED && (!c->model || c->max_iterations > 127)) return LOUVAIN_E_INVAL;
   if (c->trace_capacity < 0 || c->learned_fallback < 0 || c->learned_fallback > 2) return LOUVAIN_E_INVAL;
-  if (c->table_window < 0) return LOUVAIN_E_INVAL;
+  if (c->table_window < 0 || c->learned_min_degree < 0) return LOUVAIN_E_INVAL;
   if (c->asynchronous != 0 && c->asynchronous != 1) return LOUVAIN_E_INVAL;
   if (c->asynchronous && (c->mode != LOUVAIN_MODE_PLAIN || c->trace_capacity > 0)) return LOUVAIN_E_INVAL;
   return LOUVAIN_OK;
@@ -1497,6 +1503,7 @@ void louvain_config_default(louvain_config *c) {
   c->learned_skip_clears = 0;
   c->table_window = 0;
   c->asynchronous = 0;
+  c->learned_min_degree = 0;
 }
 
 louvain_status louvain_create(const louvain_graph *graph, const louvain_config *cfg, void *stream, louvain_ctx **out) {
@@ -1609,7 +1616,7 @@ uint64_t fnv1a_words(const uint64_t *w, size_t n) {
 uint64_t config_fingerprint(const louvain_ctx *x) {
   const louvain_config &c = x->cfg;
   const bool learned = c.mode == LOUVAIN_MODE_LEARNED;
-  int64_t f[15] = {};
+  int64_t f[16] = {};
   f[0] = c.max_passes;
   f[1] = c.max_iterations;
   memcpy(&f[2], &c.tolerance, 8);
@@ -1626,6 +1633,7 @@ uint64_t config_fingerprint(const louvain_ctx *x) {
     f[11] = c.learned_fallback;
     f[12] = c.learned_skip_clears;
     f[13] = (int64_t)x->model_hash;
+    f[15] = c.learned_min_degree;
   }
   return fnv1a_bytes(f, sizeof f);
 }
@@ -2199,13 +2207,19 @@ louvain_status louvain_modularity_of(const louvain_graph *graph, const int32_t *
     cudaMemcpyAsync(dm, membership, (size_t)n * 4, cudaMemcpyHostToDevice, x->stream);
     memb = dm;
   }
-  if ((st = dalloc_n(x, &sig, std::max<int64_t>(n, 1)))) {
+  int32_t *rows = nullptr;
+  if ((st = dalloc_n(x, &sig, std::max<int64_t>(n, 1))) || (st = dalloc_n(x, &rows, 2 * std::max<int64_t>(n, 1)))) {
     louvain_destroy(x);
     return st;
   }
   i128 qn = 0, qd = 0;
   GView g{n, x->off0, x->off0 + 1, x->col0, x->w0};
-  if (n > 0) st = modularity_into(x, g, x->weighted ? W_U32 : W_UNIT, memb, nullptr, sig, &qn, &qd);
+  int32_t *const lists[2] = {rows, rows + n};
+  if (n > 0) st = modularity_into(x, g, x->weighted ? W_U32 : W_UNIT, memb, nullptr, sig, &qn, &qd, lists);
+  if (!st && (x->h_ctr->error & ERR_MEMB)) {
+    set_err(x, "membership id outside [0, n)");
+    st = LOUVAIN_E_INVAL;
+  }
   if (!st) {
     if (q) *q = qd ? (double)qn / (double)qd : 0.0;
     if (num) put128(num, qn);

@@ -92,7 +92,8 @@ __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
         const uint32_t h = fmix32(local ^ salt);
         const uint32_t bk = pow2 ? (h & (a.nbuckets - 1)) : (h % a.nbuckets);
         if (bk == a.bucket) {
-          if (a.learn.enabled && a.learn.feat[i].w > 0.f) {
+          if (a.learn.enabled && (a.learn.min_degree == 0 || a.g.end[i] - a.g.begin[i] >= a.learn.min_degree) &&
+              a.learn.feat[i].w > 0.f) {
             cand = true;  // the predictor decides (k_mlp_select); the flag stays until then
           } else {
             clear |= 0xFFull << (8 * v);

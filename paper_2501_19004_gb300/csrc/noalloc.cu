@@ -14,9 +14,16 @@
 // the array until the process exits.  All calls share it, so calls that
 // overlap on the GPU (other threads, other streams) race and give wrong
 // results; serialise them.  Each call clears the part it uses first.  The
-// first call on a device looks the array's device address up
-// (cudaGetSymbolAddress) and caches it; make that first call before any
-// stream capture begins.
+// first call on a device is its set-up: it loads the library's device code
+// there (which reserves the array), looks the array's device address up
+// (cudaGetSymbolAddress) and keeps it for the rest of the process.  Make
+// that first call before any stream capture begins and before the caller's
+// own pool claims the device's memory.
+//
+// The CSR is the caller's and is read without a prior validation pass, so
+// the kernel checks every row before it reads the row's entries:
+// 0 <= offsets[i] <= offsets[i+1] <= nnz, and offsets[0] = 0, offsets[n] =
+// nnz are read back first (two 8-byte copies into a host array).
 #include <cstdio>
 #include <mutex>
 
@@ -44,31 +51,33 @@ __global__ void k_na_clear(unsigned long long *scr, int64_t n) {
 }
 
 // Warp per vertex: S_in (entries inside the vertex's community, self-loops
-// once), 2m, and K_i added into Sigma of its community.  Ids out of range
-// set the error flag and are skipped.
-__global__ void k_na_rows(int64_t n, const int64_t *off, const int32_t *col, const int32_t *w, const int32_t *memb,
-                          unsigned long long *scr) {
+// once), 2m, and K_i added into Sigma of its community.  A row outside
+// [0, nnz) or with decreasing offsets, an id out of range or a non-positive
+// weight sets the error flag, and nothing of that row or entry is read
+// further or counted.
+__global__ void k_na_rows(int64_t n, int64_t nnz, const int64_t *off, const int32_t *col, const int32_t *w,
+                          const int32_t *memb, unsigned long long *scr) {
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int lane = threadIdx.x & 31;
   unsigned long long sin = 0, tot = 0, bad = 0;
   for (int64_t i = warp; i < n; i += nw) {
     const int32_t ci = memb[i];
-    if (ci < 0 || ci >= n) {
+    const int64_t rb = off[i], re = off[i + 1];
+    if (ci < 0 || ci >= n || rb < 0 || rb > re || re > nnz) {
       bad = 1;
       continue;
     }
     unsigned long long in = 0, k = 0;
-    for (int64_t e = off[i] + lane; e < off[i + 1]; e += 32) {
+    for (int64_t e = rb + lane; e < re; e += 32) {
       const int32_t j = col[e];
       const int32_t wi = w ? w[e] : 1;
-      if (wi <= 0) bad = 1;
-      const unsigned long long we = wi > 0 ? (unsigned long long)wi : 0ull;
-      k += we;
-      if (j < 0 || j >= n) {
+      if (wi <= 0 || j < 0 || j >= n) {
         bad = 1;
         continue;
       }
+      const unsigned long long we = (unsigned long long)wi;
+      k += we;
       if (memb[j] == ci) in += we;
     }
     in = warp_sum_u(in);
@@ -130,6 +139,7 @@ extern "C" louvain_status louvain_modularity_noalloc(const louvain_graph *graph,
       (graph->nnz > 0 && !graph->cols))
     return LOUVAIN_E_INVAL;
   if (graph->n > kNoAllocMaxVertices) return LOUVAIN_E_INVAL;  // beyond the fixed scratch array
+  if (graph->nnz < 0 || (graph->n == 0 && graph->nnz != 0)) return LOUVAIN_E_INVAL;
   const int64_t n = graph->n;
   cudaStream_t s = (cudaStream_t)stream;
   typedef __int128 i128;
@@ -137,17 +147,28 @@ extern "C" louvain_status louvain_modularity_noalloc(const louvain_graph *graph,
   if (n > 0) {
     unsigned long long *scr = nullptr;
     if (scratch_for_current_device(&scr) != cudaSuccess) return LOUVAIN_E_CUDA;
-    const int sms = 152;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      return LOUVAIN_E_CUDA;
+    // offsets[0] = 0 and offsets[n] = nnz (the kernel checks every row
+    // against [0, nnz) before it reads the row's entries)
+    int64_t ends[2] = {-1, -1};
+    if (cudaMemcpyAsync(&ends[0], graph->offsets, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&ends[1], graph->offsets + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      return LOUVAIN_E_CUDA;
+    if (ends[0] != 0 || ends[1] != graph->nnz) return LOUVAIN_E_INVAL;
     k_na_clear<<<grid_for(n + kNoAllocCounters + 1, 256, sms, 8), 256, 0, s>>>(scr, n);
-    k_na_rows<<<grid_for(n * 32, 256, sms, 16), 256, 0, s>>>(n, graph->offsets, graph->cols, graph->weights,
-                                                             membership, scr);
+    k_na_rows<<<grid_for(n * 32, 256, sms, 16), 256, 0, s>>>(n, graph->nnz, graph->offsets, graph->cols,
+                                                             graph->weights, membership, scr);
     k_na_sigma_sq<<<grid_for(n, 256, sms, 8), 256, 0, s>>>(n, scr);
     unsigned long long h[kNoAllocCounters + 1];
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(h, scr, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
       return LOUVAIN_E_CUDA;
-    if (h[4]) return LOUVAIN_E_INVAL;                   // an id out of range
+    if (h[4]) return LOUVAIN_E_INVAL;                   // a bad row, id or weight
     if (h[1] >= (1ull << 32)) return LOUVAIN_E_OVERFLOW;  // 2m too large for the squares
     const i128 two_m = (i128)h[1];
     num = two_m * (i128)h[0] - (((i128)h[3] << 32) + (i128)h[2]);

@@ -61,7 +61,8 @@ class LouvainConfig(ctypes.Structure):
                 ("record_pass_modularity", ctypes.c_int32), ("check_symmetry", ctypes.c_int32),
                 ("profile_mask", ctypes.c_uint32), ("trace_capacity", ctypes.c_int64), ("trace_rate", ctypes.c_float),
                 ("learned_fallback", ctypes.c_int32), ("learned_skip_clears", ctypes.c_int32),
-                ("table_window", ctypes.c_int64), ("asynchronous", ctypes.c_int32)]
+                ("table_window", ctypes.c_int64), ("asynchronous", ctypes.c_int32),
+                ("learned_min_degree", ctypes.c_int32)]
 
 
 _lib = None
@@ -169,6 +170,7 @@ class Config:
     learned_skip_clears: int = 0
     table_window: int = 0
     asynchronous: bool = False
+    learned_min_degree: int = 0
 
     def c(self) -> LouvainConfig:
         self._model_keep = None
@@ -181,7 +183,8 @@ class Config:
                              self.schedule_seed & (2**64 - 1), self.mode, mp, self.skip_threshold,
                              int(self.record_pass_modularity), int(self.check_symmetry), self.profile_mask,
                              self.trace_capacity, self.trace_rate, self.learned_fallback,
-                             self.learned_skip_clears, self.table_window, int(self.asynchronous))
+                             self.learned_skip_clears, self.table_window, int(self.asynchronous),
+                             self.learned_min_degree)
 
 
 @dataclass

@@ -25,10 +25,12 @@ MODEL_FILE = os.path.join(HERE, "predictor_rmat20-22.f32")
 TRAINING_GRAPHS = ((20, 101), (21, 102), (22, 103))
 
 
-def collect_traces(graph, cap: int = 4_000_000, rate: float = 0.25):
-    """(features [k][8] float32, labels [k] float32) from one plain run."""
+def collect_traces(graph, cap: int = 4_000_000, rate: float = 0.25, min_degree: int = 0):
+    """(features [k][8] float32, labels [k] float32) from one plain run; with
+    min_degree only vertices of at least that degree are recorded."""
     import torch
-    with lv.Louvain(lv.DeviceCSR.from_host(graph), lv.Config(trace_capacity=cap, trace_rate=rate)) as ctx:
+    cfg = lv.Config(trace_capacity=cap, trace_rate=rate, learned_min_degree=min_degree)
+    with lv.Louvain(lv.DeviceCSR.from_host(graph), cfg) as ctx:
         ctx.run()
         X, Y = lv.louvain_traces(ctx.ctx, cap)
     torch.cuda.synchronize()

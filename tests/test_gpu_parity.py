@@ -170,3 +170,20 @@ def test_errors_are_statuses_not_crashes():
         lv.louvain_modularity(ctx.ctx)
     assert ei.value.status == 7
     ctx.close()
+
+
+def test_modularity_of_refuses_membership_ids_out_of_range():
+    """An id outside [0, n) is refused with a status, on host and device
+    input, and nothing is written for it; a valid call afterwards still
+    agrees with the oracle."""
+    g = gg.rmat(10, 8, seed=3)
+    memb = (np.arange(g.n) % 13).astype(np.int32)
+    for bad_id in (-1, g.n, 2**31 - 1):
+        m = memb.copy()
+        m[7] = bad_id
+        for graph, mm in ((g, m), (lv.DeviceCSR.from_host(g), torch.from_numpy(m).cuda())):
+            with pytest.raises(lv.LouvainError) as ei:
+                lv.louvain_modularity_of(graph, mm)
+            assert ei.value.status == 1
+    q, num, den = lv.louvain_modularity_of(g, memb)
+    assert oracle.modularity(g, memb)[1:] == (num, den)
