@@ -4,8 +4,10 @@
 One step = one whole ``louvain_run`` (every pass of local moving and
 aggregation plus the final modularity) on a graph already resident in HBM.
 |E| counts both directions of every edge (directed CSR entries), as the
-paper's Table 2 does.  Default workload: R-MAT scale 24, edge factor 16,
-(a, b, c) = (0.57, 0.19, 0.19), seed 7, unit weights (synthetic).
+paper's Table 2 does.  Default workload: R-MAT scale 27, edge factor 16,
+(a, b, c) = (0.57, 0.19, 0.19), seed 13, unit weights (synthetic; 134M
+vertices, 4.2 billion entries), timed in the plain form (`value`) and in the
+learned-skip form (`learned_skip`) on the same graph and launch schedule.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -76,7 +78,7 @@ SAMPLES = {
 
 
 # timing groups that are one kernel per launch (candidates for the roofline)
-SINGLE_KERNELS = {"select", "move_thread", "move_group", "move_half", "move_xl", "move_cluster", "move_warp", "move_mid", "move_block", "move_hub", "apply",
+SINGLE_KERNELS = {"select", "move_thread", "move_group", "move_half", "move_wide", "move_warp", "move_mid", "move_block", "move_hub", "apply",
                   "pass_init", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big", "merge_xl", "merge_group",
                   "dendrogram"}
 
@@ -172,8 +174,8 @@ def move_bin_degrees(kernel: str, sched: dict):
     are not a degree bin of local moving."""
     gm, hm, wm = sched["group_max"], sched["half_max"], sched["warp_max"]
     return {"move_thread": [1, 16], "move_group": [17, gm], "move_half": [gm + 1, hm], "move_warp": [hm + 1, wm],
-            "move_mid": [wm + 1, 1024], "move_block": [1025, 4096], "move_xl": [4097, 8192],
-            "move_cluster": [8193, 32768], "move_hub": [32769, None]}.get(kernel)
+            "move_mid": [wm + 1, 1024], "move_block": [1025, 4096], "move_wide": [4097, 32768],
+            "move_hub": [32769, None]}.get(kernel)
 
 
 def max_over_ranks(x: float, world: int, device=None) -> float:
@@ -221,14 +223,13 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat24", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="rmat27", choices=sorted(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-skip leg")
     ap.add_argument("--no-async", action="store_true", help="skip the asynchronous-form leg")
-    ap.add_argument("--skip-threshold", type=float, default=0.8)
-    ap.add_argument("--skip-clears", type=int, default=1)
-    ap.add_argument("--learned-fallback", type=int, default=0)
+    ap.add_argument("--skip-threshold", type=float, default=None, help="default: the stored model's setting")
+    ap.add_argument("--learned-min-degree", type=int, default=None, help="default: the stored model's setting")
     ap.add_argument("--graphs", type=int, default=0, help="batch workloads: run only the first N graphs")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch schedule")
     ap.add_argument("--autotune-runs", type=int, default=32)
@@ -401,15 +402,21 @@ def main():
         if model is None:
             model, _ = predictor.train_default()
             source = "trained in this run (R-MAT 20-22 traces)"
-        lms, lres, lst = timed_leg(lv.Config(mode=lv.MODE_LEARNED, model=model, skip_threshold=args.skip_threshold,
-                                             learned_skip_clears=args.skip_clears,
-                                             learned_fallback=args.learned_fallback))
+        over = {}
+        if args.skip_threshold is not None:
+            over["skip_threshold"] = args.skip_threshold
+        if args.learned_min_degree is not None:
+            over["learned_min_degree"] = args.learned_min_degree
+        lcfg = predictor.default_config(model, **over)
+        lms, lres, lst = timed_leg(lcfg)
         learned = {"value": job_rate(g.nnz, args.steps, world, lms / 1e3), "unit": UNIT,
                    "ms_per_step": lms / args.steps, "modularity": lres.modularity,
-                   "dq_vs_plain": lres.modularity - res.modularity, "skip_threshold": args.skip_threshold,
-                   "skip_clears": args.skip_clears, "fallback": args.learned_fallback,
+                   "dq_vs_plain": lres.modularity - res.modularity, "skip_threshold": lcfg.skip_threshold,
+                   "min_degree": lcfg.learned_min_degree, "fallback": lcfg.learned_fallback,
+                   "skip_clears": lcfg.learned_skip_clears,
                    "evaluated": lst["evaluated"], "evaluated_plain": st["evaluated"], "skipped": lst["skipped"],
-                   "passes": lres.passes, "learned_passes": lst.get("learned_passes"), "model": source}
+                   "passes": lres.passes, "learned_passes": lst.get("learned_passes"), "model": source,
+                   "speedup_vs_plain": (lms and ms / lms)}
 
     # asynchronous form (moves applied at their decision; not reproducible)
     asynchronous = None

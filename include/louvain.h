@@ -54,8 +54,7 @@ typedef enum {
   LOUVAIN_E_HASH_OVERFLOW = 4,  /* a hashtable probe sequence exceeded its bound
                                    (the paper's "failed" result of Algorithm 7) */
   LOUVAIN_E_TIMEOUT = 5,        /* a bounded device-side wait gave up (reserved: no
-                                   kernel of this library waits on a flag; thread-block
-                                   clusters meet at hardware barriers) */
+                                   kernel of this library waits on a flag) */
   LOUVAIN_E_OVERFLOW = 6,       /* 2m >= 2^32: scores would not fit in int64 */
   LOUVAIN_E_STATE = 7           /* call out of order (e.g. memberships before run) */
 } louvain_status;
@@ -109,7 +108,13 @@ typedef struct {
                                        dQ <= tau (the plain rule);
                                     1: first over all vertices, until an iteration
                                        makes no move;
-                                    2: first over all vertices, until dQ <= tau */
+                                    2: first over all vertices, until dQ <= tau;
+                                    3: none; instead, when a learned iteration's
+                                       dQ <= tau, the vertices the predictor
+                                       skipped in it are evaluated at once (its
+                                       completion step, same iteration), and the
+                                       phase ends only if the iteration's dQ,
+                                       completion included, is still <= tau */
   int32_t learned_skip_clears;   /* LEARNED: 1 = a skip counts as a decision to stay
                                     and clears the vertex's flag (it returns when a
                                     neighbour moves); 0 = skipped vertices keep
@@ -232,9 +237,9 @@ louvain_status louvain_set_profile(louvain_ctx *ctx, uint32_t profile_mask);
  *       warp_max: largest degree handled by a warp (half_max .. 256; larger
  *       degrees up to 1024 go to 128-thread blocks);
  *   [3..11] blocks per SM of the local-moving kernels of the thread, warp,
- *       128-thread, 512-thread, hub (<= 3), 8-lane group, 1024-thread,
- *       4-block-cluster (the grid is rounded to whole clusters) and 16-lane
- *       group bins (1 .. 64);
+ *       128-thread, 512-thread, hub (<= 3), 8-lane group, wide (degrees
+ *       4097 .. 32768; its kernel runs one block per SM from a work queue and
+ *       ignores this word), a reserved word, and 16-lane group bins (1 .. 64);
  *   [12..18] blocks per SM of the aggregation kernels of the thread, warp,
  *       128-thread, 512-thread, big-community (<= 3), 1024-thread and group
  *       bins;
@@ -390,6 +395,17 @@ louvain_status louvain_mlp_train(float *params, const float *X, const float *Y, 
 
 /* Library build description (architecture, version). */
 const char *louvain_version(void);
+
+/* Longest probe sequence of a hashtable insert, the MAX_RETRIES of the
+ * paper's Algorithm 7 (hashtableAccumulate), after which the insert fails
+ * and the run returns LOUVAIN_E_HASH_OVERFLOW (Algorithm 7's "failed").
+ * Every table of this library holds at least twice as many slots as keys,
+ * so by default (max_probes = 0: no limit but the table size) no input
+ * fails; a small limit makes collisions fail, which exercises that failure
+ * path.  It applies on the current device to every later call, of every
+ * context, until changed.  A run that failed leaves the context usable:
+ * the next louvain_run starts from clean tables. */
+louvain_status louvain_set_probe_limit(uint32_t max_probes);
 
 #ifdef __cplusplus
 }

@@ -382,8 +382,7 @@ __global__ void __launch_bounds__(kNT) k_big_decide(BigArgs a, int r) {
       for (int64_t q = b + threadIdx.x; q < e; q += kNT) {
         const int32_t j = __ldg(a.g.col + q);
         if (j != i) {
-          a.flag[j] = 1;
-          learn_mark(a.learn, j);
+          mark_neighbour(a.flag, a.learn, j);
         }
       }
     __syncthreads();
@@ -486,5 +485,7 @@ void big_merge(const BigArgs &b, int wkind, int num_sms, cudaStream_t s, KernelP
   if (wkind == W_UNIT) big_rounds<MODE_MERGE, W_UNIT>(b, num_sms, s, prof);
   else big_rounds<MODE_MERGE, W_U32>(b, num_sms, s, prof);
 }
+
+cudaError_t set_probe_limit_big(uint32_t v) { return set_probe_limit_here(v); }
 
 }  // namespace lv

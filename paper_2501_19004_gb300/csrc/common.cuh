@@ -40,6 +40,7 @@ enum ErrBits : unsigned long long { ERR_HASH = 1ull, ERR_RANGE = 2ull, ERR_TIMEO
 struct Counters {
   unsigned long long bin_count[9];  // local-moving bin sizes of the current bucket (one per move bin)
   unsigned long long movers;        // decisions to move in this bucket
+  unsigned long long wide_next;     // work queue of the wide bin: next list position to take
   // ---- zeroed every iteration ----
   unsigned long long it_gain_lo;    // sum of low 32 bits of the gains
   unsigned long long it_gain_hi;    // sum of high 32 bits of the gains
@@ -62,6 +63,8 @@ struct Counters {
   unsigned long long cand_count;    // learned mode: candidates of the bucket for the predictor
   unsigned long long trace_count;   // recorded (features, moved) samples
   unsigned long long mod_count[2];  // modularity: rows handed to warps / to whole blocks
+  unsigned long long descents[2];   // validation: adjacent entries with col[k-1] >= col[k] (all / at row starts)
+  unsigned long long skip_listed;   // learned mode: vertices the predictor skipped in the current iteration
 };
 constexpr int kIterCounterWords = 5 + 45;
 

@@ -32,18 +32,22 @@ __host__ __device__ __forceinline__ int degree_bin(int64_t d) {
 constexpr int kGroupLanes = 8;
 constexpr int kGroupMaxDeg = 64;  // kGroupLanes lanes x 8 entries
 constexpr int kGroupBin = 5;
-// Local moving also splits the big bin: 4096 < degree <= kXlMaxDeg goes to
-// one 1024-thread block with a 16384-slot shared table (144 KB); only larger
-// degrees use global tables.
+// Local moving also splits the big bin: 4096 < degree <= kWideMaxDeg goes to
+// the wide bin, one 1024-thread block with a 16384-slot shared table that
+// holds only the entries whose community is not a known singleton (at most
+// kWideCap distinct keys; beyond that the block's own global table of
+// kWideSpill slots takes over); only larger degrees use the chunked global
+// tables.  When aggregating, communities of total member degree (4096,
+// kXlMaxDeg] take one 1024-thread block with a 16384-slot table (144 KB).
 constexpr int kXlMaxDeg = 8192;
 constexpr int kXlCap = 16384;
 constexpr int kXlBin = 6;
-// Hubs of degree (kXlMaxDeg, kClusterMaxDeg] go to a thread-block cluster of
-// kClusterSize 1024-thread blocks whose shared tables form one distributed
-// table of kClusterSize * kXlCap slots (distributed shared memory).
-constexpr int kClusterSize = 4;
-constexpr int kClusterMaxDeg = kXlMaxDeg * kClusterSize;
-constexpr int kClusterBin = 7;
+constexpr int kWideMaxDeg = 32768;
+constexpr int kWideCap = 12288;   // keys a wide vertex keeps in shared memory
+constexpr int kWideSpill = 65536; // slots of a wide block's global table (2 x kWideMaxDeg)
+// Bin 7 takes no vertices (its list serves as scratch for the modularity
+// rows; its schedule word is kept so that schedules keep their layout).
+constexpr int kSpareBin = 7;
 // Degrees (group_max, half_max] go to groups of 16 lanes (two vertices per
 // warp, rows of up to 128 entries).
 constexpr int kHalfLanes = 16;
@@ -86,6 +90,21 @@ struct Sched {
 };
 constexpr int kSchedWords = 3 + kMoveBins + kMergeBins + 2;
 
+// Flag byte of a vertex: kFlagUnproc = not processed since a neighbour moved
+// (vertex pruning, Sec. 4.1.6); kFlagTracked = the learned predictor keeps
+// its features (set at pass start, kept by every later write).
+constexpr uint8_t kFlagUnproc = 0x01;
+constexpr uint8_t kFlagTracked = 0x02;
+constexpr unsigned long long kFlagUnproc8 = 0x0101010101010101ull;  // kFlagUnproc in each of 8 bytes
+
+// Per-vertex byte of the pass (pass_init): the move bin in the low six bits
+// (kVbinNone for degree 0) and kVbinTracked when the learned predictor keeps
+// features for the vertex (degree at least its minimum; only then do
+// neighbour moves count for it).
+constexpr uint8_t kVbinBinMask = 0x3F;
+constexpr uint8_t kVbinNone = 0x3F;
+constexpr uint8_t kVbinTracked = 0x40;
+
 // Side streams for concurrent bin kernels (created with the context).
 constexpr int kSideStreams = 3;
 struct SideStreams {
@@ -101,8 +120,7 @@ __host__ __device__ __forceinline__ int move_bin(int64_t d, int group_max, int h
   if (d <= warp_max) return 1;
   if (d <= kMidMaxDeg) return 2;
   if (d <= kBlockMaxDeg) return 3;
-  if (d <= kXlMaxDeg) return kXlBin;
-  return d <= kClusterMaxDeg ? kClusterBin : kBigBin;
+  return d <= kWideMaxDeg ? kXlBin : kBigBin;
 }
 
 // Global tables of big items (hub vertices in local moving, communities with
@@ -171,6 +189,8 @@ struct LearnArgs {
   float thr_logit = 0.f;        // evaluate iff logit >= thr_logit
   int skip_clears = 0;          // a skip clears the flag (counts as "stay")
   int64_t min_degree = 0;       // only vertices of at least this degree are candidates and keep features
+  int32_t *skip_list = nullptr; // [n] vertices skipped in the current iteration (count in ctr->skip_listed)
+  const uint8_t *vbin = nullptr; // [n] per-vertex byte of the pass (kVbinTracked: features kept)
   float t_norm = 0.f, p_norm = 0.f;
   float *trace_x = nullptr;     // [cap][8] recorded features
   float *trace_y = nullptr;     // [cap] recorded labels (moved)
@@ -256,15 +276,26 @@ struct MoveArgs {
   BatchView batch;
   Sched sched;
   const uint32_t *iter = nullptr;  // graph replay: device words {salt, pickless} of the iteration
-  const uint8_t *vbin = nullptr;   // [n'] move bin of every vertex this pass (0xFF: degree 0)
+  const uint8_t *vbin = nullptr;   // [n'] move bin of every vertex this pass (kVbinNone: degree 0), kVbinTracked bit
   int async_apply = 0;             // asynchronous form: movers apply their move at once (emit_move)
+  // Known singletons (wide bin): bit c of `recv` is set once any vertex has
+  // moved into community c this pass (k_apply sets it for every target).  A
+  // neighbour j with C'[j] = j and bit j clear is alone in its community, so
+  // with rows free of repeated columns (`solo`) its weight is K_{i->j}.
+  uint32_t *recv = nullptr;        // [n'/32 + 1], cleared at every pass start
+  int solo = 0;                    // 1: rows hold no repeated column and recv is maintained
+  // Completion step of a learned iteration: the vertices of sel_list (count
+  // *sel_count) are evaluated instead of a bucket's flagged vertices.
+  const int32_t *sel_list = nullptr;
+  const unsigned long long *sel_count = nullptr;
+  unsigned long long *wide_spill = nullptr;  // [SMs][kWideSpill] global tables of the wide bin, kept empty
 };
 
 // Kernel identifiers for the optional per-kernel event timing.
 enum KernelId : int {
   K_SELECT = 0, K_MOVE_THREAD, K_MOVE_WARP, K_MOVE_MID, K_MOVE_BLOCK, K_MOVE_HUB, K_APPLY, K_PASS_INIT,
   K_COMM_COUNT, K_SCATTER, K_MERGE_THREAD, K_MERGE_WARP, K_MERGE_MID, K_MERGE_BLOCK, K_MERGE_BIG, K_DENDRO,
-  K_MODULARITY, K_RENUMBER, K_MOVE_HUB_EVAL, K_MERGE_BIG_EMIT, K_MLP_SELECT, K_MOVE_GROUP, K_MOVE_XL, K_MERGE_XL, K_MOVE_CLUSTER, K_MERGE_GROUP, K_MOVE_HALF, K_NUM_KERNELS
+  K_MODULARITY, K_RENUMBER, K_MOVE_HUB_EVAL, K_MERGE_BIG_EMIT, K_MLP_SELECT, K_MOVE_GROUP, K_MOVE_XL, K_MERGE_XL, K_MERGE_GROUP, K_MOVE_HALF, K_NUM_KERNELS
 };
 extern const char *const kKernelNames[K_NUM_KERNELS];
 
@@ -311,6 +342,8 @@ void pass_init(const GView &g, int wkind, int first_pass, int64_t *K, int64_t *S
                uint8_t *vbin = nullptr, const Sched *sched = nullptr);
 
 void iota_i32(int32_t *x, int64_t n, int num_sms, cudaStream_t s);
+// every vertex unprocessed (the tracked bits kept)
+void flag_all(uint8_t *flag, int64_t n, int num_sms, cudaStream_t s);
 
 // aggregation phase
 struct AggArgs {
@@ -395,6 +428,11 @@ void batch_gather(const int64_t *src, const int64_t *idx, int64_t m, int64_t *ou
 void batch_final(int64_t n0, int32_t *C, const int32_t *ogid, const int32_t *Cp, const int64_t *newid,
                  const int64_t *vo, const int8_t *fin, int32_t *out, int num_sms, cudaStream_t s);
 void batch_exclude(int64_t n, const int32_t *gid, const int8_t *fin, int32_t *Cp, int num_sms, cudaStream_t s);
+
+// Probe limit of the table inserts of each translation unit (tables.cuh).
+cudaError_t set_probe_limit_move(uint32_t v);
+cudaError_t set_probe_limit_aggr(uint32_t v);
+cudaError_t set_probe_limit_big(uint32_t v);
 
 // Kernel launches issued by this thread since the last reset (the library's
 // own kernels only; memsets and copies are not counted).

@@ -63,11 +63,23 @@ __device__ __forceinline__ void learn_record(const LearnArgs &L, Counters *ctr, 
   L.marks[i] = 0;
 }
 
-// Moves of the current bucket count for the neighbours' next evaluation: they
-// go to marks_next, which the next selection folds into marks, so a
-// decision never sees marks that change while its bucket runs.
-__device__ __forceinline__ void learn_mark(const LearnArgs &L, int32_t j) {
-  if (L.record) atomicAdd(L.marks_next + j, 1u);
+// A mover's neighbour j: marked unprocessed (vertex pruning, bit kFlagUnproc
+// of its flag byte) and, when features are kept, the move counts for j's
+// next evaluation.  Moves go to marks_next, which the next selection folds
+// into marks, so a decision never sees marks that change while its bucket
+// runs.  When only vertices of some minimum degree keep features, their
+// flag bytes carry kFlagTracked (set at pass start): the byte is read and
+// written back, one sector as for the plain store, and only tracked
+// neighbours pay the atomic.
+__device__ __forceinline__ void mark_neighbour(uint8_t *flag, const LearnArgs &L, int32_t j) {
+  if (L.record && L.min_degree > 0) {
+    const uint8_t f = flag[j];
+    flag[j] = (uint8_t)(f | kFlagUnproc);
+    if (f & kFlagTracked) atomicAdd(L.marks_next + j, 1u);
+  } else {
+    flag[j] = kFlagUnproc;
+    if (L.record) atomicAdd(L.marks_next + j, 1u);
+  }
 }
 
 }  // namespace lv

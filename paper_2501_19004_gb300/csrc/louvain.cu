@@ -24,6 +24,7 @@
 #include <numeric>
 
 #include "../../include/louvain.h"
+#include "exact.cuh"
 #include "internal.h"
 #include "mlp.cuh"
 
@@ -69,6 +70,9 @@ struct louvain_ctx {
   int64_t *K = nullptr, *Kalt = nullptr, *Sigma = nullptr;
   uint8_t *flag = nullptr;
   uint8_t *vbin = nullptr;  // move bin per vertex of the current pass
+  uint32_t *recv = nullptr; // bit c: some vertex moved into community c this pass (known singletons)
+  unsigned long long *wide_spill = nullptr;  // [SMs][kWideSpill] global tables of the wide bin (kept empty)
+  bool rows_unique = false; // the input's rows are strictly increasing (no repeated column)
   // local moving
   int32_t *bins[kMoveBins] = {};
   int32_t *mv_vertex = nullptr, *mv_target = nullptr;
@@ -89,6 +93,7 @@ struct louvain_ctx {
   float4 *feat = nullptr;
   uint32_t *marks = nullptr, *marks_next = nullptr;
   int32_t *cand = nullptr;
+  int32_t *skip_list = nullptr;  // learned: vertices skipped in the current iteration
   float *trace_x = nullptr, *trace_y = nullptr;
   int64_t trace_count = 0;
   std::vector<std::array<long long, 3>> learned_log;  // per pass: learned iterations, fallback iterations, last moves
@@ -110,6 +115,10 @@ struct louvain_ctx {
   int passes = 0, exit_reason = 0;
   std::vector<int64_t> iter_stats, pass_stats;
   std::vector<PassTiming> timing;
+  // iteration starts of every pass (iter_ev[p * (max_iterations + 1) + t]),
+  // and the end of its local-moving phase at t = l_i; created on first use
+  std::vector<cudaEvent_t> iter_ev;
+  std::vector<int> iter_timed;  // per pass: iterations timed one by one (0: the phase as a whole)
   cudaEvent_t run0 = nullptr, run1 = nullptr;
   double run_ms = 0;
   long long it_total = 0, moves_total = 0, evaluated_total = 0, skipped_total = 0;
@@ -134,6 +143,17 @@ struct louvain_ctx {
   bool graph_broken = false;         // a capture failed: direct launches for the rest of the run
   uint32_t *d_iter = nullptr;        // {salt, pickless} read by the kernels under replay
   uint32_t *h_iter = nullptr;        // pinned
+  // device-controlled local-moving phase (sched.graphs = 2): one graph per
+  // pass whose conditional while node repeats the iteration until the
+  // device-side tolerance test ends it
+  cudaGraphExec_t pexec = nullptr;
+  int pexec_pass = -1;               // pass the phase graph was captured for
+  bool phase_broken = false;         // a capture failed: host control for the rest of the run
+  long long phase_launches = 0;      // kernels per iteration of the phase graph
+  int32_t *d_phase = nullptr;        // {current iteration, iterations performed}
+  unsigned long long *d_rec = nullptr;  // [max_iterations][kIterCounterWords] per-iteration counters
+  int32_t *h_phase = nullptr;        // pinned copies
+  unsigned long long *h_rec = nullptr;
 
   // batched runs: G graphs as one union graph (batch.cu)
   bool batched = false;
@@ -144,6 +164,8 @@ struct louvain_ctx {
   int32_t *b_gid = nullptr, *b_ogid = nullptr, *b_out = nullptr;
   int64_t *b_vo = nullptr, *b_bound = nullptr;
   long long *b_two_m = nullptr;
+  int32_t *b_li = nullptr;              // [G] iterations of each graph's moving phase (device-controlled phase)
+  int32_t *h_li = nullptr;              // pinned copy
   int8_t *b_moving = nullptr, *b_sel = nullptr;
   unsigned long long *b_acc = nullptr;  // [6][G]: gain lo, gain hi, moves, S_in, Sigma^2 lo, Sigma^2 hi
   unsigned long long *h_acc = nullptr;  // pinned copies
@@ -208,15 +230,23 @@ void release_pool_threshold(int device) {
   done[device] = true;
 }
 
-// Warp per row: offsets non-decreasing, columns in range, weights positive;
-// the weight total 2m goes to ctr->q_sin.
 // Input validation: offsets non-decreasing (thread per row), then every
 // entry's column in [0, n) and weight > 0, with the weights summed into 2m
 // (thread per entry, coalesced); per-warp reductions before the atomics.
-__global__ void k_validate_rows(int64_t n, const int64_t *off, Counters *ctr) {
+// Both kernels also count descents, adjacent entries with col[k-1] >=
+// col[k]: all of them (entries) and those where k starts a non-empty row
+// (rows).  Every row is strictly increasing, so holds no repeated column,
+// exactly when the two counts agree (descents[0] == descents[1]).
+__global__ void k_validate_rows(int64_t n, const int64_t *off, const int32_t *col, Counters *ctr) {
   bool bad = false;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    if (off[i + 1] < off[i]) bad = true;
+  unsigned long long starts = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = off[i], e = off[i + 1];
+    if (e < b) bad = true;
+    else if (b > 0 && e > b && col[b - 1] >= col[b]) ++starts;  // b - 1 ends the previous non-empty row
+  }
+  starts = warp_sum_u(starts);
+  if ((threadIdx.x & 31) == 0 && starts) atomicAdd(&ctr->descents[1], starts);
   if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(&ctr->error, (unsigned long long)ERR_RANGE);
 }
 
@@ -226,20 +256,99 @@ __global__ void k_validate_rows(int64_t n, const int64_t *off, Counters *ctr) {
 template <typename WT>
 __global__ void k_validate_entries(int64_t nnz, int64_t n, const int32_t *col, const WT *w, Counters *ctr) {
   bool bad = false;
-  unsigned long long wsum = 0;
+  unsigned long long wsum = 0, desc = 0;
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x) {
     const int32_t c = col[k];
     if (c < 0 || c >= n) bad = true;
+    if (k > 0 && col[k - 1] >= c) ++desc;
     const WT ww = w ? w[k] : WT(1);
     if (ww <= WT(0)) bad = true;
     wsum += (unsigned long long)(ww > WT(0) ? ww : WT(0));
   }
   wsum = warp_sum_u(wsum);
+  desc = warp_sum_u(desc);
   const bool any_bad = __any_sync(0xFFFFFFFFu, bad);
   if ((threadIdx.x & 31) == 0) {
     if (any_bad) atomicOr(&ctr->error, (unsigned long long)ERR_RANGE);
     if (wsum) atomicAdd(&ctr->q_sin, wsum);
+    if (desc) atomicAdd(&ctr->descents[0], desc);
   }
+}
+
+// End of one local-moving iteration when the whole phase runs under device
+// control (a conditional while node): the iteration's counters are kept in
+// rec[t], the tolerance test of Algorithm 2 is taken with the host's exact
+// arithmetic (the 128-bit gain, correctly rounded conversions, one double
+// division), and either the next iteration's salt and Pick-Less flag are
+// set or the loop ends (phase[1] = iterations performed).
+struct PhaseStep {
+  long long two_m;
+  double tau;
+  int max_it, pass, rho;
+  uint64_t seed;
+};
+__global__ void k_phase_step(const Counters *ctr, uint32_t *iter, int32_t *phase, unsigned long long *rec, PhaseStep p,
+                             cudaGraphConditionalHandle handle) {
+  const int t = phase[0];
+  const unsigned long long *w = &ctr->it_gain_lo;
+  for (int k = threadIdx.x; k < kIterCounterWords; k += blockDim.x) rec[(size_t)t * kIterCounterWords + k] = w[k];
+  if (threadIdx.x != 0) return;
+  const unsigned long long glo = ctr->it_gain_lo, ghi = ctr->it_gain_hi;
+  const unsigned long long lo = glo + (ghi << 32);                 // gain = ghi 2^32 + glo
+  const unsigned long long hi = (ghi >> 32) + (lo < glo ? 1ull : 0ull);
+  const unsigned long long tlo = lo << 1, thi = (hi << 1) | (lo >> 63);  // 2 gain
+  const unsigned long long den2 = (unsigned long long)p.two_m * (unsigned long long)p.two_m;  // (2m)^2 < 2^64
+  const double total = den2 ? u128_to_double(thi, tlo) / u128_to_double(0, den2) : 0.0;
+  const bool stop = total <= p.tau || t + 1 >= p.max_it;
+  if (stop) {
+    phase[1] = t + 1;
+  } else {
+    phase[0] = t + 1;
+    iter[0] = bucket_salt(p.pass, t + 1, p.seed);
+    iter[1] = (p.rho > 0 && ((t + 1 + p.rho / 2) % p.rho) == 0) ? 1u : 0u;
+  }
+  cudaGraphSetConditional(handle, stop ? 0u : 1u);
+}
+
+// The same for a batch: every graph still moving takes its own tolerance
+// test with its own 2m (its gain sums in gain_lo/gain_hi); a graph that
+// meets it stops moving (moving[k] = 0, li[k] = t + 1).  The loop ends when
+// no graph moves or at the iteration cap.  One block.
+__global__ void __launch_bounds__(1024) k_batch_phase_step(const Counters *ctr, uint32_t *iter, int32_t *phase,
+                                                           unsigned long long *rec, PhaseStep p,
+                                                           const unsigned long long *gain_lo,
+                                                           const unsigned long long *gain_hi,
+                                                           const long long *two_m, int8_t *moving, int32_t *li,
+                                                           int64_t G, cudaGraphConditionalHandle handle) {
+  const int t = phase[0];
+  const unsigned long long *w = &ctr->it_gain_lo;
+  for (int k = threadIdx.x; k < kIterCounterWords; k += blockDim.x) rec[(size_t)t * kIterCounterWords + k] = w[k];
+  bool any = false;
+  for (int64_t k = threadIdx.x; k < G; k += blockDim.x) {
+    if (!moving[k]) continue;
+    const unsigned long long glo = gain_lo[k], ghi = gain_hi[k];
+    const unsigned long long lo = glo + (ghi << 32);
+    const unsigned long long hi = (ghi >> 32) + (lo < glo ? 1ull : 0ull);
+    const unsigned long long den2 = (unsigned long long)two_m[k] * (unsigned long long)two_m[k];
+    const double total = den2 ? u128_to_double((hi << 1) | (lo >> 63), lo << 1) / u128_to_double(0, den2) : 0.0;
+    if (total <= p.tau) {
+      moving[k] = 0;
+      li[k] = t + 1;
+    } else {
+      any = true;
+    }
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x != 0) return;
+  const bool stop = !any || t + 1 >= p.max_it;
+  if (stop) {
+    phase[1] = t + 1;
+  } else {
+    phase[0] = t + 1;
+    iter[0] = bucket_salt(p.pass, t + 1, p.seed);
+    iter[1] = (p.rho > 0 && ((t + 1 + p.rho / 2) % p.rho) == 0) ? 1u : 0u;
+  }
+  cudaGraphSetConditional(handle, stop ? 0u : 1u);
 }
 
 // Rows of a holey CSR copied to consecutive positions (row i to off[i]),
@@ -348,7 +457,7 @@ louvain_status read_counters(louvain_ctx *x) {
   LV_CK(cudaMemcpyAsync(x->h_ctr, x->d_ctr, sizeof(Counters), cudaMemcpyDeviceToHost, x->stream));
   LV_CK(cudaStreamSynchronize(x->stream));
   if (x->h_ctr->error & ERR_HASH) {
-    set_err(x, "hashtable probe bound exceeded (table sizing error)");
+    set_err(x, "a hashtable insert exceeded its probe limit (the failed result of Algorithm 7)");
     return LOUVAIN_E_HASH_OVERFLOW;
   }
   return LOUVAIN_OK;
@@ -390,7 +499,6 @@ void account_move(louvain_ctx *x, int64_t n, const Counters &h) {
     }
     const int kid = b == kGroupBin     ? K_MOVE_GROUP
                     : b == kXlBin      ? K_MOVE_XL
-                    : b == kClusterBin ? K_MOVE_CLUSTER
                     : b == kHalfBin    ? K_MOVE_HALF
                                        : K_MOVE_THREAD + b;
     x->kbytes[kid] += 40.0 * w[0] + (8.0 + wb) * w[1] + 8.0 * w[2] + 8.0 * w[3] + 1.0 * w[4];
@@ -438,6 +546,8 @@ LearnArgs learn_args(louvain_ctx *x, int pass, int t, bool skipping) {
   L.thr_logit = (float)std::log(th / (1.0 - th));
   L.skip_clears = cfg.learned_skip_clears;
   L.min_degree = cfg.learned_min_degree;
+  L.vbin = x->vbin;
+  if (cfg.learned_fallback == 3) L.skip_list = x->skip_list;
   L.t_norm = (float)t / (float)cfg.max_iterations;
   L.p_norm = (float)pass / (float)std::max(cfg.max_passes, 1);
   if (x->trace_x) {
@@ -451,16 +561,181 @@ LearnArgs learn_args(louvain_ctx *x, int pass, int t, bool skipping) {
   return L;
 }
 
-// One iteration of the local-moving phase (all buckets); fills *h.
+// One iteration of the local-moving phase (all buckets); fills *h.  With
+// `completion`, the completion step of learned iteration t instead: the
+// vertices the predictor skipped in it are evaluated, and the counts and gain
+// are added to iteration t's record.
 louvain_status move_iteration(louvain_ctx *x, const GView &g, int wk, int pass, int t, bool skipping,
-                              const Counters **h_out);
+                              const Counters **h_out, bool completion = false);
 louvain_status begin_run(louvain_ctx *x);
 
-// Local-moving phase (Algorithm 5) under the bucket schedule; returns l_i.
-// Learned mode: iterations with the predictor until the tolerance is met,
-// then a full plain sweep and plain iterations until one makes no move.
-louvain_status move_phase(louvain_ctx *x, const GView &g, int wk, int pass, double tau, int *li_out) {
+louvain_status enqueue_iteration(louvain_ctx *x, const GView &g, int wk, int pass, int t, bool skipping,
+                                 const uint32_t *iter, bool completion);
+void record_iteration(louvain_ctx *x, const GView &g, int pass, int t, const Counters &h, bool completion);
+louvain_status mark_iteration(louvain_ctx *x, int pass, int t);
+
+// The phase graph of a pass: a conditional while node whose body is one
+// local-moving iteration (the kernels read the salt and Pick-Less flag from
+// x->d_iter) followed by k_phase_step, which ends the loop on the device.
+// A capture that fails sets phase_broken (host control from then on).
+louvain_status capture_phase(louvain_ctx *x, const GView &g, int wk, int pass, double tau) {
   const louvain_config &cfg = x->cfg;
+  cudaStream_t s = x->stream;
+  louvain_status st;
+  if (!x->d_iter) {
+    if ((st = dalloc_n(x, &x->d_iter, 2))) return st;
+    if (cudaMallocHost((void **)&x->h_iter, 2 * sizeof(uint32_t)) != cudaSuccess) {
+      set_err(x, "pinned allocation failed");
+      return LOUVAIN_E_NOMEM;
+    }
+  }
+  if (!x->d_phase) {
+    const size_t words = (size_t)cfg.max_iterations * kIterCounterWords;
+    if ((st = dalloc_n(x, &x->d_phase, 2)) || (st = dalloc_n(x, &x->d_rec, (int64_t)words))) return st;
+    if (cudaMallocHost((void **)&x->h_phase, 2 * sizeof(int32_t)) != cudaSuccess ||
+        cudaMallocHost((void **)&x->h_rec, words * sizeof(unsigned long long)) != cudaSuccess) {
+      set_err(x, "pinned allocation failed");
+      return LOUVAIN_E_NOMEM;
+    }
+  }
+  if (x->pexec) {
+    cudaGraphExecDestroy(x->pexec);
+    x->pexec = nullptr;
+  }
+  cudaGraph_t graph = nullptr;
+  cudaGraphConditionalHandle handle;
+  cudaGraphNodeParams cp{};
+  cudaGraphNode_t node;
+  bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess &&
+            cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  if (ok) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    ok = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp) == cudaSuccess;
+  }
+  const long long l0 = g_launches;
+  if (ok) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      st = enqueue_iteration(x, g, wk, pass, 0, false, x->d_iter, false);
+      const PhaseStep ps{x->two_m, tau, cfg.max_iterations, pass, cfg.pickless_period, cfg.schedule_seed};
+      if (x->batched)
+        LV_LAUNCH(k_batch_phase_step<<<1, 1024, 0, s>>>(x->d_ctr, x->d_iter, x->d_phase, x->d_rec, ps,
+                                                         x->bview.gain_lo, x->bview.gain_hi, x->b_two_m, x->b_moving,
+                                                         x->b_li, x->G, handle));
+      else
+        LV_LAUNCH(k_phase_step<<<1, 64, 0, s>>>(x->d_ctr, x->d_iter, x->d_phase, x->d_rec, ps, handle));
+      cudaGraph_t captured = nullptr;
+      ok = cudaStreamEndCapture(s, &captured) == cudaSuccess && st == LOUVAIN_OK;
+    }
+  }
+  x->phase_launches = g_launches - l0;
+  g_launches = l0;
+  if (ok) ok = cudaGraphInstantiate(&x->pexec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  if (!ok) {
+    cudaGetLastError();
+    if (x->pexec) cudaGraphExecDestroy(x->pexec);
+    x->pexec = nullptr;
+    x->phase_broken = true;
+    return LOUVAIN_OK;
+  }
+  x->pexec_pass = pass;
+  return LOUVAIN_OK;
+}
+
+// The local-moving phase of a plain pass under device control: one graph
+// launch, one synchronisation, then the per-iteration records (for a batch
+// also each graph's iteration count, in x->h_li; the caller has set every
+// graph's moving flag and b_li = max_iterations).
+louvain_status device_phase(louvain_ctx *x, const GView &g, int wk, int pass, double tau, int *li_out) {
+  const louvain_config &cfg = x->cfg;
+  louvain_status st;
+  if (x->pexec_pass != pass && (st = capture_phase(x, g, wk, pass, tau))) return st;
+  if (x->phase_broken) return LOUVAIN_OK;
+  const int rho = cfg.pickless_period;
+  x->h_iter[0] = bucket_salt(pass, 0, cfg.schedule_seed);
+  x->h_iter[1] = (rho > 0 && ((0 + rho / 2) % rho) == 0) ? 1u : 0u;
+  LV_CK(cudaMemcpyAsync(x->d_iter, x->h_iter, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice, x->stream));
+  LV_CK(cudaMemsetAsync(x->d_phase, 0, 2 * sizeof(int32_t), x->stream));
+  if ((size_t)pass < x->iter_timed.size()) x->iter_timed[pass] = 0;  // timed as a whole
+  if ((st = mark_iteration(x, pass, 0))) return st;
+  LV_CK(cudaGraphLaunch(x->pexec, x->stream));
+  LV_CK(cudaMemcpyAsync(x->h_phase, x->d_phase, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, x->stream));
+  LV_CK(cudaMemcpyAsync(x->h_rec, x->d_rec, (size_t)cfg.max_iterations * kIterCounterWords * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToHost, x->stream));
+  if (x->batched)
+    LV_CK(cudaMemcpyAsync(x->h_li, x->b_li, (size_t)x->G * sizeof(int32_t), cudaMemcpyDeviceToHost, x->stream));
+  if ((st = read_counters(x))) return st;  // synchronises; hashtable errors of any iteration
+  const int li = x->h_phase[1];
+  if (li < 1 || li > cfg.max_iterations) {
+    set_err(x, "device-controlled local moving ended after %d iterations", li);
+    return LOUVAIN_E_CUDA;
+  }
+  g_launches += x->phase_launches * li;
+  for (int t = 0; t < li; ++t) {
+    Counters h{};
+    memcpy(&h.it_gain_lo, x->h_rec + (size_t)t * kIterCounterWords, kIterCounterWords * sizeof(unsigned long long));
+    record_iteration(x, g, pass, t, h, false);
+  }
+  *li_out = li;
+  return LOUVAIN_OK;
+}
+
+// Event at iteration t of pass p (t = l_i: the end of the phase).
+louvain_status mark_iteration(louvain_ctx *x, int pass, int t) {
+  const size_t k = (size_t)pass * (x->cfg.max_iterations + 1) + t;
+  if (k >= x->iter_ev.size()) return LOUVAIN_OK;
+  if (!x->iter_ev[k]) LV_CK(cudaEventCreate(&x->iter_ev[k]));
+  LV_CK(cudaEventRecord(x->iter_ev[k], x->stream));
+  return LOUVAIN_OK;
+}
+
+// Local-moving phase (Algorithm 5) under the bucket schedule; returns l_i.
+// Plain single-graph runs with sched.graphs = 2 run it under device control
+// (device_phase); the result is the same as the host-controlled loop's.
+// Learned mode with completion (learned_fallback 3): iterations with the
+// predictor; when an iteration's gain meets the tolerance, the vertices it
+// skipped are evaluated at once (its completion step, gains added to the
+// iteration's), and the phase ends only if the iteration's total still
+// meets it: the plain stopping rule, checked on every vertex the iteration
+// would have evaluated without the predictor.  Learned mode otherwise:
+// iterations with the predictor until the tolerance is met, then plain
+// iterations (learned_fallback 0, 1, 2).
+louvain_status move_phase_impl(louvain_ctx *x, const GView &g, int wk, int pass, double tau, int *li_out) {
+  const louvain_config &cfg = x->cfg;
+  if (cfg.mode == LOUVAIN_MODE_LEARNED && cfg.learned_fallback == 3) {
+    const i128 den2 = (i128)x->two_m * x->two_m;
+    int li = cfg.max_iterations;
+    long long completions = 0, last_moves = -1;
+    for (int t = 0; t < cfg.max_iterations; ++t) {
+      const Counters *h;
+      louvain_status st = move_iteration(x, g, wk, pass, t, true, &h);
+      if (st) return st;
+      i128 gain = ((i128)h->it_gain_hi << 32) + (i128)h->it_gain_lo;
+      last_moves = (long long)h->it_moves;
+      double total = den2 ? (double)(2 * gain) / (double)den2 : 0.0;
+      if (total > tau) continue;
+      if (h->skip_listed > 0) {  // the completion step judges the iteration
+        const Counters *hc;
+        if ((st = move_iteration(x, g, wk, pass, t, false, &hc, true))) return st;
+        ++completions;
+        last_moves += (long long)hc->it_moves;
+        gain += ((i128)hc->it_gain_hi << 32) + (i128)hc->it_gain_lo;
+        total = den2 ? (double)(2 * gain) / (double)den2 : 0.0;
+      }
+      if (total <= tau) {
+        li = t + 1;
+        break;
+      }
+    }
+    x->learned_log.push_back({(long long)li, completions, last_moves});
+    *li_out = li;
+    return LOUVAIN_OK;
+  }
   if (cfg.mode == LOUVAIN_MODE_LEARNED) {
     const i128 den2 = (i128)x->two_m * x->two_m;
     int t = 0;
@@ -481,7 +756,7 @@ louvain_status move_phase(louvain_ctx *x, const GView &g, int wk, int pass, doub
     // until an iteration makes no move
     const int learned_iters = t;
     long long last_moves = -1;
-    if (cfg.learned_fallback != 0) LV_CK(cudaMemsetAsync(x->flag, 1, (size_t)g.n, x->stream));
+    if (cfg.learned_fallback != 0) flag_all(x->flag, g.n, x->num_sms, x->stream);
     for (int f = 0; f < cfg.max_iterations; ++f, ++t) {
       const Counters *h;
       louvain_status st = move_iteration(x, g, wk, pass, t, false, &h);
@@ -497,6 +772,11 @@ louvain_status move_phase(louvain_ctx *x, const GView &g, int wk, int pass, doub
     x->learned_log.push_back({(long long)learned_iters, (long long)(t - learned_iters), last_moves});
     *li_out = t;
     return LOUVAIN_OK;
+  }
+  if (x->sched.graphs == 2 && !x->batched && !x->prof.mask && !x->trace_x && !x->phase_broken &&
+      cfg.mode == LOUVAIN_MODE_PLAIN) {
+    louvain_status st = device_phase(x, g, wk, pass, tau, li_out);
+    if (st || !x->phase_broken) return st;
   }
   const i128 den2 = (i128)x->two_m * x->two_m;
   int li = cfg.max_iterations;
@@ -516,17 +796,46 @@ louvain_status move_phase(louvain_ctx *x, const GView &g, int wk, int pass, doub
   return LOUVAIN_OK;
 }
 
+louvain_status move_phase(louvain_ctx *x, const GView &g, int wk, int pass, double tau, int *li_out) {
+  if ((size_t)pass < x->iter_timed.size()) x->iter_timed[pass] = 1;
+  louvain_status st = move_phase_impl(x, g, wk, pass, tau, li_out);
+  if (st) return st;
+  return mark_iteration(x, pass, *li_out);
+}
+
+// Bookkeeping of one iteration from its counters: bytes per kernel, the
+// per-iteration record (added to iteration t's with `completion`), totals.
+void record_iteration(louvain_ctx *x, const GView &g, int pass, int t, const Counters &h, bool completion) {
+  const louvain_config &cfg = x->cfg;
+  const i128 gain = ((i128)h.it_gain_hi << 32) + (i128)h.it_gain_lo;
+  account_move(x, g.n, h);
+  if (pass < cfg.max_passes && t < cfg.max_iterations) {
+    int64_t *r = &x->iter_stats[((size_t)pass * cfg.max_iterations + t) * 4];
+    i128 g0 = 0;
+    if (completion) g0 = ((i128)r[2] << 64) + (i128)(uint64_t)r[3];
+    r[0] = (completion ? r[0] : 0) + (int64_t)h.it_evaluated;
+    r[1] = (completion ? r[1] : 0) + (int64_t)h.it_moves;
+    put128(r + 2, g0 + gain);
+  }
+  if (!completion) x->it_total += 1;
+  x->moves_total += (long long)h.it_moves;
+  x->evaluated_total += (long long)h.it_evaluated;
+  x->skipped_total += (long long)h.it_skipped;
+}
+
 // Launches of one local-moving iteration (all buckets) on x->stream; with
 // `iter` the kernels read the salt and Pick-Less flag from device memory and
 // the hub path launches its rounds without asking (graph capture).
 louvain_status enqueue_iteration(louvain_ctx *x, const GView &g, int wk, int pass, int t, bool skipping,
-                                 const uint32_t *iter) {
+                                 const uint32_t *iter, bool completion) {
   const louvain_config &cfg = x->cfg;
   {
     const int rho = cfg.pickless_period;
-    const LearnArgs L = learn_args(x, pass, t, skipping && t > 0);
+    const LearnArgs L = learn_args(x, pass, t, skipping && t > 0 && !completion);
     const int pickless = rho > 0 && ((t + rho / 2) % rho) == 0;
     LV_CK(cudaMemsetAsync(&x->d_ctr->it_gain_lo, 0, kIterCounterWords * sizeof(unsigned long long), x->stream));
+    if (L.enabled && L.skip_list)
+      LV_CK(cudaMemsetAsync(&x->d_ctr->skip_listed, 0, sizeof(unsigned long long), x->stream));
     if (x->batched) LV_CK(cudaMemsetAsync(x->b_acc, 0, 3 * (size_t)x->G * sizeof(unsigned long long), x->stream));
     MoveArgs a{};
     a.g = g;
@@ -549,6 +858,15 @@ louvain_status enqueue_iteration(louvain_ctx *x, const GView &g, int wk, int pas
     a.sched = x->sched;
     a.iter = iter;
     a.vbin = x->vbin;
+    a.recv = x->recv;
+    a.wide_spill = x->wide_spill;
+    // known singletons need rows without repeated columns: super-vertex rows
+    // have none, the input's were checked by louvain_create
+    a.solo = !cfg.asynchronous && (pass > 0 || x->rows_unique);
+    if (completion) {
+      a.sel_list = x->skip_list;
+      a.sel_count = &x->d_ctr->skip_listed;
+    }
     BigArgs big{};
     big.g = g;
     big.Cp = x->Cp;
@@ -577,7 +895,7 @@ louvain_status enqueue_iteration(louvain_ctx *x, const GView &g, int wk, int pas
     big.accum_blocks = x->sched.move[kBigBin];
     big.iter = iter;
     big.static_rounds = iter != nullptr;
-    for (int b = 0; b < nbuckets; ++b) {
+    for (int b = 0; b < (completion ? 1 : nbuckets); ++b) {
       LV_CK(cudaMemsetAsync(x->d_ctr, 0, offsetof(Counters, it_gain_lo), x->stream));
       if (L.enabled) LV_CK(cudaMemsetAsync(&x->d_ctr->cand_count, 0, sizeof(unsigned long long), x->stream));
       a.bucket = (uint32_t)b;
@@ -606,7 +924,7 @@ louvain_status capture_iteration(louvain_ctx *x, const GView &g, int wk, int pas
     x->graph_broken = true;
     return LOUVAIN_OK;
   }
-  louvain_status st = enqueue_iteration(x, g, wk, pass, 0, false, x->d_iter);
+  louvain_status st = enqueue_iteration(x, g, wk, pass, 0, false, x->d_iter, false);
   const cudaError_t ec = cudaStreamEndCapture(s, &graph);
   x->graph_launches = g_launches - l0;
   g_launches = l0;
@@ -639,11 +957,15 @@ louvain_status capture_iteration(louvain_ctx *x, const GView &g, int wk, int pas
 }
 
 louvain_status move_iteration(louvain_ctx *x, const GView &g, int wk, int pass, int t, bool skipping,
-                              const Counters **h_out) {
+                              const Counters **h_out, bool completion) {
   const louvain_config &cfg = x->cfg;
+  if (!completion) {
+    louvain_status st = mark_iteration(x, pass, t);
+    if (st) return st;
+  }
   {
     const bool replay = x->sched.graphs && !x->graph_broken && !x->prof.mask && cfg.mode == LOUVAIN_MODE_PLAIN &&
-                        !x->trace_x;
+                        !x->trace_x && !completion;  // graphs = 2 reaches here only when the phase graph is unusable
     louvain_status st0;
     if (replay && x->graph_pass != pass && (st0 = capture_iteration(x, g, wk, pass))) return st0;
     if (replay && !x->graph_broken) {
@@ -653,7 +975,7 @@ louvain_status move_iteration(louvain_ctx *x, const GView &g, int wk, int pass, 
       LV_CK(cudaMemcpyAsync(x->d_iter, x->h_iter, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice, x->stream));
       LV_CK(cudaGraphLaunch(x->gexec, x->stream));
       g_launches += x->graph_launches;
-    } else if ((st0 = enqueue_iteration(x, g, wk, pass, t, skipping, nullptr))) {
+    } else if ((st0 = enqueue_iteration(x, g, wk, pass, t, skipping, nullptr, completion))) {
       return st0;
     }
     LV_CK(cudaGetLastError());
@@ -662,20 +984,8 @@ louvain_status move_iteration(louvain_ctx *x, const GView &g, int wk, int pass, 
                             x->stream));
     louvain_status st = read_counters(x);
     if (st) return st;
-    const Counters &h = *x->h_ctr;
-    const i128 gain = ((i128)h.it_gain_hi << 32) + (i128)h.it_gain_lo;
-    account_move(x, g.n, h);
-    if (pass < cfg.max_passes && t < cfg.max_iterations) {
-      int64_t *r = &x->iter_stats[((size_t)pass * cfg.max_iterations + t) * 4];
-      r[0] = (int64_t)h.it_evaluated;
-      r[1] = (int64_t)h.it_moves;
-      put128(r + 2, gain);
-    }
-    x->it_total += 1;
-    x->moves_total += (long long)h.it_moves;
-    x->evaluated_total += (long long)h.it_evaluated;
-    x->skipped_total += (long long)h.it_skipped;
-    *h_out = &h;
+    record_iteration(x, g, pass, t, *x->h_ctr, completion);
+    *h_out = x->h_ctr;
   }
   return LOUVAIN_OK;
 }
@@ -687,7 +997,7 @@ louvain_status modularity_into(louvain_ctx *x, const GView &g, int wk, const int
                                int64_t *sigma_scratch, i128 *num, i128 *den, int32_t *const *rows = nullptr) {
   LV_CK(cudaMemsetAsync(&x->d_ctr->q_sin, 0, 3 * sizeof(unsigned long long), x->stream));
   int32_t *warp_rows = rows ? rows[0] : x->bins[kBigBin];
-  int32_t *block_rows = rows ? rows[1] : x->bins[kClusterBin];
+  int32_t *block_rows = rows ? rows[1] : x->bins[kSpareBin];
   modularity_sums(g, wk, memb, sigma, sigma_scratch, warp_rows, block_rows, x->d_ctr, x->num_sms, x->stream);
   LV_CK(cudaGetLastError());
   louvain_status st = read_counters(x);
@@ -706,6 +1016,8 @@ louvain_status begin_run(louvain_ctx *x) {
   x->ran = false;
   x->graph_pass = -1;  // every pass captures its own iteration graph
   x->graph_broken = false;
+  x->pexec_pass = -1;
+  x->phase_broken = false;
   x->iter_stats.assign((size_t)std::max(cfg.max_passes, 1) * cfg.max_iterations * 4, 0);
   x->pass_stats.assign((size_t)std::max(cfg.max_passes, 1) * 6, 0);
   x->it_total = x->moves_total = x->evaluated_total = x->skipped_total = 0;
@@ -836,6 +1148,8 @@ louvain_status run_impl(louvain_ctx *x, bool fresh = true, int32_t budget = 0, i
     x->suspended = false;
     x->graph_pass = -1;
     x->graph_broken = false;
+    x->pexec_pass = -1;
+    x->phase_broken = false;
     LV_CK(cudaEventRecord(x->run0, s));
   }
   if (x->big_dirty && x->big.slots > 0) {  // a failed run may have left table entries behind
@@ -869,6 +1183,7 @@ louvain_status run_impl(louvain_ctx *x, bool fresh = true, int32_t budget = 0, i
     {
       const LearnArgs L = learn_args(x, p, 0, false);
       pass_init(g, wk, p == 0, x->K, x->Sigma, x->Cp, x->flag, x->d_ctr, x->num_sms, s, &L, x->vbin, &x->sched);
+      LV_CK(cudaMemsetAsync(x->recv, 0, (size_t)(g.n / 32 + 1) * sizeof(uint32_t), s));  // every community a singleton
     }
     x->prof.end(K_PASS_INIT, s);
     LV_CK(cudaGetLastError());
@@ -1034,6 +1349,7 @@ louvain_status run_batched(louvain_ctx *x) {
     LV_CK(cudaMemsetAsync(&x->d_ctr->big_slots, 0, 2 * sizeof(unsigned long long), s));
     x->prof.begin(K_PASS_INIT, s);
     pass_init(g, wk, p == 0, x->K, x->Sigma, x->Cp, x->flag, x->d_ctr, x->num_sms, s, nullptr, x->vbin, &x->sched);
+    LV_CK(cudaMemsetAsync(x->recv, 0, (size_t)(g.n / 32 + 1) * sizeof(uint32_t), s));  // every community a singleton
     x->prof.end(K_PASS_INIT, s);
     LV_CK(cudaGetLastError());
     if ((st = read_counters(x))) return st;
@@ -1048,7 +1364,18 @@ louvain_status run_batched(louvain_ctx *x) {
     }
     LV_CK(cudaMemcpyAsync(x->b_moving, x->h_flags, (size_t)G, cudaMemcpyHostToDevice, s));
     int li_union = 0;
-    for (int t = 0; t < cfg.max_iterations; ++t) {
+    bool device_done = false;
+    if (x->sched.graphs == 2 && !x->prof.mask && !x->phase_broken) {  // per-graph tests on the device
+      for (int64_t k = 0; k < G; ++k) x->h_li[k] = cfg.max_iterations;
+      LV_CK(cudaMemcpyAsync(x->b_li, x->h_li, (size_t)G * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+      if ((st = device_phase(x, g, wk, p, tau, &li_union))) return st;
+      if (!x->phase_broken) {
+        device_done = true;
+        for (int64_t k = 0; k < G; ++k)
+          if (mv[k]) li[k] = x->h_li[k];
+      }
+    }
+    for (int t = 0; t < cfg.max_iterations && !device_done; ++t) {
       const Counters *h;
       if ((st = move_iteration(x, g, wk, p, t, false, &h))) return st;
       li_union = t + 1;
@@ -1198,7 +1525,7 @@ louvain_status validate_config(const louvain_config *c) {
   if (!(c->tolerance >= 0) || !(c->tolerance_drop > 0) || !(c->aggregation_tolerance >= 0)) return LOUVAIN_E_INVAL;
   if (c->mode != LOUVAIN_MODE_PLAIN && c->mode != LOUVAIN_MODE_LEARNED) return LOUVAIN_E_INVAL;
   if (c->mode == LOUVAIN_MODE_LEARNED && (!c->model || c->max_iterations > 127)) return LOUVAIN_E_INVAL;
-  if (c->trace_capacity < 0 || c->learned_fallback < 0 || c->learned_fallback > 2) return LOUVAIN_E_INVAL;
+  if (c->trace_capacity < 0 || c->learned_fallback < 0 || c->learned_fallback > 3) return LOUVAIN_E_INVAL;
   if (c->table_window < 0 || c->learned_min_degree < 0) return LOUVAIN_E_INVAL;
   if (c->asynchronous != 0 && c->asynchronous != 1) return LOUVAIN_E_INVAL;
   if (c->asynchronous && (c->mode != LOUVAIN_MODE_PLAIN || c->trace_capacity > 0)) return LOUVAIN_E_INVAL;
@@ -1310,7 +1637,7 @@ louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg
   if (cudaMemsetAsync(x->d_ctr, 0, sizeof(Counters), x->stream)) return fail(LOUVAIN_E_CUDA);
   // validation and 2m
   if (n > 0) {
-    LV_LAUNCH(k_validate_rows<<<grid_for(n, 256, x->num_sms, 8), 256, 0, x->stream>>>(n, x->off0, x->d_ctr));
+    LV_LAUNCH(k_validate_rows<<<grid_for(n, 256, x->num_sms, 8), 256, 0, x->stream>>>(n, x->off0, x->col0, x->d_ctr));
     if (nnz > 0)
       LV_LAUNCH(k_validate_entries<int32_t><<<grid_for(nnz, 256, x->num_sms, 8), 256, 0, x->stream>>>(nnz, n, x->col0, x->w0,
                                                                                             x->d_ctr));
@@ -1341,6 +1668,7 @@ louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg
       return fail(LOUVAIN_E_INVAL);
     }
     x->two_m = (long long)x->h_ctr->q_sin;
+    x->rows_unique = x->h_ctr->descents[0] == x->h_ctr->descents[1];
     if (!batched && (unsigned long long)x->two_m >= (1ull << 32)) {  // a batch checks each graph's 2m
       set_err(x, "total weight 2m = %lld is 2^32 or more; int64 scores would overflow", x->two_m);
       return fail(LOUVAIN_E_OVERFLOW);
@@ -1354,8 +1682,11 @@ louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg
   // per-vertex state and work arrays
   if ((st = dalloc_n(x, &x->C, nv)) || (st = dalloc_n(x, &x->Cp, nv)) || (st = dalloc_n(x, &x->K, nv)) ||
       (st = dalloc_n(x, &x->Kalt, nv)) || (st = dalloc_n(x, &x->Sigma, nv)) || (st = dalloc_n(x, &x->flag, nv)) ||
-      (st = dalloc_n(x, &x->vbin, nv)))
+      (st = dalloc_n(x, &x->vbin, nv)) || (st = dalloc_n(x, &x->recv, nv / 32 + 1)) ||
+      (st = dalloc_n(x, &x->wide_spill, (int64_t)x->num_sms * kWideSpill)))
     return fail(st);
+  if (cudaMemsetAsync(x->wide_spill, 0, (size_t)x->num_sms * kWideSpill * sizeof(unsigned long long), x->stream))
+    return fail(LOUVAIN_E_CUDA);
   for (int k = 0; k < kMoveBins; ++k)
     if ((st = dalloc_n(x, &x->bins[k], nv))) return fail(st);
   if ((st = dalloc_n(x, &x->mv_vertex, nv)) || (st = dalloc_n(x, &x->mv_target, nv))) return fail(st);
@@ -1374,7 +1705,9 @@ louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg
       return fail(st);
   }
   if (cfg->mode == LOUVAIN_MODE_LEARNED) {
-    if ((st = dalloc_n(x, &x->cand, nv)) || (st = dalloc_n(x, &x->mlp, (int64_t)kMlpParams))) return fail(st);
+    if ((st = dalloc_n(x, &x->cand, nv)) || (st = dalloc_n(x, &x->skip_list, nv)) ||
+        (st = dalloc_n(x, &x->mlp, (int64_t)kMlpParams)))
+      return fail(st);
     if (cudaMemcpyAsync(x->mlp, cfg->model, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, x->stream)) {
       set_err(x, "copy of the model parameters failed");
       return fail(LOUVAIN_E_CUDA);
@@ -1387,6 +1720,8 @@ louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg
       return fail(st);
   }
   x->timing.resize((size_t)std::max(cfg->max_passes, 1));
+  x->iter_ev.assign((size_t)std::max(cfg->max_passes, 1) * (cfg->max_iterations + 1), nullptr);
+  x->iter_timed.assign((size_t)std::max(cfg->max_passes, 1), 0);
   for (auto &pt : x->timing) {
     if (cudaEventCreate(&pt.t0) || cudaEventCreate(&pt.t1) || cudaEventCreate(&pt.t2)) {
       set_err(x, "event creation failed");
@@ -1442,7 +1777,7 @@ louvain_status setup_batch(louvain_ctx *x, const int64_t *vo, int64_t G) {
   if ((st = dalloc_n(x, &x->b_gid, nv)) || (st = dalloc_n(x, &x->b_ogid, nv)) || (st = dalloc_n(x, &x->b_out, nv)) ||
       (st = dalloc_n(x, &x->b_vo, G + 1)) || (st = dalloc_n(x, &x->b_bound, G + 1)) ||
       (st = dalloc_n(x, &x->b_two_m, G)) || (st = dalloc_n(x, &x->b_moving, G)) || (st = dalloc_n(x, &x->b_sel, G)) ||
-      (st = dalloc_n(x, &x->b_acc, 6 * G)))
+      (st = dalloc_n(x, &x->b_acc, 6 * G)) || (st = dalloc_n(x, &x->b_li, G)) || (st = pinned_n(x, &x->h_li, G)))
     return st;
   if ((st = pinned_n(x, &x->h_acc, 6 * G)) || (st = pinned_n(x, &x->h_bound, G + 1)) ||
       (st = pinned_n(x, &x->h_flags, G)))
@@ -1884,8 +2219,22 @@ louvain_status louvain_stats(const louvain_ctx *xc, char *json, size_t cap) {
     if (x->timing[p].aggregated) cudaEventElapsedTime(&b, x->timing[p].t1, x->timing[p].t2);
     tm += a;
     ta += b;
-    snprintf(buf, sizeof buf, "%s{\"move_ms\": %.4f, \"aggregate_ms\": %.4f}", p ? ", " : "", a, b);
+    snprintf(buf, sizeof buf, "%s{\"move_ms\": %.4f, \"aggregate_ms\": %.4f, \"iteration_ms\": [", p ? ", " : "",
+             a, b);
     per += buf;
+    // local-moving time per iteration (completion steps included); a phase
+    // under device control is one entry
+    const int li = (int)x->pass_stats[(size_t)p * 6 + 2];
+    const int steps = ((size_t)p < x->iter_timed.size() && x->iter_timed[p]) ? li : 1;
+    const size_t base = (size_t)p * (x->cfg.max_iterations + 1);
+    for (int t = 0; t < steps && x->timing[p].timed; ++t) {
+      const size_t k0 = base + t, k1 = base + (steps == li ? t + 1 : li);
+      float it = 0;
+      if (k1 < x->iter_ev.size() && x->iter_ev[k0] && x->iter_ev[k1]) cudaEventElapsedTime(&it, x->iter_ev[k0], x->iter_ev[k1]);
+      snprintf(buf, sizeof buf, "%s%.4f", t ? ", " : "", it);
+      per += buf;
+    }
+    per += "]}";
   }
   per += "]";
   snprintf(buf, sizeof buf, "\"move_ms\": %.4f, \"aggregate_ms\": %.4f, \"other_ms\": %.4f, ", tm, ta,
@@ -1962,7 +2311,7 @@ static bool sched_from_words(const int32_t *w, Sched *s) {
   for (int b = 0; b < kMergeBins; ++b)
     if (t.merge[b] < 1 || t.merge[b] > 64) return false;
   if (t.move[kBigBin] > 3 || t.merge[kBigBin] > 3) return false;  // accumulation: 3 blocks per SM at most
-  if (t.graphs != 0 && t.graphs != 1) return false;
+  if (t.graphs < 0 || t.graphs > 2) return false;
   if (t.concurrent != 0 && t.concurrent != 1) return false;
   *s = t;
   return true;
@@ -2075,8 +2424,8 @@ louvain_status louvain_autotune(louvain_ctx *x, int32_t max_runs, char *json, si
       mg_best[b] = 1e30;
       mg_arg[b] = best.merge[b];
     }
-    static const int mv_kid[kMoveBins] = {K_MOVE_THREAD, K_MOVE_WARP, K_MOVE_MID,     K_MOVE_BLOCK, K_MOVE_HUB,
-                                          K_MOVE_GROUP,  K_MOVE_XL,   K_MOVE_CLUSTER, K_MOVE_HALF};
+    static const int mv_kid[kMoveBins] = {K_MOVE_THREAD, K_MOVE_WARP, K_MOVE_MID, K_MOVE_BLOCK, K_MOVE_HUB,
+                                          K_MOVE_GROUP,  K_MOVE_XL,   -1,         K_MOVE_HALF};
     static const int mg_kid[kMergeBins] = {K_MERGE_THREAD, K_MERGE_WARP, K_MERGE_MID,   K_MERGE_BLOCK,
                                            K_MERGE_BIG,    K_MERGE_XL,   K_MERGE_GROUP};
     for (int v : cands) {
@@ -2087,7 +2436,7 @@ louvain_status louvain_autotune(louvain_ctx *x, int32_t max_runs, char *json, si
       if ((st = run_once(t, true, &ms))) goto fail;
       note("blocks", t, ms);
       for (int b = 0; b < kMoveBins; ++b)
-        if (x->prof.launches[mv_kid[b]] > 0 && x->prof.ms[mv_kid[b]] < mv_best[b]) {
+        if (mv_kid[b] >= 0 && x->prof.launches[mv_kid[b]] > 0 && x->prof.ms[mv_kid[b]] < mv_best[b]) {
           mv_best[b] = x->prof.ms[mv_kid[b]];
           mv_arg[b] = t.move[b];
         }
@@ -2121,9 +2470,10 @@ louvain_status louvain_autotune(louvain_ctx *x, int32_t max_runs, char *json, si
         best = t;
       }
     }
-    if (runs < max_runs) {
+    for (int gm = 0; gm <= 2; ++gm) {  // graph replay: none, per iteration, whole phase under device control
+      if (runs >= max_runs || gm == best.graphs) continue;
       Sched t = best;
-      t.graphs = best.graphs ? 0 : 1;
+      t.graphs = gm;
       if ((st = run_once(t, false, &ms))) goto fail;
       note("graphs", t, ms);
       if (ms < best_ms) {
@@ -2176,6 +2526,11 @@ void louvain_destroy(louvain_ctx *x) {
   if (x->side.fork) cudaEventDestroy(x->side.fork);
   if (x->h_iter) cudaFreeHost(x->h_iter);
   if (x->gexec) cudaGraphExecDestroy(x->gexec);
+  if (x->pexec) cudaGraphExecDestroy(x->pexec);
+  for (cudaEvent_t e : x->iter_ev)
+    if (e) cudaEventDestroy(e);
+  if (x->h_phase) cudaFreeHost(x->h_phase);
+  if (x->h_rec) cudaFreeHost(x->h_rec);
   if (x->plan_done) cudaEventDestroy(x->plan_done);
   for (void *p : x->pinned) cudaFreeHost(p);
   delete x;
@@ -2345,5 +2700,15 @@ louvain_status louvain_mlp_train(float *params, const float *X, const float *Y, 
 }
 
 const char *louvain_version(void) { return "gb300-louvain 0.1 (sm_103a)"; }
+
+louvain_status louvain_set_probe_limit(uint32_t max_probes) {
+  const uint32_t v = max_probes ? max_probes : 0xFFFFFFFFu;
+  if (set_probe_limit_move(v) != cudaSuccess || set_probe_limit_aggr(v) != cudaSuccess ||
+      set_probe_limit_big(v) != cudaSuccess) {
+    set_err(nullptr, "could not set the probe limit on the current device");
+    return LOUVAIN_E_CUDA;
+  }
+  return LOUVAIN_OK;
+}
 
 }  // extern "C"

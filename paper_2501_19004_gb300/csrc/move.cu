@@ -20,7 +20,6 @@
 #include <climits>
 
 #include <algorithm>
-#include <cooperative_groups.h>
 
 #include "internal.h"
 #include "learn.cuh"
@@ -54,7 +53,8 @@ __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
     unsigned long long fl = 0, vbw = 0;
     if (whole) {
       fl = *reinterpret_cast<const unsigned long long *>(a.flag + i0);
-      if (fl && a.vbin) vbw = *reinterpret_cast<const unsigned long long *>(a.vbin + i0);
+      if (((fl & kFlagUnproc8) || a.learn.record) && a.vbin)
+        vbw = *reinterpret_cast<const unsigned long long *>(a.vbin + i0);
     } else {
 #pragma unroll
       for (int v = 0; v < kSelVPT; ++v)
@@ -74,14 +74,18 @@ __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
       const int64_t i = i0 + v;
       vb[v] = -1;
       bool cand = false;
-      if (a.learn.record && i < n) {  // the previous bucket's neighbour moves
+      const unsigned vbyte = (unsigned)((vbw >> (8 * v)) & 0xFFull);
+      const bool tracked = a.learn.min_degree == 0 ||
+                           (a.vbin ? (vbyte & kVbinTracked) != 0
+                                   : (i < n && a.g.end[i] - a.g.begin[i] >= a.learn.min_degree));
+      if (a.learn.record && i < n && tracked) {  // the previous bucket's neighbour moves
         const uint32_t mn = a.learn.marks_next[i];
         if (mn) {
           a.learn.marks[i] += mn;
           a.learn.marks_next[i] = 0;
         }
       }
-      bool live = ((fl >> (8 * v)) & 0xFFull) != 0;
+      bool live = ((fl >> (8 * v)) & (unsigned long long)kFlagUnproc) != 0;
       uint32_t local = (uint32_t)i;
       if (live && a.batch.gid) {  // batched: only graphs still moving, hashed by their local ids
         const int32_t gg = a.batch.gid[i];
@@ -92,16 +96,15 @@ __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
         const uint32_t h = fmix32(local ^ salt);
         const uint32_t bk = pow2 ? (h & (a.nbuckets - 1)) : (h % a.nbuckets);
         if (bk == a.bucket) {
-          if (a.learn.enabled && (a.learn.min_degree == 0 || a.g.end[i] - a.g.begin[i] >= a.learn.min_degree) &&
-              a.learn.feat[i].w > 0.f) {
+          if (a.learn.enabled && tracked && a.learn.feat[i].w > 0.f) {
             cand = true;  // the predictor decides (k_mlp_select); the flag stays until then
           } else {
-            clear |= 0xFFull << (8 * v);
+            clear |= (unsigned long long)kFlagUnproc << (8 * v);
             ++nsel;
             int b = -1;
             if (a.vbin) {
-              const unsigned byte = (unsigned)((vbw >> (8 * v)) & 0xFFull);
-              if (byte != 0xFFu) b = (int)byte;
+              const unsigned byte = vbyte & kVbinBinMask;
+              if (byte != kVbinNone) b = (int)byte;
             } else {
               const int64_t deg = a.g.end[i] - a.g.begin[i];
               if (deg > 0) b = move_bin(deg, a.sched.group_max, a.sched.half_max, a.sched.warp_max);
@@ -131,7 +134,7 @@ __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
       } else {
 #pragma unroll
         for (int v = 0; v < kSelVPT; ++v)
-          if ((clear >> (8 * v)) & 0xFFull) a.flag[i0 + v] = 0;
+          if ((clear >> (8 * v)) & 0xFFull) a.flag[i0 + v] &= (uint8_t)~kFlagUnproc;
       }
     }
     // per bin: this thread's offset within the warp, the warp's offset
@@ -171,6 +174,45 @@ __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
   }
 }
 
+// ------------------------------------------------------------ list select
+// Completion step of a learned iteration: every vertex of sel_list is
+// evaluated (its flag cleared) and sorted into its degree bin.
+__global__ void __launch_bounds__(256) k_select_list(MoveArgs a) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long cnt = *a.sel_count;
+  unsigned long long evaluated = 0;
+  for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x; base < cnt;
+       base += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long idx = base + threadIdx.x;
+    int bin = -1;
+    int32_t i = -1;
+    if (idx < cnt) {
+      i = a.sel_list[idx];
+      a.flag[i] &= (uint8_t)~kFlagUnproc;
+      ++evaluated;
+      if (a.vbin) {
+        const unsigned byte = a.vbin[i] & kVbinBinMask;
+        if (byte != kVbinNone) bin = (int)byte;
+      } else {
+        const int64_t deg = a.g.end[i] - a.g.begin[i];
+        if (deg > 0) bin = move_bin(deg, a.sched.group_max, a.sched.half_max, a.sched.warp_max);
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < kMoveBins; ++b) {
+      const unsigned m = __ballot_sync(kFull, bin == b);
+      if (!m) continue;
+      const int leader = __ffs(m) - 1;
+      unsigned long long pos = 0;
+      if (lane == leader) pos = atomicAdd(&a.ctr->bin_count[b], (unsigned long long)__popc(m));
+      pos = __shfl_sync(kFull, pos, leader);
+      if (bin == b) a.bins[b][pos + __popc(m & lanemask_lt())] = i;
+    }
+  }
+  evaluated = warp_sum_u(evaluated);
+  if (lane == 0 && evaluated) atomicAdd(&a.ctr->it_evaluated, evaluated);
+}
+
 // ------------------------------------------------------------ learned select
 // One warp per 16 candidates: features, the BF16 MLP on the tensor cores, and
 // the skip decision.  Evaluated vertices are marked processed and binned;
@@ -207,13 +249,24 @@ __global__ void __launch_bounds__(256) k_mlp_select(MoveArgs a) {
     const bool eval = mine >= 0 && logit >= a.learn.thr_logit;
     int bin = -1;
     if (eval) {
-      a.flag[mine] = 0;
+      a.flag[mine] &= (uint8_t)~kFlagUnproc;
       const int64_t deg = a.g.end[mine] - a.g.begin[mine];
       if (deg > 0) bin = move_bin(deg, a.sched.group_max, a.sched.half_max, a.sched.warp_max);
       ++evaluated;
     } else if (mine >= 0) {
       ++skipped;
-      if (a.learn.skip_clears) a.flag[mine] = 0;
+      if (a.learn.skip_clears) a.flag[mine] &= (uint8_t)~kFlagUnproc;
+    }
+    if (a.learn.skip_list) {  // the iteration's skipped vertices, for its completion step
+      const bool sk = mine >= 0 && !eval;
+      const unsigned m = __ballot_sync(kFull, sk);
+      if (m) {
+        const int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(&a.ctr->skip_listed, (unsigned long long)__popc(m));
+        base = __shfl_sync(kFull, base, leader);
+        if (sk) a.learn.skip_list[base + __popc(m & lanemask_lt())] = mine;
+      }
     }
 #pragma unroll
     for (int b = 0; b < kMoveBins; ++b) {
@@ -311,8 +364,7 @@ __global__ void __launch_bounds__(256) k_move_thread(MoveArgs a) {
 #pragma unroll
         for (int k = 0; k < D; ++k)
           if (jj[k] != i) {
-            a.flag[jj[k]] = 1;
-            learn_mark(a.learn, jj[k]);
+            mark_neighbour(a.flag, a.learn, jj[k]);
           }
       }
     }
@@ -436,8 +488,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_move_warp(MoveArgs a) {
       for (int64_t k = b + lane; k < e; k += 32) {
         const int32_t j = __ldg(a.g.col + k);
         if (j != i) {
-          a.flag[j] = 1;
-          learn_mark(a.learn, j);
+          mark_neighbour(a.flag, a.learn, j);
         }
       }
     __syncwarp();
@@ -549,8 +600,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_move_group(MoveArgs a) {
       for (int64_t k = b + gl; k < b + deg; k += GS) {
         const int32_t j = __ldg(a.g.col + k);
         if (j != i) {
-          a.flag[j] = 1;
-          learn_mark(a.learn, j);
+          mark_neighbour(a.flag, a.learn, j);
         }
       }
     __syncwarp();
@@ -641,8 +691,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : NT == 512 ? 2 : 1) k_move_
       for (int64_t k = b + threadIdx.x; k < e; k += NT) {
         const int32_t j = __ldg(a.g.col + k);
         if (j != i) {
-          a.flag[j] = 1;
-          learn_mark(a.learn, j);
+          mark_neighbour(a.flag, a.learn, j);
         }
       }
     __syncthreads();
@@ -651,168 +700,200 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : NT == 512 ? 2 : 1) k_move_
   flush_work(work, a.ctr->mv_work[BIN]);
 }
 
-// -------------------------------------------------------------- cluster bin
-// 8192 < degree <= 32768: a cluster of kClusterSize 1024-thread blocks per
-// vertex.  The blocks' shared tables form one table of kClusterSize * 16384
-// slots: key k's home slot h lies in block h / 16384, which owns the key and
-// probes only within its own 16384 slots.  The row is taken in rounds of
-// 8192 entries: every block gathers its share and sends each (key, weight)
-// to the owner's staging buffer through distributed shared memory (one
-// posted store per entry after one reservation per warp and owner); after a
-// cluster barrier every block adds its staged entries into its own part with
-// local shared-memory atomics.  Then every block scans the slots it claimed
-// for its partial argmax, and block 0 of the cluster reduces the partials and
-// decides.  All blocks of a cluster take the same vertices and rounds, so
-// they meet the same cluster barriers.
-constexpr int kClusterRound = kClusterSize * 1024 * 2;  // entries per round (2 per thread)
+// ----------------------------------------------------------------- wide bin
+// 4096 < degree <= 32768: one 1024-thread block per vertex, one block per
+// SM taking vertices from a work queue.  An entry whose neighbour j is alone
+// in its community (a known singleton: C'[j] = j and no vertex has moved into
+// community j this pass) contributes K_{i->j} = w_ij by itself when rows hold
+// no repeated column, so its score is formed at once and kept in a
+// per-thread running argmax; such a community is never the vertex's own
+// (that would hold i and j).  Only the other entries go through the
+// 16384-slot shared table.  Every slot claimed there first takes a ticket;
+// once more than kWideCap keys would be held, the remaining entries go to
+// the block's own global table of kWideSpill packed 64-bit slots (twice the
+// largest row, so at most half full), the shared table is flushed into it,
+// and the vertex is decided from that table, which its scan leaves empty.
+// At iteration 0 of a pass every community is a singleton, so those scans
+// touch no table at all.
+constexpr uint16_t kNoSlot = 0xFFFFu;
+constexpr int kWideRun = 4;  // entries per thread per round (1024 x 4 in flight per block)
 
-__device__ __forceinline__ void owner_insert(int32_t *keys, uint32_t *vals, uint16_t *occ, unsigned *nocc,
-                                             uint32_t h, int32_t key, uint32_t w, Counters *ctr) {
-  uint32_t s = h % kXlCap;
-  for (int t = 0; t < kXlCap; ++t) {
-    int32_t cur = ((volatile int32_t *)keys)[s];
-    bool claimed = false;
-    if (cur == kEmpty) {
-      cur = atomicCAS(keys + s, kEmpty, key);
-      if (cur == kEmpty) {
-        cur = key;
-        claimed = true;
+__device__ __forceinline__ bool recv_bit(const uint32_t *recv, int32_t c) {
+  return (__ldg(recv + (c >> 5)) >> (c & 31)) & 1u;
+}
+
+// Insert into the shared wide table; false when the ticket count passed
+// kWideCap (*over is set, nothing inserted).  Tickets bound the claimed
+// slots, so the table stays at most three quarters full and probing always
+// finds a slot.
+__device__ __forceinline__ bool wide_insert(int32_t *keys, uint32_t *vals, uint16_t *occ, unsigned *nocc, int *over,
+                                            int32_t key, uint32_t w, Counters *ctr) {
+  constexpr uint32_t mask = kXlCap - 1;
+  uint32_t s = slot_of(key, mask);
+  for (uint32_t t = 0; t <= mask && t < c_probe_limit; ++t) {
+    int32_t k = ((volatile int32_t *)keys)[s];
+    if (k == kEmpty) {
+      const unsigned ticket = atomicAdd(nocc, 1u);
+      if (ticket >= (unsigned)kWideCap) {
+        *(volatile int *)over = 1;
+        return false;
       }
+      k = atomicCAS(keys + s, kEmpty, key);
+      if (k == kEmpty) {
+        occ[ticket] = (uint16_t)s;
+        atomicAdd(vals + s, w);
+        return true;
+      }
+      occ[ticket] = kNoSlot;  // another thread took the slot: the ticket stays unused
     }
-    if (cur == key) {
+    if (k == key) {
       atomicAdd(vals + s, w);
-      if (claimed) occ[atomicAdd(nocc, 1u)] = (uint16_t)s;
-      return;
+      return true;
     }
-    s = (s + 1) & (kXlCap - 1);
+    s = (s + 1) & mask;
   }
   atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
+  return false;
+}
+
+__device__ __forceinline__ void spill_insert(unsigned long long *tab, int32_t key, uint32_t w, Counters *ctr) {
+  const uint32_t home = slot_of(key, kWideSpill - 1);
+  gm_insert_packed_from(tab, kWideSpill, home, __ldcg(tab + home), key, w, ctr);
 }
 
 template <int WK>
-__global__ void __cluster_dims__(kClusterSize, 1, 1) __launch_bounds__(1024, 1) k_move_cluster(MoveArgs a) {
-  namespace cg = cooperative_groups;
+__global__ void __launch_bounds__(1024, 1) k_move_wide(MoveArgs a) {
   constexpr int NT = 1024;
-  constexpr uint32_t kMask = (uint32_t)kClusterSize * kXlCap - 1;
-  constexpr int kStage = kClusterRound;  // worst case: a whole round sent to one owner
-  cg::cluster_group cl = cg::this_cluster();
-  const int rank = (int)cl.block_rank();
-  const int lane = threadIdx.x & 31;
-  // dynamic shared memory: keys[16384], vals[16384], occupied list[16384],
-  // staged keys[kStage], staged weights[kStage]
+  // dynamic shared memory: keys[16384], vals[16384], occupied list[kWideCap]
   extern __shared__ uint32_t dyn[];
   int32_t *keys = (int32_t *)dyn;
   uint32_t *vals = dyn + kXlCap;
   uint16_t *occ = (uint16_t *)(dyn + 2 * kXlCap);
-  int32_t *stage_k = (int32_t *)(dyn + 2 * kXlCap + kXlCap / 2);
-  uint32_t *stage_w = (uint32_t *)(stage_k + kStage);
-  __shared__ unsigned s_nocc, s_nstage;
-  __shared__ long long s_part_s[kClusterSize], s_part_kid[kClusterSize];
-  __shared__ int32_t s_part_c[kClusterSize];
+  __shared__ unsigned s_nocc;
+  __shared__ int s_over;
   __shared__ int32_t s_target;
+  __shared__ unsigned long long s_idx;
+  unsigned long long *spill = a.wide_spill + (size_t)blockIdx.x * kWideSpill;  // left empty between vertices
   for (int s = threadIdx.x; s < kXlCap; s += NT) {
     keys[s] = kEmpty;
     vals[s] = 0;
   }
   if (threadIdx.x == 0) {
     s_nocc = 0;
-    s_nstage = 0;
+    s_over = 0;
   }
-  cl.sync();
-  const unsigned long long cnt = a.ctr->bin_count[kClusterBin];
-  const unsigned long long nclusters = gridDim.x / kClusterSize;
+  const unsigned long long cnt = a.ctr->bin_count[kXlBin];
   unsigned long long glo = 0, ghi = 0, gm = 0;
   unsigned long long work[5] = {0, 0, 0, 0, 0};
-  for (unsigned long long idx = blockIdx.x / kClusterSize; idx < cnt; idx += nclusters) {
-    const int32_t i = a.bins[kClusterBin][idx];
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_idx = atomicAdd(&a.ctr->wide_next, 1ull);
+    __syncthreads();
+    const unsigned long long idx = s_idx;
+    if (idx >= cnt) break;
+    const int32_t i = a.bins[kXlBin][idx];
     const int64_t b = a.g.begin[i], e = a.g.end[i];
     const int64_t deg = e - b;
-    for (int64_t r0 = 0; r0 < deg; r0 += kClusterRound) {
-      // this block's 2 * NT entries of the round, routed to their owners
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int64_t p = r0 + (int64_t)rank * 2 * NT + u * NT + threadIdx.x;
-        int32_t key = kEmpty;
-        uint32_t w = 0;
-        if (p < deg) {
-          const int32_t j = __ldg(a.g.col + b + p);
-          if (j != i) {
-            key = a.Cp[j];
-            w = load_w<WK>(a.g.w, b + p);
-          }
-        }
-        const int owner = key == kEmpty ? -1 : (int)(slot_of(key, kMask) / kXlCap);
-#pragma unroll
-        for (int o = 0; o < kClusterSize; ++o) {
-          const unsigned m = __ballot_sync(kFull, owner == o);
-          if (!m) continue;
-          const int leader = __ffs(m) - 1;
-          unsigned base = 0;
-          if (lane == leader) base = atomicAdd(cl.map_shared_rank(&s_nstage, o), (unsigned)__popc(m));
-          base = __shfl_sync(kFull, base, leader);
-          if (owner == o) {
-            const unsigned pos = base + __popc(m & lanemask_lt());
-            cl.map_shared_rank(stage_k, o)[pos] = key;
-            cl.map_shared_rank(stage_w, o)[pos] = w;
-          }
-        }
-      }
-      cl.sync();  // every block's staging buffer is complete
-      const unsigned ns = s_nstage;
-      for (unsigned t = threadIdx.x; t < ns; t += NT) {
-        const int32_t key = stage_k[t];
-        owner_insert(keys, vals, occ, &s_nocc, slot_of(key, kMask), key, stage_w[t], a.ctr);
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) s_nstage = 0;
-      cl.sync();  // staging buffers are free for the next round
-    }
-    const int32_t d = a.Cp[i];
     const long long Ki = a.K[i];
     const long long tm = vertex_two_m(a.batch, a.two_m, i);
     long long best_s = LLONG_MIN, Kid = 0;
     int32_t best_c = INT_MAX;
-    const unsigned nk = s_nocc;
-    for (unsigned t = threadIdx.x; t < nk; t += NT) {
-      const uint32_t s = occ[t];
-      const int32_t c = keys[s];
-      const long long v = vals[s];
-      keys[s] = kEmpty;
-      vals[s] = 0;
-      if (c == d) {
-        Kid = v;
-        continue;
+    for (int64_t x0 = 0; x0 < deg; x0 += (int64_t)NT * kWideRun) {
+      int32_t jj[kWideRun], kk[kWideRun];
+      uint32_t ww[kWideRun];
+#pragma unroll
+      for (int u = 0; u < kWideRun; ++u) {
+        const int64_t p = x0 + threadIdx.x + (int64_t)u * NT;
+        jj[u] = -2;
+        ww[u] = 0;
+        if (p < deg) {
+          jj[u] = __ldg(a.g.col + b + p);
+          ww[u] = load_w<WK>(a.g.w, b + p);
+        }
       }
-      ++work[2];
-      const long long sc = tm * v - Ki * a.Sigma[c];
-      if (better(sc, c, best_s, best_c)) {
-        best_s = sc;
-        best_c = c;
+#pragma unroll
+      for (int u = 0; u < kWideRun; ++u) kk[u] = (jj[u] >= 0 && jj[u] != i) ? a.Cp[jj[u]] : kEmpty;
+      bool solo[kWideRun];
+#pragma unroll
+      for (int u = 0; u < kWideRun; ++u) solo[u] = a.solo && kk[u] != kEmpty && kk[u] == jj[u] && !recv_bit(a.recv, kk[u]);
+      long long sig[kWideRun];
+#pragma unroll
+      for (int u = 0; u < kWideRun; ++u) sig[u] = solo[u] ? a.Sigma[kk[u]] : 0;
+#pragma unroll
+      for (int u = 0; u < kWideRun; ++u) {
+        if (kk[u] == kEmpty) continue;
+        if (solo[u]) {
+          ++work[2];
+          const long long sc = tm * (long long)ww[u] - Ki * sig[u];
+          if (better(sc, kk[u], best_s, best_c)) {
+            best_s = sc;
+            best_c = kk[u];
+          }
+        } else if (*(volatile int *)&s_over ||
+                   !wide_insert(keys, vals, occ, &s_nocc, &s_over, kk[u], ww[u], a.ctr)) {
+          spill_insert(spill, kk[u], ww[u], a.ctr);
+        }
+      }
+    }
+    __syncthreads();
+    const unsigned nk = min(s_nocc, (unsigned)kWideCap);
+    const bool over = s_over != 0;
+    const int32_t d = a.Cp[i];
+    if (over) {
+      // the shared table's keys join the spilled ones; the vertex is decided
+      // from the block's global table, whose slots are cleared as read
+      for (unsigned t = threadIdx.x; t < nk; t += NT) {
+        const uint16_t sl = occ[t];
+        if (sl == kNoSlot) continue;
+        spill_insert(spill, keys[sl], vals[sl], a.ctr);
+        keys[sl] = kEmpty;
+        vals[sl] = 0;
+      }
+      __syncthreads();
+      for (int r = threadIdx.x; r < kWideSpill; r += NT) {
+        const unsigned long long pv = __ldcg(spill + r);
+        if (pv == 0ull) continue;
+        spill[r] = 0ull;
+        const int32_t c = packed_key(pv);
+        const long long v = packed_val(pv);
+        if (c == d) {
+          Kid = v;
+          continue;
+        }
+        ++work[2];
+        const long long sc = tm * v - Ki * a.Sigma[c];
+        if (better(sc, c, best_s, best_c)) {
+          best_s = sc;
+          best_c = c;
+        }
+      }
+    } else {
+      for (unsigned t = threadIdx.x; t < nk; t += NT) {
+        const uint16_t sl = occ[t];
+        if (sl == kNoSlot) continue;
+        const int32_t c = keys[sl];
+        const long long v = vals[sl];
+        keys[sl] = kEmpty;
+        vals[sl] = 0;
+        if (c == d) {
+          Kid = v;
+          continue;
+        }
+        ++work[2];
+        const long long sc = tm * v - Ki * a.Sigma[c];
+        if (better(sc, c, best_s, best_c)) {
+          best_s = sc;
+          best_c = c;
+        }
       }
     }
     block_argmax_sum<NT>(best_s, best_c, Kid);
     if (threadIdx.x == 0) {
-      s_nocc = 0;  // read by every thread before block_argmax_sum's barriers
-      cl.map_shared_rank(s_part_s, 0)[rank] = best_s;
-      cl.map_shared_rank(s_part_c, 0)[rank] = best_c;
-      cl.map_shared_rank(s_part_kid, 0)[rank] = Kid;
-    }
-    cl.sync();  // partials in block 0
-    if (rank == 0 && threadIdx.x == 0) {
-      long long bs = LLONG_MIN, kid = 0;
-      int32_t bc = INT_MAX;
-      for (int r = 0; r < kClusterSize; ++r) {
-        kid += s_part_kid[r];
-        if (better(s_part_s[r], s_part_c[r], bs, bc)) {
-          bs = s_part_s[r];
-          bc = s_part_c[r];
-        }
-      }
       long long s_d = 0;
-      const int32_t t =
-          finish_decision(tm, a.Sigma, a.iter ? (int)a.iter[1] : a.pickless, d, Ki, kid, bs, bc, glo, ghi, gm, &s_d);
-      learn_record(a.learn, a.ctr, a.g, a.Cp, a.Sigma, a.two_m, i, Ki, kid, bs, bc, s_d, t >= 0);
-      if (t >= 0) batch_gain(a.batch, i, bs, s_d);
+      const int32_t t = finish_decision(tm, a.Sigma, a.iter ? (int)a.iter[1] : a.pickless, d, Ki, Kid, best_s,
+                                        best_c, glo, ghi, gm, &s_d);
+      learn_record(a.learn, a.ctr, a.g, a.Cp, a.Sigma, a.two_m, i, Ki, Kid, best_s, best_c, s_d, t >= 0);
+      if (t >= 0) batch_gain(a.batch, i, best_s, s_d);
       work[0] += 1;
       work[1] += (unsigned long long)deg;
       if (t >= 0) {
@@ -821,20 +902,21 @@ __global__ void __cluster_dims__(kClusterSize, 1, 1) __launch_bounds__(1024, 1) 
         const unsigned long long pos = atomicAdd(&a.ctr->movers, 1ull);
         emit_move(a.async_apply, a.Cp, a.K, a.Sigma, a.mv_vertex, a.mv_target, pos, i, t);
       }
-      for (int r = 0; r < kClusterSize; ++r) cl.map_shared_rank(&s_target, r)[0] = t;
+      s_target = t;
+      s_nocc = 0;  // every thread read it before block_argmax_sum's barriers
+      s_over = 0;
     }
-    cl.sync();  // decision in every block
+    __syncthreads();
     if (s_target >= 0)
-      for (int64_t k = b + (int64_t)rank * NT + threadIdx.x; k < e; k += (int64_t)kClusterSize * NT) {
+      for (int64_t k = b + threadIdx.x; k < e; k += NT) {
         const int32_t j = __ldg(a.g.col + k);
         if (j != i) {
-          a.flag[j] = 1;
-          learn_mark(a.learn, j);
+          mark_neighbour(a.flag, a.learn, j);
         }
       }
   }
   flush_gains(glo, ghi, gm, a.ctr);
-  flush_work(work, a.ctr->mv_work[kClusterBin]);
+  flush_work(work, a.ctr->mv_work[kXlBin]);
 }
 
 // -------------------------------------------------------------------- apply
@@ -846,6 +928,7 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
     const int32_t d = a.Cp[i];
     const long long Ki = a.K[i];
     a.Cp[i] = c;
+    if (a.recv) atomicOr(a.recv + (c >> 5), 1u << (c & 31));  // community c is no longer a known singleton
     atomicAdd((unsigned long long *)(a.Sigma + d), as_ull(-Ki));
     atomicAdd((unsigned long long *)(a.Sigma + c), as_ull(Ki));
   }
@@ -859,15 +942,17 @@ template <int WK>
 __global__ void __launch_bounds__(256) k_pass_init(GView g, int first_pass, int64_t *K, int64_t *Sigma,
                                                    int32_t *Cp, uint8_t *flag, Counters *ctr, float4 *feat,
                                                    uint32_t *marks, uint32_t *marks_next, uint8_t *vbin,
-                                                   int group_max, int half_max, int warp_max) {
+                                                   int group_max, int half_max, int warp_max, int64_t track_min) {
   unsigned long long md = 0, big_slots = 0, big_items = 0;
   const int lane = threadIdx.x & 31;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = g.begin[i], e = g.end[i];
     const unsigned long long deg = (unsigned long long)(e - b);
     if (deg > md) md = deg;
-    if (vbin) vbin[i] = deg > 0 ? (uint8_t)move_bin((int64_t)deg, group_max, half_max, warp_max) : (uint8_t)0xFF;
-    if (deg > (unsigned long long)kClusterMaxDeg) {  // hubs of the global tables
+    if (vbin)
+      vbin[i] = (uint8_t)((deg > 0 ? (unsigned)move_bin((int64_t)deg, group_max, half_max, warp_max) : kVbinNone) |
+                          (track_min > 0 && (int64_t)deg >= track_min ? kVbinTracked : 0u));
+    if (deg > (unsigned long long)kWideMaxDeg) {  // hubs of the global tables
       big_slots += big_table_cap(deg, (unsigned long long)g.n);
       big_items += 1;
     }
@@ -885,7 +970,7 @@ __global__ void __launch_bounds__(256) k_pass_init(GView g, int first_pass, int6
     }
     Sigma[i] = k;
     Cp[i] = (int32_t)i;
-    flag[i] = 1;
+    flag[i] = (uint8_t)(kFlagUnproc | (track_min > 0 && (int64_t)deg >= track_min ? kFlagTracked : 0));
     if (feat) {
       feat[i] = make_float4(0.f, 0.f, 0.f, 0.f);
       marks[i] = 0;
@@ -906,6 +991,12 @@ __global__ void __launch_bounds__(256) k_pass_init(GView g, int first_pass, int6
   }
 }
 
+// Every vertex unprocessed (bit kFlagUnproc set, the tracked bit kept).
+__global__ void k_flag_all(uint8_t *flag, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    flag[i] |= kFlagUnproc;
+}
+
 __global__ void k_iota(int32_t *x, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     x[i] = (int32_t)i;
@@ -918,19 +1009,21 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
   constexpr size_t kMidSmem = (size_t)kMidCap * (sizeof(uint32_t) + sizeof(int32_t)) + kMidCap / 2 * sizeof(uint16_t);
   constexpr size_t kBlockSmem =
       (size_t)kBlockCap * (sizeof(uint32_t) + sizeof(int32_t)) + kBlockCap / 2 * sizeof(uint16_t);
-  constexpr size_t kXlSmem = (size_t)kXlCap * (sizeof(uint32_t) + sizeof(int32_t)) + kXlCap / 2 * sizeof(uint16_t);
-  constexpr size_t kClSmem = (size_t)kXlCap * (sizeof(uint32_t) + sizeof(int32_t) + sizeof(uint16_t)) +
-                             (size_t)kClusterRound * (sizeof(int32_t) + sizeof(uint32_t));
+  constexpr size_t kWideSmem =
+      (size_t)kXlCap * (sizeof(uint32_t) + sizeof(int32_t)) + (size_t)kWideCap * sizeof(uint16_t);
   if (!attr_done) {
-    cudaFuncSetAttribute(k_move_cluster<WK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClSmem);
     cudaFuncSetAttribute(k_move_block<WK, 512, kBlockCap, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kBlockSmem);
-    cudaFuncSetAttribute(k_move_block<WK, 1024, kXlCap, kXlBin>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)kXlSmem);
+    cudaFuncSetAttribute(k_move_wide<WK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWideSmem);
     attr_done = true;
   }
-  LV_TIMED(prof, K_SELECT, s, k_select<<<grid_for((a.g.n + kSelVPT - 1) / kSelVPT, 256, num_sms, 8), 256, 0, s>>>(a));
-  if (a.learn.enabled) LV_TIMED(prof, K_MLP_SELECT, s, k_mlp_select<<<num_sms * 4, 256, 0, s>>>(a));
+  if (a.sel_list) {
+    LV_TIMED(prof, K_SELECT, s, k_select_list<<<num_sms * 4, 256, 0, s>>>(a));
+  } else {
+    LV_TIMED(prof, K_SELECT, s,
+             k_select<<<grid_for((a.g.n + kSelVPT - 1) / kSelVPT, 256, num_sms, 8), 256, 0, s>>>(a));
+    if (a.learn.enabled) LV_TIMED(prof, K_MLP_SELECT, s, k_mlp_select<<<num_sms * 4, 256, 0, s>>>(a));
+  }
   const bool hubs = big.ws.slots > 0;
   if (hubs) big_move_plan(big, s, prof);  // the round count reaches the host while the bins below run
   const int *bk = a.sched.move;
@@ -957,12 +1050,7 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
   LV_TIMED(prof, K_MOVE_MID, s3, k_move_block<WK, 128, kMidCap, 2><<<num_sms * bk[2], 128, kMidSmem, s3>>>(a));
   LV_TIMED(prof, K_MOVE_BLOCK, s3,
            k_move_block<WK, 512, kBlockCap, 3><<<num_sms * bk[3], 512, kBlockSmem, s3>>>(a));
-  LV_TIMED(prof, K_MOVE_XL, s,
-           k_move_block<WK, 1024, kXlCap, kXlBin><<<num_sms * bk[kXlBin], 1024, kXlSmem, s>>>(a));
-  {
-    const int clusters = std::max(1, num_sms * bk[kClusterBin] / kClusterSize);
-    LV_TIMED(prof, K_MOVE_CLUSTER, s, k_move_cluster<WK><<<clusters * kClusterSize, 1024, kClSmem, s>>>(a));
-  }
+  LV_TIMED(prof, K_MOVE_XL, s, k_move_wide<WK><<<num_sms, 1024, kWideSmem, s>>>(a));  // one block per SM, work queue
   if (hubs) big_move_rounds(big, WK, num_sms, s, prof);
   if (conc)
     for (int k = 0; k < kSideStreams; ++k) {
@@ -982,7 +1070,9 @@ void pass_init_t(const GView &g, int first, int64_t *K, int64_t *Sigma, int32_t 
                                                                              marks, marks_next, vbin,
                                                                              sched ? sched->group_max : 0,
                                                                              sched ? sched->half_max : 0,
-                                                                             sched ? sched->warp_max : 0));
+                                                                             sched ? sched->warp_max : 0,
+                                                                             (learn && learn->record) ? learn->min_degree
+                                                                                                      : 0));
 }
 
 }  // namespace
@@ -1002,6 +1092,11 @@ void pass_init(const GView &g, int wkind, int first_pass, int64_t *K, int64_t *S
   else pass_init_t<W_U32>(g, first_pass, K, Sigma, Cp, flag, ctr, num_sms, s, learn, vbin, sched);
 }
 
+void flag_all(uint8_t *flag, int64_t n, int num_sms, cudaStream_t s) {
+  if (n <= 0) return;
+  LV_LAUNCH(k_flag_all<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(flag, n));
+}
+
 void iota_i32(int32_t *x, int64_t n, int num_sms, cudaStream_t s) {
   if (n <= 0) return;
   LV_LAUNCH(k_iota<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(x, n));
@@ -1010,6 +1105,8 @@ void iota_i32(int32_t *x, int64_t n, int num_sms, cudaStream_t s) {
 const char *const kKernelNames[K_NUM_KERNELS] = {
     "select", "move_thread", "move_warp", "move_mid", "move_block", "move_hub", "apply", "pass_init",
     "comm_count", "comm_scatter", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big",
-    "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit", "mlp_select", "move_group", "move_xl", "merge_xl", "move_cluster", "merge_group", "move_half"};
+    "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit", "mlp_select", "move_group", "move_wide", "merge_xl", "merge_group", "move_half"};
+
+cudaError_t set_probe_limit_move(uint32_t v) { return set_probe_limit_here(v); }
 
 }  // namespace lv

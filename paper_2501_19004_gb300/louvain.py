@@ -29,7 +29,7 @@ MODE_PLAIN, MODE_LEARNED = 0, 1
 KERNELS = ["select", "move_thread", "move_warp", "move_mid", "move_block", "move_hub", "apply", "pass_init",
            "comm_count", "comm_scatter", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big",
            "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit", "mlp_select", "move_group",
-           "move_xl", "merge_xl", "move_cluster", "merge_group", "move_half"]
+           "move_wide", "merge_xl", "merge_group", "move_half"]
 
 
 def kernel_mask(*names) -> int:
@@ -118,6 +118,8 @@ def load(path: Optional[str] = None):
     lib.louvain_mlp_gradient.argtypes = [vp, vp, vp, i64, vp, vp, vp]
     lib.louvain_mlp_train.restype = ctypes.c_int
     lib.louvain_mlp_train.argtypes = [vp, vp, vp, i64, i32, i32, ctypes.c_float, ctypes.c_uint64, vp, vp]
+    lib.louvain_set_probe_limit.restype = ctypes.c_int
+    lib.louvain_set_probe_limit.argtypes = [ctypes.c_uint32]
     lib.louvain_modularity_noalloc.restype = ctypes.c_int
     lib.louvain_modularity_noalloc.argtypes = [P(LouvainGraph), vp, vp, P(ctypes.c_double), vp, vp]
     lib.louvain_create_batched.restype = ctypes.c_int
@@ -446,8 +448,8 @@ def louvain_batch_results(ctx, num_graphs: int, max_passes: int):
 
 
 SCHEDULE_FIELDS = ["group_max", "half_max", "warp_max",
-                   "move_thread", "move_warp", "move_mid", "move_block", "move_hub", "move_group", "move_xl",
-                   "move_cluster", "move_half",
+                   "move_thread", "move_warp", "move_mid", "move_block", "move_hub", "move_group", "move_wide",
+                   "unused_bin7", "move_half",
                    "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big", "merge_xl", "merge_group",
                    "graphs", "concurrent"]
 
@@ -485,6 +487,12 @@ def louvain_autotune(ctx, max_runs: int = 24) -> dict:
 
 def louvain_model_size() -> int:
     return int(load().louvain_model_size())
+
+
+def louvain_set_probe_limit(max_probes: int) -> None:
+    """Algorithm 7's MAX_RETRIES for every hashtable insert on the current
+    device (0 = the table size, never reached)."""
+    _check(load().louvain_set_probe_limit(max_probes), None)
 
 
 def louvain_version() -> str:

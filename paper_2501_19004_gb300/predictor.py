@@ -2,11 +2,15 @@
 
 Traces come from plain runs of the library with trace recording on: each
 sample is the 8-feature vector a vertex had when it was selected for
-evaluation and whether it then moved.  Training uses the library's own
-tensor-core kernels (louvain_mlp_train, Adam on the mean binary
-cross-entropy).  The default model is trained on R-MAT graphs of scales 20,
-21 and 22 (seeds 101, 102, 103; edge factor 16) and stored next to this file
-by running ``python -m paper_2501_19004_gb300.predictor``.
+evaluation and whether it then moved.  Only vertices of at least
+MIN_DEGREE entries are recorded, the same vertices the predictor later
+decides for: skipping pays only where a re-evaluation scans a long row, and
+below that degree the inference would cost about as much as the scan.
+Training uses the library's own tensor-core kernels (louvain_mlp_train,
+Adam on the mean binary cross-entropy).  The default model is trained on
+R-MAT graphs of scales 20, 21 and 22 (seeds 101, 102, 103; edge factor 16)
+and stored next to this file, with the settings it is meant for, by running
+``python -m paper_2501_19004_gb300.predictor``.
 """
 from __future__ import annotations
 
@@ -23,6 +27,9 @@ from . import louvain as lv
 HERE = os.path.dirname(os.path.abspath(__file__))
 MODEL_FILE = os.path.join(HERE, "predictor_rmat20-22.f32")
 TRAINING_GRAPHS = ((20, 101), (21, 102), (22, 103))
+MIN_DEGREE = 1024
+# run settings the stored model is meant for (louvain_config fields)
+SETTINGS = dict(learned_min_degree=MIN_DEGREE, skip_threshold=0.1, learned_fallback=3, learned_skip_clears=1)
 
 
 def collect_traces(graph, cap: int = 4_000_000, rate: float = 0.25, min_degree: int = 0):
@@ -57,12 +64,12 @@ def train(X, Y, epochs: int = 8, batch: int = 8192, lr: float = 3e-3, seed: int 
     return p.cpu().numpy(), losses
 
 
-def train_default(epochs: int = 8, verbose: bool = False):
+def train_default(epochs: int = 30, verbose: bool = False):
     Xs, Ys = [], []
     for scale, seed in TRAINING_GRAPHS:
         t0 = time.time()
         g = gg.rmat(scale, 16, seed=seed)
-        X, Y = collect_traces(g)
+        X, Y = collect_traces(g, rate=1.0, min_degree=MIN_DEGREE)
         Xs.append(X)
         Ys.append(Y)
         if verbose:
@@ -70,9 +77,9 @@ def train_default(epochs: int = 8, verbose: bool = False):
                   file=sys.stderr)
     X = np.concatenate(Xs)
     Y = np.concatenate(Ys)
-    params, losses = train(X, Y, epochs=epochs)
+    params, losses = train(X, Y, epochs=epochs, batch=2048)
     info = {"samples": int(X.shape[0]), "positive_rate": float(Y.mean()), "losses": [float(v) for v in losses],
-            "graphs": [f"rmat{s}-ef16-seed{sd}" for s, sd in TRAINING_GRAPHS]}
+            "graphs": [f"rmat{s}-ef16-seed{sd}" for s, sd in TRAINING_GRAPHS], "settings": SETTINGS}
     return params, info
 
 
@@ -82,6 +89,14 @@ def load_default():
         return None
     p = np.fromfile(MODEL_FILE, dtype=np.float32)
     return p if p.shape[0] == lv.louvain_model_size() else None
+
+
+def default_config(model=None, **over) -> "lv.Config":
+    """A learned-mode Config with the stored model and the settings it was
+    trained for (keyword arguments override them)."""
+    kw = dict(SETTINGS)
+    kw.update(over)
+    return lv.Config(mode=lv.MODE_LEARNED, model=load_default() if model is None else model, **kw)
 
 
 if __name__ == "__main__":

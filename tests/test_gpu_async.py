@@ -121,7 +121,7 @@ def test_async_settings_and_edges():
     cfg = lv.Config(asynchronous=True)
     for e in (gg.CSR(np.zeros(6, dtype=np.int64), np.zeros(0, dtype=np.int32), None), gg.from_pairs(2, [0], [1])):
         check_valid(e, lv.run(e, cfg), cfg)
-    n = 9000  # a star: one hub in the cluster bin
+    n = 9000  # a star: one hub in the wide bin
     star = gg.from_pairs(n, np.zeros(n - 1, dtype=np.int64), np.arange(1, n, dtype=np.int64))
     check_valid(star, lv.run(lv.DeviceCSR.from_host(star), cfg), cfg)
 

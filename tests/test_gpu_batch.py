@@ -92,7 +92,7 @@ def test_batch_settings(cfg):
 
 def test_batch_weighted_and_hubs():
     # a weighted graph and an R-MAT graph whose hubs (up to degree 9767) take the
-    # 512-thread, 1024-thread and cluster bins, next
+    # 512-thread and wide bins, next
     # to unit-weight graphs, which the union stores with weight 1
     graphs = [gg.rmat(14, 8, seed=3, weight_range=(1, 5)), gg.batched_sbm(1), gg.rmat(16, 16, seed=7),
               gg.batched_sbm(10)]

@@ -6,10 +6,10 @@ benchmark times (concurrent bins, CUDA-graph replay, the batched context).
 - The 4,096-graph batch: one batched run of all graphs; 32 graphs sampled
   with a stride are checked bit-exactly against the oracle run on each.
 - The 8192 x 8192 grid: bit-exact against a full oracle run.
-- R-MAT scale 27 (4.2 billion entries): properties that hold at any size,
-  checked exactly: the oracle's modularity of the GPU's memberships equals
-  the GPU's exact numerator and denominator, the memberships are dense ids
-  and the community count matches.
+- R-MAT scale 27 (4.2 billion entries, the learned-skip evaluation graph):
+  bit-exact against a full oracle run on the host cores (memberships,
+  per-iteration and per-pass records, exact modularity), plus the oracle's
+  modularity of the GPU's memberships.
 """
 import numpy as np
 import pytest
@@ -79,16 +79,25 @@ def test_grid8192_bit_exact_full_size():
 
 
 @pytest.mark.slow
-def test_rmat27_properties_full_size():
-    """4.2 billion entries: the oracle's exact modularity of the GPU's
-    memberships (a full oracle run would take many minutes)."""
+def test_rmat27_bit_exact_full_size():
+    """4.2 billion entries, in the benchmark's launch configuration: the
+    GPU's run against a complete oracle run (OpenMP over the host cores,
+    about 110 GB of host memory), element by element."""
     g = gg.rmat(27, 16, seed=13)
     dg = lv.DeviceCSR.from_host(g)
-    with lv.Louvain(dg) as ctx:
+    with lv.Louvain(dg, lv.Config(record_pass_modularity=True)) as ctx:
         ctx.set_schedule(FAST)
         res = ctx.run().result()
     del dg
+    torch.cuda.empty_cache()
     q, num, den = oracle.modularity(g, res.membership)
     assert (num, den) == (res.q_num, res.q_den)
     used = np.unique(res.membership)
     assert used[0] == 0 and used[-1] == res.communities - 1 and used.shape[0] == res.communities
+    ref = oracle.louvain(g, oracle.Config())
+    assert (res.passes, res.exit_reason, res.communities) == (ref.passes, ref.exit_reason, ref.communities)
+    P = ref.passes
+    assert np.array_equal(res.pass_stats[:P], ref.pass_stats[:P])
+    assert np.array_equal(res.iter_stats[:P], ref.iter_stats[:P])
+    assert np.array_equal(res.membership, ref.membership)
+    assert (res.q_num, res.q_den) == (ref.q_num, ref.q_den)

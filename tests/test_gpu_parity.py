@@ -60,7 +60,7 @@ CASES = {
     "rmat12": lambda: gg.rmat(12, 16, seed=7),
     "rmat14_weighted": lambda: gg.rmat(14, 8, seed=3, weight_range=(1, 5)),
     "rmat16_hubs": lambda: gg.rmat(16, 16, seed=7),
-    "rmat18_hubs": lambda: gg.rmat(18, 16, seed=7),  # 172 vertices above 4096, 19 above 8192 (cluster bin)
+    "rmat18_hubs": lambda: gg.rmat(18, 16, seed=7),  # 172 vertices above 4096 (wide bin), 19 above 8192
     "rmat19_hubs": lambda: gg.rmat(19, 16, seed=7),  # one vertex above 32768 (global tables)
     "grid96": lambda: gg.grid(96, 0.02, seed=11),
     "ring8x10": lambda: gg.ring_of_cliques(8, 10),
@@ -118,13 +118,47 @@ def test_edge_cases():
     z = gg.CSR(np.zeros(1, dtype=np.int64), np.zeros(0, dtype=np.int32), None)
     res = lv.run(z)
     assert res.membership.shape == (0,)
-    # stars: one hub with many leaves, in the cluster bin (8999 leaves) and
+    # stars: one hub with many leaves, in the wide bin (8999 leaves) and
     # in the global-table bin (40000 leaves)
     for n in (9000, 40001):
         u = np.zeros(n - 1, dtype=np.int64)
         v = np.arange(1, n, dtype=np.int64)
         star = gg.from_pairs(n, u, v)
         res, ref = run_both(star)
+        assert_same(res, ref)
+
+
+def _pendant_paths(p):
+    """A hub (vertex 0) with p paths of length two: 0 - a_k - b_k.  Once each
+    pair (a_k, b_k) forms a community, the hub's row holds p distinct
+    communities of two members each: none of them a known singleton."""
+    a = np.arange(1, p + 1, dtype=np.int64)
+    return gg.from_pairs(2 * p + 1, np.concatenate([np.zeros(p, dtype=np.int64), a]), np.concatenate([a, a + p]))
+
+
+def test_wide_bin_spills_to_its_global_table():
+    """Hubs of degree 4097..32768 keep at most 12288 distinct non-singleton
+    communities in shared memory; more go to the block's global table.  Both
+    sizes, and the largest wide degree, are bit-exact against the oracle."""
+    for p in (10000, 20000, 32768):
+        g = _pendant_paths(p)
+        res, ref = run_both(g)
+        assert_same(res, ref)
+        assert res.iter_stats[0, 1, 0] > 0  # the hub was evaluated again after the pairs formed
+
+
+def test_rows_with_repeated_columns():
+    """Input rows that are not strictly increasing (here every row listed
+    twice, a multigraph) turn the known-singleton shortcut off for the input
+    graph: results still equal the oracle's, which sums repeated entries."""
+    for base in (gg.from_pairs(12001, np.zeros(12000, dtype=np.int64), np.arange(1, 12001, dtype=np.int64)),
+                 gg.rmat(13, 16, seed=4)):
+        deg = np.diff(base.offsets)
+        off = np.concatenate([[0], np.cumsum(2 * deg)]).astype(np.int64)
+        cols = np.concatenate([np.concatenate([base.cols[base.offsets[i]:base.offsets[i + 1]]] * 2)
+                               for i in range(base.n)]).astype(np.int32)
+        g = gg.CSR(off, cols, None)
+        res, ref = run_both(g)
         assert_same(res, ref)
 
 
@@ -187,3 +221,25 @@ def test_modularity_of_refuses_membership_ids_out_of_range():
             assert ei.value.status == 1
     q, num, den = lv.louvain_modularity_of(g, memb)
     assert oracle.modularity(g, memb)[1:] == (num, den)
+
+
+def test_probe_limit_gives_hash_overflow_and_recovers():
+    """Algorithm 7's "failed" result: with the probe limit lowered to one slot,
+    colliding inserts give up, the run returns LOUVAIN_E_HASH_OVERFLOW (a
+    status, no fault), and with the limit restored the same context runs
+    again bit-exactly.  Shared tables (warp and block bins) and the hubs'
+    global tables (R-MAT scale 19) both reach the limit."""
+    for g in (gg.rmat(14, 16, seed=7), gg.rmat(19, 16, seed=7)):
+        ref = oracle.louvain(g, oracle.Config())
+        with lv.Louvain(lv.DeviceCSR.from_host(g)) as ctx:
+            try:
+                lv.louvain_set_probe_limit(1)
+                with pytest.raises(lv.LouvainError) as ei:
+                    ctx.run()
+                assert ei.value.status == 4  # LOUVAIN_E_HASH_OVERFLOW
+                assert "probe" in lv.louvain_last_error(ctx.ctx)
+            finally:
+                lv.louvain_set_probe_limit(0)
+            res = ctx.run().result()
+        assert np.array_equal(res.membership, ref.membership)
+        assert (res.q_num, res.q_den) == (ref.q_num, ref.q_den)

@@ -40,6 +40,8 @@ SCHEDULES = [
     dict(graphs=1, group_max=16, half_max=16, warp_max=64, move_hub=2),
     dict(concurrent=1),
     dict(concurrent=1, graphs=1),
+    dict(graphs=2),                                        # whole phase under device control
+    dict(graphs=2, concurrent=1, group_max=32, half_max=64, warp_max=128),
 ]
 
 
@@ -60,17 +62,24 @@ def test_schedules_bit_exact(sched, name):
     check_single(g, r2)
 
 
-def test_graph_replay_batch():
+@pytest.mark.parametrize("mode", [1, 2])
+def test_graph_replay_batch(mode):
+    """Per-iteration replay (graphs = 1) and the device-controlled phase
+    (graphs = 2: every graph's tolerance test on the device) on a batch: each
+    graph's result and per-pass records equal its own oracle run."""
     graphs = [gg.batched_sbm(k) for k in (0, 1, 3, 8, 10)] + [gg.rmat(12, 16, seed=7)]
     union, vo = gg.concat(graphs)
     with lv.LouvainBatch(lv.DeviceCSR.from_host(union), vo) as b:
-        b.set_schedule(dict(graphs=1, concurrent=1))
+        b.set_schedule(dict(graphs=mode, concurrent=1))
         res = b.run().result()
-    for k, g in enumerate(graphs):
-        memb, q, num, den, passes, comms, why = res.graph(k)
-        ref = oracle.louvain(g, oracle.Config())
-        assert np.array_equal(memb, ref.membership), k
-        assert (num, den, passes, why) == (ref.q_num, ref.q_den, ref.passes, ref.exit_reason), k
+        res2 = b.run().result()
+    for r in (res, res2):
+        for k, g in enumerate(graphs):
+            memb, q, num, den, passes, comms, why = r.graph(k)
+            ref = oracle.louvain(g, oracle.Config())
+            assert np.array_equal(memb, ref.membership), k
+            assert (num, den, passes, why) == (ref.q_num, ref.q_den, ref.passes, ref.exit_reason), k
+            assert np.array_equal(r.pass_records[k, :passes, 1], ref.pass_stats[:passes, 2]), k  # l_i per pass
 
 
 def test_autotune_keeps_results():
@@ -106,10 +115,41 @@ def test_bad_schedules_refused():
     with lv.Louvain(g) as ctx:
         for bad in (dict(group_max=8), dict(group_max=65), dict(group_max=64, warp_max=32), dict(warp_max=300),
                     dict(half_max=200), dict(group_max=64, half_max=32),
-                    dict(move_warp=0), dict(move_hub=4), dict(merge_big=5), dict(graphs=2), dict(move_thread=65),
+                    dict(move_warp=0), dict(move_hub=4), dict(merge_big=5), dict(graphs=3), dict(move_thread=65),
                     dict(concurrent=3)):
             before = ctx.schedule()
             with pytest.raises(lv.LouvainError) as ei:
                 ctx.set_schedule(bad)
             assert ei.value.status == 1
             assert ctx.schedule() == before
+
+
+@pytest.mark.parametrize("name", ["grid96_many_iterations", "rmat19_hubs", "sbm_iteration_cap"])
+def test_device_controlled_phase(name):
+    """graphs = 2: each pass's local-moving phase is one graph launch whose
+    conditional while node repeats the iteration until the device-side
+    tolerance test stops it (no host synchronisation per iteration).  The
+    iteration counts, per-iteration records and results equal the oracle's,
+    also with the hub path (static rounds) and at the iteration cap."""
+    cfg = lv.Config()
+    if name == "grid96_many_iterations":
+        g = gg.grid(96, 0.02, seed=3, weight_range=(1, 8))
+    elif name == "rmat19_hubs":
+        g = gg.rmat(19, 16, seed=7)
+    else:
+        g = gg.sbm(3000, 50, 0.3, 0.004, seed=4)
+        cfg = lv.Config(tolerance=0.0, max_iterations=7)  # every phase runs to the cap
+    with lv.Louvain(lv.DeviceCSR.from_host(g), cfg) as ctx:
+        ctx.set_schedule(dict(graphs=2, concurrent=1))
+        res = ctx.run().result()
+        st = ctx.stats()
+        res2 = ctx.run().result()
+    ref = oracle.louvain(g, oracle.Config(tolerance=cfg.tolerance, max_iterations=cfg.max_iterations))
+    for r in (res, res2):
+        assert r.passes == ref.passes
+        P = ref.passes
+        assert np.array_equal(r.iter_stats[:P], ref.iter_stats[:P])
+        assert np.array_equal(r.pass_stats[:P, :4], ref.pass_stats[:P, :4])
+        assert np.array_equal(r.membership, ref.membership)
+        assert (r.q_num, r.q_den) == (ref.q_num, ref.q_den)
+    assert st["iterations"] == int(ref.pass_stats[:ref.passes, 2].sum())
