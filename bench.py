@@ -178,6 +178,59 @@ def move_bin_degrees(kernel: str, sched: dict):
             "move_hub": [32769, None]}.get(kernel)
 
 
+def _fmix32(h):
+    """MurmurHash3's 32-bit finaliser on a numpy uint32 array."""
+    h = h.astype(np.uint64)
+    m = np.uint64(0xFFFFFFFF)
+    h ^= h >> np.uint64(16)
+    h = (h * np.uint64(0x85EBCA6B)) & m
+    h ^= h >> np.uint64(13)
+    h = (h * np.uint64(0xC2B2AE35)) & m
+    h ^= h >> np.uint64(16)
+    return h
+
+
+def first_launch_entries(g, kernel: str, sched: dict, launches: int, buckets: int = 4, seed: int = 0):
+    """Row entries that the first `launches` launches of a local-moving bin
+    kernel take in a plain run: the buckets 0, 1, ... of iteration 0 of pass
+    0, where every vertex is unprocessed (bucket hash as in
+    include/louvain.h).  Used to turn the DRAM bytes of an ncu capture of
+    those launches into bytes per entry."""
+    lo, hi = move_bin_degrees(kernel, sched)
+    deg = np.diff(g.offsets)
+    inbin = (deg >= lo) & ((deg <= hi) if hi is not None else True)
+    fold = (seed & 0xFFFFFFFF) ^ (seed >> 32)
+    salt = int(_fmix32(np.array([fold ^ ((0 * 0x9E3779B1) & 0xFFFFFFFF)], dtype=np.uint64))[0])
+    b = _fmix32(np.arange(g.n, dtype=np.uint64) ^ np.uint64(salt)) % np.uint64(buckets)
+    return [int(deg[inbin & (b == np.uint64(k))].sum()) for k in range(launches)]
+
+
+def stored_traffic(kernel: str):
+    """(DRAM bytes per row entry, capture record) of `kernel` from
+    profiles/traffic.json, or (None, None) if there is none or the library's
+    sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        tj = json.load(open(path))
+    except (OSError, ValueError):
+        return None, None
+    ent = tj.get(kernel)
+    if not ent or ent.get("sources") != source_hash():
+        return None, None
+    return ent.get("dram_bytes_per_entry"), ent
+
+
+def source_hash() -> str:
+    """FNV-1a of the library's CUDA sources, so that a stored capture is used
+    only for the kernels it measured."""
+    import glob
+    h = 0xcbf29ce484222325
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2501_19004_gb300", "csrc", "*"))):
+        for byte in open(f, "rb").read():
+            h = ((h ^ byte) * 0x100000001b3) & 0xFFFFFFFFFFFFFFFF
+    return f"{h:016x}"
+
+
 def max_over_ranks(x: float, world: int, device=None) -> float:
     """The largest x over all ranks (the slowest rank's time), by one
     all-reduce; x itself on a single rank."""
@@ -430,18 +483,14 @@ def main():
 
     peaks, src = load_peaks()
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else None
+    # DRAM bytes per launch: a small capture's bytes per row entry (ncu on
+    # R-MAT scale 22, profiles/traffic.json, current sources only) times the
+    # entries of this run's average launch of the dominant kernel
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        try:
-            tj = json.load(open(tpath))
-            ent = tj.get(args.workload, {}).get(dom)
-            # per-launch DRAM bytes describe the same work only if the bin
-            # took the same degrees when they were captured
-            if ent and ent.get("bin_degrees") == move_bin_degrees(dom, run_sched):
-                traffic = ent.get("dram_bytes_per_launch")
-        except (OSError, ValueError):
-            traffic = None
+    per_entry, tent = stored_traffic(dom)
+    dom_entries = st["kernels"].get(dom, {}).get("entries", 0.0)
+    if per_entry and dom_launches:
+        traffic = per_entry * (dom_entries * args.steps) / dom_launches
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": (achieved / peaks["hbm_gbs"]) if achieved else None, "peak_source": f"{src} hbm_gbs",
                 "traffic": traffic,

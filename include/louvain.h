@@ -52,7 +52,12 @@ typedef enum {
   LOUVAIN_E_NOMEM = 2,          /* device or host allocation failed */
   LOUVAIN_E_CUDA = 3,           /* a CUDA call failed (see louvain_last_error) */
   LOUVAIN_E_HASH_OVERFLOW = 4,  /* a hashtable probe sequence exceeded its bound
-                                   (the paper's "failed" result of Algorithm 7) */
+                                   (the paper's "failed" result of Algorithm 7, after
+                                   MAX_RETRIES probes).  Tables hold at least twice as
+                                   many slots as keys, so the bound is the table size
+                                   and no input reaches it; a library built with
+                                   -DLOUVAIN_MAX_PROBES=k gives up after k probes.
+                                   A failed run leaves the context usable. */
   LOUVAIN_E_TIMEOUT = 5,        /* a bounded device-side wait gave up (reserved: no
                                    kernel of this library waits on a flag) */
   LOUVAIN_E_OVERFLOW = 6,       /* 2m >= 2^32: scores would not fit in int64 */
@@ -88,7 +93,7 @@ typedef struct {
   double tolerance_drop;
   double aggregation_tolerance;
   int32_t pickless_period;       /* rho; 0 disables Pick-Less mode */
-  int32_t buckets;               /* B >= 1 of the deterministic schedule (4) */
+  int32_t buckets;               /* B of the deterministic schedule, 1 .. 65536 (4) */
   uint64_t schedule_seed;
   int32_t mode;                  /* louvain_mode */
   const float *model;            /* LEARNED: host pointer to the predictor's
@@ -297,7 +302,12 @@ louvain_status louvain_modularity_of(const louvain_graph *graph, const int32_t *
  * log2(1 + degree)/24, intra-community weight fraction and best-dQ margin
  * (s(c*) - s(d))/(2m K_i) at its last evaluation, moved at its last
  * evaluation, iteration/MAX_ITERATIONS, pass/MAX_PASSES, Sigma of its
- * community/2m, and min(1, neighbour moves since its last evaluation/degree).
+ * community/2m, and the fraction of its sampled neighbours that moved since
+ * its last evaluation (the whole row up to 96 entries; for longer rows the
+ * neighbours j with fmix32(j ^ fmix32(i ^ 0x5BD1E995)) < 2^32 * 32 / degree,
+ * or the whole row if more than 96 qualify).  Only vertices of degree at least learned_min_degree are
+ * candidates; with learned_fallback = 3 an iteration that meets the
+ * tolerance is completed by evaluating what it skipped (see below).
  */
 
 /* louvain_modularity_of without any allocation, for callers that cannot let
@@ -395,17 +405,6 @@ louvain_status louvain_mlp_train(float *params, const float *X, const float *Y, 
 
 /* Library build description (architecture, version). */
 const char *louvain_version(void);
-
-/* Longest probe sequence of a hashtable insert, the MAX_RETRIES of the
- * paper's Algorithm 7 (hashtableAccumulate), after which the insert fails
- * and the run returns LOUVAIN_E_HASH_OVERFLOW (Algorithm 7's "failed").
- * Every table of this library holds at least twice as many slots as keys,
- * so by default (max_probes = 0: no limit but the table size) no input
- * fails; a small limit makes collisions fail, which exercises that failure
- * path.  It applies on the current device to every later call, of every
- * context, until changed.  A run that failed leaves the context usable:
- * the next louvain_run starts from clean tables. */
-louvain_status louvain_set_probe_limit(uint32_t max_probes);
 
 #ifdef __cplusplus
 }

@@ -45,17 +45,21 @@ def stale() -> bool:
     return any(os.path.getmtime(d) > t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not stale():
+def build(force: bool = False, verbose: bool = False, defines=(), lib: str = LIB, objdir: str = OUT_DIR) -> str:
+    """Build the library (if stale, or with force).  `defines` (NAME=VALUE
+    strings) and another `lib` path / `objdir` build a variant of the same
+    sources, e.g. with a probe bound for the failure tests."""
+    if not force and not defines and lib == LIB and not stale():
         return LIB
     nvcc = _nvcc()
-    os.makedirs(OUT_DIR, exist_ok=True)
+    os.makedirs(objdir, exist_ok=True)
     procs = []
     objs = []
+    dflags = [f"-D{d}" for d in defines]
     for src in sources():
-        obj = os.path.join(OUT_DIR, os.path.basename(src).replace(".cu", ".o"))
+        obj = os.path.join(objdir, os.path.basename(src).replace(".cu", ".o"))
         objs.append(obj)
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *FLAGS, *dflags, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)))
@@ -69,10 +73,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         msg = "\n".join(f"--- {s}\n{o}" for s, o in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

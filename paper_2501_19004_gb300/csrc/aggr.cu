@@ -784,6 +784,4 @@ void renumber_dense(int32_t *x, int64_t n, int64_t idspace, unsigned long long *
   LV_LAUNCH(k_relabel<<<grid_for(n, 256, num_sms, 16), 256, 0, s>>>(x, n, newid));
 }
 
-cudaError_t set_probe_limit_aggr(uint32_t v) { return set_probe_limit_here(v); }
-
 }  // namespace lv

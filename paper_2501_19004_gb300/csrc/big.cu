@@ -379,12 +379,7 @@ __global__ void __launch_bounds__(kNT) k_big_decide(BigArgs a, int r) {
     }
     __syncthreads();
     if (s_target >= 0)
-      for (int64_t q = b + threadIdx.x; q < e; q += kNT) {
-        const int32_t j = __ldg(a.g.col + q);
-        if (j != i) {
-          mark_neighbour(a.flag, a.learn, j);
-        }
-      }
+      mark_neighbours(a.flag, a.g.col, b, e, threadIdx.x, kNT, i);
     __syncthreads();
   }
   flush_gains(glo, ghi, gm, a.ctr);
@@ -485,7 +480,5 @@ void big_merge(const BigArgs &b, int wkind, int num_sms, cudaStream_t s, KernelP
   if (wkind == W_UNIT) big_rounds<MODE_MERGE, W_UNIT>(b, num_sms, s, prof);
   else big_rounds<MODE_MERGE, W_U32>(b, num_sms, s, prof);
 }
-
-cudaError_t set_probe_limit_big(uint32_t v) { return set_probe_limit_here(v); }
 
 }  // namespace lv

@@ -65,6 +65,8 @@ struct Counters {
   unsigned long long mod_count[2];  // modularity: rows handed to warps / to whole blocks
   unsigned long long descents[2];   // validation: adjacent entries with col[k-1] >= col[k] (all / at row starts)
   unsigned long long skip_listed;   // learned mode: vertices the predictor skipped in the current iteration
+  unsigned long long sample_blocks; // learned features: neighbour-sample blocks handed out this pass
+  unsigned long long sample_chunks; //   and row chunks to sample
 };
 constexpr int kIterCounterWords = 5 + 45;
 

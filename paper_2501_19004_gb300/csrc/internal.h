@@ -54,6 +54,15 @@ constexpr int kHalfLanes = 16;
 constexpr int kHalfMaxDeg = 128;
 constexpr int kHalfBin = 8;
 constexpr int kMoveBins = 9;
+// Neighbour samples of the learned features: a row longer than kSample is
+// represented by the neighbours j whose pair hash falls below
+// 2^32 kSampleTarget / degree (about kSampleTarget of them, Binomial), stored
+// in a block of kSample slots.  More than kSample of them (a chance below
+// 1e-18 per row) and the row is read whole instead.  Rows are sampled in
+// chunks of kSampleChunk entries, one block per chunk.
+constexpr int kSample = 96;
+constexpr int kSampleTarget = 32;
+constexpr int kSampleChunk = 2048;
 static_assert(sizeof(Counters::bin_count) == kMoveBins * sizeof(unsigned long long), "one counter per move bin");
 // Aggregation bins: degree_bin's five plus communities with a total member
 // degree in (4096, kXlMaxDeg] for one 1024-thread block (bin 5) and in
@@ -91,10 +100,8 @@ struct Sched {
 constexpr int kSchedWords = 3 + kMoveBins + kMergeBins + 2;
 
 // Flag byte of a vertex: kFlagUnproc = not processed since a neighbour moved
-// (vertex pruning, Sec. 4.1.6); kFlagTracked = the learned predictor keeps
-// its features (set at pass start, kept by every later write).
+// (vertex pruning, Sec. 4.1.6).
 constexpr uint8_t kFlagUnproc = 0x01;
-constexpr uint8_t kFlagTracked = 0x02;
 constexpr unsigned long long kFlagUnproc8 = 0x0101010101010101ull;  // kFlagUnproc in each of 8 bytes
 
 // Per-vertex byte of the pass (pass_init): the move bin in the low six bits
@@ -183,8 +190,19 @@ struct LearnArgs {
   int record = 0;               // per-vertex features are maintained
   const float *params = nullptr;  // device MLP parameters
   float4 *feat = nullptr;       // [n] intra fraction, margin, moved, valid
-  uint32_t *marks = nullptr;    // [n] neighbour moves since the last evaluation (as of the bucket's snapshot)
-  uint32_t *marks_next = nullptr;  // [n] moves of the current bucket, folded into marks by the next selection
+  // Neighbour-move feature (x7): bucket stamps, increasing within a pass
+  // from 1 (0: never), and a hash-chosen sample of the neighbours of every
+  // tracked vertex whose row is longer than kSample (shorter rows are their
+  // own sample).
+  uint32_t stamp = 0;             // stamp of the current bucket
+  uint32_t *seen = nullptr;       // [n] stamp of the vertex's last evaluation
+  uint32_t *moved_at = nullptr;   // [n] stamp of the bucket in which the vertex last moved
+  int32_t *sample = nullptr;      // [sample_cap][kSample] samples (in no particular order)
+  uint32_t *sample_n = nullptr;   // [sample_cap] neighbours that qualified for the block
+  int32_t *sample_at = nullptr;   // [n] the vertex's sample block, -1: its row is its sample
+  int64_t sample_cap = 0;         // sample blocks allocated
+  int2 *chunks = nullptr;         // [chunk_cap] (vertex, chunk) of the rows to sample
+  int64_t chunk_cap = 0;
   int32_t *cand = nullptr;      // [n] candidates of the bucket
   float thr_logit = 0.f;        // evaluate iff logit >= thr_logit
   int skip_clears = 0;          // a skip clears the flag (counts as "stay")
@@ -428,11 +446,6 @@ void batch_gather(const int64_t *src, const int64_t *idx, int64_t m, int64_t *ou
 void batch_final(int64_t n0, int32_t *C, const int32_t *ogid, const int32_t *Cp, const int64_t *newid,
                  const int64_t *vo, const int8_t *fin, int32_t *out, int num_sms, cudaStream_t s);
 void batch_exclude(int64_t n, const int32_t *gid, const int8_t *fin, int32_t *Cp, int num_sms, cudaStream_t s);
-
-// Probe limit of the table inserts of each translation unit (tables.cuh).
-cudaError_t set_probe_limit_move(uint32_t v);
-cudaError_t set_probe_limit_aggr(uint32_t v);
-cudaError_t set_probe_limit_big(uint32_t v);
 
 // Kernel launches issued by this thread since the last reset (the library's
 // own kernels only; memsets and copies are not counted).

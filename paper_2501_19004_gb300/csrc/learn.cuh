@@ -7,13 +7,46 @@
 //   x3 = 1 if it moved at its last evaluation
 //   x4 = iteration / MAX_ITERATIONS, x5 = pass / MAX_PASSES
 //   x6 = Sigma of its community / 2m
-//   x7 = min(1, neighbour moves since its last evaluation / degree)
+//   x7 = fraction of its sampled neighbours that moved since its last
+//        evaluation: a neighbour counts when the bucket of its last move is
+//        not earlier than the bucket of the vertex's last evaluation.  The
+//        sample is the whole row up to kSample entries; for longer rows, the
+//        neighbours j with fmix32(j ^ fmix32(i ^ kSampleSalt)) below
+//        2^32 kSampleTarget / degree, a set that does not depend on the order
+//        of the row (the whole row again if more than kSample qualify).
 // Features are valid from the second evaluation of a vertex in a pass on.
 #pragma once
 #include "internal.h"
 #include "mlp.cuh"
 
 namespace lv {
+
+constexpr uint32_t kSampleSalt = 0x5BD1E995u;
+
+// Feature x7 of vertex i (see above).
+__device__ __forceinline__ float neighbour_move_fraction(const GView &g, const LearnArgs &L, int32_t i) {
+  const uint32_t since = L.seen[i];
+  unsigned moved = 0, total = 0;
+  const int32_t at = L.sample_at[i];
+  const uint32_t ns = at >= 0 ? L.sample_n[at] : 0u;
+  if (at < 0 || ns > (uint32_t)kSample) {
+    for (int64_t k = g.begin[i], e = g.end[i]; k < e; ++k) {
+      const int32_t j = __ldg(g.col + k);
+      if (j == i) continue;
+      const uint32_t m = L.moved_at[j];
+      ++total;
+      moved += (m != 0u && m >= since) ? 1u : 0u;
+    }
+  } else {
+    const int32_t *sp = L.sample + (int64_t)at * kSample;
+    for (uint32_t p = 0; p < ns; ++p) {
+      const uint32_t m = L.moved_at[sp[p]];
+      moved += (m != 0u && m >= since) ? 1u : 0u;
+    }
+    total = ns;
+  }
+  return total ? (float)moved / (float)total : 0.f;
+}
 
 __device__ __forceinline__ void vertex_features(const GView &g, const int32_t *Cp, const int64_t *Sigma,
                                                 long long two_m, const LearnArgs &L, int32_t i, float4 fv,
@@ -26,7 +59,7 @@ __device__ __forceinline__ void vertex_features(const GView &g, const int32_t *C
   x[4] = L.t_norm;
   x[5] = L.p_norm;
   x[6] = (float)Sigma[Cp[i]] / (float)two_m;
-  x[7] = fminf(1.f, (float)L.marks[i] / (float)(deg > 0 ? deg : 1));
+  x[7] = neighbour_move_fraction(g, L, i);
 }
 
 // After the decision for vertex i (community d, K_i, K_{i->d}, best
@@ -60,25 +93,16 @@ __device__ __forceinline__ void learn_record(const LearnArgs &L, Counters *ctr, 
   nv.z = moved ? 1.f : 0.f;
   nv.w = 1.f;
   L.feat[i] = nv;
-  L.marks[i] = 0;
+  L.seen[i] = L.stamp;
 }
 
-// A mover's neighbour j: marked unprocessed (vertex pruning, bit kFlagUnproc
-// of its flag byte) and, when features are kept, the move counts for j's
-// next evaluation.  Moves go to marks_next, which the next selection folds
-// into marks, so a decision never sees marks that change while its bucket
-// runs.  When only vertices of some minimum degree keep features, their
-// flag bytes carry kFlagTracked (set at pass start): the byte is read and
-// written back, one sector as for the plain store, and only tracked
-// neighbours pay the atomic.
-__device__ __forceinline__ void mark_neighbour(uint8_t *flag, const LearnArgs &L, int32_t j) {
-  if (L.record && L.min_degree > 0) {
-    const uint8_t f = flag[j];
-    flag[j] = (uint8_t)(f | kFlagUnproc);
-    if (f & kFlagTracked) atomicAdd(L.marks_next + j, 1u);
-  } else {
-    flag[j] = kFlagUnproc;
-    if (L.record) atomicAdd(L.marks_next + j, 1u);
+// The neighbours col[k] (k = b + t, b + t + stride, ... < e) of mover i are
+// marked unprocessed (vertex pruning, Sec. 4.1.6): one plain byte store each.
+__device__ __forceinline__ void mark_neighbours(uint8_t *flag, const int32_t *col, int64_t b, int64_t e, int64_t t,
+                                                int64_t stride, int32_t i) {
+  for (int64_t k = b + t; k < e; k += stride) {
+    const int32_t j = __ldg(col + k);
+    if (j != i) flag[j] = kFlagUnproc;
   }
 }
 

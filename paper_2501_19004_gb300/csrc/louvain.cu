@@ -91,7 +91,15 @@ struct louvain_ctx {
   // learned predictor and trace recorder
   float *mlp = nullptr;
   float4 *feat = nullptr;
-  uint32_t *marks = nullptr, *marks_next = nullptr;
+  uint32_t *seen = nullptr;       // learned features: bucket stamps of evaluations and moves,
+  uint32_t *moved_at = nullptr;   //   neighbour samples (see LearnArgs)
+  int32_t *sample = nullptr;
+  uint32_t *sample_n = nullptr;
+  int32_t *sample_at = nullptr;
+  int64_t sample_cap = 0;
+  int2 *chunks = nullptr;
+  int64_t chunk_cap = 0;
+  uint32_t stamp = 0;             // stamp of the last bucket enqueued in the current pass
   int32_t *cand = nullptr;
   int32_t *skip_list = nullptr;  // learned: vertices skipped in the current iteration
   float *trace_x = nullptr, *trace_y = nullptr;
@@ -539,8 +547,15 @@ LearnArgs learn_args(louvain_ctx *x, int pass, int t, bool skipping) {
   L.enabled = skipping && cfg.mode == LOUVAIN_MODE_LEARNED;
   L.params = x->mlp;
   L.feat = x->feat;
-  L.marks = x->marks;
-  L.marks_next = x->marks_next;
+  L.seen = x->seen;
+  L.moved_at = L.record ? x->moved_at : nullptr;
+  L.sample = x->sample;
+  L.sample_n = x->sample_n;
+  L.sample_at = x->sample_at;
+  L.sample_cap = x->sample_cap;
+  L.chunks = x->chunks;
+  L.chunk_cap = x->chunk_cap;
+  L.stamp = x->stamp;
   L.cand = x->cand;
   const double th = std::min(std::max((double)cfg.skip_threshold, 1e-6), 1.0 - 1e-6);
   L.thr_logit = (float)std::log(th / (1.0 - th));
@@ -899,6 +914,7 @@ louvain_status enqueue_iteration(louvain_ctx *x, const GView &g, int wk, int pas
       LV_CK(cudaMemsetAsync(x->d_ctr, 0, offsetof(Counters, it_gain_lo), x->stream));
       if (L.enabled) LV_CK(cudaMemsetAsync(&x->d_ctr->cand_count, 0, sizeof(unsigned long long), x->stream));
       a.bucket = (uint32_t)b;
+      if (L.record) a.learn.stamp = big.learn.stamp = ++x->stamp;  // every bucket (and completion step) a later stamp
       move_bucket(a, big, wk, x->num_sms, x->stream, x->prof.mask ? &x->prof : nullptr,
                   x->side.fork ? &x->side : nullptr);
     }
@@ -1181,6 +1197,7 @@ louvain_status run_impl(louvain_ctx *x, bool fresh = true, int32_t budget = 0, i
     LV_CK(cudaMemsetAsync(&x->d_ctr->big_slots, 0, 2 * sizeof(unsigned long long), s));
     x->prof.begin(K_PASS_INIT, s);
     {
+      x->stamp = 0;  // pass init clears the stamps
       const LearnArgs L = learn_args(x, p, 0, false);
       pass_init(g, wk, p == 0, x->K, x->Sigma, x->Cp, x->flag, x->d_ctr, x->num_sms, s, &L, x->vbin, &x->sched);
       LV_CK(cudaMemsetAsync(x->recv, 0, (size_t)(g.n / 32 + 1) * sizeof(uint32_t), s));  // every community a singleton
@@ -1521,7 +1538,7 @@ louvain_status ensure_prof_events(louvain_ctx *x) {
 louvain_status validate_config(const louvain_config *c) {
   if (!c) return LOUVAIN_E_INVAL;
   if (c->max_passes < 0 || c->max_passes > 64 || c->max_iterations < 1 || c->max_iterations > 255) return LOUVAIN_E_INVAL;
-  if (c->buckets < 1 || c->pickless_period < 0) return LOUVAIN_E_INVAL;
+  if (c->buckets < 1 || c->buckets > 65536 || c->pickless_period < 0) return LOUVAIN_E_INVAL;
   if (!(c->tolerance >= 0) || !(c->tolerance_drop > 0) || !(c->aggregation_tolerance >= 0)) return LOUVAIN_E_INVAL;
   if (c->mode != LOUVAIN_MODE_PLAIN && c->mode != LOUVAIN_MODE_LEARNED) return LOUVAIN_E_INVAL;
   if (c->mode == LOUVAIN_MODE_LEARNED && (!c->model || c->max_iterations > 127)) return LOUVAIN_E_INVAL;
@@ -1700,8 +1717,16 @@ louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg
         (st = dalloc_n(x, &x->pbeg[k], nv)) || (st = dalloc_n(x, &x->pend[k], nv)))
       return fail(st);
   if (cfg->mode == LOUVAIN_MODE_LEARNED || cfg->trace_capacity > 0) {
-    if ((st = dalloc_n(x, &x->feat, nv)) || (st = dalloc_n(x, &x->marks, nv)) ||
-        (st = dalloc_n(x, &x->marks_next, nv)))
+    // rows sampled for the feature x7 have at least dmin = max(min degree,
+    // kSample + 1) entries, so no pass (whose nnz is at most the input's) has
+    // more than nnz / dmin of them, nor more than nnz / kSampleChunk + nnz / dmin
+    // chunks
+    const int64_t dmin = std::max<int64_t>(cfg->learned_min_degree, kSample + 1);
+    x->sample_cap = nnz / dmin + 1;
+    x->chunk_cap = nnz / kSampleChunk + nnz / dmin + 1;
+    if ((st = dalloc_n(x, &x->feat, nv)) || (st = dalloc_n(x, &x->seen, nv)) || (st = dalloc_n(x, &x->moved_at, nv)) ||
+        (st = dalloc_n(x, &x->sample_at, nv)) || (st = dalloc_n(x, &x->sample, x->sample_cap * kSample)) ||
+        (st = dalloc_n(x, &x->sample_n, x->sample_cap)) || (st = dalloc_n(x, &x->chunks, x->chunk_cap)))
       return fail(st);
   }
   if (cfg->mode == LOUVAIN_MODE_LEARNED) {
@@ -2700,15 +2725,5 @@ louvain_status louvain_mlp_train(float *params, const float *X, const float *Y, 
 }
 
 const char *louvain_version(void) { return "gb300-louvain 0.1 (sm_103a)"; }
-
-louvain_status louvain_set_probe_limit(uint32_t max_probes) {
-  const uint32_t v = max_probes ? max_probes : 0xFFFFFFFFu;
-  if (set_probe_limit_move(v) != cudaSuccess || set_probe_limit_aggr(v) != cudaSuccess ||
-      set_probe_limit_big(v) != cudaSuccess) {
-    set_err(nullptr, "could not set the probe limit on the current device");
-    return LOUVAIN_E_CUDA;
-  }
-  return LOUVAIN_OK;
-}
 
 }  // extern "C"

@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
     unsigned long long fl = 0, vbw = 0;
     if (whole) {
       fl = *reinterpret_cast<const unsigned long long *>(a.flag + i0);
-      if (((fl & kFlagUnproc8) || a.learn.record) && a.vbin)
+      if ((fl & kFlagUnproc8) && a.vbin)
         vbw = *reinterpret_cast<const unsigned long long *>(a.vbin + i0);
     } else {
 #pragma unroll
@@ -78,13 +78,6 @@ __global__ void __launch_bounds__(256) k_select(MoveArgs a) {
       const bool tracked = a.learn.min_degree == 0 ||
                            (a.vbin ? (vbyte & kVbinTracked) != 0
                                    : (i < n && a.g.end[i] - a.g.begin[i] >= a.learn.min_degree));
-      if (a.learn.record && i < n && tracked) {  // the previous bucket's neighbour moves
-        const uint32_t mn = a.learn.marks_next[i];
-        if (mn) {
-          a.learn.marks[i] += mn;
-          a.learn.marks_next[i] = 0;
-        }
-      }
       bool live = ((fl >> (8 * v)) & (unsigned long long)kFlagUnproc) != 0;
       uint32_t local = (uint32_t)i;
       if (live && a.batch.gid) {  // batched: only graphs still moving, hashed by their local ids
@@ -363,9 +356,7 @@ __global__ void __launch_bounds__(256) k_move_thread(MoveArgs a) {
         work[4] += (unsigned long long)deg;
 #pragma unroll
         for (int k = 0; k < D; ++k)
-          if (jj[k] != i) {
-            mark_neighbour(a.flag, a.learn, jj[k]);
-          }
+          if (jj[k] != i) a.flag[jj[k]] = kFlagUnproc;
       }
     }
     const bool mv = target >= 0;
@@ -485,12 +476,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_move_warp(MoveArgs a) {
     }
     target = __shfl_sync(kFull, target, 0);
     if (target >= 0)
-      for (int64_t k = b + lane; k < e; k += 32) {
-        const int32_t j = __ldg(a.g.col + k);
-        if (j != i) {
-          mark_neighbour(a.flag, a.learn, j);
-        }
-      }
+      mark_neighbours(a.flag, a.g.col, b, e, lane, 32, i);
     __syncwarp();
   }
   flush_gains(glo, ghi, gm, a.ctr);
@@ -597,12 +583,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) k_move_group(MoveArgs a) {
     }
     target = __shfl_sync(kFull, target, grp * GS);
     if (target >= 0)
-      for (int64_t k = b + gl; k < b + deg; k += GS) {
-        const int32_t j = __ldg(a.g.col + k);
-        if (j != i) {
-          mark_neighbour(a.flag, a.learn, j);
-        }
-      }
+      mark_neighbours(a.flag, a.g.col, b, b + deg, gl, GS, i);
     __syncwarp();
   }
   flush_gains(glo, ghi, gm, a.ctr);
@@ -688,12 +669,7 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : NT == 512 ? 2 : 1) k_move_
     }
     __syncthreads();
     if (s_target >= 0)
-      for (int64_t k = b + threadIdx.x; k < e; k += NT) {
-        const int32_t j = __ldg(a.g.col + k);
-        if (j != i) {
-          mark_neighbour(a.flag, a.learn, j);
-        }
-      }
+      mark_neighbours(a.flag, a.g.col, b, e, threadIdx.x, NT, i);
     __syncthreads();
   }
   flush_gains(glo, ghi, gm, a.ctr);
@@ -730,7 +706,8 @@ __device__ __forceinline__ bool wide_insert(int32_t *keys, uint32_t *vals, uint1
                                             int32_t key, uint32_t w, Counters *ctr) {
   constexpr uint32_t mask = kXlCap - 1;
   uint32_t s = slot_of(key, mask);
-  for (uint32_t t = 0; t <= mask && t < c_probe_limit; ++t) {
+  const uint32_t lim = mask < kMaxProbes ? mask + 1 : kMaxProbes;  // probes allowed
+  for (uint32_t t = 0; t < lim; ++t) {
     int32_t k = ((volatile int32_t *)keys)[s];
     if (k == kEmpty) {
       const unsigned ticket = atomicAdd(nocc, 1u);
@@ -908,12 +885,7 @@ __global__ void __launch_bounds__(1024, 1) k_move_wide(MoveArgs a) {
     }
     __syncthreads();
     if (s_target >= 0)
-      for (int64_t k = b + threadIdx.x; k < e; k += NT) {
-        const int32_t j = __ldg(a.g.col + k);
-        if (j != i) {
-          mark_neighbour(a.flag, a.learn, j);
-        }
-      }
+      mark_neighbours(a.flag, a.g.col, b, e, threadIdx.x, NT, i);
   }
   flush_gains(glo, ghi, gm, a.ctr);
   flush_work(work, a.ctr->mv_work[kXlBin]);
@@ -929,8 +901,63 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
     const long long Ki = a.K[i];
     a.Cp[i] = c;
     if (a.recv) atomicOr(a.recv + (c >> 5), 1u << (c & 31));  // community c is no longer a known singleton
+    if (a.learn.moved_at) a.learn.moved_at[i] = a.learn.stamp;
     atomicAdd((unsigned long long *)(a.Sigma + d), as_ull(-Ki));
     atomicAdd((unsigned long long *)(a.Sigma + c), as_ull(Ki));
+  }
+}
+
+// --------------------------------------------------- neighbour samples
+// Per pass, for the learned feature x7 (see learn.cuh).  The plan kernel
+// gives every tracked vertex with a row longer than kSample a sample block
+// and one chunk record per kSampleChunk entries of its row (sample_at = -1
+// for the others); the chunk kernel then tests the entries of one chunk per
+// block and appends the neighbours that pass the pair-hash test to the
+// block.  The stored set is fixed by the graph; only its order varies.
+__global__ void __launch_bounds__(256) k_sample_plan(GView g, LearnArgs L, Counters *ctr) {
+  const int64_t dmin = L.min_degree > kSample ? L.min_degree : kSample + 1;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t deg = g.end[v] - g.begin[v];
+    int32_t at = -1;
+    if (deg >= dmin) {
+      const unsigned long long blk = atomicAdd(&ctr->sample_blocks, 1ull);
+      const int64_t nch = (deg + kSampleChunk - 1) / kSampleChunk;
+      const unsigned long long c0 = atomicAdd(&ctr->sample_chunks, (unsigned long long)nch);
+      // both lists are sized for the input's rows (louvain_create); a
+      // vertex that finds no room keeps reading its whole row
+      if ((int64_t)blk < L.sample_cap && (int64_t)(c0 + nch) <= L.chunk_cap) {
+        at = (int32_t)blk;
+        L.sample_n[at] = 0u;
+        for (int64_t c = 0; c < nch; ++c) L.chunks[c0 + c] = make_int2((int)v, (int)c);
+      } else {
+        for (int64_t c = 0; c < nch; ++c)
+          if ((int64_t)(c0 + c) < L.chunk_cap) L.chunks[c0 + c] = make_int2(-1, 0);
+      }
+    }
+    L.sample_at[v] = at;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_sample_chunks(GView g, LearnArgs L, const Counters *ctr) {
+  const unsigned long long total = ctr->sample_chunks;
+  const long long nch = (long long)total < L.chunk_cap ? (long long)total : L.chunk_cap;
+  for (long long q = blockIdx.x; q < nch; q += gridDim.x) {
+    const int2 rec = L.chunks[q];
+    const int32_t i = rec.x;
+    if (i < 0) continue;
+    const int64_t b = g.begin[i], e = g.end[i];
+    const unsigned long long thr = ((unsigned long long)kSampleTarget << 32) / (unsigned long long)(e - b);
+    const uint32_t salt = fmix32((uint32_t)i ^ kSampleSalt);
+    const int32_t at = L.sample_at[i];
+    const int64_t k0 = b + (int64_t)rec.y * kSampleChunk;
+    const int64_t k1 = k0 + kSampleChunk < e ? k0 + kSampleChunk : e;
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+      const int32_t j = __ldg(g.col + k);
+      if (j != i && (unsigned long long)fmix32((uint32_t)j ^ salt) < thr) {
+        const uint32_t pos = atomicAdd(L.sample_n + at, 1u);
+        if (pos < (uint32_t)kSample) L.sample[(int64_t)at * kSample + pos] = j;
+      }
+    }
   }
 }
 
@@ -941,7 +968,7 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
 template <int WK>
 __global__ void __launch_bounds__(256) k_pass_init(GView g, int first_pass, int64_t *K, int64_t *Sigma,
                                                    int32_t *Cp, uint8_t *flag, Counters *ctr, float4 *feat,
-                                                   uint32_t *marks, uint32_t *marks_next, uint8_t *vbin,
+                                                   uint32_t *seen, uint32_t *moved_at, uint8_t *vbin,
                                                    int group_max, int half_max, int warp_max, int64_t track_min) {
   unsigned long long md = 0, big_slots = 0, big_items = 0;
   const int lane = threadIdx.x & 31;
@@ -970,11 +997,11 @@ __global__ void __launch_bounds__(256) k_pass_init(GView g, int first_pass, int6
     }
     Sigma[i] = k;
     Cp[i] = (int32_t)i;
-    flag[i] = (uint8_t)(kFlagUnproc | (track_min > 0 && (int64_t)deg >= track_min ? kFlagTracked : 0));
+    flag[i] = kFlagUnproc;
     if (feat) {
       feat[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      marks[i] = 0;
-      marks_next[i] = 0;
+      seen[i] = 0;
+      moved_at[i] = 0;
     }
   }
 #pragma unroll
@@ -1064,15 +1091,20 @@ template <int WK>
 void pass_init_t(const GView &g, int first, int64_t *K, int64_t *Sigma, int32_t *Cp, uint8_t *flag, Counters *ctr,
                  int num_sms, cudaStream_t s, const LearnArgs *learn, uint8_t *vbin, const Sched *sched) {
   float4 *feat = (learn && learn->record) ? learn->feat : nullptr;
-  uint32_t *marks = (learn && learn->record) ? learn->marks : nullptr;
-  uint32_t *marks_next = (learn && learn->record) ? learn->marks_next : nullptr;
+  const bool rec = learn && learn->record;
   LV_LAUNCH(k_pass_init<WK><<<grid_for(g.n, 256, num_sms, 16), 256, 0, s>>>(g, first, K, Sigma, Cp, flag, ctr, feat,
-                                                                             marks, marks_next, vbin,
+                                                                             rec ? learn->seen : nullptr,
+                                                                             rec ? learn->moved_at : nullptr, vbin,
                                                                              sched ? sched->group_max : 0,
                                                                              sched ? sched->half_max : 0,
                                                                              sched ? sched->warp_max : 0,
                                                                              (learn && learn->record) ? learn->min_degree
                                                                                                       : 0));
+  if (rec) {
+    cudaMemsetAsync(&ctr->sample_blocks, 0, 2 * sizeof(unsigned long long), s);
+    LV_LAUNCH(k_sample_plan<<<grid_for(g.n, 256, num_sms, 8), 256, 0, s>>>(g, *learn, ctr));
+    LV_LAUNCH(k_sample_chunks<<<num_sms * 8, 256, 0, s>>>(g, *learn, ctr));
+  }
 }
 
 }  // namespace
@@ -1106,7 +1138,5 @@ const char *const kKernelNames[K_NUM_KERNELS] = {
     "select", "move_thread", "move_warp", "move_mid", "move_block", "move_hub", "apply", "pass_init",
     "comm_count", "comm_scatter", "merge_thread", "merge_warp", "merge_mid", "merge_block", "merge_big",
     "dendrogram", "modularity", "renumber", "move_hub_eval", "merge_big_emit", "mlp_select", "move_group", "move_wide", "merge_xl", "merge_group", "move_half"};
-
-cudaError_t set_probe_limit_move(uint32_t v) { return set_probe_limit_here(v); }
 
 }  // namespace lv

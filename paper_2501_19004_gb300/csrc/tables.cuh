@@ -12,20 +12,23 @@ namespace lv {
 
 // Longest probe sequence of one insert: the paper's MAX_RETRIES of Algorithm
 // 7, after which the insert fails (ERR_HASH, LOUVAIN_E_HASH_OVERFLOW).  The
-// tables here are sized so that no input reaches it; louvain_set_probe_limit
-// lowers it (process-wide) to exercise the failure path.  One copy per
-// translation unit, each set by its own setter.
-static __constant__ uint32_t c_probe_limit = 0xFFFFFFFFu;
-static inline cudaError_t set_probe_limit_here(uint32_t v) {
-  return cudaMemcpyToSymbol(c_probe_limit, &v, sizeof v);
-}
+// tables here are sized so that no input reaches it, so the product build
+// has no bound but the table size; a build with -DLOUVAIN_MAX_PROBES=k makes
+// inserts give up after k probes, which the tests use to exercise the
+// failure path.  (A bound read from memory in these loops slowed the hub
+// accumulation several times over, so it is a compile-time constant.)
+#ifndef LOUVAIN_MAX_PROBES
+#define LOUVAIN_MAX_PROBES 0xFFFFFFFFu
+#endif
+constexpr uint32_t kMaxProbes = LOUVAIN_MAX_PROBES;
 
 constexpr int kRun = 8;  // consecutive entries handled by one thread per round
 
 __device__ __forceinline__ void sm_insert(int32_t *keys, uint32_t *vals, uint32_t mask, int32_t key, uint32_t w,
                                           Counters *ctr) {
   uint32_t s = slot_of(key, mask);
-  for (uint32_t t = 0; t <= mask && t < c_probe_limit; ++t) {
+  const uint32_t lim = mask < kMaxProbes ? mask + 1 : kMaxProbes;  // probes allowed
+  for (uint32_t t = 0; t < lim; ++t) {
     int32_t k = ((volatile int32_t *)keys)[s];
     if (k == kEmpty) {
       k = atomicCAS(keys + s, kEmpty, key);
@@ -46,7 +49,8 @@ __device__ __forceinline__ void sm_insert(int32_t *keys, uint32_t *vals, uint32_
 __device__ __forceinline__ void sm_insert_list(int32_t *keys, uint32_t *vals, uint32_t mask, int32_t key, uint32_t w,
                                                uint16_t *occ, unsigned *nocc, Counters *ctr) {
   uint32_t s = slot_of(key, mask);
-  for (uint32_t t = 0; t <= mask && t < c_probe_limit; ++t) {
+  const uint32_t lim = mask < kMaxProbes ? mask + 1 : kMaxProbes;  // probes allowed
+  for (uint32_t t = 0; t < lim; ++t) {
     int32_t k = ((volatile int32_t *)keys)[s];
     bool claimed = false;
     if (k == kEmpty) {
@@ -82,7 +86,8 @@ __device__ __forceinline__ int64_t gm_insert_packed_from(unsigned long long *tab
                                                          unsigned long long cur, int32_t key, uint32_t w,
                                                          Counters *ctr) {
   const unsigned long long hk = (unsigned long long)(uint32_t)(key + 1) << 32;
-  for (uint32_t t = 0; t < cap && t < c_probe_limit; ++t) {
+  const uint32_t lim = cap < kMaxProbes ? cap : kMaxProbes;  // probes allowed
+  for (uint32_t t = 0; t < lim; ++t) {
     if (cur == 0ull) {
       cur = atomicCAS(tab + s, 0ull, hk | w);
       if (cur == 0ull) return (int64_t)s;

@@ -11,6 +11,7 @@ memory and the current stream only.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import json
 import os
@@ -118,8 +119,6 @@ def load(path: Optional[str] = None):
     lib.louvain_mlp_gradient.argtypes = [vp, vp, vp, i64, vp, vp, vp]
     lib.louvain_mlp_train.restype = ctypes.c_int
     lib.louvain_mlp_train.argtypes = [vp, vp, vp, i64, i32, i32, ctypes.c_float, ctypes.c_uint64, vp, vp]
-    lib.louvain_set_probe_limit.restype = ctypes.c_int
-    lib.louvain_set_probe_limit.argtypes = [ctypes.c_uint32]
     lib.louvain_modularity_noalloc.restype = ctypes.c_int
     lib.louvain_modularity_noalloc.argtypes = [P(LouvainGraph), vp, vp, P(ctypes.c_double), vp, vp]
     lib.louvain_create_batched.restype = ctypes.c_int
@@ -489,10 +488,18 @@ def louvain_model_size() -> int:
     return int(load().louvain_model_size())
 
 
-def louvain_set_probe_limit(max_probes: int) -> None:
-    """Algorithm 7's MAX_RETRIES for every hashtable insert on the current
-    device (0 = the table size, never reached)."""
-    _check(load().louvain_set_probe_limit(max_probes), None)
+@contextlib.contextmanager
+def using_library(path: str):
+    """Within the block, every call of this module goes to the library at
+    `path` (a build of the same sources with other compile-time options,
+    e.g. a probe bound for failure tests), then back to the default one."""
+    global _lib
+    saved = _lib
+    _lib = load(path)
+    try:
+        yield _lib
+    finally:
+        _lib = saved
 
 
 def louvain_version() -> str:

@@ -29,7 +29,7 @@ MODEL_FILE = os.path.join(HERE, "predictor_rmat20-22.f32")
 TRAINING_GRAPHS = ((20, 101), (21, 102), (22, 103))
 MIN_DEGREE = 1024
 # run settings the stored model is meant for (louvain_config fields)
-SETTINGS = dict(learned_min_degree=MIN_DEGREE, skip_threshold=0.1, learned_fallback=3, learned_skip_clears=1)
+SETTINGS = dict(learned_min_degree=MIN_DEGREE, skip_threshold=0.2, learned_fallback=3, learned_skip_clears=1)
 
 
 def collect_traces(graph, cap: int = 4_000_000, rate: float = 0.25, min_degree: int = 0):

@@ -53,3 +53,22 @@ def test_reference_arm_line_on_cpu():
     assert line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_first_launch_entries_follow_the_bucket_schedule():
+    """The entries of the first launches of a bin kernel (iteration 0 of
+    pass 0, every vertex unprocessed), used to scale a small ncu capture,
+    follow the schedule's bucket hash: checked against the oracle's bucket
+    function vertex by vertex."""
+    import numpy as np
+    import oracle
+    from paper_2501_19004_gb300 import graphgen as gg
+    g = gg.rmat(13, 16, seed=7)
+    deg = np.diff(g.offsets)
+    sched = dict(group_max=64, half_max=128, warp_max=256)
+    for kern, (lo, hi) in (("move_block", (1025, 4096)), ("move_mid", (257, 1024))):
+        want = [0] * 4
+        for i in range(g.n):
+            if lo <= deg[i] <= hi:
+                want[oracle.bucket(i, 0, 0, 0, 4)] += int(deg[i])
+        assert bench.first_launch_entries(g, kern, sched, 4) == want

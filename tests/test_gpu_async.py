@@ -10,7 +10,12 @@ any run must satisfy is checked instead:
 - the pass records obey Algorithm 1: each aggregated pass's |Gamma| is the
   next pass's n', the exit reason matches the last pass's l_i and shrink;
 - the modularity is close to the deterministic form's wherever the fully
-  simultaneous schedule is (see stable_under_simultaneity).
+  simultaneous schedule is (see stable_under_simultaneity) and no vertex
+  has more than 4096 neighbours.  Vertices above that take the wide and hub
+  bins, where up to one vertex per SM decides at the same time against
+  memberships the others are changing: on R-MAT scale 16 those hubs can
+  pile onto the same communities (the swaps and pile-ons of Sec. 4.3.1),
+  e.g. Q 0.063 against 0.091, so there only validity is asserted.
 """
 import numpy as np
 import pytest
@@ -89,7 +94,7 @@ def test_async_runs_are_valid(name):
     dg = lv.DeviceCSR.from_host(g)
     plain = lv.run(dg, lv.Config())
     cfg = lv.Config(asynchronous=True)
-    stable = stable_under_simultaneity(g)
+    stable = stable_under_simultaneity(g) and (g.n == 0 or int(np.diff(g.offsets).max()) <= 4096)
     with lv.Louvain(dg, cfg) as ctx:
         for _ in range(3):
             res = ctx.run().result()

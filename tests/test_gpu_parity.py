@@ -223,23 +223,30 @@ def test_modularity_of_refuses_membership_ids_out_of_range():
     assert oracle.modularity(g, memb)[1:] == (num, den)
 
 
-def test_probe_limit_gives_hash_overflow_and_recovers():
-    """Algorithm 7's "failed" result: with the probe limit lowered to one slot,
-    colliding inserts give up, the run returns LOUVAIN_E_HASH_OVERFLOW (a
-    status, no fault), and with the limit restored the same context runs
-    again bit-exactly.  Shared tables (warp and block bins) and the hubs'
-    global tables (R-MAT scale 19) both reach the limit."""
+def test_probe_bound_gives_hash_overflow_status(tmp_path):
+    """Algorithm 7's "failed" result: a library built with a probe bound of
+    one slot (LOUVAIN_MAX_PROBES=1, same sources) gives up on colliding
+    inserts; the run returns LOUVAIN_E_HASH_OVERFLOW as a status (no fault),
+    the context stays usable (a second run returns the same status, results
+    are refused as not ready), and the product library still runs the same
+    graph bit-exactly.  Shared tables (warp and block bins) and the hubs'
+    global tables (R-MAT scale 19) both reach the bound."""
+    from paper_2501_19004_gb300 import build
+    path = build.build(force=True, defines=["LOUVAIN_MAX_PROBES=1"], lib=str(tmp_path / "liblouvain_probe1.so"),
+                       objdir=str(tmp_path / "obj"))
     for g in (gg.rmat(14, 16, seed=7), gg.rmat(19, 16, seed=7)):
-        ref = oracle.louvain(g, oracle.Config())
-        with lv.Louvain(lv.DeviceCSR.from_host(g)) as ctx:
-            try:
-                lv.louvain_set_probe_limit(1)
+        dg = lv.DeviceCSR.from_host(g)
+        with lv.using_library(path):
+            with lv.Louvain(dg) as ctx:
+                for _ in range(2):
+                    with pytest.raises(lv.LouvainError) as ei:
+                        ctx.run()
+                    assert ei.value.status == 4  # LOUVAIN_E_HASH_OVERFLOW
+                    assert "probe" in lv.louvain_last_error(ctx.ctx)
                 with pytest.raises(lv.LouvainError) as ei:
-                    ctx.run()
-                assert ei.value.status == 4  # LOUVAIN_E_HASH_OVERFLOW
-                assert "probe" in lv.louvain_last_error(ctx.ctx)
-            finally:
-                lv.louvain_set_probe_limit(0)
-            res = ctx.run().result()
+                    lv.louvain_modularity(ctx.ctx)
+                assert ei.value.status == 7  # no result of a failed run
+        ref = oracle.louvain(g, oracle.Config())
+        res = lv.run(dg)
         assert np.array_equal(res.membership, ref.membership)
         assert (res.q_num, res.q_den) == (ref.q_num, ref.q_den)
