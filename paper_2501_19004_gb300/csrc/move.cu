@@ -684,53 +684,68 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 8 : NT == 512 ? 2 : 1) k_move_
 // no repeated column, so its score is formed at once and kept in a
 // per-thread running argmax; such a community is never the vertex's own
 // (that would hold i and j).  Only the other entries go through the
-// 16384-slot shared table.  Every slot claimed there first takes a ticket;
-// once more than kWideCap keys would be held, the remaining entries go to
+// 16384-slot shared table (claims appended to the occupied list once per
+// warp); once it holds kWideCap keys, the remaining entries go to
 // the block's own global table of kWideSpill packed 64-bit slots (twice the
 // largest row, so at most half full), the shared table is flushed into it,
 // and the vertex is decided from that table, which its scan leaves empty.
 // At iteration 0 of a pass every community is a singleton, so those scans
 // touch no table at all.
-constexpr uint16_t kNoSlot = 0xFFFFu;
+constexpr int kWideOcc = kWideCap + 1024;  // occupied-list entries: the cap plus one late claim per thread
 constexpr int kWideRun = 4;  // entries per thread per round (1024 x 4 in flight per block)
 
 __device__ __forceinline__ bool recv_bit(const uint32_t *recv, int32_t c) {
   return (__ldg(recv + (c >> 5)) >> (c & 31)) & 1u;
 }
 
-// Insert into the shared wide table; false when the ticket count passed
-// kWideCap (*over is set, nothing inserted).  Tickets bound the claimed
-// slots, so the table stays at most three quarters full and probing always
-// finds a slot.
-__device__ __forceinline__ bool wide_insert(int32_t *keys, uint32_t *vals, uint16_t *occ, unsigned *nocc, int *over,
-                                            int32_t key, uint32_t w, Counters *ctr) {
+// Insert into the shared wide table by the whole warp (every lane calls it;
+// key = kEmpty for nothing).  Returns false, inserting nothing, once the
+// table holds kWideCap keys (*over is set): the caller spills the pair.  The
+// count read before a claim lags by at most one claim per thread, so the
+// table holds fewer than kWideCap + 1024 keys, at most 13/16 full, and
+// probing always finds a slot.  Claimed slots are appended to the occupied
+// list with one atomic per warp.
+__device__ __forceinline__ bool wide_insert_warp(int32_t *keys, uint32_t *vals, uint16_t *occ, unsigned *nocc,
+                                                 int *over, int32_t key, uint32_t w, Counters *ctr) {
   constexpr uint32_t mask = kXlCap - 1;
-  uint32_t s = slot_of(key, mask);
-  const uint32_t lim = mask < kMaxProbes ? mask + 1 : kMaxProbes;  // probes allowed
-  for (uint32_t t = 0; t < lim; ++t) {
-    int32_t k = ((volatile int32_t *)keys)[s];
-    if (k == kEmpty) {
-      const unsigned ticket = atomicAdd(nocc, 1u);
-      if (ticket >= (unsigned)kWideCap) {
-        *(volatile int *)over = 1;
-        return false;
+  int32_t claimed = -1;
+  bool ok = true;
+  if (key != kEmpty) {
+    if (*(volatile int *)over || *(volatile unsigned *)nocc >= (unsigned)kWideCap) {
+      *(volatile int *)over = 1;
+      ok = false;
+    } else {
+      uint32_t s = slot_of(key, mask);
+      const uint32_t lim = mask < kMaxProbes ? mask + 1 : kMaxProbes;  // probes allowed
+      uint32_t t = 0;
+      for (; t < lim; ++t) {
+        int32_t k = ((volatile int32_t *)keys)[s];
+        if (k == kEmpty) {
+          k = atomicCAS(keys + s, kEmpty, key);
+          if (k == kEmpty) {
+            k = key;
+            claimed = (int32_t)s;
+          }
+        }
+        if (k == key) {
+          atomicAdd(vals + s, w);
+          break;
+        }
+        s = (s + 1) & mask;
       }
-      k = atomicCAS(keys + s, kEmpty, key);
-      if (k == kEmpty) {
-        occ[ticket] = (uint16_t)s;
-        atomicAdd(vals + s, w);
-        return true;
-      }
-      occ[ticket] = kNoSlot;  // another thread took the slot: the ticket stays unused
+      if (t == lim) atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
     }
-    if (k == key) {
-      atomicAdd(vals + s, w);
-      return true;
-    }
-    s = (s + 1) & mask;
   }
-  atomicOr(&ctr->error, (unsigned long long)ERR_HASH);
-  return false;
+  const unsigned m = __ballot_sync(kFull, claimed >= 0);
+  if (m) {
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(nocc, (unsigned)__popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (claimed >= 0) occ[base + __popc(m & lanemask_lt())] = (uint16_t)claimed;
+  }
+  return ok;
 }
 
 __device__ __forceinline__ void spill_insert(unsigned long long *tab, int32_t key, uint32_t w, Counters *ctr) {
@@ -741,7 +756,7 @@ __device__ __forceinline__ void spill_insert(unsigned long long *tab, int32_t ke
 template <int WK>
 __global__ void __launch_bounds__(1024, 1) k_move_wide(MoveArgs a) {
   constexpr int NT = 1024;
-  // dynamic shared memory: keys[16384], vals[16384], occupied list[kWideCap]
+  // dynamic shared memory: keys[16384], vals[16384], occupied list[kWideOcc]
   extern __shared__ uint32_t dyn[];
   int32_t *keys = (int32_t *)dyn;
   uint32_t *vals = dyn + kXlCap;
@@ -806,14 +821,17 @@ __global__ void __launch_bounds__(1024, 1) k_move_wide(MoveArgs a) {
             best_s = sc;
             best_c = kk[u];
           }
-        } else if (*(volatile int *)&s_over ||
-                   !wide_insert(keys, vals, occ, &s_nocc, &s_over, kk[u], ww[u], a.ctr)) {
-          spill_insert(spill, kk[u], ww[u], a.ctr);
         }
+      }
+#pragma unroll
+      for (int u = 0; u < kWideRun; ++u) {
+        const int32_t key = (kk[u] != kEmpty && !solo[u]) ? kk[u] : kEmpty;
+        if (!wide_insert_warp(keys, vals, occ, &s_nocc, &s_over, key, ww[u], a.ctr))
+          spill_insert(spill, key, ww[u], a.ctr);
       }
     }
     __syncthreads();
-    const unsigned nk = min(s_nocc, (unsigned)kWideCap);
+    const unsigned nk = s_nocc;
     const bool over = s_over != 0;
     const int32_t d = a.Cp[i];
     if (over) {
@@ -821,7 +839,6 @@ __global__ void __launch_bounds__(1024, 1) k_move_wide(MoveArgs a) {
       // from the block's global table, whose slots are cleared as read
       for (unsigned t = threadIdx.x; t < nk; t += NT) {
         const uint16_t sl = occ[t];
-        if (sl == kNoSlot) continue;
         spill_insert(spill, keys[sl], vals[sl], a.ctr);
         keys[sl] = kEmpty;
         vals[sl] = 0;
@@ -847,7 +864,6 @@ __global__ void __launch_bounds__(1024, 1) k_move_wide(MoveArgs a) {
     } else {
       for (unsigned t = threadIdx.x; t < nk; t += NT) {
         const uint16_t sl = occ[t];
-        if (sl == kNoSlot) continue;
         const int32_t c = keys[sl];
         const long long v = vals[sl];
         keys[sl] = kEmpty;
@@ -1037,7 +1053,7 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
   constexpr size_t kBlockSmem =
       (size_t)kBlockCap * (sizeof(uint32_t) + sizeof(int32_t)) + kBlockCap / 2 * sizeof(uint16_t);
   constexpr size_t kWideSmem =
-      (size_t)kXlCap * (sizeof(uint32_t) + sizeof(int32_t)) + (size_t)kWideCap * sizeof(uint16_t);
+      (size_t)kXlCap * (sizeof(uint32_t) + sizeof(int32_t)) + (size_t)kWideOcc * sizeof(uint16_t);
   if (!attr_done) {
     cudaFuncSetAttribute(k_move_block<WK, 512, kBlockCap, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kBlockSmem);
