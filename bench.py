@@ -215,17 +215,31 @@ def stored_traffic(kernel: str):
     except (OSError, ValueError):
         return None, None
     ent = tj.get(kernel)
-    if not ent or ent.get("sources") != source_hash():
+    if not ent or ent.get("sources") != source_hash(kernel_sources(kernel)):
         return None, None
     return ent.get("dram_bytes_per_entry"), ent
 
 
-def source_hash() -> str:
-    """FNV-1a of the library's CUDA sources, so that a stored capture is used
-    only for the kernels it measured."""
+def kernel_sources(kernel: str):
+    """The CUDA source files whose code a kernel group runs: its own
+    translation unit and every header (the hub path lives in big.cu, the
+    aggregation kernels in aggr.cu, local moving in move.cu)."""
+    tu = ("big.cu" if kernel in ("move_hub", "move_hub_eval", "merge_big", "merge_big_emit")
+          else "move.cu" if kernel.startswith("move_") or kernel in ("select", "apply", "pass_init", "mlp_select")
+          else "aggr.cu")
+    headers = [f for f in os.listdir(os.path.join(ROOT, "paper_2501_19004_gb300", "csrc")) if f.endswith((".cuh", ".h"))]
+    return [tu] + headers
+
+
+def source_hash(files=None) -> str:
+    """FNV-1a of the library's CUDA sources (all of them, or the named files
+    of the source folder), so that a stored capture is used only for the
+    kernels it measured."""
     import glob
     h = 0xcbf29ce484222325
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2501_19004_gb300", "csrc", "*"))):
+    csrc = os.path.join(ROOT, "paper_2501_19004_gb300", "csrc")
+    paths = glob.glob(os.path.join(csrc, "*")) if files is None else [os.path.join(csrc, f) for f in files]
+    for f in sorted(paths):
         for byte in open(f, "rb").read():
             h = ((h ^ byte) * 0x100000001b3) & 0xFFFFFFFFFFFFFFFF
     return f"{h:016x}"
@@ -284,6 +298,8 @@ def main():
     ap.add_argument("--skip-threshold", type=float, default=None, help="default: the stored model's setting")
     ap.add_argument("--learned-min-degree", type=int, default=None, help="default: the stored model's setting")
     ap.add_argument("--graphs", type=int, default=0, help="batch workloads: run only the first N graphs")
+    ap.add_argument("--batch-leg", type=int, default=4096,
+                    help="single-graph workloads: also time the batched workload on its first N graphs (0: no leg)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch schedule")
     ap.add_argument("--autotune-runs", type=int, default=32)
     ap.add_argument("--sequential-sample", type=int, default=256,
@@ -538,6 +554,38 @@ def main():
                       "stride": stride, "ms_total": seq_ms,
                       "note": "each sampled graph in its own context, one louvain_run each"}
 
+    # the batched workload as an extra leg beside a single-graph workload: one
+    # context over the first N graphs of the 4,096-graph planted-partition
+    # batch, default schedule with concurrent bins, timed like the main leg
+    batch_leg = None
+    if not batch and args.batch_leg > 0:
+        del dg
+        torch.cuda.empty_cache()
+        wb = dict(WORKLOADS["bsbm4096"], G=min(args.batch_leg, 4096))
+        ub, vob = make_graph(wb)
+        dub = lv.DeviceCSR.from_host(ub, dev)
+        with lv.LouvainBatch(dub, vob) as cb:
+            cb.set_schedule(dict(concurrent=1))
+            for _ in range(max(args.warmup, 1)):
+                cb.run()
+            torch.cuda.synchronize()
+            barrier()
+            b0 = torch.cuda.Event(enable_timing=True)
+            b1 = torch.cuda.Event(enable_timing=True)
+            b0.record(stream)
+            for _ in range(args.steps):
+                cb.run()
+            b1.record(stream)
+            torch.cuda.synchronize()
+            bms = max_over_ranks(b0.elapsed_time(b1), world, dev)
+            bst = cb.stats()
+        batch_leg = {"workload": wb["desc"] + (f" (first {wb['G']} graphs)" if wb["G"] < 4096 else ""),
+                     "graphs": wb["G"], "n": ub.n, "edges_directed": ub.nnz,
+                     "value": job_rate(ub.nnz, args.steps, world, bms / 1e3), "unit": UNIT,
+                     "ms_per_step": bms / args.steps, "schedule": "default, concurrent bins",
+                     "pass_ms": [round(q["move_ms"] + q["aggregate_ms"], 3) for q in bst["per_pass"]]}
+        del dub
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample = SAMPLES[args.workload]
@@ -556,7 +604,8 @@ def main():
                        "l2": f"inputs larger than L2 (CSR {(g.offsets.nbytes + g.cols.nbytes) / 1e9:.2f} GB), no flush",
                        **summary},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
-            "learned_skip": learned, "asynchronous": asynchronous, "sequential": sequential, "autotune": tune,
+            "learned_skip": learned, "asynchronous": asynchronous, "sequential": sequential, "batch": batch_leg,
+            "autotune": tune,
             "phases_ms": {"move": st["move_ms"], "aggregate": st["aggregate_ms"], "other": st["other_ms"]},
             "kernels_ms_warmup": {k: round(v["ms"], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},
         }

@@ -1413,6 +1413,10 @@ louvain_status run_batched(louvain_ctx *x) {
       for (int64_t k = 0; k < G; ++k) x->h_flags[k] = mv[k];
       LV_CK(cudaMemcpyAsync(x->b_moving, x->h_flags, (size_t)G, cudaMemcpyHostToDevice, s));
     }
+    if (!device_done) {  // host-controlled iterations are timed one by one
+      if ((size_t)p < x->iter_timed.size()) x->iter_timed[p] = 1;
+      if ((st = mark_iteration(x, p, li_union))) return st;
+    }
     LV_CK(cudaEventRecord(pt.t1, s));
     ++passes;
     AggArgs aa = agg_args(x, g, wk, slot);

@@ -72,3 +72,14 @@ def test_first_launch_entries_follow_the_bucket_schedule():
             if lo <= deg[i] <= hi:
                 want[oracle.bucket(i, 0, 0, 0, 4)] += int(deg[i])
         assert bench.first_launch_entries(g, kern, sched, 4) == want
+
+
+def test_stored_traffic_describes_the_current_wide_kernel():
+    """profiles/traffic.json holds the DRAM bytes per entry of the dominant
+    kernel of the default workload; it must have been taken on the current
+    move.cu and headers (the bench reports no traffic figure otherwise)."""
+    per_entry, rec = bench.stored_traffic("move_wide")
+    assert per_entry is not None and rec is not None
+    assert 0 < per_entry < 100
+    assert "move.cu" in bench.kernel_sources("move_wide")
+    assert bench.kernel_sources("move_hub")[0] == "big.cu" and bench.kernel_sources("merge_mid")[0] == "aggr.cu"
