@@ -146,6 +146,28 @@ typedef struct {
                                     and keep features (and only they are recorded);
                                     lower-degree vertices are always evaluated when
                                     flagged, as in the plain method.  0 = all. */
+  int32_t refine;                /* 1: the Leiden form (Traag, Waltman and van Eck
+                                    2019, which Sec. 5.2 and Sec. 6 of the paper
+                                    expect its findings to extend to): after local
+                                    moving, the partition P is refined and the
+                                    refined partition is aggregated; the next pass
+                                    starts every super-vertex in its community of P.
+                                    Refinement: one sweep over the buckets of
+                                    (vertex, pass, iteration 255); a vertex that is
+                                    still a singleton of the refined partition and
+                                    well connected to its community C of P
+                                    (2m K_{i->C} >= K_i (Sigma_C - K_i), K_{i->C}
+                                    without the self-loop) joins the refined
+                                    community inside C with the largest score
+                                    2m K_{i->T} - K_i Sigma_T (lowest id on ties)
+                                    if that score is positive; a vertex that any
+                                    decision of the bucket chose as its target stays
+                                    and stops being a singleton.  The low-shrink test
+                                    compares the refined communities with n'; the
+                                    memberships are P's.  PLAIN mode, deterministic
+                                    schedule, single graphs only, and not with
+                                    louvain_run_passes (LOUVAIN_E_INVAL otherwise).
+                                    0: the Louvain form. */
 } louvain_config;
 
 /* Fill `cfg` with the defaults above (mode PLAIN, seed 0). */

@@ -19,6 +19,11 @@ Parity status per function (what pins it, in tests/test_oracle_pins.py):
   louvain              Alg. 1/4 whole run -- pinned by invariants, closed forms
                        (ring of cliques, disjoint cliques), brute-force optimum
                        bound, planted-partition recovery
+  refine               Leiden refinement (Traag et al. 2019; Sec. 5.2, Sec. 6)
+                       -- pinned by brute-force merge choices, connectivity
+                       and containment of the refined communities, the
+                       well-connectedness condition, and aggregation
+                       invariance; louvain(refine=True) by the whole-run pins
 """
 from __future__ import annotations
 
@@ -63,6 +68,7 @@ class OrConfig(ctypes.Structure):
         ("schedule_seed", ctypes.c_uint64),
         ("check_invariants", ctypes.c_int32),
         ("num_threads", ctypes.c_int32),
+        ("refine", ctypes.c_int32),
     ]
 
 
@@ -84,6 +90,8 @@ def _load():
             lib.or_decide.argtypes = [i64, vp, vp, vp, vp, i64, i32, vp]
             lib.or_aggregate.restype = ctypes.c_int
             lib.or_aggregate.argtypes = [i64, vp, vp, vp, vp, i64, vp, vp, vp, vp]
+            lib.or_refine.restype = ctypes.c_int
+            lib.or_refine.argtypes = [i64, vp, vp, vp, vp, i32, u64, i32, vp]
             lib.or_fmix32.restype = u32
             lib.or_fmix32.argtypes = [u32]
             lib.or_bucket.restype = u32
@@ -121,11 +129,13 @@ class Config:
     schedule_seed: int = 0
     check_invariants: bool = False
     num_threads: int = 0
+    refine: bool = False  # Leiden: refine P before aggregating (or_louvain's refine)
 
     def c(self) -> OrConfig:
         return OrConfig(self.max_passes, self.max_iterations, self.tolerance, self.tolerance_drop,
                         self.aggregation_tolerance, self.pickless_period, self.buckets,
-                        self.schedule_seed & (2**64 - 1), int(self.check_invariants), self.num_threads)
+                        self.schedule_seed & (2**64 - 1), int(self.check_invariants), self.num_threads,
+                        int(self.refine))
 
 
 @dataclass
@@ -231,6 +241,21 @@ def aggregate(g, membership, ncomm: int):
     if st != 0:
         raise RuntimeError(f"oracle aggregate failed with status {st}")
     return o, c[:nnz.value], ww[:nnz.value]
+
+
+def refine(g, bound, pass_: int = 0, seed: int = 0, buckets: int = 4) -> np.ndarray:
+    """The Leiden refinement of partition `bound` (ids in [0, n)) on g:
+    refined ids, each the vertex id of one member (leiden_refine in
+    louvain_oracle.c)."""
+    lib = _load()
+    off, col, w = _graph_args(g)
+    n = off.shape[0] - 1
+    b = np.ascontiguousarray(bound, dtype=np.int32)
+    out = np.empty(max(n, 1), dtype=np.int32)
+    st = lib.or_refine(n, _ptr(off), _ptr(col), _ptr(w), _ptr(b), pass_, seed & (2**64 - 1), buckets, _ptr(out))
+    if st != 0:
+        raise RuntimeError(f"oracle refine failed with status {st}")
+    return out[:n]
 
 
 def fmix32(h: int) -> int:

@@ -12,7 +12,11 @@
  *   - the local-moving phase of Algorithm 2 / Algorithm 5 (Sec. 4.2.2),
  *     with vertex pruning (Sec. 4.1.6) and Pick-Less mode (Sec. 4.3.1);
  *   - the aggregation phase of Algorithm 3 / Algorithm 6 (Sec. 4.2.3);
- *   - modularity, Eq. 1, and delta-modularity, Eq. 2 (Sec. 3.2).
+ *   - modularity, Eq. 1, and delta-modularity, Eq. 2 (Sec. 3.2);
+ *   - optionally the refinement phase of the Leiden algorithm (Traag,
+ *     Waltman and van Eck 2019), which Sec. 5.2 and Sec. 6 expect the
+ *     paper's findings to carry over to; the greedy, bucketed form used
+ *     here is described at leiden_refine below.
  *
  * The paper's algorithms move vertices asynchronously.  This oracle instead
  * fixes one deterministic semi-synchronous schedule: in every iteration the
@@ -33,6 +37,7 @@
  * reads the snapshot only) and over communities in aggregation (each writes
  * its own output row); results do not depend on the thread count.
  */
+#include <limits.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -54,6 +59,7 @@ typedef struct {
   uint64_t schedule_seed;        /* seed of the bucket hash */
   int32_t check_invariants;      /* verify sum(Sigma') == 2m after every bucket */
   int32_t num_threads;           /* 0 = OpenMP default */
+  int32_t refine;                /* 1: Leiden refinement before aggregation (see or_refine) */
 } or_config;
 
 enum { OR_OK = 0, OR_E_INVAL = 1, OR_E_NOMEM = 2, OR_E_INVARIANT = 3 };
@@ -290,6 +296,117 @@ out:
   free(A);
   free(dec);
   return li_done;
+}
+
+/* ---- Leiden refinement (Traag, Waltman & van Eck 2019, the refinement of
+ * the partition P that local moving produced; the paper's Sec. 5.2 and
+ * Sec. 6 expect its findings to extend to Leiden) ----
+ *
+ * Greedy and deterministic, in the same bucket form as local moving:
+ *   - The refined partition starts as singletons: Cr[v] = v, Sr[v] = K_v.
+ *   - A vertex v may move only while it is a singleton, and only if it is
+ *     well connected to its community C = P(v):
+ *       2m K_{v->C} >= K_v (Sigma_C - K_v)
+ *     where K_{v->C} sums v's edges to the other members of C.
+ *   - One sweep over the buckets of (v, pass, iteration 255).  In a bucket,
+ *     every such vertex decides against the snapshot (Cr, Sr) exactly as in
+ *     local moving, but sees only neighbours inside its own community C: it
+ *     picks the refined community T (within C) with the largest
+ *     s(T) = 2m K_{v->T} - K_v Sr[T], lowest id on ties, and moves iff
+ *     s(T) > 0 (its own singleton scores 0).  No Pick-Less.
+ *   - A vertex that any decision of the bucket chose as its target stays
+ *     where it is and can no longer move; the other movers are applied.
+ *     So no mover is ever the target of another, and every refined
+ *     community keeps the id of one of its members (its first vertex).
+ * Every merge needs K_{v->T} > 0, so refined communities are connected
+ * subsets of the communities of P.  Leiden's randomised choice among the
+ * merges that do not lower the quality is replaced by the best one. */
+
+/* G' restricted to the edges inside the communities of `bound`, self-loops
+ * dropped (rows keep their order). */
+static int filter_to_bounds(const graph_t *g, const int32_t *bound, graph_t *out) {
+  out->n = g->n;
+  out->off = (int64_t *)malloc((size_t)(g->n + 1) * sizeof(int64_t));
+  if (!out->off) return OR_E_NOMEM;
+  int64_t k = 0;
+  out->off[0] = 0;
+  for (int64_t i = 0; i < g->n; ++i) {
+    for (int64_t e = g->off[i]; e < g->off[i + 1]; ++e)
+      if (g->col[e] != i && bound[g->col[e]] == bound[i]) ++k;
+    out->off[i + 1] = k;
+  }
+  out->nnz = k;
+  out->col = (int32_t *)malloc((size_t)(k ? k : 1) * sizeof(int32_t));
+  out->w = (int64_t *)malloc((size_t)(k ? k : 1) * sizeof(int64_t));
+  if (!out->col || !out->w) return OR_E_NOMEM;
+  k = 0;
+  for (int64_t i = 0; i < g->n; ++i)
+    for (int64_t e = g->off[i]; e < g->off[i + 1]; ++e)
+      if (g->col[e] != i && bound[g->col[e]] == bound[i]) {
+        out->col[k] = g->col[e];
+        out->w[k] = g->w[e];
+        ++k;
+      }
+  return OR_OK;
+}
+
+/* Refined partition Cr (raw ids: a member's vertex id) of G' under P =
+ * bound, whose community totals are Sigma_b; K are the vertex weights. */
+static int leiden_refine(const graph_t *g, const int32_t *bound, const int64_t *K, const int64_t *Sigma_b,
+                         int64_t two_m, int32_t pass, const or_config *cfg, int32_t *Cr) {
+  const int64_t n = g->n;
+  graph_t F = {0, 0, NULL, NULL, NULL};
+  int st = filter_to_bounds(g, bound, &F);
+  const int T = nthreads();
+  int64_t *Sr = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
+  uint8_t *elig = (uint8_t *)malloc((size_t)(n ? n : 1));
+  uint8_t *chosen = (uint8_t *)calloc((size_t)(n ? n : 1), 1);
+  int64_t *A = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
+  decision_t *dec = (decision_t *)malloc((size_t)(n ? n : 1) * sizeof(decision_t));
+  pair_t **bufs = (pair_t **)calloc((size_t)T, sizeof(pair_t *));
+  const int64_t md = max_degree(g);
+  if (st || !Sr || !elig || !chosen || !A || !dec || !bufs) st = OR_E_NOMEM;
+  for (int t = 0; !st && t < T; ++t) {
+    bufs[t] = (pair_t *)malloc((size_t)(md ? md : 1) * sizeof(pair_t));
+    if (!bufs[t]) st = OR_E_NOMEM;
+  }
+  if (st) goto out;
+  for (int64_t v = 0; v < n; ++v) {
+    int64_t kin = 0;
+    for (int64_t e = F.off[v]; e < F.off[v + 1]; ++e) kin += F.w[e];
+    elig[v] = (i128)two_m * kin >= (i128)K[v] * (Sigma_b[bound[v]] - K[v]);
+    Cr[v] = (int32_t)v;
+    Sr[v] = K[v];
+  }
+  for (int32_t b = 0; b < cfg->buckets; ++b) {
+    int64_t na = 0;
+    for (int64_t v = 0; v < n; ++v)
+      if (elig[v] && !chosen[v] && (int32_t)bucket_of(v, pass, 255, cfg->schedule_seed, cfg->buckets) == b)
+        A[na++] = v;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t a = 0; a < na; ++a)
+      dec[a] = decide(&F, Cr, K, Sr, two_m, A[a], 0, bufs[thread_id()]);
+    for (int64_t a = 0; a < na; ++a)
+      if (dec[a].moves) chosen[dec[a].target] = 1;
+    for (int64_t a = 0; a < na; ++a) {
+      const int64_t v = A[a];
+      if (!dec[a].moves || chosen[v]) continue;
+      const int32_t t = dec[a].target;
+      Sr[v] -= K[v];
+      Sr[t] += K[v];
+      Cr[v] = t;
+    }
+  }
+out:
+  if (bufs) for (int t = 0; t < T; ++t) free(bufs[t]);
+  free(bufs);
+  free(Sr);
+  free(elig);
+  free(chosen);
+  free(A);
+  free(dec);
+  graph_free(&F);
+  return st;
 }
 
 /* Renumber communities densely, keeping their order (the new id of c is the
@@ -596,7 +713,43 @@ int or_aggregate(int64_t n, const int64_t *off, const int32_t *col, const int32_
   return OR_OK;
 }
 
-/* The whole method (Algorithm 1 / 4).
+/* The Leiden refinement alone (leiden_refine): the refined partition of
+ * the input graph under the partition `bound` (ids in [0, n)), with vertex
+ * weights from the rows, at pass index `pass` of the bucket hash.
+ * refined_out [n]: raw refined ids (a member's vertex id). */
+int or_refine(int64_t n, const int64_t *off, const int32_t *col, const int32_t *w, const int32_t *bound,
+              int32_t pass, uint64_t seed, int32_t buckets, int32_t *refined_out) {
+  if (validate_input(n, off, col, w) || buckets < 1) return OR_E_INVAL;
+  for (int64_t i = 0; i < n; ++i)
+    if (bound[i] < 0 || bound[i] >= n) return OR_E_INVAL;
+  graph_t G;
+  if (graph_from_input(&G, n, off, col, w)) return OR_E_NOMEM;
+  int64_t *K = (int64_t *)calloc((size_t)(n ? n : 1), sizeof(int64_t));
+  int64_t *Sb = (int64_t *)calloc((size_t)(n ? n : 1), sizeof(int64_t));
+  int st = (K && Sb) ? OR_OK : OR_E_NOMEM;
+  int64_t two_m = 0;
+  for (int64_t i = 0; !st && i < n; ++i) {
+    for (int64_t e = G.off[i]; e < G.off[i + 1]; ++e) K[i] += G.w[e];
+    Sb[bound[i]] += K[i];
+    two_m += K[i];
+  }
+  or_config cfg;
+  memset(&cfg, 0, sizeof cfg);
+  cfg.buckets = buckets;
+  cfg.schedule_seed = seed;
+  if (!st) st = leiden_refine(&G, bound, K, Sb, two_m, pass, &cfg, refined_out);
+  free(K);
+  free(Sb);
+  graph_free(&G);
+  return st;
+}
+
+/* The whole method (Algorithm 1 / 4); with cfg->refine, the Leiden form:
+ * after local moving, the partition C' (P) is refined (leiden_refine), the
+ * refined partition is aggregated, and the next pass starts every
+ * super-vertex in its community of P (represented by the smallest
+ * super-vertex of that community).  The low-shrink test then compares the
+ * number of refined communities with n'; the final memberships are P's.
  *   membership_out [n]: final community of every input vertex, renumbered
  *                       densely in order of first id.
  *   iter_stats [max_passes * max_iterations * OR_ITER_FIELDS] or NULL
@@ -609,7 +762,7 @@ int or_louvain(int64_t n, const int64_t *off, const int32_t *col, const int32_t 
                const or_config *cfg, int32_t *membership_out, int64_t *iter_stats,
                int64_t *pass_stats, int64_t *summary, double *q_out) {
   if (!cfg || cfg->max_passes < 0 || cfg->max_iterations < 1 || cfg->max_iterations > 255 ||
-      cfg->buckets < 1 || cfg->pickless_period < 0)
+      cfg->buckets < 1 || cfg->pickless_period < 0 || cfg->refine < 0 || cfg->refine > 1)
     return OR_E_INVAL;
   if (validate_input(n, off, col, w)) return OR_E_INVAL;
 #ifdef _OPENMP
@@ -629,6 +782,15 @@ int or_louvain(int64_t n, const int64_t *off, const int32_t *col, const int32_t 
   int64_t *K = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
   int64_t *Sigma = (int64_t *)malloc((size_t)(n ? n : 1) * sizeof(int64_t));
   uint8_t *unproc = (uint8_t *)malloc((size_t)(n ? n : 1));
+  /* Leiden: refined partition, next pass's initial partition, and the
+   * smallest super-vertex of every community of P */
+  int32_t *Cr = NULL, *init = NULL, *rep = NULL;
+  if (cfg->refine) {
+    Cr = (int32_t *)malloc((size_t)(n ? n : 1) * sizeof(int32_t));
+    init = (int32_t *)malloc((size_t)(n ? n : 1) * sizeof(int32_t));
+    rep = (int32_t *)malloc((size_t)(n ? n : 1) * sizeof(int32_t));
+    if (!Cr || !init || !rep) { st = OR_E_NOMEM; goto done; }
+  }
   if (!Cp || !K || !Sigma || !unproc) { st = OR_E_NOMEM; goto done; }
   double tau = cfg->tolerance;
   int pending = 0;  /* C' of the last pass not yet looked up into C */
@@ -643,6 +805,13 @@ int or_louvain(int64_t n, const int64_t *off, const int32_t *col, const int32_t 
       Sigma[i] = s;
       Cp[i] = (int32_t)i;
       unproc[i] = 1;  /* mark all vertices as unprocessed */
+    }
+    if (cfg->refine && lp > 0) {  /* Leiden: start from the previous pass's P */
+      for (int64_t i = 0; i < np; ++i) Sigma[i] = 0;
+      for (int64_t i = 0; i < np; ++i) {
+        Cp[i] = init[i];
+        Sigma[init[i]] += K[i];
+      }
     }
     int li = louvain_move(&G, Cp, K, Sigma, unproc, two_m, tau, lp, cfg, iter_stats, &st);
     if (st) goto done;
@@ -660,15 +829,31 @@ int or_louvain(int64_t n, const int64_t *off, const int32_t *col, const int32_t 
       put128(r + 4, qn);
     }
     if (li <= 1) { pending = 1; exit_reason = 1; break; }             /* globally converged */
-    if ((double)gamma / (double)np > cfg->aggregation_tolerance) {    /* low shrink */
+    /* the partition to aggregate: C' (Louvain) or its refinement (Leiden) */
+    int32_t *agg = Cp;
+    int64_t nagg = gamma;
+    if (cfg->refine) {
+      st = leiden_refine(&G, Cp, K, Sigma, two_m, lp, cfg, Cr);
+      if (st) goto done;
+      agg = Cr;
+      nagg = count_distinct(Cr, np, np);
+      if (nagg < 0) { st = OR_E_NOMEM; goto done; }
+    }
+    if ((double)nagg / (double)np > cfg->aggregation_tolerance) {     /* low shrink */
       pending = 1;
       exit_reason = 2;
       break;
     }
-    if (renumber(Cp, np, np) < 0) { st = OR_E_NOMEM; goto done; }
-    for (int64_t v = 0; v < n; ++v) C[v] = Cp[C[v]];                  /* dendrogram lookup */
+    if (renumber(agg, np, np) < 0) { st = OR_E_NOMEM; goto done; }
+    for (int64_t v = 0; v < n; ++v) C[v] = agg[C[v]];                 /* dendrogram lookup */
+    if (cfg->refine) {  /* next pass starts every super-vertex in its community of P */
+      for (int64_t c = 0; c < np; ++c) rep[c] = INT32_MAX;
+      for (int64_t v = 0; v < np; ++v)
+        if (Cr[v] < rep[Cp[v]]) rep[Cp[v]] = Cr[v];
+      for (int64_t v = 0; v < np; ++v) init[Cr[v]] = rep[Cp[v]];
+    }
     graph_t H;
-    st = louvain_aggregate(&G, Cp, gamma, &H);
+    st = louvain_aggregate(&G, agg, nagg, &H);
     if (st) goto done;
     graph_free(&G);
     G = H;
@@ -676,6 +861,8 @@ int or_louvain(int64_t n, const int64_t *off, const int32_t *col, const int32_t 
   }
   if (pending)
     for (int64_t v = 0; v < n; ++v) C[v] = Cp[C[v]];
+  if (!pending && cfg->refine && passes > 0)  /* pass cap: the last pass's P, not its refinement */
+    for (int64_t v = 0; v < n; ++v) C[v] = init[C[v]];
   {
     int64_t gamma = renumber(C, n, n);
     if (gamma < 0) { st = OR_E_NOMEM; goto done; }
@@ -696,6 +883,9 @@ int or_louvain(int64_t n, const int64_t *off, const int32_t *col, const int32_t 
     if (q_out) *q_out = qd ? (double)qn / (double)qd : 0.0;
   }
 done:
+  free(Cr);
+  free(init);
+  free(rep);
   free(Cp);
   free(K);
   free(Sigma);

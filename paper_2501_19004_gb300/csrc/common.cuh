@@ -67,6 +67,7 @@ struct Counters {
   unsigned long long skip_listed;   // learned mode: vertices the predictor skipped in the current iteration
   unsigned long long sample_blocks; // learned features: neighbour-sample blocks handed out this pass
   unsigned long long sample_chunks; //   and row chunks to sample
+  unsigned long long refine_chunks; // Leiden refinement: chunk records of long rows
 };
 constexpr int kIterCounterWords = 5 + 45;
 

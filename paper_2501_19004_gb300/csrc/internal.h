@@ -307,7 +307,44 @@ struct MoveArgs {
   const int32_t *sel_list = nullptr;
   const unsigned long long *sel_count = nullptr;
   unsigned long long *wide_spill = nullptr;  // [SMs][kWideSpill] global tables of the wide bin, kept empty
+  int refine = 0;                  // Leiden refinement step: decisions only (refine_resolve applies them)
 };
+
+// Leiden refinement (refine.cu).  Rows of at most kRefineRowMax entries are
+// filtered by one warp; longer ones are cut into kRefineChunk-entry chunks,
+// one block each (at most nnz / kRefineChunk + nnz / kRefineRowMax chunks).
+constexpr int64_t kRefineRowMax = 2048;
+constexpr int kRefineChunk = 4096;
+// The filtered view of G' is
+// GView{g.n, g.begin, fend, fcol, fw}: row i keeps its entries inside its
+// community of P, at its own offsets.
+struct RefineArgs {
+  GView g;                      // current graph G'
+  const int32_t *Cp;            // P (C' after local moving)
+  const int64_t *K;             // vertex weights
+  const int64_t *Sigma;         // Sigma' of P's communities
+  long long two_m;
+  int64_t *fend;                // [n] ends of the filtered rows
+  int32_t *fcol;                // filtered entries (capacity: the ping-pong buffer)
+  uint32_t *fw;                 // their weights, or null for unit weights
+  unsigned long long *kin;      // [n] K_{i->C} of rows filtered in chunks
+  uint8_t *elig;                // [n] well connected to its community of P
+  uint8_t *chosen;              // [n] chosen as a target (no longer a singleton)
+  uint8_t *flag;                // [n] move flags (kFlagUnproc: decides in its bucket)
+  int32_t *Cr;                  // [n] refined partition
+  int64_t *Sr;                  // [n] its community totals
+  int2 *chunks;                 // chunk records (vertex, chunk) of long rows
+  int64_t chunk_cap;
+  Counters *ctr;
+};
+void refine_rows(const RefineArgs &r, int wkind, int num_sms, cudaStream_t s);
+void refine_resolve(const RefineArgs &r, const int32_t *mv_vertex, const int32_t *mv_target, uint32_t *recv,
+                    int num_sms, cudaStream_t s);
+void refine_flags(const RefineArgs &r, uint32_t salt, uint32_t nbuckets, uint32_t bucket, int num_sms, cudaStream_t s);
+void leiden_next_init(int64_t n, const int32_t *Cp, const int32_t *Cr, int32_t *rep, int32_t *init, int num_sms,
+                      cudaStream_t s);
+void leiden_start(int64_t n, const int32_t *init, const int64_t *K, int32_t *Cp, int64_t *Sigma, uint32_t *recv,
+                  int num_sms, cudaStream_t s);
 
 // Kernel identifiers for the optional per-kernel event timing.
 enum KernelId : int {

@@ -100,6 +100,16 @@ struct louvain_ctx {
   int2 *chunks = nullptr;
   int64_t chunk_cap = 0;
   uint32_t stamp = 0;             // stamp of the last bucket enqueued in the current pass
+  // Leiden form (refine): refined partition and totals, per-vertex
+  // refinement state, chunk records of long rows, and the next pass's
+  // starting partition (linit) with its representatives (lrep)
+  int32_t *Cr = nullptr;
+  int64_t *Sr = nullptr;
+  uint8_t *relig = nullptr, *rchosen = nullptr;
+  unsigned long long *rkin = nullptr;
+  int2 *rchunks = nullptr;
+  int64_t rchunk_cap = 0;
+  int32_t *linit = nullptr, *lrep = nullptr;
   int32_t *cand = nullptr;
   int32_t *skip_list = nullptr;  // learned: vertices skipped in the current iteration
   float *trace_x = nullptr, *trace_y = nullptr;
@@ -972,6 +982,90 @@ louvain_status capture_iteration(louvain_ctx *x, const GView &g, int wk, int pas
   return LOUVAIN_OK;
 }
 
+// Leiden refinement of P = C' on G' (the refine field of include/louvain.h):
+// the filtered rows go to the ping-pong buffer that this pass's aggregation
+// writes afterwards; one sweep over the buckets of (vertex, pass, iteration
+// 255) runs the local-moving decision kernels on the filtered view with the
+// refined partition, and resolve + flags after every bucket.
+louvain_status refine_phase(louvain_ctx *x, const GView &g, int wk, int slot, int pass) {
+  const louvain_config &cfg = x->cfg;
+  cudaStream_t s = x->stream;
+  RefineArgs r{};
+  r.g = g;
+  r.Cp = x->Cp;
+  r.K = x->K;
+  r.Sigma = x->Sigma;
+  r.two_m = x->two_m;
+  r.fend = x->pend[slot];
+  r.fcol = x->pcol[slot];
+  r.fw = wk == W_UNIT ? nullptr : x->pw[slot];
+  r.kin = x->rkin;
+  r.elig = x->relig;
+  r.chosen = x->rchosen;
+  r.flag = x->flag;
+  r.Cr = x->Cr;
+  r.Sr = x->Sr;
+  r.chunks = x->rchunks;
+  r.chunk_cap = x->rchunk_cap;
+  r.ctr = x->d_ctr;
+  LV_CK(cudaMemsetAsync(x->rchosen, 0, (size_t)g.n, s));
+  LV_CK(cudaMemsetAsync(x->recv, 0, (size_t)(g.n / 32 + 1) * sizeof(uint32_t), s));  // every refined community a singleton
+  refine_rows(r, wk, x->num_sms, s);
+  const GView f{g.n, g.begin, x->pend[slot], x->pcol[slot], r.fw};
+  const uint32_t salt = bucket_salt(pass, 255, cfg.schedule_seed);
+  MoveArgs a{};
+  a.g = f;
+  a.Cp = x->Cr;
+  a.K = x->K;
+  a.Sigma = x->Sr;
+  a.flag = x->flag;
+  a.two_m = x->two_m;
+  a.pickless = 0;
+  a.salt = salt;
+  a.nbuckets = (uint32_t)cfg.buckets;
+  for (int k = 0; k < kMoveBins; ++k) a.bins[k] = x->bins[k];
+  a.mv_vertex = x->mv_vertex;
+  a.mv_target = x->mv_target;
+  a.ctr = x->d_ctr;
+  a.sched = x->sched;
+  a.recv = x->recv;
+  a.wide_spill = x->wide_spill;
+  a.solo = pass > 0 || x->rows_unique;  // the filtered rows keep the rows' distinct columns
+  a.refine = 1;
+  BigArgs big{};
+  big.g = f;
+  big.Cp = x->Cr;
+  big.items = x->bins[kBigBin];
+  big.count = &x->d_ctr->bin_count[kBigBin];
+  big.keyspace = g.n;
+  big.ws = x->big;
+  big.window = x->hub_window;
+  big.rounds = x->hub_rounds;
+  big.h_rounds = x->h_rounds;
+  big.plan_done = x->plan_done;
+  if (!x->pass_has_hubs) big.ws.slots = 0;  // filtered rows are no longer than the rows
+  big.ctr = x->d_ctr;
+  big.K = x->K;
+  big.Sigma = x->Sr;
+  big.flag = x->flag;
+  big.two_m = x->two_m;
+  big.pickless = 0;
+  big.mv_vertex = x->mv_vertex;
+  big.mv_target = x->mv_target;
+  big.apply_Cp = x->Cr;
+  big.apply_Sigma = x->Sr;
+  big.accum_blocks = x->sched.move[kBigBin];
+  for (int b = 0; b < cfg.buckets; ++b) {
+    LV_CK(cudaMemsetAsync(x->d_ctr, 0, offsetof(Counters, it_gain_lo), s));
+    a.bucket = (uint32_t)b;
+    move_bucket(a, big, wk, x->num_sms, s, x->prof.mask ? &x->prof : nullptr, x->side.fork ? &x->side : nullptr);
+    refine_resolve(r, x->mv_vertex, x->mv_target, x->recv, x->num_sms, s);
+    refine_flags(r, salt, (uint32_t)cfg.buckets, (uint32_t)b, x->num_sms, s);
+  }
+  LV_CK(cudaGetLastError());
+  return read_counters(x);  // hashtable and range errors of the refinement
+}
+
 louvain_status move_iteration(louvain_ctx *x, const GView &g, int wk, int pass, int t, bool skipping,
                               const Counters **h_out, bool completion) {
   const louvain_config &cfg = x->cfg;
@@ -1093,7 +1187,7 @@ louvain_status aggregate(louvain_ctx *x, AggArgs &aa, int64_t gamma, PassTiming 
   agg_scatter_compact(aa, x->num_sms, s);
   x->prof.end(K_SCATTER, s);
   x->prof.begin(K_DENDRO, s);
-  dendrogram_lookup(x->C, x->Cp, x->n0, x->num_sms, s);
+  dendrogram_lookup(x->C, aa.Cp, x->n0, x->num_sms, s);
   x->prof.end(K_DENDRO, s);
   LV_CK(cudaGetLastError());
   if ((st = read_counters(x))) return st;
@@ -1106,7 +1200,7 @@ louvain_status aggregate(louvain_ctx *x, AggArgs &aa, int64_t gamma, PassTiming 
   aa.big.h_rounds = x->h_rounds;
   aa.big.plan_done = x->plan_done;
   aa.big.g = g;
-  aa.big.Cp = x->Cp;
+  aa.big.Cp = aa.Cp;
   aa.big.items = x->bins[kBigBin];
   aa.big.count = &x->d_ctr->mbin_count[kBigBin];
   aa.big.keyspace = gamma;
@@ -1201,6 +1295,8 @@ louvain_status run_impl(louvain_ctx *x, bool fresh = true, int32_t budget = 0, i
       const LearnArgs L = learn_args(x, p, 0, false);
       pass_init(g, wk, p == 0, x->K, x->Sigma, x->Cp, x->flag, x->d_ctr, x->num_sms, s, &L, x->vbin, &x->sched);
       LV_CK(cudaMemsetAsync(x->recv, 0, (size_t)(g.n / 32 + 1) * sizeof(uint32_t), s));  // every community a singleton
+      if (cfg.refine && p > 0)  // Leiden: the pass starts from the previous pass's P
+        leiden_start(g.n, x->linit, x->K, x->Cp, x->Sigma, x->recv, x->num_sms, s);
     }
     x->prof.end(K_PASS_INIT, s);
     LV_CK(cudaGetLastError());
@@ -1239,13 +1335,27 @@ louvain_status run_impl(louvain_ctx *x, bool fresh = true, int32_t budget = 0, i
       exit_reason = 1;
       break;
     }
-    if ((double)gamma / (double)g.n > cfg.aggregation_tolerance) {  // low shrink
+    // the partition to aggregate: C' (Louvain) or its refinement (Leiden)
+    int64_t nagg = gamma;
+    if (cfg.refine) {
+      if ((st = refine_phase(x, g, wk, slot, p))) return st;
+      aa.Cp = x->Cr;
+      aa.Sigma = x->Sr;
+      agg_count_scan(aa, x->num_sms, s);
+      LV_CK(cudaGetLastError());
+      if ((st = read_counters(x))) return st;
+      nagg = (int64_t)x->h_ctr->scan_total[0];
+      aa.gamma = nagg;  // the key space of the merge tables: the refined communities
+    }
+    if ((double)nagg / (double)g.n > cfg.aggregation_tolerance) {  // low shrink
       pending = true;
       exhausted = false;
       exit_reason = 2;
       break;
     }
-    if ((st = aggregate(x, aa, gamma, pt, g, wk, slot, nnzp))) return st;
+    const int64_t n_before = g.n;
+    if ((st = aggregate(x, aa, nagg, pt, g, wk, slot, nnzp))) return st;
+    if (cfg.refine) leiden_next_init(n_before, x->Cp, x->Cr, x->lrep, x->linit, x->num_sms, s);
     tau /= cfg.tolerance_drop;
     have_pass_state = false;
   }
@@ -1256,6 +1366,10 @@ louvain_status run_impl(louvain_ctx *x, bool fresh = true, int32_t budget = 0, i
     // identity memberships on the current graph (after max passes, or none)
     LV_CK(cudaMemsetAsync(&x->d_ctr->maxdeg, 0, sizeof(unsigned long long), s));
     pass_init(g, wk, passes == 0, x->K, x->Sigma, x->Cp, x->flag, x->d_ctr, x->num_sms, s);
+    if (cfg.refine && passes > 0) {  // Leiden after the pass cap: the last pass's P, not its refinement
+      leiden_start(g.n, x->linit, x->K, x->Cp, x->Sigma, x->recv, x->num_sms, s);
+      dendrogram_lookup(x->C, x->Cp, x->n0, x->num_sms, s);
+    }
     have_pass_state = true;
   }
   (void)have_pass_state;
@@ -1550,6 +1664,8 @@ louvain_status validate_config(const louvain_config *c) {
   if (c->table_window < 0 || c->learned_min_degree < 0) return LOUVAIN_E_INVAL;
   if (c->asynchronous != 0 && c->asynchronous != 1) return LOUVAIN_E_INVAL;
   if (c->asynchronous && (c->mode != LOUVAIN_MODE_PLAIN || c->trace_capacity > 0)) return LOUVAIN_E_INVAL;
+  if (c->refine != 0 && c->refine != 1) return LOUVAIN_E_INVAL;
+  if (c->refine && (c->mode != LOUVAIN_MODE_PLAIN || c->asynchronous || c->trace_capacity > 0)) return LOUVAIN_E_INVAL;
   return LOUVAIN_OK;
 }
 
@@ -1733,6 +1849,14 @@ louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg
         (st = dalloc_n(x, &x->sample_n, x->sample_cap)) || (st = dalloc_n(x, &x->chunks, x->chunk_cap)))
       return fail(st);
   }
+  if (cfg->refine) {
+    x->rchunk_cap = nnz / kRefineChunk + nnz / kRefineRowMax + 1;
+    if ((st = dalloc_n(x, &x->Cr, nv)) || (st = dalloc_n(x, &x->Sr, nv)) || (st = dalloc_n(x, &x->relig, nv)) ||
+        (st = dalloc_n(x, &x->rchosen, nv)) || (st = dalloc_n(x, &x->rkin, nv)) ||
+        (st = dalloc_n(x, &x->rchunks, x->rchunk_cap)) || (st = dalloc_n(x, &x->linit, nv)) ||
+        (st = dalloc_n(x, &x->lrep, nv)))
+      return fail(st);
+  }
   if (cfg->mode == LOUVAIN_MODE_LEARNED) {
     if ((st = dalloc_n(x, &x->cand, nv)) || (st = dalloc_n(x, &x->skip_list, nv)) ||
         (st = dalloc_n(x, &x->mlp, (int64_t)kMlpParams)))
@@ -1868,6 +1992,7 @@ void louvain_config_default(louvain_config *c) {
   c->table_window = 0;
   c->asynchronous = 0;
   c->learned_min_degree = 0;
+  c->refine = 0;
 }
 
 louvain_status louvain_create(const louvain_graph *graph, const louvain_config *cfg, void *stream, louvain_ctx **out) {
@@ -1883,8 +2008,8 @@ louvain_status louvain_create_batched(const louvain_graph *graph, const int64_t 
     set_err(nullptr, "null argument or bad number of graphs");
     return LOUVAIN_E_INVAL;
   }
-  if (cfg->mode != LOUVAIN_MODE_PLAIN || cfg->trace_capacity != 0 || cfg->asynchronous) {
-    set_err(nullptr, "batched runs use the plain mode without traces, on the deterministic schedule");
+  if (cfg->mode != LOUVAIN_MODE_PLAIN || cfg->trace_capacity != 0 || cfg->asynchronous || cfg->refine) {
+    set_err(nullptr, "batched runs use the plain Louvain form without traces, on the deterministic schedule");
     return LOUVAIN_E_INVAL;
   }
   if (vertex_offsets[0] != 0 || vertex_offsets[num_graphs] != graph->n) {
@@ -1928,7 +2053,7 @@ louvain_status louvain_run(louvain_ctx *x) {
 }
 
 louvain_status louvain_run_passes(louvain_ctx *x, int32_t max_new_passes, int32_t *suspended) {
-  if (!x || x->batched) return LOUVAIN_E_INVAL;
+  if (!x || x->batched || x->cfg.refine) return LOUVAIN_E_INVAL;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev != x->device) cudaSetDevice(x->device);
   louvain_status st = run_impl(x, true, max_new_passes, suspended);
@@ -1991,7 +2116,7 @@ uint64_t config_fingerprint(const louvain_ctx *x) {
   f[7] = (int64_t)c.schedule_seed;
   f[8] = c.mode;
   f[9] = c.record_pass_modularity;
-  f[14] = c.asynchronous;
+  f[14] = c.asynchronous + 2 * (int64_t)c.refine;
   if (learned) {
     memcpy(&f[10], &c.skip_threshold, 4);
     f[11] = c.learned_fallback;

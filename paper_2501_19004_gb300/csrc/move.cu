@@ -1100,7 +1100,7 @@ void move_bucket_t(const MoveArgs &a, const BigArgs &big, int num_sms, cudaStrea
       cudaEventRecord(side->join[k], side->s[k]);
       cudaStreamWaitEvent(s, side->join[k], 0);
     }
-  if (!a.async_apply) LV_TIMED(prof, K_APPLY, s, k_apply<<<num_sms * 4, 256, 0, s>>>(a));
+  if (!a.async_apply && !a.refine) LV_TIMED(prof, K_APPLY, s, k_apply<<<num_sms * 4, 256, 0, s>>>(a));
 }
 
 template <int WK>

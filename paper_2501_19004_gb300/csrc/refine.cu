@@ -1,0 +1,267 @@
+// The Leiden form (Traag, Waltman and van Eck 2019; the paper's Sec. 5.2 and
+// Sec. 6 expect its findings to extend to Leiden): refinement of the
+// partition P that local moving produced, and the start of the next pass
+// from P.
+//
+// The refinement is greedy and bucketed (the refine field of
+// include/louvain.h).  It reuses the local-moving decision kernels on a
+// filtered view of G': every row keeps only its entries inside the
+// vertex's community of P (self-loops dropped), written into the spare
+// ping-pong buffer at the row's own offsets, so the view is a holey CSR
+// with the same row starts.  The decision kernels then run with the refined
+// partition (Cr, Sr) in place of (C', Sigma'); their apply step is replaced
+// by the two kernels here that let a decision through only when no decision
+// of the bucket chose the deciding vertex as its target.
+#include <climits>
+
+#include "internal.h"
+
+namespace lv {
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kRefineNT = 256;
+constexpr int kRefineSteps = kRefineChunk / kRefineNT;  // 32-entry steps per warp: 16
+
+__device__ __forceinline__ bool well_connected(long long two_m, unsigned long long kin, long long Ki, long long Sc) {
+  // 2m K_{i->C} >= K_i (Sigma_C - K_i); both sides are below 2^64
+  return (unsigned long long)two_m * kin >= (unsigned long long)Ki * (unsigned long long)(Sc - Ki);
+}
+
+// One warp per row of at most kRefineRowMax entries (32 consecutive
+// vertices per warp step); a longer row gets chunk records and its entries
+// are appended by k_refine_chunks.  Every vertex starts as its own refined
+// community.
+template <int WK>
+__global__ void __launch_bounds__(256) k_refine_rows(RefineArgs r) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t base = warp * 32; base < r.g.n; base += nwarps * 32) {
+    const int64_t v = base + lane;
+    int64_t b = 0, deg = 0;
+    if (v < r.g.n) {
+      b = r.g.begin[v];
+      deg = r.g.end[v] - b;
+      r.Cr[v] = (int32_t)v;
+      r.Sr[v] = r.K[v];
+      if (deg > kRefineRowMax) {
+        const int64_t nch = (deg + kRefineChunk - 1) / kRefineChunk;
+        const unsigned long long c0 = atomicAdd(&r.ctr->refine_chunks, (unsigned long long)nch);
+        // the list is sized for the input's rows (louvain_create), so it never runs out
+        if ((int64_t)(c0 + nch) > r.chunk_cap) atomicOr(&r.ctr->error, (unsigned long long)ERR_RANGE);
+        for (int64_t c = 0; c < nch; ++c)
+          if ((int64_t)(c0 + c) < r.chunk_cap) r.chunks[c0 + c] = make_int2((int)v, (int)c);
+        r.fend[v] = b;  // the chunks append from here
+        r.kin[v] = 0ull;
+      }
+    }
+    unsigned todo = __ballot_sync(kFull, v < r.g.n && deg <= kRefineRowMax);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int32_t i = (int32_t)(base + src);
+      const int64_t bi = __shfl_sync(kFull, b, src), ei = bi + __shfl_sync(kFull, deg, src);
+      const int32_t ci = r.Cp[i];
+      unsigned cnt = 0;
+      unsigned long long kin = 0;
+      for (int64_t k0 = bi; k0 < ei; k0 += 32) {
+        const int64_t k = k0 + lane;
+        int32_t j = -1;
+        if (k < ei) j = __ldg(r.g.col + k);
+        const bool keep = j >= 0 && j != i && r.Cp[j] == ci;
+        const uint32_t w = keep ? load_w<WK>(r.g.w, k) : 0u;
+        const unsigned m = __ballot_sync(kFull, keep);
+        if (keep) {
+          const int64_t pos = bi + cnt + __popc(m & lanemask_lt());
+          r.fcol[pos] = j;
+          if (r.fw) r.fw[pos] = w;
+        }
+        cnt += __popc(m);
+        kin += w;
+      }
+      kin = warp_sum_u(kin);
+      if (lane == 0) {
+        r.fend[i] = bi + cnt;
+        const bool ok = well_connected(r.two_m, kin, r.K[i], r.Sigma[ci]);
+        r.elig[i] = ok ? 1 : 0;
+        r.flag[i] = ok ? kFlagUnproc : 0;
+      }
+    }
+  }
+}
+
+// One block per chunk of a long row: each warp filters 16 steps of 32
+// entries, takes its place in the row with one atomic, then writes.
+template <int WK>
+__global__ void __launch_bounds__(kRefineNT) k_refine_chunks(RefineArgs r) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned long long total = r.ctr->refine_chunks;
+  const long long nch = (long long)total < r.chunk_cap ? (long long)total : r.chunk_cap;
+  for (long long q = blockIdx.x; q < nch; q += gridDim.x) {
+    const int2 rec = r.chunks[q];
+    const int32_t i = rec.x;
+    const int64_t e = r.g.end[i];
+    const int64_t k0 = r.g.begin[i] + (int64_t)rec.y * kRefineChunk + (int64_t)warp * (32 * kRefineSteps);
+    const int32_t ci = r.Cp[i];
+    int32_t jj[kRefineSteps];
+    unsigned keepbits = 0, n_keep = 0;
+    unsigned long long kin = 0;
+#pragma unroll
+    for (int t = 0; t < kRefineSteps; ++t) {
+      const int64_t k = k0 + t * 32 + lane;
+      int32_t j = -1;
+      if (k < e) j = __ldg(r.g.col + k);  // the 8 warps cover the chunk's 4096 entries
+      const bool keep = j >= 0 && j != i && r.Cp[j] == ci;
+      jj[t] = j;
+      if (keep) {
+        keepbits |= 1u << t;
+        kin += load_w<WK>(r.g.w, k);
+      }
+      n_keep += __popc(__ballot_sync(kFull, keep));
+    }
+    unsigned long long at = 0;
+    if (lane == 0 && n_keep) at = atomicAdd((unsigned long long *)(r.fend + i), (unsigned long long)n_keep);
+    at = __shfl_sync(kFull, at, 0);
+#pragma unroll
+    for (int t = 0; t < kRefineSteps; ++t) {
+      const bool keep = (keepbits >> t) & 1u;
+      const unsigned m = __ballot_sync(kFull, keep);
+      if (keep) {
+        const int64_t pos = (int64_t)at + __popc(m & lanemask_lt());
+        r.fcol[pos] = jj[t];
+        if (r.fw) r.fw[pos] = load_w<WK>(r.g.w, k0 + t * 32 + lane);
+      }
+      at += __popc(m);
+    }
+    kin = warp_sum_u(kin);
+    if (lane == 0 && kin) atomicAdd(r.kin + i, kin);
+  }
+}
+
+// Well-connectedness of the long rows, once their chunks are summed.
+__global__ void k_refine_long_elig(RefineArgs r) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < r.g.n; v += (int64_t)gridDim.x * blockDim.x) {
+    if (r.g.end[v] - r.g.begin[v] <= kRefineRowMax) continue;
+    const bool ok = well_connected(r.two_m, r.kin[v], r.K[v], r.Sigma[r.Cp[v]]);
+    r.elig[v] = ok ? 1 : 0;
+    r.flag[v] = ok ? kFlagUnproc : 0;
+  }
+}
+
+// A bucket's decisions: every target a decision chose is marked ...
+__global__ void k_refine_choose(const Counters *ctr, const int32_t *mv_target, uint8_t *chosen) {
+  const unsigned long long cnt = ctr->movers;
+  for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < cnt;
+       k += (unsigned long long)gridDim.x * blockDim.x)
+    chosen[mv_target[k]] = 1;
+}
+
+// ... and a decision moves its vertex only if no decision chose that vertex
+// (so no mover is the target of another, and every refined community keeps
+// the id of a member).  The target community is no longer a known singleton.
+__global__ void k_refine_apply(const Counters *ctr, const int32_t *mv_vertex, const int32_t *mv_target,
+                               const uint8_t *chosen, int32_t *Cr, int64_t *Sr, const int64_t *K, uint32_t *recv) {
+  const unsigned long long cnt = ctr->movers;
+  for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < cnt;
+       k += (unsigned long long)gridDim.x * blockDim.x) {
+    const int32_t v = mv_vertex[k];
+    if (chosen[v]) continue;
+    const int32_t t = mv_target[k];
+    const long long Kv = K[v];
+    Cr[v] = t;
+    atomicAdd((unsigned long long *)(Sr + v), as_ull(-Kv));
+    atomicAdd((unsigned long long *)(Sr + t), as_ull(Kv));
+    atomicOr(recv + (t >> 5), 1u << (t & 31));
+  }
+}
+
+// Flags for the rest of the sweep: a vertex still decides if it is well
+// connected, no decision has chosen it, and its bucket comes after `bucket`
+// (the decision kernels re-mark neighbours of movers; that is undone here).
+__global__ void k_refine_flags(int64_t n, const uint8_t *elig, const uint8_t *chosen, uint8_t *flag, uint32_t salt,
+                               uint32_t nbuckets, uint32_t bucket) {
+  const bool pow2 = (nbuckets & (nbuckets - 1)) == 0;
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t h = fmix32((uint32_t)v ^ salt);
+    const uint32_t bk = pow2 ? (h & (nbuckets - 1)) : (h % nbuckets);
+    flag[v] = (elig[v] && !chosen[v] && bk > bucket) ? kFlagUnproc : 0;
+  }
+}
+
+// Start of the next pass from P: super-vertex s of the refined partition
+// (dense id Cr[v] of its members v) starts in the community of P of its
+// members, represented by the smallest super-vertex of that community.
+__global__ void k_fill_i32(int32_t *x, int64_t n, int32_t value) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = value;
+}
+__global__ void k_leiden_rep(int64_t n, const int32_t *Cp, const int32_t *Cr, int32_t *rep) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    atomicMin(rep + Cp[v], Cr[v]);
+}
+__global__ void k_leiden_init(int64_t n, const int32_t *Cp, const int32_t *Cr, const int32_t *rep, int32_t *init) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    init[Cr[v]] = rep[Cp[v]];
+}
+
+// After pass initialisation (C' = identity, Sigma' = K): every super-vertex
+// joins its starting community, whose Sigma' receives its K; a community
+// with more than one member is no longer a known singleton.
+__global__ void k_leiden_start(int64_t n, const int32_t *init, const int64_t *K, int32_t *Cp, int64_t *Sigma,
+                               uint32_t *recv) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = init[s];
+    Cp[s] = c;
+    if (c == (int32_t)s) continue;
+    const long long Ks = K[s];
+    atomicAdd((unsigned long long *)(Sigma + c), as_ull(Ks));
+    atomicAdd((unsigned long long *)(Sigma + s), as_ull(-Ks));
+    atomicOr(recv + (c >> 5), 1u << (c & 31));
+  }
+}
+
+}  // namespace
+
+void refine_rows(const RefineArgs &r, int wkind, int num_sms, cudaStream_t s) {
+  if (r.g.n <= 0) return;
+  cudaMemsetAsync(&r.ctr->refine_chunks, 0, sizeof(unsigned long long), s);
+  const int grid = grid_for((r.g.n + 31) / 32 * 32, 256, num_sms, 8);
+  if (wkind == W_UNIT) {
+    LV_LAUNCH(k_refine_rows<W_UNIT><<<grid, 256, 0, s>>>(r));
+    LV_LAUNCH(k_refine_chunks<W_UNIT><<<num_sms * 8, kRefineNT, 0, s>>>(r));
+  } else {
+    LV_LAUNCH(k_refine_rows<W_U32><<<grid, 256, 0, s>>>(r));
+    LV_LAUNCH(k_refine_chunks<W_U32><<<num_sms * 8, kRefineNT, 0, s>>>(r));
+  }
+  LV_LAUNCH(k_refine_long_elig<<<grid_for(r.g.n, 256, num_sms, 8), 256, 0, s>>>(r));
+}
+
+void refine_resolve(const RefineArgs &r, const int32_t *mv_vertex, const int32_t *mv_target, uint32_t *recv,
+                    int num_sms, cudaStream_t s) {
+  LV_LAUNCH(k_refine_choose<<<num_sms * 4, 256, 0, s>>>(r.ctr, mv_target, r.chosen));
+  LV_LAUNCH(k_refine_apply<<<num_sms * 4, 256, 0, s>>>(r.ctr, mv_vertex, mv_target, r.chosen, r.Cr, r.Sr, r.K, recv));
+}
+
+void refine_flags(const RefineArgs &r, uint32_t salt, uint32_t nbuckets, uint32_t bucket, int num_sms, cudaStream_t s) {
+  if (r.g.n <= 0) return;
+  LV_LAUNCH(k_refine_flags<<<grid_for(r.g.n, 256, num_sms, 8), 256, 0, s>>>(r.g.n, r.elig, r.chosen, r.flag, salt,
+                                                                            nbuckets, bucket));
+}
+
+void leiden_next_init(int64_t n, const int32_t *Cp, const int32_t *Cr, int32_t *rep, int32_t *init, int num_sms,
+                      cudaStream_t s) {
+  if (n <= 0) return;
+  const int grid = grid_for(n, 256, num_sms, 8);
+  LV_LAUNCH(k_fill_i32<<<grid, 256, 0, s>>>(rep, n, INT_MAX));
+  LV_LAUNCH(k_leiden_rep<<<grid, 256, 0, s>>>(n, Cp, Cr, rep));
+  LV_LAUNCH(k_leiden_init<<<grid, 256, 0, s>>>(n, Cp, Cr, rep, init));
+}
+
+void leiden_start(int64_t n, const int32_t *init, const int64_t *K, int32_t *Cp, int64_t *Sigma, uint32_t *recv,
+                  int num_sms, cudaStream_t s) {
+  if (n <= 0) return;
+  LV_LAUNCH(k_leiden_start<<<grid_for(n, 256, num_sms, 8), 256, 0, s>>>(n, init, K, Cp, Sigma, recv));
+}
+
+}  // namespace lv

@@ -63,7 +63,7 @@ class LouvainConfig(ctypes.Structure):
                 ("profile_mask", ctypes.c_uint32), ("trace_capacity", ctypes.c_int64), ("trace_rate", ctypes.c_float),
                 ("learned_fallback", ctypes.c_int32), ("learned_skip_clears", ctypes.c_int32),
                 ("table_window", ctypes.c_int64), ("asynchronous", ctypes.c_int32),
-                ("learned_min_degree", ctypes.c_int32)]
+                ("learned_min_degree", ctypes.c_int32), ("refine", ctypes.c_int32)]
 
 
 _lib = None
@@ -172,6 +172,7 @@ class Config:
     table_window: int = 0
     asynchronous: bool = False
     learned_min_degree: int = 0
+    refine: bool = False  # the Leiden form: refine P before aggregating it
 
     def c(self) -> LouvainConfig:
         self._model_keep = None
@@ -185,7 +186,7 @@ class Config:
                              int(self.record_pass_modularity), int(self.check_symmetry), self.profile_mask,
                              self.trace_capacity, self.trace_rate, self.learned_fallback,
                              self.learned_skip_clears, self.table_window, int(self.asynchronous),
-                             self.learned_min_degree)
+                             self.learned_min_degree, int(self.refine))
 
 
 @dataclass

@@ -4,8 +4,10 @@ Each mutant is one plausible mistake planted in a scratch copy of the
 oracle.  In oracle/louvain_oracle.c: a dropped or sign-flipped term of
 Eq. 2, a reversed tie-break or Pick-Less rule, a missing Sigma' or C'
 update, a stopping rule off at its boundary, a missing dendrogram lookup,
-and so on; the copy is compiled and tests/test_oracle_pins.py runs against
-it.  In oracle/mlp.py (the predictor): a missing ReLU or bias, a transposed
+and so on, and in its Leiden form a refinement that ignores P, lets chosen
+vertices move or misstates the well-connectedness condition; the copy is
+compiled and tests/test_oracle_pins.py and tests/test_oracle_leiden.py run
+against it.  In oracle/mlp.py (the predictor): a missing ReLU or bias, a transposed
 weight or gradient, a wrong loss scale or sign, bf16 rounding without ties
 to even; tests/test_oracle_mlp.py runs against it.  Every mutant must make
 some pin fail.  The repository's own oracle is never modified.
@@ -48,13 +50,13 @@ MUTANTS = {
     "m instead of 2m": ("  for (int64_t k = 0; k < G.nnz; ++k) two_m += G.w[k];\n",
                         "  for (int64_t k = 0; k < G.nnz; ++k) two_m += G.w[k];\n  two_m /= 2;\n"),
     "converged only at l_i < 1": ("if (li <= 1) { pending = 1;", "if (li < 1) { pending = 1;"),
-    "aggregation tolerance >=": ("(double)gamma / (double)np > cfg->aggregation_tolerance",
-                                 "(double)gamma / (double)np >= cfg->aggregation_tolerance"),
+    "aggregation tolerance >=": ("(double)nagg / (double)np > cfg->aggregation_tolerance",
+                                 "(double)nagg / (double)np >= cfg->aggregation_tolerance"),
     "tau grows": ("tau /= cfg->tolerance_drop;", "tau *= cfg->tolerance_drop;"),
     "tau scaled before the first pass": ("  double tau = cfg->tolerance;",
                                          "  double tau = cfg->tolerance / cfg->tolerance_drop;"),
     "no dendrogram lookup": (
-        "    for (int64_t v = 0; v < n; ++v) C[v] = Cp[C[v]];                  /* dendrogram lookup */\n", ""),
+        "    for (int64_t v = 0; v < n; ++v) C[v] = agg[C[v]];                 /* dendrogram lookup */\n", ""),
     "no final lookup after a break": ("  if (pending)\n    for (int64_t v = 0; v < n; ++v) C[v] = Cp[C[v]];\n", ""),
     "renumbering reversed": ("  for (int64_t i = 0; i < len; ++i) x[i] = newid[x[i]];",
                              "  for (int64_t i = 0; i < len; ++i) x[i] = (int32_t)(run - 1 - newid[x[i]]);"),
@@ -63,6 +65,14 @@ MUTANTS = {
     "S_tot not squared": ("s_tot += (i128)Sig[c] * Sig[c];", "s_tot += (i128)Sig[c];"),
     "bucket by mask": ("return fmix32((uint32_t)i ^ salt) % (uint32_t)B;",
                        "return fmix32((uint32_t)i ^ salt) & (uint32_t)(B - 1);"),
+    # the Leiden form
+    "refine ignores the communities of P": ("g->col[e] != i && bound[g->col[e]] == bound[i]", "g->col[e] != i"),
+    "refine: chosen vertices still move": ("if (!dec[a].moves || chosen[v]) continue;", "if (!dec[a].moves) continue;"),
+    "refine: well-connectedness reversed": ("elig[v] = (i128)two_m * kin >= ", "elig[v] = (i128)two_m * kin < "),
+    "refine: well-connectedness without -K_v": ("(Sigma_b[bound[v]] - K[v]);", "Sigma_b[bound[v]];"),
+    "refine: target total not updated": ("      Sr[t] += K[v];\n", ""),
+    "Leiden: next pass from singletons": ("if (cfg->refine && lp > 0) {", "if (0) {"),
+    "Leiden: pass cap returns the refinement": ("if (!pending && cfg->refine && passes > 0)", "if (0)"),
 }
 
 
@@ -85,7 +95,7 @@ def copy_tree(scratch: str) -> str:
         shutil.copytree(os.path.join(ROOT, sub), os.path.join(scratch, sub), dirs_exist_ok=True,
                         ignore=shutil.ignore_patterns("__pycache__", "*.so"))
     for f in ("paper_2501_19004_gb300/__init__.py", "tests/conftest.py", "tests/test_oracle_pins.py",
-              "tests/test_oracle_mlp.py"):
+              "tests/test_oracle_leiden.py", "tests/test_oracle_mlp.py"):
         shutil.copy(os.path.join(ROOT, f), os.path.join(scratch, f))
     return os.path.join(scratch, "oracle", "louvain_oracle.c")
 
@@ -103,7 +113,8 @@ def main() -> int:
     build_libs(scratch)
     orig = open(src).read()
     lib = os.path.join(scratch, "oracle", "liblouvain_oracle.so")
-    pins = [sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "-x", "-q", "-p", "no:cacheprovider"]
+    pins = [sys.executable, "-m", "pytest", "tests/test_oracle_pins.py", "tests/test_oracle_leiden.py", "-x", "-q",
+            "-p", "no:cacheprovider"]
     assert subprocess.run(pins, cwd=scratch, capture_output=True).returncode == 0, "pins fail on the unmutated copy"
     survivors = 0
     try:
