@@ -295,6 +295,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-skip leg")
     ap.add_argument("--no-async", action="store_true", help="skip the asynchronous-form leg")
+    ap.add_argument("--no-leiden", action="store_true", help="skip the Leiden-form leg")
     ap.add_argument("--skip-threshold", type=float, default=None, help="default: the stored model's setting")
     ap.add_argument("--learned-min-degree", type=int, default=None, help="default: the stored model's setting")
     ap.add_argument("--graphs", type=int, default=0, help="batch workloads: run only the first N graphs")
@@ -497,6 +498,15 @@ def main():
                         "iterations": ast["iterations"], "evaluated": ast["evaluated"],
                         "evaluated_plain": st["evaluated"], "communities": ares.communities}
 
+    # the Leiden form (refinement before aggregation; deterministic)
+    leiden = None
+    if not args.no_leiden and not batch:
+        rms, rres, rst = timed_leg(lv.Config(refine=True))
+        leiden = {"value": job_rate(g.nnz, args.steps, world, rms / 1e3), "unit": UNIT,
+                  "ms_per_step": rms / args.steps, "modularity": rres.modularity,
+                  "dq_vs_plain": rres.modularity - res.modularity, "passes": rres.passes,
+                  "communities": rres.communities, "exit_reason": rres.exit_reason}
+
     peaks, src = load_peaks()
     achieved = dom_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else None
     # DRAM bytes per launch: a small capture's bytes per row entry (ncu on
@@ -604,7 +614,8 @@ def main():
                        "l2": f"inputs larger than L2 (CSR {(g.offsets.nbytes + g.cols.nbytes) / 1e9:.2f} GB), no flush",
                        **summary},
             "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
-            "learned_skip": learned, "asynchronous": asynchronous, "sequential": sequential, "batch": batch_leg,
+            "learned_skip": learned, "asynchronous": asynchronous, "leiden": leiden, "sequential": sequential,
+            "batch": batch_leg,
             "autotune": tune,
             "phases_ms": {"move": st["move_ms"], "aggregate": st["aggregate_ms"], "other": st["other_ms"]},
             "kernels_ms_warmup": {k: round(v["ms"], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:8]},

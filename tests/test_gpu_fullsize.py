@@ -1,8 +1,8 @@
 """Parity at the benchmark's full sizes, in the launch configuration the
 benchmark times (concurrent bins, CUDA-graph replay, the batched context).
 
-- R-MAT scale 24 (the default benchmark workload): bit-exact against a full
-  oracle run (memberships, per-pass records, exact modularity).
+- R-MAT scale 24: bit-exact against a full oracle run (memberships, per-pass
+  records, exact modularity), in the Louvain and in the Leiden form.
 - The 4,096-graph batch: one batched run of all graphs; 32 graphs sampled
   with a stride are checked bit-exactly against the oracle run on each.
 - The 8192 x 8192 grid: bit-exact against a full oracle run.
@@ -45,6 +45,20 @@ def test_rmat24_bit_exact_full_size():
     assert np.array_equal(res.membership, ref.membership)
     assert (res.q_num, res.q_den) == (ref.q_num, ref.q_den)
     assert abs(res.modularity - ref.modularity) <= 1e-9
+
+
+def test_rmat24_leiden_bit_exact_full_size():
+    g = gg.rmat(24, 16, seed=7)
+    with lv.Louvain(lv.DeviceCSR.from_host(g), lv.Config(refine=True, record_pass_modularity=True)) as ctx:
+        ctx.set_schedule(FAST)
+        res = ctx.run().result()
+    ref = oracle.louvain(g, oracle.Config(refine=True))
+    assert res.passes == ref.passes and res.exit_reason == ref.exit_reason
+    P = ref.passes
+    assert np.array_equal(res.pass_stats[:P], ref.pass_stats[:P])
+    assert np.array_equal(res.iter_stats[:P], ref.iter_stats[:P])
+    assert np.array_equal(res.membership, ref.membership)
+    assert (res.q_num, res.q_den) == (ref.q_num, ref.q_den)
 
 
 def test_batch4096_sampled_bit_exact():
