@@ -44,6 +44,9 @@ WORKLOADS = {
                    "int32 ids / int64 offsets, seed 7"),
     "grid8192": dict(kind="grid", side=8192, frac=0.02, seed=11, desc="8192x8192 4-neighbour grid + 2% random "
                      "long-range edges, uniform integer weights 1-8, seed 11"),
+    "grid4096": dict(kind="grid", side=4096, frac=0.02, seed=11, desc="4096x4096 4-neighbour grid + 2% random "
+                     "long-range edges, uniform integer weights 1-8, seed 11 (profiling case: the grid workload's "
+                     "generator at a quarter of the size)"),
     "sbm1000": dict(kind="sbm", n=1000, block=100, p_in=0.1, p_out=0.002, seed=1, desc="planted-partition SBM, "
                     "1,000 vertices in 10 blocks of 100, p_in=0.1, p_out=0.002, seed 1"),
     "rmat22": dict(kind="rmat", scale=22, ef=16, seed=7, desc="R-MAT scale 22, edge factor 16, "
@@ -62,6 +65,7 @@ WORKLOADS = {
 REF_SAMPLES = {
     "rmat24": dict(kind="rmat", scale=20, ef=16, seed=7, desc="R-MAT scale 20 (same generator and parameters)"),
     "grid8192": dict(kind="grid", side=1024, frac=0.02, seed=11, desc="1024x1024 grid (same generator)"),
+    "grid4096": dict(kind="grid", side=1024, frac=0.02, seed=11, desc="1024x1024 grid (same generator)"),
     "sbm1000": dict(kind="sbm", n=1000, block=100, p_in=0.1, p_out=0.002, seed=1, desc="the full workload"),
     "rmat22": dict(kind="rmat", scale=20, ef=16, seed=7, desc="R-MAT scale 20 (same generator and parameters)"),
     "rmat27": dict(kind="rmat", scale=20, ef=16, seed=13, desc="R-MAT scale 20 (same generator and parameters)"),
@@ -70,6 +74,7 @@ REF_SAMPLES = {
 SAMPLES = {
     "rmat24": dict(kind="rmat", scale=21, ef=16, seed=7, desc="R-MAT scale 21 (same generator and parameters)"),
     "grid8192": dict(kind="grid", side=1448, frac=0.02, seed=11, desc="1448x1448 grid (same generator)"),
+    "grid4096": dict(kind="grid", side=1024, frac=0.02, seed=11, desc="1024x1024 grid (same generator)"),
     "sbm1000": dict(kind="sbm", n=1000, block=100, p_in=0.1, p_out=0.002, seed=1, desc="the full workload"),
     "rmat22": dict(kind="rmat", scale=20, ef=16, seed=7, desc="R-MAT scale 20 (same generator and parameters)"),
     "rmat27": dict(kind="rmat", scale=21, ef=16, seed=13, desc="R-MAT scale 21 (same generator and parameters)"),
