@@ -932,13 +932,38 @@ __global__ void __launch_bounds__(256) k_apply(MoveArgs a) {
 // block.  The stored set is fixed by the graph; only its order varies.
 __global__ void __launch_bounds__(256) k_sample_plan(GView g, LearnArgs L, Counters *ctr) {
   const int64_t dmin = L.min_degree > kSample ? L.min_degree : kSample + 1;
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.n; v += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t deg = g.end[v] - g.begin[v];
+  const int lane = threadIdx.x & 31;
+  // whole warps step together, so the blocks and chunks of a warp's
+  // vertices are taken with one atomic each
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < g.n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = base + threadIdx.x;
+    const int64_t deg = v < g.n ? g.end[v] - g.begin[v] : 0;
+    const bool mine = v < g.n && deg >= dmin;
+    const int64_t nch = mine ? (deg + kSampleChunk - 1) / kSampleChunk : 0;
+    const unsigned m = __ballot_sync(kFull, mine);
+    if (!m) {
+      if (v < g.n) L.sample_at[v] = -1;
+      continue;
+    }
+    unsigned long long incl = (unsigned long long)nch;  // inclusive scan of the chunk counts
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const unsigned long long wtot = __shfl_sync(kFull, incl, 31);
+    unsigned long long b0 = 0, cb = 0;
+    if (lane == 0) {
+      b0 = atomicAdd(&ctr->sample_blocks, (unsigned long long)__popc(m));
+      cb = atomicAdd(&ctr->sample_chunks, wtot);
+    }
+    b0 = __shfl_sync(kFull, b0, 0);
+    cb = __shfl_sync(kFull, cb, 0);
+    if (v >= g.n) continue;
     int32_t at = -1;
-    if (deg >= dmin) {
-      const unsigned long long blk = atomicAdd(&ctr->sample_blocks, 1ull);
-      const int64_t nch = (deg + kSampleChunk - 1) / kSampleChunk;
-      const unsigned long long c0 = atomicAdd(&ctr->sample_chunks, (unsigned long long)nch);
+    if (mine) {
+      const unsigned long long blk = b0 + __popc(m & lanemask_lt());
+      const unsigned long long c0 = cb + incl - (unsigned long long)nch;
       // both lists are sized for the input's rows (louvain_create); a
       // vertex that finds no room keeps reading its whole row
       if ((int64_t)blk < L.sample_cap && (int64_t)(c0 + nch) <= L.chunk_cap) {
