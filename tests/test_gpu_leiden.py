@@ -114,3 +114,26 @@ def test_leiden_refused_combinations():
         res = ctx.run().result()  # the context stays usable
     ref = oracle.louvain(g, oracle.Config(refine=True))
     assert np.array_equal(res.membership, ref.membership)
+
+
+@pytest.mark.parametrize("buckets,window", [(1, 4096), (4, 4096)])
+def test_leiden_hub_rounds(buckets, window):
+    """Small table windows put the hub tables of local moving and of the
+    refinement, and the big-community merge tables, through many rounds."""
+    res, ref = run_leiden(gg.rmat(19, 16, seed=7), lv.Config(buckets=buckets, table_window=window))
+    assert_same(res, ref)
+
+
+def test_leiden_edge_cases():
+    # isolated vertices only, a single edge, a single vertex
+    for g in (gg.CSR(np.zeros(6, dtype=np.int64), np.zeros(0, dtype=np.int32), None), gg.from_pairs(2, [0], [1]),
+              gg.CSR(np.zeros(2, dtype=np.int64), np.zeros(0, dtype=np.int32), None)):
+        res, ref = run_leiden(g, device_input=False)
+        assert_same(res, ref)
+    z = gg.CSR(np.zeros(1, dtype=np.int64), np.zeros(0, dtype=np.int32), None)
+    assert lv.run(z, lv.Config(refine=True)).membership.shape == (0,)
+    # stars: the hub in the wide bin (8999 leaves) and in the global-table bin (40000 leaves)
+    for n in (9000, 40001):
+        star = gg.from_pairs(n, np.zeros(n - 1, dtype=np.int64), np.arange(1, n, dtype=np.int64))
+        res, ref = run_leiden(star)
+        assert_same(res, ref)
