@@ -28,10 +28,13 @@ __device__ __forceinline__ bool well_connected(long long two_m, unsigned long lo
   return (unsigned long long)two_m * kin >= (unsigned long long)Ki * (unsigned long long)(Sc - Ki);
 }
 
-// One warp per row of at most kRefineRowMax entries (32 consecutive
-// vertices per warp step); a longer row gets chunk records and its entries
-// are appended by k_refine_chunks.  Every vertex starts as its own refined
-// community.
+// Rows of at most kRefineLaneMax entries: one lane each, four entries'
+// loads in flight at a time.  Longer rows up to kRefineRowMax: one warp per
+// row (32 consecutive vertices per warp step); a longer row gets chunk
+// records and its entries are appended by k_refine_chunks.  Every vertex
+// starts as its own refined community.
+constexpr int64_t kRefineLaneMax = 16;
+
 template <int WK>
 __global__ void __launch_bounds__(256) k_refine_rows(RefineArgs r) {
   const int lane = threadIdx.x & 31;
@@ -56,7 +59,33 @@ __global__ void __launch_bounds__(256) k_refine_rows(RefineArgs r) {
         r.kin[v] = 0ull;
       }
     }
-    unsigned todo = __ballot_sync(kFull, v < r.g.n && deg <= kRefineRowMax);
+    if (v < r.g.n && deg <= kRefineLaneMax) {
+      const int32_t ci = r.Cp[v];
+      int64_t cnt = 0;
+      unsigned long long kin = 0;
+      for (int64_t k0 = b; k0 < b + deg; k0 += 4) {
+        int32_t jj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) jj[u] = k0 + u < b + deg ? __ldg(r.g.col + k0 + u) : -1;
+        int32_t cc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cc[u] = (jj[u] >= 0 && jj[u] != (int32_t)v) ? r.Cp[jj[u]] : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (cc[u] == ci) {
+            const uint32_t w = load_w<WK>(r.g.w, k0 + u);
+            r.fcol[b + cnt] = jj[u];
+            if (r.fw) r.fw[b + cnt] = w;
+            ++cnt;
+            kin += w;
+          }
+      }
+      r.fend[v] = b + cnt;
+      const bool ok = well_connected(r.two_m, kin, r.K[v], r.Sigma[ci]);
+      r.elig[v] = ok ? 1 : 0;
+      r.flag[v] = ok ? kFlagUnproc : 0;
+    }
+    unsigned todo = __ballot_sync(kFull, v < r.g.n && deg > kRefineLaneMax && deg <= kRefineRowMax);
     while (todo) {
       const int src = __ffs(todo) - 1;
       todo &= todo - 1;
