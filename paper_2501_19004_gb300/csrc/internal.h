@@ -311,10 +311,11 @@ struct MoveArgs {
 };
 
 // Leiden refinement (refine.cu).  Rows of at most kRefineRowMax entries are
-// filtered by one warp; longer ones are cut into kRefineChunk-entry chunks,
-// one block each (at most nnz / kRefineChunk + nnz / kRefineRowMax chunks).
-constexpr int64_t kRefineRowMax = 2048;
-constexpr int kRefineChunk = 4096;
+// filtered by one lane each; longer ones are cut into kRefineChunk-entry
+// chunks, one warp each (at most nnz / kRefineChunk + nnz / (kRefineRowMax
+// + 1) chunks).
+constexpr int64_t kRefineRowMax = 16;
+constexpr int kRefineChunk = 512;
 // The filtered view of G' is
 // GView{g.n, g.begin, fend, fcol, fw}: row i keeps its entries inside its
 // community of P, at its own offsets.

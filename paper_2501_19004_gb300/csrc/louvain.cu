@@ -1850,7 +1850,7 @@ louvain_status create_impl(const louvain_graph *graph, const louvain_config *cfg
       return fail(st);
   }
   if (cfg->refine) {
-    x->rchunk_cap = nnz / kRefineChunk + nnz / kRefineRowMax + 1;
+    x->rchunk_cap = nnz / kRefineChunk + nnz / (kRefineRowMax + 1) + 1;
     if ((st = dalloc_n(x, &x->Cr, nv)) || (st = dalloc_n(x, &x->Sr, nv)) || (st = dalloc_n(x, &x->relig, nv)) ||
         (st = dalloc_n(x, &x->rchosen, nv)) || (st = dalloc_n(x, &x->rkin, nv)) ||
         (st = dalloc_n(x, &x->rchunks, x->rchunk_cap)) || (st = dalloc_n(x, &x->linit, nv)) ||

@@ -20,37 +20,43 @@ namespace lv {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kRefineNT = 256;
-constexpr int kRefineSteps = kRefineChunk / kRefineNT;  // 32-entry steps per warp: 16
+constexpr int kRefineSteps = kRefineChunk / 32;  // 32-entry steps of a chunk's warp: 16
 
 __device__ __forceinline__ bool well_connected(long long two_m, unsigned long long kin, long long Ki, long long Sc) {
   // 2m K_{i->C} >= K_i (Sigma_C - K_i); both sides are below 2^64
   return (unsigned long long)two_m * kin >= (unsigned long long)Ki * (unsigned long long)(Sc - Ki);
 }
 
-// Rows of at most kRefineLaneMax entries: one lane each, four entries'
-// loads in flight at a time.  Longer rows up to kRefineRowMax: one warp per
-// row (32 consecutive vertices per warp step); a longer row gets chunk
-// records and its entries are appended by k_refine_chunks.  Every vertex
-// starts as its own refined community.
-constexpr int64_t kRefineLaneMax = 16;
-
+// Every vertex starts as its own refined community.  A row of at most
+// kRefineRowMax entries is filtered by its own lane, four entries' loads in
+// flight at a time; a longer row gets one chunk record per kRefineChunk
+// entries (taken with one atomic per warp) and k_refine_chunks appends its
+// entries.
 template <int WK>
 __global__ void __launch_bounds__(256) k_refine_rows(RefineArgs r) {
   const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base = warp * 32; base < r.g.n; base += nwarps * 32) {
-    const int64_t v = base + lane;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < r.g.n; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t v = base + threadIdx.x;
     int64_t b = 0, deg = 0;
     if (v < r.g.n) {
       b = r.g.begin[v];
       deg = r.g.end[v] - b;
       r.Cr[v] = (int32_t)v;
       r.Sr[v] = r.K[v];
-      if (deg > kRefineRowMax) {
-        const int64_t nch = (deg + kRefineChunk - 1) / kRefineChunk;
-        const unsigned long long c0 = atomicAdd(&r.ctr->refine_chunks, (unsigned long long)nch);
+    }
+    const bool longrow = v < r.g.n && deg > kRefineRowMax;
+    const int64_t nch = longrow ? (deg + kRefineChunk - 1) / kRefineChunk : 0;
+    if (__ballot_sync(kFull, longrow)) {
+      unsigned long long incl = (unsigned long long)nch;  // inclusive scan of the warp's chunk counts
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
+      }
+      unsigned long long c0 = 0;
+      if (lane == 31) c0 = atomicAdd(&r.ctr->refine_chunks, incl);
+      c0 = __shfl_sync(kFull, c0, 31) + incl - (unsigned long long)nch;
+      if (longrow) {
         // the list is sized for the input's rows (louvain_create), so it never runs out
         if ((int64_t)(c0 + nch) > r.chunk_cap) atomicOr(&r.ctr->error, (unsigned long long)ERR_RANGE);
         for (int64_t c = 0; c < nch; ++c)
@@ -59,7 +65,7 @@ __global__ void __launch_bounds__(256) k_refine_rows(RefineArgs r) {
         r.kin[v] = 0ull;
       }
     }
-    if (v < r.g.n && deg <= kRefineLaneMax) {
+    if (v < r.g.n && !longrow) {
       const int32_t ci = r.Cp[v];
       int64_t cnt = 0;
       unsigned long long kin = 0;
@@ -85,67 +91,37 @@ __global__ void __launch_bounds__(256) k_refine_rows(RefineArgs r) {
       r.elig[v] = ok ? 1 : 0;
       r.flag[v] = ok ? kFlagUnproc : 0;
     }
-    unsigned todo = __ballot_sync(kFull, v < r.g.n && deg > kRefineLaneMax && deg <= kRefineRowMax);
-    while (todo) {
-      const int src = __ffs(todo) - 1;
-      todo &= todo - 1;
-      const int32_t i = (int32_t)(base + src);
-      const int64_t bi = __shfl_sync(kFull, b, src), ei = bi + __shfl_sync(kFull, deg, src);
-      const int32_t ci = r.Cp[i];
-      unsigned cnt = 0;
-      unsigned long long kin = 0;
-      for (int64_t k0 = bi; k0 < ei; k0 += 32) {
-        const int64_t k = k0 + lane;
-        int32_t j = -1;
-        if (k < ei) j = __ldg(r.g.col + k);
-        const bool keep = j >= 0 && j != i && r.Cp[j] == ci;
-        const uint32_t w = keep ? load_w<WK>(r.g.w, k) : 0u;
-        const unsigned m = __ballot_sync(kFull, keep);
-        if (keep) {
-          const int64_t pos = bi + cnt + __popc(m & lanemask_lt());
-          r.fcol[pos] = j;
-          if (r.fw) r.fw[pos] = w;
-        }
-        cnt += __popc(m);
-        kin += w;
-      }
-      kin = warp_sum_u(kin);
-      if (lane == 0) {
-        r.fend[i] = bi + cnt;
-        const bool ok = well_connected(r.two_m, kin, r.K[i], r.Sigma[ci]);
-        r.elig[i] = ok ? 1 : 0;
-        r.flag[i] = ok ? kFlagUnproc : 0;
-      }
-    }
   }
 }
 
-// One block per chunk of a long row: each warp filters 16 steps of 32
-// entries, takes its place in the row with one atomic, then writes.
+// One warp per chunk of a long row: 16 steps of 32 entries with their loads
+// in flight, one atomic for the chunk's place in the row, then the writes.
 template <int WK>
-__global__ void __launch_bounds__(kRefineNT) k_refine_chunks(RefineArgs r) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__global__ void __launch_bounds__(256) k_refine_chunks(RefineArgs r) {
+  const int lane = threadIdx.x & 31;
   const unsigned long long total = r.ctr->refine_chunks;
   const long long nch = (long long)total < r.chunk_cap ? (long long)total : r.chunk_cap;
-  for (long long q = blockIdx.x; q < nch; q += gridDim.x) {
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long q = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nch; q += nwarps) {
     const int2 rec = r.chunks[q];
     const int32_t i = rec.x;
     const int64_t e = r.g.end[i];
-    const int64_t k0 = r.g.begin[i] + (int64_t)rec.y * kRefineChunk + (int64_t)warp * (32 * kRefineSteps);
+    const int64_t k0 = r.g.begin[i] + (int64_t)rec.y * kRefineChunk;
     const int32_t ci = r.Cp[i];
     int32_t jj[kRefineSteps];
+#pragma unroll
+    for (int t = 0; t < kRefineSteps; ++t) {
+      const int64_t k = k0 + t * 32 + lane;
+      jj[t] = k < e ? __ldg(r.g.col + k) : -1;
+    }
     unsigned keepbits = 0, n_keep = 0;
     unsigned long long kin = 0;
 #pragma unroll
     for (int t = 0; t < kRefineSteps; ++t) {
-      const int64_t k = k0 + t * 32 + lane;
-      int32_t j = -1;
-      if (k < e) j = __ldg(r.g.col + k);  // the 8 warps cover the chunk's 4096 entries
-      const bool keep = j >= 0 && j != i && r.Cp[j] == ci;
-      jj[t] = j;
+      const bool keep = jj[t] >= 0 && jj[t] != i && r.Cp[jj[t]] == ci;
       if (keep) {
         keepbits |= 1u << t;
-        kin += load_w<WK>(r.g.w, k);
+        kin += load_w<WK>(r.g.w, k0 + t * 32 + lane);
       }
       n_keep += __popc(__ballot_sync(kFull, keep));
     }
@@ -255,13 +231,13 @@ __global__ void k_leiden_start(int64_t n, const int32_t *init, const int64_t *K,
 void refine_rows(const RefineArgs &r, int wkind, int num_sms, cudaStream_t s) {
   if (r.g.n <= 0) return;
   cudaMemsetAsync(&r.ctr->refine_chunks, 0, sizeof(unsigned long long), s);
-  const int grid = grid_for((r.g.n + 31) / 32 * 32, 256, num_sms, 8);
+  const int grid = grid_for(r.g.n, 256, num_sms, 8);
   if (wkind == W_UNIT) {
     LV_LAUNCH(k_refine_rows<W_UNIT><<<grid, 256, 0, s>>>(r));
-    LV_LAUNCH(k_refine_chunks<W_UNIT><<<num_sms * 8, kRefineNT, 0, s>>>(r));
+    LV_LAUNCH(k_refine_chunks<W_UNIT><<<num_sms * 8, 256, 0, s>>>(r));
   } else {
     LV_LAUNCH(k_refine_rows<W_U32><<<grid, 256, 0, s>>>(r));
-    LV_LAUNCH(k_refine_chunks<W_U32><<<num_sms * 8, kRefineNT, 0, s>>>(r));
+    LV_LAUNCH(k_refine_chunks<W_U32><<<num_sms * 8, 256, 0, s>>>(r));
   }
   LV_LAUNCH(k_refine_long_elig<<<grid_for(r.g.n, 256, num_sms, 8), 256, 0, s>>>(r));
 }
