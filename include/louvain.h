@@ -25,6 +25,10 @@
  * 2 * sum(gains) / (2m)^2 <= tau.  All of this is exact integer arithmetic.
  * louvain_config.asynchronous = 1 selects the paper's own asynchronous form
  * instead (moves applied in place as they are decided; not reproducible).
+ * louvain_config.refine = 1 selects the Leiden form (Traag, Waltman and van
+ * Eck 2019, which Sec. 5.2 and Sec. 6 expect the paper's findings to extend
+ * to): each pass's partition is refined, deterministically, before it is
+ * aggregated (see the field).
  *
  * Conventions for every function below:
  *   - A status code is returned; nothing aborts, exits or traps.  On error,
