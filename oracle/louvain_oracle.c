@@ -317,7 +317,8 @@ out:
  *   - A vertex that any decision of the bucket chose as its target stays
  *     where it is and can no longer move; the other movers are applied.
  *     So no mover is ever the target of another, and every refined
- *     community keeps the id of one of its members (its first vertex).
+ *     community keeps the id of one of its members (the target the others
+ *     joined, which never moves).
  * Every merge needs K_{v->T} > 0, so refined communities are connected
  * subsets of the communities of P.  Leiden's randomised choice among the
  * merges that do not lower the quality is replaced by the best one. */
