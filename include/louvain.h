@@ -289,10 +289,10 @@ louvain_status louvain_set_schedule(louvain_ctx *ctx, const int32_t *words, int3
  * max_runs trials; a whole-run trial is the faster of two runs), in order:
  * the bin thresholds by whole-run time (a triple replaces the current one
  * only if it is at least 1.5% faster, more than run-to-run noise); the
- * blocks per SM of every bin by
- * per-kernel CUDA-event time; concurrent bin kernels on or off; graph replay
- * on or off.  The tuned schedule is kept only if it beats the starting one.
- * json (may be NULL) receives {"runs", "start_ms", "tuned_ms", "schedule",
+ * blocks per SM of every bin by per-kernel CUDA-event time (the current
+ * values are one of the candidates); concurrent bin kernels on or off;
+ * graph replay on or off.  The tuned schedule is kept only if it beats the
+ * starting one.  json (may be NULL) receives {"runs", "start_ms", "tuned_ms", "schedule",
  * "trials"}.  The context holds a valid result of the chosen schedule
  * afterwards. */
 louvain_status louvain_autotune(louvain_ctx *ctx, int32_t max_runs, char *json, size_t cap);

@@ -2566,8 +2566,9 @@ louvain_status louvain_autotune(louvain_ctx *x, int32_t max_runs, char *json, si
             best = t;
           }
         }
-    // 2. blocks per SM, all bins at once per candidate
-    const int cands[] = {2, 3, 4, 6, 8, 12, 16};
+    // 2. blocks per SM, all bins at once per candidate; the current values
+    // are measured first, so a bin keeps them unless a candidate is faster
+    const int cands[] = {0, 2, 3, 4, 6, 8, 12, 16};  // 0: the current values
     double mv_best[kMoveBins], mg_best[kMergeBins];
     int mv_arg[kMoveBins], mg_arg[kMergeBins];
     for (int b = 0; b < kMoveBins; ++b) {
@@ -2585,10 +2586,12 @@ louvain_status louvain_autotune(louvain_ctx *x, int32_t max_runs, char *json, si
     for (int v : cands) {
       if (runs >= max_runs) break;
       Sched t = best;
-      for (int b = 0; b < kMoveBins; ++b) t.move[b] = b == kBigBin ? std::min(v, 3) : v;
-      for (int b = 0; b < kMergeBins; ++b) t.merge[b] = b == kBigBin ? std::min(v, 3) : v;
+      if (v > 0) {
+        for (int b = 0; b < kMoveBins; ++b) t.move[b] = b == kBigBin ? std::min(v, 3) : v;
+        for (int b = 0; b < kMergeBins; ++b) t.merge[b] = b == kBigBin ? std::min(v, 3) : v;
+      }
       if ((st = run_once(t, true, &ms))) goto fail;
-      note("blocks", t, ms);
+      note(v > 0 ? "blocks" : "blocks current", t, ms);
       for (int b = 0; b < kMoveBins; ++b)
         if (mv_kid[b] >= 0 && x->prof.launches[mv_kid[b]] > 0 && x->prof.ms[mv_kid[b]] < mv_best[b]) {
           mv_best[b] = x->prof.ms[mv_kid[b]];
