@@ -96,6 +96,26 @@ def test_autotune_keeps_results():
     check_single(g, again)
 
 
+def test_autotune_measures_the_current_blocks_first():
+    """The blocks-per-SM step times the current values before the
+    candidates, so a bin keeps its value unless a candidate's kernel time
+    beats it; the tuned schedule still gives the oracle's result."""
+    g = gg.rmat(13, 16, seed=4)
+    with lv.Louvain(lv.DeviceCSR.from_host(g)) as ctx:
+        start = ctx.schedule()
+        rep = ctx.autotune(max_runs=40)
+        steps = [t["step"] for t in rep["trials"]]
+        assert "blocks current" in steps
+        k = steps.index("blocks current")
+        assert steps[k + 1] == "blocks"
+        current = rep["trials"][k]["schedule"]
+        blocks = slice(3, 19)  # blocks per SM of the local-moving and aggregation bins
+        assert current[blocks] == [start[f] for f in lv.SCHEDULE_FIELDS][blocks]
+        assert rep["tuned_ms"] <= rep["start_ms"] + 1e-9
+        res = ctx.result()
+    check_single(g, res)
+
+
 def test_autotune_batch():
     graphs = [gg.batched_sbm(k) for k in (0, 1, 3, 8)]
     union, vo = gg.concat(graphs)
