@@ -17,8 +17,7 @@
 // first call on a device is its set-up: it loads the library's device code
 // there (which reserves the array), looks the array's device address up
 // (cudaGetSymbolAddress) and keeps it for the rest of the process.  Make
-// that first call before any stream capture begins and before the caller's
-// own pool claims the device's memory.
+// that first call before the caller's own pool claims the device's memory.
 //
 // The CSR is the caller's and is read without a prior validation pass, so
 // the kernel checks every row before it reads the row's entries:
