@@ -345,10 +345,11 @@ louvain_status louvain_modularity_of(const louvain_graph *graph, const int32_t *
  * beyond that).  Scratch lives in a fixed 8 MiB array inside the library
  * that every GPU loading the library keeps until exit; calls share it, so
  * calls that overlap on the GPU race.  The first call on a device does the
- * set-up: it loads the library's device code there (which reserves the
- * array) and looks the array's address up once for the rest of the process.
- * Make that first call before your own pool claims the device's memory;
- * do not use the library on a device after cudaDeviceReset of it.  The CSR is checked on the device before any entry
+ * set-up: it loads the library's device code there, which reserves the
+ * array; make it before your own pool claims the device's memory.  Every
+ * call looks the array's address up again (no allocation once the code is
+ * loaded), so a call after cudaDeviceReset of the device does that set-up
+ * again.  The CSR is checked on the device before any entry
  * is read: offsets[0] = 0, offsets[n] = nnz, every row within [0, nnz) and
  * not decreasing, columns and membership ids in [0, n), weights > 0
  * (LOUVAIN_E_INVAL otherwise); 2m >= 2^32 gives LOUVAIN_E_OVERFLOW. */

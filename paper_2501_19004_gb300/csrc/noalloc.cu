@@ -15,16 +15,16 @@
 // overlap on the GPU (other threads, other streams) race and give wrong
 // results; serialise them.  Each call clears the part it uses first.  The
 // first call on a device is its set-up: it loads the library's device code
-// there (which reserves the array), looks the array's device address up
-// (cudaGetSymbolAddress) and keeps it for the rest of the process.  Make
-// that first call before the caller's own pool claims the device's memory.
+// there, which reserves the array; make it before the caller's own pool
+// claims the device's memory.  Every call looks the array's device address
+// up again (cudaGetSymbolAddress, which allocates nothing once the code is
+// loaded), so no address outlives a reset of the device.
 //
 // The CSR is the caller's and is read without a prior validation pass, so
 // the kernel checks every row before it reads the row's entries:
 // 0 <= offsets[i] <= offsets[i+1] <= nnz, and offsets[0] = 0, offsets[n] =
 // nnz are read back first (two 8-byte copies into a host array).
 #include <cstdio>
-#include <mutex>
 
 #include "../../include/louvain.h"
 #include "internal.h"
@@ -39,9 +39,6 @@ constexpr int64_t kNoAllocWords = kNoAllocCounters + 1 + kNoAllocMaxVertices;
 // Layout: [0] internal weight S_in, [1] total weight 2m, [2] low halves of
 // Sigma_c^2, [3] high halves, [4] error flag, [5 ...] Sigma_c per community.
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocWords];
-
-std::mutex g_setup_mu;
-unsigned long long *g_scratch_ptr[64] = {};
 
 __global__ void k_na_clear(unsigned long long *scr, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n + kNoAllocCounters + 1;
@@ -108,21 +105,13 @@ __global__ void k_na_sigma_sq(int64_t n, unsigned long long *scr) {
   }
 }
 
-// Device address of the scratch array on the current device.  The first
-// call on a device looks it up (cudaGetSymbolAddress) and caches it.
+// Device address of the scratch array on the current device, looked up on
+// every call.
 cudaError_t scratch_for_current_device(unsigned long long **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = (unsigned long long *)p;
-  }
-  *out = g_scratch_ptr[dev];
+  *out = (unsigned long long *)p;
   return cudaSuccess;
 }
 
