@@ -247,6 +247,27 @@ def test_learned_skip_run():
     assert oracle.modularity(g, r1.membership)[1:] == (r1.q_num, r1.q_den)
 
 
+@pytest.mark.parametrize("schedule", [dict(), dict(concurrent=1)])
+def test_stored_predictor_run_rmat22(schedule):
+    """The learned form with the stored model and its settings on R-MAT 22
+    (hubs of degree above 32768 in both passes, completion steps): a valid
+    partition whose exact Q the oracle confirms, within 1e-3 of plain, and
+    repeated runs that agree bit for bit."""
+    from paper_2501_19004_gb300 import predictor
+    g = gg.rmat(22, 16, seed=7)
+    dg = lv.DeviceCSR.from_host(g)
+    plain = lv.run(dg)
+    with lv.Louvain(dg, predictor.default_config()) as ctx:
+        ctx.set_schedule(schedule)
+        a = ctx.run().result()
+        b = ctx.run().result()
+        st = ctx.stats()
+    assert np.array_equal(a.membership, b.membership) and (a.q_num, a.q_den) == (b.q_num, b.q_den)
+    assert st["skipped"] > 0
+    assert oracle.modularity(g, a.membership)[1:] == (a.q_num, a.q_den)
+    assert abs(a.modularity - plain.modularity) <= 1e-3, (a.modularity, plain.modularity)
+
+
 def test_untrained_threshold_zero_is_plain_plus_sweeps():
     g = gg.rmat(13, 16, seed=9)
     p = np.zeros(omlp.N_PARAMS, dtype=np.float32)  # logit 0 -> p = 0.5 >= threshold 0.25: nothing skipped
