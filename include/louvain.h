@@ -156,8 +156,11 @@ typedef struct {
                                     moving, the partition P is refined and the
                                     refined partition is aggregated; the next pass
                                     starts every super-vertex in its community of P.
-                                    Refinement: one sweep over the buckets of
-                                    (vertex, pass, iteration 255); a vertex that is
+                                    Refinement: one sweep over 4B buckets of
+                                    (vertex, pass, iteration 255), the hash of the
+                                    schedule with 4B in place of B (fewer
+                                    simultaneous decisions than local moving); a
+                                    vertex that is
                                     still a singleton of the refined partition and
                                     well connected to its community C of P
                                     (2m K_{i->C} >= K_i (Sigma_C - K_i), K_{i->C}

@@ -243,8 +243,9 @@ def aggregate(g, membership, ncomm: int):
     return o, c[:nnz.value], ww[:nnz.value]
 
 
-def refine(g, bound, pass_: int = 0, seed: int = 0, buckets: int = 4) -> np.ndarray:
-    """The Leiden refinement of partition `bound` (ids in [0, n)) on g:
+def refine(g, bound, pass_: int = 0, seed: int = 0, buckets: int = 16) -> np.ndarray:
+    """The Leiden refinement of partition `bound` (ids in [0, n)) on g, one
+    sweep over `buckets` buckets (a whole run with B buckets refines over 4B):
     refined ids, each the vertex id of one member (leiden_refine in
     louvain_oracle.c)."""
     lib = _load()

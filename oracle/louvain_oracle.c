@@ -298,6 +298,8 @@ out:
   return li_done;
 }
 
+#define OR_REFINE_BUCKETS_PER_B 4
+
 /* ---- Leiden refinement (Traag, Waltman & van Eck 2019, the refinement of
  * the partition P that local moving produced; the paper's Sec. 5.2 and
  * Sec. 6 expect its findings to extend to Leiden) ----
@@ -308,7 +310,10 @@ out:
  *     well connected to its community C = P(v):
  *       2m K_{v->C} >= K_v (Sigma_C - K_v)
  *     where K_{v->C} sums v's edges to the other members of C.
- *   - One sweep over the buckets of (v, pass, iteration 255).  In a bucket,
+ *   - One sweep over R buckets of (v, pass, iteration 255); a whole run
+ *     uses R = 4B (OR_REFINE_BUCKETS_PER_B), so that fewer decisions are
+ *     simultaneous than in local moving: Leiden visits vertices one at a
+ *     time, each seeing the merges made before it.  In a bucket,
  *     every such vertex decides against the snapshot (Cr, Sr) exactly as in
  *     local moving, but sees only neighbours inside its own community C: it
  *     picks the refined community T (within C) with the largest
@@ -352,9 +357,10 @@ static int filter_to_bounds(const graph_t *g, const int32_t *bound, graph_t *out
 }
 
 /* Refined partition Cr (raw ids: a member's vertex id) of G' under P =
- * bound, whose community totals are Sigma_b; K are the vertex weights. */
+ * bound, whose community totals are Sigma_b; K are the vertex weights; the
+ * sweep runs over `rbuckets` buckets of the schedule's hash. */
 static int leiden_refine(const graph_t *g, const int32_t *bound, const int64_t *K, const int64_t *Sigma_b,
-                         int64_t two_m, int32_t pass, const or_config *cfg, int32_t *Cr) {
+                         int64_t two_m, int32_t pass, int32_t rbuckets, uint64_t seed, int32_t *Cr) {
   const int64_t n = g->n;
   graph_t F = {0, 0, NULL, NULL, NULL};
   int st = filter_to_bounds(g, bound, &F);
@@ -379,10 +385,10 @@ static int leiden_refine(const graph_t *g, const int32_t *bound, const int64_t *
     Cr[v] = (int32_t)v;
     Sr[v] = K[v];
   }
-  for (int32_t b = 0; b < cfg->buckets; ++b) {
+  for (int32_t b = 0; b < rbuckets; ++b) {
     int64_t na = 0;
     for (int64_t v = 0; v < n; ++v)
-      if (elig[v] && !chosen[v] && (int32_t)bucket_of(v, pass, 255, cfg->schedule_seed, cfg->buckets) == b)
+      if (elig[v] && !chosen[v] && (int32_t)bucket_of(v, pass, 255, seed, rbuckets) == b)
         A[na++] = v;
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t a = 0; a < na; ++a)
@@ -716,7 +722,8 @@ int or_aggregate(int64_t n, const int64_t *off, const int32_t *col, const int32_
 
 /* The Leiden refinement alone (leiden_refine): the refined partition of
  * the input graph under the partition `bound` (ids in [0, n)), with vertex
- * weights from the rows, at pass index `pass` of the bucket hash.
+ * weights from the rows, at pass index `pass` of the bucket hash, in one
+ * sweep over `buckets` buckets (a whole run's sweep uses 4B).
  * refined_out [n]: raw refined ids (a member's vertex id). */
 int or_refine(int64_t n, const int64_t *off, const int32_t *col, const int32_t *w, const int32_t *bound,
               int32_t pass, uint64_t seed, int32_t buckets, int32_t *refined_out) {
@@ -734,11 +741,7 @@ int or_refine(int64_t n, const int64_t *off, const int32_t *col, const int32_t *
     Sb[bound[i]] += K[i];
     two_m += K[i];
   }
-  or_config cfg;
-  memset(&cfg, 0, sizeof cfg);
-  cfg.buckets = buckets;
-  cfg.schedule_seed = seed;
-  if (!st) st = leiden_refine(&G, bound, K, Sb, two_m, pass, &cfg, refined_out);
+  if (!st) st = leiden_refine(&G, bound, K, Sb, two_m, pass, buckets, seed, refined_out);
   free(K);
   free(Sb);
   graph_free(&G);
@@ -763,7 +766,7 @@ int or_louvain(int64_t n, const int64_t *off, const int32_t *col, const int32_t 
                const or_config *cfg, int32_t *membership_out, int64_t *iter_stats,
                int64_t *pass_stats, int64_t *summary, double *q_out) {
   if (!cfg || cfg->max_passes < 0 || cfg->max_iterations < 1 || cfg->max_iterations > 255 ||
-      cfg->buckets < 1 || cfg->pickless_period < 0 || cfg->refine < 0 || cfg->refine > 1)
+      cfg->buckets < 1 || cfg->buckets > 65536 || cfg->pickless_period < 0 || cfg->refine < 0 || cfg->refine > 1)
     return OR_E_INVAL;
   if (validate_input(n, off, col, w)) return OR_E_INVAL;
 #ifdef _OPENMP
@@ -834,7 +837,8 @@ int or_louvain(int64_t n, const int64_t *off, const int32_t *col, const int32_t 
     int32_t *agg = Cp;
     int64_t nagg = gamma;
     if (cfg->refine) {
-      st = leiden_refine(&G, Cp, K, Sigma, two_m, lp, cfg, Cr);
+      st = leiden_refine(&G, Cp, K, Sigma, two_m, lp, OR_REFINE_BUCKETS_PER_B * cfg->buckets,
+                         cfg->schedule_seed, Cr);
       if (st) goto done;
       agg = Cr;
       nagg = count_distinct(Cr, np, np);

@@ -982,11 +982,16 @@ louvain_status capture_iteration(louvain_ctx *x, const GView &g, int wk, int pas
   return LOUVAIN_OK;
 }
 
+// The refinement's sweep runs over this many buckets per bucket B of local
+// moving (Leiden visits vertices one at a time, each seeing the merges made
+// before it; more buckets make fewer decisions simultaneous).
+constexpr int kRefineBucketsPerB = 4;
+
 // Leiden refinement of P = C' on G' (the refine field of include/louvain.h):
 // the filtered rows go to the ping-pong buffer that this pass's aggregation
-// writes afterwards; one sweep over the buckets of (vertex, pass, iteration
-// 255) runs the local-moving decision kernels on the filtered view with the
-// refined partition, and resolve + flags after every bucket.
+// writes afterwards; one sweep over the 4B buckets of (vertex, pass,
+// iteration 255) runs the local-moving decision kernels on the filtered view
+// with the refined partition, and resolve + flags after every bucket.
 louvain_status refine_phase(louvain_ctx *x, const GView &g, int wk, int slot, int pass) {
   const louvain_config &cfg = x->cfg;
   cudaStream_t s = x->stream;
@@ -1013,6 +1018,7 @@ louvain_status refine_phase(louvain_ctx *x, const GView &g, int wk, int slot, in
   refine_rows(r, wk, x->num_sms, s);
   const GView f{g.n, g.begin, x->pend[slot], x->pcol[slot], r.fw};
   const uint32_t salt = bucket_salt(pass, 255, cfg.schedule_seed);
+  const int rbuckets = kRefineBucketsPerB * cfg.buckets;  // fewer simultaneous decisions than local moving
   MoveArgs a{};
   a.g = f;
   a.Cp = x->Cr;
@@ -1022,7 +1028,7 @@ louvain_status refine_phase(louvain_ctx *x, const GView &g, int wk, int slot, in
   a.two_m = x->two_m;
   a.pickless = 0;
   a.salt = salt;
-  a.nbuckets = (uint32_t)cfg.buckets;
+  a.nbuckets = (uint32_t)rbuckets;
   for (int k = 0; k < kMoveBins; ++k) a.bins[k] = x->bins[k];
   a.mv_vertex = x->mv_vertex;
   a.mv_target = x->mv_target;
@@ -1055,12 +1061,12 @@ louvain_status refine_phase(louvain_ctx *x, const GView &g, int wk, int slot, in
   big.apply_Cp = x->Cr;
   big.apply_Sigma = x->Sr;
   big.accum_blocks = x->sched.move[kBigBin];
-  for (int b = 0; b < cfg.buckets; ++b) {
+  for (int b = 0; b < rbuckets; ++b) {
     LV_CK(cudaMemsetAsync(x->d_ctr, 0, offsetof(Counters, it_gain_lo), s));
     a.bucket = (uint32_t)b;
     move_bucket(a, big, wk, x->num_sms, s, x->prof.mask ? &x->prof : nullptr, x->side.fork ? &x->side : nullptr);
     refine_resolve(r, x->mv_vertex, x->mv_target, x->recv, x->num_sms, s);
-    refine_flags(r, salt, (uint32_t)cfg.buckets, (uint32_t)b, x->num_sms, s);
+    refine_flags(r, salt, (uint32_t)rbuckets, (uint32_t)b, x->num_sms, s);
   }
   LV_CK(cudaGetLastError());
   return read_counters(x);  // hashtable and range errors of the refinement

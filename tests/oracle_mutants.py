@@ -71,6 +71,7 @@ MUTANTS = {
     "refine: well-connectedness reversed": ("elig[v] = (i128)two_m * kin >= ", "elig[v] = (i128)two_m * kin < "),
     "refine: well-connectedness without -K_v": ("(Sigma_b[bound[v]] - K[v]);", "Sigma_b[bound[v]];"),
     "refine: target total not updated": ("      Sr[t] += K[v];\n", ""),
+    "Leiden: refinement over B buckets, not 4B": ("OR_REFINE_BUCKETS_PER_B * cfg->buckets", "cfg->buckets"),
     "Leiden: next pass from singletons": ("if (cfg->refine && lp > 0) {", "if (0) {"),
     "Leiden: pass cap returns the refinement": ("if (!pending && cfg->refine && passes > 0)", "if (0)"),
 }

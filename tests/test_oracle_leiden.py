@@ -190,6 +190,45 @@ def test_aggregating_a_refinement_keeps_the_partition_q():
 
 
 # ------------------------------------------------------------ whole runs
+@pytest.mark.parametrize("B", [1, 4])
+def test_whole_run_refines_over_four_times_the_buckets(B):
+    """A whole run refines each pass's P in one sweep over 4B buckets: the
+    second pass's n' is the number of refined communities of that sweep
+    (and not of a sweep over B buckets, which differs on every graph
+    here)."""
+    for g in (gg.rmat(12, 16, seed=7), gg.sbm(400, 40, 0.25, 0.02, seed=3), gg.grid(48, 0.02, seed=5),
+              gg.rmat(11, 8, seed=3, weight_range=(1, 5))):
+        P = oracle.louvain(g, oracle.Config(refine=True, max_passes=1, buckets=B)).membership  # the pass cap gives P
+        r = oracle.louvain(g, oracle.Config(refine=True, max_passes=2, buckets=B))
+        assert r.passes == 2
+        n1 = int(r.pass_stats[1][0])
+        assert np.unique(oracle.refine(g, P, pass_=0, buckets=4 * B)).size == n1
+        assert np.unique(oracle.refine(g, P, pass_=0, buckets=B)).size != n1
+
+
+@pytest.mark.parametrize("B", [1, 4])
+def test_next_pass_starts_from_p(B):
+    """Disjoint cliques: pass 0 finds the cliques (P) and the refinement
+    splits some of them into pieces.  The next pass starts every piece in
+    its clique's community of P, which is already optimal, so its first
+    iteration moves nothing and the run converges there; from singletons the
+    pieces of a clique would have to move together again."""
+    split = 0
+    for sizes in ((5, 5), (6, 7, 8), (12, 12, 12, 12)):
+        n = sum(sizes)
+        W = np.zeros((n, n), dtype=np.int64)
+        o = 0
+        for k in sizes:
+            W[o:o + k, o:o + k] = 1
+            o += k
+        np.fill_diagonal(W, 0)
+        r = oracle.louvain(csr_from_dense(W), oracle.Config(refine=True, buckets=B))
+        assert r.passes == 2 and r.communities == len(sizes)
+        assert r.iter_stats[1][0][1] == 0 and r.pass_stats[1][2] == 1
+        split += int(r.pass_stats[1][0] > len(sizes))  # more pieces than cliques
+    assert split >= 1
+
+
 def test_leiden_two_disjoint_cliques():
     W = np.zeros((10, 10), dtype=np.int64)
     for blk in (range(0, 5), range(5, 10)):
